@@ -1,0 +1,31 @@
+"""Plain, slow FP64 CPU oracle for GEM's multi-vector scoring path (arXiv 2603.20336).
+
+TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+benchmark's CPU-baseline leg may import this package; the product path (the CUDA
+library and its Python binding) never does, and this package never imports the
+product.  Each function restates one definition of the paper in float64 with
+numpy; a library matmul or sort may serve as a step, with no blocking or
+reordering beyond a loop over documents.
+
+Contents and the passage each follows:
+  chamfer, score_all, score_ids   Sec. 3.1, Definition 1 (Eq. 1), Sim = inner product
+  topk                            Sec. 3.1, problem statement (Eq. 2); ties by lower id
+  rerank                          Algorithm 5, final step: exact CH over a candidate pool
+  assign_codes                    Sec. 4.1.1 / Sec. 4.2.2: NN(x) = nearest centroid of C_quant
+  qch_distance, qch_similarity    Sec. 4.5.3, Eq. 16, with d_X = 1 - <.,.> (Sec. 4.2.1)
+  k1_for                          Sec. 5.1 parameter settings: |C_quant| = 2^floor(log2(16 sqrt(#vectors)))
+  bf16_round, fp8_e4m3_quantize   storage formats of the low-precision path (not in the paper)
+  maxsim_grad, contrastive_*      gradient of Eq. 1 (not in the paper)
+  kmeans_update                   Sec. 4.1.1, one Lloyd update of the stage-1 k-means
+
+Pinned by tests/test_oracle_pins.py against brute force, closed forms, invariants
+and the paper's worked example, except:
+  parity unpinned: kmeans_update (k-means is a heuristic; only its fixed-point
+  invariants are tested).
+"""
+from .maxsim import (  # noqa: F401
+    chamfer, score_all, score_ids, topk, rerank, recall_at_k,
+    assign_codes, qch_distance, qch_similarity, qch_score_all, qch_score_ids, k1_for,
+    bf16_round, fp8_e4m3_round, fp8_e4m3_quantize,
+    maxsim_grad, contrastive_loss, contrastive_dscores, kmeans_update,
+)

@@ -1,0 +1,337 @@
+"""FP64 reference definitions (test infrastructure only; see the package docstring).
+
+All inputs are converted to float64 before any arithmetic.  Vector sets are given
+CSR-packed: rows vecs[offsets[i]:offsets[i+1]] are the vectors of set i.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# Rows of documents multiplied against one query at a time.  This only bounds
+# memory: every document's score is computed independently of the others.
+_DOC_ROWS_PER_STEP = 1 << 21
+
+
+def _f64(x) -> np.ndarray:
+    if hasattr(x, "detach"):
+        x = x.detach().cpu().numpy()
+    return np.asarray(x, dtype=np.float64)
+
+
+def _i64(x) -> np.ndarray:
+    if hasattr(x, "detach"):
+        x = x.detach().cpu().numpy()
+    return np.asarray(x, dtype=np.int64)
+
+
+# ---------------------------------------------------------------------------
+# Chamfer / MaxSim (Sec. 3.1, Definition 1, Eq. 1)
+# ---------------------------------------------------------------------------
+
+def chamfer(A, B) -> float:
+    """CH(A, B) = sum over a in A of max over b in B of <a, b>.
+
+    Definition 1 (Eq. 1) with Sim taken as the inner product, which is the cosine
+    similarity on the unit-norm vectors every workload uses.
+    """
+    A = _f64(A)
+    B = _f64(B)
+    sims = A @ B.T                   # sims[i, j] = <a_i, b_j>
+    return float(sims.max(axis=1).sum())
+
+
+def score_all(q, q_offsets, vecs, offsets) -> np.ndarray:
+    """CH(Q_b, P_n) for every query set b and every stored set n: float64 [B, N].
+
+    The multi-vector retrieval problem (Eq. 2) ranks every P in D by CH(Q, P);
+    this returns all of those scores.
+    """
+    q = _f64(q)
+    qo = _i64(q_offsets)
+    off = _i64(offsets)
+    n_sets = len(off) - 1
+    out = np.empty((len(qo) - 1, n_sets), dtype=np.float64)
+    # group documents so that one matmul covers about _DOC_ROWS_PER_STEP rows
+    groups = []
+    d0 = 0
+    while d0 < n_sets:
+        d1 = int(np.searchsorted(off, off[d0] + _DOC_ROWS_PER_STEP, side="right")) - 1
+        d1 = max(d1, d0 + 1)
+        d1 = min(d1, n_sets)
+        groups.append((d0, d1))
+        d0 = d1
+    for d0, d1 in groups:
+        r0, r1 = int(off[d0]), int(off[d1])
+        X = _f64(vecs[r0:r1])
+        starts = off[d0:d1] - r0
+        for b in range(len(qo) - 1):
+            Q = q[qo[b]:qo[b + 1]]
+            sims = Q @ X.T                                   # [m_q, rows]
+            per_doc_max = np.maximum.reduceat(sims, starts, axis=1)   # max over each doc's rows
+            out[b, d0:d1] = per_doc_max.sum(axis=0)          # sum over the query's vectors
+    return out
+
+
+def score_ids(q, q_offsets, vecs, offsets, cand_offsets, cand_ids) -> np.ndarray:
+    """CH(Q_b, P_id) for each id of query b's candidate list (Algorithm 5, candidate scoring).
+
+    Returns float64 aligned with cand_ids.  A negative id stands for "no candidate"
+    and scores -inf.
+    """
+    q = _f64(q)
+    qo = _i64(q_offsets)
+    off = _i64(offsets)
+    co = _i64(cand_offsets)
+    ids = _i64(cand_ids)
+    out = np.empty(len(ids), dtype=np.float64)
+    for b in range(len(qo) - 1):
+        Q = q[qo[b]:qo[b + 1]]
+        for t in range(co[b], co[b + 1]):
+            i = ids[t]
+            out[t] = -np.inf if i < 0 else chamfer(Q, vecs[off[i]:off[i + 1]])
+    return out
+
+
+# ---------------------------------------------------------------------------
+# top-k (Eq. 2) and the final exact rerank of Algorithm 5
+# ---------------------------------------------------------------------------
+
+def topk(scores, k: int, ids=None):
+    """k-argmax of one row of scores: sorted by score descending, ties by lower id.
+
+    Returns (ids int64 [min(k, n)], scores float64 [min(k, n)]).
+    """
+    s = _f64(scores)
+    i = np.arange(len(s), dtype=np.int64) if ids is None else _i64(ids)
+    order = np.lexsort((i, -s))      # primary key: -score, secondary: id
+    order = order[:k]
+    return i[order], s[order]
+
+
+def rerank(q, q_offsets, vecs, offsets, pool_ids, k: int):
+    """Exact-CH rerank of each query's candidate pool, then top-k (Algorithm 5, last step).
+
+    pool_ids: int64 [B, R] (negative entries are empty slots).
+    Returns (ids int64 [B, k], scores float64 [B, k]); short rows are padded with
+    id -1 and score -inf.
+    """
+    pool = _i64(pool_ids)
+    B, R = pool.shape
+    co = np.arange(B + 1, dtype=np.int64) * R
+    s = score_ids(q, q_offsets, vecs, offsets, co, pool.reshape(-1)).reshape(B, R)
+    out_i = np.full((B, k), -1, dtype=np.int64)
+    out_s = np.full((B, k), -np.inf)
+    for b in range(B):
+        keep = pool[b] >= 0
+        ii, ss = topk(s[b][keep], k, pool[b][keep])
+        out_i[b, :len(ii)] = ii
+        out_s[b, :len(ss)] = ss
+    return out_i, out_s
+
+
+def recall_at_k(found_ids, true_ids) -> float:
+    """|found ∩ true| / |true| for one query (recall against the exact top-k)."""
+    t = set(int(x) for x in np.asarray(true_ids).ravel() if x >= 0)
+    f = set(int(x) for x in np.asarray(found_ids).ravel() if x >= 0)
+    return len(t & f) / max(1, len(t))
+
+
+# ---------------------------------------------------------------------------
+# Codes and the quantized Chamfer estimate
+# ---------------------------------------------------------------------------
+
+def assign_codes(X, C) -> np.ndarray:
+    """NN(x): index of the centroid of C_quant with the largest inner product with x.
+
+    Sec. 4.1.1 assigns each vector to its nearest centroid; with unit-norm vectors
+    and unit-norm centroids the nearest centroid under d_X = 1 - <x, c> (Sec. 4.2.1)
+    is the one with the largest inner product.  Ties go to the lowest index.
+    Returns int64 [n].
+    """
+    C = _f64(C)
+    n = len(X)
+    out = np.empty(n, dtype=np.int64)
+    step = max(1, (1 << 24) // max(1, len(C)))
+    for s in range(0, n, step):
+        sims = _f64(X[s:s + step]) @ C.T
+        out[s:s + step] = np.argmax(sims, axis=1)      # first maximum = lowest index
+    return out
+
+
+def qch_distance(q_codes, p_codes, C) -> float:
+    """qCH(Q, P) = sum over q of min over p of d_X(NN(q), NN(p)) (Sec. 4.5.3, Eq. 16).
+
+    d_X(x, y) = 1 - <x, y> (cosine form, Sec. 4.2.1); both sides are quantized to
+    their codebook entries, as Eq. 16 writes NN(q) and NN(p).
+    """
+    C = _f64(C)
+    a = C[_i64(q_codes)]
+    b = C[_i64(p_codes)]
+    dist = 1.0 - a @ b.T
+    return float(dist.min(axis=1).sum())
+
+
+def qch_similarity(q_codes, p_codes, C) -> float:
+    """The similarity form of qCH: sum over q of max over p of <NN(q), NN(p)>.
+
+    Equals m_q - qCH(Q, P) up to rounding; ranking by it is ranking by qCH.
+    """
+    C = _f64(C)
+    a = C[_i64(q_codes)]
+    b = C[_i64(p_codes)]
+    return float((a @ b.T).max(axis=1).sum())
+
+
+def qch_score_all(q_codes, q_offsets, p_codes, offsets, C) -> np.ndarray:
+    """qch_similarity(Q_b, P_n) for every query b and stored set n: float64 [B, N]."""
+    C = _f64(C)
+    qo = _i64(q_offsets)
+    off = _i64(offsets)
+    pc = _i64(p_codes)
+    qc = _i64(q_codes)
+    starts = off[:-1]
+    out = np.empty((len(qo) - 1, len(off) - 1))
+    for b in range(len(qo) - 1):
+        a = C[qc[qo[b]:qo[b + 1]]]
+        table = a @ C.T                          # <C_{a_i}, C_c> for every centroid c
+        sims = table[:, pc]                      # [m_q, rows]: <C_{a_i}, C_{NN(p_j)}>
+        out[b] = np.maximum.reduceat(sims, starts, axis=1).sum(axis=0)
+    return out
+
+
+def qch_score_ids(q_codes, q_offsets, p_codes, offsets, cand_offsets, cand_ids, C) -> np.ndarray:
+    """qch_similarity over each query's candidate list, aligned with cand_ids."""
+    qo = _i64(q_offsets)
+    off = _i64(offsets)
+    pc = _i64(p_codes)
+    qc = _i64(q_codes)
+    co = _i64(cand_offsets)
+    ids = _i64(cand_ids)
+    out = np.empty(len(ids))
+    for b in range(len(qo) - 1):
+        for t in range(co[b], co[b + 1]):
+            i = ids[t]
+            out[t] = qch_similarity(qc[qo[b]:qo[b + 1]], pc[off[i]:off[i + 1]], C)
+    return out
+
+
+def k1_for(n_vectors: int) -> int:
+    """|C_quant| = 2^floor(log2(16 * sqrt(#vectors))) (Sec. 5.1, parameter settings)."""
+    return 1 << int(math.floor(math.log2(16.0 * math.sqrt(n_vectors))))
+
+
+# ---------------------------------------------------------------------------
+# Storage formats of the low-precision path, written from the format definitions
+# ---------------------------------------------------------------------------
+
+def _round_to_format(x: np.ndarray, mant_bits: int, min_exp: int) -> np.ndarray:
+    """Round float64 values to the nearest number with `mant_bits` fraction bits
+    (normal exponent >= min_exp, subnormal spacing 2^(min_exp - mant_bits)),
+    ties to even.  No overflow handling."""
+    x = np.asarray(x, dtype=np.float64)
+    ax = np.abs(x)
+    _, e = np.frexp(ax)                 # ax = f * 2^e, f in [0.5, 1)
+    e = e - 1                           # ax in [2^e, 2^(e+1))
+    e = np.maximum(e, min_exp)
+    quantum = np.ldexp(1.0, e - mant_bits)
+    r = np.round(ax / quantum) * quantum     # np.round: half to even; the division is exact
+    return np.copysign(r, x)
+
+
+def bf16_round(x) -> np.ndarray:
+    """float32 -> bfloat16 (8 exponent bits, 7 fraction bits), round to nearest even.
+
+    Returned as float32 values.  Finite inputs only; results beyond the largest
+    bfloat16 become +-inf.
+    """
+    x = np.asarray(x, dtype=np.float32).astype(np.float64)
+    r = _round_to_format(x, 7, -126)
+    r = np.where(np.abs(r) > 3.3895313892515355e38, np.copysign(np.inf, x), r)
+    return r.astype(np.float32)
+
+
+FP8_E4M3_MAX = 448.0
+
+
+def fp8_e4m3_round(x) -> np.ndarray:
+    """float -> FP8 E4M3 (4 exponent bits, bias 7, 3 fraction bits, no infinities),
+    round to nearest even, saturating to +-448.  Returned as float64 values."""
+    x = np.asarray(x, dtype=np.float64)
+    r = _round_to_format(x, 3, -6)
+    return np.clip(r, -FP8_E4M3_MAX, FP8_E4M3_MAX)
+
+
+def fp8_e4m3_quantize(X):
+    """Per-vector scaled E4M3 storage: s_j = max_k |x_jk| / 448 (FP32 division),
+    code_jk = E4M3(x_jk / s_j) with the division in FP32, round to nearest even,
+    saturating.  A zero vector gets s_j = 1.  Returns (codes float64 [n, d] holding
+    the E4M3 values, scales float32 [n]); the dequantised vector is codes * scale."""
+    X = np.asarray(X, dtype=np.float32)
+    amax = np.abs(X).max(axis=1)
+    scale = (amax / np.float32(FP8_E4M3_MAX)).astype(np.float32)
+    scale = np.where(amax == 0, np.float32(1.0), scale).astype(np.float32)
+    ratio = (X / scale[:, None]).astype(np.float32)         # IEEE float32 division
+    return fp8_e4m3_round(ratio.astype(np.float64)), scale
+
+
+# ---------------------------------------------------------------------------
+# Gradient of Eq. 1 and the contrastive loss used to exercise it
+# ---------------------------------------------------------------------------
+
+def maxsim_grad(Q, P):
+    """Gradients of CH(Q, P) = sum_i max_j <q_i, p_j> for a fixed argmax.
+
+    j*(i) = argmax_j <q_i, p_j> (lowest j on ties); dCH/dq_i = p_{j*(i)} and
+    dCH/dp_j = sum of q_i over the i with j*(i) = j.  Returns (dQ, dP, jstar).
+    """
+    Q = _f64(Q)
+    P = _f64(P)
+    sims = Q @ P.T
+    jstar = np.argmax(sims, axis=1)
+    dQ = P[jstar].copy()
+    dP = np.zeros_like(P)
+    np.add.at(dP, jstar, Q)
+    return dQ, dP, jstar
+
+
+def contrastive_loss(S, tau: float) -> float:
+    """L = (1/B) sum_b CE(softmax(S_b / tau), target 0): the positive sits at column 0."""
+    S = _f64(S) / tau
+    m = S.max(axis=1, keepdims=True)
+    lse = m[:, 0] + np.log(np.exp(S - m).sum(axis=1))
+    return float(np.mean(lse - S[:, 0]))
+
+
+def contrastive_dscores(S, tau: float) -> np.ndarray:
+    """dL/dS[b, d] = (softmax(S_b / tau)[d] - [d == 0]) / (tau * B)."""
+    S = _f64(S)
+    B = S.shape[0]
+    z = S / tau
+    z = z - z.max(axis=1, keepdims=True)
+    p = np.exp(z)
+    p /= p.sum(axis=1, keepdims=True)
+    p[:, 0] -= 1.0
+    return p / (tau * B)
+
+
+# ---------------------------------------------------------------------------
+# Stage-1 k-means (Sec. 4.1.1) -- parity unpinned (heuristic)
+# ---------------------------------------------------------------------------
+
+def kmeans_update(X, codes, C_prev) -> np.ndarray:
+    """One spherical Lloyd update: each centroid becomes the L2-normalised mean of
+    the vectors assigned to it; a centroid with no vectors keeps its old value."""
+    X = _f64(X)
+    C_prev = _f64(C_prev)
+    codes = _i64(codes)
+    k, d = C_prev.shape
+    sums = np.zeros((k, d))
+    np.add.at(sums, codes, X)
+    counts = np.bincount(codes, minlength=k)
+    C = C_prev.copy()
+    nz = counts > 0
+    norms = np.linalg.norm(sums[nz], axis=1, keepdims=True)
+    C[nz] = sums[nz] / np.where(norms > 0, norms, 1.0)
+    return C

@@ -1,0 +1,368 @@
+"""Pins for the FP64 oracle: brute force, closed forms, invariants and the paper's
+worked example.  Nothing here touches the CUDA library."""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _unit(rng, n, d):
+    x = rng.standard_normal((n, d))
+    return x / np.linalg.norm(x, axis=1, keepdims=True)
+
+
+def _brute_ch(A, B):
+    """Eq. 1 with pure-Python loops (inputs are small integers, so FP64 is exact)."""
+    total = 0.0
+    for a in A:
+        best = None
+        for b in B:
+            s = sum(float(x) * float(y) for x, y in zip(a, b))
+            best = s if best is None or s > best else best
+        total += best
+    return total
+
+
+# --------------------------------------------------------------------------- CH
+
+def test_intro_worked_example():
+    g = json.load(open(os.path.join(GOLD, "intro_example.json")))
+    Q = np.array(g["sims"])
+    P = np.eye(4)                      # <q_i, e_j> = sims[i][j]
+    assert oracle.chamfer(Q, P) == pytest.approx(g["ch"], abs=1e-12)
+    _, _, jstar = oracle.maxsim_grad(Q, P)
+    assert list(jstar) == g["argmax"]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_chamfer_matches_brute_force_on_integers(seed):
+    rng = np.random.default_rng(seed)
+    d = int(rng.integers(1, 9))
+    lens = rng.integers(1, 5, size=5)
+    X = rng.integers(-3, 4, size=(int(lens.sum()), d)).astype(np.float64)
+    off = np.concatenate([[0], np.cumsum(lens)])
+    mq = rng.integers(1, 5, size=3)
+    q = rng.integers(-3, 4, size=(int(mq.sum()), d)).astype(np.float64)
+    qo = np.concatenate([[0], np.cumsum(mq)])
+    S = oracle.score_all(q, qo, X, off)
+    for b in range(3):
+        for n in range(5):
+            want = _brute_ch(q[qo[b]:qo[b + 1]], X[off[n]:off[n + 1]])
+            assert S[b, n] == want
+            assert oracle.chamfer(q[qo[b]:qo[b + 1]], X[off[n]:off[n + 1]]) == want
+    co = np.array([0, 2, 2, 5])
+    ids = np.array([4, 0, 1, 1, 3])
+    got = oracle.score_ids(q, qo, X, off, co, ids)
+    want = [S[0, 4], S[0, 0], S[2, 1], S[2, 1], S[2, 3]]
+    assert list(got) == want
+
+
+def test_single_pair_is_dot_product():
+    rng = np.random.default_rng(1)
+    q, p = rng.standard_normal((1, 128)), rng.standard_normal((1, 128))
+    assert oracle.chamfer(q, p) == pytest.approx(math.fsum(q[0] * p[0]), rel=1e-14)
+
+
+def test_single_doc_vector_closed_form():
+    # m_p = 1: every query vector's max is the one product, so CH = <sum_i q_i, p>.
+    rng = np.random.default_rng(2)
+    Q, p = rng.standard_normal((7, 16)), rng.standard_normal((1, 16))
+    assert oracle.chamfer(Q, p) == pytest.approx(float(Q.sum(0) @ p[0]), rel=1e-13)
+
+
+def test_unit_set_against_itself_equals_cardinality():
+    rng = np.random.default_rng(3)
+    for m in (1, 5, 33):
+        P = _unit(rng, m, 128)
+        assert oracle.chamfer(P, P) == pytest.approx(m, abs=1e-12)
+
+
+def test_permutation_invariance_and_asymmetry():
+    rng = np.random.default_rng(4)
+    Q, P = _unit(rng, 6, 32), _unit(rng, 9, 32)
+    base = oracle.chamfer(Q, P)
+    assert oracle.chamfer(Q[rng.permutation(6)], P) == pytest.approx(base, abs=1e-13)
+    assert oracle.chamfer(Q, P[rng.permutation(9)]) == pytest.approx(base, abs=1e-13)
+    # the operands are not interchangeable: a transposed implementation fails here
+    assert abs(oracle.chamfer(P, Q) - base) > 1e-3
+
+
+def test_superset_monotone_and_query_additive():
+    rng = np.random.default_rng(5)
+    Q1, Q2, P, P2 = _unit(rng, 4, 16), _unit(rng, 3, 16), _unit(rng, 5, 16), _unit(rng, 4, 16)
+    assert oracle.chamfer(Q1, np.vstack([P, P2])) >= oracle.chamfer(Q1, P) - 1e-15
+    assert oracle.chamfer(np.vstack([Q1, Q2]), P) == pytest.approx(
+        oracle.chamfer(Q1, P) + oracle.chamfer(Q2, P), abs=1e-13)
+
+
+def test_terms_bounded_by_single_pair_products():
+    rng = np.random.default_rng(6)
+    Q, P = _unit(rng, 8, 64), _unit(rng, 11, 64)
+    sims = Q @ P.T
+    ch = oracle.chamfer(Q, P)
+    assert sims.min(1).sum() - 1e-12 <= ch <= sims.max(1).sum() + 1e-12
+    assert abs(ch) <= len(Q) + 1e-12
+    # dropping one query vector removes exactly its best single-pair product
+    assert ch - oracle.chamfer(Q[1:], P) == pytest.approx(sims[0].max(), abs=1e-13)
+
+
+def test_score_all_on_generated_workload():
+    w = synth.exact_fp32(n_sets=40, n_queries=2)
+    S = oracle.score_all(w.queries.vecs, w.queries.offsets, w.docs.vecs, w.docs.offsets)
+    qv, dv = w.queries.vecs.numpy(), w.docs.vecs.numpy()
+    for b in range(2):
+        for n in (0, 17, 39):
+            Q = qv[w.queries.offsets[b]:w.queries.offsets[b + 1]].astype(np.float64)
+            P = dv[w.docs.offsets[n]:w.docs.offsets[n + 1]].astype(np.float64)
+            want = sum(max(float(np.dot(a, p)) for p in P) for a in Q)
+            assert S[b, n] == pytest.approx(want, abs=1e-12)
+
+
+# --------------------------------------------------------------------------- top-k
+
+def _brute_topk(scores, k, ids):
+    pairs = sorted(zip(scores, ids), key=lambda t: (-t[0], t[1]))
+    return [p[1] for p in pairs[:k]], [p[0] for p in pairs[:k]]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_topk_matches_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 300))
+    s = np.round(rng.standard_normal(n), 1)           # many ties
+    ids = rng.permutation(10 * n)[:n]
+    for k in (1, 5, n, n + 3):
+        got_i, got_s = oracle.topk(s, k, ids)
+        want_i, want_s = _brute_topk(s.tolist(), k, ids.tolist())
+        assert got_i.tolist() == want_i
+        assert got_s.tolist() == want_s
+
+
+def test_topk_all_equal_and_full_sort():
+    got_i, _ = oracle.topk(np.full(50, 0.25), 7)
+    assert got_i.tolist() == list(range(7))
+    s = np.array([3.0, 1.0, 2.0])
+    got_i, got_s = oracle.topk(s, 10)
+    assert got_i.tolist() == [0, 2, 1] and got_s.tolist() == [3.0, 2.0, 1.0]
+
+
+def test_rerank_is_topk_of_exact_scores_over_pool():
+    w = synth.exact_fp32(n_sets=30, n_queries=2)
+    S = oracle.score_all(w.queries.vecs, w.queries.offsets, w.docs.vecs, w.docs.offsets)
+    pool = np.array([[3, 7, 1, 22, 9, -1], [0, 1, 2, 3, 4, 5]])
+    ids, sc = oracle.rerank(w.queries.vecs, w.queries.offsets, w.docs.vecs, w.docs.offsets, pool, 4)
+    for b in range(2):
+        p = pool[b][pool[b] >= 0]
+        want_i, want_s = _brute_topk(S[b, p].tolist(), 4, p.tolist())
+        assert ids[b].tolist() == want_i
+        assert sc[b] == pytest.approx(want_s, abs=1e-12)
+    ids, sc = oracle.rerank(w.queries.vecs, w.queries.offsets[:2], w.docs.vecs, w.docs.offsets,
+                            np.array([[5, -1, -1]]), 2)
+    assert ids.tolist() == [[5, -1]] and sc[0, 1] == -np.inf
+
+
+# --------------------------------------------------------------------------- codes / qCH
+
+def test_assign_codes_brute_force_self_and_ties():
+    rng = np.random.default_rng(7)
+    C = _unit(rng, 20, 8)
+    X = _unit(rng, 50, 8)
+    codes = oracle.assign_codes(X, C)
+    for x, c in zip(X, codes):
+        sims = [float(np.dot(x, cc)) for cc in C]
+        assert c == max(range(20), key=lambda t: (sims[t], -t))
+    assert oracle.assign_codes(C, C).tolist() == list(range(20))
+    Cdup = np.vstack([C[:5], C[3:4], C[5:]])      # row 5 duplicates row 3
+    assert oracle.assign_codes(C[3:4], Cdup).tolist() == [3]
+
+
+def test_qch_lossless_codes_equal_exact_chamfer():
+    """With a codebook holding every vector exactly, NN is the identity and qCH is CH."""
+    rng = np.random.default_rng(8)
+    Q, P = _unit(rng, 6, 32), _unit(rng, 9, 32)
+    C = np.vstack([Q, P])
+    qc, pc = oracle.assign_codes(Q, C), oracle.assign_codes(P, C)
+    assert qc.tolist() == list(range(6)) and pc.tolist() == list(range(6, 15))
+    ch = oracle.chamfer(Q, P)
+    assert oracle.qch_similarity(qc, pc, C) == pytest.approx(ch, abs=1e-13)
+    assert oracle.qch_distance(qc, pc, C) == pytest.approx(len(Q) - ch, abs=1e-13)
+
+
+def test_qch_brute_force_and_batched_forms():
+    rng = np.random.default_rng(9)
+    C = _unit(rng, 16, 8)
+    lens = np.array([3, 1, 4, 2])
+    off = np.concatenate([[0], np.cumsum(lens)])
+    pc = rng.integers(0, 16, size=int(lens.sum()))
+    qc = rng.integers(0, 16, size=5)
+    qo = np.array([0, 2, 5])
+    S = oracle.qch_score_all(qc, qo, pc, off, C)
+    for b in range(2):
+        for n in range(4):
+            a = qc[qo[b]:qo[b + 1]]
+            bb = pc[off[n]:off[n + 1]]
+            dist = sum(min(1.0 - float(np.dot(C[x], C[y])) for y in bb) for x in a)
+            assert oracle.qch_distance(a, bb, C) == pytest.approx(dist, abs=1e-13)
+            assert S[b, n] == pytest.approx(len(a) - dist, abs=1e-13)
+    got = oracle.qch_score_ids(qc, qo, pc, off, np.array([0, 1, 3]), np.array([2, 0, 3]), C)
+    assert got.tolist() == pytest.approx([S[0, 2], S[1, 0], S[1, 3]], abs=1e-13)
+
+
+def test_codebook_size_formula_reproduces_paper():
+    g = json.load(open(os.path.join(GOLD, "codebook_sizes.json")))
+    for c in g["cases"]:
+        assert oracle.k1_for(c["vectors"]) == c["k1"], c["dataset"]
+
+
+# --------------------------------------------------------------------------- formats
+
+def test_bf16_round_matches_torch_and_ties_to_even():
+    rng = np.random.default_rng(10)
+    x = np.concatenate([rng.standard_normal(10000).astype(np.float32),
+                        (rng.standard_normal(1000) * 1e-39).astype(np.float32)])
+    want = torch.from_numpy(x).to(torch.bfloat16).float().numpy()
+    np.testing.assert_array_equal(oracle.bf16_round(x), want)
+    # exact halfway cases between 1 and the next bfloat16 (1 + 2^-7)
+    half = np.float32(1.0 + 2.0 ** -8)
+    assert oracle.bf16_round(np.array([half]))[0] == 1.0                 # ties to even (down)
+    half2 = np.float32(1.0 + 3 * 2.0 ** -8)
+    assert oracle.bf16_round(np.array([half2]))[0] == np.float32(1.0 + 2 * 2.0 ** -7)  # up
+
+
+def test_fp8_e4m3_round_matches_torch_in_range():
+    rng = np.random.default_rng(11)
+    x = np.concatenate([rng.uniform(-448, 448, 5000), rng.standard_normal(5000) * 0.01,
+                        rng.standard_normal(1000) * 1e-3]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.float8_e4m3fn).float().numpy().astype(np.float64)
+    np.testing.assert_array_equal(oracle.fp8_e4m3_round(x), want)
+    # every finite E4M3 value maps to itself; saturation at the top
+    allv = torch.arange(256, dtype=torch.uint8).view(torch.float8_e4m3fn).float().numpy()
+    allv = allv[np.isfinite(allv)]
+    np.testing.assert_array_equal(oracle.fp8_e4m3_round(allv), allv.astype(np.float64))
+    assert oracle.fp8_e4m3_round(np.array([1000.0, -500.0])).tolist() == [448.0, -448.0]
+
+
+def test_fp8_quantize_scales_and_error_bound():
+    rng = np.random.default_rng(12)
+    X = _unit(rng, 200, 128).astype(np.float32)
+    codes, s = oracle.fp8_e4m3_quantize(X)
+    assert np.all(np.abs(codes).max(axis=1) == 448.0)
+    deq = codes * s[:, None].astype(np.float64)
+    # normal range: relative half-spacing 2^-4; below 2^-6 * s the spacing is 2^-9 * s
+    bound = np.maximum(np.abs(X) * 2.0 ** -4, s[:, None] * 2.0 ** -10) * (1 + 1e-6)
+    assert np.all(np.abs(deq - X) <= bound)
+    c0, s0 = oracle.fp8_e4m3_quantize(np.zeros((1, 4), np.float32))
+    assert s0[0] == 1.0 and np.all(c0 == 0)
+
+
+# --------------------------------------------------------------------------- gradients
+
+def test_maxsim_grad_euler_identity_and_finite_differences():
+    rng = np.random.default_rng(13)
+    Q, P = _unit(rng, 5, 16), _unit(rng, 7, 16)
+    dQ, dP, jstar = oracle.maxsim_grad(Q, P)
+    ch = oracle.chamfer(Q, P)
+    # 1-homogeneous in Q (and in P) for a fixed argmax
+    assert float((dQ * Q).sum()) == pytest.approx(ch, abs=1e-13)
+    assert float((dP * P).sum()) == pytest.approx(ch, abs=1e-13)
+    h = 1e-6
+    for (M, G) in ((Q, dQ), (P, dP)):
+        for idx in [(0, 0), (2, 5), (4, 15)]:
+            Mp, Mm = M.copy(), M.copy()
+            Mp[idx] += h
+            Mm[idx] -= h
+            args_p = (Mp, P) if M is Q else (Q, Mp)
+            args_m = (Mm, P) if M is Q else (Q, Mm)
+            fd = (oracle.chamfer(*args_p) - oracle.chamfer(*args_m)) / (2 * h)
+            assert fd == pytest.approx(G[idx], abs=1e-7)
+
+
+def test_contrastive_chain_rule_finite_differences_4x4():
+    """FD check of dL/dQ and dL/dP through Eq. 1 and the contrastive loss."""
+    rng = np.random.default_rng(14)
+    tau, B, ND, m, d = 0.05, 4, 4, 3, 8
+    Qs = [_unit(rng, m, d) for _ in range(B)]
+    Ps = [[_unit(rng, int(rng.integers(2, 5)), d) for _ in range(ND)] for _ in range(B)]
+
+    def loss(Qs, Ps):
+        S = np.array([[oracle.chamfer(Qs[b], Ps[b][n]) for n in range(ND)] for b in range(B)])
+        return oracle.contrastive_loss(S, tau), S
+
+    L, S = loss(Qs, Ps)
+    g = oracle.contrastive_dscores(S, tau)
+    dQs = [np.zeros_like(x) for x in Qs]
+    dPs = [[np.zeros_like(p) for p in row] for row in Ps]
+    for b in range(B):
+        for n in range(ND):
+            dq, dp, _ = oracle.maxsim_grad(Qs[b], Ps[b][n])
+            margin = np.sort(Qs[b] @ Ps[b][n].T, axis=1)
+            assert margin.shape[1] < 2 or np.min(margin[:, -1] - margin[:, -2]) > 1e-4
+            dQs[b] += g[b, n] * dq
+            dPs[b][n] += g[b, n] * dp
+    h = 1e-6
+    for b, i, k in [(0, 0, 0), (1, 2, 3), (3, 1, 7)]:
+        Qp = [x.copy() for x in Qs]
+        Qm = [x.copy() for x in Qs]
+        Qp[b][i, k] += h
+        Qm[b][i, k] -= h
+        fd = (loss(Qp, Ps)[0] - loss(Qm, Ps)[0]) / (2 * h)
+        assert fd == pytest.approx(dQs[b][i, k], rel=1e-5, abs=1e-7)
+    for b, n, j, k in [(0, 0, 0, 1), (2, 3, 1, 4)]:
+        Pp = [[p.copy() for p in row] for row in Ps]
+        Pm = [[p.copy() for p in row] for row in Ps]
+        Pp[b][n][j, k] += h
+        Pm[b][n][j, k] -= h
+        fd = (loss(Qs, Pp)[0] - loss(Qs, Pm)[0]) / (2 * h)
+        assert fd == pytest.approx(dPs[b][n][j, k], rel=1e-5, abs=1e-7)
+
+
+def test_contrastive_dscores_rows_sum_to_zero():
+    rng = np.random.default_rng(15)
+    S = rng.standard_normal((5, 6))
+    g = oracle.contrastive_dscores(S, 0.05)
+    np.testing.assert_allclose(g.sum(axis=1), 0.0, atol=1e-12)
+    assert np.all(g[:, 0] <= 0) and np.all(g[:, 1:] >= 0)
+
+
+# --------------------------------------------------------------------------- k-means (unpinned)
+
+def test_kmeans_update_fixed_point_invariants():
+    rng = np.random.default_rng(16)
+    X = _unit(rng, 300, 8)
+    C = _unit(rng, 10, 8)
+    for _ in range(30):
+        codes = oracle.assign_codes(X, C)
+        C = oracle.kmeans_update(X, codes, C)
+    codes = oracle.assign_codes(X, C)
+    for c in range(10):
+        mem = X[codes == c]
+        if len(mem):
+            m = mem.sum(0)
+            np.testing.assert_allclose(C[c], m / np.linalg.norm(m), atol=1e-9)
+    sims = X @ C.T
+    assert np.all(sims[np.arange(300), codes] >= sims.max(1) - 1e-15)
+
+
+def test_synthetic_generators_shapes_and_norms():
+    w = synth.exact_fp32(n_sets=100, n_queries=3)
+    L = w.docs.lengths()
+    assert L.min() >= 16 and L.max() <= 64 and len(L) == 100
+    norms = torch.linalg.vector_norm(w.docs.vecs.double(), dim=1)
+    assert torch.allclose(norms, torch.ones_like(norms), atol=1e-6)
+    lens = synth.lengths_lognormal(200000, 70.0, 0.5, 20, 180, 1)
+    assert lens.min() >= 20 and lens.max() <= 180 and 65 < lens.mean() < 72
+    co, ci = synth.candidate_lists(20, 1000, 64, 128, 0.3, 50, 3)
+    for b in range(20):
+        row = ci[co[b]:co[b + 1]]
+        assert len(set(row.tolist())) == len(row) and 64 <= len(row) <= 128
+    w2 = synth.exact_fp32(n_sets=100, n_queries=3)
+    assert torch.equal(w.docs.vecs, w2.docs.vecs)
