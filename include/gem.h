@@ -1,0 +1,203 @@
+/*
+ * gem.h -- C ABI of the B300 (sm_103a) multi-vector scoring library.
+ *
+ * The library scores query vector sets against a CSR-packed store of document
+ * vector sets under the Chamfer / MaxSim similarity of GEM (arXiv 2603.20336,
+ * Sec. 3.1, Definition 1, Eq. 1):
+ *
+ *     CH(Q, P) = sum over q in Q of  max over p in P of <q, p>
+ *
+ * with Sim taken as the inner product (cosine on the unit-norm vectors the
+ * paper's encoders emit).  Scores are similarities: higher is better.
+ *
+ * Conventions shared by every call
+ *  - Vectors have d = 128 float32 components, rows packed contiguously.
+ *  - A set collection is CSR-packed: set i owns rows offsets[i] .. offsets[i+1]-1;
+ *    offsets is int64 with offsets[0] = 0 and strictly increasing (no empty set).
+ *  - Unless a parameter says "host", every pointer is a device pointer that the
+ *    caller allocated and owns; the library never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every call is asynchronous on that stream; outputs are valid once the stream
+ *    reaches the call.  Calls on a workspace allocate no device memory, so they
+ *    may be captured into a CUDA graph.
+ *  - Errors: invalid arguments are detected on the host before anything is
+ *    enqueued and returned synchronously (the outputs are left untouched).
+ *    Inconsistent device-resident metadata (non-monotone offsets, ids outside
+ *    [0, n_sets)) and bounded-wait timeouts are recorded in the workspace's
+ *    device status word; gem_stream_status() returns it.
+ *    gem_last_error_message() describes the last synchronous error of the
+ *    calling thread.
+ *  - A store is immutable after creation and may be shared by concurrent calls;
+ *    a workspace must be used by one stream at a time.
+ */
+#ifndef GEM_H_
+#define GEM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GEM_OK = 0,
+  GEM_ERR_INVALID = 1,     /* bad argument or inconsistent metadata */
+  GEM_ERR_OOM = 2,         /* device allocation failed (creation calls only) */
+  GEM_ERR_CUDA = 3,        /* a CUDA runtime/driver call failed */
+  GEM_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out */
+  GEM_ERR_UNSUPPORTED = 5, /* device is not sm_103, or an unsupported option */
+  GEM_ERR_STATE = 6,       /* object lacks what the call needs (e.g. no bf16 copy) */
+  GEM_ERR_BOUNDS = 7       /* a device-side index check failed */
+} gem_status;
+
+/* Arithmetic of the scoring pass. */
+typedef enum {
+  GEM_F32 = 0,      /* FP32 SIMT, fixed summation order, Kahan sum over query vectors */
+  GEM_BF16 = 1,     /* BF16 operands on tcgen05 tensor cores, FP32 accumulation */
+  GEM_FP8_E4M3 = 2  /* E4M3 operands with per-vector FP32 scales, FP32 accumulation */
+} gem_dtype;
+
+/* Which copies of the vectors a store keeps (bit mask). */
+enum {
+  GEM_KEEP_F32 = 1u,   /* FP32 master copy (needed by GEM_F32 scoring and the rerank) */
+  GEM_KEEP_BF16 = 2u,  /* BF16, round to nearest even */
+  GEM_KEEP_FP8 = 4u    /* E4M3 codes + per-vector FP32 scale s_j = max_k |x_jk| / 448 */
+};
+
+/* Internal arrays a store can copy out (gem_store_export). */
+enum {
+  GEM_EXPORT_BF16 = 0,       /* uint16 [n_vecs * 128] bfloat16 bit patterns */
+  GEM_EXPORT_FP8 = 1,        /* uint8  [n_vecs * 128] E4M3 bit patterns */
+  GEM_EXPORT_FP8_SCALE = 2,  /* float  [n_vecs] per-vector scales */
+  GEM_EXPORT_OFFSETS = 3     /* int64  [n_sets + 1] */
+};
+
+typedef struct gem_store gem_store;
+typedef struct gem_workspace gem_workspace;
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int gem_version(void);
+
+/* Human-readable text of the last synchronous error on the calling thread. */
+const char* gem_last_error_message(void);
+
+/* Checks that `device` is an sm_103 GPU (B300).  GEM_ERR_UNSUPPORTED otherwise. */
+gem_status gem_device_check(int device);
+
+/*
+ * Builds a store of n_sets vector sets (the database D of Sec. 3.1, problem
+ * statement).  vecs: float32 [offsets[n_sets] * dim]; offsets: int64 [n_sets+1].
+ * inputs_on_host != 0: vecs and offsets are host pointers (copied in);
+ * otherwise device pointers (copied; the caller keeps ownership).  dim must be
+ * 128.  keep_mask: GEM_KEEP_* bits, at least one.  Sets must be non-empty.
+ * The call synchronises `stream` once (it reads the offsets on the host to plan
+ * the tile map).  On success *out owns all of its device memory.
+ */
+gem_status gem_store_create(const float* vecs, const int64_t* offsets, int64_t n_sets, int32_t dim,
+                            uint32_t keep_mask, int inputs_on_host, void* stream, gem_store** out);
+void gem_store_destroy(gem_store* store);
+
+/* Sizes of a store.  Any output pointer may be NULL. */
+gem_status gem_store_info(const gem_store* store, int64_t* n_sets, int64_t* n_vecs,
+                          uint32_t* keep_mask);
+
+/* Copies one internal array (GEM_EXPORT_*) into the device buffer dst of
+ * dst_bytes bytes (must be at least the array's size). */
+gem_status gem_store_export(const gem_store* store, int32_t what, void* dst, size_t dst_bytes,
+                            void* stream);
+
+/*
+ * Scratch for scoring calls against `store`.  Bounds fix the memory once:
+ *   max_queries  -- query sets per call
+ *   max_q_rows   -- total query vectors per call
+ *   max_q_len    -- vectors in the longest query set (1..256)
+ *   max_cands    -- candidate ids per call (gem_score_ids and the rerank pool
+ *                   of gem_search: n_queries * rerank_depth)
+ *   max_k        -- largest k for gem_topk / gem_search (1..4096)
+ */
+gem_status gem_workspace_create(const gem_store* store, int32_t max_queries, int64_t max_q_rows,
+                                int32_t max_q_len, int64_t max_cands, int32_t max_k,
+                                gem_workspace** out);
+void gem_workspace_destroy(gem_workspace* ws);
+
+/*
+ * Exact CH of every query set against every stored set (Eq. 1 for all P in D,
+ * the scores ranked by Eq. 2).
+ *   q          float32 [n_q_rows * 128] query vectors, CSR by q_offsets
+ *   q_offsets  int64 [n_queries + 1] (device), q_offsets[n_queries] == n_q_rows
+ *   compute    GEM_F32 (FP32 SIMT), GEM_BF16 or GEM_FP8_E4M3 (tensor cores;
+ *              the store must keep that copy)
+ *   scores     float32 [n_queries * n_sets], row-major: scores[b * n_sets + n]
+ */
+gem_status gem_score_all(const gem_store* store, gem_workspace* ws, const float* q,
+                         const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
+                         int32_t compute, float* scores, void* stream);
+
+/*
+ * Exact CH over per-query candidate lists (the candidate scoring of one
+ * beam-search expansion, Algorithm 5).
+ *   cand_offsets  int64 [n_queries + 1] (device), cand_offsets[n_queries] == n_cands
+ *   cand_ids      int64 [n_cands]; ids of query b are cand_ids[cand_offsets[b] ..
+ *                 cand_offsets[b+1]-1]; each must lie in [0, n_sets) (a negative id
+ *                 is an empty slot and scores -inf; an id >= n_sets records
+ *                 GEM_ERR_BOUNDS and scores NaN).  Duplicates are scored per position.
+ *   scores        float32 [n_cands], aligned with cand_ids
+ * compute GEM_F32 uses FP32 FMA in a fixed order per dot product and a Kahan
+ * (compensated) sum over the query vectors in ascending order.
+ */
+gem_status gem_score_ids(const gem_store* store, gem_workspace* ws, const float* q,
+                         const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
+                         const int64_t* cand_offsets, const int64_t* cand_ids, int64_t n_cands,
+                         int32_t compute, float* scores, void* stream);
+
+/*
+ * Per-row top-k (the k-argmax of Eq. 2): sorted by score descending, ties by
+ * lower id.  Rows are either dense (row_offsets == NULL: row r is
+ * scores[r * cols .. r * cols + cols - 1]) or ragged (row_offsets int64
+ * [rows + 1], device).  ids == NULL: an element's id is its index within its
+ * row; otherwise ids is int64 aligned with scores.  Ids must be < 2^32.
+ * out_ids int64 [rows * k], out_scores float32 [rows * k] (may be NULL); a row
+ * with fewer than k elements is padded with id -1 and score -inf.  NaN scores
+ * are not supported.
+ */
+gem_status gem_topk(gem_workspace* ws, const float* scores, const int64_t* row_offsets, int32_t rows,
+                    int64_t cols, const int64_t* ids, int32_t k, int64_t* out_ids, float* out_scores,
+                    void* stream);
+
+/*
+ * Exhaustive search with an exact rerank (Eq. 2 answered as in the last step
+ * of Algorithm 5): score every stored set with `compute`, keep the top
+ * rerank_depth per query, rescore that pool with exact FP32 CH (Kahan sum over
+ * query vectors) and return the top k of it.  rerank_depth == 0 skips the
+ * rerank (the top k of the first pass is returned).  Needs GEM_KEEP_F32 when
+ * rerank_depth > 0.  out_ids int64 [n_queries * k], out_scores float32 [n_queries * k].
+ */
+gem_status gem_search(const gem_store* store, gem_workspace* ws, const float* q,
+                      const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
+                      int32_t compute, int32_t rerank_depth, int32_t k, int64_t* out_ids,
+                      float* out_scores, void* stream);
+
+/*
+ * gem_search with HOST buffers: q, q_offsets, out_ids and out_scores are host
+ * pointers (pinned memory gives overlapped copies).  The call copies the
+ * queries in, runs the search on `stream`, copies the results out and
+ * synchronises the stream before returning.
+ */
+gem_status gem_search_host(const gem_store* store, gem_workspace* ws, const float* q_host,
+                           const int64_t* q_offsets_host, int32_t n_queries, int32_t compute,
+                           int32_t rerank_depth, int32_t k, int64_t* out_ids_host,
+                           float* out_scores_host, void* stream);
+
+/* Number of kernels this library has enqueued since it was loaded (all
+ * devices and threads); lets a caller count the library's launches in a region. */
+int64_t gem_kernel_launches(void);
+
+/* Synchronises `stream`, then returns and clears the workspace's device status
+ * word (GEM_OK if no device-side error was recorded since the last check). */
+gem_status gem_stream_status(gem_workspace* ws, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEM_H_ */

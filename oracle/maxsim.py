@@ -42,17 +42,20 @@ def chamfer(A, B) -> float:
     return float(sims.max(axis=1).sum())
 
 
-def score_all(q, q_offsets, vecs, offsets) -> np.ndarray:
+def score_all(q, q_offsets, vecs, offsets, with_l1: bool = False):
     """CH(Q_b, P_n) for every query set b and every stored set n: float64 [B, N].
 
     The multi-vector retrieval problem (Eq. 2) ranks every P in D by CH(Q, P);
-    this returns all of those scores.
+    this returns all of those scores.  with_l1=True also returns
+    sum_i |max_j <q_i, p_j>| per (b, n), the scale a relative error of the sum is
+    measured against.
     """
     q = _f64(q)
     qo = _i64(q_offsets)
     off = _i64(offsets)
     n_sets = len(off) - 1
     out = np.empty((len(qo) - 1, n_sets), dtype=np.float64)
+    l1 = np.empty_like(out) if with_l1 else None
     # group documents so that one matmul covers about _DOC_ROWS_PER_STEP rows
     groups = []
     d0 = 0
@@ -71,7 +74,9 @@ def score_all(q, q_offsets, vecs, offsets) -> np.ndarray:
             sims = Q @ X.T                                   # [m_q, rows]
             per_doc_max = np.maximum.reduceat(sims, starts, axis=1)   # max over each doc's rows
             out[b, d0:d1] = per_doc_max.sum(axis=0)          # sum over the query's vectors
-    return out
+            if with_l1:
+                l1[b, d0:d1] = np.abs(per_doc_max).sum(axis=0)
+    return (out, l1) if with_l1 else out
 
 
 def score_ids(q, q_offsets, vecs, offsets, cand_offsets, cand_ids) -> np.ndarray:

@@ -1,0 +1,213 @@
+"""Python binding of libgem, the B300 (sm_103a) multi-vector MaxSim library.
+
+Argument marshalling only: every step of every call runs in the library's CUDA
+kernels.  Tensors are passed by device pointer on torch's current stream; torch
+supplies device memory and streams.  There is no CPU fallback: importing this
+package without the compiled library raises ImportError, and every scoring
+call needs a CUDA device.
+
+    store = Store(vecs, offsets, keep=("f32", "bf16"))     # CSR doc-set store
+    ws = Workspace(store, max_queries=1000, max_q_rows=32000)
+    scores = score_all(store, ws, q, q_offsets, "bf16")    # [B, n_sets]
+    ids, sc = search(store, ws, q, q_offsets, "bf16", rerank_depth=1000, k=100)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import _abi
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgem.so")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libgem.so is not built ({_LIB_PATH}); run python paper_2603_20336_b300/build.py")
+
+lib = ctypes.CDLL(_LIB_PATH)
+_abi.declare(lib)
+
+DTYPES = {"f32": 0, "bf16": 1, "fp8": 2}
+KEEP = {"f32": 1, "bf16": 2, "fp8": 4}
+STATUS = {0: "GEM_OK", 1: "GEM_ERR_INVALID", 2: "GEM_ERR_OOM", 3: "GEM_ERR_CUDA", 4: "GEM_ERR_TIMEOUT",
+          5: "GEM_ERR_UNSUPPORTED", 6: "GEM_ERR_STATE", 7: "GEM_ERR_BOUNDS"}
+
+
+class GemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(code: int):
+    if code != 0:
+        raise GemError(code, lib.gem_last_error_message().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return t
+
+
+def _dtype_code(compute):
+    return DTYPES[compute] if isinstance(compute, str) else int(compute)
+
+
+class Store:
+    """CSR doc-set store (Sec. 3.1 problem statement: the database D of vector sets)."""
+
+    def __init__(self, vecs: torch.Tensor, offsets, keep=("f32", "bf16"), stream=None):
+        mask = 0
+        for k in keep:
+            mask |= KEEP[k]
+        offsets = torch.as_tensor(offsets, dtype=torch.int64)
+        n_sets = offsets.numel() - 1
+        h = ctypes.c_void_p()
+        if vecs.is_cuda:
+            vecs = _dev(vecs, torch.float32, "vecs")
+            off = offsets.to(vecs.device).contiguous()
+            _check(lib.gem_store_create(_ptr(vecs), _ptr(off), n_sets, vecs.shape[1], mask, 0,
+                                        _stream(stream), ctypes.byref(h)))
+        else:
+            v = vecs.contiguous().to(torch.float32)
+            off = offsets.contiguous()
+            _check(lib.gem_store_create(_ptr(v), _ptr(off), n_sets, v.shape[1], mask, 1,
+                                        _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self.n_sets = n_sets
+        self.n_vecs = int(offsets[-1])
+        self.keep = tuple(keep)
+
+    def export(self, what: str, stream=None) -> torch.Tensor:
+        """Copy of an internal array: 'bf16' (uint16 bits), 'fp8' (uint8 bits),
+        'fp8_scale' (float32) or 'offsets' (int64)."""
+        spec = {"bf16": (0, torch.int16, (self.n_vecs, 128)), "fp8": (1, torch.uint8, (self.n_vecs, 128)),
+                "fp8_scale": (2, torch.float32, (self.n_vecs,)), "offsets": (3, torch.int64, (self.n_sets + 1,))}
+        code, dt, shape = spec[what]
+        out = torch.empty(shape, dtype=dt, device="cuda")
+        _check(lib.gem_store_export(self.handle, code, _ptr(out), out.numel() * out.element_size(),
+                                    _stream(stream)))
+        return out
+
+    def close(self):
+        if self.handle:
+            lib.gem_store_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Workspace:
+    """Preallocated scratch for scoring calls against one store."""
+
+    def __init__(self, store: Store, max_queries: int, max_q_rows: int, max_q_len: int = 64,
+                 max_cands: int = 0, max_k: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib.gem_workspace_create(store.handle, max_queries, max_q_rows, max_q_len, max_cands,
+                                        max_k, ctypes.byref(h)))
+        self.handle = h
+        self.store = store
+        self.max_k = max_k
+
+    def status(self, stream=None) -> int:
+        """Synchronise and return (then clear) the device status word."""
+        return lib.gem_stream_status(self.handle, _stream(stream))
+
+    def close(self):
+        if self.handle:
+            lib.gem_workspace_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _queries(q, q_offsets):
+    q = _dev(q, torch.float32, "q")
+    qo = _dev(q_offsets, torch.int64, "q_offsets")
+    return q, qo, qo.numel() - 1, q.shape[0]
+
+
+def score_all(store: Store, ws: Workspace, q, q_offsets, compute="bf16", out=None, stream=None):
+    """Exact CH (Eq. 1) of every query set against every stored set: float32 [B, n_sets]."""
+    q, qo, B, rows = _queries(q, q_offsets)
+    if out is None:
+        out = torch.empty((B, store.n_sets), dtype=torch.float32, device=q.device)
+    _check(lib.gem_score_all(store.handle, ws.handle, _ptr(q), _ptr(qo), B, rows, _dtype_code(compute),
+                             _ptr(out), _stream(stream)))
+    return out
+
+
+def score_ids(store: Store, ws: Workspace, q, q_offsets, cand_offsets, cand_ids, compute="f32",
+              out=None, stream=None):
+    """Exact CH over per-query candidate id lists (Algorithm 5 candidate scoring)."""
+    q, qo, B, rows = _queries(q, q_offsets)
+    co = _dev(cand_offsets, torch.int64, "cand_offsets")
+    ci = _dev(cand_ids, torch.int64, "cand_ids")
+    if out is None:
+        out = torch.empty(ci.numel(), dtype=torch.float32, device=q.device)
+    _check(lib.gem_score_ids(store.handle, ws.handle, _ptr(q), _ptr(qo), B, rows, _ptr(co), _ptr(ci),
+                             ci.numel(), _dtype_code(compute), _ptr(out), _stream(stream)))
+    return out
+
+
+def topk(ws: Workspace, scores, k: int, ids=None, row_offsets=None, stream=None):
+    """Per-row top-k by (score desc, id asc): (ids int64 [rows, k], scores float32 [rows, k])."""
+    scores = _dev(scores, torch.float32, "scores")
+    if row_offsets is None:
+        rows, cols = scores.shape
+        ro = None
+    else:
+        ro = _dev(row_offsets, torch.int64, "row_offsets")
+        rows, cols = ro.numel() - 1, 0
+    if ids is not None:
+        ids = _dev(ids, torch.int64, "ids")
+    out_i = torch.empty((rows, k), dtype=torch.int64, device=scores.device)
+    out_s = torch.empty((rows, k), dtype=torch.float32, device=scores.device)
+    _check(lib.gem_topk(ws.handle, _ptr(scores), _ptr(ro), rows, cols, _ptr(ids), k, _ptr(out_i),
+                        _ptr(out_s), _stream(stream)))
+    return out_i, out_s
+
+
+def search(store: Store, ws: Workspace, q, q_offsets, compute="bf16", rerank_depth=1000, k=100,
+           stream=None):
+    """Exhaustive search (Eq. 2) with an exact FP32 rerank of the top rerank_depth."""
+    q, qo, B, rows = _queries(q, q_offsets)
+    out_i = torch.empty((B, k), dtype=torch.int64, device=q.device)
+    out_s = torch.empty((B, k), dtype=torch.float32, device=q.device)
+    _check(lib.gem_search(store.handle, ws.handle, _ptr(q), _ptr(qo), B, rows, _dtype_code(compute),
+                          rerank_depth, k, _ptr(out_i), _ptr(out_s), _stream(stream)))
+    return out_i, out_s
+
+
+def search_host(store: Store, ws: Workspace, q_host, q_offsets_host, compute="bf16", rerank_depth=1000,
+                k=100, out_ids=None, out_scores=None, stream=None):
+    """search() with host tensors in and out (copies run inside the call)."""
+    q = q_host.contiguous()
+    qo = torch.as_tensor(q_offsets_host, dtype=torch.int64).contiguous()
+    B = qo.numel() - 1
+    if out_ids is None:
+        out_ids = torch.empty((B, k), dtype=torch.int64, pin_memory=True)
+    if out_scores is None:
+        out_scores = torch.empty((B, k), dtype=torch.float32, pin_memory=True)
+    _check(lib.gem_search_host(store.handle, ws.handle, _ptr(q), _ptr(qo), B, _dtype_code(compute),
+                               rerank_depth, k, _ptr(out_ids), _ptr(out_scores), _stream(stream)))
+    return out_ids, out_scores

@@ -1,0 +1,34 @@
+"""ctypes signatures of the C ABI in include/gem.h."""
+import ctypes as C
+
+P = C.c_void_p
+I32 = C.c_int32
+I64 = C.c_int64
+U32 = C.c_uint32
+SZ = C.c_size_t
+
+SIGNATURES = {
+    "gem_version": (C.c_int, []),
+    "gem_last_error_message": (C.c_char_p, []),
+    "gem_device_check": (C.c_int, [C.c_int]),
+    "gem_store_create": (C.c_int, [P, P, I64, I32, U32, C.c_int, P, C.POINTER(P)]),
+    "gem_store_destroy": (None, [P]),
+    "gem_store_info": (C.c_int, [P, P, P, P]),
+    "gem_store_export": (C.c_int, [P, I32, P, SZ, P]),
+    "gem_workspace_create": (C.c_int, [P, I32, I64, I32, I64, I32, C.POINTER(P)]),
+    "gem_workspace_destroy": (None, [P]),
+    "gem_score_all": (C.c_int, [P, P, P, P, I32, I64, I32, P, P]),
+    "gem_score_ids": (C.c_int, [P, P, P, P, I32, I64, P, P, I64, I32, P, P]),
+    "gem_topk": (C.c_int, [P, P, P, I32, I64, P, I32, P, P, P]),
+    "gem_search": (C.c_int, [P, P, P, P, I32, I64, I32, I32, I32, P, P, P]),
+    "gem_search_host": (C.c_int, [P, P, P, P, I32, I32, I32, I32, P, P, P]),
+    "gem_stream_status": (C.c_int, [P, P]),
+    "gem_kernel_launches": (I64, []),
+}
+
+
+def declare(lib):
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args

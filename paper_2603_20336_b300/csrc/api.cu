@@ -1,0 +1,471 @@
+// C-ABI entry points of libgem (declared in include/gem.h): argument checks,
+// object lifetime and the dispatch of each call onto the kernels.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+namespace gem {
+
+namespace {
+thread_local std::string g_last_error;
+
+// Default schedule of the tensor-core scoring kernel: 2 M tiles (256 resident
+// query rows) x 128-column document tiles, chunks of about 64K vectors.
+constexpr int kDefaultMTiles = 2;
+constexpr int kDefaultChunkRows = 1 << 16;
+
+bool device_is_sm103(int dev) {
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return false;
+  return p.major == 10 && p.minor == 3;
+}
+
+gem_status check_current_device(int want) {
+  int dev = -1;
+  GEM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != want) return fail(GEM_ERR_INVALID, "current device differs from the store's device");
+  return GEM_OK;
+}
+
+template <typename T>
+gem_status dmalloc(T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) return GEM_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GEM_ERR_OOM, std::string("cudaMalloc failed for ") + what);
+  }
+  return GEM_OK;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+}  // namespace
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+gem_status fail(gem_status code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+gem_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return GEM_ERR_CUDA;
+}
+
+}  // namespace gem
+
+using namespace gem;
+
+extern "C" {
+
+int gem_version(void) { return 100; }
+
+const char* gem_last_error_message(void) { return g_last_error.c_str(); }
+
+gem_status gem_device_check(int device) {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return fail(GEM_ERR_UNSUPPORTED, "no CUDA device with that index");
+  }
+  if (!device_is_sm103(device)) return fail(GEM_ERR_UNSUPPORTED, "device is not sm_103 (B300)");
+  return GEM_OK;
+}
+
+// ----------------------------------------------------------------------------- store
+
+void gem_store_destroy(gem_store* s) {
+  if (!s) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  dfree(s->d_offsets);
+  dfree(s->d_f32);
+  dfree(s->d_bf16);
+  dfree(s->d_fp8);
+  dfree(s->d_fp8_scale);
+  for (auto& kv : s->chunks) dfree(kv.second.d_chunk_doc);
+  cudaSetDevice(prev);
+  delete s;
+}
+
+gem_status gem_store_create(const float* vecs, const int64_t* offsets, int64_t n_sets, int32_t dim,
+                            uint32_t keep_mask, int inputs_on_host, void* stream, gem_store** out) {
+  if (!out) return fail(GEM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!vecs || !offsets) return fail(GEM_ERR_INVALID, "vecs/offsets is NULL");
+  if (n_sets < 1 || n_sets >= (int64_t)1 << 31) return fail(GEM_ERR_INVALID, "n_sets out of range");
+  if (dim != kDim) return fail(GEM_ERR_UNSUPPORTED, "only dim = 128 is supported");
+  if (keep_mask == 0 || (keep_mask & ~7u)) return fail(GEM_ERR_INVALID, "bad keep_mask");
+  int dev = 0;
+  GEM_CUDA_TRY(cudaGetDevice(&dev));
+  if (!device_is_sm103(dev)) return fail(GEM_ERR_UNSUPPORTED, "device is not sm_103 (B300)");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+  gem_store* s = new gem_store();
+  s->device = dev;
+  s->keep = keep_mask;
+  s->n_sets = n_sets;
+  {
+    cudaDeviceProp p;
+    cudaGetDeviceProperties(&p, dev);
+    s->n_sm = p.multiProcessorCount;
+  }
+  s->h_offsets.resize(n_sets + 1);
+  if (inputs_on_host) {
+    std::memcpy(s->h_offsets.data(), offsets, sizeof(int64_t) * (n_sets + 1));
+  } else {
+    cudaError_t e = cudaMemcpyAsync(s->h_offsets.data(), offsets, sizeof(int64_t) * (n_sets + 1),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { gem_store_destroy(s); return cuda_fail(e, "reading offsets"); }
+  }
+  if (s->h_offsets[0] != 0) { gem_store_destroy(s); return fail(GEM_ERR_INVALID, "offsets[0] != 0"); }
+  for (int64_t i = 0; i < n_sets; ++i) {
+    const int64_t len = s->h_offsets[i + 1] - s->h_offsets[i];
+    if (len < 1) { gem_store_destroy(s); return fail(GEM_ERR_INVALID, "empty or non-monotone set"); }
+    if (len > s->max_set_len) s->max_set_len = len;
+  }
+  s->n_vecs = s->h_offsets[n_sets];
+  if (s->n_vecs >= (int64_t)1 << 31) { gem_store_destroy(s); return fail(GEM_ERR_INVALID, "too many vectors"); }
+  const int64_t V = s->n_vecs;
+
+  gem_status r;
+  if ((r = dmalloc(&s->d_offsets, n_sets + 1, "offsets")) != GEM_OK) { gem_store_destroy(s); return r; }
+  cudaError_t e = cudaMemcpyAsync(s->d_offsets, s->h_offsets.data(), sizeof(int64_t) * (n_sets + 1),
+                                  cudaMemcpyHostToDevice, st);
+  // the FP32 source of the quantised copies lives on the device during the build
+  float* src = nullptr;
+  float* tmp = nullptr;
+  if (e == cudaSuccess) {
+    if (keep_mask & GEM_KEEP_F32) {
+      if ((r = dmalloc(&s->d_f32, V * kDim, "f32 copy")) != GEM_OK) { gem_store_destroy(s); return r; }
+      src = s->d_f32;
+    } else if (inputs_on_host) {
+      if ((r = dmalloc(&tmp, V * kDim, "staging copy")) != GEM_OK) { gem_store_destroy(s); return r; }
+      src = tmp;
+    } else {
+      src = const_cast<float*>(vecs);
+    }
+    if (src != vecs)
+      e = cudaMemcpyAsync(src, vecs, sizeof(float) * V * kDim,
+                          inputs_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
+  }
+  if (e == cudaSuccess && (keep_mask & GEM_KEEP_BF16)) {
+    if ((r = dmalloc(&s->d_bf16, V * kDim, "bf16 copy")) != GEM_OK) { dfree(tmp); gem_store_destroy(s); return r; }
+    launch_quantize_bf16(src, s->d_bf16, V * kDim, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && (keep_mask & GEM_KEEP_FP8)) {
+    if ((r = dmalloc(&s->d_fp8, V * kDim, "fp8 copy")) != GEM_OK) { dfree(tmp); gem_store_destroy(s); return r; }
+    // scales padded so that 1-D TMA boxes past the last vector stay in bounds
+    if ((r = dmalloc(&s->d_fp8_scale, V + 1024, "fp8 scales")) != GEM_OK) { dfree(tmp); gem_store_destroy(s); return r; }
+    e = cudaMemsetAsync(s->d_fp8_scale, 0, sizeof(float) * (V + 1024), st);
+    if (e == cudaSuccess) {
+      launch_quantize_fp8(src, s->d_fp8, s->d_fp8_scale, V, st);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dfree(tmp);
+  if (e != cudaSuccess) { gem_store_destroy(s); return cuda_fail(e, "building the store"); }
+  *out = s;
+  return GEM_OK;
+}
+
+gem_status gem_store_info(const gem_store* s, int64_t* n_sets, int64_t* n_vecs, uint32_t* keep_mask) {
+  if (!s) return fail(GEM_ERR_INVALID, "store is NULL");
+  if (n_sets) *n_sets = s->n_sets;
+  if (n_vecs) *n_vecs = s->n_vecs;
+  if (keep_mask) *keep_mask = s->keep;
+  return GEM_OK;
+}
+
+gem_status gem_store_export(const gem_store* s, int32_t what, void* dst, size_t dst_bytes, void* stream) {
+  if (!s || !dst) return fail(GEM_ERR_INVALID, "store or dst is NULL");
+  const void* src = nullptr;
+  size_t bytes = 0;
+  switch (what) {
+    case GEM_EXPORT_BF16: src = s->d_bf16; bytes = sizeof(uint16_t) * s->n_vecs * kDim; break;
+    case GEM_EXPORT_FP8: src = s->d_fp8; bytes = (size_t)s->n_vecs * kDim; break;
+    case GEM_EXPORT_FP8_SCALE: src = s->d_fp8_scale; bytes = sizeof(float) * s->n_vecs; break;
+    case GEM_EXPORT_OFFSETS: src = s->d_offsets; bytes = sizeof(int64_t) * (s->n_sets + 1); break;
+    default: return fail(GEM_ERR_INVALID, "unknown export");
+  }
+  if (!src) return fail(GEM_ERR_STATE, "store does not keep that array");
+  if (dst_bytes < bytes) return fail(GEM_ERR_INVALID, "dst too small");
+  GEM_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream)));
+  return GEM_OK;
+}
+
+// ----------------------------------------------------------------------------- workspace
+
+void gem_workspace_destroy(gem_workspace* w) {
+  if (!w) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(w->device);
+  void* ptrs[] = {w->d_status, w->d_plan_hdr, w->d_part_query, w->d_part_rows, w->d_part_g,
+                  w->d_part_pass, w->d_part_slot, w->d_part_row0, w->d_row_part, w->d_qpack_bf16,
+                  w->d_qpack_fp8, w->d_qpack_scale, w->d_scores, w->d_pool_ids, w->d_pool_off,
+                  w->d_pool_scores, w->d_q_in, w->d_qo_in, w->d_out_ids, w->d_out_scores};
+  for (void* p : ptrs) dfree(p);
+  cudaSetDevice(prev);
+  delete w;
+}
+
+gem_status gem_workspace_create(const gem_store* s, int32_t max_queries, int64_t max_q_rows,
+                                int32_t max_q_len, int64_t max_cands, int32_t max_k,
+                                gem_workspace** out) {
+  if (!out) return fail(GEM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!s) return fail(GEM_ERR_INVALID, "store is NULL");
+  if (max_queries < 1 || max_queries > (1 << 20)) return fail(GEM_ERR_INVALID, "max_queries out of range");
+  if (max_q_rows < 1 || max_q_rows > ((int64_t)1 << 28)) return fail(GEM_ERR_INVALID, "max_q_rows out of range");
+  if (max_q_len < 1 || max_q_len > 32 * kMaxPasses) return fail(GEM_ERR_INVALID, "max_q_len must be 1..256");
+  if (max_cands < 0) return fail(GEM_ERR_INVALID, "max_cands < 0");
+  if (max_k < 0 || max_k > kMaxK) return fail(GEM_ERR_INVALID, "max_k must be 0..4096");
+  gem_status r = check_current_device(s->device);
+  if (r != GEM_OK) return r;
+
+  gem_workspace* w = new gem_workspace();
+  w->store = s;
+  w->device = s->device;
+  w->max_queries = max_queries;
+  w->max_q_rows = max_q_rows;
+  w->max_q_len = max_q_len;
+  w->max_cands = max_cands;
+  w->max_k = max_k;
+  w->n_passes = (max_q_len + 31) / 32;
+  // every part of r rows takes a slot of g < 2r rows; each pass is padded to a
+  // whole query block of at most 512 rows
+  w->packed_cap = ((2 * max_q_rows + 512 * (kMaxPasses + 1)) + 511) / 512 * 512;
+  w->max_parts = std::min<int64_t>(max_q_rows, (int64_t)max_queries * kMaxPasses);
+#define WS_ALLOC(ptr, count)                                                 \
+  if ((r = dmalloc(&w->ptr, (size_t)(count), #ptr)) != GEM_OK) {            \
+    gem_workspace_destroy(w);                                               \
+    return r;                                                               \
+  }
+  WS_ALLOC(d_status, 1);
+  WS_ALLOC(d_plan_hdr, kPlanHdrInts);
+  WS_ALLOC(d_part_query, w->max_parts);
+  WS_ALLOC(d_part_rows, w->max_parts);
+  WS_ALLOC(d_part_g, w->max_parts);
+  WS_ALLOC(d_part_pass, w->max_parts);
+  WS_ALLOC(d_part_slot, w->max_parts);
+  WS_ALLOC(d_part_row0, w->max_parts);
+  WS_ALLOC(d_row_part, w->packed_cap);
+  if (s->d_bf16) WS_ALLOC(d_qpack_bf16, w->packed_cap * kDim);
+  if (s->d_fp8) {
+    WS_ALLOC(d_qpack_fp8, w->packed_cap * kDim);
+    WS_ALLOC(d_qpack_scale, w->packed_cap);
+  }
+  if (max_k > 0) {
+    WS_ALLOC(d_scores, (size_t)max_queries * s->n_sets);
+    WS_ALLOC(d_pool_off, max_queries + 1);
+    WS_ALLOC(d_q_in, max_q_rows * kDim);
+    WS_ALLOC(d_qo_in, max_queries + 1);
+    WS_ALLOC(d_out_ids, (size_t)max_queries * max_k);
+    WS_ALLOC(d_out_scores, (size_t)max_queries * max_k);
+  }
+  if (max_cands > 0) {
+    WS_ALLOC(d_pool_ids, max_cands);
+    WS_ALLOC(d_pool_scores, max_cands);
+  }
+#undef WS_ALLOC
+  cudaError_t e = cudaMemset(w->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(w->d_plan_hdr, 0, sizeof(int) * kPlanHdrInts);
+  if (e != cudaSuccess) { gem_workspace_destroy(w); return cuda_fail(e, "workspace init"); }
+  if (w->d_qpack_bf16 &&
+      !encode_tmap_2d(&w->tmap_q_bf16, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w->d_qpack_bf16, kDim,
+                      w->packed_cap, kDim * 2, 64, 128, CU_TENSOR_MAP_SWIZZLE_128B)) {
+    gem_workspace_destroy(w);
+    return fail(GEM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the packed queries");
+  }
+  if (w->d_qpack_fp8 &&
+      !encode_tmap_2d(&w->tmap_q_fp8, CU_TENSOR_MAP_DATA_TYPE_UINT8, w->d_qpack_fp8, kDim,
+                      w->packed_cap, kDim, 128, 128, CU_TENSOR_MAP_SWIZZLE_128B)) {
+    gem_workspace_destroy(w);
+    return fail(GEM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the packed fp8 queries");
+  }
+  *out = w;
+  return GEM_OK;
+}
+
+// ----------------------------------------------------------------------------- scoring
+
+static gem_status check_query_args(const gem_store* s, gem_workspace* w, const float* q,
+                                   const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows) {
+  if (!s || !w) return fail(GEM_ERR_INVALID, "store or workspace is NULL");
+  if (w->store != s) return fail(GEM_ERR_INVALID, "workspace was created for another store");
+  if (!q || !q_offsets) return fail(GEM_ERR_INVALID, "q or q_offsets is NULL");
+  if (n_queries < 1 || n_queries > w->max_queries) return fail(GEM_ERR_INVALID, "n_queries out of range");
+  if (n_q_rows < n_queries || n_q_rows > w->max_q_rows) return fail(GEM_ERR_INVALID, "n_q_rows out of range");
+  return check_current_device(s->device);
+}
+
+static gem_status score_all_impl(const gem_store* s, gem_workspace* w, const float* q,
+                                 const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
+                                 int32_t compute, float* scores, cudaStream_t st) {
+  if (compute == GEM_F32) {
+    if (!s->d_f32) return fail(GEM_ERR_STATE, "store keeps no fp32 copy");
+    return launch_f32_score(s, w, q, q_offsets, n_queries, nullptr, nullptr, 0, scores, st);
+  }
+  if (compute == GEM_BF16) {
+    if (!s->d_bf16) return fail(GEM_ERR_STATE, "store keeps no bf16 copy");
+    const int mt = kDefaultMTiles;
+    gem_status r = launch_plan(w, q, q_offsets, n_queries, n_q_rows, 128 * mt, compute, st);
+    if (r != GEM_OK) return r;
+    return launch_tc_score_all(s, w, compute, mt, kDefaultChunkRows, scores, st);
+  }
+  if (compute == GEM_FP8_E4M3) return fail(GEM_ERR_UNSUPPORTED, "fp8 scoring is not available");
+  return fail(GEM_ERR_INVALID, "unknown compute dtype");
+}
+
+gem_status gem_score_all(const gem_store* s, gem_workspace* w, const float* q,
+                         const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
+                         int32_t compute, float* scores, void* stream) {
+  gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
+  if (r != GEM_OK) return r;
+  if (!scores) return fail(GEM_ERR_INVALID, "scores is NULL");
+  return score_all_impl(s, w, q, q_offsets, n_queries, n_q_rows, compute, scores,
+                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+gem_status gem_score_ids(const gem_store* s, gem_workspace* w, const float* q,
+                         const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
+                         const int64_t* cand_offsets, const int64_t* cand_ids, int64_t n_cands,
+                         int32_t compute, float* scores, void* stream) {
+  gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
+  if (r != GEM_OK) return r;
+  if (!cand_offsets || (n_cands > 0 && (!cand_ids || !scores)))
+    return fail(GEM_ERR_INVALID, "candidate arrays or scores is NULL");
+  if (n_cands < 0) return fail(GEM_ERR_INVALID, "n_cands < 0");
+  if (n_cands == 0) return GEM_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (compute == GEM_F32) {
+    if (!s->d_f32) return fail(GEM_ERR_STATE, "store keeps no fp32 copy");
+    return launch_f32_score(s, w, q, q_offsets, n_queries, cand_offsets, cand_ids, n_cands, scores, st);
+  }
+  if (compute == GEM_BF16 || compute == GEM_FP8_E4M3)
+    return fail(GEM_ERR_UNSUPPORTED, "id-list scoring in this dtype is not available");
+  return fail(GEM_ERR_INVALID, "unknown compute dtype");
+}
+
+gem_status gem_topk(gem_workspace* w, const float* scores, const int64_t* row_offsets, int32_t rows,
+                    int64_t cols, const int64_t* ids, int32_t k, int64_t* out_ids, float* out_scores,
+                    void* stream) {
+  if (!w) return fail(GEM_ERR_INVALID, "workspace is NULL");
+  if (!scores || !out_ids) return fail(GEM_ERR_INVALID, "scores or out_ids is NULL");
+  if (rows < 0 || (!row_offsets && cols < 0)) return fail(GEM_ERR_INVALID, "bad shape");
+  if (k < 1 || k > kMaxK) return fail(GEM_ERR_INVALID, "k must be 1..4096");
+  gem_status r = check_current_device(w->device);
+  if (r != GEM_OK) return r;
+  return launch_topk(w, scores, row_offsets, rows, cols, ids, k, out_ids, out_scores,
+                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+static gem_status search_impl(const gem_store* s, gem_workspace* w, const float* q,
+                              const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
+                              int32_t compute, int32_t rerank_depth, int32_t k, int64_t* out_ids,
+                              float* out_scores, cudaStream_t st) {
+  if (k < 1 || k > w->max_k) return fail(GEM_ERR_INVALID, "k must be 1..max_k");
+  if (rerank_depth < 0 || rerank_depth > kMaxK) return fail(GEM_ERR_INVALID, "rerank_depth must be 0..4096");
+  if (rerank_depth > 0 && rerank_depth < k) return fail(GEM_ERR_INVALID, "rerank_depth < k");
+  if (rerank_depth > 0 && (int64_t)rerank_depth * n_queries > w->max_cands)
+    return fail(GEM_ERR_INVALID, "n_queries * rerank_depth exceeds max_cands");
+  if (rerank_depth > 0 && !s->d_f32) return fail(GEM_ERR_STATE, "the rerank needs the fp32 copy");
+  gem_status r = score_all_impl(s, w, q, q_offsets, n_queries, n_q_rows, compute, w->d_scores, st);
+  if (r != GEM_OK) return r;
+  if (rerank_depth == 0)
+    return launch_topk(w, w->d_scores, nullptr, n_queries, s->n_sets, nullptr, k, out_ids, out_scores, st);
+  r = launch_topk(w, w->d_scores, nullptr, n_queries, s->n_sets, nullptr, rerank_depth, w->d_pool_ids,
+                  nullptr, st);
+  if (r != GEM_OK) return r;
+  launch_iota_offsets(w->d_pool_off, n_queries, rerank_depth, st);
+  GEM_CUDA_TRY(cudaGetLastError());
+  r = launch_f32_score(s, w, q, q_offsets, n_queries, w->d_pool_off, w->d_pool_ids,
+                       (int64_t)n_queries * rerank_depth, w->d_pool_scores, st);
+  if (r != GEM_OK) return r;
+  return launch_topk(w, w->d_pool_scores, nullptr, n_queries, rerank_depth, w->d_pool_ids, k, out_ids,
+                     out_scores, st);
+}
+
+gem_status gem_search(const gem_store* s, gem_workspace* w, const float* q,
+                      const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
+                      int32_t compute, int32_t rerank_depth, int32_t k, int64_t* out_ids,
+                      float* out_scores, void* stream) {
+  gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
+  if (r != GEM_OK) return r;
+  if (!out_ids) return fail(GEM_ERR_INVALID, "out_ids is NULL");
+  if (!w->d_scores) return fail(GEM_ERR_STATE, "workspace was created with max_k = 0");
+  return search_impl(s, w, q, q_offsets, n_queries, n_q_rows, compute, rerank_depth, k, out_ids,
+                     out_scores, reinterpret_cast<cudaStream_t>(stream));
+}
+
+gem_status gem_search_host(const gem_store* s, gem_workspace* w, const float* q_host,
+                           const int64_t* q_offsets_host, int32_t n_queries, int32_t compute,
+                           int32_t rerank_depth, int32_t k, int64_t* out_ids_host,
+                           float* out_scores_host, void* stream) {
+  if (!s || !w || !q_host || !q_offsets_host || !out_ids_host)
+    return fail(GEM_ERR_INVALID, "NULL argument");
+  if (!w->d_scores) return fail(GEM_ERR_STATE, "workspace was created with max_k = 0");
+  if (n_queries < 1 || n_queries > w->max_queries) return fail(GEM_ERR_INVALID, "n_queries out of range");
+  const int64_t n_q_rows = q_offsets_host[n_queries];
+  if (q_offsets_host[0] != 0) return fail(GEM_ERR_INVALID, "q_offsets[0] != 0");
+  for (int32_t b = 0; b < n_queries; ++b) {
+    const int64_t m = q_offsets_host[b + 1] - q_offsets_host[b];
+    if (m < 1 || m > w->max_q_len) return fail(GEM_ERR_INVALID, "query set length out of range");
+  }
+  gem_status r = check_query_args(s, w, w->d_q_in, w->d_qo_in, n_queries, n_q_rows);
+  if (r != GEM_OK) return r;
+  if (k < 1 || k > w->max_k) return fail(GEM_ERR_INVALID, "k must be 1..max_k");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  GEM_CUDA_TRY(cudaMemcpyAsync(w->d_q_in, q_host, sizeof(float) * n_q_rows * kDim, cudaMemcpyHostToDevice, st));
+  GEM_CUDA_TRY(cudaMemcpyAsync(w->d_qo_in, q_offsets_host, sizeof(int64_t) * (n_queries + 1),
+                               cudaMemcpyHostToDevice, st));
+  r = search_impl(s, w, w->d_q_in, w->d_qo_in, n_queries, n_q_rows, compute, rerank_depth, k, w->d_out_ids,
+                  w->d_out_scores, st);
+  if (r != GEM_OK) return r;
+  GEM_CUDA_TRY(cudaMemcpyAsync(out_ids_host, w->d_out_ids, sizeof(int64_t) * n_queries * k,
+                               cudaMemcpyDeviceToHost, st));
+  if (out_scores_host)
+    GEM_CUDA_TRY(cudaMemcpyAsync(out_scores_host, w->d_out_scores, sizeof(float) * n_queries * k,
+                                 cudaMemcpyDeviceToHost, st));
+  GEM_CUDA_TRY(cudaStreamSynchronize(st));
+  return GEM_OK;
+}
+
+int64_t gem_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+gem_status gem_stream_status(gem_workspace* w, void* stream) {
+  if (!w) return fail(GEM_ERR_INVALID, "workspace is NULL");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  GEM_CUDA_TRY(cudaStreamSynchronize(st));
+  int code = 0;
+  GEM_CUDA_TRY(cudaMemcpy(&code, w->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  GEM_CUDA_TRY(cudaMemset(w->d_status, 0, sizeof(int)));
+  if (code != 0) {
+    set_error(code == GEM_ERR_TIMEOUT ? "a device-side wait timed out"
+              : code == GEM_ERR_BOUNDS ? "a device-side index check failed"
+                                       : "device-side metadata check failed");
+    return (gem_status)code;
+  }
+  return GEM_OK;
+}
+
+}  // extern "C"

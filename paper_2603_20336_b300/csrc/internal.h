@@ -1,0 +1,164 @@
+// Internal runtime types of libgem: the store, the workspace, the query plan and
+// the kernel launchers.  Nothing here is part of the C ABI.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/gem.h"
+
+namespace gem {
+
+constexpr int kDim = 128;         // vector dimension handled by every kernel
+constexpr int kMaxPasses = 8;     // query sets of up to 8 * 32 = 256 vectors
+constexpr int kClasses = 6;       // slot sizes 32, 16, 8, 4, 2, 1 rows
+constexpr int kCombos = kMaxPasses * kClasses;
+constexpr int kMaxK = 4096;       // largest top-k
+constexpr int kPlanHdrInts = 64;
+
+// Plan header layout (device int32 array).
+enum : int {
+  kHdrParts = 0,       // number of query parts
+  kHdrPackedRows = 1,  // rows of the packed query buffer in use (multiple of m_res)
+  kHdrQBlocks = 2,     // total query blocks
+  kHdrPasses = 3,      // passes with any work
+  kHdrQbBegin = 4,     // kMaxPasses + 1 entries: first query block of each pass
+};
+
+// A document chunk map: contiguous runs of whole sets holding about
+// `chunk_rows` vectors each (a set longer than that forms a chunk of its own).
+struct ChunkMap {
+  int chunk_rows = 0;
+  int n_chunks = 0;
+  int* d_chunk_doc = nullptr;  // [n_chunks + 1] first set of each chunk
+};
+
+struct TmapSet {
+  bool valid = false;
+  CUtensorMap map;
+};
+
+}  // namespace gem
+
+struct gem_store {
+  int device = 0;
+  int n_sm = 0;
+  int64_t n_sets = 0;
+  int64_t n_vecs = 0;
+  uint32_t keep = 0;
+  std::vector<int64_t> h_offsets;
+  int64_t* d_offsets = nullptr;
+  float* d_f32 = nullptr;
+  __nv_bfloat16* d_bf16 = nullptr;
+  uint8_t* d_fp8 = nullptr;
+  float* d_fp8_scale = nullptr;
+  int64_t max_set_len = 0;
+  // tensor maps of the doc copies, keyed by tile rows (box height)
+  mutable std::map<int, CUtensorMap> tmap_bf16;
+  mutable std::map<int, CUtensorMap> tmap_fp8;
+  mutable std::map<int, gem::ChunkMap> chunks;
+};
+
+struct gem_workspace {
+  const gem_store* store = nullptr;
+  int device = 0;
+  int32_t max_queries = 0;
+  int64_t max_q_rows = 0;
+  int32_t max_q_len = 0;
+  int64_t max_cands = 0;
+  int32_t max_k = 0;
+  int n_passes = 0;
+
+  int* d_status = nullptr;
+
+  // query plan
+  int64_t packed_cap = 0;  // rows of the packed query buffers
+  int64_t max_parts = 0;
+  int* d_plan_hdr = nullptr;
+  int* d_part_query = nullptr;
+  int* d_part_rows = nullptr;
+  int* d_part_g = nullptr;
+  int* d_part_pass = nullptr;
+  int* d_part_slot = nullptr;
+  int64_t* d_part_row0 = nullptr;
+  int* d_row_part = nullptr;
+  __nv_bfloat16* d_qpack_bf16 = nullptr;
+  uint8_t* d_qpack_fp8 = nullptr;
+  float* d_qpack_scale = nullptr;
+  CUtensorMap tmap_q_bf16;
+  CUtensorMap tmap_q_fp8;
+
+  // search pipeline
+  float* d_scores = nullptr;       // [max_queries * n_sets]
+  int64_t* d_pool_ids = nullptr;   // [max_cands]
+  int64_t* d_pool_off = nullptr;   // [max_queries + 1]
+  float* d_pool_scores = nullptr;  // [max_cands]
+
+  // host-buffer entry point staging
+  float* d_q_in = nullptr;
+  int64_t* d_qo_in = nullptr;
+  int64_t* d_out_ids = nullptr;
+  float* d_out_scores = nullptr;
+};
+
+namespace gem {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+gem_status fail(gem_status code, const std::string& msg);
+gem_status cuda_fail(cudaError_t e, const char* what);
+#define GEM_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t e__ = (expr);                               \
+    if (e__ != cudaSuccess) return ::gem::cuda_fail(e__, #expr); \
+  } while (0)
+
+// Counts kernels enqueued by this library (gem_kernel_launches).
+void note_launches(int n);
+
+// ---------------------------------------------------------------- TMA maps
+bool encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, void* base, uint64_t inner,
+                    uint64_t rows, uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows,
+                    CUtensorMapSwizzle swz);
+bool encode_tmap_1d_f32(CUtensorMap* map, void* base, uint64_t n, uint32_t box);
+
+// ---------------------------------------------------------------- store helpers
+gem_status store_chunk_map(const gem_store* s, int chunk_rows, const ChunkMap** out);
+gem_status store_tmap_bf16(const gem_store* s, int box_rows, const CUtensorMap** out);
+gem_status store_tmap_fp8(const gem_store* s, int box_rows, const CUtensorMap** out);
+
+// ---------------------------------------------------------------- launchers
+// Query plan: split sets into <= 32-row parts, pack them into m_res-row blocks
+// and convert to the tensor-core operand type (bf16 or e4m3 + scale).
+gem_status launch_plan(gem_workspace* ws, const float* q, const int64_t* q_offsets,
+                       int32_t n_queries, int64_t n_q_rows, int m_res, int compute,
+                       cudaStream_t st);
+
+// Tensor-core exact MaxSim over all stored sets.
+gem_status launch_tc_score_all(const gem_store* s, gem_workspace* ws, int compute, int m_tiles,
+                               int chunk_rows, float* scores, cudaStream_t st);
+
+// FP32 SIMT exact MaxSim (Kahan over query vectors), all sets or id lists.
+gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* q,
+                            const int64_t* q_offsets, int32_t n_queries, const int64_t* cand_offsets,
+                            const int64_t* cand_ids, int64_t n_cands, float* scores, cudaStream_t st);
+
+// Per-row top-k by (score desc, id asc).
+gem_status launch_topk(gem_workspace* ws, const float* scores, const int64_t* row_offsets,
+                       int32_t rows, int64_t cols, const int64_t* ids, int32_t k,
+                       int64_t* out_ids, float* out_scores, cudaStream_t st);
+
+// FP32 -> bf16 / e4m3 store copies.
+void launch_quantize_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStream_t st);
+void launch_quantize_fp8(const float* src, uint8_t* dst, float* scale, int64_t rows,
+                         cudaStream_t st);
+
+// Build the uniform rerank-pool offsets b * depth.
+void launch_iota_offsets(int64_t* off, int32_t n, int64_t step, cudaStream_t st);
+
+}  // namespace gem

@@ -1,0 +1,383 @@
+// Exact MaxSim over every stored set on the sm_103a tensor cores (tcgen05).
+//
+// CH(Q, P) = sum_i max_j <q_i, p_j>  (Sec. 3.1, Definition 1, Eq. 1) for all
+// query parts of one pass of the plan against every set of the store.
+//
+// Work unit = (query block of M_RES = 128 * MT packed rows, document chunk).
+// A persistent CTA per SM walks units chunk-major, so the CTAs running at any
+// moment share a few chunks and the document tiles they stream are L2 hits
+// after the first reader.
+//
+// Roles inside a CTA (warp specialisation):
+//   warps 0 .. 4*MT-1  epilogue: warp w reads TMEM lanes 32*(w%4).. of M tile
+//                      w/4; one thread owns one packed query row
+//   warp 4*MT          TMA producer: query block once per unit, then the
+//                      chunk's document tiles (N rows x 128) through a
+//                      STAGES-deep shared-memory ring
+//   warp 4*MT+1        MMA issuer: per tile, MT x (K/16) tcgen05.mma into a
+//                      double-buffered TMEM accumulator (2 x MT x N columns)
+//
+// Epilogue: every thread walks its row's N accumulator columns in order.  The
+// column -> set map is the same for all rows, so a set boundary is a uniform
+// branch: the thread keeps a running max, and when a set ends the rows of each
+// query slot are summed by a g-lane xor butterfly (g = slot size) and one lane
+// writes the score.  A set never spans two chunks, so no partial maximum ever
+// leaves registers and no similarity matrix is written anywhere.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace gem {
+namespace {
+
+template <int MT, bool FP8>
+struct TcCfg {
+  static constexpr int M_RES = 128 * MT;
+  static constexpr int N = 256 / MT;              // columns per tile
+  static constexpr int ROW_BYTES = FP8 ? 128 : 256;
+  static constexpr int HALVES = FP8 ? 1 : 2;      // 128-byte swizzle atoms per row
+  static constexpr int K_STEP = FP8 ? 32 : 16;    // K per MMA instruction
+  static constexpr int K_STEPS = kDim / K_STEP;   // MMAs per tile and M tile
+  static constexpr int Q_TILE_BYTES = 128 * ROW_BYTES;
+  static constexpr int Q_BYTES = M_RES * ROW_BYTES;
+  static constexpr int STAGE_TILE_BYTES = N * ROW_BYTES;
+  static constexpr int STAGE_SCALE_BYTES = FP8 ? N * 4 : 0;
+  static constexpr int STAGE_BYTES = STAGE_TILE_BYTES + (FP8 ? 1024 : 0);
+  static constexpr int STAGES = (MT == 1) ? (FP8 ? 4 : 3) : (MT == 2 ? (FP8 ? 6 : 4) : (FP8 ? 8 : 6));
+  static constexpr int EPI_WARPS = 4 * MT;
+  static constexpr int THREADS = (EPI_WARPS + 2) * 32;
+  static constexpr int ACC_COLS = MT * N;         // 256 per accumulator buffer
+  static constexpr int TMEM_COLS = 2 * ACC_COLS;  // 512
+  static constexpr int SMEM_BYTES = 1024 /*align slack*/ + Q_BYTES + STAGES * STAGE_BYTES + 256;
+  static constexpr uint32_t IDESC = make_idesc(128, N, FP8 ? 0u : 1u, FP8 ? 0u : 1u);
+};
+
+struct TcArgs {
+  const int* hdr;
+  const int* row_part;
+  const int* part_query;
+  const int* part_g;
+  const int* part_pass;
+  const int* part_slot;
+  const float* q_scale;      // fp8 only: per packed row
+  const int64_t* doc_off;    // [n_sets + 1]
+  const int* chunk_doc;      // [n_chunks + 1]
+  int n_chunks;
+  int pass;
+  int64_t n_sets;
+  float* scores;             // [n_queries * n_sets]
+  int* status;
+};
+
+__device__ __forceinline__ float max32(const float (&v)[32], float run) {
+  float a = fmax3(v[0], v[1], v[2]);
+  float b = fmax3(v[3], v[4], v[5]);
+  float c = fmax3(v[6], v[7], v[8]);
+  float d = fmax3(v[9], v[10], v[11]);
+  float e = fmax3(v[12], v[13], v[14]);
+  float f = fmax3(v[15], v[16], v[17]);
+  float g = fmax3(v[18], v[19], v[20]);
+  float h = fmax3(v[21], v[22], v[23]);
+  float i = fmax3(v[24], v[25], v[26]);
+  float j = fmax3(v[27], v[28], v[29]);
+  float k = fmax3(v[30], v[31], run);
+  a = fmax3(a, b, c);
+  d = fmax3(d, e, f);
+  g = fmax3(g, h, i);
+  j = fmax3(j, k, a);
+  return fmax3(d, g, j);
+}
+
+template <int MT, bool FP8>
+__global__ void __launch_bounds__(TcCfg<MT, FP8>::THREADS, 1)
+tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_d,
+                    const __grid_constant__ CUtensorMap tm_scale, TcArgs a) {
+  using C = TcCfg<MT, FP8>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* q_smem = smem;
+  uint8_t* d_smem = smem + C::Q_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(d_smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + C::STAGES;
+  uint64_t* acc_full = bars + 2 * C::STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* q_full = acc_empty + 2;
+  uint64_t* q_empty = q_full + 1;
+  uint64_t* done_bar = q_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done_bar + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int qb0 = a.hdr[kHdrQbBegin + a.pass];
+  const int nqb = a.hdr[kHdrQbBegin + a.pass + 1] - qb0;
+  const long long n_units = (long long)nqb * a.n_chunks;
+  if (blockIdx.x >= n_units) return;  // uniform for the CTA
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], C::EPI_WARPS); }
+    mbar_init(q_full, 1);
+    mbar_init(q_empty, 1);
+    mbar_init(done_bar, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == C::EPI_WARPS + 1) tmem_alloc(tmem_slot, C::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == C::EPI_WARPS) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      tma_prefetch_desc(&tm_q);
+      tma_prefetch_desc(&tm_d);
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued[C::STAGES];
+      for (int s = 0; s < C::STAGES; ++s) issued[s] = 0;
+      int it = 0;
+      uint32_t q_issued = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
+        const int chunk = (int)(u / nqb);
+        const int qb = qb0 + (int)(u % nqb);
+        if (it > 0 && !mbar_wait(q_empty, (it - 1) & 1, a.status, abort_flag)) { ok = false; break; }
+        mbar_arrive_expect_tx(q_full, C::Q_BYTES);
+        ++q_issued;
+        for (int m = 0; m < MT; ++m)
+          for (int h = 0; h < C::HALVES; ++h)
+            tma_load_2d(q_smem + (m * C::HALVES + h) * 16384, &tm_q, q_full, h * 64,
+                        qb * C::M_RES + m * 128);
+        const int64_t r0 = a.doc_off[a.chunk_doc[chunk]];
+        const int64_t r1 = a.doc_off[a.chunk_doc[chunk + 1]];
+        const int64_t tile0 = FP8 ? (r0 & ~int64_t(3)) : r0;
+        const int ntiles = (int)((r1 - tile0 + C::N - 1) / C::N);
+        for (int t = 0; t < ntiles; ++t) {
+          if (!mbar_wait(&empty[stage], phase ^ 1, a.status, abort_flag)) { ok = false; break; }
+          uint8_t* dst = d_smem + stage * C::STAGE_BYTES;
+          const int row = (int)(tile0 + (int64_t)t * C::N);
+          mbar_arrive_expect_tx(&full[stage], C::STAGE_TILE_BYTES + C::STAGE_SCALE_BYTES);
+          for (int h = 0; h < C::HALVES; ++h)
+            tma_load_2d(dst + h * (C::N * 128), &tm_d, &full[stage], h * 64, row);
+          if constexpr (FP8) tma_load_1d(dst + C::STAGE_TILE_BYTES, &tm_scale, &full[stage], row);
+          issued[stage]++;
+          if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+        }
+      }
+      if (!ok) {
+        // drain: every load this thread issued must land before the CTA exits
+        for (int s = 0; s < C::STAGES; ++s)
+          if (issued[s]) { int z = 0; mbar_wait(&full[s], (issued[s] - 1) & 1, nullptr, &z); }
+        int z = 0;
+        if (q_issued) mbar_wait(q_full, (q_issued - 1) & 1, nullptr, &z);
+      }
+    }
+  } else if (warp == C::EPI_WARPS + 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      int it = 0;
+      bool ok = true;
+      for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
+        const int chunk = (int)(u / nqb);
+        const int64_t r0 = a.doc_off[a.chunk_doc[chunk]];
+        const int64_t r1 = a.doc_off[a.chunk_doc[chunk + 1]];
+        const int64_t tile0 = FP8 ? (r0 & ~int64_t(3)) : r0;
+        const int ntiles = (int)((r1 - tile0 + C::N - 1) / C::N);
+        if (!mbar_wait(q_full, it & 1, a.status, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t q_base = smem_u32(q_smem);
+        for (int t = 0; t < ntiles; ++t) {
+          if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1, a.status, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&full[stage], phase, a.status, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d_base = smem_u32(d_smem + stage * C::STAGE_BYTES);
+#pragma unroll
+          for (int m = 0; m < MT; ++m) {
+#pragma unroll
+            for (int k = 0; k < C::K_STEPS; ++k) {
+              const int half = (k * C::K_STEP * (FP8 ? 1 : 2)) / 128;
+              const int within = (k * C::K_STEP * (FP8 ? 1 : 2)) % 128;
+              uint64_t ad = sw128_desc(q_base + (m * C::HALVES + half) * 16384 + within);
+              uint64_t bd = sw128_desc(d_base + half * (C::N * 128) + within);
+              const uint32_t dt = tmem + acc * C::ACC_COLS + m * C::N;
+              if constexpr (FP8) mma_f8(dt, ad, bd, C::IDESC, k > 0);
+              else mma_bf16(dt, ad, bd, C::IDESC, k > 0);
+            }
+          }
+          mma_commit(&empty[stage]);
+          mma_commit(&acc_full[acc]);
+          if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+          if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+        }
+        if (ok) mma_commit(q_empty);
+      }
+      // all MMAs of this thread complete before the CTA releases TMEM
+      mma_commit(done_bar);
+      int z = 0;
+      mbar_wait(done_bar, 0, nullptr, &z);
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int m_tile = warp >> 2;
+    const int quad = warp & 3;
+    const int local_row = m_tile * 128 + quad * 32 + lane;
+    const uint32_t t_lane = (uint32_t)(quad * 32) << 16;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    bool ok = true;
+    for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      const int chunk = (int)(u / nqb);
+      const int qb = qb0 + (int)(u % nqb);
+      const int prow = qb * C::M_RES + local_row;
+      const int p = a.row_part[prow];
+      int g = 1;
+      bool writer = false, add = false;
+      float* dst = nullptr;
+      float row_scale = 1.f;
+      if (p >= 0) {
+        g = a.part_g[p];
+        writer = (prow == a.part_slot[p]);
+        add = a.part_pass[p] > 0;
+        dst = a.scores + (int64_t)a.part_query[p] * a.n_sets;
+      }
+      if constexpr (FP8) row_scale = a.q_scale[prow];
+      const int d0 = a.chunk_doc[chunk];
+      const int d1 = a.chunk_doc[chunk + 1];
+      const int64_t r0 = a.doc_off[d0];
+      const int64_t r1 = a.doc_off[d1];
+      const int64_t tile0 = FP8 ? (r0 & ~int64_t(3)) : r0;
+      const int ntiles = (int)((r1 - tile0 + C::N - 1) / C::N);
+      int cur = d0;
+      int64_t next_start = a.doc_off[d0 + 1];
+      float run = -INFINITY;
+
+      auto commit = [&](int doc, float v) {
+        float s = v * row_scale;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          float t = __shfl_xor_sync(0xffffffffu, s, o);
+          if (o < g) s += t;
+        }
+        if (writer) {
+          float* d = dst + doc;
+          *d = add ? (*d + s) : s;
+        }
+      };
+
+      for (int t = 0; t < ntiles; ++t) {
+        // every lane waits, then the warp agrees, so the .sync.aligned TMEM
+        // loads below always run with the whole warp
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[acc], acc_phase, a.status, abort_flag))) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int64_t base_col = tile0 + (int64_t)t * C::N;
+#pragma unroll
+        for (int grp = 0; grp < C::N / 32; ++grp) {
+          float v[32];
+          tmem_ld32(tmem + t_lane + acc * C::ACC_COLS + m_tile * C::N + grp * 32, v);
+          if (grp == C::N / 32 - 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[acc]);
+          }
+          const int64_t g0 = base_col + grp * 32;
+          if (cur >= d1) continue;
+          if (g0 < r0 - 31) continue;
+          if (g0 >= r0 && next_start >= g0 + 32) {
+            run = max32(v, run);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int64_t col = g0 + j;
+              if (col < r0 || cur >= d1) continue;
+              if (col == next_start) {
+                commit(cur, run);
+                run = -INFINITY;
+                ++cur;
+                if (cur >= d1) continue;
+                next_start = a.doc_off[cur + 1];
+              }
+              run = fmaxf(run, v[j]);
+            }
+          }
+        }
+        if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+      }
+      if (ok && cur < d1) commit(cur, run);
+    }
+  }
+
+  __syncthreads();
+  if (warp == C::EPI_WARPS + 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+template <int MT, bool FP8>
+gem_status launch_tc(const gem_store* s, gem_workspace* ws, const CUtensorMap& tm_q,
+                     const CUtensorMap& tm_d, const CUtensorMap& tm_scale, const ChunkMap* cm,
+                     float* scores, cudaStream_t st) {
+  using C = TcCfg<MT, FP8>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    GEM_CUDA_TRY(cudaFuncSetAttribute(tc_score_all_kernel<MT, FP8>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
+    attr_set = true;
+  }
+  TcArgs a;
+  a.hdr = ws->d_plan_hdr;
+  a.row_part = ws->d_row_part;
+  a.part_query = ws->d_part_query;
+  a.part_g = ws->d_part_g;
+  a.part_pass = ws->d_part_pass;
+  a.part_slot = ws->d_part_slot;
+  a.q_scale = ws->d_qpack_scale;
+  a.doc_off = s->d_offsets;
+  a.chunk_doc = cm->d_chunk_doc;
+  a.n_chunks = cm->n_chunks;
+  a.n_sets = s->n_sets;
+  a.scores = scores;
+  a.status = ws->d_status;
+  for (int pass = 0; pass < ws->n_passes; ++pass) {
+    a.pass = pass;
+    tc_score_all_kernel<MT, FP8><<<s->n_sm, C::THREADS, C::SMEM_BYTES, st>>>(tm_q, tm_d, tm_scale, a);
+    GEM_CUDA_TRY(cudaGetLastError());
+    note_launches(1);
+  }
+  return GEM_OK;
+}
+
+}  // namespace
+
+gem_status launch_tc_score_all(const gem_store* s, gem_workspace* ws, int compute, int m_tiles,
+                               int chunk_rows, float* scores, cudaStream_t st) {
+  const ChunkMap* cm = nullptr;
+  gem_status r = store_chunk_map(s, chunk_rows, &cm);
+  if (r != GEM_OK) return r;
+  if (compute == GEM_BF16) {
+    const int n = 256 / m_tiles;
+    const CUtensorMap* td = nullptr;
+    if ((r = store_tmap_bf16(s, n, &td)) != GEM_OK) return r;
+    switch (m_tiles) {
+      case 1: return launch_tc<1, false>(s, ws, ws->tmap_q_bf16, *td, *td, cm, scores, st);
+      case 2: return launch_tc<2, false>(s, ws, ws->tmap_q_bf16, *td, *td, cm, scores, st);
+      case 4: return launch_tc<4, false>(s, ws, ws->tmap_q_bf16, *td, *td, cm, scores, st);
+      default: return fail(GEM_ERR_INVALID, "m_tiles must be 1, 2 or 4");
+    }
+  }
+  return fail(GEM_ERR_UNSUPPORTED, "tensor-core scoring supports bf16 here");
+}
+
+}  // namespace gem

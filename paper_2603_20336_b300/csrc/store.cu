@@ -1,0 +1,183 @@
+// The CSR doc-set store: device copies of the vectors in FP32 / BF16 / E4M3
+// (+ per-vector scale), the offsets, chunk maps for the persistent kernels and
+// TMA tensor maps of the low-precision copies.
+#include <cuda_fp8.h>
+
+#include <mutex>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace gem {
+namespace {
+
+__global__ void quantize_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                                     int64_t n4) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float4 v = reinterpret_cast<const float4*>(src)[i];
+    __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
+    __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
+    uint2 w;
+    w.x = *reinterpret_cast<uint32_t*>(&lo);
+    w.y = *reinterpret_cast<uint32_t*>(&hi);
+    reinterpret_cast<uint2*>(dst)[i] = w;
+  }
+}
+
+// One warp per vector: s = max_k |x_k| / 448 (IEEE division), codes = E4M3(x_k / s)
+// round to nearest even, saturating; a zero vector gets s = 1.
+__global__ void quantize_fp8_kernel(const float* __restrict__ src, uint8_t* __restrict__ dst,
+                                    float* __restrict__ scale, int64_t rows) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < rows;
+       r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    float4 v = reinterpret_cast<const float4*>(src + r * kDim)[lane];
+    float a = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+    const float s = (a == 0.f) ? 1.f : __fdiv_rn(a, 448.f);
+    const float xs[4] = {v.x, v.y, v.z, v.w};
+    uint32_t packed = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(__fdiv_rn(xs[j], s), __NV_SATFINITE, __NV_E4M3);
+      packed |= (uint32_t)c << (8 * j);
+    }
+    reinterpret_cast<uint32_t*>(dst + r * kDim)[lane] = packed;
+    if (lane == 0) scale[r] = s;
+  }
+}
+
+__global__ void iota_offsets_kernel(int64_t* off, int n, int64_t step) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
+    off[i] = (int64_t)i * step;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+std::mutex g_store_mutex;  // guards the lazily built per-store caches
+
+}  // namespace
+
+bool encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, void* base, uint64_t inner,
+                    uint64_t rows, uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows,
+                    CUtensorMapSwizzle swz) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_inner, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, dtype, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_tmap_1d_f32(CUtensorMap* map, void* base, uint64_t n, uint32_t box) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[1] = {n};
+  cuuint64_t strides[1] = {n * 4};
+  cuuint32_t boxd[1] = {box};
+  cuuint32_t estr[1] = {1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 1, base, dims, strides, boxd, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void launch_quantize_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStream_t st) {
+  const int64_t n4 = n / 4;
+  const int grid = (int)std::min<int64_t>((n4 + 255) / 256, 148 * 16);
+  if (grid > 0) { quantize_bf16_kernel<<<grid, 256, 0, st>>>(src, dst, n4); note_launches(1); }
+}
+
+void launch_quantize_fp8(const float* src, uint8_t* dst, float* scale, int64_t rows, cudaStream_t st) {
+  const int grid = (int)std::min<int64_t>((rows * 32 + 255) / 256, 148 * 16);
+  if (grid > 0) { quantize_fp8_kernel<<<grid, 256, 0, st>>>(src, dst, scale, rows); note_launches(1); }
+}
+
+void launch_iota_offsets(int64_t* off, int32_t n, int64_t step, cudaStream_t st) {
+  iota_offsets_kernel<<<(n + 256) / 256, 256, 0, st>>>(off, n, step);
+  note_launches(1);
+}
+
+gem_status store_chunk_map(const gem_store* s, int chunk_rows, const ChunkMap** out) {
+  std::lock_guard<std::mutex> lk(g_store_mutex);
+  auto it = s->chunks.find(chunk_rows);
+  if (it != s->chunks.end()) { *out = &it->second; return GEM_OK; }
+  std::vector<int> starts;
+  starts.reserve(s->n_sets / 64 + 2);
+  int64_t d = 0;
+  const auto& off = s->h_offsets;
+  while (d < s->n_sets) {
+    starts.push_back((int)d);
+    const int64_t limit = off[d] + chunk_rows;
+    int64_t e = d + 1;
+    while (e < s->n_sets && off[e + 1] <= limit) ++e;
+    d = e;
+  }
+  starts.push_back((int)s->n_sets);
+  ChunkMap cm;
+  cm.chunk_rows = chunk_rows;
+  cm.n_chunks = (int)starts.size() - 1;
+  int dev_prev = 0;
+  cudaGetDevice(&dev_prev);
+  cudaSetDevice(s->device);
+  cudaError_t e1 = cudaMalloc(&cm.d_chunk_doc, sizeof(int) * starts.size());
+  if (e1 == cudaSuccess)
+    e1 = cudaMemcpy(cm.d_chunk_doc, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice);
+  cudaSetDevice(dev_prev);
+  if (e1 != cudaSuccess) return cuda_fail(e1, "chunk map upload");
+  auto res = s->chunks.emplace(chunk_rows, cm);
+  *out = &res.first->second;
+  return GEM_OK;
+}
+
+gem_status store_tmap_bf16(const gem_store* s, int box_rows, const CUtensorMap** out) {
+  std::lock_guard<std::mutex> lk(g_store_mutex);
+  if (!s->d_bf16) return fail(GEM_ERR_STATE, "store keeps no bf16 copy");
+  auto it = s->tmap_bf16.find(box_rows);
+  if (it == s->tmap_bf16.end()) {
+    CUtensorMap m;
+    if (!encode_tmap_2d(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, s->d_bf16, kDim, s->n_vecs, kDim * 2, 64,
+                        box_rows, CU_TENSOR_MAP_SWIZZLE_128B))
+      return fail(GEM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the bf16 store");
+    it = s->tmap_bf16.emplace(box_rows, m).first;
+  }
+  *out = &it->second;
+  return GEM_OK;
+}
+
+gem_status store_tmap_fp8(const gem_store* s, int box_rows, const CUtensorMap** out) {
+  std::lock_guard<std::mutex> lk(g_store_mutex);
+  if (!s->d_fp8) return fail(GEM_ERR_STATE, "store keeps no fp8 copy");
+  auto it = s->tmap_fp8.find(box_rows);
+  if (it == s->tmap_fp8.end()) {
+    CUtensorMap m;
+    if (!encode_tmap_2d(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, s->d_fp8, kDim, s->n_vecs, kDim, 128,
+                        box_rows, CU_TENSOR_MAP_SWIZZLE_128B))
+      return fail(GEM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fp8 store");
+    it = s->tmap_fp8.emplace(box_rows, m).first;
+  }
+  *out = &it->second;
+  return GEM_OK;
+}
+
+}  // namespace gem

@@ -1,0 +1,227 @@
+"""GPU parity of the store, exact scoring (FP32 SIMT and BF16 tensor cores),
+id-list scoring, top-k and the search pipeline against the FP64 oracle.
+
+Tolerances (also derived in the design notes):
+  FP32 path:  |s - s64| <= 1e-5 * sum_i |max_j <q_i, p_j>|  (relative to the L1
+              of the per-query-vector terms; 128-term FMA chains of unit vectors
+              carry ~1e-7 relative error per term)
+  BF16 path:  |s - s64| <= 2e-2 per score against the FP64 score of the FP32
+              inputs (storage rounding), and <= 2e-4 * m_q against the FP64
+              score of the bf16-rounded inputs (FP32 accumulation only)
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gem():
+    import paper_2603_20336_b300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def cfg1(gem):
+    w = synth.exact_fp32()
+    store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("f32", "bf16", "fp8"))
+    q = w.queries.vecs.cuda()
+    qo = torch.from_numpy(w.queries.offsets).cuda()
+    ws = gem.Workspace(store, max_queries=64, max_q_rows=4096, max_q_len=128, max_cands=64 * 256,
+                       max_k=256)
+    S64, L1 = oracle.score_all(w.queries.vecs, w.queries.offsets, w.docs.vecs, w.docs.offsets,
+                               with_l1=True)
+    return dict(w=w, store=store, ws=ws, q=q, qo=qo, S64=S64, L1=L1)
+
+
+def test_store_copies_match_oracle_rounding(gem, cfg1):
+    w, store = cfg1["w"], cfg1["store"]
+    X = w.docs.vecs.numpy()
+    bits = store.export("bf16").cpu().numpy().view(np.uint16)
+    want = oracle.bf16_round(X).view(np.uint32) >> 16
+    np.testing.assert_array_equal(bits.astype(np.uint32), want.astype(np.uint32))
+    codes, scale = oracle.fp8_e4m3_quantize(X)
+    got_scale = store.export("fp8_scale").cpu().numpy()
+    np.testing.assert_array_equal(got_scale, scale)
+    got_codes = store.export("fp8").cpu().view(torch.float8_e4m3fn).float().numpy()
+    np.testing.assert_array_equal(got_codes.astype(np.float64), codes)
+    np.testing.assert_array_equal(store.export("offsets").cpu().numpy(), w.docs.offsets)
+
+
+def test_score_all_f32_matches_oracle(gem, cfg1):
+    S = gem.score_all(cfg1["store"], cfg1["ws"], cfg1["q"], cfg1["qo"], "f32").cpu().numpy()
+    err = np.abs(S.astype(np.float64) - cfg1["S64"])
+    assert np.all(err <= 1e-5 * cfg1["L1"]), err.max()
+    assert cfg1["ws"].status() == 0
+
+
+def test_score_all_bf16_matches_oracle(gem, cfg1):
+    w = cfg1["w"]
+    S = gem.score_all(cfg1["store"], cfg1["ws"], cfg1["q"], cfg1["qo"], "bf16").cpu().numpy()
+    assert cfg1["ws"].status() == 0
+    err = np.abs(S.astype(np.float64) - cfg1["S64"])
+    assert err.max() <= 2e-2, err.max()
+    # against the FP64 score of the bf16-rounded inputs only FP32 accumulation remains
+    Sq = oracle.score_all(oracle.bf16_round(w.queries.vecs.numpy()), w.queries.offsets,
+                          oracle.bf16_round(w.docs.vecs.numpy()), w.docs.offsets)
+    err2 = np.abs(S.astype(np.float64) - Sq)
+    assert err2.max() <= 2e-4 * 32, err2.max()
+
+
+@pytest.mark.parametrize("lens", [
+    [1, 2, 3, 5, 8, 13, 21, 32],          # every slot size, single pass
+    [33, 64, 40, 7, 100, 128, 31, 65],    # multi-part queries (up to 4 passes)
+    [32] * 19,                            # several query blocks
+])
+def test_score_all_bf16_query_length_mix(gem, cfg1, lens):
+    w = cfg1["w"]
+    lens = np.array(lens)
+    qs = synth.vector_sets(lens, synth.centres(64, 1235), 4242)
+    q = qs.vecs.cuda()
+    qo = torch.from_numpy(qs.offsets).cuda()
+    S = gem.score_all(cfg1["store"], cfg1["ws"], q, qo, "bf16").cpu().numpy()
+    assert cfg1["ws"].status() == 0
+    Sq = oracle.score_all(oracle.bf16_round(qs.vecs.numpy()), qs.offsets,
+                          oracle.bf16_round(w.docs.vecs.numpy()), w.docs.offsets)
+    tol = 2e-4 * lens[:, None]
+    assert np.all(np.abs(S - Sq) <= tol), np.abs(S - Sq).max()
+
+
+def test_score_ids_f32_matches_oracle(gem, cfg1):
+    w = cfg1["w"]
+    rng = np.random.default_rng(5)
+    B = 10
+    lens = rng.integers(0, 40, size=B)
+    co = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    ids = rng.integers(-1, w.docs.n_sets, size=int(co[-1])).astype(np.int64)
+    S = gem.score_ids(cfg1["store"], cfg1["ws"], cfg1["q"], cfg1["qo"], torch.from_numpy(co).cuda(),
+                      torch.from_numpy(ids).cuda(), "f32").cpu().numpy()
+    assert cfg1["ws"].status() == 0
+    want = oracle.score_ids(w.queries.vecs, w.queries.offsets, w.docs.vecs, w.docs.offsets, co, ids)
+    for t in range(len(ids)):
+        if ids[t] < 0:
+            assert S[t] == -np.inf
+        else:
+            b = int(np.searchsorted(co, t, side="right") - 1)
+            assert abs(S[t] - want[t]) <= 1e-5 * cfg1["L1"][b, ids[t]]
+            # bit-identical to the all-sets FP32 form (same arithmetic order)
+    S_all = gem.score_all(cfg1["store"], cfg1["ws"], cfg1["q"], cfg1["qo"], "f32").cpu().numpy()
+    for t in range(len(ids)):
+        if ids[t] >= 0:
+            b = int(np.searchsorted(co, t, side="right") - 1)
+            assert S[t] == S_all[b, ids[t]]
+
+
+def test_score_ids_out_of_range_id_sets_status(gem, cfg1):
+    co = torch.tensor([0, 2] + [2] * 9, dtype=torch.int64, device="cuda")
+    ids = torch.tensor([0, 10**6], dtype=torch.int64, device="cuda")
+    S = gem.score_ids(cfg1["store"], cfg1["ws"], cfg1["q"], cfg1["qo"], co, ids, "f32")
+    assert cfg1["ws"].status() == 7          # GEM_ERR_BOUNDS
+    assert torch.isnan(S[1]).item() and torch.isfinite(S[0]).item()
+    assert cfg1["ws"].status() == 0          # cleared after the read
+
+
+def _check_topk(ids, sc, want_ids, want_sc):
+    np.testing.assert_array_equal(ids, want_ids)
+    np.testing.assert_array_equal(sc.astype(np.float64), want_sc)
+
+
+@pytest.mark.parametrize("n,k", [(1, 1), (5, 10), (1000, 10), (4099, 1000), (70000, 2000), (300, 300)])
+def test_topk_matches_oracle(gem, cfg1, n, k):
+    rng = np.random.default_rng(n + k)
+    s = np.round(rng.standard_normal((3, n)), 2).astype(np.float32)   # heavy ties
+    ids, sc = gem.topk(cfg1["ws"], torch.from_numpy(s).cuda(), k)
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    for r in range(3):
+        wi, ws_ = oracle.topk(s[r], k)
+        m = len(wi)
+        _check_topk(ids[r, :m], sc[r, :m], wi, ws_)
+        assert np.all(ids[r, m:] == -1) and np.all(sc[r, m:] == -np.inf)
+
+
+def test_topk_explicit_ids_ragged_and_all_equal(gem, cfg1):
+    rng = np.random.default_rng(3)
+    lens = np.array([0, 7, 500, 3])
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    s = np.full(int(off[-1]), 0.5, np.float32)
+    s[7:507] = np.round(rng.standard_normal(500), 1)
+    ids = rng.permutation(100000)[: int(off[-1])].astype(np.int64)
+    ids[2] = -1                                        # empty slot is skipped
+    gi, gs = gem.topk(cfg1["ws"], torch.from_numpy(s).cuda(), 20, ids=torch.from_numpy(ids).cuda(),
+                      row_offsets=torch.from_numpy(off).cuda())
+    gi, gs = gi.cpu().numpy(), gs.cpu().numpy()
+    for r in range(4):
+        seg = slice(off[r], off[r + 1])
+        keep = ids[seg] >= 0
+        wi, ws_ = oracle.topk(s[seg][keep], 20, ids[seg][keep])
+        m = len(wi)
+        _check_topk(gi[r, :m], gs[r, :m], wi, ws_)
+        assert np.all(gi[r, m:] == -1)
+
+
+@pytest.mark.parametrize("compute", ["bf16", "f32"])
+def test_search_pipeline_matches_exact_top10(gem, cfg1, compute):
+    ids, sc = gem.search(cfg1["store"], cfg1["ws"], cfg1["q"], cfg1["qo"], compute, rerank_depth=200, k=10)
+    assert cfg1["ws"].status() == 0
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    S64 = cfg1["S64"]
+    for b in range(S64.shape[0]):
+        wi, ws_ = oracle.topk(S64[b], 10)
+        got = set(ids[b].tolist())
+        for x in set(wi.tolist()) ^ got:
+            # a swap is accepted only between ids whose exact scores tie within 1e-6
+            assert abs(S64[b, x] - ws_[-1]) <= 1e-6 * max(1.0, abs(ws_[-1])), (b, x)
+        err = np.abs(sc[b].astype(np.float64) - S64[b, ids[b]])
+        assert np.all(err <= 1e-5 * cfg1["L1"][b, ids[b]])
+
+
+def test_search_host_buffers(gem, cfg1):
+    w = cfg1["w"]
+    q = w.queries.vecs.pin_memory()
+    qo = torch.from_numpy(w.queries.offsets)
+    ids_h, sc_h = gem.search_host(cfg1["store"], cfg1["ws"], q, qo, "bf16", rerank_depth=100, k=10)
+    ids_d, sc_d = gem.search(cfg1["store"], cfg1["ws"], cfg1["q"], cfg1["qo"], "bf16", rerank_depth=100, k=10)
+    assert torch.equal(ids_h, ids_d.cpu()) and torch.equal(sc_h, sc_d.cpu())
+
+
+def test_edge_cases_single_set_single_vector_and_long_set(gem):
+    rng = np.random.default_rng(9)
+    # one set of one vector; one long set spanning several chunks; short sets
+    lens = np.array([1, 70000, 1, 3, 200])
+    X = rng.standard_normal((int(lens.sum()), 128))
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    X = X.astype(np.float32)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    store = gem.Store(torch.from_numpy(X).cuda(), off, keep=("f32", "bf16"))
+    ws = gem.Workspace(store, max_queries=4, max_q_rows=256, max_q_len=64)
+    qlens = np.array([1, 32, 64])
+    Q = rng.standard_normal((int(qlens.sum()), 128))
+    Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+    Q = Q.astype(np.float32)
+    qo = np.concatenate([[0], np.cumsum(qlens)]).astype(np.int64)
+    S64, L1 = oracle.score_all(Q, qo, X, off, with_l1=True)
+    Sf = gem.score_all(store, ws, torch.from_numpy(Q).cuda(), torch.from_numpy(qo).cuda(), "f32").cpu().numpy()
+    assert np.all(np.abs(Sf - S64) <= 1e-5 * L1)
+    Sb = gem.score_all(store, ws, torch.from_numpy(Q).cuda(), torch.from_numpy(qo).cuda(), "bf16").cpu().numpy()
+    Sq = oracle.score_all(oracle.bf16_round(Q), qo, oracle.bf16_round(X), off)
+    assert np.all(np.abs(Sb - Sq) <= 2e-4 * qlens[:, None])
+    assert ws.status() == 0
+
+
+def test_invalid_arguments_are_rejected_before_launch(gem, cfg1):
+    with pytest.raises(gem.GemError) as e:
+        gem.score_all(cfg1["store"], cfg1["ws"], cfg1["q"], cfg1["qo"], 7)
+    assert e.value.code == 1
+    with pytest.raises(gem.GemError):
+        gem.search(cfg1["store"], cfg1["ws"], cfg1["q"], cfg1["qo"], "bf16", rerank_depth=5, k=10)
+    # device-resident offsets that are not monotone are caught on the device
+    bad = cfg1["qo"].clone()
+    bad[3] = bad[2]
+    out = torch.full((10, cfg1["store"].n_sets), 7.0, device="cuda")
+    gem.score_all(cfg1["store"], cfg1["ws"], cfg1["q"], bad, "bf16", out=out)
+    assert cfg1["ws"].status() == 1
+    assert torch.all(out == 7.0)             # nothing was scored
