@@ -65,12 +65,17 @@ enum {
   GEM_KEEP_FP8 = 4u    /* E4M3 codes + per-vector FP32 scale s_j = max_k |x_jk| / 448 */
 };
 
-/* Internal arrays a store can copy out (gem_store_export). */
+/* Internal arrays a store can copy out (gem_store_export).  The bf16 and
+ * E4M3 copies use a padded layout: set i owns rows pad_offsets[i] ..
+ * pad_offsets[i+1]-1, its length rounded up to a multiple of 8, and the extra
+ * rows repeat the set's last vector (a repeated vector leaves every maximum of
+ * Eq. 1 unchanged). */
 enum {
-  GEM_EXPORT_BF16 = 0,       /* uint16 [n_vecs * 128] bfloat16 bit patterns */
-  GEM_EXPORT_FP8 = 1,        /* uint8  [n_vecs * 128] E4M3 bit patterns */
-  GEM_EXPORT_FP8_SCALE = 2,  /* float  [n_vecs] per-vector scales */
-  GEM_EXPORT_OFFSETS = 3     /* int64  [n_sets + 1] */
+  GEM_EXPORT_BF16 = 0,        /* uint16 [n_pad_vecs * 128] bfloat16 bit patterns */
+  GEM_EXPORT_FP8 = 1,         /* uint8  [n_pad_vecs * 128] E4M3 bit patterns */
+  GEM_EXPORT_FP8_SCALE = 2,   /* float  [n_pad_vecs] per-vector scales */
+  GEM_EXPORT_OFFSETS = 3,     /* int64  [n_sets + 1] */
+  GEM_EXPORT_PAD_OFFSETS = 4  /* int64  [n_sets + 1] offsets of the padded layout */
 };
 
 typedef struct gem_store gem_store;
@@ -98,9 +103,10 @@ gem_status gem_store_create(const float* vecs, const int64_t* offsets, int64_t n
                             uint32_t keep_mask, int inputs_on_host, void* stream, gem_store** out);
 void gem_store_destroy(gem_store* store);
 
-/* Sizes of a store.  Any output pointer may be NULL. */
+/* Sizes of a store (n_pad_vecs: rows of the padded bf16 / E4M3 layout).  Any
+ * output pointer may be NULL. */
 gem_status gem_store_info(const gem_store* store, int64_t* n_sets, int64_t* n_vecs,
-                          uint32_t* keep_mask);
+                          int64_t* n_pad_vecs, uint32_t* keep_mask);
 
 /* Copies one internal array (GEM_EXPORT_*) into the device buffer dst of
  * dst_bytes bytes (must be at least the array's size). */
@@ -120,6 +126,15 @@ gem_status gem_workspace_create(const gem_store* store, int32_t max_queries, int
                                 int32_t max_q_len, int64_t max_cands, int32_t max_k,
                                 gem_workspace** out);
 void gem_workspace_destroy(gem_workspace* ws);
+
+/*
+ * Schedule of the tensor-core scoring kernels on this workspace (the knobs the
+ * autotuner varies; results do not depend on them):
+ *   m_tiles     resident query rows per CTA / 128: 1, 2 or 4 (document tile
+ *               width 256 / m_tiles columns)
+ *   chunk_rows  document rows per work unit (whole sets; 1024 .. 2^24)
+ */
+gem_status gem_workspace_set_schedule(gem_workspace* ws, int32_t m_tiles, int32_t chunk_rows);
 
 /*
  * Exact CH of every query set against every stored set (Eq. 1 for all P in D,

@@ -85,15 +85,21 @@ class Store:
             _check(lib.gem_store_create(_ptr(v), _ptr(off), n_sets, v.shape[1], mask, 1,
                                         _stream(stream), ctypes.byref(h)))
         self.handle = h
-        self.n_sets = n_sets
-        self.n_vecs = int(offsets[-1])
+        n_s, n_v, n_p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.gem_store_info(h, ctypes.byref(n_s), ctypes.byref(n_v), ctypes.byref(n_p), None))
+        self.n_sets = n_s.value
+        self.n_vecs = n_v.value
+        self.n_pad_vecs = n_p.value
         self.keep = tuple(keep)
 
     def export(self, what: str, stream=None) -> torch.Tensor:
-        """Copy of an internal array: 'bf16' (uint16 bits), 'fp8' (uint8 bits),
-        'fp8_scale' (float32) or 'offsets' (int64)."""
-        spec = {"bf16": (0, torch.int16, (self.n_vecs, 128)), "fp8": (1, torch.uint8, (self.n_vecs, 128)),
-                "fp8_scale": (2, torch.float32, (self.n_vecs,)), "offsets": (3, torch.int64, (self.n_sets + 1,))}
+        """Copy of an internal array: 'bf16' (uint16 bits, padded layout), 'fp8'
+        (uint8 bits, padded), 'fp8_scale' (float32, padded), 'offsets' or
+        'pad_offsets' (int64)."""
+        P = self.n_pad_vecs
+        spec = {"bf16": (0, torch.int16, (P, 128)), "fp8": (1, torch.uint8, (P, 128)),
+                "fp8_scale": (2, torch.float32, (P,)), "offsets": (3, torch.int64, (self.n_sets + 1,)),
+                "pad_offsets": (4, torch.int64, (self.n_sets + 1,))}
         code, dt, shape = spec[what]
         out = torch.empty(shape, dtype=dt, device="cuda")
         _check(lib.gem_store_export(self.handle, code, _ptr(out), out.numel() * out.element_size(),
@@ -211,3 +217,8 @@ def search_host(store: Store, ws: Workspace, q_host, q_offsets_host, compute="bf
     _check(lib.gem_search_host(store.handle, ws.handle, _ptr(q), _ptr(qo), B, _dtype_code(compute),
                                rerank_depth, k, _ptr(out_ids), _ptr(out_scores), _stream(stream)))
     return out_ids, out_scores
+
+
+def set_schedule(ws: Workspace, m_tiles: int = 2, chunk_rows: int = 1 << 16):
+    """Tensor-core kernel schedule of a workspace (results do not depend on it)."""
+    _check(lib.gem_workspace_set_schedule(ws.handle, m_tiles, chunk_rows))

@@ -13,10 +13,11 @@ SIGNATURES = {
     "gem_device_check": (C.c_int, [C.c_int]),
     "gem_store_create": (C.c_int, [P, P, I64, I32, U32, C.c_int, P, C.POINTER(P)]),
     "gem_store_destroy": (None, [P]),
-    "gem_store_info": (C.c_int, [P, P, P, P]),
+    "gem_store_info": (C.c_int, [P, P, P, P, P]),
     "gem_store_export": (C.c_int, [P, I32, P, SZ, P]),
     "gem_workspace_create": (C.c_int, [P, I32, I64, I32, I64, I32, C.POINTER(P)]),
     "gem_workspace_destroy": (None, [P]),
+    "gem_workspace_set_schedule": (C.c_int, [P, I32, I32]),
     "gem_score_all": (C.c_int, [P, P, P, P, I32, I64, I32, P, P]),
     "gem_score_ids": (C.c_int, [P, P, P, P, I32, I64, P, P, I64, I32, P, P]),
     "gem_topk": (C.c_int, [P, P, P, I32, I64, P, I32, P, P, P]),

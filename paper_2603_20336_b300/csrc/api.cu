@@ -12,11 +12,6 @@ namespace gem {
 namespace {
 thread_local std::string g_last_error;
 
-// Default schedule of the tensor-core scoring kernel: 2 M tiles (256 resident
-// query rows) x 128-column document tiles, chunks of about 64K vectors.
-constexpr int kDefaultMTiles = 2;
-constexpr int kDefaultChunkRows = 1 << 16;
-
 bool device_is_sm103(int dev) {
   cudaDeviceProp p;
   if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return false;
@@ -94,6 +89,7 @@ void gem_store_destroy(gem_store* s) {
   cudaGetDevice(&prev);
   cudaSetDevice(s->device);
   dfree(s->d_offsets);
+  dfree(s->d_pad_offsets);
   dfree(s->d_f32);
   dfree(s->d_bf16);
   dfree(s->d_fp8);
@@ -141,13 +137,25 @@ gem_status gem_store_create(const float* vecs, const int64_t* offsets, int64_t n
     if (len > s->max_set_len) s->max_set_len = len;
   }
   s->n_vecs = s->h_offsets[n_sets];
-  if (s->n_vecs >= (int64_t)1 << 31) { gem_store_destroy(s); return fail(GEM_ERR_INVALID, "too many vectors"); }
+  s->h_pad_offsets.resize(n_sets + 1);
+  s->h_pad_offsets[0] = 0;
+  for (int64_t i = 0; i < n_sets; ++i) {
+    const int64_t len = s->h_offsets[i + 1] - s->h_offsets[i];
+    s->h_pad_offsets[i + 1] = s->h_pad_offsets[i] + (len + kRowAlign - 1) / kRowAlign * kRowAlign;
+  }
+  s->n_pad_vecs = s->h_pad_offsets[n_sets];
+  if (s->n_pad_vecs >= (int64_t)1 << 31) { gem_store_destroy(s); return fail(GEM_ERR_INVALID, "too many vectors"); }
   const int64_t V = s->n_vecs;
+  const int64_t VP = s->n_pad_vecs;
 
   gem_status r;
   if ((r = dmalloc(&s->d_offsets, n_sets + 1, "offsets")) != GEM_OK) { gem_store_destroy(s); return r; }
+  if ((r = dmalloc(&s->d_pad_offsets, n_sets + 1, "padded offsets")) != GEM_OK) { gem_store_destroy(s); return r; }
   cudaError_t e = cudaMemcpyAsync(s->d_offsets, s->h_offsets.data(), sizeof(int64_t) * (n_sets + 1),
                                   cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_pad_offsets, s->h_pad_offsets.data(), sizeof(int64_t) * (n_sets + 1),
+                        cudaMemcpyHostToDevice, st);
   // the FP32 source of the quantised copies lives on the device during the build
   float* src = nullptr;
   float* tmp = nullptr;
@@ -166,17 +174,17 @@ gem_status gem_store_create(const float* vecs, const int64_t* offsets, int64_t n
                           inputs_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
   }
   if (e == cudaSuccess && (keep_mask & GEM_KEEP_BF16)) {
-    if ((r = dmalloc(&s->d_bf16, V * kDim, "bf16 copy")) != GEM_OK) { dfree(tmp); gem_store_destroy(s); return r; }
-    launch_quantize_bf16(src, s->d_bf16, V * kDim, st);
+    if ((r = dmalloc(&s->d_bf16, VP * kDim, "bf16 copy")) != GEM_OK) { dfree(tmp); gem_store_destroy(s); return r; }
+    launch_quantize_bf16(src, s->d_offsets, s->d_pad_offsets, n_sets, s->d_bf16, st);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && (keep_mask & GEM_KEEP_FP8)) {
-    if ((r = dmalloc(&s->d_fp8, V * kDim, "fp8 copy")) != GEM_OK) { dfree(tmp); gem_store_destroy(s); return r; }
+    if ((r = dmalloc(&s->d_fp8, VP * kDim, "fp8 copy")) != GEM_OK) { dfree(tmp); gem_store_destroy(s); return r; }
     // scales padded so that 1-D TMA boxes past the last vector stay in bounds
-    if ((r = dmalloc(&s->d_fp8_scale, V + 1024, "fp8 scales")) != GEM_OK) { dfree(tmp); gem_store_destroy(s); return r; }
-    e = cudaMemsetAsync(s->d_fp8_scale, 0, sizeof(float) * (V + 1024), st);
+    if ((r = dmalloc(&s->d_fp8_scale, VP + 1024, "fp8 scales")) != GEM_OK) { dfree(tmp); gem_store_destroy(s); return r; }
+    e = cudaMemsetAsync(s->d_fp8_scale, 0, sizeof(float) * (VP + 1024), st);
     if (e == cudaSuccess) {
-      launch_quantize_fp8(src, s->d_fp8, s->d_fp8_scale, V, st);
+      launch_quantize_fp8(src, s->d_offsets, s->d_pad_offsets, n_sets, s->d_fp8, s->d_fp8_scale, st);
       e = cudaGetLastError();
     }
   }
@@ -187,10 +195,12 @@ gem_status gem_store_create(const float* vecs, const int64_t* offsets, int64_t n
   return GEM_OK;
 }
 
-gem_status gem_store_info(const gem_store* s, int64_t* n_sets, int64_t* n_vecs, uint32_t* keep_mask) {
+gem_status gem_store_info(const gem_store* s, int64_t* n_sets, int64_t* n_vecs, int64_t* n_pad_vecs,
+                          uint32_t* keep_mask) {
   if (!s) return fail(GEM_ERR_INVALID, "store is NULL");
   if (n_sets) *n_sets = s->n_sets;
   if (n_vecs) *n_vecs = s->n_vecs;
+  if (n_pad_vecs) *n_pad_vecs = s->n_pad_vecs;
   if (keep_mask) *keep_mask = s->keep;
   return GEM_OK;
 }
@@ -200,10 +210,11 @@ gem_status gem_store_export(const gem_store* s, int32_t what, void* dst, size_t 
   const void* src = nullptr;
   size_t bytes = 0;
   switch (what) {
-    case GEM_EXPORT_BF16: src = s->d_bf16; bytes = sizeof(uint16_t) * s->n_vecs * kDim; break;
-    case GEM_EXPORT_FP8: src = s->d_fp8; bytes = (size_t)s->n_vecs * kDim; break;
-    case GEM_EXPORT_FP8_SCALE: src = s->d_fp8_scale; bytes = sizeof(float) * s->n_vecs; break;
+    case GEM_EXPORT_BF16: src = s->d_bf16; bytes = sizeof(uint16_t) * s->n_pad_vecs * kDim; break;
+    case GEM_EXPORT_FP8: src = s->d_fp8; bytes = (size_t)s->n_pad_vecs * kDim; break;
+    case GEM_EXPORT_FP8_SCALE: src = s->d_fp8_scale; bytes = sizeof(float) * s->n_pad_vecs; break;
     case GEM_EXPORT_OFFSETS: src = s->d_offsets; bytes = sizeof(int64_t) * (s->n_sets + 1); break;
+    case GEM_EXPORT_PAD_OFFSETS: src = s->d_pad_offsets; bytes = sizeof(int64_t) * (s->n_sets + 1); break;
     default: return fail(GEM_ERR_INVALID, "unknown export");
   }
   if (!src) return fail(GEM_ERR_STATE, "store does not keep that array");
@@ -306,6 +317,15 @@ gem_status gem_workspace_create(const gem_store* s, int32_t max_queries, int64_t
   return GEM_OK;
 }
 
+gem_status gem_workspace_set_schedule(gem_workspace* w, int32_t m_tiles, int32_t chunk_rows) {
+  if (!w) return fail(GEM_ERR_INVALID, "workspace is NULL");
+  if (m_tiles != 1 && m_tiles != 2 && m_tiles != 4) return fail(GEM_ERR_INVALID, "m_tiles must be 1, 2 or 4");
+  if (chunk_rows < 1024 || chunk_rows > (1 << 24)) return fail(GEM_ERR_INVALID, "chunk_rows out of range");
+  w->tc_m_tiles = m_tiles;
+  w->tc_chunk_rows = chunk_rows;
+  return GEM_OK;
+}
+
 // ----------------------------------------------------------------------------- scoring
 
 static gem_status check_query_args(const gem_store* s, gem_workspace* w, const float* q,
@@ -327,10 +347,10 @@ static gem_status score_all_impl(const gem_store* s, gem_workspace* w, const flo
   }
   if (compute == GEM_BF16) {
     if (!s->d_bf16) return fail(GEM_ERR_STATE, "store keeps no bf16 copy");
-    const int mt = kDefaultMTiles;
+    const int mt = w->tc_m_tiles;
     gem_status r = launch_plan(w, q, q_offsets, n_queries, n_q_rows, 128 * mt, compute, st);
     if (r != GEM_OK) return r;
-    return launch_tc_score_all(s, w, compute, mt, kDefaultChunkRows, scores, st);
+    return launch_tc_score_all(s, w, compute, mt, w->tc_chunk_rows, scores, st);
   }
   if (compute == GEM_FP8_E4M3) return fail(GEM_ERR_UNSUPPORTED, "fp8 scoring is not available");
   return fail(GEM_ERR_INVALID, "unknown compute dtype");

@@ -20,6 +20,9 @@ constexpr int kClasses = 6;       // slot sizes 32, 16, 8, 4, 2, 1 rows
 constexpr int kCombos = kMaxPasses * kClasses;
 constexpr int kMaxK = 4096;       // largest top-k
 constexpr int kPlanHdrInts = 64;
+// The low-precision store copies pad every set to a multiple of kRowAlign rows
+// with copies of the set's last vector, so set boundaries fall on 8-row steps.
+constexpr int kRowAlign = 8;
 
 // Plan header layout (device int32 array).
 enum : int {
@@ -53,6 +56,10 @@ struct gem_store {
   uint32_t keep = 0;
   std::vector<int64_t> h_offsets;
   int64_t* d_offsets = nullptr;
+  // padded layout of the bf16 / fp8 copies
+  int64_t n_pad_vecs = 0;
+  std::vector<int64_t> h_pad_offsets;
+  int64_t* d_pad_offsets = nullptr;
   float* d_f32 = nullptr;
   __nv_bfloat16* d_bf16 = nullptr;
   uint8_t* d_fp8 = nullptr;
@@ -73,6 +80,8 @@ struct gem_workspace {
   int64_t max_cands = 0;
   int32_t max_k = 0;
   int n_passes = 0;
+  int tc_m_tiles = 2;          // schedule of the tensor-core kernels
+  int tc_chunk_rows = 1 << 16;
 
   int* d_status = nullptr;
 
@@ -153,10 +162,11 @@ gem_status launch_topk(gem_workspace* ws, const float* scores, const int64_t* ro
                        int32_t rows, int64_t cols, const int64_t* ids, int32_t k,
                        int64_t* out_ids, float* out_scores, cudaStream_t st);
 
-// FP32 -> bf16 / e4m3 store copies.
-void launch_quantize_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStream_t st);
-void launch_quantize_fp8(const float* src, uint8_t* dst, float* scale, int64_t rows,
-                         cudaStream_t st);
+// FP32 -> bf16 / e4m3 store copies in the padded layout.
+void launch_quantize_bf16(const float* src, const int64_t* off, const int64_t* pad_off,
+                          int64_t n_sets, __nv_bfloat16* dst, cudaStream_t st);
+void launch_quantize_fp8(const float* src, const int64_t* off, const int64_t* pad_off,
+                         int64_t n_sets, uint8_t* dst, float* scale, cudaStream_t st);
 
 // Build the uniform rerank-pool offsets b * depth.
 void launch_iota_offsets(int64_t* off, int32_t n, int64_t step, cudaStream_t st);

@@ -18,11 +18,14 @@
 //                      double-buffered TMEM accumulator (2 x MT x N columns)
 //
 // Epilogue: every thread walks its row's N accumulator columns in order.  The
-// column -> set map is the same for all rows, so a set boundary is a uniform
-// branch: the thread keeps a running max, and when a set ends the rows of each
-// query slot are summed by a g-lane xor butterfly (g = slot size) and one lane
-// writes the score.  A set never spans two chunks, so no partial maximum ever
-// leaves registers and no similarity matrix is written anywhere.
+// low-precision store copies pad each set to a multiple of 8 rows with copies of
+// the set's own last vector (a repeated vector cannot change a maximum), so sets
+// end only at 8-column subgroup boundaries.  Per subgroup the thread folds 8
+// columns into a running max with three-input max instructions; when a set ends
+// (a warp-uniform bit) the rows of each query slot are summed by a g-lane xor
+// butterfly (g = slot size) and one lane writes the score.  A set never spans two
+// chunks, so no partial maximum leaves registers and no similarity matrix is
+// written anywhere.
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -69,25 +72,6 @@ struct TcArgs {
   float* scores;             // [n_queries * n_sets]
   int* status;
 };
-
-__device__ __forceinline__ float max32(const float (&v)[32], float run) {
-  float a = fmax3(v[0], v[1], v[2]);
-  float b = fmax3(v[3], v[4], v[5]);
-  float c = fmax3(v[6], v[7], v[8]);
-  float d = fmax3(v[9], v[10], v[11]);
-  float e = fmax3(v[12], v[13], v[14]);
-  float f = fmax3(v[15], v[16], v[17]);
-  float g = fmax3(v[18], v[19], v[20]);
-  float h = fmax3(v[21], v[22], v[23]);
-  float i = fmax3(v[24], v[25], v[26]);
-  float j = fmax3(v[27], v[28], v[29]);
-  float k = fmax3(v[30], v[31], run);
-  a = fmax3(a, b, c);
-  d = fmax3(d, e, f);
-  g = fmax3(g, h, i);
-  j = fmax3(j, k, a);
-  return fmax3(d, g, j);
-}
 
 template <int MT, bool FP8>
 __global__ void __launch_bounds__(TcCfg<MT, FP8>::THREADS, 1)
@@ -155,12 +139,11 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
                         qb * C::M_RES + m * 128);
         const int64_t r0 = a.doc_off[a.chunk_doc[chunk]];
         const int64_t r1 = a.doc_off[a.chunk_doc[chunk + 1]];
-        const int64_t tile0 = FP8 ? (r0 & ~int64_t(3)) : r0;
-        const int ntiles = (int)((r1 - tile0 + C::N - 1) / C::N);
+        const int ntiles = (int)((r1 - r0 + C::N - 1) / C::N);
         for (int t = 0; t < ntiles; ++t) {
           if (!mbar_wait(&empty[stage], phase ^ 1, a.status, abort_flag)) { ok = false; break; }
           uint8_t* dst = d_smem + stage * C::STAGE_BYTES;
-          const int row = (int)(tile0 + (int64_t)t * C::N);
+          const int row = (int)(r0 + (int64_t)t * C::N);
           mbar_arrive_expect_tx(&full[stage], C::STAGE_TILE_BYTES + C::STAGE_SCALE_BYTES);
           for (int h = 0; h < C::HALVES; ++h)
             tma_load_2d(dst + h * (C::N * 128), &tm_d, &full[stage], h * 64, row);
@@ -190,8 +173,7 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
         const int chunk = (int)(u / nqb);
         const int64_t r0 = a.doc_off[a.chunk_doc[chunk]];
         const int64_t r1 = a.doc_off[a.chunk_doc[chunk + 1]];
-        const int64_t tile0 = FP8 ? (r0 & ~int64_t(3)) : r0;
-        const int ntiles = (int)((r1 - tile0 + C::N - 1) / C::N);
+        const int ntiles = (int)((r1 - r0 + C::N - 1) / C::N);
         if (!mbar_wait(q_full, it & 1, a.status, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const uint32_t q_base = smem_u32(q_smem);
@@ -254,24 +236,9 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
       const int d1 = a.chunk_doc[chunk + 1];
       const int64_t r0 = a.doc_off[d0];
       const int64_t r1 = a.doc_off[d1];
-      const int64_t tile0 = FP8 ? (r0 & ~int64_t(3)) : r0;
-      const int ntiles = (int)((r1 - tile0 + C::N - 1) / C::N);
+      const int ntiles = (int)((r1 - r0 + C::N - 1) / C::N);
       int cur = d0;
-      int64_t next_start = a.doc_off[d0 + 1];
       float run = -INFINITY;
-
-      auto commit = [&](int doc, float v) {
-        float s = v * row_scale;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          float t = __shfl_xor_sync(0xffffffffu, s, o);
-          if (o < g) s += t;
-        }
-        if (writer) {
-          float* d = dst + doc;
-          *d = add ? (*d + s) : s;
-        }
-      };
 
       for (int t = 0; t < ntiles; ++t) {
         // every lane waits, then the warp agrees, so the .sync.aligned TMEM
@@ -281,40 +248,56 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
           break;
         }
         tc_fence_after();
-        const int64_t base_col = tile0 + (int64_t)t * C::N;
+        // Sets are padded to multiples of kRowAlign rows, so a set ends only at
+        // the end of an 8-column subgroup.  Lane l checks whether set cur + l
+        // ends inside this tile; the warp ORs the answers into one bit per
+        // subgroup.  At most N / 8 <= 32 sets end inside a tile.
+        const int64_t ts = r0 + (int64_t)t * C::N;
+        const int64_t te = min(ts + (int64_t)C::N, r1);
+        uint32_t bit = 0;
+        if (cur + lane < d1) {
+          const int64_t e = a.doc_off[cur + lane + 1];
+          if (e <= te) bit = 1u << (int)((e - ts) / kRowAlign - 1);
+        }
+        const uint32_t ends = __reduce_or_sync(0xffffffffu, bit);
+        const int n_sub = (int)((te - ts) / kRowAlign);
 #pragma unroll
-        for (int grp = 0; grp < C::N / 32; ++grp) {
-          float v[32];
-          tmem_ld32(tmem + t_lane + acc * C::ACC_COLS + m_tile * C::N + grp * 32, v);
-          if (grp == C::N / 32 - 1) {
+        for (int h = 0; h < C::N / 64; ++h) {
+          float v[64];
+          tmem_ld64(tmem + t_lane + acc * C::ACC_COLS + m_tile * C::N + h * 64, v);
+          if (h == C::N / 64 - 1) {
+            // the accumulator is in registers: hand the buffer back to the MMA warp
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[acc]);
           }
-          const int64_t g0 = base_col + grp * 32;
-          if (cur >= d1) continue;
-          if (g0 < r0 - 31) continue;
-          if (g0 >= r0 && next_start >= g0 + 32) {
-            run = max32(v, run);
-          } else {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int64_t col = g0 + j;
-              if (col < r0 || cur >= d1) continue;
-              if (col == next_start) {
-                commit(cur, run);
-                run = -INFINITY;
+          for (int s = 0; s < 8; ++s) {
+            const int sg = h * 8 + s;
+            if (sg < n_sub) {
+              const float* x = v + 8 * s;
+              run = fmax3(run, fmax3(x[0], x[1], x[2]), fmax3(x[3], x[4], x[5]));
+              run = fmax3(run, x[6], x[7]);
+              if ((ends >> sg) & 1u) {
+                // set `cur` is complete: sum its row maxima over each query slot
+                float sum = run * row_scale;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                  const float other = __shfl_xor_sync(0xffffffffu, sum, o);
+                  if (o < g) sum += other;
+                }
+                if (writer) {
+                  float* d = dst + cur;
+                  *d = add ? (*d + sum) : sum;
+                }
                 ++cur;
-                if (cur >= d1) continue;
-                next_start = a.doc_off[cur + 1];
+                run = -INFINITY;
               }
-              run = fmaxf(run, v[j]);
             }
           }
         }
         if (++acc == 2) { acc = 0; acc_phase ^= 1; }
       }
-      if (ok && cur < d1) commit(cur, run);
     }
   }
 
@@ -344,7 +327,7 @@ gem_status launch_tc(const gem_store* s, gem_workspace* ws, const CUtensorMap& t
   a.part_pass = ws->d_part_pass;
   a.part_slot = ws->d_part_slot;
   a.q_scale = ws->d_qpack_scale;
-  a.doc_off = s->d_offsets;
+  a.doc_off = s->d_pad_offsets;
   a.chunk_doc = cm->d_chunk_doc;
   a.n_chunks = cm->n_chunks;
   a.n_sets = s->n_sets;

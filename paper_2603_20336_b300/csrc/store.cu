@@ -11,41 +11,55 @@
 namespace gem {
 namespace {
 
-__global__ void quantize_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
-                                     int64_t n4) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float4 v = reinterpret_cast<const float4*>(src)[i];
-    __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
-    __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
-    uint2 w;
-    w.x = *reinterpret_cast<uint32_t*>(&lo);
-    w.y = *reinterpret_cast<uint32_t*>(&hi);
-    reinterpret_cast<uint2*>(dst)[i] = w;
+// One warp per set: every padded row r of set d takes source row
+// off[d] + min(r, len - 1), so pad rows repeat the set's last vector.
+__global__ void quantize_bf16_kernel(const float* __restrict__ src, const int64_t* __restrict__ off,
+                                     const int64_t* __restrict__ pad_off, int64_t n_sets,
+                                     __nv_bfloat16* __restrict__ dst) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t d = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; d < n_sets;
+       d += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t s0 = off[d], len = off[d + 1] - s0;
+    const int64_t p0 = pad_off[d], plen = pad_off[d + 1] - p0;
+    for (int64_t r = 0; r < plen; ++r) {
+      const float4 v = reinterpret_cast<const float4*>(src + (s0 + min(r, len - 1)) * kDim)[lane];
+      __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
+      __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
+      uint2 w;
+      w.x = *reinterpret_cast<uint32_t*>(&lo);
+      w.y = *reinterpret_cast<uint32_t*>(&hi);
+      reinterpret_cast<uint2*>(dst + (p0 + r) * kDim)[lane] = w;
+    }
   }
 }
 
-// One warp per vector: s = max_k |x_k| / 448 (IEEE division), codes = E4M3(x_k / s)
-// round to nearest even, saturating; a zero vector gets s = 1.
-__global__ void quantize_fp8_kernel(const float* __restrict__ src, uint8_t* __restrict__ dst,
-                                    float* __restrict__ scale, int64_t rows) {
+// One warp per set, padded as above.  Per vector: s = max_k |x_k| / 448 (IEEE
+// division), codes = E4M3(x_k / s) round to nearest even, saturating; a zero
+// vector gets s = 1.
+__global__ void quantize_fp8_kernel(const float* __restrict__ src, const int64_t* __restrict__ off,
+                                    const int64_t* __restrict__ pad_off, int64_t n_sets,
+                                    uint8_t* __restrict__ dst, float* __restrict__ scale) {
   const int lane = threadIdx.x & 31;
-  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < rows;
-       r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    float4 v = reinterpret_cast<const float4*>(src + r * kDim)[lane];
-    float a = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+  for (int64_t d = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; d < n_sets;
+       d += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t s0 = off[d], len = off[d + 1] - s0;
+    const int64_t p0 = pad_off[d], plen = pad_off[d + 1] - p0;
+    for (int64_t r = 0; r < plen; ++r) {
+      const float4 v = reinterpret_cast<const float4*>(src + (s0 + min(r, len - 1)) * kDim)[lane];
+      float a = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
-    const float s = (a == 0.f) ? 1.f : __fdiv_rn(a, 448.f);
-    const float xs[4] = {v.x, v.y, v.z, v.w};
-    uint32_t packed = 0;
+      for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+      const float sc = (a == 0.f) ? 1.f : __fdiv_rn(a, 448.f);
+      const float xs[4] = {v.x, v.y, v.z, v.w};
+      uint32_t packed = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(__fdiv_rn(xs[j], s), __NV_SATFINITE, __NV_E4M3);
-      packed |= (uint32_t)c << (8 * j);
+      for (int j = 0; j < 4; ++j) {
+        __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(__fdiv_rn(xs[j], sc), __NV_SATFINITE, __NV_E4M3);
+        packed |= (uint32_t)c << (8 * j);
+      }
+      reinterpret_cast<uint32_t*>(dst + (p0 + r) * kDim)[lane] = packed;
+      if (lane == 0) scale[p0 + r] = sc;
     }
-    reinterpret_cast<uint32_t*>(dst + r * kDim)[lane] = packed;
-    if (lane == 0) scale[r] = s;
   }
 }
 
@@ -102,15 +116,19 @@ bool encode_tmap_1d_f32(CUtensorMap* map, void* base, uint64_t n, uint32_t box) 
             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-void launch_quantize_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStream_t st) {
-  const int64_t n4 = n / 4;
-  const int grid = (int)std::min<int64_t>((n4 + 255) / 256, 148 * 16);
-  if (grid > 0) { quantize_bf16_kernel<<<grid, 256, 0, st>>>(src, dst, n4); note_launches(1); }
+void launch_quantize_bf16(const float* src, const int64_t* off, const int64_t* pad_off,
+                          int64_t n_sets, __nv_bfloat16* dst, cudaStream_t st) {
+  const int grid = (int)std::min<int64_t>((n_sets * 32 + 255) / 256, 148 * 16);
+  if (grid > 0) { quantize_bf16_kernel<<<grid, 256, 0, st>>>(src, off, pad_off, n_sets, dst); note_launches(1); }
 }
 
-void launch_quantize_fp8(const float* src, uint8_t* dst, float* scale, int64_t rows, cudaStream_t st) {
-  const int grid = (int)std::min<int64_t>((rows * 32 + 255) / 256, 148 * 16);
-  if (grid > 0) { quantize_fp8_kernel<<<grid, 256, 0, st>>>(src, dst, scale, rows); note_launches(1); }
+void launch_quantize_fp8(const float* src, const int64_t* off, const int64_t* pad_off,
+                         int64_t n_sets, uint8_t* dst, float* scale, cudaStream_t st) {
+  const int grid = (int)std::min<int64_t>((n_sets * 32 + 255) / 256, 148 * 16);
+  if (grid > 0) {
+    quantize_fp8_kernel<<<grid, 256, 0, st>>>(src, off, pad_off, n_sets, dst, scale);
+    note_launches(1);
+  }
 }
 
 void launch_iota_offsets(int64_t* off, int32_t n, int64_t step, cudaStream_t st) {
@@ -125,7 +143,7 @@ gem_status store_chunk_map(const gem_store* s, int chunk_rows, const ChunkMap** 
   std::vector<int> starts;
   starts.reserve(s->n_sets / 64 + 2);
   int64_t d = 0;
-  const auto& off = s->h_offsets;
+  const auto& off = s->h_pad_offsets;
   while (d < s->n_sets) {
     starts.push_back((int)d);
     const int64_t limit = off[d] + chunk_rows;
@@ -156,7 +174,7 @@ gem_status store_tmap_bf16(const gem_store* s, int box_rows, const CUtensorMap**
   auto it = s->tmap_bf16.find(box_rows);
   if (it == s->tmap_bf16.end()) {
     CUtensorMap m;
-    if (!encode_tmap_2d(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, s->d_bf16, kDim, s->n_vecs, kDim * 2, 64,
+    if (!encode_tmap_2d(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, s->d_bf16, kDim, s->n_pad_vecs, kDim * 2, 64,
                         box_rows, CU_TENSOR_MAP_SWIZZLE_128B))
       return fail(GEM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the bf16 store");
     it = s->tmap_bf16.emplace(box_rows, m).first;
@@ -171,7 +189,7 @@ gem_status store_tmap_fp8(const gem_store* s, int box_rows, const CUtensorMap** 
   auto it = s->tmap_fp8.find(box_rows);
   if (it == s->tmap_fp8.end()) {
     CUtensorMap m;
-    if (!encode_tmap_2d(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, s->d_fp8, kDim, s->n_vecs, kDim, 128,
+    if (!encode_tmap_2d(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, s->d_fp8, kDim, s->n_pad_vecs, kDim, 128,
                         box_rows, CU_TENSOR_MAP_SWIZZLE_128B))
       return fail(GEM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fp8 store");
     it = s->tmap_fp8.emplace(box_rows, m).first;

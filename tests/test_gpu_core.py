@@ -38,13 +38,28 @@ def cfg1(gem):
     return dict(w=w, store=store, ws=ws, q=q, qo=qo, S64=S64, L1=L1)
 
 
+def _padded_source_rows(off):
+    """Source row of every padded row: each set rounded up to a multiple of 8
+    rows, the extra rows repeating the set's last vector."""
+    lens = np.diff(off)
+    plens = (lens + 7) // 8 * 8
+    src = []
+    for d in range(len(lens)):
+        r = np.arange(plens[d])
+        src.append(off[d] + np.minimum(r, lens[d] - 1))
+    return np.concatenate([[0], np.cumsum(plens)]), np.concatenate(src)
+
+
 def test_store_copies_match_oracle_rounding(gem, cfg1):
     w, store = cfg1["w"], cfg1["store"]
     X = w.docs.vecs.numpy()
+    pad_off, src = _padded_source_rows(w.docs.offsets)
+    np.testing.assert_array_equal(store.export("pad_offsets").cpu().numpy(), pad_off)
+    assert store.n_pad_vecs == pad_off[-1]
     bits = store.export("bf16").cpu().numpy().view(np.uint16)
-    want = oracle.bf16_round(X).view(np.uint32) >> 16
+    want = oracle.bf16_round(X[src]).view(np.uint32) >> 16
     np.testing.assert_array_equal(bits.astype(np.uint32), want.astype(np.uint32))
-    codes, scale = oracle.fp8_e4m3_quantize(X)
+    codes, scale = oracle.fp8_e4m3_quantize(X[src])
     got_scale = store.export("fp8_scale").cpu().numpy()
     np.testing.assert_array_equal(got_scale, scale)
     got_codes = store.export("fp8").cpu().view(torch.float8_e4m3fn).float().numpy()
