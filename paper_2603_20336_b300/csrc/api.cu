@@ -352,7 +352,13 @@ static gem_status score_all_impl(const gem_store* s, gem_workspace* w, const flo
     if (r != GEM_OK) return r;
     return launch_tc_score_all(s, w, compute, mt, w->tc_chunk_rows, scores, st);
   }
-  if (compute == GEM_FP8_E4M3) return fail(GEM_ERR_UNSUPPORTED, "fp8 scoring is not available");
+  if (compute == GEM_FP8_E4M3) {
+    if (!s->d_fp8) return fail(GEM_ERR_STATE, "store keeps no fp8 copy");
+    const int mt = w->tc_m_tiles;
+    gem_status r = launch_plan(w, q, q_offsets, n_queries, n_q_rows, 128 * mt, compute, st);
+    if (r != GEM_OK) return r;
+    return launch_tc_score_all(s, w, compute, mt, w->tc_chunk_rows, scores, st);
+  }
   return fail(GEM_ERR_INVALID, "unknown compute dtype");
 }
 

@@ -68,6 +68,7 @@ struct gem_store {
   // tensor maps of the doc copies, keyed by tile rows (box height)
   mutable std::map<int, CUtensorMap> tmap_bf16;
   mutable std::map<int, CUtensorMap> tmap_fp8;
+  mutable std::map<int, CUtensorMap> tmap_fp8_scale;
   mutable std::map<int, gem::ChunkMap> chunks;
 };
 
@@ -140,6 +141,7 @@ bool encode_tmap_1d_f32(CUtensorMap* map, void* base, uint64_t n, uint32_t box);
 gem_status store_chunk_map(const gem_store* s, int chunk_rows, const ChunkMap** out);
 gem_status store_tmap_bf16(const gem_store* s, int box_rows, const CUtensorMap** out);
 gem_status store_tmap_fp8(const gem_store* s, int box_rows, const CUtensorMap** out);
+gem_status store_tmap_fp8_scale(const gem_store* s, int box_rows, const CUtensorMap** out);
 
 // ---------------------------------------------------------------- launchers
 // Query plan: split sets into <= 32-row parts, pack them into m_res-row blocks

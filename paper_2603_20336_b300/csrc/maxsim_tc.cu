@@ -42,17 +42,18 @@ struct TcCfg {
   static constexpr int HALVES = FP8 ? 1 : 2;      // 128-byte swizzle atoms per row
   static constexpr int K_STEP = FP8 ? 32 : 16;    // K per MMA instruction
   static constexpr int K_STEPS = kDim / K_STEP;   // MMAs per tile and M tile
-  static constexpr int Q_TILE_BYTES = 128 * ROW_BYTES;
   static constexpr int Q_BYTES = M_RES * ROW_BYTES;
-  static constexpr int STAGE_TILE_BYTES = N * ROW_BYTES;
-  static constexpr int STAGE_SCALE_BYTES = FP8 ? N * 4 : 0;
-  static constexpr int STAGE_BYTES = STAGE_TILE_BYTES + (FP8 ? 1024 : 0);
-  static constexpr int STAGES = (MT == 1) ? (FP8 ? 4 : 3) : (MT == 2 ? (FP8 ? 6 : 4) : (FP8 ? 8 : 6));
+  static constexpr int STAGE_BYTES = N * ROW_BYTES;
+  static constexpr int STAGES = (MT == 1) ? (FP8 ? 6 : 3) : (MT == 2 ? (FP8 ? 8 : 4) : (FP8 ? 12 : 6));
+  // fp8: per-column dequantisation scales of each tile, in a ring of their own
+  // (the operand stage is recycled as soon as the MMA has read it)
+  static constexpr int SC_SLOTS = FP8 ? 8 : 0;
+  static constexpr int SC_BYTES = SC_SLOTS * N * 4;
   static constexpr int EPI_WARPS = 4 * MT;
   static constexpr int THREADS = (EPI_WARPS + 2) * 32;
   static constexpr int ACC_COLS = MT * N;         // 256 per accumulator buffer
   static constexpr int TMEM_COLS = 2 * ACC_COLS;  // 512
-  static constexpr int SMEM_BYTES = 1024 /*align slack*/ + Q_BYTES + STAGES * STAGE_BYTES + 256;
+  static constexpr int SMEM_BYTES = 1024 /*align slack*/ + Q_BYTES + STAGES * STAGE_BYTES + SC_BYTES + 512;
   static constexpr uint32_t IDESC = make_idesc(128, N, FP8 ? 0u : 1u, FP8 ? 0u : 1u);
 };
 
@@ -82,7 +83,8 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* q_smem = smem;
   uint8_t* d_smem = smem + C::Q_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(d_smem + C::STAGES * C::STAGE_BYTES);
+  float* sc_smem = reinterpret_cast<float*>(d_smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(d_smem + C::STAGES * C::STAGE_BYTES + C::SC_BYTES);
   uint64_t* full = bars;
   uint64_t* empty = bars + C::STAGES;
   uint64_t* acc_full = bars + 2 * C::STAGES;
@@ -90,7 +92,9 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
   uint64_t* q_full = acc_empty + 2;
   uint64_t* q_empty = q_full + 1;
   uint64_t* done_bar = q_empty + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done_bar + 1);
+  uint64_t* sc_full = done_bar + 1;
+  uint64_t* sc_empty = sc_full + C::SC_SLOTS;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sc_empty + C::SC_SLOTS);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5;
@@ -106,6 +110,7 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
     mbar_init(q_full, 1);
     mbar_init(q_empty, 1);
     mbar_init(done_bar, 1);
+    for (int s = 0; s < C::SC_SLOTS; ++s) { mbar_init(&sc_full[s], 1); mbar_init(&sc_empty[s], C::EPI_WARPS); }
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -124,6 +129,9 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
       uint32_t phase = 0;
       uint32_t issued[C::STAGES];
       for (int s = 0; s < C::STAGES; ++s) issued[s] = 0;
+      int sslot = 0;
+      uint32_t sphase = 0;
+      uint32_t sc_issued[C::SC_SLOTS > 0 ? C::SC_SLOTS : 1] = {};
       int it = 0;
       uint32_t q_issued = 0;
       bool ok = true;
@@ -144,18 +152,27 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
           if (!mbar_wait(&empty[stage], phase ^ 1, a.status, abort_flag)) { ok = false; break; }
           uint8_t* dst = d_smem + stage * C::STAGE_BYTES;
           const int row = (int)(r0 + (int64_t)t * C::N);
-          mbar_arrive_expect_tx(&full[stage], C::STAGE_TILE_BYTES + C::STAGE_SCALE_BYTES);
+          mbar_arrive_expect_tx(&full[stage], C::STAGE_BYTES);
           for (int h = 0; h < C::HALVES; ++h)
             tma_load_2d(dst + h * (C::N * 128), &tm_d, &full[stage], h * 64, row);
-          if constexpr (FP8) tma_load_1d(dst + C::STAGE_TILE_BYTES, &tm_scale, &full[stage], row);
           issued[stage]++;
           if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+          if constexpr (FP8) {
+            // the tile's column scales (row is a multiple of 8: 16-byte aligned)
+            if (!mbar_wait(&sc_empty[sslot], sphase ^ 1, a.status, abort_flag)) { ok = false; break; }
+            mbar_arrive_expect_tx(&sc_full[sslot], C::N * 4);
+            tma_load_1d(sc_smem + sslot * C::N, &tm_scale, &sc_full[sslot], row);
+            sc_issued[sslot]++;
+            if (++sslot == C::SC_SLOTS) { sslot = 0; sphase ^= 1; }
+          }
         }
       }
       if (!ok) {
         // drain: every load this thread issued must land before the CTA exits
         for (int s = 0; s < C::STAGES; ++s)
           if (issued[s]) { int z = 0; mbar_wait(&full[s], (issued[s] - 1) & 1, nullptr, &z); }
+        for (int s = 0; s < C::SC_SLOTS; ++s)
+          if (sc_issued[s]) { int z = 0; mbar_wait(&sc_full[s], (sc_issued[s] - 1) & 1, nullptr, &z); }
         int z = 0;
         if (q_issued) mbar_wait(q_full, (q_issued - 1) & 1, nullptr, &z);
       }
@@ -215,6 +232,8 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
     const uint32_t t_lane = (uint32_t)(quad * 32) << 16;
     int acc = 0;
     uint32_t acc_phase = 0;
+    int sslot = 0;
+    uint32_t sphase = 0;
     bool ok = true;
     for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
       const int chunk = (int)(u / nqb);
@@ -239,62 +258,101 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
       const int ntiles = (int)((r1 - r0 + C::N - 1) / C::N);
       int cur = d0;
       float run = -INFINITY;
+      // ends of the 32 sets win .. win + 31, one per lane; refreshed when a
+      // tile could reach past the window
+      int win = d0;
+      int64_t e_win = (win + lane < d1) ? a.doc_off[win + lane + 1] : INT64_MAX;
+      constexpr int CH = C::N < 128 ? C::N : 128;  // columns per TMEM load
+
+      // fold the 8-column subgroups of one loaded chunk into the running max;
+      // a set that ends is summed over each query slot and written
+      // (fp8: each column is first multiplied by its vector's scale s_j, read
+      // as a broadcast from the tile's scale slot)
+      auto fold = [&](const float (&v)[CH], int sg0, uint32_t ends, int n_sub, const float* sc) {
+#pragma unroll
+        for (int s = 0; s < CH / 8; ++s) {
+          const int sg = sg0 + s;
+          if (sg < n_sub) {
+            float x[8];
+            if constexpr (FP8) {
+              const float4 s0 = reinterpret_cast<const float4*>(sc)[2 * s];
+              const float4 s1 = reinterpret_cast<const float4*>(sc)[2 * s + 1];
+              const float2 p0 = fmul2(make_float2(v[8 * s + 0], v[8 * s + 1]), make_float2(s0.x, s0.y));
+              const float2 p1 = fmul2(make_float2(v[8 * s + 2], v[8 * s + 3]), make_float2(s0.z, s0.w));
+              const float2 p2 = fmul2(make_float2(v[8 * s + 4], v[8 * s + 5]), make_float2(s1.x, s1.y));
+              const float2 p3 = fmul2(make_float2(v[8 * s + 6], v[8 * s + 7]), make_float2(s1.z, s1.w));
+              x[0] = p0.x; x[1] = p0.y; x[2] = p1.x; x[3] = p1.y;
+              x[4] = p2.x; x[5] = p2.y; x[6] = p3.x; x[7] = p3.y;
+            } else {
+#pragma unroll
+              for (int j = 0; j < 8; ++j) x[j] = v[8 * s + j];
+            }
+            run = fmax3(run, fmax3(x[0], x[1], x[2]), fmax3(x[3], x[4], x[5]));
+            run = fmax3(run, x[6], x[7]);
+            if ((ends >> sg) & 1u) {
+              float sum = run * row_scale;
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) {
+                const float other = __shfl_xor_sync(0xffffffffu, sum, o);
+                if (o < g) sum += other;
+              }
+              if (writer) {
+                float* d = dst + cur;
+                *d = add ? (*d + sum) : sum;
+              }
+              ++cur;
+              run = -INFINITY;
+            }
+          }
+        }
+      };
 
       for (int t = 0; t < ntiles; ++t) {
         // every lane waits, then the warp agrees, so the .sync.aligned TMEM
         // loads below always run with the whole warp
-        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[acc], acc_phase, a.status, abort_flag))) {
+        bool got = mbar_wait(&acc_full[acc], acc_phase, a.status, abort_flag);
+        if constexpr (FP8) got = got && mbar_wait(&sc_full[sslot], sphase, a.status, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) {
           ok = false;
           break;
         }
         tc_fence_after();
+        const float* sc = FP8 ? sc_smem + sslot * C::N : nullptr;
+        const uint32_t tcol = tmem + t_lane + acc * C::ACC_COLS + m_tile * C::N;
+        float v[CH];
+        tmem_ld_cols<CH>(tcol, v);
+        if constexpr (C::N == CH) {
+          // the accumulator is in registers: hand the buffer back to the MMA warp
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[acc]);
+        }
         // Sets are padded to multiples of kRowAlign rows, so a set ends only at
-        // the end of an 8-column subgroup.  Lane l checks whether set cur + l
+        // the end of an 8-column subgroup.  Lane l checks whether set win + l
         // ends inside this tile; the warp ORs the answers into one bit per
         // subgroup.  At most N / 8 <= 32 sets end inside a tile.
         const int64_t ts = r0 + (int64_t)t * C::N;
         const int64_t te = min(ts + (int64_t)C::N, r1);
-        uint32_t bit = 0;
-        if (cur + lane < d1) {
-          const int64_t e = a.doc_off[cur + lane + 1];
-          if (e <= te) bit = 1u << (int)((e - ts) / kRowAlign - 1);
+        if (cur + C::N / kRowAlign > win + 32) {
+          win = cur;
+          e_win = (win + lane < d1) ? a.doc_off[win + lane + 1] : INT64_MAX;
         }
+        uint32_t bit = 0;
+        if (win + lane >= cur && e_win <= te) bit = 1u << (int)((e_win - ts) / kRowAlign - 1);
         const uint32_t ends = __reduce_or_sync(0xffffffffu, bit);
         const int n_sub = (int)((te - ts) / kRowAlign);
-#pragma unroll
-        for (int h = 0; h < C::N / 64; ++h) {
-          float v[64];
-          tmem_ld64(tmem + t_lane + acc * C::ACC_COLS + m_tile * C::N + h * 64, v);
-          if (h == C::N / 64 - 1) {
-            // the accumulator is in registers: hand the buffer back to the MMA warp
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[acc]);
-          }
-#pragma unroll
-          for (int s = 0; s < 8; ++s) {
-            const int sg = h * 8 + s;
-            if (sg < n_sub) {
-              const float* x = v + 8 * s;
-              run = fmax3(run, fmax3(x[0], x[1], x[2]), fmax3(x[3], x[4], x[5]));
-              run = fmax3(run, x[6], x[7]);
-              if ((ends >> sg) & 1u) {
-                // set `cur` is complete: sum its row maxima over each query slot
-                float sum = run * row_scale;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                  const float other = __shfl_xor_sync(0xffffffffu, sum, o);
-                  if (o < g) sum += other;
-                }
-                if (writer) {
-                  float* d = dst + cur;
-                  *d = add ? (*d + sum) : sum;
-                }
-                ++cur;
-                run = -INFINITY;
-              }
-            }
-          }
+        fold(v, 0, ends, n_sub, sc);
+        if constexpr (C::N > CH) {
+          tmem_ld_cols<CH>(tcol + CH, v);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[acc]);
+          fold(v, CH / 8, ends, n_sub, FP8 ? sc + CH : nullptr);
+        }
+        if constexpr (FP8) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sc_empty[sslot]);
+          if (++sslot == C::SC_SLOTS) { sslot = 0; sphase ^= 1; }
         }
         if (++acc == 2) { acc = 0; acc_phase ^= 1; }
       }
@@ -360,7 +418,20 @@ gem_status launch_tc_score_all(const gem_store* s, gem_workspace* ws, int comput
       default: return fail(GEM_ERR_INVALID, "m_tiles must be 1, 2 or 4");
     }
   }
-  return fail(GEM_ERR_UNSUPPORTED, "tensor-core scoring supports bf16 here");
+  if (compute == GEM_FP8_E4M3) {
+    const int n = 256 / m_tiles;
+    const CUtensorMap* td = nullptr;
+    const CUtensorMap* tsc = nullptr;
+    if ((r = store_tmap_fp8(s, n, &td)) != GEM_OK) return r;
+    if ((r = store_tmap_fp8_scale(s, n, &tsc)) != GEM_OK) return r;
+    switch (m_tiles) {
+      case 1: return launch_tc<1, true>(s, ws, ws->tmap_q_fp8, *td, *tsc, cm, scores, st);
+      case 2: return launch_tc<2, true>(s, ws, ws->tmap_q_fp8, *td, *tsc, cm, scores, st);
+      case 4: return launch_tc<4, true>(s, ws, ws->tmap_q_fp8, *td, *tsc, cm, scores, st);
+      default: return fail(GEM_ERR_INVALID, "m_tiles must be 1, 2 or 4");
+    }
+  }
+  return fail(GEM_ERR_INVALID, "tensor-core scoring takes bf16 or fp8");
 }
 
 }  // namespace gem

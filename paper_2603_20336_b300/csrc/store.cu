@@ -198,4 +198,19 @@ gem_status store_tmap_fp8(const gem_store* s, int box_rows, const CUtensorMap** 
   return GEM_OK;
 }
 
+gem_status store_tmap_fp8_scale(const gem_store* s, int box_rows, const CUtensorMap** out) {
+  std::lock_guard<std::mutex> lk(g_store_mutex);
+  if (!s->d_fp8_scale) return fail(GEM_ERR_STATE, "store keeps no fp8 copy");
+  auto it = s->tmap_fp8_scale.find(box_rows);
+  if (it == s->tmap_fp8_scale.end()) {
+    CUtensorMap m;
+    // the scale allocation has 1024 spare entries past the last padded row
+    if (!encode_tmap_1d_f32(&m, s->d_fp8_scale, s->n_pad_vecs + 1024, box_rows))
+      return fail(GEM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fp8 scales");
+    it = s->tmap_fp8_scale.emplace(box_rows, m).first;
+  }
+  *out = &it->second;
+  return GEM_OK;
+}
+
 }  // namespace gem

@@ -87,6 +87,30 @@ def test_score_all_bf16_matches_oracle(gem, cfg1):
     assert err2.max() <= 2e-4 * 32, err2.max()
 
 
+def _fp8_dequantised(X):
+    codes, scale = oracle.fp8_e4m3_quantize(np.asarray(X, np.float32))
+    return codes * scale[:, None].astype(np.float64)
+
+
+@pytest.mark.parametrize("lens", [[32] * 10, [1, 5, 17, 32, 33, 64, 100, 7]])
+def test_score_all_fp8_matches_oracle_on_dequantised_inputs(gem, cfg1, lens):
+    """E4M3 path: per-vector scales on both sides; against the FP64 score of the
+    oracle's own E4M3 rounding of the same inputs only FP32 accumulation and the
+    two scale multiplies remain."""
+    w = cfg1["w"]
+    lens = np.array(lens)
+    qs = synth.vector_sets(lens, synth.centres(64, 1235), 777)
+    S = gem.score_all(cfg1["store"], cfg1["ws"], qs.vecs.cuda(), torch.from_numpy(qs.offsets).cuda(),
+                      "fp8").cpu().numpy()
+    assert cfg1["ws"].status() == 0
+    Sq = oracle.score_all(_fp8_dequantised(qs.vecs.numpy()), qs.offsets,
+                          _fp8_dequantised(w.docs.vecs.numpy()), w.docs.offsets)
+    err = np.abs(S - Sq)
+    assert np.all(err <= 2e-4 * lens[:, None]), err.max()
+    S64 = oracle.score_all(qs.vecs, qs.offsets, w.docs.vecs, w.docs.offsets)
+    print("fp8 max |err| vs fp64 of fp32 inputs: %.3e" % np.abs(S - S64).max())
+
+
 @pytest.mark.parametrize("lens", [
     [1, 2, 3, 5, 8, 13, 21, 32],          # every slot size, single pass
     [33, 64, 40, 7, 100, 128, 31, 65],    # multi-part queries (up to 4 passes)
@@ -178,7 +202,7 @@ def test_topk_explicit_ids_ragged_and_all_equal(gem, cfg1):
         assert np.all(gi[r, m:] == -1)
 
 
-@pytest.mark.parametrize("compute", ["bf16", "f32"])
+@pytest.mark.parametrize("compute", ["bf16", "fp8", "f32"])
 def test_search_pipeline_matches_exact_top10(gem, cfg1, compute):
     ids, sc = gem.search(cfg1["store"], cfg1["ws"], cfg1["q"], cfg1["qo"], compute, rerank_depth=200, k=10)
     assert cfg1["ws"].status() == 0
