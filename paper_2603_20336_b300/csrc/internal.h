@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/gem.h"
+#include "gem.h"
 
 namespace gem {
 
