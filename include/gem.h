@@ -55,7 +55,9 @@ typedef enum {
 typedef enum {
   GEM_F32 = 0,      /* FP32 SIMT, fixed summation order, Kahan sum over query vectors */
   GEM_BF16 = 1,     /* BF16 operands on tcgen05 tensor cores, FP32 accumulation */
-  GEM_FP8_E4M3 = 2  /* E4M3 operands with per-vector FP32 scales, FP32 accumulation */
+  GEM_FP8_E4M3 = 2, /* E4M3 operands with per-vector FP32 scales, FP32 accumulation */
+  GEM_CODES = 3     /* id lists only: the GEM_F32 arithmetic with every query and stored
+                       vector replaced by its centroid (the quantized estimate) */
 } gem_dtype;
 
 /* Which copies of the vectors a store keeps (bit mask). */
@@ -75,11 +77,14 @@ enum {
   GEM_EXPORT_FP8 = 1,         /* uint8  [n_pad_vecs * 128] E4M3 bit patterns */
   GEM_EXPORT_FP8_SCALE = 2,   /* float  [n_pad_vecs] per-vector scales */
   GEM_EXPORT_OFFSETS = 3,     /* int64  [n_sets + 1] */
-  GEM_EXPORT_PAD_OFFSETS = 4  /* int64  [n_sets + 1] offsets of the padded layout */
+  GEM_EXPORT_PAD_OFFSETS = 4, /* int64  [n_sets + 1] offsets of the padded layout */
+  GEM_EXPORT_CODES = 5,       /* int32  [n_vecs] NN code of every stored vector */
+  GEM_EXPORT_CODEBOOK = 6     /* float  [k1 * 128] centroids of C_quant */
 };
 
 typedef struct gem_store gem_store;
 typedef struct gem_workspace gem_workspace;
+typedef struct gem_batch gem_batch;
 
 /* Library version, major * 10000 + minor * 100 + patch. */
 int gem_version(void);
@@ -112,6 +117,38 @@ gem_status gem_store_info(const gem_store* store, int64_t* n_sets, int64_t* n_ve
  * dst_bytes bytes (must be at least the array's size). */
 gem_status gem_store_export(const gem_store* store, int32_t what, void* dst, size_t dst_bytes,
                             void* stream);
+
+/*
+ * Nearest-centroid codes NN(x) = argmax_c <x, C_c> (Sec. 4.1.1 and Sec. 4.2.2:
+ * each vector maps to its closest centroid of C_quant; with unit vectors and
+ * centroids, closest under d_X = 1 - <x, c> is largest inner product).  Dot
+ * products are FP32 fused multiply-add chains over k = 0..127; ties go to the
+ * lowest index.  x float32 [n * 128], centroids float32 [k1 * 128], codes int32
+ * [n]; best (may be NULL) receives the winning inner product.  Device pointers.
+ */
+gem_status gem_assign_codes(const float* x, int64_t n, const float* centroids, int32_t k1,
+                            int32_t* codes, float* best, void* stream);
+
+/*
+ * Stage-1 k-means of Sec. 4.1.1 (spherical Lloyd: assign with gem_assign_codes,
+ * then each centroid becomes the L2-normalised mean of its vectors; a centroid
+ * without vectors keeps its value).  Runs on `sample` vectors of the store's
+ * FP32 copy drawn with `seed` (all vectors if sample <= 0 or >= n_vecs),
+ * initialised with k1 distinct sampled vectors, for `iters` iterations.
+ * centroids_out float32 [k1 * 128] (device).  A build step: allocates its own
+ * scratch and synchronises `stream`.  The paper sizes k1 as
+ * 2^floor(log2(16 sqrt(#vectors))) (Sec. 5.1).
+ */
+gem_status gem_train_codebook(const gem_store* store, int32_t k1, int32_t iters, int64_t sample,
+                              uint64_t seed, float* centroids_out, void* stream);
+
+/*
+ * Attaches C_quant (float32 [k1 * 128], device, unit rows expected) to the
+ * store and assigns the code of every stored vector (needs GEM_KEEP_F32).  A
+ * build step: synchronises `stream`; not concurrent with other calls on the
+ * store.  Workspaces created afterwards can run gem_estimate_codes.
+ */
+gem_status gem_store_set_codebook(gem_store* store, const float* centroids, int32_t k1, void* stream);
 
 /*
  * Scratch for scoring calls against `store`.  Bounds fix the memory once:
@@ -167,6 +204,19 @@ gem_status gem_score_ids(const gem_store* store, gem_workspace* ws, const float*
                          int32_t compute, float* scores, void* stream);
 
 /*
+ * Quantized Chamfer estimate (Sec. 4.5.3, Eq. 16) in similarity form:
+ *   est = sum_i max_j <C_{NN(q_i)}, C_{NN(p_j)}> = m_q - qCH(Q, P)
+ * The query vectors are coded on the fly; stored vectors use the store's codes.
+ * cand_offsets == NULL: every stored set, est float32 [n_queries * n_sets]
+ * row-major; otherwise est is aligned with cand_ids as in gem_score_ids.  The
+ * store needs a codebook before the workspace is created.
+ */
+gem_status gem_estimate_codes(const gem_store* store, gem_workspace* ws, const float* q,
+                              const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
+                              const int64_t* cand_offsets, const int64_t* cand_ids, int64_t n_cands,
+                              float* est, void* stream);
+
+/*
  * Per-row top-k (the k-argmax of Eq. 2): sorted by score descending, ties by
  * lower id.  Rows are either dense (row_offsets == NULL: row r is
  * scores[r * cols .. r * cols + cols - 1]) or ragged (row_offsets int64
@@ -203,6 +253,69 @@ gem_status gem_search_host(const gem_store* store, gem_workspace* ws, const floa
                            const int64_t* q_offsets_host, int32_t n_queries, int32_t compute,
                            int32_t rerank_depth, int32_t k, int64_t* out_ids_host,
                            float* out_scores_host, void* stream);
+
+/*
+ * MaxSim forward over (query, set) pairs with the argmax side output, for
+ * training: S_t = sum_i max_j <q_i, p_j> (Eq. 1) for every pair t, and
+ * argmax[t * max_q_len + i] = j*(t, i), the set row attaining the max (lowest j
+ * on ties).  Vector sets are raw device arrays (not a store) so that gradients
+ * can flow to them: q float32 [n_q_rows * 128] CSR by q_offsets [n_queries + 1];
+ * docs float32 [n_doc_rows * 128] CSR by doc_offsets [n_docs + 1]; the pairs of
+ * query b are pair_ids[pair_offsets[b] .. pair_offsets[b+1]-1] (set ids).
+ * compute GEM_BF16 rounds every component to bfloat16 before the FP32
+ * accumulation; GEM_F32 uses the FP32 values.  scores float32 [n_pairs];
+ * argmax int32 [n_pairs * max_q_len].  ws (may be NULL) receives device-side
+ * errors (an id outside [0, n_docs) scores NaN).
+ */
+gem_status gem_maxsim_fwd(const float* q, const int64_t* q_offsets, int32_t n_queries, const float* docs,
+                          const int64_t* doc_offsets, int64_t n_docs, const int64_t* pair_offsets,
+                          const int64_t* pair_ids, int64_t n_pairs, int32_t max_q_len, int32_t compute,
+                          float* scores, int32_t* argmax, gem_workspace* ws, void* stream);
+
+/*
+ * Backward of gem_maxsim_fwd for upstream gradients grad_scores [n_pairs]:
+ *   grad_q[i of query b] = sum over b's pairs t (ascending) of g_t * p_{j*(t,i)}
+ *   grad_docs[row j of set d] = sum over pairs t of d of g_t * (sum of q_i with j*(t,i) = j)
+ * with the FP32 input values (the bf16 rounding of the forward is treated as the
+ * identity).  grad_q float32 [n_q_rows * 128] and grad_docs float32
+ * [n_doc_rows * 128] are overwritten (either may be NULL).  grad_q is
+ * deterministic; grad_docs is deterministic when no set occurs in two pairs.
+ */
+gem_status gem_maxsim_bwd(const float* q, const int64_t* q_offsets, int32_t n_queries, const float* docs,
+                          const int64_t* doc_offsets, int64_t n_docs, int64_t n_doc_rows,
+                          const int64_t* pair_offsets, const int64_t* pair_ids, int64_t n_pairs,
+                          const int32_t* argmax, int32_t max_q_len, const float* grad_scores, float* grad_q,
+                          float* grad_docs, void* stream);
+
+/*
+ * Batched candidate scoring: the scoring step of one beam-search expansion
+ * (Algorithm 5, the neighbours of each popped node scored against its query) for
+ * many queries with uneven set sizes and uneven candidate lists, as one
+ * persistent launch replayed from a CUDA graph.
+ *   mode         GEM_F32 (exact) or GEM_CODES (quantized); scores are
+ *                bit-identical to gem_score_ids with the same compute
+ *   max_*        capacity of the batch's own device buffers
+ *   seg          candidates per work item (1..1024; the autotuner's knob)
+ *   ctas_per_sm  persistent CTAs per SM (0 = as many as fit)
+ * GEM_CODES needs a store codebook.  The caller owns the device buffers the
+ * graph reads and writes; their addresses are fixed for the batch's lifetime and
+ * the caller refills them before each run: q float32 [max_q_rows * 128],
+ * q_offsets and cand_offsets int64 [max_queries + 1], cand_ids int64
+ * [max_cands] (same meaning as in gem_score_ids), scores float32 [max_cands]
+ * (output).  gem_batch_run scores n_queries queries with n_q_rows vectors and
+ * n_cands candidates on `stream`; it first waits until the previous run of the
+ * same batch has finished.  use_graph = 0 runs the same launches without the
+ * graph.  Inconsistent offsets are reported by gem_batch_status.
+ */
+gem_status gem_batch_create(const gem_store* store, int32_t mode, int32_t max_queries, int64_t max_q_rows,
+                            int32_t max_q_len, int64_t max_cands, int32_t seg, int32_t ctas_per_sm,
+                            float* q, int64_t* q_offsets, int64_t* cand_offsets, int64_t* cand_ids,
+                            float* scores, gem_batch** out);
+gem_status gem_batch_run(gem_batch* batch, int32_t n_queries, int64_t n_q_rows, int64_t n_cands,
+                         int32_t use_graph, void* stream);
+/* Synchronises the batch's last run and returns and clears its device status. */
+gem_status gem_batch_status(gem_batch* batch);
+void gem_batch_destroy(gem_batch* batch);
 
 /* Number of kernels this library has enqueued since it was loaded (all
  * devices and threads); lets a caller count the library's launches in a region. */

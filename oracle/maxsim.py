@@ -285,15 +285,19 @@ def fp8_e4m3_quantize(X):
 # Gradient of Eq. 1 and the contrastive loss used to exercise it
 # ---------------------------------------------------------------------------
 
-def maxsim_grad(Q, P):
+def maxsim_grad(Q, P, decide=None):
     """Gradients of CH(Q, P) = sum_i max_j <q_i, p_j> for a fixed argmax.
 
     j*(i) = argmax_j <q_i, p_j> (lowest j on ties); dCH/dq_i = p_{j*(i)} and
     dCH/dp_j = sum of q_i over the i with j*(i) = j.  Returns (dQ, dP, jstar).
+    decide = (Qd, Pd): take the argmax on these inputs instead (a forward that
+    rounds its inputs decides j* on the rounded values); the gradient values
+    still come from Q and P.
     """
     Q = _f64(Q)
     P = _f64(P)
-    sims = Q @ P.T
+    Qd, Pd = (Q, P) if decide is None else (_f64(decide[0]), _f64(decide[1]))
+    sims = Qd @ Pd.T
     jstar = np.argmax(sims, axis=1)
     dQ = P[jstar].copy()
     dP = np.zeros_like(P)

@@ -28,7 +28,7 @@ if not os.path.exists(_LIB_PATH):
 lib = ctypes.CDLL(_LIB_PATH)
 _abi.declare(lib)
 
-DTYPES = {"f32": 0, "bf16": 1, "fp8": 2}
+DTYPES = {"f32": 0, "bf16": 1, "fp8": 2, "codes": 3}
 KEEP = {"f32": 1, "bf16": 2, "fp8": 4}
 STATUS = {0: "GEM_OK", 1: "GEM_ERR_INVALID", 2: "GEM_ERR_OOM", 3: "GEM_ERR_CUDA", 4: "GEM_ERR_TIMEOUT",
           5: "GEM_ERR_UNSUPPORTED", 6: "GEM_ERR_STATE", 7: "GEM_ERR_BOUNDS"}
@@ -99,7 +99,9 @@ class Store:
         P = self.n_pad_vecs
         spec = {"bf16": (0, torch.int16, (P, 128)), "fp8": (1, torch.uint8, (P, 128)),
                 "fp8_scale": (2, torch.float32, (P,)), "offsets": (3, torch.int64, (self.n_sets + 1,)),
-                "pad_offsets": (4, torch.int64, (self.n_sets + 1,))}
+                "pad_offsets": (4, torch.int64, (self.n_sets + 1,)),
+                "codes": (5, torch.int32, (self.n_vecs,)),
+                "codebook": (6, torch.float32, (getattr(self, "k1", 0), 128))}
         code, dt, shape = spec[what]
         out = torch.empty(shape, dtype=dt, device="cuda")
         _check(lib.gem_store_export(self.handle, code, _ptr(out), out.numel() * out.element_size(),
@@ -222,3 +224,147 @@ def search_host(store: Store, ws: Workspace, q_host, q_offsets_host, compute="bf
 def set_schedule(ws: Workspace, m_tiles: int = 2, chunk_rows: int = 1 << 16):
     """Tensor-core kernel schedule of a workspace (results do not depend on it)."""
     _check(lib.gem_workspace_set_schedule(ws.handle, m_tiles, chunk_rows))
+
+
+def assign_codes(x, centroids, with_best: bool = False, stream=None):
+    """NN(x): index of the centroid with the largest inner product (ties: lowest)."""
+    x = _dev(x, torch.float32, "x")
+    c = _dev(centroids, torch.float32, "centroids")
+    codes = torch.empty(x.shape[0], dtype=torch.int32, device=x.device)
+    best = torch.empty(x.shape[0], dtype=torch.float32, device=x.device) if with_best else None
+    _check(lib.gem_assign_codes(_ptr(x), x.shape[0], _ptr(c), c.shape[0], _ptr(codes), _ptr(best),
+                                _stream(stream)))
+    return (codes, best) if with_best else codes
+
+
+def train_codebook(store: Store, k1: int, iters: int = 10, sample: int = 0, seed: int = 0, stream=None):
+    """Stage-1 spherical k-means on (a sample of) the store's vectors: float32 [k1, 128]."""
+    out = torch.empty((k1, 128), dtype=torch.float32, device="cuda")
+    _check(lib.gem_train_codebook(store.handle, k1, iters, sample, seed, _ptr(out), _stream(stream)))
+    return out
+
+
+def set_codebook(store: Store, centroids, stream=None):
+    """Attach C_quant to the store and code every stored vector."""
+    c = _dev(centroids, torch.float32, "centroids")
+    _check(lib.gem_store_set_codebook(store.handle, _ptr(c), c.shape[0], _stream(stream)))
+    store.k1 = c.shape[0]
+
+
+def estimate_codes(store: Store, ws: Workspace, q, q_offsets, cand_offsets=None, cand_ids=None, out=None,
+                   stream=None):
+    """qCH estimate (Eq. 16) in similarity form, all sets [B, n_sets] or per candidate id."""
+    q, qo, B, rows = _queries(q, q_offsets)
+    if cand_offsets is None:
+        co = ci = None
+        n = 0
+        shape = (B, store.n_sets)
+    else:
+        co = _dev(cand_offsets, torch.int64, "cand_offsets")
+        ci = _dev(cand_ids, torch.int64, "cand_ids")
+        n = ci.numel()
+        shape = (n,)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=q.device)
+    _check(lib.gem_estimate_codes(store.handle, ws.handle, _ptr(q), _ptr(qo), B, rows, _ptr(co), _ptr(ci), n,
+                                  _ptr(out), _stream(stream)))
+    return out
+
+
+class Batch:
+    """Batched candidate scoring of many queries in one persistent, graph-replayed
+    launch (the scoring step of a beam-search expansion, Algorithm 5).
+
+    The batch owns torch tensors at fixed addresses (q, q_offsets, cand_offsets,
+    cand_ids, scores); run() copies a round's inputs into them and launches.
+    """
+
+    def __init__(self, store: Store, mode="f32", max_queries=4096, max_q_rows=4096 * 64, max_q_len=64,
+                 max_cands=4096 * 512, seg=32, ctas_per_sm=0):
+        dev = torch.device("cuda")
+        self.store = store
+        self.mode = {"f32": 0, "codes": 3}[mode] if isinstance(mode, str) else int(mode)
+        self.q = torch.zeros((max_q_rows, 128), dtype=torch.float32, device=dev)
+        self.q_offsets = torch.zeros(max_queries + 1, dtype=torch.int64, device=dev)
+        self.cand_offsets = torch.zeros(max_queries + 1, dtype=torch.int64, device=dev)
+        self.cand_ids = torch.zeros(max(max_cands, 1), dtype=torch.int64, device=dev)
+        self.scores = torch.zeros(max(max_cands, 1), dtype=torch.float32, device=dev)
+        h = ctypes.c_void_p()
+        _check(lib.gem_batch_create(store.handle, self.mode, max_queries, max_q_rows, max_q_len, max_cands, seg,
+                                    ctas_per_sm, _ptr(self.q), _ptr(self.q_offsets), _ptr(self.cand_offsets),
+                                    _ptr(self.cand_ids), _ptr(self.scores), ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, q, q_offsets, cand_offsets, cand_ids, use_graph=True, stream=None):
+        """Score one round; returns a view of the scores (valid until the next run)."""
+        B = q_offsets.numel() - 1
+        R, n = q.shape[0], cand_ids.numel()
+        self.q[:R].copy_(q, non_blocking=True)
+        self.q_offsets[:B + 1].copy_(q_offsets, non_blocking=True)
+        self.cand_offsets[:B + 1].copy_(cand_offsets, non_blocking=True)
+        self.cand_ids[:n].copy_(cand_ids, non_blocking=True)
+        _check(lib.gem_batch_run(self.handle, B, R, n, 1 if use_graph else 0, _stream(stream)))
+        return self.scores[:n]
+
+    def status(self) -> int:
+        return lib.gem_batch_status(self.handle)
+
+    def close(self):
+        if self.handle:
+            lib.gem_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def maxsim_fwd(q, q_offsets, docs, doc_offsets, pair_offsets, pair_ids, compute="bf16", max_q_len=None,
+               ws=None, stream=None):
+    """Scores of (query, set) pairs and the argmax rows j*(t, i) (int32 [n_pairs, max_q_len])."""
+    q, qo, B, _ = _queries(q, q_offsets)
+    docs = _dev(docs, torch.float32, "docs")
+    do = _dev(doc_offsets, torch.int64, "doc_offsets")
+    po = _dev(pair_offsets, torch.int64, "pair_offsets")
+    pid = _dev(pair_ids, torch.int64, "pair_ids")
+    if max_q_len is None:
+        max_q_len = int((qo[1:] - qo[:-1]).max().item())
+    n = pid.numel()
+    scores = torch.empty(n, dtype=torch.float32, device=q.device)
+    argmax = torch.empty((n, max_q_len), dtype=torch.int32, device=q.device)
+    _check(lib.gem_maxsim_fwd(_ptr(q), _ptr(qo), B, _ptr(docs), _ptr(do), do.numel() - 1, _ptr(po), _ptr(pid), n,
+                              max_q_len, _dtype_code(compute), _ptr(scores), _ptr(argmax),
+                              ws.handle if ws is not None else None, _stream(stream)))
+    return scores, argmax
+
+
+def maxsim_bwd(q, q_offsets, docs, doc_offsets, pair_offsets, pair_ids, argmax, grad_scores, stream=None):
+    """(grad_q, grad_docs) of the pair scores for upstream gradients grad_scores."""
+    q, qo, B, _ = _queries(q, q_offsets)
+    g = _dev(grad_scores.contiguous(), torch.float32, "grad_scores")
+    grad_q = torch.empty_like(q)
+    grad_d = torch.empty_like(docs)
+    _check(lib.gem_maxsim_bwd(_ptr(q), _ptr(qo), B, _ptr(docs), _ptr(doc_offsets), doc_offsets.numel() - 1,
+                              docs.shape[0], _ptr(pair_offsets), _ptr(pair_ids), pair_ids.numel(), _ptr(argmax),
+                              argmax.shape[1], _ptr(g), _ptr(grad_q), _ptr(grad_d), _stream(stream)))
+    return grad_q, grad_d
+
+
+class MaxSimFn(torch.autograd.Function):
+    """Differentiable pair scores S_t = CH(Q_b, P_d) (Eq. 1) with the library's
+    forward (argmax side output) and hand-written backward."""
+
+    @staticmethod
+    def forward(ctx, q, docs, q_offsets, doc_offsets, pair_offsets, pair_ids, compute="bf16"):
+        scores, argmax = maxsim_fwd(q.detach().contiguous(), q_offsets, docs.detach().contiguous(), doc_offsets,
+                                    pair_offsets, pair_ids, compute)
+        ctx.save_for_backward(q, docs, q_offsets, doc_offsets, pair_offsets, pair_ids, argmax)
+        return scores
+
+    @staticmethod
+    def backward(ctx, g):
+        q, docs, qo, do, po, pid, argmax = ctx.saved_tensors
+        gq, gd = maxsim_bwd(q.detach().contiguous(), qo, docs.detach().contiguous(), do, po, pid, argmax, g)
+        return gq, gd, None, None, None, None, None

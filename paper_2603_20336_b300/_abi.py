@@ -15,6 +15,10 @@ SIGNATURES = {
     "gem_store_destroy": (None, [P]),
     "gem_store_info": (C.c_int, [P, P, P, P, P]),
     "gem_store_export": (C.c_int, [P, I32, P, SZ, P]),
+    "gem_assign_codes": (C.c_int, [P, I64, P, I32, P, P, P]),
+    "gem_train_codebook": (C.c_int, [P, I32, I32, I64, C.c_uint64, P, P]),
+    "gem_store_set_codebook": (C.c_int, [P, P, I32, P]),
+    "gem_estimate_codes": (C.c_int, [P, P, P, P, I32, I64, P, P, I64, P, P]),
     "gem_workspace_create": (C.c_int, [P, I32, I64, I32, I64, I32, C.POINTER(P)]),
     "gem_workspace_destroy": (None, [P]),
     "gem_workspace_set_schedule": (C.c_int, [P, I32, I32]),
@@ -24,6 +28,12 @@ SIGNATURES = {
     "gem_search": (C.c_int, [P, P, P, P, I32, I64, I32, I32, I32, P, P, P]),
     "gem_search_host": (C.c_int, [P, P, P, P, I32, I32, I32, I32, P, P, P]),
     "gem_stream_status": (C.c_int, [P, P]),
+    "gem_maxsim_fwd": (C.c_int, [P, P, I32, P, P, I64, P, P, I64, I32, I32, P, P, P, P]),
+    "gem_maxsim_bwd": (C.c_int, [P, P, I32, P, P, I64, I64, P, P, I64, P, I32, P, P, P, P]),
+    "gem_batch_create": (C.c_int, [P, I32, I32, I64, I32, I64, I32, I32, P, P, P, P, P, C.POINTER(P)]),
+    "gem_batch_run": (C.c_int, [P, I32, I64, I64, I32, P]),
+    "gem_batch_status": (C.c_int, [P]),
+    "gem_batch_destroy": (None, [P]),
     "gem_kernel_launches": (I64, []),
 }
 

@@ -1,7 +1,10 @@
 // C-ABI entry points of libgem (declared in include/gem.h): argument checks,
 // object lifetime and the dispatch of each call onto the kernels.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <numeric>
+#include <random>
 #include <cstring>
 #include <string>
 
@@ -94,6 +97,8 @@ void gem_store_destroy(gem_store* s) {
   dfree(s->d_bf16);
   dfree(s->d_fp8);
   dfree(s->d_fp8_scale);
+  dfree(s->d_codebook);
+  dfree(s->d_codes);
   for (auto& kv : s->chunks) dfree(kv.second.d_chunk_doc);
   cudaSetDevice(prev);
   delete s;
@@ -215,6 +220,8 @@ gem_status gem_store_export(const gem_store* s, int32_t what, void* dst, size_t 
     case GEM_EXPORT_FP8_SCALE: src = s->d_fp8_scale; bytes = sizeof(float) * s->n_pad_vecs; break;
     case GEM_EXPORT_OFFSETS: src = s->d_offsets; bytes = sizeof(int64_t) * (s->n_sets + 1); break;
     case GEM_EXPORT_PAD_OFFSETS: src = s->d_pad_offsets; bytes = sizeof(int64_t) * (s->n_sets + 1); break;
+    case GEM_EXPORT_CODES: src = s->d_codes; bytes = sizeof(int32_t) * s->n_vecs; break;
+    case GEM_EXPORT_CODEBOOK: src = s->d_codebook; bytes = sizeof(float) * (size_t)s->k1 * kDim; break;
     default: return fail(GEM_ERR_INVALID, "unknown export");
   }
   if (!src) return fail(GEM_ERR_STATE, "store does not keep that array");
@@ -233,7 +240,8 @@ void gem_workspace_destroy(gem_workspace* w) {
   void* ptrs[] = {w->d_status, w->d_plan_hdr, w->d_part_query, w->d_part_rows, w->d_part_g,
                   w->d_part_pass, w->d_part_slot, w->d_part_row0, w->d_row_part, w->d_qpack_bf16,
                   w->d_qpack_fp8, w->d_qpack_scale, w->d_scores, w->d_pool_ids, w->d_pool_off,
-                  w->d_pool_scores, w->d_q_in, w->d_qo_in, w->d_out_ids, w->d_out_scores};
+                  w->d_pool_scores, w->d_q_in, w->d_qo_in, w->d_out_ids, w->d_out_scores,
+                  w->d_qcodes, w->d_tables};
   for (void* p : ptrs) dfree(p);
   cudaSetDevice(prev);
   delete w;
@@ -297,6 +305,13 @@ gem_status gem_workspace_create(const gem_store* s, int32_t max_queries, int64_t
     WS_ALLOC(d_pool_ids, max_cands);
     WS_ALLOC(d_pool_scores, max_cands);
   }
+  if (s->k1 > 0) {
+    // tables of up to 16 query parts (8 MB each at k1 = 65536)
+    const int max_np = (max_q_len + 31) / 32;
+    w->table_parts = std::max(max_np, std::min(16, max_queries * max_np));
+    WS_ALLOC(d_qcodes, max_q_rows);
+    WS_ALLOC(d_tables, (size_t)w->table_parts * s->k1 * 32);
+  }
 #undef WS_ALLOC
   cudaError_t e = cudaMemset(w->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(w->d_plan_hdr, 0, sizeof(int) * kPlanHdrInts);
@@ -314,6 +329,94 @@ gem_status gem_workspace_create(const gem_store* s, int32_t max_queries, int64_t
     return fail(GEM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the packed fp8 queries");
   }
   *out = w;
+  return GEM_OK;
+}
+
+gem_status gem_assign_codes(const float* x, int64_t n, const float* centroids, int32_t k1,
+                            int32_t* codes, float* best, void* stream) {
+  if (!x || !centroids || !codes) return fail(GEM_ERR_INVALID, "NULL argument");
+  if (n < 0 || k1 < 1) return fail(GEM_ERR_INVALID, "bad sizes");
+  return launch_assign(x, n, centroids, k1, codes, best, reinterpret_cast<cudaStream_t>(stream));
+}
+
+gem_status gem_train_codebook(const gem_store* s, int32_t k1, int32_t iters, int64_t sample,
+                              uint64_t seed, float* centroids_out, void* stream) {
+  if (!s || !centroids_out) return fail(GEM_ERR_INVALID, "NULL argument");
+  if (!s->d_f32) return fail(GEM_ERR_STATE, "training reads the fp32 copy");
+  if (iters < 0) return fail(GEM_ERR_INVALID, "iters < 0");
+  gem_status r = check_current_device(s->device);
+  if (r != GEM_OK) return r;
+  const int64_t n = (sample <= 0 || sample >= s->n_vecs) ? s->n_vecs : sample;
+  if (k1 < 1 || k1 > n) return fail(GEM_ERR_INVALID, "k1 must be 1..sample size");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // sample rows (without replacement) and the initial centroids: a seeded
+  // shuffle of the sample; both are host-side index choices only
+  std::mt19937_64 rng(seed);
+  std::vector<int64_t> rows;
+  if (n == s->n_vecs) {
+    rows.resize(n);
+    std::iota(rows.begin(), rows.end(), 0);
+  } else {
+    std::vector<int64_t> all(s->n_vecs);
+    std::iota(all.begin(), all.end(), 0);
+    for (int64_t i = 0; i < n; ++i) {
+      std::uniform_int_distribution<int64_t> pick(i, s->n_vecs - 1);
+      std::swap(all[i], all[pick(rng)]);
+    }
+    rows.assign(all.begin(), all.begin() + n);
+  }
+  std::vector<int64_t> init(rows.begin(), rows.end());
+  for (int64_t i = 0; i < k1; ++i) {
+    std::uniform_int_distribution<int64_t> pick(i, n - 1);
+    std::swap(init[i], init[pick(rng)]);
+  }
+  init.resize(k1);
+  float* X = nullptr;
+  int64_t* d_rows = nullptr;
+  int32_t* codes = nullptr;
+  double* sums = nullptr;
+  int* counts = nullptr;
+  auto cleanup = [&]() { dfree(X); dfree(d_rows); dfree(codes); dfree(sums); dfree(counts); };
+  if ((r = dmalloc(&X, (size_t)n * kDim, "sample")) != GEM_OK ||
+      (r = dmalloc(&d_rows, (size_t)std::max<int64_t>(n, k1), "sample rows")) != GEM_OK ||
+      (r = dmalloc(&codes, (size_t)n, "sample codes")) != GEM_OK ||
+      (r = dmalloc(&sums, (size_t)k1 * kDim, "centroid sums")) != GEM_OK ||
+      (r = dmalloc(&counts, (size_t)k1, "centroid counts")) != GEM_OK) {
+    cleanup();
+    return r;
+  }
+  cudaError_t e = cudaMemcpyAsync(d_rows, init.data(), sizeof(int64_t) * k1, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) r = launch_gather_rows(s->d_f32, d_rows, k1, centroids_out, st);
+  if (e == cudaSuccess && r == GEM_OK)
+    e = cudaMemcpyAsync(d_rows, rows.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && r == GEM_OK) r = launch_gather_rows(s->d_f32, d_rows, n, X, st);
+  for (int it = 0; it < iters && e == cudaSuccess && r == GEM_OK; ++it) {
+    r = launch_assign(X, n, centroids_out, k1, codes, nullptr, st);
+    if (r == GEM_OK) r = launch_kmeans_step(X, n, codes, sums, counts, k1, centroids_out, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "codebook training");
+  return r;
+}
+
+gem_status gem_store_set_codebook(gem_store* s, const float* centroids, int32_t k1, void* stream) {
+  if (!s || !centroids) return fail(GEM_ERR_INVALID, "NULL argument");
+  if (k1 < 1) return fail(GEM_ERR_INVALID, "k1 < 1");
+  if (!s->d_f32) return fail(GEM_ERR_STATE, "codes are assigned from the fp32 copy");
+  gem_status r = check_current_device(s->device);
+  if (r != GEM_OK) return r;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  dfree(s->d_codebook);
+  s->d_codebook = nullptr;
+  s->k1 = 0;
+  if (!s->d_codes && (r = dmalloc(&s->d_codes, (size_t)s->n_vecs, "codes")) != GEM_OK) return r;
+  if ((r = dmalloc(&s->d_codebook, (size_t)k1 * kDim, "codebook")) != GEM_OK) return r;
+  GEM_CUDA_TRY(cudaMemcpyAsync(s->d_codebook, centroids, sizeof(float) * (size_t)k1 * kDim,
+                               cudaMemcpyDeviceToDevice, st));
+  if ((r = launch_assign(s->d_f32, s->n_vecs, s->d_codebook, k1, s->d_codes, nullptr, st)) != GEM_OK) return r;
+  GEM_CUDA_TRY(cudaStreamSynchronize(st));
+  s->k1 = k1;
   return GEM_OK;
 }
 
@@ -387,9 +490,32 @@ gem_status gem_score_ids(const gem_store* s, gem_workspace* w, const float* q,
     if (!s->d_f32) return fail(GEM_ERR_STATE, "store keeps no fp32 copy");
     return launch_f32_score(s, w, q, q_offsets, n_queries, cand_offsets, cand_ids, n_cands, scores, st);
   }
+  if (compute == GEM_CODES) {
+    if (!s->d_f32 || s->k1 == 0 || !w->d_qcodes)
+      return fail(GEM_ERR_STATE, "the codes form needs a codebook before the workspace is created");
+    r = launch_assign(q, n_q_rows, s->d_codebook, s->k1, w->d_qcodes, nullptr, st);
+    if (r != GEM_OK) return r;
+    return launch_f32_score(s, w, q, q_offsets, n_queries, cand_offsets, cand_ids, n_cands, scores, st,
+                            w->d_qcodes);
+  }
   if (compute == GEM_BF16 || compute == GEM_FP8_E4M3)
-    return fail(GEM_ERR_UNSUPPORTED, "id-list scoring in this dtype is not available");
+    return fail(GEM_ERR_UNSUPPORTED, "id-list scoring runs in GEM_F32 or GEM_CODES");
   return fail(GEM_ERR_INVALID, "unknown compute dtype");
+}
+
+gem_status gem_estimate_codes(const gem_store* s, gem_workspace* w, const float* q,
+                              const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
+                              const int64_t* cand_offsets, const int64_t* cand_ids, int64_t n_cands,
+                              float* est, void* stream) {
+  gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
+  if (r != GEM_OK) return r;
+  if (!est) return fail(GEM_ERR_INVALID, "est is NULL");
+  if (s->k1 == 0 || !w->d_tables)
+    return fail(GEM_ERR_STATE, "store had no codebook when the workspace was created");
+  if (cand_offsets && n_cands > 0 && !cand_ids) return fail(GEM_ERR_INVALID, "cand_ids is NULL");
+  if (cand_offsets && n_cands == 0) return GEM_OK;
+  return launch_qch(s, w, q, q_offsets, n_queries, n_q_rows, cand_offsets, cand_ids, est,
+                    reinterpret_cast<cudaStream_t>(stream));
 }
 
 gem_status gem_topk(gem_workspace* w, const float* scores, const int64_t* row_offsets, int32_t rows,
@@ -475,6 +601,87 @@ gem_status gem_search_host(const gem_store* s, gem_workspace* w, const float* q_
   GEM_CUDA_TRY(cudaStreamSynchronize(st));
   return GEM_OK;
 }
+
+static int current_sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+gem_status gem_maxsim_fwd(const float* q, const int64_t* q_offsets, int32_t n_queries, const float* docs,
+                          const int64_t* doc_offsets, int64_t n_docs, const int64_t* pair_offsets,
+                          const int64_t* pair_ids, int64_t n_pairs, int32_t max_q_len, int32_t compute,
+                          float* scores, int32_t* argmax, gem_workspace* ws, void* stream) {
+  if (!q || !q_offsets || !docs || !doc_offsets || !pair_offsets || !scores || !argmax || (n_pairs > 0 && !pair_ids))
+    return fail(GEM_ERR_INVALID, "NULL argument");
+  if (n_queries < 1 || n_docs < 1 || n_pairs < 0) return fail(GEM_ERR_INVALID, "bad sizes");
+  if (max_q_len < 1 || max_q_len > 256) return fail(GEM_ERR_INVALID, "max_q_len must be 1..256");
+  if (compute != GEM_F32 && compute != GEM_BF16) return fail(GEM_ERR_INVALID, "compute must be GEM_F32 or GEM_BF16");
+  if (n_pairs == 0) return GEM_OK;
+  return launch_maxsim_fwd(q, q_offsets, n_queries, docs, doc_offsets, n_docs, pair_offsets, pair_ids, max_q_len,
+                           compute == GEM_BF16, scores, argmax, ws ? ws->d_status : nullptr, current_sm_count(),
+                           reinterpret_cast<cudaStream_t>(stream));
+}
+
+gem_status gem_maxsim_bwd(const float* q, const int64_t* q_offsets, int32_t n_queries, const float* docs,
+                          const int64_t* doc_offsets, int64_t n_docs, int64_t n_doc_rows,
+                          const int64_t* pair_offsets, const int64_t* pair_ids, int64_t n_pairs,
+                          const int32_t* argmax, int32_t max_q_len, const float* grad_scores, float* grad_q,
+                          float* grad_docs, void* stream) {
+  if (!q || !q_offsets || !docs || !doc_offsets || !pair_offsets || !argmax || !grad_scores ||
+      (n_pairs > 0 && !pair_ids))
+    return fail(GEM_ERR_INVALID, "NULL argument");
+  if (n_queries < 1 || n_docs < 1 || n_pairs < 0 || n_doc_rows < n_docs) return fail(GEM_ERR_INVALID, "bad sizes");
+  if (max_q_len < 1 || max_q_len > 256) return fail(GEM_ERR_INVALID, "max_q_len must be 1..256");
+  return launch_maxsim_bwd(q, q_offsets, n_queries, docs, doc_offsets, n_docs, n_doc_rows, pair_offsets, pair_ids,
+                           n_pairs, argmax, max_q_len, grad_scores, grad_q, grad_docs, current_sm_count(),
+                           reinterpret_cast<cudaStream_t>(stream));
+}
+
+gem_status gem_batch_create(const gem_store* s, int32_t mode, int32_t max_queries, int64_t max_q_rows,
+                            int32_t max_q_len, int64_t max_cands, int32_t seg, int32_t ctas_per_sm,
+                            float* q, int64_t* q_offsets, int64_t* cand_offsets, int64_t* cand_ids,
+                            float* scores, gem_batch** out) {
+  if (!out) return fail(GEM_ERR_INVALID, "out is NULL");
+  if (!q || !q_offsets || !cand_offsets || (max_cands > 0 && (!cand_ids || !scores)))
+    return fail(GEM_ERR_INVALID, "batch buffer is NULL");
+  *out = nullptr;
+  if (!s) return fail(GEM_ERR_INVALID, "store is NULL");
+  if (mode != GEM_F32 && mode != GEM_CODES) return fail(GEM_ERR_INVALID, "mode must be GEM_F32 or GEM_CODES");
+  if (!s->d_f32) return fail(GEM_ERR_STATE, "batched scoring reads the fp32 copy");
+  if (mode == GEM_CODES && s->k1 == 0) return fail(GEM_ERR_STATE, "GEM_CODES needs a store codebook");
+  if (max_queries < 1 || max_q_rows < 1 || max_cands < 0) return fail(GEM_ERR_INVALID, "bad capacity");
+  if (max_q_len < 1 || max_q_len > 32 * kMaxPasses) return fail(GEM_ERR_INVALID, "max_q_len must be 1..256");
+  if (seg < 1 || seg > 1024) return fail(GEM_ERR_INVALID, "seg must be 1..1024");
+  gem_status r = check_current_device(s->device);
+  if (r != GEM_OK) return r;
+  return batch_create(s, mode, max_queries, max_q_rows, max_q_len, max_cands, seg, ctas_per_sm, q, q_offsets,
+                      cand_offsets, cand_ids, scores, out);
+}
+
+gem_status gem_batch_run(gem_batch* b, int32_t n_queries, int64_t n_q_rows, int64_t n_cands,
+                         int32_t use_graph, void* stream) {
+  if (!b) return fail(GEM_ERR_INVALID, "batch is NULL");
+  if (n_queries < 1 || n_queries > b->max_queries) return fail(GEM_ERR_INVALID, "n_queries out of range");
+  if (n_q_rows < n_queries || n_q_rows > b->max_q_rows) return fail(GEM_ERR_INVALID, "n_q_rows out of range");
+  if (n_cands < 0 || n_cands > b->max_cands) return fail(GEM_ERR_INVALID, "n_cands out of range");
+  gem_status r = check_current_device(b->device);
+  if (r != GEM_OK) return r;
+  return batch_run(b, n_queries, n_q_rows, n_cands, use_graph, reinterpret_cast<cudaStream_t>(stream));
+}
+
+gem_status gem_batch_status(gem_batch* b) {
+  if (!b) return fail(GEM_ERR_INVALID, "batch is NULL");
+  if (b->launched) GEM_CUDA_TRY(cudaEventSynchronize(b->done));
+  int code = 0;
+  GEM_CUDA_TRY(cudaMemcpy(&code, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  GEM_CUDA_TRY(cudaMemset(b->d_status, 0, sizeof(int)));
+  if (code != 0) set_error("device-side check failed in a batched run");
+  return (gem_status)code;
+}
+
+void gem_batch_destroy(gem_batch* b) { batch_destroy(b); }
 
 int64_t gem_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 

@@ -1,0 +1,246 @@
+// MaxSim forward with argmax side output, and its backward.
+//
+// Forward, per (query b, set d) pair: S = sum_i max_j <q_i, p_j> (Eq. 1) and
+// j*(i) = argmax_j <q_i, p_j> (lowest j on ties).  Compute GEM_BF16 rounds every
+// component of q and p to bfloat16 (nearest even) before the FP32 fused
+// multiply-add chain over k; GEM_F32 uses the FP32 values.  The sum over i is a
+// Kahan sum in ascending i.
+//
+// Backward, for an upstream gradient g[t] per pair t (the score is piecewise
+// linear; the gradient is taken at the forward's argmax, treating the bf16
+// rounding as the identity):
+//   dL/dq_i   += g[t] * p_{j*(t,i)}                     (FP32 values of p)
+//   dL/dp_j   += g[t] * sum over i with j*(t,i) = j of q_i
+// grad_q is accumulated per query over its pairs in ascending pair order (one
+// thread per output element, deterministic); grad_docs is zeroed and each pair
+// adds its contribution with one atomic add per element, which is deterministic
+// whenever every set occurs in at most one pair.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace gem {
+namespace {
+
+constexpr int kFbWarps = 4;
+constexpr int kFbStride = kDim + 4;
+constexpr int kFbBlock = 8;
+
+__device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+struct FwdArgs {
+  const float* q;
+  const int64_t* q_off;
+  int n_queries;
+  const float* docs;
+  const int64_t* d_off;
+  int64_t n_docs;
+  const int64_t* pair_off;
+  const int64_t* pair_ids;
+  int bf16;
+  int max_q_len;
+  float* scores;
+  int32_t* argmax;   // [n_pairs * max_q_len]
+  int* status;
+};
+
+// One CTA per query (grid-stride), one warp per pair; lane = query row.
+__global__ void __launch_bounds__(kFbWarps * 32) maxsim_fwd_kernel(FwdArgs a) {
+  extern __shared__ float sm[];
+  float* qs = sm;                                          // [max_q_len * kFbStride]
+  float* stage_all = qs + a.max_q_len * kFbStride;         // [warps][kFbBlock * 128]
+  float* rmax_all = stage_all + kFbWarps * kFbBlock * kDim;  // [warps][max_q_len]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* stage = stage_all + warp * kFbBlock * kDim;
+  float* rmax = rmax_all + warp * a.max_q_len;
+  for (int b = blockIdx.x; b < a.n_queries; b += gridDim.x) {
+    const int64_t q0 = a.q_off[b];
+    const int m_q = (int)(a.q_off[b + 1] - q0);
+    __syncthreads();
+    if (m_q < 1 || m_q > a.max_q_len) {
+      if (threadIdx.x == 0) set_status(a.status, kDevInvalid);
+      continue;
+    }
+    for (int idx = threadIdx.x; idx < m_q * kDim; idx += blockDim.x) {
+      const int i = idx / kDim, k = idx % kDim;
+      const float v = a.q[(q0 + i) * kDim + k];
+      qs[i * kFbStride + k] = a.bf16 ? round_bf16(v) : v;
+    }
+    __syncthreads();
+    for (int64_t t = a.pair_off[b] + warp; t < a.pair_off[b + 1]; t += kFbWarps) {
+      const int64_t d = a.pair_ids[t];
+      if (d < 0 || d >= a.n_docs) {
+        if (lane == 0) {
+          set_status(a.status, kDevBounds);
+          a.scores[t] = __int_as_float(0x7fc00000);
+        }
+        continue;
+      }
+      const int64_t r0 = a.d_off[d];
+      const int m_p = (int)(a.d_off[d + 1] - r0);
+      for (int rg = 0; rg < (m_q + 31) / 32; ++rg) {
+        const int i = rg * 32 + lane;
+        float best = -INFINITY;
+        int best_j = 0;
+        for (int j0 = 0; j0 < m_p; j0 += kFbBlock) {
+          const int nv = min(kFbBlock, m_p - j0);
+          __syncwarp();
+          for (int v = 0; v < nv; ++v) {
+            float4 x = reinterpret_cast<const float4*>(a.docs + (r0 + j0 + v) * kDim)[lane];
+            if (a.bf16) x = make_float4(round_bf16(x.x), round_bf16(x.y), round_bf16(x.z), round_bf16(x.w));
+            reinterpret_cast<float4*>(stage + v * kDim)[lane] = x;
+          }
+          __syncwarp();
+          if (i < m_q) {
+            for (int v = 0; v < nv; ++v) {
+              float acc = 0.f;
+#pragma unroll 8
+              for (int k = 0; k < kDim; ++k) acc = __fmaf_rn(qs[i * kFbStride + k], stage[v * kDim + k], acc);
+              if (acc > best) { best = acc; best_j = j0 + v; }
+            }
+          }
+        }
+        if (i < m_q) {
+          rmax[i] = best;
+          a.argmax[t * a.max_q_len + i] = best_j;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        float s = 0.f, c = 0.f;
+        for (int i = 0; i < m_q; ++i) {
+          const float y = __fsub_rn(rmax[i], c);
+          const float tt = __fadd_rn(s, y);
+          c = __fsub_rn(__fsub_rn(tt, s), y);
+          s = tt;
+        }
+        a.scores[t] = s;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+struct BwdArgs {
+  const float* q;
+  const int64_t* q_off;
+  int n_queries;
+  const float* docs;
+  const int64_t* d_off;
+  int64_t n_docs;
+  const int64_t* pair_off;
+  const int64_t* pair_ids;
+  const int32_t* argmax;
+  int max_q_len;
+  const float* g;
+  float* grad_q;
+  float* grad_docs;
+};
+
+// grad_q: one CTA per query; thread per (row i, 4 components).
+__global__ void __launch_bounds__(256) maxsim_bwd_q_kernel(BwdArgs a) {
+  for (int b = blockIdx.x; b < a.n_queries; b += gridDim.x) {
+    const int64_t q0 = a.q_off[b];
+    const int m_q = (int)(a.q_off[b + 1] - q0);
+    for (int idx = threadIdx.x; idx < m_q * (kDim / 4); idx += blockDim.x) {
+      const int i = idx / (kDim / 4), k4 = idx % (kDim / 4);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int64_t t = a.pair_off[b]; t < a.pair_off[b + 1]; ++t) {
+        const int64_t d = a.pair_ids[t];
+        if (d < 0 || d >= a.n_docs) continue;
+        const int j = a.argmax[t * a.max_q_len + i];
+        const float gt = a.g[t];
+        const float4 p = reinterpret_cast<const float4*>(a.docs + (a.d_off[d] + j) * kDim)[k4];
+        acc.x = __fmaf_rn(gt, p.x, acc.x);
+        acc.y = __fmaf_rn(gt, p.y, acc.y);
+        acc.z = __fmaf_rn(gt, p.z, acc.z);
+        acc.w = __fmaf_rn(gt, p.w, acc.w);
+      }
+      reinterpret_cast<float4*>(a.grad_q + (q0 + i) * kDim)[k4] = acc;
+    }
+  }
+}
+
+// grad_docs: one CTA per pair (grid-stride over queries' pairs); thread per
+// (set row j, 4 components): sum of q_i over the rows i whose argmax is j.
+__global__ void __launch_bounds__(256) maxsim_bwd_p_kernel(BwdArgs a, int64_t n_pairs) {
+  __shared__ int js[256];
+  for (int64_t t = blockIdx.x; t < n_pairs; t += gridDim.x) {
+    // query of pair t
+    int lo = 0, hi = a.n_queries - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.pair_off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int b = lo;
+    const int64_t d = a.pair_ids[t];
+    if (d < 0 || d >= a.n_docs) continue;
+    const int64_t q0 = a.q_off[b];
+    const int m_q = (int)(a.q_off[b + 1] - q0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m_q; i += blockDim.x) js[i] = a.argmax[t * a.max_q_len + i];
+    __syncthreads();
+    const int64_t r0 = a.d_off[d];
+    const int m_p = (int)(a.d_off[d + 1] - r0);
+    const float gt = a.g[t];
+    for (int idx = threadIdx.x; idx < m_p * (kDim / 4); idx += blockDim.x) {
+      const int j = idx / (kDim / 4), k4 = idx % (kDim / 4);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      bool any = false;
+      for (int i = 0; i < m_q; ++i) {
+        if (js[i] != j) continue;
+        const float4 qv = reinterpret_cast<const float4*>(a.q + (q0 + i) * kDim)[k4];
+        acc.x += qv.x; acc.y += qv.y; acc.z += qv.z; acc.w += qv.w;
+        any = true;
+      }
+      if (any) {
+        float* out = a.grad_docs + (r0 + j) * kDim + 4 * k4;
+        atomicAdd(out + 0, gt * acc.x);
+        atomicAdd(out + 1, gt * acc.y);
+        atomicAdd(out + 2, gt * acc.z);
+        atomicAdd(out + 3, gt * acc.w);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+gem_status launch_maxsim_fwd(const float* q, const int64_t* q_off, int32_t n_queries, const float* docs,
+                             const int64_t* d_off, int64_t n_docs, const int64_t* pair_off,
+                             const int64_t* pair_ids, int32_t max_q_len, int bf16, float* scores,
+                             int32_t* argmax, int* status, int n_sm, cudaStream_t st) {
+  FwdArgs a{q, q_off, n_queries, docs, d_off, n_docs, pair_off, pair_ids, bf16, max_q_len, scores, argmax, status};
+  const size_t smem = sizeof(float) * ((size_t)max_q_len * kFbStride + kFbWarps * kFbBlock * kDim +
+                                       (size_t)kFbWarps * max_q_len);
+  GEM_CUDA_TRY(cudaFuncSetAttribute(maxsim_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = std::min(n_queries, n_sm * 8);
+  maxsim_fwd_kernel<<<grid, kFbWarps * 32, smem, st>>>(a);
+  GEM_CUDA_TRY(cudaGetLastError());
+  note_launches(1);
+  return GEM_OK;
+}
+
+gem_status launch_maxsim_bwd(const float* q, const int64_t* q_off, int32_t n_queries, const float* docs,
+                             const int64_t* d_off, int64_t n_docs, int64_t n_doc_rows, const int64_t* pair_off,
+                             const int64_t* pair_ids, int64_t n_pairs, const int32_t* argmax, int32_t max_q_len,
+                             const float* g, float* grad_q, float* grad_docs, int n_sm, cudaStream_t st) {
+  BwdArgs a{q, q_off, n_queries, docs, d_off, n_docs, pair_off, pair_ids, argmax, max_q_len, g, grad_q, grad_docs};
+  if (grad_q) {
+    maxsim_bwd_q_kernel<<<std::min(n_queries, n_sm * 8), 256, 0, st>>>(a);
+    GEM_CUDA_TRY(cudaGetLastError());
+    note_launches(1);
+  }
+  if (grad_docs) {
+    GEM_CUDA_TRY(cudaMemsetAsync(grad_docs, 0, sizeof(float) * n_doc_rows * kDim, st));
+    if (n_pairs > 0) {
+      maxsim_bwd_p_kernel<<<(int)std::min<int64_t>(n_pairs, (int64_t)n_sm * 16), 256, 0, st>>>(a, n_pairs);
+      GEM_CUDA_TRY(cudaGetLastError());
+      note_launches(1);
+    }
+  }
+  return GEM_OK;
+}
+
+}  // namespace gem

@@ -65,6 +65,10 @@ struct gem_store {
   uint8_t* d_fp8 = nullptr;
   float* d_fp8_scale = nullptr;
   int64_t max_set_len = 0;
+  // stage-1 codebook C_quant and the codes NN(p) of every stored vector
+  int k1 = 0;
+  float* d_codebook = nullptr;   // [k1 * 128], unit rows
+  int32_t* d_codes = nullptr;    // [n_vecs], original (unpadded) row order
   // tensor maps of the doc copies, keyed by tile rows (box height)
   mutable std::map<int, CUtensorMap> tmap_bf16;
   mutable std::map<int, CUtensorMap> tmap_fp8;
@@ -103,6 +107,11 @@ struct gem_workspace {
   CUtensorMap tmap_q_bf16;
   CUtensorMap tmap_q_fp8;
 
+  // quantized estimate
+  int32_t* d_qcodes = nullptr;     // [max_q_rows]
+  float* d_tables = nullptr;       // [table_parts * k1 * 32]
+  int table_parts = 0;
+
   // search pipeline
   float* d_scores = nullptr;       // [max_queries * n_sets]
   int64_t* d_pool_ids = nullptr;   // [max_cands]
@@ -114,6 +123,38 @@ struct gem_workspace {
   int64_t* d_qo_in = nullptr;
   int64_t* d_out_ids = nullptr;
   float* d_out_scores = nullptr;
+};
+
+// A batched candidate scorer: its own buffers and the captured CUDA graph of
+// one round (batch.cu).
+struct gem_batch {
+  const gem_store* store = nullptr;
+  int device = 0;
+  int mode = GEM_F32;
+  int32_t max_queries = 0;
+  int64_t max_q_rows = 0;
+  int32_t max_q_len = 0;
+  int64_t max_cands = 0;
+  int seg = 32;
+  int grid = 0;
+  int n_warps = 4;
+  // caller-owned inputs and output (fixed addresses, read by the graph)
+  float* d_q = nullptr;
+  int64_t* d_q_off = nullptr;
+  int64_t* d_cand_off = nullptr;
+  int64_t* d_cand_ids = nullptr;
+  float* d_scores = nullptr;
+  // internal
+  int64_t* h_hdr = nullptr;  // pinned: n_queries, n_q_rows, n_cands
+  int64_t* d_hdr = nullptr;  // + [3] total items
+  int64_t* d_item_off = nullptr;
+  unsigned long long* d_counter = nullptr;
+  int32_t* d_qcodes = nullptr;
+  int* d_status = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  bool launched = false;
 };
 
 namespace gem {
@@ -154,15 +195,48 @@ gem_status launch_plan(gem_workspace* ws, const float* q, const int64_t* q_offse
 gem_status launch_tc_score_all(const gem_store* s, gem_workspace* ws, int compute, int m_tiles,
                                int chunk_rows, float* scores, cudaStream_t st);
 
-// FP32 SIMT exact MaxSim (Kahan over query vectors), all sets or id lists.
+// FP32 SIMT exact MaxSim (Kahan over query vectors), all sets or id lists;
+// qcodes != nullptr selects the codes form (centroids in place of vectors).
 gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* q,
                             const int64_t* q_offsets, int32_t n_queries, const int64_t* cand_offsets,
-                            const int64_t* cand_ids, int64_t n_cands, float* scores, cudaStream_t st);
+                            const int64_t* cand_ids, int64_t n_cands, float* scores, cudaStream_t st,
+                            const int32_t* qcodes = nullptr);
+
+// MaxSim forward with argmax and backward (backward.cu).
+gem_status launch_maxsim_fwd(const float* q, const int64_t* q_off, int32_t n_queries, const float* docs,
+                             const int64_t* d_off, int64_t n_docs, const int64_t* pair_off,
+                             const int64_t* pair_ids, int32_t max_q_len, int bf16, float* scores,
+                             int32_t* argmax, int* status, int n_sm, cudaStream_t st);
+gem_status launch_maxsim_bwd(const float* q, const int64_t* q_off, int32_t n_queries, const float* docs,
+                             const int64_t* d_off, int64_t n_docs, int64_t n_doc_rows, const int64_t* pair_off,
+                             const int64_t* pair_ids, int64_t n_pairs, const int32_t* argmax, int32_t max_q_len,
+                             const float* g, float* grad_q, float* grad_docs, int n_sm, cudaStream_t st);
+
+// Batched candidate scoring (batch.cu).
+gem_status batch_create(const gem_store* s, int32_t mode, int32_t max_queries, int64_t max_q_rows,
+                        int32_t max_q_len, int64_t max_cands, int32_t seg, int32_t ctas_per_sm,
+                        float* q, int64_t* q_offsets, int64_t* cand_offsets, int64_t* cand_ids,
+                        float* scores, gem_batch** out);
+gem_status batch_run(gem_batch* bt, int32_t n_queries, int64_t n_q_rows, int64_t n_cands, int use_graph,
+                     cudaStream_t st);
+void batch_destroy(gem_batch* bt);
 
 // Per-row top-k by (score desc, id asc).
 gem_status launch_topk(gem_workspace* ws, const float* scores, const int64_t* row_offsets,
                        int32_t rows, int64_t cols, const int64_t* ids, int32_t k,
                        int64_t* out_ids, float* out_scores, cudaStream_t st);
+
+// Codes, k-means and the quantized estimate (codes.cu).
+gem_status launch_assign(const float* X, int64_t n, const float* C, int k1, int32_t* codes, float* best,
+                         cudaStream_t st);
+gem_status launch_assign_dev_n(const float* X, int64_t max_n, const int64_t* n_dev, const float* C, int k1,
+                               int32_t* codes, cudaStream_t st);
+gem_status launch_kmeans_step(const float* X, int64_t n, const int32_t* codes, double* sums, int* counts,
+                              int k1, float* C, cudaStream_t st);
+gem_status launch_gather_rows(const float* src, const int64_t* rows, int64_t n, float* dst, cudaStream_t st);
+gem_status launch_qch(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
+                      int32_t n_queries, int64_t n_q_rows, const int64_t* cand_offsets,
+                      const int64_t* cand_ids, float* est, cudaStream_t st);
 
 // FP32 -> bf16 / e4m3 store copies in the padded layout.
 void launch_quantize_bf16(const float* src, const int64_t* off, const int64_t* pad_off,

@@ -2,16 +2,10 @@
 // vectors.  Serves the FP32 exhaustive form and the exact rerank of a candidate
 // pool (the final step of Algorithm 5, CH of Sec. 3.1 Eq. 1).
 //
-// Arithmetic order (fixed, independent of launch shape):
-//   dot(q_i, p_j): one FP32 fused multiply-add chain over k = 0 .. 127
-//   m_i = max_j dot(q_i, p_j)
-//   CH  = Kahan sum of m_i over i = 0 .. m_q - 1 in ascending order
-//
-// Mapping: one CTA per work unit, lane = query row (32 rows per pass, the row's
-// 128 components held in registers), one warp per document; the document's
-// vectors are staged 8 at a time in the warp's shared-memory slice and read as
-// broadcasts.
+// One CTA per work unit (query, segment of sets), one warp per set; the per-pair
+// arithmetic is warp_chamfer (maxsim_simt.cuh).
 #include "internal.h"
+#include "maxsim_simt.cuh"
 #include "ptx.cuh"
 
 namespace gem {
@@ -19,8 +13,6 @@ namespace {
 
 constexpr int kF32Warps = 4;
 constexpr int kF32Threads = kF32Warps * 32;
-constexpr int kVecBlock = 8;          // document vectors staged per step
-constexpr int kQStride = kDim + 4;    // padded query row stride in shared memory (floats)
 constexpr int kSegDocs = 128;         // documents per unit in the all-sets form
 
 struct F32Args {
@@ -34,68 +26,10 @@ struct F32Args {
   const int64_t* cand_ids;
   float* scores;
   int* status;
+  const int32_t* codes;      // codes form: store codes, centroids and query codes
+  const float* centroids;
+  const int32_t* qcodes;
 };
-
-// CH of query rows qs[0 .. m_q) (shared, stride kQStride) against one set.
-// Called by a full warp; returns the score in every lane.
-__device__ __forceinline__ float warp_chamfer(const float* __restrict__ qs, int m_q, const float* __restrict__ P,
-                              int m_p, float* __restrict__ stage, float* __restrict__ rowmax,
-                              float (&qr)[kDim], int& loaded_rg) {
-  const int lane = threadIdx.x & 31;
-  const int n_rg = (m_q + 31) >> 5;
-  for (int rg = 0; rg < n_rg; ++rg) {
-    if (rg != loaded_rg) {
-      const int i = rg * 32 + lane;
-#pragma unroll
-      for (int k = 0; k < kDim; ++k) qr[k] = (i < m_q) ? qs[i * kQStride + k] : 0.f;
-      loaded_rg = rg;
-    }
-    float best = -INFINITY;
-    for (int j0 = 0; j0 < m_p; j0 += kVecBlock) {
-      const int nv = min(kVecBlock, m_p - j0);
-      __syncwarp();
-#pragma unroll
-      for (int v = 0; v < kVecBlock; ++v) {
-        if (v < nv) {
-          float4 x = reinterpret_cast<const float4*>(P + (int64_t)(j0 + v) * kDim)[lane];
-          reinterpret_cast<float4*>(stage + v * kDim)[lane] = x;
-        }
-      }
-      __syncwarp();
-      float acc[kVecBlock];
-#pragma unroll
-      for (int v = 0; v < kVecBlock; ++v) acc[v] = 0.f;
-#pragma unroll
-      for (int k4 = 0; k4 < kDim / 4; ++k4) {
-#pragma unroll
-        for (int v = 0; v < kVecBlock; ++v) {
-          const float4 p = reinterpret_cast<const float4*>(stage + v * kDim)[k4];
-          acc[v] = __fmaf_rn(qr[4 * k4 + 0], p.x, acc[v]);
-          acc[v] = __fmaf_rn(qr[4 * k4 + 1], p.y, acc[v]);
-          acc[v] = __fmaf_rn(qr[4 * k4 + 2], p.z, acc[v]);
-          acc[v] = __fmaf_rn(qr[4 * k4 + 3], p.w, acc[v]);
-        }
-      }
-#pragma unroll
-      for (int v = 0; v < kVecBlock; ++v)
-        if (v < nv) best = fmaxf(best, acc[v]);
-    }
-    const int i = rg * 32 + lane;
-    if (i < m_q) rowmax[i] = best;
-  }
-  __syncwarp();
-  float s = 0.f;
-  if (lane == 0) {
-    float c = 0.f;  // Kahan compensation
-    for (int i = 0; i < m_q; ++i) {
-      const float y = __fsub_rn(rowmax[i], c);
-      const float t = __fadd_rn(s, y);
-      c = __fsub_rn(__fsub_rn(t, s), y);
-      s = t;
-    }
-  }
-  return __shfl_sync(0xffffffffu, s, 0);
-}
 
 __global__ void __launch_bounds__(kF32Threads)
 f32_score_kernel(F32Args a, int max_q_len) {
@@ -119,7 +53,8 @@ f32_score_kernel(F32Args a, int max_q_len) {
     __syncthreads();
     for (int idx = threadIdx.x; idx < m_q * (kDim / 4); idx += blockDim.x) {
       const int i = idx / (kDim / 4), k4 = idx % (kDim / 4);
-      float4 x = reinterpret_cast<const float4*>(a.q + (q0 + i) * kDim)[k4];
+      const float* src = a.qcodes ? a.centroids + (int64_t)a.qcodes[q0 + i] * kDim : a.q + (q0 + i) * kDim;
+      float4 x = reinterpret_cast<const float4*>(src)[k4];
       reinterpret_cast<float4*>(qs + i * kQStride)[k4] = x;
     }
     __syncthreads();
@@ -144,7 +79,8 @@ f32_score_kernel(F32Args a, int max_q_len) {
       } else {
         const int64_t r0 = a.doc_off[id];
         const int m_p = (int)(a.doc_off[id + 1] - r0);
-        score = warp_chamfer(qs, m_q, a.docs + r0 * kDim, m_p, stage, rowmax, qr, loaded_rg);
+        score = warp_chamfer(qs, m_q, a.docs + r0 * kDim, a.qcodes ? a.codes + r0 : nullptr, a.centroids, m_p,
+                             stage, rowmax, qr, loaded_rg);
       }
       if (lane == 0) {
         if (all_sets) a.scores[(int64_t)b * a.n_sets + t] = score;
@@ -158,7 +94,8 @@ f32_score_kernel(F32Args a, int max_q_len) {
 
 gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* q,
                             const int64_t* q_offsets, int32_t n_queries, const int64_t* cand_offsets,
-                            const int64_t* cand_ids, int64_t n_cands, float* scores, cudaStream_t st) {
+                            const int64_t* cand_ids, int64_t n_cands, float* scores, cudaStream_t st,
+                            const int32_t* qcodes) {
   (void)n_cands;
   F32Args a;
   a.q = q;
@@ -171,6 +108,9 @@ gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* 
   a.cand_ids = cand_ids;
   a.scores = scores;
   a.status = ws->d_status;
+  a.codes = s->d_codes;
+  a.centroids = s->d_codebook;
+  a.qcodes = qcodes;
   const int mq = ws->max_q_len;
   const size_t smem = sizeof(float) * ((size_t)mq * kQStride + kF32Warps * kVecBlock * kDim +
                                        (size_t)kF32Warps * mq);
