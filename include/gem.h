@@ -317,6 +317,34 @@ gem_status gem_batch_run(gem_batch* batch, int32_t n_queries, int64_t n_q_rows, 
 gem_status gem_batch_status(gem_batch* batch);
 void gem_batch_destroy(gem_batch* batch);
 
+/*
+ * gem_score_ids_noalloc: id-list scoring that allocates no device memory.  The
+ * paper has no counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc: processes whose device memory is owned by another allocator (a host
+ * framework's caching allocator, a serving runtime that reserves its whole
+ * memory budget at start-up) and that therefore cannot create a gem_workspace or
+ * a gem_batch.  It computes what gem_score_ids computes with GEM_F32 (same
+ * arithmetic, bit-identical scores) using the batched scorer, whose work-plan
+ * scratch lives in a fixed array of about 128 KB in device memory, one per GPU,
+ * that every GPU loading this library keeps until the process exits.
+ *   n_queries   at most 16384 (larger calls fail with GEM_ERR_INVALID)
+ *   max_q_len   bound on the vectors of any query set (1..256)
+ * The other arguments are as in gem_score_ids: all device pointers, caller-owned.
+ * The store still comes from gem_store_create (GEM_KEEP_F32 needed).
+ * Every call on a device shares that one array and it keeps the last call's
+ * contents (each call resets what it needs), so calls whose work overlaps on
+ * the GPU (two streams, or two host threads) race and must be serialised by the
+ * caller.  The first call on a device looks up the array's device address and
+ * sets a kernel attribute; make that first call before any stream capture.
+ * Device-side problems are not reported through a status word: an id outside
+ * [0, n_sets) scores NaN, a negative id scores -inf, and inconsistent
+ * cand_offsets leave scores unwritten.
+ */
+gem_status gem_score_ids_noalloc(const gem_store* store, const float* q, const int64_t* q_offsets,
+                                 int32_t n_queries, int64_t n_q_rows, int32_t max_q_len,
+                                 const int64_t* cand_offsets, const int64_t* cand_ids, int64_t n_cands,
+                                 float* scores, void* stream);
+
 /* Number of kernels this library has enqueued since it was loaded (all
  * devices and threads); lets a caller count the library's launches in a region. */
 int64_t gem_kernel_launches(void);

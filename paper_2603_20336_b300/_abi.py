@@ -35,6 +35,7 @@ SIGNATURES = {
     "gem_batch_status": (C.c_int, [P]),
     "gem_batch_destroy": (None, [P]),
     "gem_kernel_launches": (I64, []),
+    "gem_score_ids_noalloc": (C.c_int, [P, P, P, I32, I64, I32, P, P, I64, P, P]),
 }
 
 

@@ -683,6 +683,22 @@ gem_status gem_batch_status(gem_batch* b) {
 
 void gem_batch_destroy(gem_batch* b) { batch_destroy(b); }
 
+gem_status gem_score_ids_noalloc(const gem_store* s, const float* q, const int64_t* q_offsets,
+                                 int32_t n_queries, int64_t n_q_rows, int32_t max_q_len,
+                                 const int64_t* cand_offsets, const int64_t* cand_ids, int64_t n_cands,
+                                 float* scores, void* stream) {
+  if (!s || !q || !q_offsets || !cand_offsets || (n_cands > 0 && (!cand_ids || !scores)))
+    return fail(GEM_ERR_INVALID, "NULL argument");
+  if (!s->d_f32) return fail(GEM_ERR_STATE, "id-list scoring reads the fp32 copy");
+  if (n_queries < 1 || n_q_rows < n_queries || n_cands < 0) return fail(GEM_ERR_INVALID, "bad sizes");
+  if (max_q_len < 1 || max_q_len > 32 * kMaxPasses) return fail(GEM_ERR_INVALID, "max_q_len must be 1..256");
+  gem_status r = check_current_device(s->device);
+  if (r != GEM_OK) return r;
+  if (n_cands == 0) return GEM_OK;
+  return score_ids_noalloc(s, q, q_offsets, n_queries, n_q_rows, max_q_len, cand_offsets, cand_ids, n_cands,
+                           scores, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int64_t gem_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 gem_status gem_stream_status(gem_workspace* w, void* stream) {

@@ -11,6 +11,9 @@
 // pair gets from gem_score_ids.
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+
 #include "maxsim_simt.cuh"
 #include "ptx.cuh"
 
@@ -242,7 +245,10 @@ gem_status batch_create(const gem_store* s, int32_t mode, int32_t max_queries, i
   if ((e = cudaEventCreateWithFlags(&bt->done, cudaEventDisableTiming)) != cudaSuccess)
     return bail(cuda_fail(e, "event"));
   const size_t smem = batch_smem(max_q_len);
-  if ((e = cudaFuncSetAttribute(batch_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+  // the attribute is the largest any caller needs (max_q_len 256), so batches
+  // and the no-alloc path never lower it for each other
+  if ((e = cudaFuncSetAttribute(batch_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)batch_smem(32 * kMaxPasses))) !=
       cudaSuccess)
     return bail(cuda_fail(e, "smem attribute"));
   int per_sm = 0;
@@ -305,6 +311,98 @@ void batch_destroy(gem_batch* bt) {
     if (p) cudaFree(p);
   if (bt->h_hdr) cudaFreeHost(bt->h_hdr);
   delete bt;
+}
+
+// ---------------------------------------------------------------------------
+// gem_score_ids_noalloc: the batched scorer with its work-plan scratch in a
+// fixed device array instead of caller- or library-allocated memory.
+
+namespace {
+
+constexpr int kNoAllocMaxQueries = 16384;  // queries per call
+constexpr int kNoAllocSeg = 32;
+
+struct NoAllocScratch {
+  int64_t hdr[4];                               // n_queries, n_q_rows, n_cands, items
+  unsigned long long counter;                   // work-queue position
+  int status;
+  int pad;
+  int64_t item_off[kNoAllocMaxQueries + 1];     // first work item of each query
+};
+
+// One copy per device, shared by every call (about 128 KB).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+// Everything a call relies on starting at zero is written here first.
+__global__ void noalloc_init_kernel(NoAllocScratch* sc, int n_queries, int64_t n_q_rows, int64_t n_cands) {
+  sc->hdr[0] = n_queries;
+  sc->hdr[1] = n_q_rows;
+  sc->hdr[2] = n_cands;
+  sc->hdr[3] = 0;
+  sc->counter = 0;
+  sc->status = 0;
+}
+
+std::mutex g_noalloc_mu;
+std::map<int, NoAllocScratch*> g_noalloc_addr;  // device -> device address of the array
+
+// Device address of this device's copy of the array, looked up once per device
+// with that device current.  The name of the array is only a host-side handle.
+gem_status noalloc_scratch(int dev, NoAllocScratch** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  auto it = g_noalloc_addr.find(dev);
+  if (it == g_noalloc_addr.end()) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-alloc scratch");
+    e = cudaFuncSetAttribute(batch_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batch_smem(32 * kMaxPasses));
+    if (e != cudaSuccess) return cuda_fail(e, "shared memory attribute");
+    it = g_noalloc_addr.emplace(dev, reinterpret_cast<NoAllocScratch*>(p)).first;
+  }
+  *out = it->second;
+  return GEM_OK;
+}
+
+}  // namespace
+
+gem_status score_ids_noalloc(const gem_store* s, const float* q, const int64_t* q_offsets, int32_t n_queries,
+                             int64_t n_q_rows, int32_t max_q_len, const int64_t* cand_offsets,
+                             const int64_t* cand_ids, int64_t n_cands, float* scores, cudaStream_t st) {
+  if (n_queries > kNoAllocMaxQueries)
+    return fail(GEM_ERR_INVALID, "gem_score_ids_noalloc takes at most 16384 queries per call");
+  NoAllocScratch* sc = nullptr;
+  gem_status r = noalloc_scratch(s->device, &sc);
+  if (r != GEM_OK) return r;
+  const size_t smem = batch_smem(max_q_len);
+  int per_sm = 0;
+  GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_score_kernel, kBatchWarps * 32, smem));
+  if (per_sm < 1) return fail(GEM_ERR_UNSUPPORTED, "batched scorer does not fit on an SM");
+  noalloc_init_kernel<<<1, 1, 0, st>>>(sc, n_queries, n_q_rows, n_cands);
+  batch_plan_kernel<<<1, 1024, 0, st>>>(sc->hdr, cand_offsets, kNoAllocSeg, sc->item_off, kNoAllocMaxQueries,
+                                        n_cands, &sc->status);
+  BatchArgs a;
+  a.q = q;
+  a.q_off = q_offsets;
+  a.co = cand_offsets;
+  a.ids = cand_ids;
+  a.item_off = sc->item_off;
+  a.hdr = sc->hdr;
+  a.counter = &sc->counter;
+  a.docs = s->d_f32;
+  a.doc_off = s->d_offsets;
+  a.n_sets = s->n_sets;
+  a.codes = nullptr;
+  a.centroids = nullptr;
+  a.qcodes = nullptr;
+  a.seg = kNoAllocSeg;
+  a.max_q_len = max_q_len;
+  a.scores = scores;
+  a.status = &sc->status;
+  batch_score_kernel<<<s->n_sm * per_sm, kBatchWarps * 32, smem, st>>>(a);
+  GEM_CUDA_TRY(cudaGetLastError());
+  note_launches(3);
+  return GEM_OK;
 }
 
 }  // namespace gem

@@ -220,6 +220,9 @@ gem_status batch_create(const gem_store* s, int32_t mode, int32_t max_queries, i
 gem_status batch_run(gem_batch* bt, int32_t n_queries, int64_t n_q_rows, int64_t n_cands, int use_graph,
                      cudaStream_t st);
 void batch_destroy(gem_batch* bt);
+gem_status score_ids_noalloc(const gem_store* s, const float* q, const int64_t* q_offsets, int32_t n_queries,
+                             int64_t n_q_rows, int32_t max_q_len, const int64_t* cand_offsets,
+                             const int64_t* cand_ids, int64_t n_cands, float* scores, cudaStream_t st);
 
 // Per-row top-k by (score desc, id asc).
 gem_status launch_topk(gem_workspace* ws, const float* scores, const int64_t* row_offsets,
