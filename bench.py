@@ -114,31 +114,152 @@ def _barrier(dist):
 
 
 def cpu_baseline(docs_host: torch.Tensor, offsets: np.ndarray, q_host: torch.Tensor, q_offsets: np.ndarray,
-                 n_docs: int, budget_s: float, k: int):
+                 n_queries: int, k: int, n_docs=None):
     """The FP64 oracle (exact CH of every pair + exact top-k), timed on host cores
-    over the first n_docs sets for as many queries as fit in budget_s."""
+    for the first n_queries queries against the first n_docs sets (all by default).
+    Returns the timing and the oracle's top-k (ids, scores) of those queries: the
+    ground truth for recall."""
     import oracle
     try:
         from threadpoolctl import threadpool_info
         cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
     except Exception:
         cores = os.cpu_count()
+    n_docs = len(offsets) - 1 if n_docs is None else n_docs
     off = offsets[: n_docs + 1]
     X = docs_host[: int(off[-1])].numpy()
+    n_queries = min(n_queries, len(q_offsets) - 1)
+    qo = q_offsets[: n_queries + 1]
+    Q = q_host[: int(qo[-1])].numpy()
     t0 = time.perf_counter()
-    done = 0
-    while done < len(q_offsets) - 1:
-        qo = q_offsets[done: done + 2] - q_offsets[done]
-        Q = q_host[int(q_offsets[done]): int(q_offsets[done + 1])].numpy()
-        S = oracle.score_all(Q, qo, X, off)
-        oracle.topk(S[0], k)
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
+    S = oracle.score_all(Q, qo, X, off)
+    truth = [oracle.topk(S[b], k) for b in range(n_queries)]
     dt = time.perf_counter() - t0
-    return {"value": done * n_docs / dt, "unit": "doc-sets/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} queries x first {n_docs} sets (FP64 numpy, exact CH + top-{k})",
-            "seconds": dt}
+    return {"value": n_queries * n_docs / dt, "unit": "doc-sets/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_queries} queries x {n_docs} sets (FP64 numpy, exact CH + top-{k})",
+            "seconds": dt}, truth
+
+
+def _recall(found: np.ndarray, truth):
+    """Mean |found ∩ exact| / k over the queries the oracle finished, plus the
+    swaps that are ties of the exact scores within 1e-6."""
+    rs = []
+    for b, (ids, sc) in enumerate(truth):
+        rs.append(len(set(found[b].tolist()) & set(ids.tolist())) / len(ids))
+    return float(np.mean(rs)) if rs else None
+
+
+def _time(fn, reps=3, st=None):
+    st = st or torch.cuda.current_stream()
+    fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms):
+    """Every hot-path row measured on its own (after the headline timing)."""
+    B = qo.numel() - 1
+    rows = q.shape[0]
+    flops = 2.0 * rows * store.n_vecs * 128
+    out = torch.empty((B, store.n_sets), dtype=torch.float32, device=dev)
+
+    def guard(name, fn):
+        try:
+            stages[name] = fn()
+        except Exception as e:  # a failing extra must not hide the headline line
+            stages[name] = {"error": repr(e)[:300]}
+
+    def fp8():
+        ch = gem.autotune_score_all(store, ws, q, qo, "fp8", scores=out)
+        ms = _time(lambda: gem.score_all(store, ws, q, qo, "fp8", out=out))
+        ids, _ = gem.search(store, ws, q, qo, "fp8", rerank_depth=R, k=K)
+        return {"ms": ms, "pairs_per_s": B * store.n_sets / (ms * 1e-3), "tflops_equiv": flops / ms / 1e9,
+                "schedule": ch, "recall_at_100_after_rerank": _recall(ids.cpu().numpy(), truth)}
+
+    def fp32():
+        ms = _time(lambda: gem.score_all(store, ws, q, qo, "f32", out=out), reps=1)
+        ids, _ = gem.search(store, ws, q, qo, "f32", rerank_depth=R, k=K)
+        return {"ms": ms, "pairs_per_s": B * store.n_sets / (ms * 1e-3), "tflops": flops / ms / 1e9,
+                "recall_at_100": _recall(ids.cpu().numpy(), truth),
+                "bf16_rerank_step_speedup_vs_fp32_exhaustive": ms / step_ms}
+
+    def qch():
+        V = store.n_vecs
+        k1 = 1 << int(np.floor(np.log2(16.0 * np.sqrt(V))))   # Sec. 5.1 codebook size
+        t0 = time.perf_counter()
+        C = gem.train_codebook(store, k1=k1, iters=10, sample=min(V, 2_000_000), seed=5)
+        gem.set_codebook(store, C)
+        t_build = time.perf_counter() - t0
+        ws2 = gem.Workspace(store, max_queries=B, max_q_rows=rows, max_q_len=32, max_cands=B * R)
+        nq = min(B, 64)
+        est = torch.empty((nq, store.n_sets), dtype=torch.float32, device=dev)
+        ms = _time(lambda: gem.estimate_codes(store, ws2, q[: 32 * nq], qo[: nq + 1], out=est), reps=1)
+        pid, _ = gem.topk(ws2, est, R)
+        pool_off = torch.arange(nq + 1, dtype=torch.int64, device=dev) * R
+        rs = gem.score_ids(store, ws2, q[: 32 * nq], qo[: nq + 1], pool_off, pid.view(-1), "f32")
+        ids, _ = gem.topk(ws2, rs.view(nq, R), K, ids=pid.contiguous())
+        assert ws2.status() == 0
+        return {"k1": k1, "codebook_and_codes_s": t_build, "queries": nq, "ms": ms,
+                "pairs_per_s": nq * store.n_sets / (ms * 1e-3),
+                "recall_at_100_after_rerank": _recall(ids.cpu().numpy(), truth[:nq])}
+
+    def beam():
+        nq, rounds = 4096, 20
+        qs = synth.vector_sets(synth.lengths_uniform(nq, 8, 64, 1238 + 7919), synth.centres(4096, 1236),
+                               1238 + 7919, dev)
+        co, ci0 = synth.candidate_lists(nq, store.n_sets, 64, 512, 0.3, 10_000, 1238)
+        qv, qoff = qs.vecs, torch.from_numpy(qs.offsets).to(dev)
+        co_d = torch.from_numpy(co).to(dev)
+        lists = [torch.from_numpy(synth.shift_lists(ci0, r, store.n_sets)).to(dev) for r in range(rounds)]
+        ch = gem.autotune_batch(store, qv, qoff, co_d, lists[0], mode="f32", max_q_len=64)
+        bt = gem.Batch(store, "f32", max_queries=nq, max_q_rows=qv.shape[0], max_q_len=64, max_cands=len(ci0),
+                       seg=ch["seg"], ctas_per_sm=ch["ctas_per_sm"])
+        bt.run(qv, qoff, co_d, lists[0])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for r in range(rounds):
+            bt.run(qv, qoff, co_d, lists[r])
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / rounds
+        # bit-match of the last round with the per-query path on 8 queries
+        got = bt.scores[: len(ci0)].clone()
+        ws3 = gem.Workspace(store, max_queries=1, max_q_rows=64, max_q_len=64)
+        ok = True
+        for b in range(0, nq, nq // 8):
+            lo, hi = int(co[b]), int(co[b + 1])
+            one = gem.score_ids(store, ws3, qv[qs.offsets[b]:qs.offsets[b + 1]],
+                                torch.tensor([0, qs.offsets[b + 1] - qs.offsets[b]], device=dev),
+                                torch.tensor([0, hi - lo], device=dev), lists[-1][lo:hi], "f32")
+            ok &= bool(torch.equal(one, got[lo:hi]))
+        assert bt.status() == 0
+        bt.close()
+        return {"queries": nq, "pairs_per_round": int(len(ci0)), "rounds": rounds, "ms_per_round": ms,
+                "pairs_per_s": len(ci0) / (ms * 1e-3), "schedule": ch, "bit_match_per_query_path": ok}
+
+    def backward():
+        wb = synth.contrastive_batch(device=dev)
+        nb, per_q = 256, 64
+        po = torch.arange(nb + 1, dtype=torch.int64, device=dev) * per_q
+        pid = torch.arange(nb * per_q, dtype=torch.int64, device=dev)
+        qo5 = torch.from_numpy(wb.queries.offsets).to(dev)
+        do5 = torch.from_numpy(wb.docs.offsets).to(dev)
+        s, am = gem.maxsim_fwd(wb.queries.vecs, qo5, wb.docs.vecs, do5, po, pid, "bf16", max_q_len=32)
+        g = torch.randn_like(s)
+        ms_f = _time(lambda: gem.maxsim_fwd(wb.queries.vecs, qo5, wb.docs.vecs, do5, po, pid, "bf16", max_q_len=32))
+        ms_b = _time(lambda: gem.maxsim_bwd(wb.queries.vecs, qo5, wb.docs.vecs, do5, po, pid, am, g))
+        return {"pairs": nb * per_q, "fwd_ms": ms_f, "bwd_ms": ms_b, "doc_vectors": int(wb.docs.n_vecs)}
+
+    guard("fp8_exhaustive", fp8)
+    guard("fp32_exhaustive", fp32)
+    guard("qch_estimate", qch)
+    guard("beam_batch", beam)
+    guard("backward", backward)
 
 
 def run_reference(args, dist, rank, world):
@@ -149,8 +270,8 @@ def run_reference(args, dist, rank, world):
     w = synth.text_corpus(n_sets=20_000, n_queries=max(args.steps + args.warmup, 1), device="cpu")
     per_step = []
     for s in range(args.warmup + args.steps):
-        r = cpu_baseline(w.docs.vecs, w.docs.offsets, w.queries.vecs[32 * s: 32 * (s + 1)],
-                         np.array([0, 32]), 20_000, 0.0, cfg["k"])
+        r, _ = cpu_baseline(w.docs.vecs, w.docs.offsets, w.queries.vecs[32 * s: 32 * (s + 1)],
+                            np.array([0, 32]), 1, cfg["k"])
         if s >= args.warmup:
             per_step.append(r)
     value = statistics.mean(r["value"] for r in per_step)
@@ -178,7 +299,7 @@ def run_gem(args, dist, rank, world, local):
     if rank:
         w.queries = synth.vector_sets(np.full(cfg["n_queries"], 32, np.int64), synth.centres(4096, seed),
                                       seed + 7919 + 104729 * rank, dev)
-    store = gem.Store(w.docs.vecs, w.docs.offsets, keep=("f32", "bf16"))
+    store = gem.Store(w.docs.vecs, w.docs.offsets, keep=("f32", "bf16", "fp8"))
     B = cfg["n_queries"]
     R, K = cfg["rerank"], cfg["k"]
     q = w.queries.vecs
@@ -193,6 +314,7 @@ def run_gem(args, dist, rank, world, local):
     pool_off = torch.arange(B + 1, dtype=torch.int64, device=dev) * R
     pool_sc = torch.empty(B * R, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
+    schedule = gem.autotune_score_all(store, ws, q, qo, "bf16", scores=scores)
 
     def step(ev=None):
         if ev:
@@ -261,11 +383,11 @@ def run_gem(args, dist, rank, world, local):
                                f"top-{R} -> FP32 rerank -> top-{K}",
                    "n_sets": store.n_sets, "n_vecs": V, "queries": B, "m_q": 32, "rerank": R, "k": K,
                    "l2": "inputs larger than L2 (bf16 store %.2f GB)" % (V * 256 / 1e9)},
-        "stages_ms": {"maxsim_bf16": k1_ms,
-                      "topk_rerank_topk": statistics.mean(e[1].elapsed_time(e[2]) for e in evs)},
+        "stages": {"maxsim_bf16_ms": k1_ms,
+                   "topk_rerank_topk_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in evs)},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "tc_score_all_kernel<2,false> (+ query packing)",
+                     "kernel": "tc_score_all_kernel<%d,false> (+ query packing)" % schedule["m_tiles"],
                      "peak_kind": f"{peak_kind} bf16 burst"},
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -273,11 +395,18 @@ def run_gem(args, dist, rank, world, local):
                 "h2d_bytes_per_step": int(qh.numel() * 4 + qoh.numel() * 8),
                 "d2h_bytes_per_step": int(oi.numel() * 8 + osc.numel() * 4)},
     }
+    line["config"]["schedule"] = schedule
+    truth = []
     if rank == 0 and not args.no_cpu_baseline:
-        n_cpu = 20_000
-        line["cpu_baseline"] = cpu_baseline(w.docs.vecs[: int(w.docs.offsets[n_cpu])].cpu(), w.docs.offsets,
-                                            w.queries.vecs.cpu(), w.queries.offsets, n_cpu,
-                                            args.cpu_budget, K)
+        docs_host = w.docs.vecs.cpu()
+        line["cpu_baseline"], truth = cpu_baseline(docs_host, w.docs.offsets, w.queries.vecs.cpu(),
+                                                   w.queries.offsets, args.cpu_queries, K)
+        del docs_host
+        line["recall_at_100"] = {"bf16_rerank": _recall(ids_a.cpu().numpy(), truth), "queries": len(truth),
+                                 "reference": "exact FP64 top-100 of the oracle over all sets"}
+    if rank == 0 and not args.no_extras:
+        stages = line["stages"]
+        extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, ms)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -289,8 +418,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gem", choices=["gem", "reference"])
     ap.add_argument("--workload", default="text", choices=list(WORKLOADS))
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-queries", type=int, default=4, help="queries the FP64 oracle scores (ground truth)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-row stage measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         # the oracle runs on host cores only: rank 0 times it, other ranks exit

@@ -318,6 +318,36 @@ gem_status gem_batch_status(gem_batch* batch);
 void gem_batch_destroy(gem_batch* batch);
 
 /*
+ * Autotuner.  Times the candidate schedules of a kernel with CUDA events on the
+ * given inputs and keeps the fastest; results never depend on the schedule
+ * (bit-identical scores).  cache_path (NULL: $GEM_TUNE_CACHE, unset: no cache)
+ * names a JSON file of earlier choices keyed by device name, dtype and size
+ * buckets; a hit applies the stored choice without timing (*from_cache = 1).
+ * Setup calls: they launch the kernels several times, may allocate, and
+ * synchronise `stream`.
+ *
+ * gem_autotune_score_all: schedules of gem_score_all for compute GEM_BF16 or
+ * GEM_FP8_E4M3 (m_tiles in {1, 2, 4} x chunk_rows in {2^14, 2^16, 2^18}); the
+ * choice is applied to `ws` (as gem_workspace_set_schedule).  scores float32
+ * [n_queries * n_sets] is scratch for the timing runs.
+ */
+gem_status gem_autotune_score_all(const gem_store* store, gem_workspace* ws, const float* q,
+                                  const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
+                                  int32_t compute, float* scores, const char* cache_path, int32_t* m_tiles,
+                                  int32_t* chunk_rows, float* ms, int32_t* from_cache, void* stream);
+
+/*
+ * gem_autotune_batch: schedules of a gem_batch (seg in {8, 16, 32, 64} x
+ * ctas_per_sm in {1, 2, all}) on one representative round held in the given
+ * device buffers (as for gem_batch_create); returns the fastest pair for
+ * gem_batch_create.
+ */
+gem_status gem_autotune_batch(const gem_store* store, int32_t mode, int32_t n_queries, int64_t n_q_rows,
+                              int32_t max_q_len, int64_t n_cands, float* q, int64_t* q_offsets,
+                              int64_t* cand_offsets, int64_t* cand_ids, float* scores, const char* cache_path,
+                              int32_t* seg, int32_t* ctas_per_sm, float* ms, int32_t* from_cache, void* stream);
+
+/*
  * gem_score_ids_noalloc: id-list scoring that allocates no device memory.  The
  * paper has no counterpart; this entry point exists for callers that cannot call
  * cudaMalloc: processes whose device memory is owned by another allocator (a host

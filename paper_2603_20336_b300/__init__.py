@@ -368,3 +368,35 @@ class MaxSimFn(torch.autograd.Function):
         q, docs, qo, do, po, pid, argmax = ctx.saved_tensors
         gq, gd = maxsim_bwd(q.detach().contiguous(), qo, docs.detach().contiguous(), do, po, pid, argmax, g)
         return gq, gd, None, None, None, None, None
+
+
+def autotune_score_all(store: Store, ws: Workspace, q, q_offsets, compute="bf16", scores=None, cache_path=None,
+                       stream=None):
+    """Pick and apply the fastest tensor-core schedule: dict(m_tiles, chunk_rows, ms, from_cache)."""
+    q, qo, B, rows = _queries(q, q_offsets)
+    if scores is None:
+        scores = torch.empty((B, store.n_sets), dtype=torch.float32, device=q.device)
+    mt, cr, fc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    ms = ctypes.c_float()
+    _check(lib.gem_autotune_score_all(store.handle, ws.handle, _ptr(q), _ptr(qo), B, rows, _dtype_code(compute),
+                                      _ptr(scores), cache_path.encode() if cache_path else None, ctypes.byref(mt),
+                                      ctypes.byref(cr), ctypes.byref(ms), ctypes.byref(fc), _stream(stream)))
+    return {"m_tiles": mt.value, "chunk_rows": cr.value, "ms": ms.value, "from_cache": bool(fc.value)}
+
+
+def autotune_batch(store: Store, q, q_offsets, cand_offsets, cand_ids, mode="f32", max_q_len=64, cache_path=None,
+                   stream=None):
+    """Fastest (seg, ctas_per_sm) of a Batch on one representative round."""
+    q = _dev(q.contiguous(), torch.float32, "q")
+    qo = _dev(q_offsets, torch.int64, "q_offsets")
+    co = _dev(cand_offsets, torch.int64, "cand_offsets")
+    ci = _dev(cand_ids, torch.int64, "cand_ids")
+    scores = torch.empty(ci.numel(), dtype=torch.float32, device=q.device)
+    sg, ct, fc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    ms = ctypes.c_float()
+    m = {"f32": 0, "codes": 3}[mode] if isinstance(mode, str) else int(mode)
+    _check(lib.gem_autotune_batch(store.handle, m, qo.numel() - 1, q.shape[0], max_q_len, ci.numel(), _ptr(q),
+                                  _ptr(qo), _ptr(co), _ptr(ci), _ptr(scores),
+                                  cache_path.encode() if cache_path else None, ctypes.byref(sg), ctypes.byref(ct),
+                                  ctypes.byref(ms), ctypes.byref(fc), _stream(stream)))
+    return {"seg": sg.value, "ctas_per_sm": ct.value, "ms": ms.value, "from_cache": bool(fc.value)}

@@ -683,6 +683,42 @@ gem_status gem_batch_status(gem_batch* b) {
 
 void gem_batch_destroy(gem_batch* b) { batch_destroy(b); }
 
+gem_status gem_autotune_score_all(const gem_store* s, gem_workspace* w, const float* q,
+                                  const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
+                                  int32_t compute, float* scores, const char* cache_path, int32_t* m_tiles,
+                                  int32_t* chunk_rows, float* ms, int32_t* from_cache, void* stream) {
+  gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
+  if (r != GEM_OK) return r;
+  if (!scores || !m_tiles || !chunk_rows || !ms || !from_cache) return fail(GEM_ERR_INVALID, "NULL argument");
+  if (compute == GEM_BF16 && !s->d_bf16) return fail(GEM_ERR_STATE, "store keeps no bf16 copy");
+  if (compute == GEM_FP8_E4M3 && !s->d_fp8) return fail(GEM_ERR_STATE, "store keeps no fp8 copy");
+  if (compute != GEM_BF16 && compute != GEM_FP8_E4M3) return fail(GEM_ERR_INVALID, "compute must be bf16 or fp8");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  r = autotune_score_all(s, w, q, q_offsets, n_queries, n_q_rows, compute, scores, cache_path, m_tiles, chunk_rows,
+                         ms, from_cache, st);
+  if (r == GEM_OK) GEM_CUDA_TRY(cudaStreamSynchronize(st));
+  return r;
+}
+
+gem_status gem_autotune_batch(const gem_store* s, int32_t mode, int32_t n_queries, int64_t n_q_rows,
+                              int32_t max_q_len, int64_t n_cands, float* q, int64_t* q_offsets,
+                              int64_t* cand_offsets, int64_t* cand_ids, float* scores, const char* cache_path,
+                              int32_t* seg, int32_t* ctas_per_sm, float* ms, int32_t* from_cache, void* stream) {
+  if (!s || !q || !q_offsets || !cand_offsets || !cand_ids || !scores || !seg || !ctas_per_sm || !ms || !from_cache)
+    return fail(GEM_ERR_INVALID, "NULL argument");
+  if (mode != GEM_F32 && mode != GEM_CODES) return fail(GEM_ERR_INVALID, "mode must be GEM_F32 or GEM_CODES");
+  if (!s->d_f32 || (mode == GEM_CODES && s->k1 == 0)) return fail(GEM_ERR_STATE, "store lacks fp32 copy or codebook");
+  if (n_queries < 1 || n_q_rows < n_queries || n_cands < 1) return fail(GEM_ERR_INVALID, "bad sizes");
+  if (max_q_len < 1 || max_q_len > 32 * kMaxPasses) return fail(GEM_ERR_INVALID, "max_q_len must be 1..256");
+  gem_status r = check_current_device(s->device);
+  if (r != GEM_OK) return r;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  r = autotune_batch(s, mode, n_queries, n_q_rows, max_q_len, n_cands, q, q_offsets, cand_offsets, cand_ids, scores,
+                     cache_path, seg, ctas_per_sm, ms, from_cache, st);
+  if (r == GEM_OK) GEM_CUDA_TRY(cudaStreamSynchronize(st));
+  return r;
+}
+
 gem_status gem_score_ids_noalloc(const gem_store* s, const float* q, const int64_t* q_offsets,
                                  int32_t n_queries, int64_t n_q_rows, int32_t max_q_len,
                                  const int64_t* cand_offsets, const int64_t* cand_ids, int64_t n_cands,

@@ -1,0 +1,244 @@
+// Autotuner: times candidate schedules of the scoring kernels with CUDA events
+// and keeps the fastest.  Schedules change only the launch shape (resident query
+// rows, tile width, chunking, work-item size, CTAs per SM), never the arithmetic,
+// so every candidate produces bit-identical scores.
+//
+// Results are cached in a small JSON file (path argument, else $GEM_TUNE_CACHE,
+// else no cache) keyed by a workload signature:
+//   {"entries": {"<signature>": {"a": <int>, "b": <int>, "ms": <float>}, ...}}
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace gem {
+namespace {
+
+struct Entry {
+  int a = 0, b = 0;
+  double ms = 0.0;
+};
+
+std::mutex g_cache_mu;
+
+// Minimal reader for the cache format above (the file is written only here).
+std::map<std::string, Entry> read_cache(const std::string& path) {
+  std::map<std::string, Entry> out;
+  std::ifstream f(path);
+  if (!f) return out;
+  std::stringstream ss;
+  ss << f.rdbuf();
+  const std::string s = ss.str();
+  size_t pos = s.find("\"entries\"");
+  if (pos == std::string::npos) return out;
+  pos = s.find('{', pos);
+  while (pos != std::string::npos) {
+    const size_t k0 = s.find('"', pos + 1);
+    if (k0 == std::string::npos) break;
+    const size_t k1 = s.find('"', k0 + 1);
+    if (k1 == std::string::npos) break;
+    const std::string key = s.substr(k0 + 1, k1 - k0 - 1);
+    const size_t o0 = s.find('{', k1);
+    const size_t o1 = s.find('}', o0);
+    if (o0 == std::string::npos || o1 == std::string::npos) break;
+    const std::string obj = s.substr(o0, o1 - o0 + 1);
+    Entry e;
+    auto num = [&](const char* name, double& v) {
+      const size_t p = obj.find(std::string("\"") + name + "\"");
+      if (p == std::string::npos) return false;
+      const size_t c = obj.find(':', p);
+      v = std::strtod(obj.c_str() + c + 1, nullptr);
+      return true;
+    };
+    double a = 0, b = 0, ms = 0;
+    if (num("a", a) && num("b", b) && num("ms", ms)) {
+      e.a = (int)a;
+      e.b = (int)b;
+      e.ms = ms;
+      out[key] = e;
+    }
+    pos = s.find(',', o1);
+    if (pos == std::string::npos || s.find('"', pos) == std::string::npos) break;
+  }
+  return out;
+}
+
+void write_cache(const std::string& path, const std::map<std::string, Entry>& m) {
+  const std::string tmp = path + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "{\"entries\": {");
+  bool first = true;
+  for (const auto& kv : m) {
+    std::fprintf(f, "%s\n  \"%s\": {\"a\": %d, \"b\": %d, \"ms\": %.4f}", first ? "" : ",", kv.first.c_str(),
+                 kv.second.a, kv.second.b, kv.second.ms);
+    first = false;
+  }
+  std::fprintf(f, "\n}}\n");
+  std::fclose(f);
+  std::rename(tmp.c_str(), path.c_str());
+}
+
+std::string cache_path(const char* p) {
+  if (p && *p) return p;
+  const char* e = std::getenv("GEM_TUNE_CACHE");
+  return e ? e : "";
+}
+
+std::string device_name(int dev) {
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+  std::string n = p.name;
+  for (char& c : n)
+    if (c == '"' || c == '\\') c = '_';
+  return n;
+}
+
+// Rounds up to a power of two so that nearby sizes share a cache entry.
+int64_t bucket(int64_t x) {
+  int64_t b = 1;
+  while (b < x) b <<= 1;
+  return b;
+}
+
+template <typename F>
+gem_status time_ms(F&& run, cudaStream_t st, int reps, double* ms) {
+  cudaEvent_t e0, e1;
+  GEM_CUDA_TRY(cudaEventCreate(&e0));
+  GEM_CUDA_TRY(cudaEventCreate(&e1));
+  gem_status r = run();  // warm-up (also builds lazily cached maps)
+  if (r == GEM_OK) {
+    cudaEventRecord(e0, st);
+    for (int i = 0; i < reps && r == GEM_OK; ++i) r = run();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    *ms = t / reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return r;
+}
+
+}  // namespace
+
+gem_status autotune_score_all(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
+                              int32_t n_queries, int64_t n_q_rows, int32_t compute, float* scores,
+                              const char* cache_file, int32_t* m_tiles, int32_t* chunk_rows, float* ms_out,
+                              int32_t* from_cache, cudaStream_t st) {
+  const std::string path = cache_path(cache_file);
+  std::ostringstream key;
+  key << "score_all|" << device_name(s->device) << "|dtype" << compute << "|vecs" << bucket(s->n_pad_vecs)
+      << "|sets" << bucket(s->n_sets) << "|qrows" << bucket(n_q_rows) << "|qlen" << w->max_q_len;
+  if (!path.empty()) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto m = read_cache(path);
+    auto it = m.find(key.str());
+    if (it != m.end()) {
+      w->tc_m_tiles = it->second.a;
+      w->tc_chunk_rows = it->second.b;
+      *m_tiles = it->second.a;
+      *chunk_rows = it->second.b;
+      *ms_out = (float)it->second.ms;
+      *from_cache = 1;
+      return GEM_OK;
+    }
+  }
+  const int mts[] = {2, 4, 1};
+  const int crs[] = {1 << 14, 1 << 16, 1 << 18};
+  double best = 1e30;
+  int bm = 2, bc = 1 << 16;
+  // repetitions sized so each candidate runs about a tenth of a second
+  int reps = 1;
+  for (int mt : mts) {
+    for (int cr : crs) {
+      w->tc_m_tiles = mt;
+      w->tc_chunk_rows = cr;
+      double ms = 0.0;
+      gem_status r = time_ms(
+          [&]() {
+            gem_status rr = launch_plan(w, q, q_offsets, n_queries, n_q_rows, 128 * mt, compute, st);
+            if (rr == GEM_OK) rr = launch_tc_score_all(s, w, compute, mt, cr, scores, st);
+            return rr;
+          },
+          st, reps, &ms);
+      if (r != GEM_OK) return r;
+      if (ms < best) { best = ms; bm = mt; bc = cr; }
+      if (reps == 1) reps = std::max(1, std::min(10, (int)(100.0 / std::max(ms, 1e-3))));
+    }
+  }
+  w->tc_m_tiles = bm;
+  w->tc_chunk_rows = bc;
+  *m_tiles = bm;
+  *chunk_rows = bc;
+  *ms_out = (float)best;
+  *from_cache = 0;
+  if (!path.empty()) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto m = read_cache(path);
+    m[key.str()] = Entry{bm, bc, best};
+    write_cache(path, m);
+  }
+  return GEM_OK;
+}
+
+gem_status autotune_batch(const gem_store* s, int32_t mode, int32_t n_queries, int64_t n_q_rows, int32_t max_q_len,
+                          int64_t n_cands, float* q, int64_t* q_offsets, int64_t* cand_offsets, int64_t* cand_ids,
+                          float* scores, const char* cache_file, int32_t* seg, int32_t* ctas_per_sm, float* ms_out,
+                          int32_t* from_cache, cudaStream_t st) {
+  const std::string path = cache_path(cache_file);
+  std::ostringstream key;
+  key << "batch|" << device_name(s->device) << "|mode" << mode << "|sets" << bucket(s->n_sets) << "|queries"
+      << bucket(n_queries) << "|cands" << bucket(n_cands) << "|qlen" << max_q_len;
+  if (!path.empty()) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto m = read_cache(path);
+    auto it = m.find(key.str());
+    if (it != m.end()) {
+      *seg = it->second.a;
+      *ctas_per_sm = it->second.b;
+      *ms_out = (float)it->second.ms;
+      *from_cache = 1;
+      return GEM_OK;
+    }
+  }
+  const int segs[] = {8, 16, 32, 64};
+  const int ctas[] = {1, 2, 0};
+  double best = 1e30;
+  int bs = 32, bc = 0;
+  for (int sg : segs) {
+    for (int c : ctas) {
+      gem_batch* bt = nullptr;
+      gem_status r = batch_create(s, mode, n_queries, n_q_rows, max_q_len, n_cands, sg, c, q, q_offsets,
+                                  cand_offsets, cand_ids, scores, &bt);
+      if (r != GEM_OK) return r;
+      double ms = 0.0;
+      r = time_ms([&]() { return batch_run(bt, n_queries, n_q_rows, n_cands, 1, st); }, st, 3, &ms);
+      batch_destroy(bt);
+      if (r != GEM_OK) return r;
+      if (ms < best) { best = ms; bs = sg; bc = c; }
+    }
+  }
+  *seg = bs;
+  *ctas_per_sm = bc;
+  *ms_out = (float)best;
+  *from_cache = 0;
+  if (!path.empty()) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto m = read_cache(path);
+    m[key.str()] = Entry{bs, bc, best};
+    write_cache(path, m);
+  }
+  return GEM_OK;
+}
+
+}  // namespace gem

@@ -220,6 +220,14 @@ gem_status batch_create(const gem_store* s, int32_t mode, int32_t max_queries, i
 gem_status batch_run(gem_batch* bt, int32_t n_queries, int64_t n_q_rows, int64_t n_cands, int use_graph,
                      cudaStream_t st);
 void batch_destroy(gem_batch* bt);
+gem_status autotune_score_all(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
+                              int32_t n_queries, int64_t n_q_rows, int32_t compute, float* scores,
+                              const char* cache_file, int32_t* m_tiles, int32_t* chunk_rows, float* ms_out,
+                              int32_t* from_cache, cudaStream_t st);
+gem_status autotune_batch(const gem_store* s, int32_t mode, int32_t n_queries, int64_t n_q_rows, int32_t max_q_len,
+                          int64_t n_cands, float* q, int64_t* q_offsets, int64_t* cand_offsets, int64_t* cand_ids,
+                          float* scores, const char* cache_file, int32_t* seg, int32_t* ctas_per_sm, float* ms_out,
+                          int32_t* from_cache, cudaStream_t st);
 gem_status score_ids_noalloc(const gem_store* s, const float* q, const int64_t* q_offsets, int32_t n_queries,
                              int64_t n_q_rows, int32_t max_q_len, const int64_t* cand_offsets,
                              const int64_t* cand_ids, int64_t n_cands, float* scores, cudaStream_t st);

@@ -113,24 +113,27 @@ def candidate_lists(n_queries: int, n_docs: int, len_lo: int, len_hi: int, share
     lens = rng.integers(len_lo, len_hi + 1, size=n_queries)
     lists = []
     for L in lens:
-        n_sh = int(round(shared_frac * L))
-        sh = rng.choice(pool, size=min(n_sh, len(pool)), replace=False)
-        rest = set(sh.tolist())
-        need = int(L) - len(sh)
-        extra = []
-        while len(extra) < need:
-            cand = rng.integers(0, n_docs, size=2 * (need - len(extra)) + 8)
-            for c in cand.tolist():
-                if c not in rest:
-                    rest.add(c)
-                    extra.append(c)
-                    if len(extra) == need:
-                        break
-        ids = np.concatenate([sh, np.asarray(extra, dtype=np.int64)])
+        n_sh = min(int(round(shared_frac * L)), len(pool))
+        sh = rng.choice(pool, size=n_sh, replace=False)
+        need = int(L) - n_sh
+        rest = np.zeros(0, np.int64)
+        while len(rest) < need:
+            cand = np.unique(rng.integers(0, n_docs, size=2 * need + 8))
+            cand = cand[~np.isin(cand, sh)]
+            rest = np.unique(np.concatenate([rest, cand]))
+        rest = rng.permutation(rest)[:need]
+        ids = np.concatenate([sh, rest]).astype(np.int64)
         rng.shuffle(ids)
-        lists.append(ids.astype(np.int64))
+        lists.append(ids)
     off = _offsets(np.asarray([len(x) for x in lists], dtype=np.int64))
     return off, (np.concatenate(lists) if lists else np.zeros(0, np.int64))
+
+
+def shift_lists(cand_ids: np.ndarray, rnd: int, n_docs: int, step: int = 7919) -> np.ndarray:
+    """Candidate ids of a later round: (id + rnd * step) mod n_docs.  The map is a
+    bijection, so lengths, the shared pool structure and the absence of duplicates
+    inside a list carry over unchanged."""
+    return ((cand_ids + rnd * step) % n_docs).astype(np.int64)
 
 
 # ---------------------------------------------------------------------------

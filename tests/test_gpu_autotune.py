@@ -1,0 +1,59 @@
+"""Autotuner: the chosen schedule is one of the candidates, results do not
+depend on it (bit-identical scores), and the JSON cache is written and hit."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gem():
+    import paper_2603_20336_b300 as g
+    return g
+
+
+def test_autotune_score_all_bit_identical_and_cached(gem, tmp_path):
+    w = synth.exact_fp32(n_sets=3000, n_queries=40)
+    store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("bf16", "fp8"))
+    ws = gem.Workspace(store, max_queries=64, max_q_rows=64 * 32, max_q_len=32)
+    q, qo = w.queries.vecs.cuda(), torch.from_numpy(w.queries.offsets).cuda()
+    cache = str(tmp_path / "tune.json")
+    for compute in ("bf16", "fp8"):
+        gem.set_schedule(ws, 2, 1 << 16)
+        ref = gem.score_all(store, ws, q, qo, compute).clone()
+        ch = gem.autotune_score_all(store, ws, q, qo, compute, cache_path=cache)
+        assert ch["m_tiles"] in (1, 2, 4) and ch["chunk_rows"] in (1 << 14, 1 << 16, 1 << 18)
+        assert not ch["from_cache"] and ch["ms"] > 0
+        assert torch.equal(gem.score_all(store, ws, q, qo, compute), ref)
+        again = gem.autotune_score_all(store, ws, q, qo, compute, cache_path=cache)
+        assert again["from_cache"] and again["m_tiles"] == ch["m_tiles"]
+    entries = json.load(open(cache))["entries"]
+    assert len(entries) == 2 and all(k.startswith("score_all|") for k in entries)
+
+
+def test_autotune_batch_choice_bit_matches(gem, tmp_path):
+    seed = 1238
+    cents = synth.centres(128, seed)
+    docs = synth.vector_sets(synth.lengths_lognormal(800, 70.0, 0.5, 20, 180, seed), cents, seed)
+    store = gem.Store(docs.vecs.cuda(), docs.offsets, keep=("f32",))
+    qs, co, ci = synth.beam_batch(docs, cents, seed=seed, n_queries=64, len_lo=16, len_hi=64, pool_size=50)
+    args = (qs.vecs.cuda(), torch.from_numpy(qs.offsets).cuda(), torch.from_numpy(co).cuda(),
+            torch.from_numpy(ci).cuda())
+    ch = gem.autotune_batch(store, *args, mode="f32", max_q_len=64, cache_path=str(tmp_path / "b.json"))
+    assert ch["seg"] in (8, 16, 32, 64) and ch["ctas_per_sm"] in (0, 1, 2)
+    outs = []
+    for seg, ctas in ((ch["seg"], ch["ctas_per_sm"]), (8, 1)):
+        bt = gem.Batch(store, "f32", max_queries=64, max_q_rows=64 * 64, max_q_len=64, max_cands=64 * 64,
+                       seg=seg, ctas_per_sm=ctas)
+        outs.append(bt.run(*args).clone())
+        assert bt.status() == 0
+        bt.close()
+    assert torch.equal(outs[0], outs[1])
+    assert gem.autotune_batch(store, *args, mode="f32", max_q_len=64,
+                              cache_path=str(tmp_path / "b.json"))["from_cache"]
