@@ -101,7 +101,7 @@ struct BatchArgs {
   int* status;
 };
 
-__global__ void __launch_bounds__(kBatchWarps * 32) batch_score_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kBatchWarps * 32, 2) batch_score_kernel(BatchArgs a) {
   extern __shared__ float sm[];
   float* qs = sm;
   float* stage_all = qs + a.max_q_len * kQStride;
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32) batch_score_kernel(BatchArgs
       } else {
         const int64_t r0 = a.doc_off[id];
         const int m_p = (int)(a.doc_off[id + 1] - r0);
-        score = warp_chamfer(qs, m_q, a.docs + r0 * kDim, a.codes ? a.codes + r0 : nullptr, a.centroids,
+        score = warp_chamfer(qs, kQStride, m_q, a.docs + r0 * kDim, a.codes ? a.codes + r0 : nullptr, a.centroids,
                              m_p, stage, rowmax, qr, loaded_rg);
       }
       if (lane == 0) a.scores[t] = score;

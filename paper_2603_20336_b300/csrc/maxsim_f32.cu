@@ -31,8 +31,10 @@ struct F32Args {
   const int32_t* qcodes;
 };
 
-__global__ void __launch_bounds__(kF32Threads)
-f32_score_kernel(F32Args a, int max_q_len) {
+// All sets: one CTA per (segment of kSegDocs sets, query), the query staged in
+// shared memory; consecutive CTAs share a segment, so its sets stay in L2.
+__global__ void __launch_bounds__(kF32Threads, 2)
+f32_all_kernel(F32Args a, int max_q_len) {
   extern __shared__ float sm[];
   float* qs = sm;                                              // [max_q_len * kQStride]
   float* stage_all = qs + max_q_len * kQStride;                // [warps][kVecBlock * 128]
@@ -41,52 +43,84 @@ f32_score_kernel(F32Args a, int max_q_len) {
   float* stage = stage_all + warp * kVecBlock * kDim;
   float* rowmax = rowmax_all + warp * max_q_len;
   float qr[kDim];
-
-  const bool all_sets = (a.cand_ids == nullptr);
-  const int64_t n_seg = all_sets ? (a.n_sets + kSegDocs - 1) / kSegDocs : 1;
-  const int64_t n_units = all_sets ? n_seg * a.n_queries : a.n_queries;
-
+  const int64_t n_seg = (a.n_sets + kSegDocs - 1) / kSegDocs;
+  const int64_t n_units = n_seg * a.n_queries;
   for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
-    const int b = (int)(all_sets ? (u % a.n_queries) : u);
+    const int b = (int)(u % a.n_queries);
     const int64_t q0 = a.q_off[b];
     const int m_q = (int)(a.q_off[b + 1] - q0);
     __syncthreads();
     for (int idx = threadIdx.x; idx < m_q * (kDim / 4); idx += blockDim.x) {
       const int i = idx / (kDim / 4), k4 = idx % (kDim / 4);
       const float* src = a.qcodes ? a.centroids + (int64_t)a.qcodes[q0 + i] * kDim : a.q + (q0 + i) * kDim;
-      float4 x = reinterpret_cast<const float4*>(src)[k4];
-      reinterpret_cast<float4*>(qs + i * kQStride)[k4] = x;
+      reinterpret_cast<float4*>(qs + i * kQStride)[k4] = reinterpret_cast<const float4*>(src)[k4];
     }
     __syncthreads();
     int loaded_rg = -1;
-    int64_t t0, t1;
-    if (all_sets) {
-      const int64_t seg = u / a.n_queries;
-      t0 = seg * kSegDocs;
-      t1 = min(a.n_sets, t0 + kSegDocs);
-    } else {
-      t0 = a.cand_off[b];
-      t1 = a.cand_off[b + 1];
-    }
+    const int64_t t0 = (u / a.n_queries) * kSegDocs;
+    const int64_t t1 = min(a.n_sets, t0 + kSegDocs);
     for (int64_t t = t0 + warp; t < t1; t += kF32Warps) {
-      const int64_t id = all_sets ? t : a.cand_ids[t];
-      float score;
-      if (id < 0) {
-        score = -INFINITY;
-      } else if (id >= a.n_sets) {
-        if (lane == 0) set_status(a.status, kDevBounds);
-        score = __int_as_float(0x7fc00000);
+      const int64_t r0 = a.doc_off[t];
+      const int m_p = (int)(a.doc_off[t + 1] - r0);
+      const float score = warp_chamfer(qs, kQStride, m_q, a.docs + r0 * kDim, a.qcodes ? a.codes + r0 : nullptr,
+                                       a.centroids, m_p, stage, rowmax, qr, loaded_rg);
+      if (lane == 0) a.scores[(int64_t)b * a.n_sets + t] = score;
+    }
+  }
+}
+
+// Id lists: every warp takes one contiguous range of the n_cands candidates
+// (equal shares, whatever the list lengths) and reads the rows of the current
+// query straight into registers when the query changes.
+template <bool Coded>
+__global__ void __launch_bounds__(kF32Threads, 2)
+f32_ids_kernel(F32Args a, int max_q_len, int64_t n_cands) {
+  extern __shared__ float sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* stage = sm + warp * kVecBlock * kDim;
+  float* rowmax = sm + kF32Warps * kVecBlock * kDim + warp * max_q_len;
+  float qr[kDim];
+  const int64_t n_warps = (int64_t)gridDim.x * kF32Warps;
+  const int64_t chunk = (n_cands + n_warps - 1) / n_warps;
+  const int64_t t_begin = min(n_cands, ((int64_t)blockIdx.x * kF32Warps + warp) * chunk);
+  const int64_t t_end = min(n_cands, t_begin + chunk);
+  if (t_begin >= t_end) return;
+  int lo = 0, hi = a.n_queries - 1;  // query owning t_begin
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.cand_off[mid] <= t_begin) lo = mid; else hi = mid - 1;
+  }
+  int b = lo;
+  int64_t b_end = a.cand_off[b + 1];
+  int loaded_rg = -1;
+  for (int64_t t = t_begin; t < t_end; ++t) {
+    while (t >= b_end) {
+      ++b;
+      b_end = a.cand_off[b + 1];
+      loaded_rg = -1;
+    }
+    const int64_t q0 = a.q_off[b];
+    const int m_q = (int)(a.q_off[b + 1] - q0);
+    const int64_t id = a.cand_ids[t];
+    float score;
+    if (id < 0) {
+      score = -INFINITY;
+    } else if (id >= a.n_sets || m_q > max_q_len) {
+      if (lane == 0) set_status(a.status, id >= a.n_sets ? kDevBounds : kDevInvalid);
+      score = __int_as_float(0x7fc00000);
+    } else {
+      const int64_t r0 = a.doc_off[id];
+      const int m_p = (int)(a.doc_off[id + 1] - r0);
+      if constexpr (Coded) {
+        // codes form: query rows are centroids of the query codes
+        score = warp_chamfer_coded_q(a.centroids, a.qcodes + q0, m_q, a.docs + r0 * kDim, a.codes + r0, m_p,
+                                     stage, rowmax, qr, loaded_rg);
       } else {
-        const int64_t r0 = a.doc_off[id];
-        const int m_p = (int)(a.doc_off[id + 1] - r0);
-        score = warp_chamfer(qs, m_q, a.docs + r0 * kDim, a.qcodes ? a.codes + r0 : nullptr, a.centroids, m_p,
-                             stage, rowmax, qr, loaded_rg);
-      }
-      if (lane == 0) {
-        if (all_sets) a.scores[(int64_t)b * a.n_sets + t] = score;
-        else a.scores[t] = score;
+        score = warp_chamfer(a.q + q0 * kDim, kDim, m_q, a.docs + r0 * kDim, nullptr, nullptr, m_p, stage, rowmax,
+                             qr, loaded_rg);
       }
     }
+    if (lane == 0) a.scores[t] = score;
   }
 }
 
@@ -96,7 +130,6 @@ gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* 
                             const int64_t* q_offsets, int32_t n_queries, const int64_t* cand_offsets,
                             const int64_t* cand_ids, int64_t n_cands, float* scores, cudaStream_t st,
                             const int32_t* qcodes) {
-  (void)n_cands;
   F32Args a;
   a.q = q;
   a.q_off = q_offsets;
@@ -112,18 +145,25 @@ gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* 
   a.centroids = s->d_codebook;
   a.qcodes = qcodes;
   const int mq = ws->max_q_len;
-  const size_t smem = sizeof(float) * ((size_t)mq * kQStride + kF32Warps * kVecBlock * kDim +
-                                       (size_t)kF32Warps * mq);
-  GEM_CUDA_TRY(cudaFuncSetAttribute(f32_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
   int per_sm = 0;
-  GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32_score_kernel, kF32Threads,
-                                                             smem));
-  if (per_sm < 1) return fail(GEM_ERR_UNSUPPORTED, "f32 scoring kernel does not fit on an SM");
-  int64_t units = cand_ids ? n_queries : ((s->n_sets + kSegDocs - 1) / kSegDocs) * n_queries;
-  int grid = (int)std::min<int64_t>(units, (int64_t)s->n_sm * per_sm);
-  if (grid < 1) return GEM_OK;
-  f32_score_kernel<<<grid, kF32Threads, smem, st>>>(a, mq);
+  if (cand_ids == nullptr) {
+    const size_t smem = sizeof(float) * ((size_t)mq * kQStride + kF32Warps * kVecBlock * kDim + (size_t)kF32Warps * mq);
+    GEM_CUDA_TRY(cudaFuncSetAttribute(f32_all_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32_all_kernel, kF32Threads, smem));
+    if (per_sm < 1) return fail(GEM_ERR_UNSUPPORTED, "f32 scoring kernel does not fit on an SM");
+    const int64_t units = ((s->n_sets + kSegDocs - 1) / kSegDocs) * n_queries;
+    const int grid = (int)std::min<int64_t>(units, (int64_t)s->n_sm * per_sm);
+    f32_all_kernel<<<grid, kF32Threads, smem, st>>>(a, mq);
+  } else {
+    const size_t smem = sizeof(float) * (kF32Warps * kVecBlock * kDim + (size_t)kF32Warps * mq);
+    auto kern = qcodes ? f32_ids_kernel<true> : f32_ids_kernel<false>;
+    GEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kF32Threads, smem));
+    if (per_sm < 1) return fail(GEM_ERR_UNSUPPORTED, "f32 scoring kernel does not fit on an SM");
+    const int64_t max_grid = (n_cands + kF32Warps - 1) / kF32Warps;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(max_grid, (int64_t)s->n_sm * per_sm));
+    kern<<<grid, kF32Threads, smem, st>>>(a, mq, n_cands);
+  }
   GEM_CUDA_TRY(cudaGetLastError());
   note_launches(1);
   return GEM_OK;
