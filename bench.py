@@ -100,11 +100,18 @@ def _dist():
 
 
 def _max_over_ranks(dist, x: float) -> float:
+    """The slowest rank's time: the job's time."""
     if dist is None:
         return x
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_query_seed(seed: int, rank: int) -> int:
+    """Seed of the query sets a rank scores (rank 0 keeps the workload's own)."""
+    return seed + 7919 + 104729 * rank
 
 
 def _barrier(dist):
@@ -298,7 +305,7 @@ def run_gem(args, dist, rank, world, local):
     # each rank scores its own queries (weak scaling)
     if rank:
         w.queries = synth.vector_sets(np.full(cfg["n_queries"], 32, np.int64), synth.centres(4096, seed),
-                                      seed + 7919 + 104729 * rank, dev)
+                                      rank_query_seed(seed, rank), dev)
     store = gem.Store(w.docs.vecs, w.docs.offsets, keep=("f32", "bf16", "fp8"))
     B = cfg["n_queries"]
     R, K = cfg["rerank"], cfg["k"]
