@@ -105,10 +105,10 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 2) batch_score_kernel(BatchA
   extern __shared__ float sm[];
   float* qs = sm;
   float* stage_all = qs + a.max_q_len * kQStride;
-  float* rowmax_all = stage_all + kBatchWarps * kVecBlock * kDim;
+  float* rowmax_all = stage_all + kBatchWarps * kVecBlock * kStageStride;
   __shared__ long long s_item;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* stage = stage_all + warp * kVecBlock * kDim;
+  float* stage = stage_all + warp * kVecBlock * kStageStride;
   float* rowmax = rowmax_all + warp * a.max_q_len;
   float qr[kDim];
   const int B = (int)a.hdr[0];
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 2) batch_score_kernel(BatchA
 }
 
 size_t batch_smem(int max_q_len) {
-  return sizeof(float) * ((size_t)max_q_len * kQStride + kBatchWarps * kVecBlock * kDim +
+  return sizeof(float) * ((size_t)max_q_len * kQStride + kBatchWarps * kVecBlock * kStageStride +
                           (size_t)kBatchWarps * max_q_len);
 }
 

@@ -38,9 +38,9 @@ f32_all_kernel(F32Args a, int max_q_len) {
   extern __shared__ float sm[];
   float* qs = sm;                                              // [max_q_len * kQStride]
   float* stage_all = qs + max_q_len * kQStride;                // [warps][kVecBlock * 128]
-  float* rowmax_all = stage_all + kF32Warps * kVecBlock * kDim;  // [warps][max_q_len]
+  float* rowmax_all = stage_all + kF32Warps * kVecBlock * kStageStride;  // [warps][max_q_len]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* stage = stage_all + warp * kVecBlock * kDim;
+  float* stage = stage_all + warp * kVecBlock * kStageStride;
   float* rowmax = rowmax_all + warp * max_q_len;
   float qr[kDim];
   const int64_t n_seg = (a.n_sets + kSegDocs - 1) / kSegDocs;
@@ -77,8 +77,8 @@ __global__ void __launch_bounds__(kF32Threads, 2)
 f32_ids_kernel(F32Args a, int max_q_len, int64_t n_cands) {
   extern __shared__ float sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* stage = sm + warp * kVecBlock * kDim;
-  float* rowmax = sm + kF32Warps * kVecBlock * kDim + warp * max_q_len;
+  float* stage = sm + warp * kVecBlock * kStageStride;
+  float* rowmax = sm + kF32Warps * kVecBlock * kStageStride + warp * max_q_len;
   float qr[kDim];
   const int64_t n_warps = (int64_t)gridDim.x * kF32Warps;
   const int64_t chunk = (n_cands + n_warps - 1) / n_warps;
@@ -147,7 +147,7 @@ gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* 
   const int mq = ws->max_q_len;
   int per_sm = 0;
   if (cand_ids == nullptr) {
-    const size_t smem = sizeof(float) * ((size_t)mq * kQStride + kF32Warps * kVecBlock * kDim + (size_t)kF32Warps * mq);
+    const size_t smem = sizeof(float) * ((size_t)mq * kQStride + kF32Warps * kVecBlock * kStageStride + (size_t)kF32Warps * mq);
     GEM_CUDA_TRY(cudaFuncSetAttribute(f32_all_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32_all_kernel, kF32Threads, smem));
     if (per_sm < 1) return fail(GEM_ERR_UNSUPPORTED, "f32 scoring kernel does not fit on an SM");
@@ -155,7 +155,7 @@ gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* 
     const int grid = (int)std::min<int64_t>(units, (int64_t)s->n_sm * per_sm);
     f32_all_kernel<<<grid, kF32Threads, smem, st>>>(a, mq);
   } else {
-    const size_t smem = sizeof(float) * (kF32Warps * kVecBlock * kDim + (size_t)kF32Warps * mq);
+    const size_t smem = sizeof(float) * (kF32Warps * kVecBlock * kStageStride + (size_t)kF32Warps * mq);
     auto kern = qcodes ? f32_ids_kernel<true> : f32_ids_kernel<false>;
     GEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kF32Threads, smem));

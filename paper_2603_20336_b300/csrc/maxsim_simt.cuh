@@ -2,22 +2,28 @@
 // all of them produce bit-identical scores for the same (query, set) pair.
 //
 // Arithmetic order (fixed, independent of launch shape):
-//   dot(q_i, p_j): one FP32 fused multiply-add chain over k = 0 .. 127
+//   dot(q_i, p_j) = c0 + c1, where c0 and c1 are FP32 fused multiply-add chains
+//                   over k = 0 .. 63 and k = 64 .. 127 (each in ascending k)
 //   m_i = max_j dot(q_i, p_j)
 //   CH  = Kahan (compensated) sum of m_i over i = 0 .. m_q - 1 in ascending order
 //
-// Mapping: lane = query row (32 rows per pass, the row's 128 components held in
-// registers); the set's vectors are staged 8 at a time in the warp's shared
-// slice and read as broadcasts.  In the codes form every stored vector p_j is
-// replaced by its centroid C[code_j] (the caller stages centroids of the query
-// codes as the query rows), which gives the quantized estimate in similarity form.
+// Mapping: lane l holds query rows 2(l/2) and 2(l/2)+1 of the current 32-row
+// group, components k in [64 (l%2), 64 (l%2) + 64), in registers; the set's
+// vectors are staged 8 at a time in the warp's shared slice (the upper half of a
+// staged vector is shifted by 16 bytes so both half-warps' broadcast reads fall
+// in different banks), so one 16-byte shared load feeds 8 FMAs.  The two
+// half-chains of a dot meet through one xor shuffle.  In the codes form every
+// stored vector p_j is replaced by its centroid C[code_j] and the query rows by
+// the centroids of the query codes, which gives the quantized estimate in
+// similarity form.
 #pragma once
 #include "internal.h"
 
 namespace gem {
 
-constexpr int kVecBlock = 8;        // set vectors staged per step
-constexpr int kQStride = kDim + 4;  // padded query row stride in shared memory (floats)
+constexpr int kVecBlock = 8;         // set vectors staged per step
+constexpr int kQStride = kDim + 4;   // padded query row stride in shared memory (floats)
+constexpr int kStageStride = kDim + 4;  // staged set vector: [k 0..63][4 pad][k 64..127]
 
 // One row of the set (or its centroid in the codes form) as this lane's float4.
 __device__ __forceinline__ float4 set_row4(const float* __restrict__ P, const int32_t* __restrict__ row_code,
@@ -35,23 +41,34 @@ __device__ __forceinline__ float4 set_row4(const float* __restrict__ P, const in
 template <bool CodedQ>
 __device__ __forceinline__ float warp_chamfer_impl(const float* __restrict__ qs, int q_stride,
                                                    const int32_t* __restrict__ q_code, int m_q,
-                                              const float* __restrict__ P, const int32_t* __restrict__ row_code,
-                                              const float* __restrict__ centroids, int m_p,
-                                              float* __restrict__ stage, float* __restrict__ rowmax,
-                                              float (&qr)[kDim], int& loaded_rg) {
+                                                   const float* __restrict__ P, const int32_t* __restrict__ row_code,
+                                                   const float* __restrict__ centroids, int m_p,
+                                                   float* __restrict__ stage, float* __restrict__ rowmax,
+                                                   float (&qr)[kDim], int& loaded_rg) {
   const int lane = threadIdx.x & 31;
+  const int half = lane & 1;           // component half of this lane
+  const int pair = lane >> 1;          // query rows 2 pair, 2 pair + 1
   const int n_rg = (m_q + 31) >> 5;
+  // where this lane's float4 of a set vector goes in the staged layout
+  const int st_off = 4 * lane + (lane >= 16 ? 4 : 0);
+  const int rd_off = half * (kDim / 2 + 4);
   for (int rg = 0; rg < n_rg; ++rg) {
+    const int ia = rg * 32 + 2 * pair, ib = ia + 1;
     if (rg != loaded_rg) {
-      const int i = rg * 32 + lane;
 #pragma unroll
-      for (int k = 0; k < kDim; ++k) {
-        if constexpr (CodedQ) qr[k] = (i < m_q) ? centroids[(int64_t)q_code[i] * kDim + k] : 0.f;
-        else qr[k] = (i < m_q) ? qs[(int64_t)i * q_stride + k] : 0.f;
+      for (int k = 0; k < kDim / 2; ++k) {
+        const int kk = half * (kDim / 2) + k;
+        if constexpr (CodedQ) {
+          qr[k] = (ia < m_q) ? centroids[(int64_t)q_code[ia] * kDim + kk] : 0.f;
+          qr[kDim / 2 + k] = (ib < m_q) ? centroids[(int64_t)q_code[ib] * kDim + kk] : 0.f;
+        } else {
+          qr[k] = (ia < m_q) ? qs[(int64_t)ia * q_stride + kk] : 0.f;
+          qr[kDim / 2 + k] = (ib < m_q) ? qs[(int64_t)ib * q_stride + kk] : 0.f;
+        }
       }
       loaded_rg = rg;
     }
-    float best = -INFINITY;
+    float best_a = -INFINITY, best_b = -INFINITY;
     float4 pf[kVecBlock];
     {
       const int nv0 = min(kVecBlock, m_p);
@@ -64,33 +81,44 @@ __device__ __forceinline__ float warp_chamfer_impl(const float* __restrict__ qs,
       __syncwarp();
 #pragma unroll
       for (int v = 0; v < kVecBlock; ++v)
-        if (v < nv) reinterpret_cast<float4*>(stage + v * kDim)[lane] = pf[v];
+        if (v < nv) *reinterpret_cast<float4*>(stage + v * kStageStride + st_off) = pf[v];
       __syncwarp();
       const int j1 = j0 + kVecBlock;
       const int nv1 = min(kVecBlock, m_p - j1);
 #pragma unroll
       for (int v = 0; v < kVecBlock; ++v)
         if (v < nv1) pf[v] = set_row4(P, row_code, centroids, j1 + v, lane);
-      float acc[kVecBlock];
+      float acc_a[kVecBlock], acc_b[kVecBlock];
 #pragma unroll
-      for (int v = 0; v < kVecBlock; ++v) acc[v] = 0.f;
+      for (int v = 0; v < kVecBlock; ++v) { acc_a[v] = 0.f; acc_b[v] = 0.f; }
 #pragma unroll
-      for (int k4 = 0; k4 < kDim / 4; ++k4) {
+      for (int k4 = 0; k4 < kDim / 8; ++k4) {
 #pragma unroll
         for (int v = 0; v < kVecBlock; ++v) {
-          const float4 p = reinterpret_cast<const float4*>(stage + v * kDim)[k4];
-          acc[v] = __fmaf_rn(qr[4 * k4 + 0], p.x, acc[v]);
-          acc[v] = __fmaf_rn(qr[4 * k4 + 1], p.y, acc[v]);
-          acc[v] = __fmaf_rn(qr[4 * k4 + 2], p.z, acc[v]);
-          acc[v] = __fmaf_rn(qr[4 * k4 + 3], p.w, acc[v]);
+          const float4 p = *reinterpret_cast<const float4*>(stage + v * kStageStride + rd_off + 4 * k4);
+          acc_a[v] = __fmaf_rn(qr[4 * k4 + 0], p.x, acc_a[v]);
+          acc_a[v] = __fmaf_rn(qr[4 * k4 + 1], p.y, acc_a[v]);
+          acc_a[v] = __fmaf_rn(qr[4 * k4 + 2], p.z, acc_a[v]);
+          acc_a[v] = __fmaf_rn(qr[4 * k4 + 3], p.w, acc_a[v]);
+          acc_b[v] = __fmaf_rn(qr[kDim / 2 + 4 * k4 + 0], p.x, acc_b[v]);
+          acc_b[v] = __fmaf_rn(qr[kDim / 2 + 4 * k4 + 1], p.y, acc_b[v]);
+          acc_b[v] = __fmaf_rn(qr[kDim / 2 + 4 * k4 + 2], p.z, acc_b[v]);
+          acc_b[v] = __fmaf_rn(qr[kDim / 2 + 4 * k4 + 3], p.w, acc_b[v]);
         }
       }
 #pragma unroll
-      for (int v = 0; v < kVecBlock; ++v)
-        if (v < nv) best = fmaxf(best, acc[v]);
+      for (int v = 0; v < kVecBlock; ++v) {
+        // c0 + c1 in the lane holding c0 and c1 + c0 in its partner: the same sum
+        const float da = acc_a[v] + __shfl_xor_sync(0xffffffffu, acc_a[v], 1);
+        const float db = acc_b[v] + __shfl_xor_sync(0xffffffffu, acc_b[v], 1);
+        if (v < nv) {
+          best_a = fmaxf(best_a, da);
+          best_b = fmaxf(best_b, db);
+        }
+      }
     }
-    const int i = rg * 32 + lane;
-    if (i < m_q) rowmax[i] = best;
+    if (half == 0 && ia < m_q) rowmax[ia] = best_a;
+    if (half == 1 && ib < m_q) rowmax[ib] = best_b;
   }
   __syncwarp();
   float s = 0.f;
