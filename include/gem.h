@@ -169,9 +169,12 @@ void gem_workspace_destroy(gem_workspace* ws);
  * autotuner varies; results do not depend on them):
  *   m_tiles     resident query rows per CTA / 128: 1, 2 or 4 (document tile
  *               width 256 / m_tiles columns)
+ *   a_in_tmem   1: the query rows live in tensor memory and the MMAs read only
+ *               the document tile from shared memory (m_tiles = 2 only; tile
+ *               width 96)
  *   chunk_rows  document rows per work unit (whole sets; 1024 .. 2^24)
  */
-gem_status gem_workspace_set_schedule(gem_workspace* ws, int32_t m_tiles, int32_t chunk_rows);
+gem_status gem_workspace_set_schedule(gem_workspace* ws, int32_t m_tiles, int32_t a_in_tmem, int32_t chunk_rows);
 
 /*
  * Exact CH of every query set against every stored set (Eq. 1 for all P in D,
@@ -327,14 +330,16 @@ void gem_batch_destroy(gem_batch* batch);
  * synchronise `stream`.
  *
  * gem_autotune_score_all: schedules of gem_score_all for compute GEM_BF16 or
- * GEM_FP8_E4M3 (m_tiles in {1, 2, 4} x chunk_rows in {2^14, 2^16, 2^18}); the
- * choice is applied to `ws` (as gem_workspace_set_schedule).  scores float32
- * [n_queries * n_sets] is scratch for the timing runs.
+ * GEM_FP8_E4M3 ((m_tiles, a_in_tmem) in {(2,0), (4,0), (2,1), (1,0)} x
+ * chunk_rows in {2^14, 2^16, 2^18}); the choice is applied to `ws` (as
+ * gem_workspace_set_schedule).  scores float32 [n_queries * n_sets] is scratch
+ * for the timing runs.
  */
 gem_status gem_autotune_score_all(const gem_store* store, gem_workspace* ws, const float* q,
                                   const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
                                   int32_t compute, float* scores, const char* cache_path, int32_t* m_tiles,
-                                  int32_t* chunk_rows, float* ms, int32_t* from_cache, void* stream);
+                                  int32_t* a_in_tmem, int32_t* chunk_rows, float* ms, int32_t* from_cache,
+                                  void* stream);
 
 /*
  * gem_autotune_batch: schedules of a gem_batch (seg in {8, 16, 32, 64} x

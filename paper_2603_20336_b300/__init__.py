@@ -221,9 +221,10 @@ def search_host(store: Store, ws: Workspace, q_host, q_offsets_host, compute="bf
     return out_ids, out_scores
 
 
-def set_schedule(ws: Workspace, m_tiles: int = 2, chunk_rows: int = 1 << 16):
-    """Tensor-core kernel schedule of a workspace (results do not depend on it)."""
-    _check(lib.gem_workspace_set_schedule(ws.handle, m_tiles, chunk_rows))
+def set_schedule(ws: Workspace, m_tiles: int = 2, chunk_rows: int = 1 << 16, a_in_tmem: bool = False):
+    """Tensor-core kernel schedule of a workspace (results do not depend on it).
+    a_in_tmem keeps the query rows in tensor memory (m_tiles = 2 only)."""
+    _check(lib.gem_workspace_set_schedule(ws.handle, m_tiles, int(bool(a_in_tmem)), chunk_rows))
 
 
 def assign_codes(x, centroids, with_best: bool = False, stream=None):
@@ -372,16 +373,19 @@ class MaxSimFn(torch.autograd.Function):
 
 def autotune_score_all(store: Store, ws: Workspace, q, q_offsets, compute="bf16", scores=None, cache_path=None,
                        stream=None):
-    """Pick and apply the fastest tensor-core schedule: dict(m_tiles, chunk_rows, ms, from_cache)."""
+    """Pick and apply the fastest tensor-core schedule:
+    dict(m_tiles, a_in_tmem, chunk_rows, ms, from_cache)."""
     q, qo, B, rows = _queries(q, q_offsets)
     if scores is None:
         scores = torch.empty((B, store.n_sets), dtype=torch.float32, device=q.device)
-    mt, cr, fc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    mt, at, cr, fc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     ms = ctypes.c_float()
     _check(lib.gem_autotune_score_all(store.handle, ws.handle, _ptr(q), _ptr(qo), B, rows, _dtype_code(compute),
                                       _ptr(scores), cache_path.encode() if cache_path else None, ctypes.byref(mt),
-                                      ctypes.byref(cr), ctypes.byref(ms), ctypes.byref(fc), _stream(stream)))
-    return {"m_tiles": mt.value, "chunk_rows": cr.value, "ms": ms.value, "from_cache": bool(fc.value)}
+                                      ctypes.byref(at), ctypes.byref(cr), ctypes.byref(ms), ctypes.byref(fc),
+                                      _stream(stream)))
+    return {"m_tiles": mt.value, "a_in_tmem": bool(at.value), "chunk_rows": cr.value, "ms": ms.value,
+            "from_cache": bool(fc.value)}
 
 
 def autotune_batch(store: Store, q, q_offsets, cand_offsets, cand_ids, mode="f32", max_q_len=64, cache_path=None,

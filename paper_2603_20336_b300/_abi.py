@@ -21,7 +21,7 @@ SIGNATURES = {
     "gem_estimate_codes": (C.c_int, [P, P, P, P, I32, I64, P, P, I64, P, P]),
     "gem_workspace_create": (C.c_int, [P, I32, I64, I32, I64, I32, C.POINTER(P)]),
     "gem_workspace_destroy": (None, [P]),
-    "gem_workspace_set_schedule": (C.c_int, [P, I32, I32]),
+    "gem_workspace_set_schedule": (C.c_int, [P, I32, I32, I32]),
     "gem_score_all": (C.c_int, [P, P, P, P, I32, I64, I32, P, P]),
     "gem_score_ids": (C.c_int, [P, P, P, P, I32, I64, P, P, I64, I32, P, P]),
     "gem_topk": (C.c_int, [P, P, P, I32, I64, P, I32, P, P, P]),
@@ -35,7 +35,7 @@ SIGNATURES = {
     "gem_batch_status": (C.c_int, [P]),
     "gem_batch_destroy": (None, [P]),
     "gem_kernel_launches": (I64, []),
-    "gem_autotune_score_all": (C.c_int, [P, P, P, P, I32, I64, I32, P, C.c_char_p, P, P, P, P, P]),
+    "gem_autotune_score_all": (C.c_int, [P, P, P, P, I32, I64, I32, P, C.c_char_p, P, P, P, P, P, P]),
     "gem_autotune_batch": (C.c_int, [P, I32, I32, I64, I32, I64, P, P, P, P, P, C.c_char_p, P, P, P, P, P]),
     "gem_score_ids_noalloc": (C.c_int, [P, P, P, I32, I64, I32, P, P, I64, P, P]),
 }

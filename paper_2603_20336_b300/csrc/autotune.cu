@@ -5,7 +5,8 @@
 //
 // Results are cached in a small JSON file (path argument, else $GEM_TUNE_CACHE,
 // else no cache) keyed by a workload signature:
-//   {"entries": {"<signature>": {"a": <int>, "b": <int>, "ms": <float>}, ...}}
+//   {"entries": {"<signature>": {"a": <int>, "b": <int>, "c": <int>, "ms": <float>}, ...}}
+// ("c" is optional on read and defaults to 0).
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -23,7 +24,7 @@ namespace gem {
 namespace {
 
 struct Entry {
-  int a = 0, b = 0;
+  int a = 0, b = 0, c = 0;
   double ms = 0.0;
 };
 
@@ -58,10 +59,12 @@ std::map<std::string, Entry> read_cache(const std::string& path) {
       v = std::strtod(obj.c_str() + c + 1, nullptr);
       return true;
     };
-    double a = 0, b = 0, ms = 0;
+    double a = 0, b = 0, c = 0, ms = 0;
     if (num("a", a) && num("b", b) && num("ms", ms)) {
+      num("c", c);
       e.a = (int)a;
       e.b = (int)b;
+      e.c = (int)c;
       e.ms = ms;
       out[key] = e;
     }
@@ -78,8 +81,8 @@ void write_cache(const std::string& path, const std::map<std::string, Entry>& m)
   std::fprintf(f, "{\"entries\": {");
   bool first = true;
   for (const auto& kv : m) {
-    std::fprintf(f, "%s\n  \"%s\": {\"a\": %d, \"b\": %d, \"ms\": %.4f}", first ? "" : ",", kv.first.c_str(),
-                 kv.second.a, kv.second.b, kv.second.ms);
+    std::fprintf(f, "%s\n  \"%s\": {\"a\": %d, \"b\": %d, \"c\": %d, \"ms\": %.4f}", first ? "" : ",",
+                 kv.first.c_str(), kv.second.a, kv.second.b, kv.second.c, kv.second.ms);
     first = false;
   }
   std::fprintf(f, "\n}}\n");
@@ -133,8 +136,8 @@ gem_status time_ms(F&& run, cudaStream_t st, int reps, double* ms) {
 
 gem_status autotune_score_all(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
                               int32_t n_queries, int64_t n_q_rows, int32_t compute, float* scores,
-                              const char* cache_file, int32_t* m_tiles, int32_t* chunk_rows, float* ms_out,
-                              int32_t* from_cache, cudaStream_t st) {
+                              const char* cache_file, int32_t* m_tiles, int32_t* a_in_tmem, int32_t* chunk_rows,
+                              float* ms_out, int32_t* from_cache, cudaStream_t st) {
   const std::string path = cache_path(cache_file);
   std::ostringstream key;
   key << "score_all|" << device_name(s->device) << "|dtype" << compute << "|vecs" << bucket(s->n_pad_vecs)
@@ -146,46 +149,53 @@ gem_status autotune_score_all(const gem_store* s, gem_workspace* w, const float*
     if (it != m.end()) {
       w->tc_m_tiles = it->second.a;
       w->tc_chunk_rows = it->second.b;
+      w->tc_a_tmem = it->second.c;
       *m_tiles = it->second.a;
       *chunk_rows = it->second.b;
+      *a_in_tmem = it->second.c;
       *ms_out = (float)it->second.ms;
       *from_cache = 1;
       return GEM_OK;
     }
   }
-  const int mts[] = {2, 4, 1};
+  // (m_tiles, query rows in tensor memory)
+  const int shapes[][2] = {{2, 0}, {4, 0}, {2, 1}, {1, 0}};
   const int crs[] = {1 << 14, 1 << 16, 1 << 18};
   double best = 1e30;
-  int bm = 2, bc = 1 << 16;
+  int bm = 2, ba = 0, bc = 1 << 16;
   // repetitions sized so each candidate runs about a tenth of a second
   int reps = 1;
-  for (int mt : mts) {
+  for (const auto& sh : shapes) {
+    const int mt = sh[0], at = sh[1];
     for (int cr : crs) {
       w->tc_m_tiles = mt;
+      w->tc_a_tmem = at;
       w->tc_chunk_rows = cr;
       double ms = 0.0;
       gem_status r = time_ms(
           [&]() {
             gem_status rr = launch_plan(w, q, q_offsets, n_queries, n_q_rows, 128 * mt, compute, st);
-            if (rr == GEM_OK) rr = launch_tc_score_all(s, w, compute, mt, cr, scores, st);
+            if (rr == GEM_OK) rr = launch_tc_score_all(s, w, compute, mt, at, cr, scores, st);
             return rr;
           },
           st, reps, &ms);
       if (r != GEM_OK) return r;
-      if (ms < best) { best = ms; bm = mt; bc = cr; }
+      if (ms < best) { best = ms; bm = mt; ba = at; bc = cr; }
       if (reps == 1) reps = std::max(1, std::min(10, (int)(100.0 / std::max(ms, 1e-3))));
     }
   }
   w->tc_m_tiles = bm;
+  w->tc_a_tmem = ba;
   w->tc_chunk_rows = bc;
   *m_tiles = bm;
+  *a_in_tmem = ba;
   *chunk_rows = bc;
   *ms_out = (float)best;
   *from_cache = 0;
   if (!path.empty()) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     auto m = read_cache(path);
-    m[key.str()] = Entry{bm, bc, best};
+    m[key.str()] = Entry{bm, bc, ba, best};
     write_cache(path, m);
   }
   return GEM_OK;
@@ -235,7 +245,7 @@ gem_status autotune_batch(const gem_store* s, int32_t mode, int32_t n_queries, i
   if (!path.empty()) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     auto m = read_cache(path);
-    m[key.str()] = Entry{bs, bc, best};
+    m[key.str()] = Entry{bs, bc, 0, best};
     write_cache(path, m);
   }
   return GEM_OK;

@@ -22,10 +22,11 @@
 // the set's own last vector (a repeated vector cannot change a maximum), so sets
 // end only at 8-column subgroup boundaries.  Per subgroup the thread folds 8
 // columns into a running max with three-input max instructions; when a set ends
-// (a warp-uniform bit) the rows of each query slot are summed by a g-lane xor
-// butterfly (g = slot size) and one lane writes the score.  A set never spans two
-// chunks, so no partial maximum leaves registers and no similarity matrix is
-// written anywhere.
+// (a warp-uniform bit) the rows of each query slot are summed (a 32-row slot
+// whose row maxima are all below 2 in magnitude: one integer warp reduction in
+// fixed point; otherwise a g-lane xor butterfly, g = slot size) and one lane
+// writes the score.  A set never spans two chunks, so no partial maximum leaves
+// registers and no similarity matrix is written anywhere.
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -34,25 +35,36 @@
 namespace gem {
 namespace {
 
-template <int MT, bool FP8>
+// AT: the query block (operand A) lives in tensor memory, written by the
+// epilogue warps once per unit, so the MMAs read only the document tile from
+// shared memory; the tile narrows so that accumulators and A share the 512
+// TMEM columns (bf16 MT=2: 2 x 2 x 96 + 2 x 64; e4m3 MT=2: 2 x 2 x 96 + 2 x 32).
+template <int MT, bool FP8, bool AT = false>
 struct TcCfg {
   static constexpr int M_RES = 128 * MT;
-  static constexpr int N = 256 / MT;              // columns per tile
+  static constexpr int A_COLS = AT ? (FP8 ? 32 : 64) : 0;  // TMEM columns of A per M tile
+  // tile width: with A resident, 96 columns (a multiple of 32, so every TMEM
+  // access starts on a 32-column boundary)
+  static constexpr int N = AT ? 96 : 256 / MT;  // columns per tile
+  static_assert(!AT || MT == 2, "A in tensor memory is laid out for two M tiles");
   static constexpr int ROW_BYTES = FP8 ? 128 : 256;
   static constexpr int HALVES = FP8 ? 1 : 2;      // 128-byte swizzle atoms per row
   static constexpr int K_STEP = FP8 ? 32 : 16;    // K per MMA instruction
   static constexpr int K_STEPS = kDim / K_STEP;   // MMAs per tile and M tile
-  static constexpr int Q_BYTES = M_RES * ROW_BYTES;
+  static constexpr int Q_BYTES = AT ? 0 : M_RES * ROW_BYTES;
   static constexpr int STAGE_BYTES = N * ROW_BYTES;
-  static constexpr int STAGES = (MT == 1) ? (FP8 ? 6 : 3) : (MT == 2 ? (FP8 ? 8 : 4) : (FP8 ? 12 : 6));
+  static constexpr int STAGES = AT ? (FP8 ? 12 : 8)
+                                   : (MT == 1) ? (FP8 ? 6 : 3) : (MT == 2 ? (FP8 ? 8 : 4) : (FP8 ? 12 : 6));
   // fp8: per-column dequantisation scales of each tile, in a ring of their own
   // (the operand stage is recycled as soon as the MMA has read it)
   static constexpr int SC_SLOTS = FP8 ? 8 : 0;
   static constexpr int SC_BYTES = SC_SLOTS * N * 4;
   static constexpr int EPI_WARPS = 4 * MT;
   static constexpr int THREADS = (EPI_WARPS + 2) * 32;
-  static constexpr int ACC_COLS = MT * N;         // 256 per accumulator buffer
-  static constexpr int TMEM_COLS = 2 * ACC_COLS;  // 512
+  static constexpr int ACC_COLS = MT * N;         // per accumulator buffer
+  static constexpr int A_BASE = 2 * ACC_COLS;     // first TMEM column of A (AT)
+  static constexpr int TMEM_COLS = 512;
+  static_assert(A_BASE + MT * A_COLS <= TMEM_COLS, "TMEM over-committed");
   static constexpr int SMEM_BYTES = 1024 /*align slack*/ + Q_BYTES + STAGES * STAGE_BYTES + SC_BYTES + 512;
   static constexpr uint32_t IDESC = make_idesc(128, N, FP8 ? 0u : 1u, FP8 ? 0u : 1u);
 };
@@ -65,6 +77,7 @@ struct TcArgs {
   const int* part_pass;
   const int* part_slot;
   const float* q_scale;      // fp8 only: per packed row
+  const uint32_t* qpack;     // AT: packed query rows as 32-bit words
   const int64_t* doc_off;    // [n_sets + 1]
   const int* chunk_doc;      // [n_chunks + 1]
   int n_chunks;
@@ -74,11 +87,11 @@ struct TcArgs {
   int* status;
 };
 
-template <int MT, bool FP8>
-__global__ void __launch_bounds__(TcCfg<MT, FP8>::THREADS, 1)
+template <int MT, bool FP8, bool AT>
+__global__ void __launch_bounds__(TcCfg<MT, FP8, AT>::THREADS, 1)
 tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_d,
                     const __grid_constant__ CUtensorMap tm_scale, TcArgs a) {
-  using C = TcCfg<MT, FP8>;
+  using C = TcCfg<MT, FP8, AT>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* q_smem = smem;
@@ -107,7 +120,7 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], C::EPI_WARPS); }
-    mbar_init(q_full, 1);
+    mbar_init(q_full, AT ? C::EPI_WARPS : 1);
     mbar_init(q_empty, 1);
     mbar_init(done_bar, 1);
     for (int s = 0; s < C::SC_SLOTS; ++s) { mbar_init(&sc_full[s], 1); mbar_init(&sc_empty[s], C::EPI_WARPS); }
@@ -138,13 +151,17 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
       for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
         const int chunk = (int)(u / nqb);
         const int qb = qb0 + (int)(u % nqb);
-        if (it > 0 && !mbar_wait(q_empty, (it - 1) & 1, a.status, abort_flag)) { ok = false; break; }
-        mbar_arrive_expect_tx(q_full, C::Q_BYTES);
-        ++q_issued;
-        for (int m = 0; m < MT; ++m)
-          for (int h = 0; h < C::HALVES; ++h)
-            tma_load_2d(q_smem + (m * C::HALVES + h) * 16384, &tm_q, q_full, h * 64,
-                        qb * C::M_RES + m * 128);
+        if constexpr (!AT) {
+          if (it > 0 && !mbar_wait(q_empty, (it - 1) & 1, a.status, abort_flag)) { ok = false; break; }
+          mbar_arrive_expect_tx(q_full, C::Q_BYTES);
+          ++q_issued;
+          for (int m = 0; m < MT; ++m)
+            for (int h = 0; h < C::HALVES; ++h)
+              tma_load_2d(q_smem + (m * C::HALVES + h) * 16384, &tm_q, q_full, h * 64,
+                          qb * C::M_RES + m * 128);
+        } else {
+          (void)qb;
+        }
         const int64_t r0 = a.doc_off[a.chunk_doc[chunk]];
         const int64_t r1 = a.doc_off[a.chunk_doc[chunk + 1]];
         const int ntiles = (int)((r1 - r0 + C::N - 1) / C::N);
@@ -205,11 +222,18 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
             for (int k = 0; k < C::K_STEPS; ++k) {
               const int half = (k * C::K_STEP * (FP8 ? 1 : 2)) / 128;
               const int within = (k * C::K_STEP * (FP8 ? 1 : 2)) % 128;
-              uint64_t ad = sw128_desc(q_base + (m * C::HALVES + half) * 16384 + within);
               uint64_t bd = sw128_desc(d_base + half * (C::N * 128) + within);
               const uint32_t dt = tmem + acc * C::ACC_COLS + m * C::N;
-              if constexpr (FP8) mma_f8(dt, ad, bd, C::IDESC, k > 0);
-              else mma_bf16(dt, ad, bd, C::IDESC, k > 0);
+              if constexpr (AT) {
+                // A: 128 lanes x (K_STEP elements = 8 columns of 32-bit words) per step
+                const uint32_t at = tmem + C::A_BASE + m * C::A_COLS + k * 8;
+                if constexpr (FP8) mma_f8_ta(dt, at, bd, C::IDESC, k > 0);
+                else mma_bf16_ta(dt, at, bd, C::IDESC, k > 0);
+              } else {
+                uint64_t ad = sw128_desc(q_base + (m * C::HALVES + half) * 16384 + within);
+                if constexpr (FP8) mma_f8(dt, ad, bd, C::IDESC, k > 0);
+                else mma_bf16(dt, ad, bd, C::IDESC, k > 0);
+              }
             }
           }
           mma_commit(&empty[stage]);
@@ -217,7 +241,7 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
           if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
           if (++acc == 2) { acc = 0; acc_phase ^= 1; }
         }
-        if (ok) mma_commit(q_empty);
+        if (ok && !AT) mma_commit(q_empty);
       }
       // all MMAs of this thread complete before the CTA releases TMEM
       mma_commit(done_bar);
@@ -251,6 +275,25 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
         dst = a.scores + (int64_t)a.part_query[p] * a.n_sets;
       }
       if constexpr (FP8) row_scale = a.q_scale[prow];
+      if constexpr (AT) {
+        // This unit's query row goes into TMEM as operand A (lane = row, 32-bit
+        // words of packed elements, lower k in the lower bits).  Every MMA of
+        // the previous unit has completed: this warp consumed its last tile.
+        constexpr int W = C::A_COLS;  // words per row
+        const uint4* src = reinterpret_cast<const uint4*>(a.qpack + (int64_t)prow * W);
+        uint32_t words[W];
+#pragma unroll
+        for (int i = 0; i < W / 4; ++i) {
+          const uint4 x = src[i];
+          words[4 * i] = x.x; words[4 * i + 1] = x.y; words[4 * i + 2] = x.z; words[4 * i + 3] = x.w;
+        }
+        const uint32_t ta = tmem + t_lane + C::A_BASE + m_tile * C::A_COLS;
+        if constexpr (W == 64) tmem_st64(ta, words);
+        else tmem_st32(ta, words);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(q_full);
+      }
       const int d0 = a.chunk_doc[chunk];
       const int d1 = a.chunk_doc[chunk + 1];
       const int64_t r0 = a.doc_off[d0];
@@ -267,12 +310,15 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
       // fold the 8-column subgroups of one loaded chunk into the running max;
       // a set that ends is summed over each query slot and written
       // (fp8: each column is first multiplied by its vector's scale s_j, read
-      // as a broadcast from the tile's scale slot)
-      auto fold = [&](const float (&v)[CH], int sg0, uint32_t ends, int n_sub, const float* sc) {
+      // as a broadcast from the tile's scale slot).  Columns past the chunk's
+      // last row (the next chunk's rows or the tensor map's zero fill) are
+      // folded too, without a bounds branch: no set ends there, and the
+      // running max is dropped when the unit ends.
+      auto fold = [&](const float (&v)[CH], int sg0, uint32_t ends, const float* sc) {
 #pragma unroll
         for (int s = 0; s < CH / 8; ++s) {
           const int sg = sg0 + s;
-          if (sg < n_sub) {
+          {
             float x[8];
             if constexpr (FP8) {
               const float4 s0 = reinterpret_cast<const float4*>(sc)[2 * s];
@@ -290,11 +336,21 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
             run = fmax3(run, fmax3(x[0], x[1], x[2]), fmax3(x[3], x[4], x[5]));
             run = fmax3(run, x[6], x[7]);
             if ((ends >> sg) & 1u) {
-              float sum = run * row_scale;
+              const float val = run * row_scale;
+              float sum;
+              if (__all_sync(0xffffffffu, g == 32 && fabsf(val) < 2.f)) {
+                // one 32-row slot with every row maximum below 2 in magnitude:
+                // sum in 2^-24 fixed point with one warp reduction (|sum| < 2^30,
+                // exact and independent of the order; rounding <= 2^-25 per row)
+                const int iv = __float2int_rn(val * 16777216.f);
+                sum = (float)__reduce_add_sync(0xffffffffu, iv) * (1.f / 16777216.f);
+              } else {
+                sum = val;
 #pragma unroll
-              for (int o = 16; o > 0; o >>= 1) {
-                const float other = __shfl_xor_sync(0xffffffffu, sum, o);
-                if (o < g) sum += other;
+                for (int o = 16; o > 0; o >>= 1) {
+                  const float other = __shfl_xor_sync(0xffffffffu, sum, o);
+                  if (o < g) sum += other;
+                }
               }
               if (writer) {
                 float* d = dst + cur;
@@ -340,14 +396,13 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
         uint32_t bit = 0;
         if (win + lane >= cur && e_win <= te) bit = 1u << (int)((e_win - ts) / kRowAlign - 1);
         const uint32_t ends = __reduce_or_sync(0xffffffffu, bit);
-        const int n_sub = (int)((te - ts) / kRowAlign);
-        fold(v, 0, ends, n_sub, sc);
+        fold(v, 0, ends, sc);
         if constexpr (C::N > CH) {
           tmem_ld_cols<CH>(tcol + CH, v);
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&acc_empty[acc]);
-          fold(v, CH / 8, ends, n_sub, FP8 ? sc + CH : nullptr);
+          fold(v, CH / 8, ends, FP8 ? sc + CH : nullptr);
         }
         if constexpr (FP8) {
           __syncwarp();
@@ -366,14 +421,14 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
   }
 }
 
-template <int MT, bool FP8>
+template <int MT, bool FP8, bool AT = false>
 gem_status launch_tc(const gem_store* s, gem_workspace* ws, const CUtensorMap& tm_q,
                      const CUtensorMap& tm_d, const CUtensorMap& tm_scale, const ChunkMap* cm,
                      float* scores, cudaStream_t st) {
-  using C = TcCfg<MT, FP8>;
+  using C = TcCfg<MT, FP8, AT>;
   static bool attr_set = false;
   if (!attr_set) {
-    GEM_CUDA_TRY(cudaFuncSetAttribute(tc_score_all_kernel<MT, FP8>,
+    GEM_CUDA_TRY(cudaFuncSetAttribute(tc_score_all_kernel<MT, FP8, AT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
     attr_set = true;
   }
@@ -385,6 +440,8 @@ gem_status launch_tc(const gem_store* s, gem_workspace* ws, const CUtensorMap& t
   a.part_pass = ws->d_part_pass;
   a.part_slot = ws->d_part_slot;
   a.q_scale = ws->d_qpack_scale;
+  a.qpack = FP8 ? reinterpret_cast<const uint32_t*>(ws->d_qpack_fp8)
+                : reinterpret_cast<const uint32_t*>(ws->d_qpack_bf16);
   a.doc_off = s->d_pad_offsets;
   a.chunk_doc = cm->d_chunk_doc;
   a.n_chunks = cm->n_chunks;
@@ -393,7 +450,7 @@ gem_status launch_tc(const gem_store* s, gem_workspace* ws, const CUtensorMap& t
   a.status = ws->d_status;
   for (int pass = 0; pass < ws->n_passes; ++pass) {
     a.pass = pass;
-    tc_score_all_kernel<MT, FP8><<<s->n_sm, C::THREADS, C::SMEM_BYTES, st>>>(tm_q, tm_d, tm_scale, a);
+    tc_score_all_kernel<MT, FP8, AT><<<s->n_sm, C::THREADS, C::SMEM_BYTES, st>>>(tm_q, tm_d, tm_scale, a);
     GEM_CUDA_TRY(cudaGetLastError());
     note_launches(1);
   }
@@ -403,14 +460,16 @@ gem_status launch_tc(const gem_store* s, gem_workspace* ws, const CUtensorMap& t
 }  // namespace
 
 gem_status launch_tc_score_all(const gem_store* s, gem_workspace* ws, int compute, int m_tiles,
-                               int chunk_rows, float* scores, cudaStream_t st) {
+                               int a_tmem, int chunk_rows, float* scores, cudaStream_t st) {
   const ChunkMap* cm = nullptr;
   gem_status r = store_chunk_map(s, chunk_rows, &cm);
   if (r != GEM_OK) return r;
+  if (a_tmem && m_tiles != 2) return fail(GEM_ERR_INVALID, "A in tensor memory needs m_tiles = 2");
   if (compute == GEM_BF16) {
-    const int n = 256 / m_tiles;
+    const int n = a_tmem ? TcCfg<2, false, true>::N : 256 / m_tiles;
     const CUtensorMap* td = nullptr;
     if ((r = store_tmap_bf16(s, n, &td)) != GEM_OK) return r;
+    if (a_tmem) return launch_tc<2, false, true>(s, ws, ws->tmap_q_bf16, *td, *td, cm, scores, st);
     switch (m_tiles) {
       case 1: return launch_tc<1, false>(s, ws, ws->tmap_q_bf16, *td, *td, cm, scores, st);
       case 2: return launch_tc<2, false>(s, ws, ws->tmap_q_bf16, *td, *td, cm, scores, st);
@@ -419,11 +478,12 @@ gem_status launch_tc_score_all(const gem_store* s, gem_workspace* ws, int comput
     }
   }
   if (compute == GEM_FP8_E4M3) {
-    const int n = 256 / m_tiles;
+    const int n = a_tmem ? TcCfg<2, true, true>::N : 256 / m_tiles;
     const CUtensorMap* td = nullptr;
     const CUtensorMap* tsc = nullptr;
     if ((r = store_tmap_fp8(s, n, &td)) != GEM_OK) return r;
     if ((r = store_tmap_fp8_scale(s, n, &tsc)) != GEM_OK) return r;
+    if (a_tmem) return launch_tc<2, true, true>(s, ws, ws->tmap_q_fp8, *td, *tsc, cm, scores, st);
     switch (m_tiles) {
       case 1: return launch_tc<1, true>(s, ws, ws->tmap_q_fp8, *td, *tsc, cm, scores, st);
       case 2: return launch_tc<2, true>(s, ws, ws->tmap_q_fp8, *td, *tsc, cm, scores, st);

@@ -57,3 +57,23 @@ def test_autotune_batch_choice_bit_matches(gem, tmp_path):
     assert torch.equal(outs[0], outs[1])
     assert gem.autotune_batch(store, *args, mode="f32", max_q_len=64,
                               cache_path=str(tmp_path / "b.json"))["from_cache"]
+
+
+def test_every_schedule_bit_identical(gem):
+    """The tensor-core schedules (resident query rows, query rows in tensor
+    memory or shared memory, chunk size) only change the launch shape."""
+    w = synth.exact_fp32(n_sets=2500, n_queries=37)
+    store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("bf16", "fp8"))
+    ws = gem.Workspace(store, max_queries=64, max_q_rows=64 * 32, max_q_len=32)
+    q, qo = w.queries.vecs.cuda(), torch.from_numpy(w.queries.offsets).cuda()
+    for compute in ("bf16", "fp8"):
+        outs = []
+        for mt, at, cr in ((2, True, 1 << 16), (2, False, 1 << 16), (4, False, 1 << 14), (1, False, 1 << 18),
+                           (2, True, 1 << 14)):
+            gem.set_schedule(ws, mt, cr, a_in_tmem=at)
+            outs.append(gem.score_all(store, ws, q, qo, compute).clone())
+            assert ws.status() == 0
+        for o in outs[1:]:
+            assert torch.equal(o, outs[0])
+    with pytest.raises(Exception):
+        gem.set_schedule(ws, 4, 1 << 16, a_in_tmem=True)

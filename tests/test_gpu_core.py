@@ -130,6 +130,25 @@ def test_score_all_bf16_query_length_mix(gem, cfg1, lens):
     assert np.all(np.abs(S - Sq) <= tol), np.abs(S - Sq).max()
 
 
+@pytest.mark.parametrize("compute", ["bf16", "fp8"])
+def test_score_all_rows_beyond_unit_scale(gem, cfg1, compute):
+    """Queries scaled by 0.5 .. 3: slots whose row maxima reach 2 in magnitude
+    are summed in floating point, the others in fixed point; both agree with the
+    oracle on the same rounded inputs."""
+    w = cfg1["w"]
+    lens = np.array([32, 32, 32, 32, 16, 32])
+    qs = synth.vector_sets(lens, synth.centres(64, 1235), 9191)
+    scale = np.repeat([1.0, 3.0, 0.5, 2.5, 3.0, 1.9], lens)[:, None].astype(np.float32)
+    Xq = qs.vecs.numpy() * scale
+    S = gem.score_all(cfg1["store"], cfg1["ws"], torch.from_numpy(Xq).cuda(),
+                      torch.from_numpy(qs.offsets).cuda(), compute).cpu().numpy()
+    assert cfg1["ws"].status() == 0
+    rnd = oracle.bf16_round if compute == "bf16" else _fp8_dequantised
+    Sq = oracle.score_all(rnd(Xq), qs.offsets, rnd(w.docs.vecs.numpy()), w.docs.offsets)
+    tol = 2e-4 * (lens * np.array([1.0, 3.0, 0.5, 2.5, 3.0, 1.9]))[:, None]
+    assert np.all(np.abs(S - Sq) <= tol), np.abs(S - Sq).max()
+
+
 def test_score_ids_f32_matches_oracle(gem, cfg1):
     w = cfg1["w"]
     rng = np.random.default_rng(5)
