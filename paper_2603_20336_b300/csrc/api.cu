@@ -93,6 +93,7 @@ void gem_store_destroy(gem_store* s) {
   cudaSetDevice(s->device);
   dfree(s->d_offsets);
   dfree(s->d_pad_offsets);
+  dfree(s->d_end_bits);
   dfree(s->d_f32);
   dfree(s->d_bf16);
   dfree(s->d_fp8);
@@ -156,11 +157,23 @@ gem_status gem_store_create(const float* vecs, const int64_t* offsets, int64_t n
   gem_status r;
   if ((r = dmalloc(&s->d_offsets, n_sets + 1, "offsets")) != GEM_OK) { gem_store_destroy(s); return r; }
   if ((r = dmalloc(&s->d_pad_offsets, n_sets + 1, "padded offsets")) != GEM_OK) { gem_store_destroy(s); return r; }
+  std::vector<uint32_t> end_bits((size_t)(VP / kRowAlign / 32 + 2), 0u);
+  for (int64_t i = 0; i < n_sets; ++i) {
+    const int64_t b = s->h_pad_offsets[i + 1] / kRowAlign - 1;
+    end_bits[(size_t)(b >> 5)] |= 1u << (b & 31);
+  }
+  if ((r = dmalloc(&s->d_end_bits, (int64_t)end_bits.size(), "set-end bitmap")) != GEM_OK) {
+    gem_store_destroy(s);
+    return r;
+  }
   cudaError_t e = cudaMemcpyAsync(s->d_offsets, s->h_offsets.data(), sizeof(int64_t) * (n_sets + 1),
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(s->d_pad_offsets, s->h_pad_offsets.data(), sizeof(int64_t) * (n_sets + 1),
                         cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_end_bits, end_bits.data(), sizeof(uint32_t) * end_bits.size(), cudaMemcpyHostToDevice,
+                        st);
   // the FP32 source of the quantised copies lives on the device during the build
   float* src = nullptr;
   float* tmp = nullptr;

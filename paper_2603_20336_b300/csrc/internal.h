@@ -60,6 +60,8 @@ struct gem_store {
   int64_t n_pad_vecs = 0;
   std::vector<int64_t> h_pad_offsets;
   int64_t* d_pad_offsets = nullptr;
+  // bit i set: a set ends with padded row 8 i + 7 (two words of slack at the end)
+  uint32_t* d_end_bits = nullptr;
   float* d_f32 = nullptr;
   __nv_bfloat16* d_bf16 = nullptr;
   uint8_t* d_fp8 = nullptr;

@@ -75,10 +75,10 @@ struct TcArgs {
   const int* part_query;
   const int* part_g;
   const int* part_pass;
-  const int* part_slot;
   const float* q_scale;      // fp8 only: per packed row
   const uint32_t* qpack;     // AT: packed query rows as 32-bit words
-  const int64_t* doc_off;    // [n_sets + 1]
+  const int64_t* doc_off;    // padded row offsets [n_sets + 1]
+  const uint32_t* end_bits;  // set-end bitmap over 8-row subgroups
   const int* chunk_doc;      // [n_chunks + 1]
   int n_chunks;
   int pass;
@@ -265,12 +265,11 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
       const int prow = qb * C::M_RES + local_row;
       const int p = a.row_part[prow];
       int g = 1;
-      bool writer = false, add = false;
-      float* dst = nullptr;
+      bool add = false;
+      float* dst = nullptr;  // score row of this row's query (rows of no part: none)
       float row_scale = 1.f;
       if (p >= 0) {
         g = a.part_g[p];
-        writer = (prow == a.part_slot[p]);
         add = a.part_pass[p] > 0;
         dst = a.scores + (int64_t)a.part_query[p] * a.n_sets;
       }
@@ -299,13 +298,30 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
       const int64_t r0 = a.doc_off[d0];
       const int64_t r1 = a.doc_off[d1];
       const int ntiles = (int)((r1 - r0 + C::N - 1) / C::N);
+      (void)d1;
       int cur = d0;
       float run = -INFINITY;
-      // ends of the 32 sets win .. win + 31, one per lane; refreshed when a
-      // tile could reach past the window
-      int win = d0;
-      int64_t e_win = (win + lane < d1) ? a.doc_off[win + lane + 1] : INT64_MAX;
       constexpr int CH = C::N < 128 ? C::N : 128;  // columns per TMEM load
+      // Set ends come from the store's end bitmap (bit i: a set ends with padded
+      // row 8 i + 7).  The bits of tile t + 1 are loaded while tile t is folded.
+      const int64_t sg_first = r0 / kRowAlign;
+      auto load_bits = [&](int t) -> uint32_t {
+        const int64_t gs = sg_first + (int64_t)t * (C::N / kRowAlign);
+        const uint32_t* w = a.end_bits + (gs >> 5);
+        return (uint32_t)((((uint64_t)__ldg(w + 1) << 32) | __ldg(w)) >> (gs & 31));
+      };
+      uint32_t bits = load_bits(0);
+      // Scores leave in groups: lane (set index mod g) of a slot keeps the score
+      // of its set and the slot's g lanes store a full group at once.
+      float mine = 0.f;
+      int mine_set = -1;
+      auto flush = [&]() {
+        if (mine_set >= 0 && dst != nullptr) {
+          float* d = dst + mine_set;
+          *d = add ? (*d + mine) : mine;
+        }
+        mine_set = -1;
+      };
 
       // fold the 8-column subgroups of one loaded chunk into the running max;
       // a set that ends is summed over each query slot and written
@@ -352,10 +368,9 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
                   if (o < g) sum += other;
                 }
               }
-              if (writer) {
-                float* d = dst + cur;
-                *d = add ? (*d + sum) : sum;
-              }
+              const int j = cur & (g - 1);
+              if ((lane & (g - 1)) == j) { mine = sum; mine_set = cur; }
+              if (j == g - 1) flush();
               ++cur;
               run = -INFINITY;
             }
@@ -384,18 +399,17 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
           if (lane == 0) mbar_arrive(&acc_empty[acc]);
         }
         // Sets are padded to multiples of kRowAlign rows, so a set ends only at
-        // the end of an 8-column subgroup.  Lane l checks whether set win + l
-        // ends inside this tile; the warp ORs the answers into one bit per
-        // subgroup.  At most N / 8 <= 32 sets end inside a tile.
-        const int64_t ts = r0 + (int64_t)t * C::N;
-        const int64_t te = min(ts + (int64_t)C::N, r1);
-        if (cur + C::N / kRowAlign > win + 32) {
-          win = cur;
-          e_win = (win + lane < d1) ? a.doc_off[win + lane + 1] : INT64_MAX;
+        // the end of an 8-column subgroup: one bit per subgroup, cut at the
+        // chunk's last row (the next chunk's sets are not this unit's).
+        uint32_t ends = bits;
+        {
+          const int64_t n_sub = (r1 - r0) / kRowAlign - (int64_t)t * (C::N / kRowAlign);
+          if (n_sub < 32) ends &= (1u << n_sub) - 1u;
         }
-        uint32_t bit = 0;
-        if (win + lane >= cur && e_win <= te) bit = 1u << (int)((e_win - ts) / kRowAlign - 1);
-        const uint32_t ends = __reduce_or_sync(0xffffffffu, bit);
+        // the same in every lane; the reduction makes that visible to the
+        // compiler, so the per-subgroup tests below are uniform branches
+        ends = __reduce_or_sync(0xffffffffu, ends);
+        if (t + 1 < ntiles) bits = load_bits(t + 1);
         fold(v, 0, ends, sc);
         if constexpr (C::N > CH) {
           tmem_ld_cols<CH>(tcol + CH, v);
@@ -411,6 +425,7 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
         }
         if (++acc == 2) { acc = 0; acc_phase ^= 1; }
       }
+      flush();  // the unit's last, partial group
     }
   }
 
@@ -438,11 +453,11 @@ gem_status launch_tc(const gem_store* s, gem_workspace* ws, const CUtensorMap& t
   a.part_query = ws->d_part_query;
   a.part_g = ws->d_part_g;
   a.part_pass = ws->d_part_pass;
-  a.part_slot = ws->d_part_slot;
   a.q_scale = ws->d_qpack_scale;
   a.qpack = FP8 ? reinterpret_cast<const uint32_t*>(ws->d_qpack_fp8)
                 : reinterpret_cast<const uint32_t*>(ws->d_qpack_bf16);
   a.doc_off = s->d_pad_offsets;
+  a.end_bits = s->d_end_bits;
   a.chunk_doc = cm->d_chunk_doc;
   a.n_chunks = cm->n_chunks;
   a.n_sets = s->n_sets;
