@@ -321,7 +321,12 @@ def run_gem(args, dist, rank, world, local):
     pool_off = torch.arange(B + 1, dtype=torch.int64, device=dev) * R
     pool_sc = torch.empty(B * R, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
-    schedule = gem.autotune_score_all(store, ws, q, qo, "bf16", scores=scores)
+    if args.schedule:
+        mt, var, cr = args.schedule.split(",")
+        gem.set_schedule(ws, int(mt), int(cr), variant=var)
+        schedule = {"m_tiles": int(mt), "variant": var, "chunk_rows": int(cr), "fixed": True}
+    else:
+        schedule = gem.autotune_score_all(store, ws, q, qo, "bf16", scores=scores)
 
     def step(ev=None):
         if ev:
@@ -394,7 +399,7 @@ def run_gem(args, dist, rank, world, local):
                    "topk_rerank_topk_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in evs)},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "tc_score_all_kernel<%d,false> (+ query packing)" % schedule["m_tiles"],
+                     "kernel": "tc_score_all_kernel<%d,bf16,%s> (+ query packing)" % (schedule["m_tiles"], schedule["variant"]),
                      "peak_kind": f"{peak_kind} bf16 burst"},
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -428,6 +433,8 @@ def main():
     ap.add_argument("--cpu-queries", type=int, default=4, help="queries the FP64 oracle scores (ground truth)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-row stage measurements")
+    ap.add_argument("--schedule", default="", help="fixed tensor-core schedule 'm_tiles,variant,chunk_rows' "
+                    "instead of the autotuner (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         # the oracle runs on host cores only: rank 0 times it, other ranks exit

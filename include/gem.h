@@ -60,6 +60,13 @@ typedef enum {
                        vector replaced by its centroid (the quantized estimate) */
 } gem_dtype;
 
+/* Launch variants of the tensor-core scoring kernels (gem_workspace_set_schedule). */
+typedef enum {
+  GEM_TC_PLAIN = 0,    /* query block in shared memory, one set of epilogue warps */
+  GEM_TC_A_TMEM = 1,   /* query block in tensor memory (m_tiles = 2) */
+  GEM_TC_TWO_SETS = 2  /* two sets of epilogue warps on alternate tiles (m_tiles = 2) */
+} gem_tc_variant;
+
 /* Which copies of the vectors a store keeps (bit mask). */
 enum {
   GEM_KEEP_F32 = 1u,   /* FP32 master copy (needed by GEM_F32 scoring and the rerank) */
@@ -169,12 +176,17 @@ void gem_workspace_destroy(gem_workspace* ws);
  * autotuner varies; results do not depend on them):
  *   m_tiles     resident query rows per CTA / 128: 1, 2 or 4 (document tile
  *               width 256 / m_tiles columns)
- *   a_in_tmem   1: the query rows live in tensor memory and the MMAs read only
+ *   variant     GEM_TC_PLAIN: query rows in shared memory, one set of 4 *
+ *               m_tiles epilogue warps;
+ *               GEM_TC_A_TMEM: the query rows live in tensor memory and the MMAs read only
  *               the document tile from shared memory (m_tiles = 2 only; tile
- *               width 96)
+ *               width 96);
+ *               GEM_TC_TWO_SETS: two sets of epilogue warps take alternate tiles
+ *               (m_tiles = 2 only)
+ *   default: m_tiles 2, GEM_TC_PLAIN, chunk_rows 2^16
  *   chunk_rows  document rows per work unit (whole sets; 1024 .. 2^24)
  */
-gem_status gem_workspace_set_schedule(gem_workspace* ws, int32_t m_tiles, int32_t a_in_tmem, int32_t chunk_rows);
+gem_status gem_workspace_set_schedule(gem_workspace* ws, int32_t m_tiles, int32_t variant, int32_t chunk_rows);
 
 /*
  * Exact CH of every query set against every stored set (Eq. 1 for all P in D,
@@ -330,7 +342,8 @@ void gem_batch_destroy(gem_batch* batch);
  * synchronise `stream`.
  *
  * gem_autotune_score_all: schedules of gem_score_all for compute GEM_BF16 or
- * GEM_FP8_E4M3 ((m_tiles, a_in_tmem) in {(2,0), (4,0), (2,1), (1,0)} x
+ * GEM_FP8_E4M3 ((m_tiles, variant) in {(2, TWO_SETS), (2, PLAIN), (4, PLAIN),
+ * (2, A_TMEM), (1, PLAIN)} x
  * chunk_rows in {2^14, 2^16, 2^18}); the choice is applied to `ws` (as
  * gem_workspace_set_schedule).  scores float32 [n_queries * n_sets] is scratch
  * for the timing runs.
@@ -338,7 +351,7 @@ void gem_batch_destroy(gem_batch* batch);
 gem_status gem_autotune_score_all(const gem_store* store, gem_workspace* ws, const float* q,
                                   const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
                                   int32_t compute, float* scores, const char* cache_path, int32_t* m_tiles,
-                                  int32_t* a_in_tmem, int32_t* chunk_rows, float* ms, int32_t* from_cache,
+                                  int32_t* variant, int32_t* chunk_rows, float* ms, int32_t* from_cache,
                                   void* stream);
 
 /*

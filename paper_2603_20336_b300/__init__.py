@@ -221,10 +221,16 @@ def search_host(store: Store, ws: Workspace, q_host, q_offsets_host, compute="bf
     return out_ids, out_scores
 
 
-def set_schedule(ws: Workspace, m_tiles: int = 2, chunk_rows: int = 1 << 16, a_in_tmem: bool = False):
+TC_VARIANTS = {"plain": 0, "a_tmem": 1, "two_sets": 2}
+
+
+def set_schedule(ws: Workspace, m_tiles: int = 2, chunk_rows: int = 1 << 16, variant: str = None):
     """Tensor-core kernel schedule of a workspace (results do not depend on it).
-    a_in_tmem keeps the query rows in tensor memory (m_tiles = 2 only)."""
-    _check(lib.gem_workspace_set_schedule(ws.handle, m_tiles, int(bool(a_in_tmem)), chunk_rows))
+    variant: "plain", "a_tmem" (query rows in tensor memory) or "two_sets" (two
+    sets of epilogue warps); the last two need m_tiles = 2."""
+    if variant is None:
+        variant = "plain"
+    _check(lib.gem_workspace_set_schedule(ws.handle, m_tiles, TC_VARIANTS[variant], chunk_rows))
 
 
 def assign_codes(x, centroids, with_best: bool = False, stream=None):
@@ -374,7 +380,7 @@ class MaxSimFn(torch.autograd.Function):
 def autotune_score_all(store: Store, ws: Workspace, q, q_offsets, compute="bf16", scores=None, cache_path=None,
                        stream=None):
     """Pick and apply the fastest tensor-core schedule:
-    dict(m_tiles, a_in_tmem, chunk_rows, ms, from_cache)."""
+    dict(m_tiles, variant, chunk_rows, ms, from_cache)."""
     q, qo, B, rows = _queries(q, q_offsets)
     if scores is None:
         scores = torch.empty((B, store.n_sets), dtype=torch.float32, device=q.device)
@@ -384,7 +390,8 @@ def autotune_score_all(store: Store, ws: Workspace, q, q_offsets, compute="bf16"
                                       _ptr(scores), cache_path.encode() if cache_path else None, ctypes.byref(mt),
                                       ctypes.byref(at), ctypes.byref(cr), ctypes.byref(ms), ctypes.byref(fc),
                                       _stream(stream)))
-    return {"m_tiles": mt.value, "a_in_tmem": bool(at.value), "chunk_rows": cr.value, "ms": ms.value,
+    names = {v: k for k, v in TC_VARIANTS.items()}
+    return {"m_tiles": mt.value, "variant": names[at.value], "chunk_rows": cr.value, "ms": ms.value,
             "from_cache": bool(fc.value)}
 
 

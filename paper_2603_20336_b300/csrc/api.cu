@@ -433,13 +433,14 @@ gem_status gem_store_set_codebook(gem_store* s, const float* centroids, int32_t 
   return GEM_OK;
 }
 
-gem_status gem_workspace_set_schedule(gem_workspace* w, int32_t m_tiles, int32_t a_in_tmem, int32_t chunk_rows) {
+gem_status gem_workspace_set_schedule(gem_workspace* w, int32_t m_tiles, int32_t variant, int32_t chunk_rows) {
   if (!w) return fail(GEM_ERR_INVALID, "workspace is NULL");
   if (m_tiles != 1 && m_tiles != 2 && m_tiles != 4) return fail(GEM_ERR_INVALID, "m_tiles must be 1, 2 or 4");
-  if (a_in_tmem && m_tiles != 2) return fail(GEM_ERR_INVALID, "a_in_tmem needs m_tiles = 2");
+  if (variant < GEM_TC_PLAIN || variant > GEM_TC_TWO_SETS) return fail(GEM_ERR_INVALID, "unknown variant");
+  if (variant != GEM_TC_PLAIN && m_tiles != 2) return fail(GEM_ERR_INVALID, "this variant needs m_tiles = 2");
   if (chunk_rows < 1024 || chunk_rows > (1 << 24)) return fail(GEM_ERR_INVALID, "chunk_rows out of range");
   w->tc_m_tiles = m_tiles;
-  w->tc_a_tmem = a_in_tmem ? 1 : 0;
+  w->tc_variant = variant;
   w->tc_chunk_rows = chunk_rows;
   return GEM_OK;
 }
@@ -468,14 +469,14 @@ static gem_status score_all_impl(const gem_store* s, gem_workspace* w, const flo
     const int mt = w->tc_m_tiles;
     gem_status r = launch_plan(w, q, q_offsets, n_queries, n_q_rows, 128 * mt, compute, st);
     if (r != GEM_OK) return r;
-    return launch_tc_score_all(s, w, compute, mt, w->tc_a_tmem, w->tc_chunk_rows, scores, st);
+    return launch_tc_score_all(s, w, compute, mt, w->tc_variant, w->tc_chunk_rows, scores, st);
   }
   if (compute == GEM_FP8_E4M3) {
     if (!s->d_fp8) return fail(GEM_ERR_STATE, "store keeps no fp8 copy");
     const int mt = w->tc_m_tiles;
     gem_status r = launch_plan(w, q, q_offsets, n_queries, n_q_rows, 128 * mt, compute, st);
     if (r != GEM_OK) return r;
-    return launch_tc_score_all(s, w, compute, mt, w->tc_a_tmem, w->tc_chunk_rows, scores, st);
+    return launch_tc_score_all(s, w, compute, mt, w->tc_variant, w->tc_chunk_rows, scores, st);
   }
   return fail(GEM_ERR_INVALID, "unknown compute dtype");
 }
@@ -701,17 +702,17 @@ void gem_batch_destroy(gem_batch* b) { batch_destroy(b); }
 gem_status gem_autotune_score_all(const gem_store* s, gem_workspace* w, const float* q,
                                   const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
                                   int32_t compute, float* scores, const char* cache_path, int32_t* m_tiles,
-                                  int32_t* a_in_tmem, int32_t* chunk_rows, float* ms, int32_t* from_cache,
+                                  int32_t* variant, int32_t* chunk_rows, float* ms, int32_t* from_cache,
                                   void* stream) {
   gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
   if (r != GEM_OK) return r;
-  if (!scores || !m_tiles || !a_in_tmem || !chunk_rows || !ms || !from_cache)
+  if (!scores || !m_tiles || !variant || !chunk_rows || !ms || !from_cache)
     return fail(GEM_ERR_INVALID, "NULL argument");
   if (compute == GEM_BF16 && !s->d_bf16) return fail(GEM_ERR_STATE, "store keeps no bf16 copy");
   if (compute == GEM_FP8_E4M3 && !s->d_fp8) return fail(GEM_ERR_STATE, "store keeps no fp8 copy");
   if (compute != GEM_BF16 && compute != GEM_FP8_E4M3) return fail(GEM_ERR_INVALID, "compute must be bf16 or fp8");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  r = autotune_score_all(s, w, q, q_offsets, n_queries, n_q_rows, compute, scores, cache_path, m_tiles, a_in_tmem,
+  r = autotune_score_all(s, w, q, q_offsets, n_queries, n_q_rows, compute, scores, cache_path, m_tiles, variant,
                          chunk_rows, ms, from_cache, st);
   if (r == GEM_OK) GEM_CUDA_TRY(cudaStreamSynchronize(st));
   return r;

@@ -136,7 +136,7 @@ gem_status time_ms(F&& run, cudaStream_t st, int reps, double* ms) {
 
 gem_status autotune_score_all(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
                               int32_t n_queries, int64_t n_q_rows, int32_t compute, float* scores,
-                              const char* cache_file, int32_t* m_tiles, int32_t* a_in_tmem, int32_t* chunk_rows,
+                              const char* cache_file, int32_t* m_tiles, int32_t* variant, int32_t* chunk_rows,
                               float* ms_out, int32_t* from_cache, cudaStream_t st) {
   const std::string path = cache_path(cache_file);
   std::ostringstream key;
@@ -149,17 +149,18 @@ gem_status autotune_score_all(const gem_store* s, gem_workspace* w, const float*
     if (it != m.end()) {
       w->tc_m_tiles = it->second.a;
       w->tc_chunk_rows = it->second.b;
-      w->tc_a_tmem = it->second.c;
+      w->tc_variant = it->second.c;
       *m_tiles = it->second.a;
       *chunk_rows = it->second.b;
-      *a_in_tmem = it->second.c;
+      *variant = it->second.c;
       *ms_out = (float)it->second.ms;
       *from_cache = 1;
       return GEM_OK;
     }
   }
-  // (m_tiles, query rows in tensor memory)
-  const int shapes[][2] = {{2, 0}, {4, 0}, {2, 1}, {1, 0}};
+  // (m_tiles, variant)
+  const int shapes[][2] = {{2, GEM_TC_TWO_SETS}, {2, GEM_TC_PLAIN}, {4, GEM_TC_PLAIN}, {2, GEM_TC_A_TMEM},
+                           {1, GEM_TC_PLAIN}};
   const int crs[] = {1 << 14, 1 << 16, 1 << 18};
   double best = 1e30;
   int bm = 2, ba = 0, bc = 1 << 16;
@@ -169,7 +170,7 @@ gem_status autotune_score_all(const gem_store* s, gem_workspace* w, const float*
     const int mt = sh[0], at = sh[1];
     for (int cr : crs) {
       w->tc_m_tiles = mt;
-      w->tc_a_tmem = at;
+      w->tc_variant = at;
       w->tc_chunk_rows = cr;
       double ms = 0.0;
       gem_status r = time_ms(
@@ -185,10 +186,10 @@ gem_status autotune_score_all(const gem_store* s, gem_workspace* w, const float*
     }
   }
   w->tc_m_tiles = bm;
-  w->tc_a_tmem = ba;
+  w->tc_variant = ba;
   w->tc_chunk_rows = bc;
   *m_tiles = bm;
-  *a_in_tmem = ba;
+  *variant = ba;
   *chunk_rows = bc;
   *ms_out = (float)best;
   *from_cache = 0;

@@ -88,7 +88,7 @@ struct gem_workspace {
   int32_t max_k = 0;
   int n_passes = 0;
   int tc_m_tiles = 2;          // schedule of the tensor-core kernels
-  int tc_a_tmem = 0;
+  int tc_variant = GEM_TC_PLAIN;
   int tc_chunk_rows = 1 << 16;
 
   int* d_status = nullptr;
@@ -196,7 +196,7 @@ gem_status launch_plan(gem_workspace* ws, const float* q, const int64_t* q_offse
 
 // Tensor-core exact MaxSim over all stored sets.
 gem_status launch_tc_score_all(const gem_store* s, gem_workspace* ws, int compute, int m_tiles,
-                               int a_tmem, int chunk_rows, float* scores, cudaStream_t st);
+                               int variant, int chunk_rows, float* scores, cudaStream_t st);
 
 // FP32 SIMT exact MaxSim (Kahan over query vectors), all sets or id lists;
 // qcodes != nullptr selects the codes form (centroids in place of vectors).
@@ -225,7 +225,7 @@ gem_status batch_run(gem_batch* bt, int32_t n_queries, int64_t n_q_rows, int64_t
 void batch_destroy(gem_batch* bt);
 gem_status autotune_score_all(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
                               int32_t n_queries, int64_t n_q_rows, int32_t compute, float* scores,
-                              const char* cache_file, int32_t* m_tiles, int32_t* a_in_tmem, int32_t* chunk_rows, float* ms_out,
+                              const char* cache_file, int32_t* m_tiles, int32_t* variant, int32_t* chunk_rows, float* ms_out,
                               int32_t* from_cache, cudaStream_t st);
 gem_status autotune_batch(const gem_store* s, int32_t mode, int32_t n_queries, int64_t n_q_rows, int32_t max_q_len,
                           int64_t n_cands, float* q, int64_t* q_offsets, int64_t* cand_offsets, int64_t* cand_ids,

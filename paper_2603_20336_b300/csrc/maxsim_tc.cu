@@ -39,7 +39,11 @@ namespace {
 // epilogue warps once per unit, so the MMAs read only the document tile from
 // shared memory; the tile narrows so that accumulators and A share the 512
 // TMEM columns (bf16 MT=2: 2 x 2 x 96 + 2 x 64; e4m3 MT=2: 2 x 2 x 96 + 2 x 32).
-template <int MT, bool FP8, bool AT = false>
+// E: sets of 4 * MT epilogue warps; set e takes the tiles t with t % E == e of
+// every unit (E = 2: each set owns one accumulator buffer), so more warps hide
+// the epilogue's latencies; the running max of a set that crosses a tile
+// boundary passes from set to set through shared memory.
+template <int MT, bool FP8, bool AT = false, int E = 1>
 struct TcCfg {
   static constexpr int M_RES = 128 * MT;
   static constexpr int A_COLS = AT ? (FP8 ? 32 : 64) : 0;  // TMEM columns of A per M tile
@@ -47,6 +51,7 @@ struct TcCfg {
   // access starts on a 32-column boundary)
   static constexpr int N = AT ? 96 : 256 / MT;  // columns per tile
   static_assert(!AT || MT == 2, "A in tensor memory is laid out for two M tiles");
+  static_assert(E == 1 || (E == 2 && !AT), "two epilogue sets only with A in shared memory");
   static constexpr int ROW_BYTES = FP8 ? 128 : 256;
   static constexpr int HALVES = FP8 ? 1 : 2;      // 128-byte swizzle atoms per row
   static constexpr int K_STEP = FP8 ? 32 : 16;    // K per MMA instruction
@@ -59,13 +64,22 @@ struct TcCfg {
   // (the operand stage is recycled as soon as the MMA has read it)
   static constexpr int SC_SLOTS = FP8 ? 8 : 0;
   static constexpr int SC_BYTES = SC_SLOTS * N * 4;
-  static constexpr int EPI_WARPS = 4 * MT;
+  static constexpr int EPI_SET = 4 * MT;          // epilogue warps per set
+  static constexpr int EPI_WARPS = E * EPI_SET;
   static constexpr int THREADS = (EPI_WARPS + 2) * 32;
+  // accumulator columns per TMEM load (two sets: 18 warps leave 96 registers a
+  // thread, so 32 columns at a time)
+  static constexpr int CH = E > 1 ? 32 : (N < 128 ? N : 128);
+  static constexpr int CARRY_BYTES = E > 1 ? E * EPI_SET * 32 * 4 : 0;
+  static constexpr int BASE_BYTES = 1024 /*align slack*/ + Q_BYTES + STAGES * STAGE_BYTES + SC_BYTES + CARRY_BYTES;
+  static constexpr int N_BARS = 2 * STAGES + 7 + 2 * SC_SLOTS + (E > 1 ? 2 * E * EPI_SET : 0);
+  static constexpr int BAR_BYTES = (N_BARS * 8 + 16 + 127) / 128 * 128;
   static constexpr int ACC_COLS = MT * N;         // per accumulator buffer
   static constexpr int A_BASE = 2 * ACC_COLS;     // first TMEM column of A (AT)
   static constexpr int TMEM_COLS = 512;
   static_assert(A_BASE + MT * A_COLS <= TMEM_COLS, "TMEM over-committed");
-  static constexpr int SMEM_BYTES = 1024 /*align slack*/ + Q_BYTES + STAGES * STAGE_BYTES + SC_BYTES + 512;
+  static constexpr int SMEM_BYTES = BASE_BYTES + BAR_BYTES;
+  static_assert(SMEM_BYTES <= 232448, "shared memory over the per-block limit");
   static constexpr uint32_t IDESC = make_idesc(128, N, FP8 ? 0u : 1u, FP8 ? 0u : 1u);
 };
 
@@ -87,17 +101,37 @@ struct TcArgs {
   int* status;
 };
 
-template <int MT, bool FP8, bool AT>
-__global__ void __launch_bounds__(TcCfg<MT, FP8, AT>::THREADS, 1)
+// o[s] for a warp-uniform s < L, by a tree of selects on the bits of s (the
+// array stays in registers).
+template <int L>
+__device__ __forceinline__ float pick(const float (&o)[L], int s) {
+  constexpr int P = L <= 2 ? 2 : (L <= 4 ? 4 : (L <= 8 ? 8 : (L <= 16 ? 16 : 32)));
+  static_assert(L <= 32, "at most 32 subgroups per tile");
+  float a[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) a[i] = i < L ? o[i] : o[0];
+#pragma unroll
+  for (int w = P / 2, b = 0; w >= 1; w /= 2, ++b) {
+    const bool hi = (s >> b) & 1;
+#pragma unroll
+    for (int i = 0; i < w; ++i) a[i] = hi ? a[2 * i + 1] : a[2 * i];
+  }
+  return a[0];
+}
+
+template <int MT, bool FP8, bool AT, int E>
+__global__ void __launch_bounds__(TcCfg<MT, FP8, AT, E>::THREADS, 1)
 tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_d,
                     const __grid_constant__ CUtensorMap tm_scale, TcArgs a) {
-  using C = TcCfg<MT, FP8, AT>;
+  using C = TcCfg<MT, FP8, AT, E>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* q_smem = smem;
   uint8_t* d_smem = smem + C::Q_BYTES;
   float* sc_smem = reinterpret_cast<float*>(d_smem + C::STAGES * C::STAGE_BYTES);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(d_smem + C::STAGES * C::STAGE_BYTES + C::SC_BYTES);
+  float* carry_smem = reinterpret_cast<float*>(d_smem + C::STAGES * C::STAGE_BYTES + C::SC_BYTES);
+  uint64_t* bars =
+      reinterpret_cast<uint64_t*>(d_smem + C::STAGES * C::STAGE_BYTES + C::SC_BYTES + C::CARRY_BYTES);
   uint64_t* full = bars;
   uint64_t* empty = bars + C::STAGES;
   uint64_t* acc_full = bars + 2 * C::STAGES;
@@ -107,7 +141,9 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
   uint64_t* done_bar = q_empty + 1;
   uint64_t* sc_full = done_bar + 1;
   uint64_t* sc_empty = sc_full + C::SC_SLOTS;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sc_empty + C::SC_SLOTS);
+  uint64_t* carry_full = sc_empty + C::SC_SLOTS;                        // [E][EPI_SET] (E > 1)
+  uint64_t* carry_empty = carry_full + (E > 1 ? E * C::EPI_SET : 0);   // [E][EPI_SET]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(carry_empty + (E > 1 ? E * C::EPI_SET : 0));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5;
@@ -119,11 +155,13 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], C::EPI_WARPS); }
-    mbar_init(q_full, AT ? C::EPI_WARPS : 1);
+    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], C::EPI_SET); }
+    mbar_init(q_full, AT ? C::EPI_SET : 1);
     mbar_init(q_empty, 1);
     mbar_init(done_bar, 1);
-    for (int s = 0; s < C::SC_SLOTS; ++s) { mbar_init(&sc_full[s], 1); mbar_init(&sc_empty[s], C::EPI_WARPS); }
+    for (int s = 0; s < C::SC_SLOTS; ++s) { mbar_init(&sc_full[s], 1); mbar_init(&sc_empty[s], C::EPI_SET); }
+    if constexpr (E > 1)
+      for (int i = 0; i < E * C::EPI_SET; ++i) { mbar_init(&carry_full[i], 32); mbar_init(&carry_empty[i], 32); }
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -250,10 +288,23 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
     }
   } else {
     // ---------------------------------------------------------------- epilogue
-    const int m_tile = warp >> 2;
-    const int quad = warp & 3;
+    constexpr int CH = C::CH;
+    constexpr int NSUB = C::N / kRowAlign;  // 8-column subgroups per tile
+    const int eset = warp / C::EPI_SET;     // this warp takes the tiles t with t % E == eset
+    const int wpos = warp % C::EPI_SET;
+    const int m_tile = wpos >> 2;
+    const int quad = wpos & 3;              // = warp % 4: the TMEM lane quarter this warp may read
     const int local_row = m_tile * 128 + quad * 32 + lane;
     const uint32_t t_lane = (uint32_t)(quad * 32) << 16;
+    // carries between sets (E > 1): this set writes slot eset, reads the previous set's slot
+    const int prev_set = (eset + E - 1) % E;
+    float* carry_out_buf = carry_smem + (eset * C::EPI_SET + wpos) * 32;
+    float* carry_in_buf = carry_smem + (prev_set * C::EPI_SET + wpos) * 32;
+    uint64_t* cfull_out = carry_full + eset * C::EPI_SET + wpos;
+    uint64_t* cempty_out = carry_empty + eset * C::EPI_SET + wpos;
+    uint64_t* cfull_in = carry_full + prev_set * C::EPI_SET + wpos;
+    uint64_t* cempty_in = carry_empty + prev_set * C::EPI_SET + wpos;
+    uint32_t n_pub = 0, n_recv = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
     int sslot = 0;
@@ -298,21 +349,20 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
       const int64_t r0 = a.doc_off[d0];
       const int64_t r1 = a.doc_off[d1];
       const int ntiles = (int)((r1 - r0 + C::N - 1) / C::N);
-      (void)d1;
-      int cur = d0;
-      float run = -INFINITY;
-      constexpr int CH = C::N < 128 ? C::N : 128;  // columns per TMEM load
+      int cur = d0;           // index of the next set to end
+      float carry = -INFINITY;  // E = 1: running max entering the next tile
       // Set ends come from the store's end bitmap (bit i: a set ends with padded
       // row 8 i + 7).  The bits of tile t + 1 are loaded while tile t is folded.
       const int64_t sg_first = r0 / kRowAlign;
       auto load_bits = [&](int t) -> uint32_t {
-        const int64_t gs = sg_first + (int64_t)t * (C::N / kRowAlign);
+        const int64_t gs = sg_first + (int64_t)t * NSUB;
         const uint32_t* w = a.end_bits + (gs >> 5);
         return (uint32_t)((((uint64_t)__ldg(w + 1) << 32) | __ldg(w)) >> (gs & 31));
       };
       uint32_t bits = load_bits(0);
       // Scores leave in groups: lane (set index mod g) of a slot keeps the score
-      // of its set and the slot's g lanes store a full group at once.
+      // of its set, and the kept scores are stored together when the group is
+      // complete or the next group begins.
       float mine = 0.f;
       int mine_set = -1;
       auto flush = [&]() {
@@ -323,62 +373,103 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
         mine_set = -1;
       };
 
-      // fold the 8-column subgroups of one loaded chunk into the running max;
-      // a set that ends is summed over each query slot and written
-      // (fp8: each column is first multiplied by its vector's scale s_j, read
-      // as a broadcast from the tile's scale slot).  Columns past the chunk's
-      // last row (the next chunk's rows or the tensor map's zero fill) are
-      // folded too, without a bounds branch: no set ends there, and the
-      // running max is dropped when the unit ends.
+      // A set that ends: sum its row maxima over each query slot and keep the
+      // score.  A 32-row slot whose row maxima are all below 2 in magnitude is
+      // summed in 2^-24 fixed point by one warp reduction (|sum| < 2^30, exact
+      // and independent of the order; rounding <= 2^-25 per row), any other
+      // slot by a g-lane xor butterfly.
+      auto set_end = [&](float m) {
+        const float val = m * row_scale;
+        float sum;
+        if (__all_sync(0xffffffffu, g == 32 && fabsf(val) < 2.f)) {
+          sum = (float)__reduce_add_sync(0xffffffffu, __float2int_rn(val * 16777216.f)) * (1.f / 16777216.f);
+        } else {
+          sum = val;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float other = __shfl_xor_sync(0xffffffffu, sum, o);
+            if (o < g) sum += other;
+          }
+        }
+        if (mine_set >= 0 && ((mine_set ^ cur) & ~(g - 1)) != 0) flush();  // another group
+        const int j = cur & (g - 1);
+        if ((lane & (g - 1)) == j) { mine = sum; mine_set = cur; }
+        if (j == g - 1) flush();
+        ++cur;
+      };
+
+      // Fold the 8-column subgroups of one loaded chunk into the running max,
+      // branch-free: out[s] is the running max after subgroup s, and the max
+      // restarts after a subgroup that ends a set.  fp8: each column is first
+      // multiplied by its vector's scale s_j, read as a broadcast from the
+      // tile's scale slot.  Columns past the chunk's last row (the next chunk's
+      // rows or the tensor map's zero fill) are folded too: no set ends there.
+      float run = -INFINITY;
+      float out[NSUB];
       auto fold = [&](const float (&v)[CH], int sg0, uint32_t ends, const float* sc) {
 #pragma unroll
         for (int s = 0; s < CH / 8; ++s) {
-          const int sg = sg0 + s;
-          {
-            float x[8];
-            if constexpr (FP8) {
-              const float4 s0 = reinterpret_cast<const float4*>(sc)[2 * s];
-              const float4 s1 = reinterpret_cast<const float4*>(sc)[2 * s + 1];
-              const float2 p0 = fmul2(make_float2(v[8 * s + 0], v[8 * s + 1]), make_float2(s0.x, s0.y));
-              const float2 p1 = fmul2(make_float2(v[8 * s + 2], v[8 * s + 3]), make_float2(s0.z, s0.w));
-              const float2 p2 = fmul2(make_float2(v[8 * s + 4], v[8 * s + 5]), make_float2(s1.x, s1.y));
-              const float2 p3 = fmul2(make_float2(v[8 * s + 6], v[8 * s + 7]), make_float2(s1.z, s1.w));
-              x[0] = p0.x; x[1] = p0.y; x[2] = p1.x; x[3] = p1.y;
-              x[4] = p2.x; x[5] = p2.y; x[6] = p3.x; x[7] = p3.y;
-            } else {
+          float x[8];
+          if constexpr (FP8) {
+            const float4 s0 = reinterpret_cast<const float4*>(sc)[2 * s];
+            const float4 s1 = reinterpret_cast<const float4*>(sc)[2 * s + 1];
+            const float2 p0 = fmul2(make_float2(v[8 * s + 0], v[8 * s + 1]), make_float2(s0.x, s0.y));
+            const float2 p1 = fmul2(make_float2(v[8 * s + 2], v[8 * s + 3]), make_float2(s0.z, s0.w));
+            const float2 p2 = fmul2(make_float2(v[8 * s + 4], v[8 * s + 5]), make_float2(s1.x, s1.y));
+            const float2 p3 = fmul2(make_float2(v[8 * s + 6], v[8 * s + 7]), make_float2(s1.z, s1.w));
+            x[0] = p0.x; x[1] = p0.y; x[2] = p1.x; x[3] = p1.y;
+            x[4] = p2.x; x[5] = p2.y; x[6] = p3.x; x[7] = p3.y;
+          } else {
 #pragma unroll
-              for (int j = 0; j < 8; ++j) x[j] = v[8 * s + j];
-            }
-            run = fmax3(run, fmax3(x[0], x[1], x[2]), fmax3(x[3], x[4], x[5]));
-            run = fmax3(run, x[6], x[7]);
-            if ((ends >> sg) & 1u) {
-              const float val = run * row_scale;
-              float sum;
-              if (__all_sync(0xffffffffu, g == 32 && fabsf(val) < 2.f)) {
-                // one 32-row slot with every row maximum below 2 in magnitude:
-                // sum in 2^-24 fixed point with one warp reduction (|sum| < 2^30,
-                // exact and independent of the order; rounding <= 2^-25 per row)
-                const int iv = __float2int_rn(val * 16777216.f);
-                sum = (float)__reduce_add_sync(0xffffffffu, iv) * (1.f / 16777216.f);
-              } else {
-                sum = val;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                  const float other = __shfl_xor_sync(0xffffffffu, sum, o);
-                  if (o < g) sum += other;
-                }
-              }
-              const int j = cur & (g - 1);
-              if ((lane & (g - 1)) == j) { mine = sum; mine_set = cur; }
-              if (j == g - 1) flush();
-              ++cur;
-              run = -INFINITY;
-            }
+            for (int j = 0; j < 8; ++j) x[j] = v[8 * s + j];
           }
+          run = fmax3(run, fmax3(x[0], x[1], x[2]), fmax3(x[3], x[4], x[5]));
+          run = fmax3(run, x[6], x[7]);
+          out[sg0 + s] = run;
+          run = ((ends >> (sg0 + s)) & 1u) ? -INFINITY : run;
         }
+      };
+      // E > 1: hand the running max entering tile t + 1 to the next set / take
+      // the one entering tile t from the previous set (bounded waits; every
+      // lane passes its own row)
+      auto publish = [&](float val) -> bool {
+        const bool w = mbar_wait(cempty_out, (n_pub & 1) ^ 1, a.status, abort_flag);
+        if (!__all_sync(0xffffffffu, w)) return false;
+        carry_out_buf[lane] = val;
+        mbar_arrive(cfull_out);
+        ++n_pub;
+        return true;
+      };
+      auto receive = [&](float& val) -> bool {
+        const bool w = mbar_wait(cfull_in, n_recv & 1, a.status, abort_flag);
+        if (!__all_sync(0xffffffffu, w)) return false;
+        val = carry_in_buf[lane];
+        mbar_arrive(cempty_in);
+        ++n_recv;
+        return true;
       };
 
       for (int t = 0; t < ntiles; ++t) {
+        // Sets are padded to multiples of kRowAlign rows, so a set ends only at
+        // the end of an 8-column subgroup: one bit per subgroup, cut at the
+        // chunk's last row (the next chunk's sets are not this unit's).
+        uint32_t ends = bits;
+        {
+          const int64_t n_sub = (r1 - r0) / kRowAlign - (int64_t)t * NSUB;
+          if (n_sub < 32) ends &= (1u << n_sub) - 1u;
+          if (NSUB < 32) ends &= (1u << (NSUB & 31)) - 1u;
+        }
+        // the same in every lane; the reduction makes that visible to the
+        // compiler, so the tests below are uniform branches
+        ends = __reduce_or_sync(0xffffffffu, ends);
+        if (t + 1 < ntiles) bits = load_bits(t + 1);
+        if (E > 1 && t % E != eset) {
+          // another set's tile: only the set count and the ring positions move
+          cur += __popc(ends);
+          if constexpr (FP8) { if (++sslot == C::SC_SLOTS) { sslot = 0; sphase ^= 1; } }
+          if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+          continue;
+        }
         // every lane waits, then the warp agrees, so the .sync.aligned TMEM
         // loads below always run with the whole warp
         bool got = mbar_wait(&acc_full[acc], acc_phase, a.status, abort_flag);
@@ -390,33 +481,17 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
         tc_fence_after();
         const float* sc = FP8 ? sc_smem + sslot * C::N : nullptr;
         const uint32_t tcol = tmem + t_lane + acc * C::ACC_COLS + m_tile * C::N;
-        float v[CH];
-        tmem_ld_cols<CH>(tcol, v);
-        if constexpr (C::N == CH) {
-          // the accumulator is in registers: hand the buffer back to the MMA warp
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&acc_empty[acc]);
-        }
-        // Sets are padded to multiples of kRowAlign rows, so a set ends only at
-        // the end of an 8-column subgroup: one bit per subgroup, cut at the
-        // chunk's last row (the next chunk's sets are not this unit's).
-        uint32_t ends = bits;
-        {
-          const int64_t n_sub = (r1 - r0) / kRowAlign - (int64_t)t * (C::N / kRowAlign);
-          if (n_sub < 32) ends &= (1u << n_sub) - 1u;
-        }
-        // the same in every lane; the reduction makes that visible to the
-        // compiler, so the per-subgroup tests below are uniform branches
-        ends = __reduce_or_sync(0xffffffffu, ends);
-        if (t + 1 < ntiles) bits = load_bits(t + 1);
-        fold(v, 0, ends, sc);
-        if constexpr (C::N > CH) {
-          tmem_ld_cols<CH>(tcol + CH, v);
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&acc_empty[acc]);
-          fold(v, CH / 8, ends, FP8 ? sc + CH : nullptr);
+#pragma unroll
+        for (int c = 0; c < C::N / CH; ++c) {
+          float v[CH];
+          tmem_ld_cols<CH>(tcol + c * CH, v);
+          if (c == C::N / CH - 1) {
+            // the accumulator is in registers: hand the buffer back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[acc]);
+          }
+          fold(v, c * (CH / 8), ends, FP8 ? sc + c * CH : nullptr);
         }
         if constexpr (FP8) {
           __syncwarp();
@@ -424,8 +499,33 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
           if (++sslot == C::SC_SLOTS) { sslot = 0; sphase ^= 1; }
         }
         if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+        // run: the max since this tile's last set end (or over the whole tile)
+        float cin = -INFINITY;
+        if constexpr (E > 1) {
+          const bool more = t + 1 < ntiles;
+          bool fine = true;
+          if (ends != 0 && more) fine = publish(run);
+          if (fine && t > 0) fine = receive(cin);
+          if (fine && ends == 0 && more) fine = publish(fmaxf(cin, run));
+          if (!fine) {
+            ok = false;
+            break;
+          }
+        } else {
+          cin = carry;
+          carry = ends != 0 ? run : fmaxf(carry, run);
+        }
+        run = -INFINITY;
+        uint32_t e = ends;
+#pragma unroll 1
+        while (e) {
+          const int sidx = __ffs(e) - 1;
+          e &= e - 1;
+          set_end(fmaxf(cin, pick(out, sidx)));
+          cin = -INFINITY;
+        }
       }
-      flush();  // the unit's last, partial group
+      flush();  // the scores this warp still keeps
     }
   }
 
@@ -436,14 +536,14 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
   }
 }
 
-template <int MT, bool FP8, bool AT = false>
+template <int MT, bool FP8, bool AT = false, int E = 1>
 gem_status launch_tc(const gem_store* s, gem_workspace* ws, const CUtensorMap& tm_q,
                      const CUtensorMap& tm_d, const CUtensorMap& tm_scale, const ChunkMap* cm,
                      float* scores, cudaStream_t st) {
-  using C = TcCfg<MT, FP8, AT>;
+  using C = TcCfg<MT, FP8, AT, E>;
   static bool attr_set = false;
   if (!attr_set) {
-    GEM_CUDA_TRY(cudaFuncSetAttribute(tc_score_all_kernel<MT, FP8, AT>,
+    GEM_CUDA_TRY(cudaFuncSetAttribute(tc_score_all_kernel<MT, FP8, AT, E>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
     attr_set = true;
   }
@@ -465,47 +565,44 @@ gem_status launch_tc(const gem_store* s, gem_workspace* ws, const CUtensorMap& t
   a.status = ws->d_status;
   for (int pass = 0; pass < ws->n_passes; ++pass) {
     a.pass = pass;
-    tc_score_all_kernel<MT, FP8, AT><<<s->n_sm, C::THREADS, C::SMEM_BYTES, st>>>(tm_q, tm_d, tm_scale, a);
+    tc_score_all_kernel<MT, FP8, AT, E><<<s->n_sm, C::THREADS, C::SMEM_BYTES, st>>>(tm_q, tm_d, tm_scale, a);
     GEM_CUDA_TRY(cudaGetLastError());
     note_launches(1);
   }
   return GEM_OK;
 }
 
+template <bool FP8>
+gem_status launch_tc_dtype(const gem_store* s, gem_workspace* ws, int m_tiles, int variant, const ChunkMap* cm,
+                           float* scores, cudaStream_t st) {
+  const int n = variant == GEM_TC_A_TMEM ? TcCfg<2, FP8, true>::N : 256 / m_tiles;
+  const CUtensorMap* td = nullptr;
+  const CUtensorMap* tsc = nullptr;
+  gem_status r = FP8 ? store_tmap_fp8(s, n, &td) : store_tmap_bf16(s, n, &td);
+  if (r != GEM_OK) return r;
+  if (FP8 && (r = store_tmap_fp8_scale(s, n, &tsc)) != GEM_OK) return r;
+  if (!FP8) tsc = td;  // unused
+  const CUtensorMap& tq = FP8 ? ws->tmap_q_fp8 : ws->tmap_q_bf16;
+  if (variant == GEM_TC_A_TMEM) return launch_tc<2, FP8, true>(s, ws, tq, *td, *tsc, cm, scores, st);
+  if (variant == GEM_TC_TWO_SETS) return launch_tc<2, FP8, false, 2>(s, ws, tq, *td, *tsc, cm, scores, st);
+  switch (m_tiles) {
+    case 1: return launch_tc<1, FP8>(s, ws, tq, *td, *tsc, cm, scores, st);
+    case 2: return launch_tc<2, FP8>(s, ws, tq, *td, *tsc, cm, scores, st);
+    case 4: return launch_tc<4, FP8>(s, ws, tq, *td, *tsc, cm, scores, st);
+    default: return fail(GEM_ERR_INVALID, "m_tiles must be 1, 2 or 4");
+  }
+}
+
 }  // namespace
 
 gem_status launch_tc_score_all(const gem_store* s, gem_workspace* ws, int compute, int m_tiles,
-                               int a_tmem, int chunk_rows, float* scores, cudaStream_t st) {
+                               int variant, int chunk_rows, float* scores, cudaStream_t st) {
   const ChunkMap* cm = nullptr;
   gem_status r = store_chunk_map(s, chunk_rows, &cm);
   if (r != GEM_OK) return r;
-  if (a_tmem && m_tiles != 2) return fail(GEM_ERR_INVALID, "A in tensor memory needs m_tiles = 2");
-  if (compute == GEM_BF16) {
-    const int n = a_tmem ? TcCfg<2, false, true>::N : 256 / m_tiles;
-    const CUtensorMap* td = nullptr;
-    if ((r = store_tmap_bf16(s, n, &td)) != GEM_OK) return r;
-    if (a_tmem) return launch_tc<2, false, true>(s, ws, ws->tmap_q_bf16, *td, *td, cm, scores, st);
-    switch (m_tiles) {
-      case 1: return launch_tc<1, false>(s, ws, ws->tmap_q_bf16, *td, *td, cm, scores, st);
-      case 2: return launch_tc<2, false>(s, ws, ws->tmap_q_bf16, *td, *td, cm, scores, st);
-      case 4: return launch_tc<4, false>(s, ws, ws->tmap_q_bf16, *td, *td, cm, scores, st);
-      default: return fail(GEM_ERR_INVALID, "m_tiles must be 1, 2 or 4");
-    }
-  }
-  if (compute == GEM_FP8_E4M3) {
-    const int n = a_tmem ? TcCfg<2, true, true>::N : 256 / m_tiles;
-    const CUtensorMap* td = nullptr;
-    const CUtensorMap* tsc = nullptr;
-    if ((r = store_tmap_fp8(s, n, &td)) != GEM_OK) return r;
-    if ((r = store_tmap_fp8_scale(s, n, &tsc)) != GEM_OK) return r;
-    if (a_tmem) return launch_tc<2, true, true>(s, ws, ws->tmap_q_fp8, *td, *tsc, cm, scores, st);
-    switch (m_tiles) {
-      case 1: return launch_tc<1, true>(s, ws, ws->tmap_q_fp8, *td, *tsc, cm, scores, st);
-      case 2: return launch_tc<2, true>(s, ws, ws->tmap_q_fp8, *td, *tsc, cm, scores, st);
-      case 4: return launch_tc<4, true>(s, ws, ws->tmap_q_fp8, *td, *tsc, cm, scores, st);
-      default: return fail(GEM_ERR_INVALID, "m_tiles must be 1, 2 or 4");
-    }
-  }
+  if (variant != GEM_TC_PLAIN && m_tiles != 2) return fail(GEM_ERR_INVALID, "this variant needs m_tiles = 2");
+  if (compute == GEM_BF16) return launch_tc_dtype<false>(s, ws, m_tiles, variant, cm, scores, st);
+  if (compute == GEM_FP8_E4M3) return launch_tc_dtype<true>(s, ws, m_tiles, variant, cm, scores, st);
   return fail(GEM_ERR_INVALID, "tensor-core scoring takes bf16 or fp8");
 }
 

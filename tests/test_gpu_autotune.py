@@ -68,12 +68,13 @@ def test_every_schedule_bit_identical(gem):
     q, qo = w.queries.vecs.cuda(), torch.from_numpy(w.queries.offsets).cuda()
     for compute in ("bf16", "fp8"):
         outs = []
-        for mt, at, cr in ((2, True, 1 << 16), (2, False, 1 << 16), (4, False, 1 << 14), (1, False, 1 << 18),
-                           (2, True, 1 << 14)):
-            gem.set_schedule(ws, mt, cr, a_in_tmem=at)
+        for mt, var, cr in ((2, "two_sets", 1 << 16), (2, "plain", 1 << 16), (2, "a_tmem", 1 << 16),
+                            (4, "plain", 1 << 14), (1, "plain", 1 << 18), (2, "a_tmem", 1 << 14),
+                            (2, "two_sets", 1 << 14)):
+            gem.set_schedule(ws, mt, cr, variant=var)
             outs.append(gem.score_all(store, ws, q, qo, compute).clone())
             assert ws.status() == 0
         for o in outs[1:]:
             assert torch.equal(o, outs[0])
     with pytest.raises(Exception):
-        gem.set_schedule(ws, 4, 1 << 16, a_in_tmem=True)
+        gem.set_schedule(ws, 4, 1 << 16, variant="a_tmem")
