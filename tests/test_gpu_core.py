@@ -174,6 +174,38 @@ def test_score_ids_f32_matches_oracle(gem, cfg1):
             assert S[t] == S_all[b, ids[t]]
 
 
+def test_score_ids_streamed_rerank_bit_matches(gem, cfg1):
+    """Queries of at most 32 rows take the streamed id-list kernel (set vectors
+    gathered ahead across pairs); it must give the bits of the per-pair kernel
+    (taken with a workspace for longer queries) and match the oracle.  60,000
+    pairs: every warp crosses several 32-pair windows; -1 ids and empty lists
+    included."""
+    w = cfg1["w"]
+    rng = np.random.default_rng(11)
+    B = 10
+    lens = rng.integers(0, 12000, size=B)
+    lens[3] = 0
+    co = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    ids = rng.integers(-1, w.docs.n_sets, size=int(co[-1])).astype(np.int64)
+    ws32 = gem.Workspace(cfg1["store"], max_queries=64, max_q_rows=4096, max_q_len=32, max_cands=int(co[-1]))
+    args = (cfg1["q"], cfg1["qo"], torch.from_numpy(co).cuda(), torch.from_numpy(ids).cuda(), "f32")
+    S32 = gem.score_ids(cfg1["store"], ws32, *args).cpu().numpy()
+    assert ws32.status() == 0
+    wsl = gem.Workspace(cfg1["store"], max_queries=64, max_q_rows=4096, max_q_len=128, max_cands=int(co[-1]))
+    Sl = gem.score_ids(cfg1["store"], wsl, *args).cpu().numpy()
+    np.testing.assert_array_equal(S32.view(np.uint32), Sl.view(np.uint32))
+    b_of = np.repeat(np.arange(B), lens)
+    pick = rng.choice(len(ids), size=300, replace=False)
+    for t in pick:
+        if ids[t] < 0:
+            assert S32[t] == -np.inf
+        else:
+            want = cfg1["S64"][b_of[t], ids[t]]
+            assert abs(S32[t] - want) <= 1e-5 * cfg1["L1"][b_of[t], ids[t]]
+    ws32.close()
+    wsl.close()
+
+
 def test_score_ids_out_of_range_id_sets_status(gem, cfg1):
     co = torch.tensor([0, 2] + [2] * 9, dtype=torch.int64, device="cuda")
     ids = torch.tensor([0, 10**6], dtype=torch.int64, device="cuda")
