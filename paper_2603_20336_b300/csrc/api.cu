@@ -437,7 +437,8 @@ gem_status gem_workspace_set_schedule(gem_workspace* w, int32_t m_tiles, int32_t
   if (!w) return fail(GEM_ERR_INVALID, "workspace is NULL");
   if (m_tiles != 1 && m_tiles != 2 && m_tiles != 4) return fail(GEM_ERR_INVALID, "m_tiles must be 1, 2 or 4");
   if (variant < GEM_TC_PLAIN || variant > GEM_TC_TWO_SETS) return fail(GEM_ERR_INVALID, "unknown variant");
-  if (variant != GEM_TC_PLAIN && m_tiles != 2) return fail(GEM_ERR_INVALID, "this variant needs m_tiles = 2");
+  if (variant == GEM_TC_A_TMEM && m_tiles != 2) return fail(GEM_ERR_INVALID, "a_tmem needs m_tiles = 2");
+  if (variant == GEM_TC_TWO_SETS && m_tiles == 4) return fail(GEM_ERR_INVALID, "two_sets needs m_tiles 1 or 2");
   if (chunk_rows < 1024 || chunk_rows > (1 << 24)) return fail(GEM_ERR_INVALID, "chunk_rows out of range");
   w->tc_m_tiles = m_tiles;
   w->tc_variant = variant;

@@ -67,9 +67,9 @@ struct TcCfg {
   static constexpr int EPI_SET = 4 * MT;          // epilogue warps per set
   static constexpr int EPI_WARPS = E * EPI_SET;
   static constexpr int THREADS = (EPI_WARPS + 2) * 32;
-  // accumulator columns per TMEM load (two sets: 18 warps leave 96 registers a
-  // thread, so 32 columns at a time)
-  static constexpr int CH = E > 1 ? 32 : (N < 128 ? N : 128);
+  // accumulator columns per TMEM load (more than 12 warps leave at most 96
+  // registers a thread, so 32 columns at a time)
+  static constexpr int CH = EPI_WARPS + 2 > 12 ? 32 : (E > 1 ? 64 : (N < 128 ? N : 128));
   static constexpr int CARRY_BYTES = E > 1 ? E * EPI_SET * 32 * 4 : 0;
   static constexpr int BASE_BYTES = 1024 /*align slack*/ + Q_BYTES + STAGES * STAGE_BYTES + SC_BYTES + CARRY_BYTES;
   static constexpr int N_BARS = 2 * STAGES + 7 + 2 * SC_SLOTS + (E > 1 ? 2 * E * EPI_SET : 0);
@@ -248,19 +248,22 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
         const int ntiles = (int)((r1 - r0 + C::N - 1) / C::N);
         if (!mbar_wait(q_full, it & 1, a.status, abort_flag)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t q_base = smem_u32(q_smem);
+        const uint64_t ad0 = sw128_desc(smem_u32(q_smem));
         for (int t = 0; t < ntiles; ++t) {
           if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1, a.status, abort_flag)) { ok = false; break; }
           if (!mbar_wait(&full[stage], phase, a.status, abort_flag)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t d_base = smem_u32(d_smem + stage * C::STAGE_BYTES);
+          // descriptors: the start-address field (bits 0-13, address / 16) of a
+          // base descriptor plus a compile-time offset (shared addresses stay
+          // below 2^18 bytes, so the field never carries)
+          const uint64_t bd0 = sw128_desc(smem_u32(d_smem + stage * C::STAGE_BYTES));
 #pragma unroll
           for (int m = 0; m < MT; ++m) {
 #pragma unroll
             for (int k = 0; k < C::K_STEPS; ++k) {
               const int half = (k * C::K_STEP * (FP8 ? 1 : 2)) / 128;
               const int within = (k * C::K_STEP * (FP8 ? 1 : 2)) % 128;
-              uint64_t bd = sw128_desc(d_base + half * (C::N * 128) + within);
+              const uint64_t bd = bd0 + (uint64_t)((half * (C::N * 128) + within) >> 4);
               const uint32_t dt = tmem + acc * C::ACC_COLS + m * C::N;
               if constexpr (AT) {
                 // A: 128 lanes x (K_STEP elements = 8 columns of 32-bit words) per step
@@ -268,7 +271,7 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
                 if constexpr (FP8) mma_f8_ta(dt, at, bd, C::IDESC, k > 0);
                 else mma_bf16_ta(dt, at, bd, C::IDESC, k > 0);
               } else {
-                uint64_t ad = sw128_desc(q_base + (m * C::HALVES + half) * 16384 + within);
+                const uint64_t ad = ad0 + (uint64_t)((((m * C::HALVES + half) * 16384) + within) >> 4);
                 if constexpr (FP8) mma_f8(dt, ad, bd, C::IDESC, k > 0);
                 else mma_bf16(dt, ad, bd, C::IDESC, k > 0);
               }
@@ -584,7 +587,10 @@ gem_status launch_tc_dtype(const gem_store* s, gem_workspace* ws, int m_tiles, i
   if (!FP8) tsc = td;  // unused
   const CUtensorMap& tq = FP8 ? ws->tmap_q_fp8 : ws->tmap_q_bf16;
   if (variant == GEM_TC_A_TMEM) return launch_tc<2, FP8, true>(s, ws, tq, *td, *tsc, cm, scores, st);
-  if (variant == GEM_TC_TWO_SETS) return launch_tc<2, FP8, false, 2>(s, ws, tq, *td, *tsc, cm, scores, st);
+  if (variant == GEM_TC_TWO_SETS) {
+    if (m_tiles == 1) return launch_tc<1, FP8, false, 2>(s, ws, tq, *td, *tsc, cm, scores, st);
+    return launch_tc<2, FP8, false, 2>(s, ws, tq, *td, *tsc, cm, scores, st);
+  }
   switch (m_tiles) {
     case 1: return launch_tc<1, FP8>(s, ws, tq, *td, *tsc, cm, scores, st);
     case 2: return launch_tc<2, FP8>(s, ws, tq, *td, *tsc, cm, scores, st);
@@ -600,7 +606,8 @@ gem_status launch_tc_score_all(const gem_store* s, gem_workspace* ws, int comput
   const ChunkMap* cm = nullptr;
   gem_status r = store_chunk_map(s, chunk_rows, &cm);
   if (r != GEM_OK) return r;
-  if (variant != GEM_TC_PLAIN && m_tiles != 2) return fail(GEM_ERR_INVALID, "this variant needs m_tiles = 2");
+  if (variant == GEM_TC_A_TMEM && m_tiles != 2) return fail(GEM_ERR_INVALID, "a_tmem needs m_tiles = 2");
+  if (variant == GEM_TC_TWO_SETS && m_tiles == 4) return fail(GEM_ERR_INVALID, "two_sets needs m_tiles 1 or 2");
   if (compute == GEM_BF16) return launch_tc_dtype<false>(s, ws, m_tiles, variant, cm, scores, st);
   if (compute == GEM_FP8_E4M3) return launch_tc_dtype<true>(s, ws, m_tiles, variant, cm, scores, st);
   return fail(GEM_ERR_INVALID, "tensor-core scoring takes bf16 or fp8");

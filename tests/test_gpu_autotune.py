@@ -68,7 +68,7 @@ def test_every_schedule_bit_identical(gem):
     q, qo = w.queries.vecs.cuda(), torch.from_numpy(w.queries.offsets).cuda()
     for compute in ("bf16", "fp8"):
         outs = []
-        for mt, var, cr in ((2, "two_sets", 1 << 16), (2, "plain", 1 << 16), (2, "a_tmem", 1 << 16),
+        for mt, var, cr in ((2, "two_sets", 1 << 16), (2, "plain", 1 << 16), (2, "a_tmem", 1 << 16), (1, "two_sets", 1 << 16),
                             (4, "plain", 1 << 14), (1, "plain", 1 << 18), (2, "a_tmem", 1 << 14),
                             (2, "two_sets", 1 << 14)):
             gem.set_schedule(ws, mt, cr, variant=var)
