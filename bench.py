@@ -31,6 +31,12 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# tc_score_all_kernel<2,bf16,plain> on the text-500k workload: mean of three
+# launches in one ncu capture (23.00/21.47/24.46 GB read, 2.03 GB written).
+# Set to None when that kernel changes, until it is captured again.
+TC_TRAFFIC_BYTES_TEXT500K = 25.0e9
+
 WORKLOADS = {
     "text": dict(n_sets=500_000, n_queries=1000, rerank=1000, k=100),
     "small": dict(n_sets=20_000, n_queries=100, rerank=1000, k=100),
@@ -398,7 +404,11 @@ def run_gem(args, dist, rank, world, local):
         "stages": {"maxsim_bf16_ms": k1_ms,
                    "topk_rerank_topk_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in evs)},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (TC_TRAFFIC_BYTES_TEXT500K
+                                 if args.workload == "text" and schedule["m_tiles"] == 2
+                                 and schedule["variant"] == "plain" else None),
+                     "algorithmic_bytes": store.n_pad_vecs * 256 + n_pairs * 4,
                      "kernel": "tc_score_all_kernel<%d,bf16,%s> (+ query packing)" % (schedule["m_tiles"], schedule["variant"]),
                      "peak_kind": f"{peak_kind} bf16 burst"},
         "gpu_launches": int(launches),
