@@ -14,8 +14,9 @@
 //   warp 4*MT          TMA producer: query block once per unit, then the
 //                      chunk's document tiles (N rows x 128) through a
 //                      STAGES-deep shared-memory ring
-//   warp 4*MT+1        MMA issuer: per tile, MT x (K/16) tcgen05.mma into a
-//                      double-buffered TMEM accumulator (2 x MT x N columns)
+//   warp 4*MT+1 (..)   MMA issuer(s): per tile, MT x (K/16) tcgen05.mma into a
+//                      double-buffered TMEM accumulator (2 x MT x N columns);
+//                      with MT >= 2 two issuers on alternate M tiles
 //
 // Epilogue: every thread walks its row's N accumulator columns in order.  The
 // low-precision store copies pad each set to a multiple of 8 rows with copies of
@@ -66,13 +67,16 @@ struct TcCfg {
   static constexpr int SC_BYTES = SC_SLOTS * N * 4;
   static constexpr int EPI_SET = 4 * MT;          // epilogue warps per set
   static constexpr int EPI_WARPS = E * EPI_SET;
-  static constexpr int THREADS = (EPI_WARPS + 2) * 32;
+  // MMA issuer warps: with two or more M tiles, two issuers (on different SM
+  // sub-partitions) take alternate M tiles, each with its own accumulator barriers
+  static constexpr int NMW = (MT >= 2 && !AT) ? 2 : 1;
+  static constexpr int THREADS = (EPI_WARPS + 1 + NMW) * 32;
   // accumulator columns per TMEM load (more than 12 warps leave at most 96
   // registers a thread, so 32 columns at a time)
-  static constexpr int CH = EPI_WARPS + 2 > 12 ? 32 : (E > 1 ? 64 : (N < 128 ? N : 128));
+  static constexpr int CH = EPI_WARPS + 1 + NMW > 12 ? 32 : (E > 1 ? 64 : (N < 128 ? N : 128));
   static constexpr int CARRY_BYTES = E > 1 ? E * EPI_SET * 32 * 4 : 0;
   static constexpr int BASE_BYTES = 1024 /*align slack*/ + Q_BYTES + STAGES * STAGE_BYTES + SC_BYTES + CARRY_BYTES;
-  static constexpr int N_BARS = 2 * STAGES + 7 + 2 * SC_SLOTS + (E > 1 ? 2 * E * EPI_SET : 0);
+  static constexpr int N_BARS = 2 * STAGES + 4 * NMW + 2 + NMW + 2 * SC_SLOTS + (E > 1 ? 2 * E * EPI_SET : 0);
   static constexpr int BAR_BYTES = (N_BARS * 8 + 16 + 127) / 128 * 128;
   static constexpr int ACC_COLS = MT * N;         // per accumulator buffer
   static constexpr int A_BASE = 2 * ACC_COLS;     // first TMEM column of A (AT)
@@ -134,12 +138,12 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
       reinterpret_cast<uint64_t*>(d_smem + C::STAGES * C::STAGE_BYTES + C::SC_BYTES + C::CARRY_BYTES);
   uint64_t* full = bars;
   uint64_t* empty = bars + C::STAGES;
-  uint64_t* acc_full = bars + 2 * C::STAGES;
-  uint64_t* acc_empty = acc_full + 2;
-  uint64_t* q_full = acc_empty + 2;
+  uint64_t* acc_full = bars + 2 * C::STAGES;    // [2 buffers][NMW]
+  uint64_t* acc_empty = acc_full + 2 * C::NMW;  // [2 buffers][NMW]
+  uint64_t* q_full = acc_empty + 2 * C::NMW;
   uint64_t* q_empty = q_full + 1;
-  uint64_t* done_bar = q_empty + 1;
-  uint64_t* sc_full = done_bar + 1;
+  uint64_t* done_bar = q_empty + 1;             // [NMW]
+  uint64_t* sc_full = done_bar + C::NMW;
   uint64_t* sc_empty = sc_full + C::SC_SLOTS;
   uint64_t* carry_full = sc_empty + C::SC_SLOTS;                        // [E][EPI_SET] (E > 1)
   uint64_t* carry_empty = carry_full + (E > 1 ? E * C::EPI_SET : 0);   // [E][EPI_SET]
@@ -154,11 +158,11 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
   if (blockIdx.x >= n_units) return;  // uniform for the CTA
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < C::STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], C::EPI_SET); }
+    for (int s = 0; s < C::STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], C::NMW); }
+    for (int i = 0; i < 2 * C::NMW; ++i) { mbar_init(&acc_full[i], 1); mbar_init(&acc_empty[i], C::EPI_SET / C::NMW); }
     mbar_init(q_full, AT ? C::EPI_SET : 1);
-    mbar_init(q_empty, 1);
-    mbar_init(done_bar, 1);
+    mbar_init(q_empty, C::NMW);
+    for (int w = 0; w < C::NMW; ++w) mbar_init(&done_bar[w], 1);
     for (int s = 0; s < C::SC_SLOTS; ++s) { mbar_init(&sc_full[s], 1); mbar_init(&sc_empty[s], C::EPI_SET); }
     if constexpr (E > 1)
       for (int i = 0; i < E * C::EPI_SET; ++i) { mbar_init(&carry_full[i], 32); mbar_init(&carry_empty[i], 32); }
@@ -232,8 +236,10 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
         if (q_issued) mbar_wait(q_full, (q_issued - 1) & 1, nullptr, &z);
       }
     }
-  } else if (warp == C::EPI_WARPS + 1) {
-    // ---------------------------------------------------------------- MMA issuer
+  } else if (warp > C::EPI_WARPS) {
+    // ---------------------------------------------------------------- MMA issuer(s)
+    // warp mw issues the MMAs of the M tiles m with m % NMW == mw
+    const int mw = warp - C::EPI_WARPS - 1;
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
@@ -250,7 +256,7 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
         tc_fence_after();
         const uint64_t ad0 = sw128_desc(smem_u32(q_smem));
         for (int t = 0; t < ntiles; ++t) {
-          if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1, a.status, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&acc_empty[acc * C::NMW + mw], acc_phase ^ 1, a.status, abort_flag)) { ok = false; break; }
           if (!mbar_wait(&full[stage], phase, a.status, abort_flag)) { ok = false; break; }
           tc_fence_after();
           // descriptors: the start-address field (bits 0-13, address / 16) of a
@@ -258,7 +264,8 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
           // below 2^18 bytes, so the field never carries)
           const uint64_t bd0 = sw128_desc(smem_u32(d_smem + stage * C::STAGE_BYTES));
 #pragma unroll
-          for (int m = 0; m < MT; ++m) {
+          for (int mi = 0; mi < MT / C::NMW; ++mi) {
+            const int m = mi * C::NMW + mw;
 #pragma unroll
             for (int k = 0; k < C::K_STEPS; ++k) {
               const int half = (k * C::K_STEP * (FP8 ? 1 : 2)) / 128;
@@ -278,16 +285,16 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
             }
           }
           mma_commit(&empty[stage]);
-          mma_commit(&acc_full[acc]);
+          mma_commit(&acc_full[acc * C::NMW + mw]);
           if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
           if (++acc == 2) { acc = 0; acc_phase ^= 1; }
         }
         if (ok && !AT) mma_commit(q_empty);
       }
       // all MMAs of this thread complete before the CTA releases TMEM
-      mma_commit(done_bar);
+      mma_commit(&done_bar[mw]);
       int z = 0;
-      mbar_wait(done_bar, 0, nullptr, &z);
+      mbar_wait(&done_bar[mw], 0, nullptr, &z);
     }
   } else {
     // ---------------------------------------------------------------- epilogue
@@ -475,7 +482,7 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
         }
         // every lane waits, then the warp agrees, so the .sync.aligned TMEM
         // loads below always run with the whole warp
-        bool got = mbar_wait(&acc_full[acc], acc_phase, a.status, abort_flag);
+        bool got = mbar_wait(&acc_full[acc * C::NMW + m_tile % C::NMW], acc_phase, a.status, abort_flag);
         if constexpr (FP8) got = got && mbar_wait(&sc_full[sslot], sphase, a.status, abort_flag);
         if (!__all_sync(0xffffffffu, got)) {
           ok = false;
@@ -492,7 +499,7 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
             // the accumulator is in registers: hand the buffer back to the MMA warp
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[acc]);
+            if (lane == 0) mbar_arrive(&acc_empty[acc * C::NMW + m_tile % C::NMW]);
           }
           fold(v, c * (CH / 8), ends, FP8 ? sc + c * CH : nullptr);
         }
