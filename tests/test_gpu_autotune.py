@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -59,22 +60,35 @@ def test_autotune_batch_choice_bit_matches(gem, tmp_path):
                               cache_path=str(tmp_path / "b.json"))["from_cache"]
 
 
-def test_every_schedule_bit_identical(gem):
+@pytest.mark.parametrize("qlens", ["32", "mixed"])
+def test_every_schedule_bit_identical(gem, qlens):
     """The tensor-core schedules (resident query rows, query rows in tensor
-    memory or shared memory, chunk size) only change the launch shape."""
+    memory or shared memory, epilogue sets, MMA issuers, chunk size) only
+    change the launch shape.  "mixed": queries of 1..100 rows, so slots of every
+    size and up to four passes that add onto the previous pass's scores."""
     w = synth.exact_fp32(n_sets=2500, n_queries=37)
     store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("bf16", "fp8"))
-    ws = gem.Workspace(store, max_queries=64, max_q_rows=64 * 32, max_q_len=32)
-    q, qo = w.queries.vecs.cuda(), torch.from_numpy(w.queries.offsets).cuda()
+    if qlens == "mixed":
+        lens = np.random.default_rng(3).integers(1, 101, size=37)
+        qs = synth.vector_sets(lens, synth.centres(64, 1235), 5150)
+        q, qo = qs.vecs.cuda(), torch.from_numpy(qs.offsets).cuda()
+        ws = gem.Workspace(store, max_queries=64, max_q_rows=int(lens.sum()), max_q_len=128)
+    else:
+        q, qo = w.queries.vecs.cuda(), torch.from_numpy(w.queries.offsets).cuda()
+        ws = gem.Workspace(store, max_queries=64, max_q_rows=64 * 32, max_q_len=32)
     for compute in ("bf16", "fp8"):
         outs = []
-        for mt, var, cr in ((2, "two_sets", 1 << 16), (2, "plain", 1 << 16), (2, "a_tmem", 1 << 16), (1, "two_sets", 1 << 16),
-                            (4, "plain", 1 << 14), (1, "plain", 1 << 18), (2, "a_tmem", 1 << 14),
-                            (2, "two_sets", 1 << 14)):
+        for mt, var, cr in ((2, "two_sets", 1 << 16), (2, "plain", 1 << 16), (2, "a_tmem", 1 << 16),
+                            (1, "two_sets", 1 << 16), (4, "plain", 1 << 14), (1, "plain", 1 << 18),
+                            (2, "a_tmem", 1 << 14), (2, "two_sets", 1 << 14)):
             gem.set_schedule(ws, mt, cr, variant=var)
             outs.append(gem.score_all(store, ws, q, qo, compute).clone())
             assert ws.status() == 0
         for o in outs[1:]:
             assert torch.equal(o, outs[0])
+        if qlens == "mixed" and compute == "bf16":
+            Sq = oracle.score_all(oracle.bf16_round(qs.vecs.numpy()), qs.offsets,
+                                  oracle.bf16_round(w.docs.vecs.numpy()), w.docs.offsets)
+            assert np.all(np.abs(outs[0].cpu().numpy() - Sq) <= 2e-4 * lens[:, None])
     with pytest.raises(Exception):
         gem.set_schedule(ws, 4, 1 << 16, variant="a_tmem")
