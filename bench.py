@@ -33,9 +33,9 @@ import synth  # noqa: E402
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
 # tc_score_all_kernel<2,bf16,plain> on the text-500k workload: mean of three
-# launches in one ncu capture (38.71/39.96/31.03 GB read, 2.02 GB written).
+# launches in one ncu capture (9.417/9.414/9.419 GB read, 2.00 GB written).
 # Set to None when that kernel changes, until it is captured again.
-TC_TRAFFIC_BYTES_TEXT500K = 38.6e9
+TC_TRAFFIC_BYTES_TEXT500K = 11.41e9
 
 WORKLOADS = {
     "text": dict(n_sets=500_000, n_queries=1000, rerank=1000, k=100),

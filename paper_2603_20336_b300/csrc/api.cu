@@ -250,7 +250,7 @@ void gem_workspace_destroy(gem_workspace* w) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(w->device);
-  void* ptrs[] = {w->d_status, w->d_plan_hdr, w->d_part_query, w->d_part_rows, w->d_part_g,
+  void* ptrs[] = {w->d_status, w->d_unit_counter, w->d_plan_hdr, w->d_part_query, w->d_part_rows, w->d_part_g,
                   w->d_part_pass, w->d_part_slot, w->d_part_row0, w->d_row_part, w->d_qpack_bf16,
                   w->d_qpack_fp8, w->d_qpack_scale, w->d_scores, w->d_pool_ids, w->d_pool_off,
                   w->d_pool_scores, w->d_q_in, w->d_qo_in, w->d_out_ids, w->d_out_scores,
@@ -293,6 +293,7 @@ gem_status gem_workspace_create(const gem_store* s, int32_t max_queries, int64_t
     return r;                                                               \
   }
   WS_ALLOC(d_status, 1);
+  WS_ALLOC(d_unit_counter, 1);
   WS_ALLOC(d_plan_hdr, kPlanHdrInts);
   WS_ALLOC(d_part_query, w->max_parts);
   WS_ALLOC(d_part_rows, w->max_parts);

@@ -92,6 +92,7 @@ struct gem_workspace {
   int tc_chunk_rows = 1 << 16;
 
   int* d_status = nullptr;
+  int* d_unit_counter = nullptr;  // work-unit counter of the tensor-core kernels
 
   // query plan
   int64_t packed_cap = 0;  // rows of the packed query buffers

@@ -76,8 +76,10 @@ struct TcCfg {
   static constexpr int CH = EPI_WARPS + 1 + NMW > 12 ? 32 : (E > 1 ? 64 : (N < 128 ? N : 128));
   static constexpr int CARRY_BYTES = E > 1 ? E * EPI_SET * 32 * 4 : 0;
   static constexpr int BASE_BYTES = 1024 /*align slack*/ + Q_BYTES + STAGES * STAGE_BYTES + SC_BYTES + CARRY_BYTES;
-  static constexpr int N_BARS = 2 * STAGES + 4 * NMW + 2 + NMW + 2 * SC_SLOTS + (E > 1 ? 2 * E * EPI_SET : 0);
-  static constexpr int BAR_BYTES = (N_BARS * 8 + 16 + 127) / 128 * 128;
+  static constexpr int UNIT_RING = 2;  // units drawn ahead by the producer
+  static constexpr int N_BARS =
+      2 * STAGES + 4 * NMW + 2 + NMW + 2 * SC_SLOTS + (E > 1 ? 2 * E * EPI_SET : 0) + 2 * UNIT_RING;
+  static constexpr int BAR_BYTES = (N_BARS * 8 + 16 + 4 * UNIT_RING + 127) / 128 * 128;
   static constexpr int ACC_COLS = MT * N;         // per accumulator buffer
   static constexpr int A_BASE = 2 * ACC_COLS;     // first TMEM column of A (AT)
   static constexpr int TMEM_COLS = 512;
@@ -103,6 +105,7 @@ struct TcArgs {
   int64_t n_sets;
   float* scores;             // [n_queries * n_sets]
   int* status;
+  int* unit_counter;         // next unit to hand out (zeroed before every launch)
 };
 
 // o[s] for a warp-uniform s < L, by a tree of selects on the bits of s (the
@@ -147,8 +150,11 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
   uint64_t* sc_empty = sc_full + C::SC_SLOTS;
   uint64_t* carry_full = sc_empty + C::SC_SLOTS;                        // [E][EPI_SET] (E > 1)
   uint64_t* carry_empty = carry_full + (E > 1 ? E * C::EPI_SET : 0);   // [E][EPI_SET]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(carry_empty + (E > 1 ? E * C::EPI_SET : 0));
+  uint64_t* unit_full = carry_empty + (E > 1 ? E * C::EPI_SET : 0);   // [UNIT_RING]
+  uint64_t* unit_empty = unit_full + C::UNIT_RING;                     // [UNIT_RING]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(unit_empty + C::UNIT_RING);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* unit_ring = abort_flag + 1;                            // [UNIT_RING]
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -166,6 +172,10 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
     for (int s = 0; s < C::SC_SLOTS; ++s) { mbar_init(&sc_full[s], 1); mbar_init(&sc_empty[s], C::EPI_SET); }
     if constexpr (E > 1)
       for (int i = 0; i < E * C::EPI_SET; ++i) { mbar_init(&carry_full[i], 32); mbar_init(&carry_empty[i], 32); }
+    for (int i = 0; i < C::UNIT_RING; ++i) {
+      mbar_init(&unit_full[i], 1);
+      mbar_init(&unit_empty[i], C::NMW + C::EPI_WARPS);
+    }
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -190,7 +200,23 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
       int it = 0;
       uint32_t q_issued = 0;
       bool ok = true;
-      for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
+      // Units are drawn in one global order from a counter, so all CTAs work
+      // on the same few chunks (which then stay in L2), and handed to the MMA
+      // and epilogue warps through a ring in shared memory.
+      int uslot = 0;
+      uint32_t uphase = 0;
+      auto draw_unit = [&]() -> long long {
+        const long long u = atomicAdd(a.unit_counter, 1);
+        if (!mbar_wait(&unit_empty[uslot], uphase ^ 1, a.status, abort_flag)) {
+          ok = false;
+          return n_units;
+        }
+        unit_ring[uslot] = (int)(u < n_units ? u : n_units);
+        mbar_arrive(&unit_full[uslot]);
+        if (++uslot == C::UNIT_RING) { uslot = 0; uphase ^= 1; }
+        return u;
+      };
+      for (long long u = draw_unit(); u < n_units && ok; u = draw_unit(), ++it) {
         const int chunk = (int)(u / nqb);
         const int qb = qb0 + (int)(u % nqb);
         if constexpr (!AT) {
@@ -247,7 +273,19 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
       uint32_t acc_phase = 0;
       int it = 0;
       bool ok = true;
-      for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++it) {
+      int uslot = 0;
+      uint32_t uphase = 0;
+      auto take_unit = [&]() -> long long {
+        if (!mbar_wait(&unit_full[uslot], uphase, a.status, abort_flag)) {
+          ok = false;
+          return n_units;
+        }
+        const long long u = unit_ring[uslot];
+        mbar_arrive(&unit_empty[uslot]);
+        if (++uslot == C::UNIT_RING) { uslot = 0; uphase ^= 1; }
+        return u;
+      };
+      for (long long u = take_unit(); u < n_units && ok; u = take_unit(), ++it) {
         const int chunk = (int)(u / nqb);
         const int64_t r0 = a.doc_off[a.chunk_doc[chunk]];
         const int64_t r1 = a.doc_off[a.chunk_doc[chunk + 1]];
@@ -320,7 +358,21 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
     int sslot = 0;
     uint32_t sphase = 0;
     bool ok = true;
-    for (long long u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+    int uslot = 0;
+    uint32_t uphase = 0;
+    auto take_unit = [&]() -> long long {
+      const bool w = mbar_wait(&unit_full[uslot], uphase, a.status, abort_flag);
+      if (!__all_sync(0xffffffffu, w)) {
+        ok = false;
+        return n_units;
+      }
+      const long long u = unit_ring[uslot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&unit_empty[uslot]);
+      if (++uslot == C::UNIT_RING) { uslot = 0; uphase ^= 1; }
+      return u;
+    };
+    for (long long u = take_unit(); u < n_units && ok; u = take_unit()) {
       const int chunk = (int)(u / nqb);
       const int qb = qb0 + (int)(u % nqb);
       const int prow = qb * C::M_RES + local_row;
@@ -573,8 +625,10 @@ gem_status launch_tc(const gem_store* s, gem_workspace* ws, const CUtensorMap& t
   a.n_sets = s->n_sets;
   a.scores = scores;
   a.status = ws->d_status;
+  a.unit_counter = ws->d_unit_counter;
   for (int pass = 0; pass < ws->n_passes; ++pass) {
     a.pass = pass;
+    GEM_CUDA_TRY(cudaMemsetAsync(ws->d_unit_counter, 0, sizeof(int), st));
     tc_score_all_kernel<MT, FP8, AT, E><<<s->n_sm, C::THREADS, C::SMEM_BYTES, st>>>(tm_q, tm_d, tm_scale, a);
     GEM_CUDA_TRY(cudaGetLastError());
     note_launches(1);
