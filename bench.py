@@ -268,8 +268,41 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms):
         ms_b = _time(lambda: gem.maxsim_bwd(wb.queries.vecs, qo5, wb.docs.vecs, do5, po, pid, am, g))
         return {"pairs": nb * per_q, "fwd_ms": ms_f, "bwd_ms": ms_b, "doc_vectors": int(wb.docs.n_vecs)}
 
+    def pages():
+        # the multi-modal page configuration: 50,000 sets x 1,024 vectors, 500
+        # queries of 16..32 vectors; per dtype: exhaustive time, the pipeline
+        # (top-2,000, FP32 rerank, top-100) and its recall against the exact
+        # FP32 exhaustive top-100 computed on the GPU
+        wp = synth.multimodal_pages(device=dev)
+        sp = gem.Store(wp.docs.vecs, wp.docs.offsets, keep=("f32", "bf16", "fp8"))
+        del wp.docs.vecs
+        qp = wp.queries.vecs
+        qop = torch.from_numpy(wp.queries.offsets).to(dev)
+        Bp = qop.numel() - 1
+        wsp = gem.Workspace(sp, max_queries=Bp, max_q_rows=qp.shape[0], max_q_len=32, max_cands=Bp * 2000,
+                            max_k=2000)
+        outp = torch.empty((Bp, sp.n_sets), dtype=torch.float32, device=dev)
+        gem.score_all(sp, wsp, qp, qop, "f32", out=outp)
+        exact = torch.topk(outp, 100, dim=1).indices.cpu().numpy()
+        fl = 2.0 * float(wp.queries.lengths().sum()) * sp.n_vecs * 128
+        res = {"n_sets": sp.n_sets, "n_vecs": sp.n_vecs, "queries": Bp}
+        for dt in ("bf16", "fp8"):
+            ch = gem.autotune_score_all(sp, wsp, qp, qop, dt, scores=outp)
+            ms = _time(lambda: gem.score_all(sp, wsp, qp, qop, dt, out=outp))
+            ms_s = _time(lambda: gem.search(sp, wsp, qp, qop, dt, rerank_depth=2000, k=100))
+            ids, _ = gem.search(sp, wsp, qp, qop, dt, rerank_depth=2000, k=100)
+            res[dt] = {"exhaustive_ms": ms, "tflops_equiv": fl / ms / 1e9, "schedule": ch,
+                       "search_ms": ms_s, "doc_sets_per_s": Bp * sp.n_sets / (ms_s * 1e-3),
+                       "recall_at_100_vs_exact_fp32": float(np.mean(
+                           [len(set(r.tolist()) & set(e.tolist())) / 100 for r, e in zip(ids.cpu().numpy(), exact)]))}
+        res["fp32_exhaustive_ms"] = _time(lambda: gem.score_all(sp, wsp, qp, qop, "f32", out=outp), reps=1)
+        wsp.close()
+        sp.close()
+        return res
+
     guard("fp8_exhaustive", fp8)
     guard("fp32_exhaustive", fp32)
+    guard("pages_50k", pages)
     guard("qch_estimate", qch)
     guard("beam_batch", beam)
     guard("backward", backward)
