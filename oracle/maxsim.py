@@ -165,6 +165,29 @@ def assign_codes(X, C) -> np.ndarray:
     return out
 
 
+def cluster_filter(q, q_offsets, C_index, t: int):
+    """C_query of every query set (Sec. 4.5.1, Eq. 15; Algorithm 5, first two steps).
+
+    The relevance matrix S = C_index Q^T scores every coarse centroid against every
+    query vector; each query vector keeps its top-t centroids (largest inner
+    product, ties to the lower centroid index) and C_query is the union of those
+    over the query's vectors.  Returns one sorted int64 array per query set.
+    """
+    C = _f64(C_index)
+    Q = _f64(q)
+    qo = _i64(q_offsets)
+    idx = np.arange(len(C))
+    out = []
+    for b in range(len(qo) - 1):
+        S = Q[qo[b]:qo[b + 1]] @ C.T          # [m_q, k2] = (C Q^T)^T
+        chosen = set()
+        for row in S:
+            order = np.lexsort((idx, -row))   # score descending, then index ascending
+            chosen.update(int(c) for c in order[:t])
+        out.append(np.array(sorted(chosen), dtype=np.int64))
+    return out
+
+
 def qch_distance(q_codes, p_codes, C) -> float:
     """qCH(Q, P) = sum over q of min over p of d_X(NN(q), NN(p)) (Sec. 4.5.3, Eq. 16).
 

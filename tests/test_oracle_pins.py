@@ -366,3 +366,60 @@ def test_synthetic_generators_shapes_and_norms():
         assert len(set(row.tolist())) == len(row) and 64 <= len(row) <= 128
     w2 = synth.exact_fp32(n_sets=100, n_queries=3)
     assert torch.equal(w.docs.vecs, w2.docs.vecs)
+
+
+# ---------------------------------------------------------------------------
+# Cluster filter (Sec. 4.5.1, Eq. 15): C_query = union of top-t centroids
+# ---------------------------------------------------------------------------
+
+def test_cluster_filter_hand_example_and_ties():
+    # d = 2: centroids east, north, west; a query vector near east
+    C = np.array([[1.0, 0.0], [0.0, 1.0], [-1.0, 0.0]])
+    Q = np.array([[0.9, 0.1]])
+    assert oracle.cluster_filter(Q, [0, 1], C, 1)[0].tolist() == [0]
+    assert oracle.cluster_filter(Q, [0, 1], C, 2)[0].tolist() == [0, 1]
+    # equal inner products with east and north: the lower index wins
+    Qt = np.array([[1.0, 1.0]]) / np.sqrt(2.0)
+    assert oracle.cluster_filter(Qt, [0, 1], C, 1)[0].tolist() == [0]
+    # two query vectors: the union of their choices, sorted
+    Q2 = np.array([[0.9, 0.1], [-0.8, 0.3]])
+    assert oracle.cluster_filter(Q2, [0, 2], C, 1)[0].tolist() == [0, 2]
+
+
+def test_cluster_filter_t_equal_k2_selects_every_centroid():
+    rng = np.random.default_rng(21)
+    C = _unit(rng, 37, 16)
+    Q = _unit(rng, 9, 16)
+    out = oracle.cluster_filter(Q, [0, 4, 9], C, 37)
+    for o in out:
+        assert o.tolist() == list(range(37))
+
+
+def test_cluster_filter_own_rows_are_the_top_1():
+    # with the query vectors themselves among the (unit) centroids, each query
+    # vector's inner product 1 with its own copy is the unique maximum
+    rng = np.random.default_rng(22)
+    Q = _unit(rng, 6, 32)
+    C = np.concatenate([_unit(rng, 20, 32), Q, _unit(rng, 5, 32)])
+    out = oracle.cluster_filter(Q, [0, 3, 6], C, 1)
+    assert out[0].tolist() == [20, 21, 22]
+    assert out[1].tolist() == [23, 24, 25]
+
+
+def test_cluster_filter_permutation_equivariant_and_monotone_in_t():
+    rng = np.random.default_rng(23)
+    C = _unit(rng, 50, 16)
+    Q = _unit(rng, 12, 16)
+    qo = [0, 5, 12]
+    perm = rng.permutation(50)
+    inv = np.argsort(perm)
+    prev = [set() for _ in qo[1:]]
+    for t in range(1, 7):
+        base = oracle.cluster_filter(Q, qo, C, t)
+        permuted = oracle.cluster_filter(Q, qo, C[perm], t)
+        for b in range(len(base)):
+            # centroid i of the permuted matrix is centroid perm[i] of the original
+            assert sorted(perm[permuted[b]].tolist()) == base[b].tolist()
+            assert prev[b] <= set(base[b].tolist())
+            prev[b] = set(base[b].tolist())
+    assert inv[perm[3]] == 3
