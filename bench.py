@@ -221,6 +221,23 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms):
                 "pairs_per_s": nq * store.n_sets / (ms * 1e-3),
                 "recall_at_100_after_rerank": _recall(ids.cpu().numpy(), truth[:nq])}
 
+    def cluster():
+        # Sec. 4.5.1: C_index = k-means of C_quant (second stage, k2 = 2,048),
+        # then C_query of every query set with t = 4
+        if getattr(store, "k1", 0) <= 0:
+            return {"error": "no codebook (the qch stage trains it)"}
+        Cq = store.export("codebook")
+        k2, t = 2048, 4
+        t0 = time.perf_counter()
+        Ci = gem.kmeans(Cq, k2, iters=10, seed=5)
+        torch.cuda.synchronize()
+        km_s = time.perf_counter() - t0
+        ms = _time(lambda: gem.cluster_filter(q, qo, Ci, t=t, max_q_len=32))
+        _, _, cnt = gem.cluster_filter(q, qo, Ci, t=t, max_q_len=32)
+        return {"k1": int(Cq.shape[0]), "k2": k2, "t": t, "kmeans_s": km_s, "ms": ms,
+                "query_vectors_x_centroids_per_s": rows * k2 / (ms * 1e-3),
+                "tflops": 2.0 * rows * k2 * 128 / ms / 1e9, "mean_c_query": float(cnt.float().mean())}
+
     def beam():
         nq, rounds = 4096, 20
         qs = synth.vector_sets(synth.lengths_uniform(nq, 8, 64, 1238 + 7919), synth.centres(4096, 1236),
@@ -304,6 +321,7 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms):
     guard("fp32_exhaustive", fp32)
     guard("pages_50k", pages)
     guard("qch_estimate", qch)
+    guard("cluster_filter", cluster)
     guard("beam_batch", beam)
     guard("backward", backward)
 

@@ -158,6 +158,42 @@ gem_status gem_train_codebook(const gem_store* store, int32_t k1, int32_t iters,
 gem_status gem_store_set_codebook(gem_store* store, const float* centroids, int32_t k1, void* stream);
 
 /*
+ * gem_kmeans: spherical k-means (Sec. 4.1.1, two-stage clustering) of the rows
+ * of any device matrix x [n x 128] FP32; the second stage clusters the stage-1
+ * codebook C_quant (k1 rows) into k2 coarse centroids C_index.  The initial
+ * centroids are k distinct rows of x picked by a seeded shuffle; each of `iters`
+ * Lloyd steps assigns every row to its nearest centroid (largest inner product,
+ * ties to the lower index) and sets each centroid with members to the
+ * renormalised mean of its members.  centroids_out [k x 128] FP32 device,
+ * caller-owned.  Blocks until done (it frees its temporaries).
+ * Errors: GEM_ERR_INVALID (NULL, k outside 1..n, iters < 0), GEM_ERR_OOM.
+ */
+gem_status gem_kmeans(const float* x, int64_t n, int32_t k, int32_t iters, uint64_t seed, float* centroids_out,
+                      void* stream);
+
+/*
+ * gem_cluster_filter: C_query of every query set (Sec. 4.5.1, Eq. 15;
+ * Algorithm 5, first two steps).  S = C_index Q^T scores the k2 centroids
+ * against every query vector (one FP32 FMA chain over k = 0..127 per dot); each
+ * query vector keeps its top-t centroids (largest score, ties to the lower
+ * centroid index) and C_query is their union over the query set.
+ *   q [n_q_rows x 128], q_offsets [n_queries + 1]  query sets (device)
+ *   centroids [k2 x 128]                           C_index (device)
+ *   t                                              1 .. min(8, k2)
+ *   out_mask  uint32 [n_queries x ceil(k2 / 32)]   bit c of row b: centroid c in C_query(b)
+ *   out_list  int32 [n_queries x max_q_len * t]    C_query(b) ascending in row b
+ *   out_count int32 [n_queries]                    |C_query(b)|; entries past the
+ *                                                  row capacity max_q_len * t
+ *                                                  (queries longer than max_q_len)
+ *                                                  are in the mask only
+ * All buffers are device, caller-owned.  Asynchronous on `stream`.
+ * Errors: GEM_ERR_INVALID (NULL, k2 outside 1..262144, t outside 1..min(8, k2)).
+ */
+gem_status gem_cluster_filter(const float* q, const int64_t* q_offsets, int32_t n_queries, int32_t max_q_len,
+                              const float* centroids, int32_t k2, int32_t t, uint32_t* out_mask, int32_t* out_list,
+                              int32_t* out_count, void* stream);
+
+/*
  * Scratch for scoring calls against `store`.  Bounds fix the memory once:
  *   max_queries  -- query sets per call
  *   max_q_rows   -- total query vectors per call

@@ -233,6 +233,29 @@ def set_schedule(ws: Workspace, m_tiles: int = 2, chunk_rows: int = 1 << 16, var
     _check(lib.gem_workspace_set_schedule(ws.handle, m_tiles, TC_VARIANTS[variant], chunk_rows))
 
 
+def kmeans(x, k: int, iters: int = 10, seed: int = 0, stream=None):
+    """Spherical k-means of the rows of x (e.g. C_quant -> C_index, the second
+    clustering stage): float32 [k, 128] unit centroids."""
+    x = _dev(x.contiguous(), torch.float32, "x")
+    out = torch.empty((k, 128), dtype=torch.float32, device=x.device)
+    _check(lib.gem_kmeans(_ptr(x), x.shape[0], k, iters, seed, _ptr(out), _stream(stream)))
+    return out
+
+
+def cluster_filter(q, q_offsets, centroids, t: int = 4, max_q_len: int = 32, stream=None):
+    """C_query of every query set: (mask uint32 [B, ceil(k2/32)], ids int32
+    [B, max_q_len * t] ascending, count int32 [B])."""
+    q, qo, B, rows = _queries(q, q_offsets)
+    c = _dev(centroids.contiguous(), torch.float32, "centroids")
+    k2 = c.shape[0]
+    mask = torch.empty((B, (k2 + 31) // 32), dtype=torch.int32, device=q.device)
+    ids = torch.full((B, max_q_len * t), -1, dtype=torch.int32, device=q.device)
+    count = torch.empty(B, dtype=torch.int32, device=q.device)
+    _check(lib.gem_cluster_filter(_ptr(q), _ptr(qo), B, max_q_len, _ptr(c), k2, t, _ptr(mask), _ptr(ids),
+                                  _ptr(count), _stream(stream)))
+    return mask, ids, count
+
+
 def assign_codes(x, centroids, with_best: bool = False, stream=None):
     """NN(x): index of the centroid with the largest inner product (ties: lowest)."""
     x = _dev(x, torch.float32, "x")

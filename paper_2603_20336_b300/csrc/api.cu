@@ -414,6 +414,65 @@ gem_status gem_train_codebook(const gem_store* s, int32_t k1, int32_t iters, int
   return r;
 }
 
+static int current_sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+gem_status gem_kmeans(const float* x, int64_t n, int32_t k, int32_t iters, uint64_t seed, float* centroids_out,
+                      void* stream) {
+  if (!x || !centroids_out) return fail(GEM_ERR_INVALID, "NULL argument");
+  if (k < 1 || k > n) return fail(GEM_ERR_INVALID, "k must be 1..n");
+  if (iters < 0) return fail(GEM_ERR_INVALID, "iters < 0");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // initial centroids: k distinct rows of x from a seeded shuffle (a host-side
+  // index choice only)
+  std::mt19937_64 rng(seed);
+  std::vector<int64_t> init(n);
+  std::iota(init.begin(), init.end(), 0);
+  for (int64_t i = 0; i < k; ++i) {
+    std::uniform_int_distribution<int64_t> pick(i, n - 1);
+    std::swap(init[i], init[pick(rng)]);
+  }
+  init.resize(k);
+  int64_t* d_rows = nullptr;
+  int32_t* codes = nullptr;
+  double* sums = nullptr;
+  int* counts = nullptr;
+  auto cleanup = [&]() { dfree(d_rows); dfree(codes); dfree(sums); dfree(counts); };
+  gem_status r;
+  if ((r = dmalloc(&d_rows, (size_t)k, "initial rows")) != GEM_OK || (r = dmalloc(&codes, (size_t)n, "codes")) != GEM_OK ||
+      (r = dmalloc(&sums, (size_t)k * kDim, "centroid sums")) != GEM_OK ||
+      (r = dmalloc(&counts, (size_t)k, "centroid counts")) != GEM_OK) {
+    cleanup();
+    return r;
+  }
+  cudaError_t e = cudaMemcpyAsync(d_rows, init.data(), sizeof(int64_t) * k, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) r = launch_gather_rows(x, d_rows, k, centroids_out, st);
+  for (int it = 0; it < iters && e == cudaSuccess && r == GEM_OK; ++it) {
+    r = launch_assign(x, n, centroids_out, k, codes, nullptr, st);
+    if (r == GEM_OK) r = launch_kmeans_step(x, n, codes, sums, counts, k, centroids_out, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "k-means");
+  return r;
+}
+
+gem_status gem_cluster_filter(const float* q, const int64_t* q_offsets, int32_t n_queries, int32_t max_q_len,
+                              const float* centroids, int32_t k2, int32_t t, uint32_t* out_mask, int32_t* out_list,
+                              int32_t* out_count, void* stream) {
+  if (!q || !q_offsets || !centroids || !out_mask || !out_list || !out_count)
+    return fail(GEM_ERR_INVALID, "NULL argument");
+  if (n_queries < 0 || max_q_len < 1) return fail(GEM_ERR_INVALID, "bad sizes");
+  if (k2 < 1 || k2 > (1 << 18)) return fail(GEM_ERR_INVALID, "k2 must be 1..262144");
+  if (t < 1 || t > 8 || t > k2) return fail(GEM_ERR_INVALID, "t must be 1..min(8, k2)");
+  return launch_cluster_filter(q, q_offsets, n_queries, centroids, k2, t, max_q_len * t, out_mask, out_list,
+                               out_count, current_sm_count(), reinterpret_cast<cudaStream_t>(stream));
+}
+
 gem_status gem_store_set_codebook(gem_store* s, const float* centroids, int32_t k1, void* stream) {
   if (!s || !centroids) return fail(GEM_ERR_INVALID, "NULL argument");
   if (k1 < 1) return fail(GEM_ERR_INVALID, "k1 < 1");
@@ -618,13 +677,6 @@ gem_status gem_search_host(const gem_store* s, gem_workspace* w, const float* q_
                                  cudaMemcpyDeviceToHost, st));
   GEM_CUDA_TRY(cudaStreamSynchronize(st));
   return GEM_OK;
-}
-
-static int current_sm_count() {
-  int dev = 0, n = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-  return n > 0 ? n : 1;
 }
 
 gem_status gem_maxsim_fwd(const float* q, const int64_t* q_offsets, int32_t n_queries, const float* docs,

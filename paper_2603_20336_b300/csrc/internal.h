@@ -242,6 +242,9 @@ gem_status launch_topk(gem_workspace* ws, const float* scores, const int64_t* ro
                        int64_t* out_ids, float* out_scores, cudaStream_t st);
 
 // Codes, k-means and the quantized estimate (codes.cu).
+gem_status launch_cluster_filter(const float* q, const int64_t* q_offsets, int32_t n_queries, const float* centroids,
+                                 int32_t k2, int32_t t, int32_t cap, uint32_t* out_mask, int32_t* out_list,
+                                 int32_t* out_count, int n_sm, cudaStream_t st);
 gem_status launch_assign(const float* X, int64_t n, const float* C, int k1, int32_t* codes, float* best,
                          cudaStream_t st);
 gem_status launch_assign_dev_n(const float* X, int64_t max_n, const int64_t* n_dev, const float* C, int k1,
