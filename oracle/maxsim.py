@@ -188,6 +188,62 @@ def cluster_filter(q, q_offsets, C_index, t: int):
     return out
 
 
+_MASK64 = (1 << 64) - 1
+_GOLDEN = 0x9E3779B97F4A7C15
+
+
+def splitmix64_next(state: int):
+    """One step of the SplitMix64 generator (Steele, Lea and Flood, 2014): the
+    state advances by the golden-ratio increment and the output is the state put
+    through the variant-13 finalizer.  Returns (new_state, output)."""
+    state = (state + _GOLDEN) & _MASK64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return state, z ^ (z >> 31)
+
+
+def entry_hash(seed: int, b: int, c: int, s: int) -> int:
+    """The counter-based draw behind the multi-entry choice: SplitMix64 outputs
+    chained over the fields, H = out(out(out(seed + b) + c) + s) where out(x) is
+    the output of one step from state x (all arithmetic mod 2^64)."""
+    h = seed & _MASK64
+    for v in (b, c, s):
+        _, h = splitmix64_next((h + v) & _MASK64)
+    return h
+
+
+def cluster_members(index_codes, offsets, k2: int):
+    """members(c) = the stored sets with at least one vector whose nearest C_index
+    centroid is c (the set's cluster representation C(P), Sec. 4.1.1, Eq. 4).
+    index_codes: int [n_vectors].  Returns k2 sorted int64 arrays."""
+    codes = _i64(index_codes)
+    off = _i64(offsets)
+    set_of = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    pairs = np.unique(codes * (len(off) + 1) + set_of)
+    cl, st = pairs // (len(off) + 1), pairs % (len(off) + 1)
+    return [st[cl == c] for c in range(k2)]
+
+
+def entry_points(query_clusters, members, seed: int):
+    """E of Algorithm 5 (Sec. 4.5.2): one random set from every cluster of C_query.
+    The draw for (query b, cluster c) is the member s with the smallest
+    entry_hash(seed, b, c, s) (then the lower s): uniform over the members and
+    independent of their order.  An empty cluster gives -1.  query_clusters: one
+    int array of cluster ids per query.  Returns one int64 array per query."""
+    out = []
+    for b, cl in enumerate(query_clusters):
+        seeds = []
+        for c in np.asarray(cl, dtype=np.int64).tolist():
+            m = members[c]
+            if len(m) == 0:
+                seeds.append(-1)
+                continue
+            seeds.append(min((entry_hash(seed, b, c, int(s)), int(s)) for s in m)[1])
+        out.append(np.array(seeds, dtype=np.int64))
+    return out
+
+
 def qch_distance(q_codes, p_codes, C) -> float:
     """qCH(Q, P) = sum over q of min over p of d_X(NN(q), NN(p)) (Sec. 4.5.3, Eq. 16).
 

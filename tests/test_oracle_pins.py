@@ -423,3 +423,43 @@ def test_cluster_filter_permutation_equivariant_and_monotone_in_t():
             assert prev[b] <= set(base[b].tolist())
             prev[b] = set(base[b].tolist())
     assert inv[perm[3]] == 3
+
+
+# ---------------------------------------------------------------------------
+# Multi-entry points (Sec. 4.5.2, Algorithm 5): members per cluster, the draw
+# ---------------------------------------------------------------------------
+
+def test_splitmix64_reference_outputs():
+    # the generator's published first outputs from state 0
+    st, out = 0, []
+    for _ in range(3):
+        st, o = oracle.splitmix64_next(st)
+        out.append(o)
+    assert out == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_cluster_members_hand_example():
+    # sets: 0 = vectors 0..2, 1 = vectors 3..4, 2 = vector 5; index codes per vector
+    off = np.array([0, 3, 5, 6])
+    codes = np.array([2, 0, 2, 2, 3, 0])
+    m = oracle.cluster_members(codes, off, 5)
+    assert [x.tolist() for x in m] == [[0, 2], [], [0, 1], [1], []]
+
+
+def test_entry_points_single_member_empty_cluster_and_membership():
+    members = [np.array([7]), np.array([], dtype=np.int64), np.array([1, 4, 9, 12])]
+    e = oracle.entry_points([np.array([0, 1, 2]), np.array([2])], members, seed=11)
+    assert e[0][0] == 7 and e[0][1] == -1
+    assert e[0][2] in (1, 4, 9, 12) and e[1][0] in (1, 4, 9, 12)
+    # the draw does not depend on the order the members are listed in
+    shuffled = [members[0], members[1], np.array([12, 4, 1, 9])]
+    assert [x.tolist() for x in oracle.entry_points([np.array([0, 1, 2]), np.array([2])], shuffled, 11)] == \
+        [x.tolist() for x in e]
+
+
+def test_entry_points_draw_is_uniform_over_members():
+    members = [np.array([3, 5, 8, 13])]
+    picks = [oracle.entry_points([np.array([0])] * 1, members, seed)[0][0] for seed in range(4000)]
+    counts = np.array([picks.count(s) for s in (3, 5, 8, 13)])
+    # 4000 draws over 4 members: each count within 5 sigma of 1000
+    assert np.all(np.abs(counts - 1000) < 5 * np.sqrt(4000 * 0.25 * 0.75)), counts
