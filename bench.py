@@ -233,10 +233,20 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms):
         torch.cuda.synchronize()
         km_s = time.perf_counter() - t0
         ms = _time(lambda: gem.cluster_filter(q, qo, Ci, t=t, max_q_len=32))
-        _, _, cnt = gem.cluster_filter(q, qo, Ci, t=t, max_q_len=32)
+        _, lst, cnt = gem.cluster_filter(q, qo, Ci, t=t, max_q_len=32)
+        # multi-entry points (Sec. 4.5.2): C_index codes and member lists of the
+        # store, then one random member set per cluster of every C_query
+        t0 = time.perf_counter()
+        gem.set_index_centroids(store, Ci)
+        torch.cuda.synchronize()
+        idx_s = time.perf_counter() - t0
+        ms_e = _time(lambda: gem.entry_points(store, lst, cnt, seed=7))
+        seeds = gem.entry_points(store, lst, cnt, seed=7)
         return {"k1": int(Cq.shape[0]), "k2": k2, "t": t, "kmeans_s": km_s, "ms": ms,
                 "query_vectors_x_centroids_per_s": rows * k2 / (ms * 1e-3),
-                "tflops": 2.0 * rows * k2 * 128 / ms / 1e9, "mean_c_query": float(cnt.float().mean())}
+                "tflops": 2.0 * rows * k2 * 128 / ms / 1e9, "mean_c_query": float(cnt.float().mean()),
+                "index_codes_and_members_s": idx_s, "entry_points_ms": ms_e,
+                "entry_points": int((seeds >= 0).sum())}
 
     def beam():
         nq, rounds = 4096, 20

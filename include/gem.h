@@ -86,7 +86,8 @@ enum {
   GEM_EXPORT_OFFSETS = 3,     /* int64  [n_sets + 1] */
   GEM_EXPORT_PAD_OFFSETS = 4, /* int64  [n_sets + 1] offsets of the padded layout */
   GEM_EXPORT_CODES = 5,       /* int32  [n_vecs] NN code of every stored vector */
-  GEM_EXPORT_CODEBOOK = 6     /* float  [k1 * 128] centroids of C_quant */
+  GEM_EXPORT_CODEBOOK = 6,    /* float  [k1 * 128] centroids of C_quant */
+  GEM_EXPORT_INDEX_CODES = 7  /* int32  [n_vecs] nearest C_index centroid of every stored vector */
 };
 
 typedef struct gem_store gem_store;
@@ -192,6 +193,37 @@ gem_status gem_kmeans(const float* x, int64_t n, int32_t k, int32_t iters, uint6
 gem_status gem_cluster_filter(const float* q, const int64_t* q_offsets, int32_t n_queries, int32_t max_q_len,
                               const float* centroids, int32_t k2, int32_t t, uint32_t* out_mask, int32_t* out_list,
                               int32_t* out_count, void* stream);
+
+/*
+ * gem_store_set_index_centroids: attach C_index (k2 coarse centroids, device
+ * [k2 x 128] FP32, copied) to the store; every stored vector gets its nearest
+ * C_index centroid (largest inner product, ties to the lower index; exported as
+ * GEM_EXPORT_INDEX_CODES) and every cluster the list of sets with a vector in it
+ * (the set's C(P), Sec. 4.1.1, Eq. 4).  Needs the FP32 copy.  Blocks until done.
+ * Errors: GEM_ERR_INVALID (NULL, k2 outside 1..262144), GEM_ERR_STATE (no FP32
+ * copy), GEM_ERR_OOM.
+ */
+gem_status gem_store_set_index_centroids(gem_store* store, const float* centroids, int32_t k2, void* stream);
+
+/*
+ * gem_entry_points: E of Algorithm 5 (Sec. 4.5.2): one random member set from
+ * every cluster of each query's C_query.
+ *   cluster_lists  int32 [n_queries x stride]  C_query(b) in row b (as written by
+ *                                              gem_cluster_filter with stride =
+ *                                              max_q_len * t)
+ *   cluster_counts int32 [n_queries]           entries of row b in use (min with
+ *                                              stride)
+ *   out_sets       int64 [n_queries x stride]  the drawn set of each cluster; -1
+ *                                              for unused slots and empty clusters
+ * The draw for (query b, cluster c) is the member set s with the smallest
+ * H(seed, b, c, s), then the lower s, where H = out(out(out(seed + b) + c) + s)
+ * and out(x) is the SplitMix64 output from state x: uniform over the cluster's
+ * member sets and reproducible for a given seed.  Device buffers, caller-owned;
+ * asynchronous on `stream`.
+ * Errors: GEM_ERR_INVALID (NULL, stride < 1), GEM_ERR_STATE (no C_index).
+ */
+gem_status gem_entry_points(const gem_store* store, const int32_t* cluster_lists, const int32_t* cluster_counts,
+                            int32_t n_queries, int32_t stride, uint64_t seed, int64_t* out_sets, void* stream);
 
 /*
  * Scratch for scoring calls against `store`.  Bounds fix the memory once:

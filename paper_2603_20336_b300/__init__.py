@@ -101,7 +101,8 @@ class Store:
                 "fp8_scale": (2, torch.float32, (P,)), "offsets": (3, torch.int64, (self.n_sets + 1,)),
                 "pad_offsets": (4, torch.int64, (self.n_sets + 1,)),
                 "codes": (5, torch.int32, (self.n_vecs,)),
-                "codebook": (6, torch.float32, (getattr(self, "k1", 0), 128))}
+                "codebook": (6, torch.float32, (getattr(self, "k1", 0), 128)),
+                "index_codes": (7, torch.int32, (self.n_vecs,))}
         code, dt, shape = spec[what]
         out = torch.empty(shape, dtype=dt, device="cuda")
         _check(lib.gem_store_export(self.handle, code, _ptr(out), out.numel() * out.element_size(),
@@ -254,6 +255,26 @@ def cluster_filter(q, q_offsets, centroids, t: int = 4, max_q_len: int = 32, str
     _check(lib.gem_cluster_filter(_ptr(q), _ptr(qo), B, max_q_len, _ptr(c), k2, t, _ptr(mask), _ptr(ids),
                                   _ptr(count), _stream(stream)))
     return mask, ids, count
+
+
+def set_index_centroids(store: Store, centroids, stream=None):
+    """Attach C_index to the store: nearest coarse centroid of every stored vector
+    and the member sets of every cluster."""
+    c = _dev(centroids.contiguous(), torch.float32, "centroids")
+    _check(lib.gem_store_set_index_centroids(store.handle, _ptr(c), c.shape[0], _stream(stream)))
+    store.k2 = c.shape[0]
+
+
+def entry_points(store: Store, cluster_lists, cluster_counts, seed: int = 0, stream=None):
+    """One random member set per cluster of each query's C_query (rows as from
+    cluster_filter): int64 [B, stride], -1 for unused slots and empty clusters."""
+    lists = _dev(cluster_lists.contiguous(), torch.int32, "cluster_lists")
+    counts = _dev(cluster_counts.contiguous(), torch.int32, "cluster_counts")
+    B, stride = lists.shape
+    out = torch.empty((B, stride), dtype=torch.int64, device=lists.device)
+    _check(lib.gem_entry_points(store.handle, _ptr(lists), _ptr(counts), B, stride, seed, _ptr(out),
+                                _stream(stream)))
+    return out
 
 
 def assign_codes(x, centroids, with_best: bool = False, stream=None):

@@ -100,6 +100,10 @@ void gem_store_destroy(gem_store* s) {
   dfree(s->d_fp8_scale);
   dfree(s->d_codebook);
   dfree(s->d_codes);
+  dfree(s->d_cindex);
+  dfree(s->d_icodes);
+  dfree(s->d_member_off);
+  dfree(s->d_members);
   for (auto& kv : s->chunks) dfree(kv.second.d_chunk_doc);
   cudaSetDevice(prev);
   delete s;
@@ -235,6 +239,7 @@ gem_status gem_store_export(const gem_store* s, int32_t what, void* dst, size_t 
     case GEM_EXPORT_PAD_OFFSETS: src = s->d_pad_offsets; bytes = sizeof(int64_t) * (s->n_sets + 1); break;
     case GEM_EXPORT_CODES: src = s->d_codes; bytes = sizeof(int32_t) * s->n_vecs; break;
     case GEM_EXPORT_CODEBOOK: src = s->d_codebook; bytes = sizeof(float) * (size_t)s->k1 * kDim; break;
+    case GEM_EXPORT_INDEX_CODES: src = s->d_icodes; bytes = sizeof(int32_t) * s->n_vecs; break;
     default: return fail(GEM_ERR_INVALID, "unknown export");
   }
   if (!src) return fail(GEM_ERR_STATE, "store does not keep that array");
@@ -471,6 +476,38 @@ gem_status gem_cluster_filter(const float* q, const int64_t* q_offsets, int32_t 
   if (t < 1 || t > 8 || t > k2) return fail(GEM_ERR_INVALID, "t must be 1..min(8, k2)");
   return launch_cluster_filter(q, q_offsets, n_queries, centroids, k2, t, max_q_len * t, out_mask, out_list,
                                out_count, current_sm_count(), reinterpret_cast<cudaStream_t>(stream));
+}
+
+gem_status gem_store_set_index_centroids(gem_store* s, const float* centroids, int32_t k2, void* stream) {
+  if (!s || !centroids) return fail(GEM_ERR_INVALID, "NULL argument");
+  if (k2 < 1 || k2 > (1 << 18)) return fail(GEM_ERR_INVALID, "k2 must be 1..262144");
+  if (!s->d_f32) return fail(GEM_ERR_STATE, "cluster codes are assigned from the fp32 copy");
+  gem_status r = check_current_device(s->device);
+  if (r != GEM_OK) return r;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  dfree(s->d_cindex);
+  dfree(s->d_member_off);
+  s->d_cindex = nullptr;
+  s->d_member_off = nullptr;
+  s->k2 = 0;
+  if (!s->d_icodes && (r = dmalloc(&s->d_icodes, (size_t)s->n_vecs, "index codes")) != GEM_OK) return r;
+  if (!s->d_members && (r = dmalloc(&s->d_members, (size_t)s->n_vecs, "cluster members")) != GEM_OK) return r;
+  if ((r = dmalloc(&s->d_cindex, (size_t)k2 * kDim, "C_index")) != GEM_OK) return r;
+  if ((r = dmalloc(&s->d_member_off, (size_t)k2 + 1, "member offsets")) != GEM_OK) return r;
+  GEM_CUDA_TRY(cudaMemcpyAsync(s->d_cindex, centroids, sizeof(float) * (size_t)k2 * kDim, cudaMemcpyDeviceToDevice,
+                               st));
+  if ((r = launch_assign(s->d_f32, s->n_vecs, s->d_cindex, k2, s->d_icodes, nullptr, st)) != GEM_OK) return r;
+  s->k2 = k2;
+  return launch_cluster_index(s, st);
+}
+
+gem_status gem_entry_points(const gem_store* s, const int32_t* cluster_lists, const int32_t* cluster_counts,
+                            int32_t n_queries, int32_t stride, uint64_t seed, int64_t* out_sets, void* stream) {
+  if (!s || !cluster_lists || !cluster_counts || !out_sets) return fail(GEM_ERR_INVALID, "NULL argument");
+  if (n_queries < 0 || stride < 1) return fail(GEM_ERR_INVALID, "bad sizes");
+  if (s->k2 <= 0) return fail(GEM_ERR_STATE, "store has no C_index (gem_store_set_index_centroids)");
+  return launch_entry_points(s, cluster_lists, cluster_counts, n_queries, stride, seed, out_sets,
+                             reinterpret_cast<cudaStream_t>(stream));
 }
 
 gem_status gem_store_set_codebook(gem_store* s, const float* centroids, int32_t k1, void* stream) {

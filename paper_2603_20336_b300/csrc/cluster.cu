@@ -15,6 +15,9 @@
 // rounds of a warp arg-max and sets the winners' bits in the set's bitmask.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstdint>
+
 #include "internal.h"
 
 namespace gem {
@@ -174,7 +177,141 @@ cluster_filter_kernel(const float* __restrict__ q, const int64_t* __restrict__ q
   }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster members and multi-entry points (Sec. 4.1.1 Eq. 4, Sec. 4.5.2,
+// Algorithm 5): every stored vector's nearest C_index centroid, per cluster the
+// sets of its vectors, and for a query's C_query one random member set per
+// cluster.  The draw for (query b, cluster c) is the member s with the smallest
+// H(seed, b, c, s) (then the lower s), H = out(out(out(seed + b) + c) + s) with
+// out(x) one SplitMix64 output from state x; the minimum does not depend on the
+// order (or repetition) of the members, so the lists are built with atomics.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t splitmix_out(uint64_t state) {
+  uint64_t z = state + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void count_codes_kernel(const int32_t* __restrict__ codes, int64_t n, int64_t* __restrict__ counts) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(reinterpret_cast<unsigned long long*>(counts + codes[i]), 1ull);
+}
+
+// exclusive scan of counts [k] into off [k + 1] by one CTA of 1024 threads
+__global__ void __launch_bounds__(1024) scan_counts_kernel(const int64_t* __restrict__ counts, int k,
+                                                         int64_t* __restrict__ off) {
+  __shared__ int64_t part[1024];
+  __shared__ int64_t base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < k; c0 += 1024) {
+    const int c = c0 + threadIdx.x;
+    const int64_t v = c < k ? counts[c] : 0;
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {  // Hillis-Steele inclusive scan
+      const int64_t add = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+      __syncthreads();
+      part[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (c < k) off[c] = base + part[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) base += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) off[k] = base;
+}
+
+// one warp per set: every vector of set `d` adds d to the member list of its cluster
+__global__ void scatter_members_kernel(const int32_t* __restrict__ codes, const int64_t* __restrict__ offsets,
+                                       int64_t n_sets, const int64_t* __restrict__ member_off,
+                                       int64_t* __restrict__ cursor, int32_t* __restrict__ members) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t d = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; d < n_sets;
+       d += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    for (int64_t v = offsets[d] + lane; v < offsets[d + 1]; v += 32) {
+      const int c = codes[v];
+      const int64_t pos = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(cursor + c), 1ull);
+      members[member_off[c] + pos] = (int32_t)d;
+    }
+  }
+}
+
+// one warp per (query b, slot j): the draw for cluster lists[b * stride + j]
+__global__ void entry_points_kernel(const int32_t* __restrict__ lists, const int32_t* __restrict__ counts,
+                                    int n_queries, int stride, const int64_t* __restrict__ member_off,
+                                    const int32_t* __restrict__ members, int k2, uint64_t seed,
+                                    int64_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_items = (int64_t)n_queries * stride;
+  for (int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; it < n_items;
+       it += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int b = (int)(it / stride), j = (int)(it % stride);
+    int64_t pick = -1;
+    if (j < counts[b]) {
+      const int c = lists[it];
+      if (c >= 0 && c < k2) {
+        const uint64_t h2 = splitmix_out(splitmix_out(seed + (uint64_t)b) + (uint64_t)c);
+        uint64_t best_h = ~0ull;
+        int64_t best_s = INT64_MAX;
+        for (int64_t m = member_off[c] + lane; m < member_off[c + 1]; m += 32) {
+          const int64_t sidx = members[m];
+          const uint64_t h = splitmix_out(h2 + (uint64_t)sidx);
+          if (h < best_h || (h == best_h && sidx < best_s)) { best_h = h; best_s = sidx; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const uint64_t oh = __shfl_xor_sync(0xffffffffu, best_h, o);
+          const int64_t os = __shfl_xor_sync(0xffffffffu, best_s, o);
+          if (oh < best_h || (oh == best_h && os < best_s)) { best_h = oh; best_s = os; }
+        }
+        pick = best_s == INT64_MAX ? -1 : best_s;
+      }
+    }
+    if (lane == 0) out[it] = pick;
+  }
+}
+
 }  // namespace
+
+gem_status launch_cluster_index(gem_store* s, cudaStream_t st) {
+  int64_t* counts = nullptr;
+  if (cudaMalloc(&counts, sizeof(int64_t) * s->k2) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GEM_ERR_OOM, "cluster counts");
+  }
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * s->k2, st);
+  if (e == cudaSuccess) {
+    count_codes_kernel<<<1024, 256, 0, st>>>(s->d_icodes, s->n_vecs, counts);
+    scan_counts_kernel<<<1, 1024, 0, st>>>(counts, s->k2, s->d_member_off);
+    e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * s->k2, st);
+  }
+  if (e == cudaSuccess) {
+    scatter_members_kernel<<<1024, 256, 0, st>>>(s->d_icodes, s->d_offsets, s->n_sets, s->d_member_off, counts,
+                                                  s->d_members);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(counts);
+  if (e != cudaSuccess) return cuda_fail(e, "cluster members");
+  note_launches(3);
+  return GEM_OK;
+}
+
+gem_status launch_entry_points(const gem_store* s, const int32_t* lists, const int32_t* counts, int32_t n_queries,
+                               int32_t stride, uint64_t seed, int64_t* out, cudaStream_t st) {
+  const int64_t warps = (int64_t)n_queries * stride;
+  if (warps == 0) return GEM_OK;
+  const int grid = (int)std::min<int64_t>((warps + 7) / 8, 4096);
+  entry_points_kernel<<<grid, 256, 0, st>>>(lists, counts, n_queries, stride, s->d_member_off, s->d_members, s->k2,
+                                            seed, out);
+  GEM_CUDA_TRY(cudaGetLastError());
+  note_launches(1);
+  return GEM_OK;
+}
 
 gem_status launch_cluster_filter(const float* q, const int64_t* q_offsets, int32_t n_queries, const float* centroids,
                                  int32_t k2, int32_t t, int32_t cap, uint32_t* out_mask, int32_t* out_list,

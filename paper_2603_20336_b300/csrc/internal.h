@@ -71,6 +71,14 @@ struct gem_store {
   int k1 = 0;
   float* d_codebook = nullptr;   // [k1 * 128], unit rows
   int32_t* d_codes = nullptr;    // [n_vecs], original (unpadded) row order
+  // coarse clusters C_index (Sec. 4.1.1): the nearest one of every stored vector
+  // and, per cluster, the sets of its vectors (one entry per vector, in no fixed
+  // order) behind member_off [k2 + 1]
+  int k2 = 0;
+  float* d_cindex = nullptr;      // [k2 * 128]
+  int32_t* d_icodes = nullptr;    // [n_vecs]
+  int64_t* d_member_off = nullptr;
+  int32_t* d_members = nullptr;   // [n_vecs] set ids
   // tensor maps of the doc copies, keyed by tile rows (box height)
   mutable std::map<int, CUtensorMap> tmap_bf16;
   mutable std::map<int, CUtensorMap> tmap_fp8;
@@ -242,6 +250,9 @@ gem_status launch_topk(gem_workspace* ws, const float* scores, const int64_t* ro
                        int64_t* out_ids, float* out_scores, cudaStream_t st);
 
 // Codes, k-means and the quantized estimate (codes.cu).
+gem_status launch_cluster_index(gem_store* s, cudaStream_t st);
+gem_status launch_entry_points(const gem_store* s, const int32_t* lists, const int32_t* counts, int32_t n_queries,
+                               int32_t stride, uint64_t seed, int64_t* out, cudaStream_t st);
 gem_status launch_cluster_filter(const float* q, const int64_t* q_offsets, int32_t n_queries, const float* centroids,
                                  int32_t k2, int32_t t, int32_t cap, uint32_t* out_mask, int32_t* out_list,
                                  int32_t* out_count, int n_sm, cudaStream_t st);

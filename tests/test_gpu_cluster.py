@@ -108,3 +108,42 @@ def test_kmeans_init_and_one_lloyd_step_match_oracle(gem):
     assert close.mean() >= 0.95, close.mean()
     C8 = gem.kmeans(torch.from_numpy(X).cuda(), k, iters=8, seed=3).cpu().numpy()
     np.testing.assert_allclose(np.linalg.norm(C8, axis=1), 1.0, atol=1e-5)
+
+
+def test_index_codes_members_and_entry_points_match_oracle(gem):
+    """C_index attached to a store: every stored vector's nearest coarse centroid
+    agrees with the oracle except FP64 near-ties; given the GPU's codes, the
+    oracle's member lists and SplitMix64 draws give exactly the GPU's entry sets,
+    for the C_query lists the GPU cluster filter returns (empty clusters give -1)."""
+    w = synth.exact_fp32(n_sets=700, n_queries=6)
+    store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("f32",))
+    k2 = 48
+    Ci = gem.kmeans(w.docs.vecs.cuda(), k2, iters=3, seed=2)
+    Ci[5] = -Ci[5]            # a centroid few vectors choose: likely an empty cluster
+    gem.set_index_centroids(store, Ci)
+    codes = store.export("index_codes").cpu().numpy()
+    X = w.docs.vecs.numpy().astype(np.float64)
+    C64 = Ci.cpu().numpy().astype(np.float64)
+    want = oracle.assign_codes(X, C64)
+    diff = np.nonzero(codes != want)[0]
+    for i in diff:
+        s = X[i] @ C64.T
+        assert s[want[i]] - s[codes[i]] <= EPS, i
+    members = oracle.cluster_members(codes, w.docs.offsets, k2)
+    q, qo = w.queries.vecs.cuda(), torch.from_numpy(w.queries.offsets).cuda()
+    _, ids, count = gem.cluster_filter(q, qo, Ci, t=4, max_q_len=32)
+    # add an empty cluster to one query's list to cover the -1 case
+    empty = [c for c in range(k2) if len(members[c]) == 0]
+    ids_np, count_np = ids.cpu().numpy(), count.cpu().numpy()
+    if empty:
+        ids_np[0, count_np[0]] = empty[0]
+        count_np[0] += 1
+    for seed in (0, 12345):
+        got = gem.entry_points(store, torch.from_numpy(ids_np).cuda(), torch.from_numpy(count_np).cuda(),
+                               seed=seed).cpu().numpy()
+        lists = [ids_np[b, :count_np[b]] for b in range(len(count_np))]
+        exp = oracle.entry_points(lists, members, seed)
+        for b in range(len(lists)):
+            assert got[b, :count_np[b]].tolist() == exp[b].tolist()
+            assert np.all(got[b, count_np[b]:] == -1)
+    store.close()
