@@ -244,6 +244,68 @@ def entry_points(query_clusters, members, seed: int):
     return out
 
 
+def beam_search(score, graph_off, graph_nbrs, set_clusters, query_clusters, entries, ef: int,
+                max_rounds: int = 1 << 30):
+    """Cluster-guided multi-path beam search of one query (Algorithm 5, Sec. 4.5.3),
+    in rounds: in every round each non-empty queue W_e pops its best set P (in
+    entry order); if P scores below tau (the worst score in R once R holds ef sets,
+    else -inf) W_e is emptied; otherwise every neighbour P' of P (in list order) that
+    is not visited and shares a cluster with C_query is marked visited and queued
+    for scoring.  After the round's expansions the new sets are scored and inserted,
+    in the order they were queued, into their own W_e and into R.
+
+    Scores are similarities (qsim = m_q - qCH: higher is closer).  "Better" means
+    higher score, then lower set id; W_e and R keep the ef best.  score(s) gives the
+    score of set s; set_clusters[s] is the set of clusters of s (C(P)) and
+    query_clusters the clusters of C_query.  entries: the entry sets, in order
+    (duplicates and -1 skipped).  Returns (R as a list of (score, id), best first,
+    the number of rounds run).
+    """
+    import bisect
+
+    def key(sc, sid):        # ascending key = better first
+        return (-sc, sid)
+
+    qc = set(int(c) for c in query_clusters)
+    visited = set()
+    R = []                   # sorted ascending by key
+    queues = []
+    for e in entries:
+        e = int(e)
+        if e < 0 or e in visited:
+            continue
+        visited.add(e)
+        sc = score(e)
+        queues.append([key(sc, e)])
+        bisect.insort(R, key(sc, e))
+        del R[ef:]
+    rounds = 0
+    while any(queues) and rounds < max_rounds:
+        rounds += 1
+        tau = -R[ef - 1][0] if len(R) >= ef else -math.inf
+        new = []             # (queue index, set)
+        for qi, W in enumerate(queues):
+            if not W:
+                continue
+            nsc, pid = W.pop(0)
+            if -nsc < tau:
+                W.clear()
+                continue
+            for nb in graph_nbrs[graph_off[pid]:graph_off[pid + 1]]:
+                nb = int(nb)
+                if nb in visited or not (set_clusters[nb] & qc):
+                    continue
+                visited.add(nb)
+                new.append((qi, nb))
+        for qi, nb in new:
+            k = key(score(nb), nb)
+            bisect.insort(queues[qi], k)
+            del queues[qi][ef:]
+            bisect.insort(R, k)
+            del R[ef:]
+    return [(-k[0], k[1]) for k in R], rounds
+
+
 def qch_distance(q_codes, p_codes, C) -> float:
     """qCH(Q, P) = sum over q of min over p of d_X(NN(q), NN(p)) (Sec. 4.5.3, Eq. 16).
 

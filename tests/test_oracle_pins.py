@@ -463,3 +463,68 @@ def test_entry_points_draw_is_uniform_over_members():
     counts = np.array([picks.count(s) for s in (3, 5, 8, 13)])
     # 4000 draws over 4 members: each count within 5 sigma of 1000
     assert np.all(np.abs(counts - 1000) < 5 * np.sqrt(4000 * 0.25 * 0.75)), counts
+
+
+# ---------------------------------------------------------------------------
+# Cluster-guided beam search (Algorithm 5), in rounds
+# ---------------------------------------------------------------------------
+
+def _chain(n, extra=()):
+    """Bidirectional path graph 0 - 1 - ... - n-1 (plus extra undirected edges) as CSR."""
+    nb = [[] for _ in range(n)]
+    for i in range(n - 1):
+        nb[i].append(i + 1)
+        nb[i + 1].append(i)
+    for a, b in extra:
+        nb[a].append(b)
+        nb[b].append(a)
+    off = np.concatenate([[0], np.cumsum([len(x) for x in nb])])
+    return off, np.array([v for x in nb for v in sorted(x)], dtype=np.int64)
+
+
+def test_beam_search_walks_a_path_and_keeps_the_best_ef():
+    off, nbrs = _chain(10)
+    clusters = [{0}] * 10
+    R, rounds = oracle.beam_search(lambda s: float(s), off, nbrs, clusters, [0], [0], ef=3)
+    assert R == [(9.0, 9), (8.0, 8), (7.0, 7)]
+    assert rounds == 10   # one node popped per round, the last pop adds nothing
+
+
+def test_beam_search_cluster_filter_stops_the_walk():
+    off, nbrs = _chain(10)
+    clusters = [{0}] * 10
+    clusters[5] = {1}     # not in C_query
+    R, _ = oracle.beam_search(lambda s: float(s), off, nbrs, clusters, [0], [0], ef=3)
+    assert R == [(4.0, 4), (3.0, 3), (2.0, 2)]
+
+
+def test_beam_search_prunes_a_path_below_tau():
+    # two components: 0..4 scoring 10..14, 5..9 scoring 0..4; entries in both
+    off, nbrs = _chain(10)
+    off2, nbrs2 = [], []
+    cut = [[j for j in nbrs[off[i]:off[i + 1]] if (j < 5) == (i < 5)] for i in range(10)]
+    off2 = np.concatenate([[0], np.cumsum([len(x) for x in cut])])
+    nbrs2 = np.array([v for x in cut for v in x], dtype=np.int64)
+    score = {i: (10.0 + i if i < 5 else float(i - 5)) for i in range(10)}
+    seen = []
+
+    def sc(s):
+        seen.append(s)
+        return score[s]
+
+    R, rounds = oracle.beam_search(sc, off2, nbrs2, [{0}] * 10, [0], [0, 5], ef=3)
+    assert R == [(14.0, 4), (13.0, 3), (12.0, 2)]
+    assert rounds == 5
+    # the second path is cut after two expansions: sets 8 and 9 are never scored
+    assert 8 not in seen and 9 not in seen and 7 in seen
+
+
+def test_beam_search_complete_graph_finds_exact_top_ef():
+    n = 12
+    off = np.arange(0, n * (n - 1) + 1, n - 1)
+    nbrs = np.array([j for i in range(n) for j in range(n) if j != i])
+    rng = np.random.default_rng(4)
+    vals = rng.permutation(n).astype(float)
+    R, _ = oracle.beam_search(lambda s: vals[s], off, nbrs, [{2}] * n, [2, 7], [3], ef=5)
+    want = sorted(((vals[i], i) for i in range(n)), key=lambda x: (-x[0], x[1]))[:5]
+    assert R == want
