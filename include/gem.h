@@ -226,6 +226,37 @@ gem_status gem_entry_points(const gem_store* store, const int32_t* cluster_lists
                             int32_t n_queries, int32_t stride, uint64_t seed, int64_t* out_sets, void* stream);
 
 /*
+ * gem_beam_search: cluster-guided multi-path beam search (Algorithm 5,
+ * Sec. 4.5.3) of a batch of queries over a graph of the stored sets, scored by
+ * qCH (the codes form of gem_score_ids; similarity qsim = m_q - qCH) and run in
+ * rounds.  Each round every non-empty queue W_e (one per entry set, in entry
+ * order) pops its best set P; P scoring below tau (the worst score in R once R
+ * holds ef sets) empties W_e, else every neighbour of P (in list order) that is
+ * not visited and has a vector in a cluster of C_query is marked visited, scored,
+ * and inserted (in that order) into W_e and R.  W_e and R keep the ef best sets
+ * (higher score, then lower id).  Rounds run until every queue is empty or
+ * max_rounds have run.
+ *   graph_off int64 [n_sets + 1], graph_nbrs int32  neighbour lists (device), each
+ *                                                   at most max_degree long, ids
+ *                                                   in [0, n_sets), no repeats
+ *   cluster_mask uint32 [n_queries x ceil(k2/32)]   C_query (gem_cluster_filter)
+ *   entries int64 [n_queries x entry_stride]       entry sets (gem_entry_points);
+ *                                                   -1 and repeats are skipped
+ *   out_ids int64, out_scores float [n_queries x ef] R best first; -1 / -inf past
+ *                                                   its size
+ *   out_rounds (host int32, may be NULL)            rounds run
+ * Needs the store's codebook (before the workspace was created) and C_index
+ * (gem_store_set_index_centroids).  Allocates its scratch and blocks until done.
+ * Errors: GEM_ERR_INVALID (NULL, ef outside 1..4096, bad sizes, a neighbour id
+ * out of range or a list longer than max_degree), GEM_ERR_STATE, GEM_ERR_OOM.
+ */
+gem_status gem_beam_search(const gem_store* store, gem_workspace* ws, const float* q, const int64_t* q_offsets,
+                           int32_t n_queries, int64_t n_q_rows, const int64_t* graph_off, const int32_t* graph_nbrs,
+                           int32_t max_degree, const uint32_t* cluster_mask, const int64_t* entries,
+                           int32_t entry_stride, int32_t ef, int32_t max_rounds, int64_t* out_ids, float* out_scores,
+                           int32_t* out_rounds, void* stream);
+
+/*
  * Scratch for scoring calls against `store`.  Bounds fix the memory once:
  *   max_queries  -- query sets per call
  *   max_q_rows   -- total query vectors per call

@@ -277,6 +277,27 @@ def entry_points(store: Store, cluster_lists, cluster_counts, seed: int = 0, str
     return out
 
 
+def beam_search(store: Store, ws: Workspace, q, q_offsets, graph_off, graph_nbrs, cluster_mask, entries,
+                ef: int = 64, max_rounds: int = 1000, max_degree: int = None, stream=None):
+    """Cluster-guided multi-path beam search (Algorithm 5) of every query over the
+    graph (CSR over the stored sets): (ids int64 [B, ef], qsim float32 [B, ef],
+    rounds)."""
+    q, qo, B, rows = _queries(q, q_offsets)
+    go = _dev(graph_off, torch.int64, "graph_off")
+    gn = _dev(graph_nbrs, torch.int32, "graph_nbrs")
+    if max_degree is None:
+        max_degree = max(1, int((go[1:] - go[:-1]).max().item())) if go.numel() > 1 else 1
+    mask = _dev(cluster_mask.contiguous(), torch.int32, "cluster_mask")
+    ent = _dev(entries.contiguous(), torch.int64, "entries")
+    out_i = torch.empty((B, ef), dtype=torch.int64, device=q.device)
+    out_s = torch.empty((B, ef), dtype=torch.float32, device=q.device)
+    rounds = ctypes.c_int32()
+    _check(lib.gem_beam_search(store.handle, ws.handle, _ptr(q), _ptr(qo), B, rows, _ptr(go), _ptr(gn), max_degree,
+                               _ptr(mask), _ptr(ent), ent.shape[1], ef, max_rounds, _ptr(out_i), _ptr(out_s),
+                               ctypes.byref(rounds), _stream(stream)))
+    return out_i, out_s, rounds.value
+
+
 def assign_codes(x, centroids, with_best: bool = False, stream=None):
     """NN(x): index of the centroid with the largest inner product (ties: lowest)."""
     x = _dev(x, torch.float32, "x")

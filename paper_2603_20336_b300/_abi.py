@@ -22,6 +22,7 @@ SIGNATURES = {
     "gem_cluster_filter": (C.c_int, [P, P, I32, I32, P, I32, I32, P, P, P, P]),
     "gem_store_set_index_centroids": (C.c_int, [P, P, I32, P]),
     "gem_entry_points": (C.c_int, [P, P, P, I32, I32, C.c_uint64, P, P]),
+    "gem_beam_search": (C.c_int, [P, P, P, P, I32, I64, P, P, I32, P, P, I32, I32, I32, P, P, P, P]),
     "gem_estimate_codes": (C.c_int, [P, P, P, P, I32, I64, P, P, I64, P, P]),
     "gem_workspace_create": (C.c_int, [P, I32, I64, I32, I64, I32, C.POINTER(P)]),
     "gem_workspace_destroy": (None, [P]),

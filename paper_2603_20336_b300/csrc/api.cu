@@ -617,6 +617,27 @@ gem_status gem_score_ids(const gem_store* s, gem_workspace* w, const float* q,
   return fail(GEM_ERR_INVALID, "unknown compute dtype");
 }
 
+gem_status gem_beam_search(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
+                           int32_t n_queries, int64_t n_q_rows, const int64_t* graph_off, const int32_t* graph_nbrs,
+                           int32_t max_degree, const uint32_t* cluster_mask, const int64_t* entries,
+                           int32_t entry_stride, int32_t ef, int32_t max_rounds, int64_t* out_ids, float* out_scores,
+                           int32_t* out_rounds, void* stream) {
+  gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
+  if (r != GEM_OK) return r;
+  if (!graph_off || !graph_nbrs || !cluster_mask || !entries || !out_ids || !out_scores)
+    return fail(GEM_ERR_INVALID, "NULL argument");
+  if (ef < 1 || ef > 4096) return fail(GEM_ERR_INVALID, "ef must be 1..4096");
+  if (entry_stride < 1 || max_degree < 1 || max_rounds < 0) return fail(GEM_ERR_INVALID, "bad sizes");
+  if (s->k1 == 0 || !w->d_qcodes)
+    return fail(GEM_ERR_STATE, "the search scores by qCH: a codebook is needed before the workspace is created");
+  if (s->k2 == 0) return fail(GEM_ERR_STATE, "the cluster test needs C_index (gem_store_set_index_centroids)");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  r = launch_assign(q, n_q_rows, s->d_codebook, s->k1, w->d_qcodes, nullptr, st);
+  if (r != GEM_OK) return r;
+  return beam_search(s, w, q, q_offsets, n_queries, graph_off, graph_nbrs, max_degree, cluster_mask, entries,
+                     entry_stride, ef, max_rounds, out_ids, out_scores, out_rounds, st);
+}
+
 gem_status gem_estimate_codes(const gem_store* s, gem_workspace* w, const float* q,
                               const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
                               const int64_t* cand_offsets, const int64_t* cand_ids, int64_t n_cands,

@@ -251,6 +251,10 @@ gem_status launch_topk(gem_workspace* ws, const float* scores, const int64_t* ro
 
 // Codes, k-means and the quantized estimate (codes.cu).
 gem_status launch_cluster_index(gem_store* s, cudaStream_t st);
+gem_status beam_search(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
+                       int32_t n_queries, const int64_t* graph_off, const int32_t* graph_nbrs, int32_t max_degree,
+                       const uint32_t* cluster_mask, const int64_t* entries, int32_t entry_stride, int32_t ef,
+                       int32_t max_rounds, int64_t* out_ids, float* out_scores, int32_t* out_rounds, cudaStream_t stm);
 gem_status launch_entry_points(const gem_store* s, const int32_t* lists, const int32_t* counts, int32_t n_queries,
                                int32_t stride, uint64_t seed, int64_t* out, cudaStream_t st);
 gem_status launch_cluster_filter(const float* q, const int64_t* q_offsets, int32_t n_queries, const float* centroids,

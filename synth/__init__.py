@@ -136,6 +136,22 @@ def shift_lists(cand_ids: np.ndarray, rnd: int, n_docs: int, step: int = 7919) -
     return ((cand_ids + rnd * step) % n_docs).astype(np.int64)
 
 
+def random_graph(n: int, degree: int, seed: int):
+    """A seeded random undirected graph over n nodes as CSR (offsets int64 [n+1],
+    neighbours int32): every node draws `degree` distinct other nodes, edges are
+    made symmetric, and each list is sorted without repeats."""
+    rng = np.random.default_rng([seed, 0x6A])
+    src = np.repeat(np.arange(n), degree)
+    dst = (src + rng.integers(1, n, size=n * degree)) % n
+    a = np.concatenate([src, dst])
+    b = np.concatenate([dst, src])
+    key = np.unique(a.astype(np.int64) * n + b)
+    a, b = key // n, key % n
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(off, a + 1, 1)
+    return np.cumsum(off), b.astype(np.int32)
+
+
 # ---------------------------------------------------------------------------
 # Workloads.  Sizes follow the five benchmark configurations; the `small`
 # variants keep the same structure at sizes the FP64 oracle finishes in seconds.

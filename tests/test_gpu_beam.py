@@ -1,0 +1,87 @@
+"""GPU parity of the cluster-guided multi-path beam search (Algorithm 5), run in
+rounds over a seeded random graph.
+
+The oracle runs the same rounds sequentially with the GPU's own inputs to the
+search logic: the qsim score of every (query, set) pair (the codes form of the
+id-list scorer, whose values are checked against FP64 under the qCH row), the
+clusters of every set (its vectors' nearest C_index centroids), C_query and the
+entry sets.  Given those, every decision is exact, so R (ids and scores, best
+first) and the number of rounds must match bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gem():
+    import paper_2603_20336_b300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def setup(gem):
+    seed = 4321
+    cents = synth.centres(96, seed)
+    docs = synth.vector_sets(synth.lengths_lognormal(3000, 40.0, 0.5, 8, 120, seed), cents, seed)
+    store = gem.Store(docs.vecs.cuda(), docs.offsets, keep=("f32",))
+    C = gem.train_codebook(store, k1=256, iters=5, seed=1)
+    gem.set_codebook(store, C)
+    Ci = gem.kmeans(C, 24, iters=5, seed=2)
+    gem.set_index_centroids(store, Ci)
+    lens = np.array([32, 20, 32, 9, 32, 27, 32, 1, 32, 16])
+    qs = synth.vector_sets(lens, cents, seed + 1)
+    q, qo = qs.vecs.cuda(), torch.from_numpy(qs.offsets).cuda()
+    ws = gem.Workspace(store, max_queries=len(lens), max_q_rows=int(lens.sum()), max_q_len=32,
+                       max_cands=len(lens) * 3000)
+    mask, lst, cnt = gem.cluster_filter(q, qo, Ci, t=2, max_q_len=32)
+    ent = gem.entry_points(store, lst, cnt, seed=9)
+    go, gn = synth.random_graph(3000, 6, seed)
+    # the GPU's qsim of every (query, set) pair, by the search's own scorer
+    B, N = len(lens), store.n_sets
+    co = torch.arange(B + 1, dtype=torch.int64, device="cuda") * N
+    ids = torch.arange(N, dtype=torch.int64, device="cuda").repeat(B)
+    allq = gem.score_ids(store, ws, q, qo, co, ids, "codes").view(B, N).cpu().numpy()
+    codes = store.export("index_codes").cpu().numpy()
+    off = docs.offsets
+    set_clusters = [set(codes[off[s]:off[s + 1]].tolist()) for s in range(N)]
+    yield dict(store=store, ws=ws, q=q, qo=qo, mask=mask, lst=lst.cpu().numpy(), cnt=cnt.cpu().numpy(),
+               ent=ent, go=go, gn=gn, allq=allq, set_clusters=set_clusters, B=B)
+    ws.close()
+    store.close()
+
+
+@pytest.mark.parametrize("ef,max_rounds", [(16, 1000), (5, 1000), (40, 3)])
+def test_beam_search_matches_oracle_rounds(gem, setup, ef, max_rounds):
+    d = setup
+    ids, sc, rounds = gem.beam_search(d["store"], d["ws"], d["q"], d["qo"], torch.from_numpy(d["go"]).cuda(),
+                                      torch.from_numpy(d["gn"]).cuda(), d["mask"], d["ent"], ef=ef,
+                                      max_rounds=max_rounds)
+    assert d["ws"].status() == 0
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    ent = d["ent"].cpu().numpy()
+    want_rounds = 0
+    for b in range(d["B"]):
+        qc = d["lst"][b, :d["cnt"][b]]
+        R, r = oracle.beam_search(lambda s, b=b: float(d["allq"][b, s]), d["go"], d["gn"], d["set_clusters"], qc,
+                                  ent[b], ef=ef, max_rounds=max_rounds)
+        want_rounds = max(want_rounds, r)
+        n = len(R)
+        assert ids[b, :n].tolist() == [i for _, i in R], b
+        np.testing.assert_array_equal(sc[b, :n], np.array([s for s, _ in R], dtype=np.float32))
+        assert np.all(ids[b, n:] == -1)
+    assert rounds == want_rounds
+
+
+def test_beam_search_rejects_a_neighbour_out_of_range(gem, setup):
+    d = setup
+    gn = d["gn"].copy()
+    gn[:] = 5000           # every neighbour id out of range
+    with pytest.raises(Exception):
+        gem.beam_search(d["store"], d["ws"], d["q"], d["qo"], torch.from_numpy(d["go"]).cuda(),
+                        torch.from_numpy(gn).cuda(), d["mask"], d["ent"], ef=8)
