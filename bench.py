@@ -178,7 +178,7 @@ def _time(fn, reps=3, st=None):
     return e0.elapsed_time(e1) / reps
 
 
-def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms):
+def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, only=None):
     """Every hot-path row measured on its own (after the headline timing)."""
     B = qo.numel() - 1
     rows = q.shape[0]
@@ -186,6 +186,8 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms):
     out = torch.empty((B, store.n_sets), dtype=torch.float32, device=dev)
 
     def guard(name, fn):
+        if only and name not in only:
+            return
         try:
             stages[name] = fn()
         except Exception as e:  # a failing extra must not hide the headline line
@@ -251,6 +253,81 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms):
                 "tflops": 2.0 * rows * k2 * 128 / ms / 1e9, "mean_c_query": float(cnt.float().mean()),
                 "index_codes_and_members_s": idx_s, "entry_points_ms": ms_e,
                 "entry_points": int((seeds >= 0).sum())}
+
+    def graph_search():
+        # Algorithm 5 end to end on a 50,000-set text-shaped store: a 16-NN graph
+        # by the BF16 scorer (symmetrised), C_quant (Sec. 5.1 size) and C_index
+        # (k2 = 256), cluster filter (t = 4), entry points, beam search (ef = 64),
+        # exact FP32 rerank of R, top-10 against the exhaustive FP32 top-10
+        n = 50_000
+        wg = synth.text_corpus(seed=1240, n_sets=n, n_queries=B, device=dev)
+        sg = gem.Store(wg.docs.vecs, wg.docs.offsets, keep=("f32", "bf16"))
+        qg = wg.queries.vecs
+        qog = torch.from_numpy(wg.queries.offsets).to(dev)
+        lens = wg.docs.lengths()
+        t0 = time.perf_counter()
+        rows_max = max(int(wg.docs.offsets[min(n, a + 5000)] - wg.docs.offsets[a]) for a in range(0, n, 5000))
+        wsg = gem.Workspace(sg, max_queries=5000, max_q_rows=rows_max, max_q_len=int(lens.max()), max_k=17)
+        nbr = []
+        for a in range(0, n, 5000):
+            b1 = min(n, a + 5000)
+            qd = wg.docs.vecs[int(wg.docs.offsets[a]):int(wg.docs.offsets[b1])]
+            qod = torch.from_numpy(wg.docs.offsets[a:b1 + 1] - wg.docs.offsets[a]).to(dev)
+            sc = gem.score_all(sg, wsg, qd, qod, "bf16")
+            ids, _ = gem.topk(wsg, sc, 17)
+            nbr.append(ids.cpu().numpy())
+        wsg.close()
+        nbr = np.concatenate(nbr)
+        src = np.repeat(np.arange(n), nbr.shape[1])
+        dst = nbr.ravel()
+        keep = dst != src
+        a_, b_ = np.concatenate([src[keep], dst[keep]]), np.concatenate([dst[keep], src[keep]])
+        key = np.unique(a_.astype(np.int64) * n + b_)
+        go = np.zeros(n + 1, dtype=np.int64)
+        np.add.at(go, key // n + 1, 1)
+        go = np.cumsum(go)
+        gn = (key % n).astype(np.int32)
+        graph_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        V = sg.n_vecs
+        k1 = 1 << int(np.floor(np.log2(16.0 * np.sqrt(V))))
+        Cg = gem.train_codebook(sg, k1=k1, iters=10, sample=min(V, 1_000_000), seed=5)
+        gem.set_codebook(sg, Cg)
+        Ci = gem.kmeans(Cg, 256, iters=10, seed=6)
+        gem.set_index_centroids(sg, Ci)
+        torch.cuda.synchronize()
+        index_s = time.perf_counter() - t0
+        wsq = gem.Workspace(sg, max_queries=B, max_q_rows=qg.shape[0], max_q_len=32, max_cands=B * 64, max_k=64)
+        go_d, gn_d = torch.from_numpy(go).to(dev), torch.from_numpy(gn).to(dev)
+        res = {}
+
+        def search():
+            mask, lst, cnt = gem.cluster_filter(qg, qog, Ci, t=4, max_q_len=32)
+            ent = gem.entry_points(sg, lst, cnt, seed=11)
+            ids, _, rounds = gem.beam_search(sg, wsq, qg, qog, go_d, gn_d, mask, ent, ef=64)
+            pool = ids.clamp(min=0).view(-1)
+            po = torch.arange(B + 1, dtype=torch.int64, device=dev) * 64
+            rs = gem.score_ids(sg, wsq, qg, qog, po, pool, "f32")
+            rs = torch.where(ids.view(-1) >= 0, rs, torch.full_like(rs, -float("inf")))
+            top, _ = gem.topk(wsq, rs.view(B, 64), 10, ids=ids.contiguous())
+            res["rounds"] = rounds
+            return top
+
+        search()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        top = search()
+        torch.cuda.synchronize()
+        ms = 1000 * (time.perf_counter() - t0)
+        exact = gem.score_all(sg, wsq, qg, qog, "f32")
+        ex10 = torch.topk(exact, 10, dim=1).indices.cpu().numpy()
+        rec = float(np.mean([len(set(a.tolist()) & set(e.tolist())) / 10 for a, e in zip(top.cpu().numpy(), ex10)]))
+        out = {"n_sets": n, "queries": B, "graph_degree_mean": float(len(gn) / n), "graph_build_s": graph_s,
+               "k1": k1, "k2": 256, "index_build_s": index_s, "ef": 64, "t": 4, "rounds": res["rounds"],
+               "search_ms": ms, "queries_per_s": B / (ms * 1e-3), "recall_at_10_vs_exact_fp32": rec}
+        wsq.close()
+        sg.close()
+        return out
 
     def beam():
         nq, rounds = 4096, 20
@@ -336,6 +413,7 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms):
     guard("pages_50k", pages)
     guard("qch_estimate", qch)
     guard("cluster_filter", cluster)
+    guard("graph_search", graph_search)
     guard("beam_batch", beam)
     guard("backward", backward)
 
@@ -494,7 +572,8 @@ def run_gem(args, dist, rank, world, local):
                                  "reference": "exact FP64 top-100 of the oracle over all sets"}
     if rank == 0 and not args.no_extras:
         stages = line["stages"]
-        extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, ms)
+        extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, ms,
+                     only=set(args.stages.split(",")) if args.stages else None)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -509,6 +588,7 @@ def main():
     ap.add_argument("--cpu-queries", type=int, default=4, help="queries the FP64 oracle scores (ground truth)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-row stage measurements")
+    ap.add_argument("--stages", default="", help="comma-separated extra stages to run (default: all)")
     ap.add_argument("--schedule", default="", help="fixed tensor-core schedule 'm_tiles,variant,chunk_rows' "
                     "instead of the autotuner (for profiling)")
     args = ap.parse_args()

@@ -228,8 +228,8 @@ gem_status gem_entry_points(const gem_store* store, const int32_t* cluster_lists
 /*
  * gem_beam_search: cluster-guided multi-path beam search (Algorithm 5,
  * Sec. 4.5.3) of a batch of queries over a graph of the stored sets, scored by
- * qCH (the codes form of gem_score_ids; similarity qsim = m_q - qCH) and run in
- * rounds.  Each round every non-empty queue W_e (one per entry set, in entry
+ * qCH (the arithmetic of gem_estimate_codes, from centroid tables built once per
+ * call; similarity qsim = m_q - qCH) and run in rounds.  Each round every non-empty queue W_e (one per entry set, in entry
  * order) pops its best set P; P scoring below tau (the worst score in R once R
  * holds ef sets) empties W_e, else every neighbour of P (in list order) that is
  * not visited and has a vector in a cluster of C_query is marked visited, scored,
@@ -247,8 +247,10 @@ gem_status gem_entry_points(const gem_store* store, const int32_t* cluster_lists
  *   out_rounds (host int32, may be NULL)            rounds run
  * Needs the store's codebook (before the workspace was created) and C_index
  * (gem_store_set_index_centroids).  Allocates its scratch and blocks until done.
- * Errors: GEM_ERR_INVALID (NULL, ef outside 1..4096, bad sizes, a neighbour id
- * out of range or a list longer than max_degree), GEM_ERR_STATE, GEM_ERR_OOM.
+ * Errors: GEM_ERR_INVALID (NULL, ef outside 1..4096, bad sizes, more than 65,535
+ * query parts of 32 rows, a neighbour id out of range or a list longer than
+ * max_degree), GEM_ERR_STATE, GEM_ERR_OOM (the tables take n_queries x
+ * ceil(max_q_len / 32) x k1 x 128 bytes).
  */
 gem_status gem_beam_search(const gem_store* store, gem_workspace* ws, const float* q, const int64_t* q_offsets,
                            int32_t n_queries, int64_t n_q_rows, const int64_t* graph_off, const int32_t* graph_nbrs,

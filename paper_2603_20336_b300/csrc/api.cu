@@ -631,6 +631,8 @@ gem_status gem_beam_search(const gem_store* s, gem_workspace* w, const float* q,
   if (s->k1 == 0 || !w->d_qcodes)
     return fail(GEM_ERR_STATE, "the search scores by qCH: a codebook is needed before the workspace is created");
   if (s->k2 == 0) return fail(GEM_ERR_STATE, "the cluster test needs C_index (gem_store_set_index_centroids)");
+  if ((int64_t)n_queries * ((w->max_q_len + 31) / 32) > 65535)
+    return fail(GEM_ERR_INVALID, "more than 65,535 query parts of 32 rows in one search");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   r = launch_assign(q, n_q_rows, s->d_codebook, s->k1, w->d_qcodes, nullptr, st);
   if (r != GEM_OK) return r;

@@ -8,8 +8,8 @@
 //            else every neighbour P' of P (in list order) that is not visited and
 //            has a vector in a cluster of C_query is marked visited and queued
 //   compact  the queued sets of all queries into one candidate list (CSR)
-//   score    qsim = m_q - qCH of every queued set, by the codes form of the
-//            id-list scorer (the same FP32 arithmetic as gem_score_ids, GEM_CODES)
+//   score    qsim = m_q - qCH of every queued set from the queries' centroid
+//            tables, built once per search (the arithmetic of gem_estimate_codes)
 //   insert   in queue order, each scored set into its W_e and into R
 // and the host runs rounds until no queue is left.  W_e and R keep the ef best
 // sets under the total order (higher score, then lower id); they are unsorted
@@ -94,6 +94,7 @@ struct BeamState {
   int32_t* candq;     // their queue
   float* score;       // their scores
   int* flag;          // any queue non-empty at a round's start
+  float* tables;      // [B * max_np * k1 * 32] qCH tables of the queries
 };
 
 // Entries: accepted entry sets (not -1, not repeated) open one queue each and are
@@ -289,6 +290,7 @@ gem_status beam_search(const gem_store* s, gem_workspace* w, const float* q, con
   st.vwords = (int)((s->n_sets + 31) / 32);
   st.mwords = (s->k2 + 31) / 32;
   const size_t B = (size_t)n_queries;
+  const int max_np = (w->max_q_len + 31) / 32;
   std::vector<void*> bufs;
   auto keep = [&](void* p) { bufs.push_back(p); return p != nullptr; };
   bool ok = keep(bs_alloc(&st.nq, B) ? (void*)st.nq : nullptr) &&
@@ -306,7 +308,8 @@ gem_status beam_search(const gem_store* s, gem_workspace* w, const float* q, con
             keep(bs_alloc(&st.cand, B * st.cap) ? (void*)st.cand : nullptr) &&
             keep(bs_alloc(&st.candq, B * st.cap) ? (void*)st.candq : nullptr) &&
             keep(bs_alloc(&st.score, B * st.cap) ? (void*)st.score : nullptr) &&
-            keep(bs_alloc(&st.flag, 1) ? (void*)st.flag : nullptr);
+            keep(bs_alloc(&st.flag, 1) ? (void*)st.flag : nullptr) &&
+            keep(bs_alloc(&st.tables, B * (size_t)max_np * s->k1 * 32) ? (void*)st.tables : nullptr);
   auto release = [&]() {
     for (void* p : bufs)
       if (p) cudaFree(p);
@@ -330,8 +333,8 @@ gem_status beam_search(const gem_store* s, gem_workspace* w, const float* q, con
     GEM_CUDA_TRY(cudaStreamSynchronize(stm));
     note_launches(2);
     if (total > 0) {
-      gem_status rr = launch_f32_score(s, w, q, q_offsets, n_queries, st.off, st.cand, total, st.score, stm,
-                                       w->d_qcodes);
+      gem_status rr = launch_qch_scan_ids(s, st.tables, q_offsets, n_queries, max_np, st.off, st.cand, st.score,
+                                          w->d_status, stm);
       if (rr != GEM_OK) return rr;
       bs_insert_kernel<<<grid, kBsThreads, 0, stm>>>(st);
       GEM_CUDA_TRY(cudaGetLastError());
@@ -347,6 +350,11 @@ gem_status beam_search(const gem_store* s, gem_workspace* w, const float* q, con
     return cuda_fail(e, "beam search state");
   }
   if (n_queries > 0) {
+    r = launch_qch_tables(s, w->d_qcodes, q_offsets, n_queries, max_np, st.tables, stm);
+    if (r != GEM_OK) {
+      release();
+      return r;
+    }
     bs_init_kernel<<<grid, kBsThreads, 0, stm>>>(st, entries, (int)s->n_sets);
     note_launches(1);
     r = score_insert();

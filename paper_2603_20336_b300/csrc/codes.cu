@@ -298,6 +298,40 @@ gem_status launch_gather_rows(const float* src, const int64_t* rows, int64_t n, 
   return GEM_OK;
 }
 
+gem_status launch_qch_tables(const gem_store* s, const int32_t* qcodes, const int64_t* q_offsets, int32_t n_queries,
+                             int max_np, float* T, cudaStream_t st) {
+  if (n_queries == 0) return GEM_OK;
+  dim3 tg((s->k1 + 255) / 256, n_queries * max_np);
+  qch_table_kernel<<<tg, 256, 0, st>>>(s->d_codebook, s->k1, qcodes, q_offsets, 0, max_np, T);
+  GEM_CUDA_TRY(cudaGetLastError());
+  note_launches(1);
+  return GEM_OK;
+}
+
+gem_status launch_qch_scan_ids(const gem_store* s, const float* T, const int64_t* q_offsets, int32_t n_queries,
+                               int max_np, const int64_t* cand_offsets, const int64_t* cand_ids, float* out,
+                               int* status, cudaStream_t st) {
+  if (n_queries == 0) return GEM_OK;
+  ScanArgs a;
+  a.T = T;
+  a.k1 = s->k1;
+  a.codes = s->d_codes;
+  a.doc_off = s->d_offsets;
+  a.n_sets = s->n_sets;
+  a.q_off = q_offsets;
+  a.q0 = 0;
+  a.nq = n_queries;
+  a.max_np = max_np;
+  a.cand_off = cand_offsets;
+  a.cand_ids = cand_ids;
+  a.out = out;
+  a.status = status;
+  qch_scan_kernel<<<s->n_sm * 8, 256, 0, st>>>(a);
+  GEM_CUDA_TRY(cudaGetLastError());
+  note_launches(1);
+  return GEM_OK;
+}
+
 gem_status launch_qch(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
                       int32_t n_queries, int64_t n_q_rows, const int64_t* cand_offsets,
                       const int64_t* cand_ids, float* est, cudaStream_t st) {

@@ -250,6 +250,11 @@ gem_status launch_topk(gem_workspace* ws, const float* scores, const int64_t* ro
                        int64_t* out_ids, float* out_scores, cudaStream_t st);
 
 // Codes, k-means and the quantized estimate (codes.cu).
+gem_status launch_qch_tables(const gem_store* s, const int32_t* qcodes, const int64_t* q_offsets, int32_t n_queries,
+                             int max_np, float* T, cudaStream_t st);
+gem_status launch_qch_scan_ids(const gem_store* s, const float* T, const int64_t* q_offsets, int32_t n_queries,
+                               int max_np, const int64_t* cand_offsets, const int64_t* cand_ids, float* out,
+                               int* status, cudaStream_t st);
 gem_status launch_cluster_index(gem_store* s, cudaStream_t st);
 gem_status beam_search(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
                        int32_t n_queries, const int64_t* graph_off, const int32_t* graph_nbrs, int32_t max_degree,

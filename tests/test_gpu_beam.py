@@ -2,8 +2,8 @@
 rounds over a seeded random graph.
 
 The oracle runs the same rounds sequentially with the GPU's own inputs to the
-search logic: the qsim score of every (query, set) pair (the codes form of the
-id-list scorer, whose values are checked against FP64 under the qCH row), the
+search logic: the qsim score of every (query, set) pair (gem_estimate_codes,
+whose values are checked against FP64 under the qCH row), the
 clusters of every set (its vectors' nearest C_index centroids), C_query and the
 entry sets.  Given those, every decision is exact, so R (ids and scores, best
 first) and the number of rounds must match bit for bit.
@@ -42,11 +42,11 @@ def setup(gem):
     mask, lst, cnt = gem.cluster_filter(q, qo, Ci, t=2, max_q_len=32)
     ent = gem.entry_points(store, lst, cnt, seed=9)
     go, gn = synth.random_graph(3000, 6, seed)
-    # the GPU's qsim of every (query, set) pair, by the search's own scorer
+    # the GPU's qsim of every (query, set) pair, by the search's own arithmetic
+    # (centroid tables and lookups; the all-sets form is bit-identical to the
+    # id-list form the search uses)
     B, N = len(lens), store.n_sets
-    co = torch.arange(B + 1, dtype=torch.int64, device="cuda") * N
-    ids = torch.arange(N, dtype=torch.int64, device="cuda").repeat(B)
-    allq = gem.score_ids(store, ws, q, qo, co, ids, "codes").view(B, N).cpu().numpy()
+    allq = gem.estimate_codes(store, ws, q, qo).cpu().numpy()
     codes = store.export("index_codes").cpu().numpy()
     off = docs.offsets
     set_clusters = [set(codes[off[s]:off[s + 1]].tolist()) for s in range(N)]
