@@ -103,13 +103,17 @@ def score_ids(q, q_offsets, vecs, offsets, cand_offsets, cand_ids) -> np.ndarray
 # top-k (Eq. 2) and the final exact rerank of Algorithm 5
 # ---------------------------------------------------------------------------
 
-def topk(scores, k: int, ids=None):
+def topk(scores, k: int, ids=None, exclude=None):
     """k-argmax of one row of scores: sorted by score descending, ties by lower id.
+    exclude: ids never returned (sets deleted lazily, Sec. 4.6).
 
     Returns (ids int64 [min(k, n)], scores float64 [min(k, n)]).
     """
     s = _f64(scores)
     i = np.arange(len(s), dtype=np.int64) if ids is None else _i64(ids)
+    if exclude is not None and len(exclude):
+        keep = ~np.isin(i, np.asarray(list(exclude), dtype=np.int64))
+        s, i = s[keep], i[keep]
     order = np.lexsort((i, -s))      # primary key: -score, secondary: id
     order = order[:k]
     return i[order], s[order]
@@ -245,7 +249,7 @@ def entry_points(query_clusters, members, seed: int):
 
 
 def beam_search(score, graph_off, graph_nbrs, set_clusters, query_clusters, entries, ef: int,
-                max_rounds: int = 1 << 30):
+                max_rounds: int = 1 << 30, dead=()):
     """Cluster-guided multi-path beam search of one query (Algorithm 5, Sec. 4.5.3),
     in rounds: in every round each non-empty queue W_e pops its best set P (in
     entry order); if P scores below tau (the worst score in R once R holds ef sets,
@@ -258,8 +262,9 @@ def beam_search(score, graph_off, graph_nbrs, set_clusters, query_clusters, entr
     higher score, then lower set id; W_e and R keep the ef best.  score(s) gives the
     score of set s; set_clusters[s] is the set of clusters of s (C(P)) and
     query_clusters the clusters of C_query.  entries: the entry sets, in order
-    (duplicates and -1 skipped).  Returns (R as a list of (score, id), best first,
-    the number of rounds run).
+    (duplicates and -1 skipped).  dead: sets deleted lazily (Sec. 4.6), still
+    traversed through their W_e but never placed in R.  Returns (R as a list of
+    (score, id), best first, the number of rounds run).
     """
     import bisect
 
@@ -277,8 +282,9 @@ def beam_search(score, graph_off, graph_nbrs, set_clusters, query_clusters, entr
         visited.add(e)
         sc = score(e)
         queues.append([key(sc, e)])
-        bisect.insort(R, key(sc, e))
-        del R[ef:]
+        if e not in dead:
+            bisect.insort(R, key(sc, e))
+            del R[ef:]
     rounds = 0
     while any(queues) and rounds < max_rounds:
         rounds += 1
@@ -301,8 +307,9 @@ def beam_search(score, graph_off, graph_nbrs, set_clusters, query_clusters, entr
             k = key(score(nb), nb)
             bisect.insort(queues[qi], k)
             del queues[qi][ef:]
-            bisect.insort(R, k)
-            del R[ef:]
+            if nb not in dead:
+                bisect.insort(R, k)
+                del R[ef:]
     return [(-k[0], k[1]) for k in R], rounds
 
 

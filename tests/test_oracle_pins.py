@@ -528,3 +528,14 @@ def test_beam_search_complete_graph_finds_exact_top_ef():
     R, _ = oracle.beam_search(lambda s: vals[s], off, nbrs, [{2}] * n, [2, 7], [3], ef=5)
     want = sorted(((vals[i], i) for i in range(n)), key=lambda x: (-x[0], x[1]))[:5]
     assert R == want
+
+
+def test_lazy_deletion_topk_and_beam_search():
+    # top-k never returns a deleted set
+    s = np.array([0.9, 0.8, 0.95, 0.1])
+    ids, _ = oracle.topk(s, 2, exclude={2})
+    assert ids.tolist() == [0, 1]
+    # a deleted set on the path is still traversed but never placed in R
+    off, nbrs = _chain(10)
+    R, _ = oracle.beam_search(lambda x: float(x), off, nbrs, [{0}] * 10, [0], [0], ef=3, dead={8})
+    assert R == [(9.0, 9), (7.0, 7), (6.0, 6)]
