@@ -17,6 +17,7 @@ Contents and the passage each follows:
                                   cluster of C_query (SplitMix64-based draw, splitmix64_next / entry_hash)
   beam_search                     Algorithm 5 / Sec. 4.5.3: cluster-guided multi-path beam search, in rounds
   qch_distance, qch_similarity    Sec. 4.5.3, Eq. 16, with d_X = 1 - <.,.> (Sec. 4.2.1)
+  qch_asym_*                      Eq. 16 with only the stored side quantized (a variant)
   k1_for                          Sec. 5.1 parameter settings: |C_quant| = 2^floor(log2(16 sqrt(#vectors)))
   bf16_round, fp8_e4m3_quantize   storage formats of the low-precision path (not in the paper)
   maxsim_grad, contrastive_*      gradient of Eq. 1 (not in the paper)
@@ -30,7 +31,7 @@ and the paper's worked example, except:
 from .maxsim import (  # noqa: F401
     chamfer, score_all, score_ids, topk, rerank, recall_at_k,
     assign_codes, cluster_filter, cluster_members, entry_points, entry_hash, splitmix64_next, beam_search,
-    qch_distance, qch_similarity, qch_score_all, qch_score_ids, k1_for,
+    qch_distance, qch_similarity, qch_score_all, qch_score_ids, qch_asym_similarity, qch_asym_score_all, k1_for,
     bf16_round, fp8_e4m3_round, fp8_e4m3_quantize,
     maxsim_grad, contrastive_loss, contrastive_dscores, kmeans_update,
 )

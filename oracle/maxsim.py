@@ -370,6 +370,33 @@ def qch_score_ids(q_codes, q_offsets, p_codes, offsets, cand_offsets, cand_ids, 
     return out
 
 
+def qch_asym_similarity(Q, p_codes, C) -> float:
+    """Asymmetric qCH in similarity form: sum over q of max over p of <q, NN(p)>.
+
+    Only the stored side is quantized; the query vectors stay exact.  This is
+    Eq. 16 with d_X(q, NN(p)) = 1 - <q, NN(p)> in place of d_X(NN(q), NN(p)), a
+    variant of the estimate (Sec. 4.5.3 quantizes both sides).
+    """
+    Q = _f64(Q)
+    b = _f64(C)[_i64(p_codes)]
+    return float((Q @ b.T).max(axis=1).sum())
+
+
+def qch_asym_score_all(q, q_offsets, p_codes, offsets, C) -> np.ndarray:
+    """qch_asym_similarity(Q_b, P_n) for every query b and stored set n: float64 [B, N]."""
+    C = _f64(C)
+    q = _f64(q)
+    qo = _i64(q_offsets)
+    off = _i64(offsets)
+    pc = _i64(p_codes)
+    out = np.empty((len(qo) - 1, len(off) - 1))
+    for b in range(len(qo) - 1):
+        table = q[qo[b]:qo[b + 1]] @ C.T         # <q_i, C_c> for every centroid c
+        sims = table[:, pc]                      # [m_q, rows]: <q_i, C_{NN(p_j)}>
+        out[b] = np.maximum.reduceat(sims, off[:-1], axis=1).sum(axis=0)
+    return out
+
+
 def k1_for(n_vectors: int) -> int:
     """|C_quant| = 2^floor(log2(16 * sqrt(#vectors))) (Sec. 5.1, parameter settings)."""
     return 1 << int(math.floor(math.log2(16.0 * math.sqrt(n_vectors))))

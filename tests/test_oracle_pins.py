@@ -217,6 +217,32 @@ def test_qch_brute_force_and_batched_forms():
     assert got.tolist() == pytest.approx([S[0, 2], S[1, 0], S[1, 3]], abs=1e-13)
 
 
+def test_asymmetric_qch_pins():
+    """Asymmetric qCH (stored side quantized only): brute force; a codebook holding
+    every stored vector makes it the exact CH whatever the query vectors are; with
+    the query vectors themselves centroids it equals the symmetric estimate."""
+    rng = np.random.default_rng(21)
+    Q, P = _unit(rng, 5, 16), _unit(rng, 7, 16)
+    C = np.vstack([_unit(rng, 3, 16), P])
+    pc = oracle.assign_codes(P, C)
+    assert pc.tolist() == list(range(3, 10))
+    assert oracle.qch_asym_similarity(Q, pc, C) == pytest.approx(oracle.chamfer(Q, P), abs=1e-13)
+    C2 = _unit(rng, 12, 16)
+    pc2 = rng.integers(0, 12, size=7)
+    brute = sum(max(float(np.dot(q, C2[c])) for c in pc2) for q in Q)
+    assert oracle.qch_asym_similarity(Q, pc2, C2) == pytest.approx(brute, abs=1e-13)
+    qc = np.array([4, 0, 11])
+    assert oracle.qch_asym_similarity(C2[qc], pc2, C2) == pytest.approx(oracle.qch_similarity(qc, pc2, C2),
+                                                                       abs=1e-13)
+    lens = np.array([3, 4])
+    off = np.concatenate([[0], np.cumsum(lens)])
+    S = oracle.qch_asym_score_all(Q, np.array([0, 2, 5]), pc2, off, C2)
+    for b, (q0, q1) in enumerate([(0, 2), (2, 5)]):
+        for n in range(2):
+            want = oracle.qch_asym_similarity(Q[q0:q1], pc2[off[n]:off[n + 1]], C2)
+            assert S[b, n] == pytest.approx(want, abs=1e-13)
+
+
 def test_codebook_size_formula_reproduces_paper():
     g = json.load(open(os.path.join(GOLD, "codebook_sizes.json")))
     for c in g["cases"]:
