@@ -9,6 +9,7 @@ reordering beyond a loop over documents.
 
 Contents and the passage each follows:
   chamfer, score_all, score_ids   Sec. 3.1, Definition 1 (Eq. 1), Sim = inner product
+  chamfer_l2, score_all_l2        Definition 1 with Sim = -(L2 distance)
   topk                            Sec. 3.1, problem statement (Eq. 2); ties by lower id
   rerank                          Algorithm 5, final step: exact CH over a candidate pool
   assign_codes                    Sec. 4.1.1 / Sec. 4.2.2: NN(x) = nearest centroid of C_quant
@@ -29,7 +30,7 @@ and the paper's worked example, except:
   invariants are tested).
 """
 from .maxsim import (  # noqa: F401
-    chamfer, score_all, score_ids, topk, rerank, recall_at_k,
+    chamfer, score_all, score_ids, chamfer_l2, score_all_l2, topk, rerank, recall_at_k,
     assign_codes, cluster_filter, cluster_members, entry_points, entry_hash, splitmix64_next, beam_search,
     qch_distance, qch_similarity, qch_score_all, qch_score_ids, qch_asym_similarity, qch_asym_score_all, k1_for,
     bf16_round, fp8_e4m3_round, fp8_e4m3_quantize,

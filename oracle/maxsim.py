@@ -79,6 +79,35 @@ def score_all(q, q_offsets, vecs, offsets, with_l1: bool = False):
     return (out, l1) if with_l1 else out
 
 
+def chamfer_l2(A, B) -> float:
+    """CH(A, B) of Definition 1 (Eq. 1) with Sim(a, b) = -||a - b||_2.
+
+    Definition 1 names the L2 distance as the other usual choice of Sim; as a
+    similarity it enters negated, so the maximum picks each a's nearest b:
+    CH = -sum over a of min over b of ||a - b||_2.
+    """
+    A = _f64(A)
+    B = _f64(B)
+    diff = A[:, None, :] - B[None, :, :]         # [m_a, m_b, d]
+    dist = np.sqrt((diff * diff).sum(axis=2))     # ||a_i - b_j||_2
+    return float(-dist.min(axis=1).sum())
+
+
+def score_all_l2(q, q_offsets, vecs, offsets, with_l1: bool = False):
+    """chamfer_l2(Q_b, P_n) for every query set b and stored set n: float64 [B, N].
+    with_l1=True also returns sum_i min_j ||q_i - p_j|| (= -score), the scale a
+    relative error of the sum is measured against."""
+    q = _f64(q)
+    qo = _i64(q_offsets)
+    off = _i64(offsets)
+    out = np.empty((len(qo) - 1, len(off) - 1))
+    for n in range(len(off) - 1):
+        P = _f64(vecs[off[n]:off[n + 1]])
+        for b in range(len(qo) - 1):
+            out[b, n] = chamfer_l2(q[qo[b]:qo[b + 1]], P)
+    return (out, -out) if with_l1 else out
+
+
 def score_ids(q, q_offsets, vecs, offsets, cand_offsets, cand_ids) -> np.ndarray:
     """CH(Q_b, P_id) for each id of query b's candidate list (Algorithm 5, candidate scoring).
 

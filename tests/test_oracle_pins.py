@@ -243,6 +243,34 @@ def test_asymmetric_qch_pins():
             assert S[b, n] == pytest.approx(want, abs=1e-13)
 
 
+def test_l2_chamfer_pins():
+    """Sim = -||a - b||: brute force on a hand example; zero on a set against
+    itself; invariant under a common translation and 1-homogeneous under a common
+    scale (the inner-product form is neither); on unit vectors the closed form
+    -sum_i sqrt(2 - 2 max_j <a_i, b_j>) links it to the inner-product maxima."""
+    A = np.array([[0.0, 0.0], [3.0, 4.0]])
+    B = np.array([[0.0, 1.0], [6.0, 8.0], [3.0, 0.0]])
+    # nearest of (0,0): (0,1) at 1; nearest of (3,4): (3,0) at 4 (vs (6,8) at 5)
+    assert oracle.chamfer_l2(A, B) == -5.0
+    rng = np.random.default_rng(31)
+    X, Y = rng.standard_normal((6, 9)), rng.standard_normal((4, 9))
+    assert oracle.chamfer_l2(X, X) == 0.0
+    t = rng.standard_normal(9) * 5
+    assert oracle.chamfer_l2(X + t, Y + t) == pytest.approx(oracle.chamfer_l2(X, Y), rel=1e-12)
+    assert oracle.chamfer_l2(2.5 * X, 2.5 * Y) == pytest.approx(2.5 * oracle.chamfer_l2(X, Y), rel=1e-12)
+    U, V = _unit(rng, 5, 9), _unit(rng, 7, 9)
+    closed = -np.sqrt(np.maximum(0.0, 2.0 - 2.0 * (U @ V.T).max(axis=1))).sum()
+    assert oracle.chamfer_l2(U, V) == pytest.approx(closed, abs=1e-12)
+    lens = np.array([2, 3])
+    off = np.concatenate([[0], np.cumsum(lens)])
+    P = np.vstack([Y[:2], Y[1:]])
+    S, L1 = oracle.score_all_l2(X, np.array([0, 4, 6]), P, off, with_l1=True)
+    for b, (q0, q1) in enumerate([(0, 4), (4, 6)]):
+        for n in range(2):
+            assert S[b, n] == oracle.chamfer_l2(X[q0:q1], P[off[n]:off[n + 1]])
+    np.testing.assert_array_equal(L1, -S)
+
+
 def test_codebook_size_formula_reproduces_paper():
     g = json.load(open(os.path.join(GOLD, "codebook_sizes.json")))
     for c in g["cases"]:
