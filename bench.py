@@ -178,7 +178,7 @@ def _time(fn, reps=3, st=None):
     return e0.elapsed_time(e1) / reps
 
 
-def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, only=None):
+def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, only=None, qch_k1=""):
     """Every hot-path row measured on its own (after the headline timing)."""
     B = qo.numel() - 1
     rows = q.shape[0]
@@ -208,24 +208,36 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, on
                 "bf16_rerank_step_speedup_vs_fp32_exhaustive": ms / step_ms}
 
     def qch():
+        # Sec. 5.1 codebook size by default; --qch-k1 sweeps it (Sec. 5.4 varies
+        # |C_quant|).  Each size is measured in both estimate forms.
         V = store.n_vecs
-        k1 = 1 << int(np.floor(np.log2(16.0 * np.sqrt(V))))   # Sec. 5.1 codebook size
-        t0 = time.perf_counter()
-        C = gem.train_codebook(store, k1=k1, iters=10, sample=min(V, 2_000_000), seed=5)
-        gem.set_codebook(store, C)
-        t_build = time.perf_counter() - t0
-        ws2 = gem.Workspace(store, max_queries=B, max_q_rows=rows, max_q_len=32, max_cands=B * R)
+        k1_formula = 1 << int(np.floor(np.log2(16.0 * np.sqrt(V))))
+        sizes = [int(x) for x in qch_k1.split(",")] if qch_k1 else [k1_formula]
         nq = min(B, 64)
-        est = torch.empty((nq, store.n_sets), dtype=torch.float32, device=dev)
-        ms = _time(lambda: gem.estimate_codes(store, ws2, q[: 32 * nq], qo[: nq + 1], out=est), reps=1)
-        pid, _ = gem.topk(ws2, est, R)
-        pool_off = torch.arange(nq + 1, dtype=torch.int64, device=dev) * R
-        rs = gem.score_ids(store, ws2, q[: 32 * nq], qo[: nq + 1], pool_off, pid.view(-1), "f32")
-        ids, _ = gem.topk(ws2, rs.view(nq, R), K, ids=pid.contiguous())
-        assert ws2.status() == 0
-        return {"k1": k1, "codebook_and_codes_s": t_build, "queries": nq, "ms": ms,
-                "pairs_per_s": nq * store.n_sets / (ms * 1e-3),
-                "recall_at_100_after_rerank": _recall(ids.cpu().numpy(), truth[:nq])}
+        runs = []
+        for k1 in sizes:
+            t0 = time.perf_counter()
+            C = gem.train_codebook(store, k1=k1, iters=10, sample=min(V, 2_000_000), seed=5)
+            gem.set_codebook(store, C)
+            t_build = time.perf_counter() - t0
+            ws2 = gem.Workspace(store, max_queries=B, max_q_rows=rows, max_q_len=32, max_cands=B * R)
+            est = torch.empty((nq, store.n_sets), dtype=torch.float32, device=dev)
+            for form in ("symmetric", "asymmetric"):
+                gem.set_qch_form(ws2, form)
+                ms = _time(lambda: gem.estimate_codes(store, ws2, q[: 32 * nq], qo[: nq + 1], out=est), reps=1)
+                pid, _ = gem.topk(ws2, est, R)
+                pool_off = torch.arange(nq + 1, dtype=torch.int64, device=dev) * R
+                rs = gem.score_ids(store, ws2, q[: 32 * nq], qo[: nq + 1], pool_off, pid.view(-1), "f32")
+                ids, _ = gem.topk(ws2, rs.view(nq, R), K, ids=pid.contiguous())
+                assert ws2.status() == 0
+                runs.append({"k1": k1, "form": form, "codebook_and_codes_s": t_build, "ms": ms,
+                             "pairs_per_s": nq * store.n_sets / (ms * 1e-3),
+                             "recall_at_100_after_rerank": _recall(ids.cpu().numpy(), truth[:nq])})
+            ws2.close()
+        head = runs[0]
+        return {"k1": head["k1"], "codebook_and_codes_s": head["codebook_and_codes_s"], "queries": nq,
+                "ms": head["ms"], "pairs_per_s": head["pairs_per_s"],
+                "recall_at_100_after_rerank": head["recall_at_100_after_rerank"], "runs": runs}
 
     def cluster():
         # Sec. 4.5.1: C_index = k-means of C_quant (second stage, k2 = 2,048),
@@ -573,7 +585,7 @@ def run_gem(args, dist, rank, world, local):
     if rank == 0 and not args.no_extras:
         stages = line["stages"]
         extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, ms,
-                     only=set(args.stages.split(",")) if args.stages else None)
+                     only=set(args.stages.split(",")) if args.stages else None, qch_k1=args.qch_k1)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -589,6 +601,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-row stage measurements")
     ap.add_argument("--stages", default="", help="comma-separated extra stages to run (default: all)")
+    ap.add_argument("--qch-k1", default="", help="comma-separated codebook sizes for the qch stage "
+                    "(default: the Sec. 5.1 formula)")
     ap.add_argument("--schedule", default="", help="fixed tensor-core schedule 'm_tiles,variant,chunk_rows' "
                     "instead of the autotuner (for profiling)")
     args = ap.parse_args()

@@ -67,6 +67,19 @@ typedef enum {
   GEM_TC_TWO_SETS = 2  /* two sets of epilogue warps on alternate tiles (m_tiles = 2) */
 } gem_tc_variant;
 
+/* Sim of Definition 1 (Eq. 1) for the exact scorers (gem_workspace_set_similarity). */
+typedef enum {
+  GEM_SIM_IP = 0,  /* inner product (cosine on unit vectors): CH = sum_i max_j <q_i, p_j> */
+  GEM_SIM_L2 = 1   /* negated L2 distance: CH = -sum_i min_j ||q_i - p_j||_2 */
+} gem_sim;
+
+/* Form of the quantized Chamfer estimate qCH (gem_workspace_set_qch_form). */
+typedef enum {
+  GEM_QCH_SYMMETRIC = 0,  /* Eq. 16 as written: both the query vectors and the stored
+                             vectors replaced by their nearest centroids */
+  GEM_QCH_ASYMMETRIC = 1  /* only the stored vectors replaced: sum_i max_j <q_i, C_{NN(p_j)}> */
+} gem_qch_form;
+
 /* Which copies of the vectors a store keeps (bit mask). */
 enum {
   GEM_KEEP_F32 = 1u,   /* FP32 master copy (needed by GEM_F32 scoring and the rerank) */
@@ -195,6 +208,19 @@ gem_status gem_cluster_filter(const float* q, const int64_t* q_offsets, int32_t 
                               int32_t* out_count, void* stream);
 
 /*
+ * gem_store_mark_deleted: lazy deletion (Sec. 4.6).  deleted != 0 marks every
+ * set in ids (int64 [n], device) deleted, deleted == 0 restores them.  A deleted
+ * set stays in the store and in any graph over it: gem_beam_search still
+ * traverses it, and every scoring call still scores it, but gem_topk,
+ * gem_search and the R of gem_beam_search never return it.  Repeated ids are
+ * fine.  Blocks until the ids are checked.
+ * Errors: GEM_ERR_INVALID (NULL with n > 0, n < 0, an id outside [0, n_sets):
+ * then no bit changes), GEM_ERR_OOM (the first call allocates ceil(n_sets / 32)
+ * + 1 words).
+ */
+gem_status gem_store_mark_deleted(gem_store* store, const int64_t* ids, int64_t n, int32_t deleted, void* stream);
+
+/*
  * gem_store_set_index_centroids: attach C_index (k2 coarse centroids, device
  * [k2 x 128] FP32, copied) to the store; every stored vector gets its nearest
  * C_index centroid (largest inner product, ties to the lower index; exported as
@@ -245,6 +271,8 @@ gem_status gem_entry_points(const gem_store* store, const int32_t* cluster_lists
  *   out_ids int64, out_scores float [n_queries x ef] R best first; -1 / -inf past
  *                                                   its size
  *   out_rounds (host int32, may be NULL)            rounds run
+ * A set the store marks deleted (gem_store_mark_deleted) is scored, queued and
+ * expanded like any other but never enters R.
  * Needs the store's codebook (before the workspace was created) and C_index
  * (gem_store_set_index_centroids).  Allocates its scratch and blocks until done.
  * Errors: GEM_ERR_INVALID (NULL, ef outside 1..4096, bad sizes, more than 65,535
@@ -271,6 +299,29 @@ gem_status gem_workspace_create(const gem_store* store, int32_t max_queries, int
                                 int32_t max_q_len, int64_t max_cands, int32_t max_k,
                                 gem_workspace** out);
 void gem_workspace_destroy(gem_workspace* ws);
+
+/*
+ * Sim of Definition 1 for every exact score computed through this workspace
+ * (gem_score_all, gem_score_ids, gem_search, gem_search_host).  Default
+ * GEM_SIM_IP.  GEM_SIM_L2 (Sim(a, b) = -||a - b||_2, so higher is still better)
+ * runs on the FP32 scorers only: each term is -sqrt(min_j sum_k (q_ik - p_jk)^2),
+ * every difference rounded to FP32 and squared into the same two 64-term FMA
+ * chains as the dot product, then the same Kahan sum over query vectors.  Under
+ * GEM_SIM_L2, GEM_BF16 / GEM_FP8_E4M3 scoring, the codes form, gem_estimate_codes
+ * and gem_beam_search return GEM_ERR_UNSUPPORTED (qCH is defined for the
+ * inner-product Sim).  gem_batch and gem_maxsim_fwd / _bwd use the inner product.
+ * Errors: GEM_ERR_INVALID (NULL, unknown sim).
+ */
+gem_status gem_workspace_set_similarity(gem_workspace* ws, int32_t sim);
+
+/*
+ * Form of every qCH estimate computed through this workspace: gem_estimate_codes,
+ * gem_score_ids with GEM_CODES and gem_beam_search.  Default
+ * GEM_QCH_SYMMETRIC.  The asymmetric form keeps the query vectors exact (the
+ * tables hold <q_i, C_c>), so no query codes are assigned.
+ * Errors: GEM_ERR_INVALID (NULL, unknown form).
+ */
+gem_status gem_workspace_set_qch_form(gem_workspace* ws, int32_t form);
 
 /*
  * Schedule of the tensor-core scoring kernels on this workspace (the knobs the
@@ -340,7 +391,8 @@ gem_status gem_estimate_codes(const gem_store* store, gem_workspace* ws, const f
  * row; otherwise ids is int64 aligned with scores.  Ids must be < 2^32.
  * out_ids int64 [rows * k], out_scores float32 [rows * k] (may be NULL); a row
  * with fewer than k elements is padded with id -1 and score -inf.  NaN scores
- * are not supported.
+ * are not supported.  An element whose id is a set the workspace's store marks
+ * deleted (gem_store_mark_deleted) is not a candidate.
  */
 gem_status gem_topk(gem_workspace* ws, const float* scores, const int64_t* row_offsets, int32_t rows,
                     int64_t cols, const int64_t* ids, int32_t k, int64_t* out_ids, float* out_scores,
@@ -352,7 +404,8 @@ gem_status gem_topk(gem_workspace* ws, const float* scores, const int64_t* row_o
  * rerank_depth per query, rescore that pool with exact FP32 CH (Kahan sum over
  * query vectors) and return the top k of it.  rerank_depth == 0 skips the
  * rerank (the top k of the first pass is returned).  Needs GEM_KEEP_F32 when
- * rerank_depth > 0.  out_ids int64 [n_queries * k], out_scores float32 [n_queries * k].
+ * rerank_depth > 0.  Deleted sets (gem_store_mark_deleted) are scored but never
+ * returned.  out_ids int64 [n_queries * k], out_scores float32 [n_queries * k].
  */
 gem_status gem_search(const gem_store* store, gem_workspace* ws, const float* q,
                       const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
@@ -501,6 +554,14 @@ int64_t gem_kernel_launches(void);
 /* Synchronises `stream`, then returns and clears the workspace's device status
  * word (GEM_OK if no device-side error was recorded since the last check). */
 gem_status gem_stream_status(gem_workspace* ws, void* stream);
+
+/* Failure-detection self-test: one warp waits, through the same bounded
+ * mbarrier wait every pipelined kernel uses, on a barrier nothing arrives on.
+ * After budget_cycles SM cycles (1 .. 2^32) the wait gives up, records
+ * GEM_ERR_TIMEOUT in the workspace's status word and the kernel returns; the
+ * next gem_stream_status returns GEM_ERR_TIMEOUT and the context stays usable.
+ * Asynchronous on `stream`.  Errors: GEM_ERR_INVALID (NULL, budget out of range). */
+gem_status gem_selftest_wait_timeout(gem_workspace* ws, int64_t budget_cycles, void* stream);
 
 #ifdef __cplusplus
 }

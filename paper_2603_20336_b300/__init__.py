@@ -234,6 +234,30 @@ def set_schedule(ws: Workspace, m_tiles: int = 2, chunk_rows: int = 1 << 16, var
     _check(lib.gem_workspace_set_schedule(ws.handle, m_tiles, TC_VARIANTS[variant], chunk_rows))
 
 
+def selftest_wait_timeout(ws: Workspace, budget_cycles: int = 1 << 20, stream=None):
+    """Run the bounded-wait self-test: a wait on a barrier nothing arrives on
+    gives up after budget_cycles and records a timeout in ws's status word."""
+    _check(lib.gem_selftest_wait_timeout(ws.handle, budget_cycles, _stream(stream)))
+
+
+QCH_FORMS = {"symmetric": 0, "asymmetric": 1}
+SIMS = {"ip": 0, "l2": 1}
+
+
+def set_similarity(ws: Workspace, sim: str = "ip"):
+    """Sim of Definition 1 for the exact scorers of this workspace: "ip" (inner
+    product) or "l2" (negated L2 distance; FP32 scoring and rerank only)."""
+    _check(lib.gem_workspace_set_similarity(ws.handle, SIMS[sim]))
+
+
+def set_qch_form(ws: Workspace, form: str = "symmetric"):
+    """Form of every qCH estimate through this workspace (estimate_codes,
+    score_ids with "codes", beam_search): "symmetric" (both sides quantized, as
+    Eq. 16 writes) or "asymmetric" (exact query vectors against the stored
+    vectors' centroids)."""
+    _check(lib.gem_workspace_set_qch_form(ws.handle, QCH_FORMS[form]))
+
+
 def kmeans(x, k: int, iters: int = 10, seed: int = 0, stream=None):
     """Spherical k-means of the rows of x (e.g. C_quant -> C_index, the second
     clustering stage): float32 [k, 128] unit centroids."""
@@ -263,6 +287,14 @@ def set_index_centroids(store: Store, centroids, stream=None):
     c = _dev(centroids.contiguous(), torch.float32, "centroids")
     _check(lib.gem_store_set_index_centroids(store.handle, _ptr(c), c.shape[0], _stream(stream)))
     store.k2 = c.shape[0]
+
+
+def mark_deleted(store: Store, ids, deleted: bool = True, stream=None):
+    """Lazy deletion (Sec. 4.6): mark the sets `ids` deleted (or restore them with
+    deleted=False).  Deleted sets are still scored and traversed by the beam
+    search but never returned by topk, search or beam_search."""
+    i = torch.as_tensor(ids).to(dtype=torch.int64, device="cuda").reshape(-1).contiguous()
+    _check(lib.gem_store_mark_deleted(store.handle, _ptr(i), i.numel(), int(bool(deleted)), _stream(stream)))
 
 
 def entry_points(store: Store, cluster_lists, cluster_counts, seed: int = 0, stream=None):

@@ -21,6 +21,10 @@ SIGNATURES = {
     "gem_kmeans": (C.c_int, [P, I64, I32, I32, C.c_uint64, P, P]),
     "gem_cluster_filter": (C.c_int, [P, P, I32, I32, P, I32, I32, P, P, P, P]),
     "gem_store_set_index_centroids": (C.c_int, [P, P, I32, P]),
+    "gem_store_mark_deleted": (C.c_int, [P, P, I64, I32, P]),
+    "gem_workspace_set_qch_form": (C.c_int, [P, I32]),
+    "gem_workspace_set_similarity": (C.c_int, [P, I32]),
+    "gem_selftest_wait_timeout": (C.c_int, [P, I64, P]),
     "gem_entry_points": (C.c_int, [P, P, P, I32, I32, C.c_uint64, P, P]),
     "gem_beam_search": (C.c_int, [P, P, P, P, I32, I64, P, P, I32, P, P, I32, I32, I32, P, P, P, P]),
     "gem_estimate_codes": (C.c_int, [P, P, P, P, I32, I64, P, P, I64, P, P]),

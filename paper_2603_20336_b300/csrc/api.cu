@@ -104,6 +104,7 @@ void gem_store_destroy(gem_store* s) {
   dfree(s->d_icodes);
   dfree(s->d_member_off);
   dfree(s->d_members);
+  dfree(s->d_dead);
   for (auto& kv : s->chunks) dfree(kv.second.d_chunk_doc);
   cudaSetDevice(prev);
   delete s;
@@ -501,6 +502,16 @@ gem_status gem_store_set_index_centroids(gem_store* s, const float* centroids, i
   return launch_cluster_index(s, st);
 }
 
+gem_status gem_store_mark_deleted(gem_store* s, const int64_t* ids, int64_t n, int32_t deleted, void* stream) {
+  if (!s || (n > 0 && !ids)) return fail(GEM_ERR_INVALID, "NULL argument");
+  if (n < 0) return fail(GEM_ERR_INVALID, "n < 0");
+  gem_status r = check_current_device(s->device);
+  if (r != GEM_OK) return r;
+  r = launch_mark_deleted(s, ids, n, deleted != 0, reinterpret_cast<cudaStream_t>(stream));
+  if (r == GEM_ERR_INVALID) return fail(r, "set id out of range");
+  return r;
+}
+
 gem_status gem_entry_points(const gem_store* s, const int32_t* cluster_lists, const int32_t* cluster_counts,
                             int32_t n_queries, int32_t stride, uint64_t seed, int64_t* out_sets, void* stream) {
   if (!s || !cluster_lists || !cluster_counts || !out_sets) return fail(GEM_ERR_INVALID, "NULL argument");
@@ -527,6 +538,20 @@ gem_status gem_store_set_codebook(gem_store* s, const float* centroids, int32_t 
   if ((r = launch_assign(s->d_f32, s->n_vecs, s->d_codebook, k1, s->d_codes, nullptr, st)) != GEM_OK) return r;
   GEM_CUDA_TRY(cudaStreamSynchronize(st));
   s->k1 = k1;
+  return GEM_OK;
+}
+
+gem_status gem_workspace_set_similarity(gem_workspace* w, int32_t sim) {
+  if (!w) return fail(GEM_ERR_INVALID, "workspace is NULL");
+  if (sim != GEM_SIM_IP && sim != GEM_SIM_L2) return fail(GEM_ERR_INVALID, "unknown similarity");
+  w->sim = sim;
+  return GEM_OK;
+}
+
+gem_status gem_workspace_set_qch_form(gem_workspace* w, int32_t form) {
+  if (!w) return fail(GEM_ERR_INVALID, "workspace is NULL");
+  if (form != GEM_QCH_SYMMETRIC && form != GEM_QCH_ASYMMETRIC) return fail(GEM_ERR_INVALID, "unknown qCH form");
+  w->qch_form = form;
   return GEM_OK;
 }
 
@@ -562,6 +587,8 @@ static gem_status score_all_impl(const gem_store* s, gem_workspace* w, const flo
     if (!s->d_f32) return fail(GEM_ERR_STATE, "store keeps no fp32 copy");
     return launch_f32_score(s, w, q, q_offsets, n_queries, nullptr, nullptr, 0, scores, st);
   }
+  if (w->sim == GEM_SIM_L2 && (compute == GEM_BF16 || compute == GEM_FP8_E4M3))
+    return fail(GEM_ERR_UNSUPPORTED, "Sim = L2 distance is scored by GEM_F32 only");
   if (compute == GEM_BF16) {
     if (!s->d_bf16) return fail(GEM_ERR_STATE, "store keeps no bf16 copy");
     const int mt = w->tc_m_tiles;
@@ -605,8 +632,12 @@ gem_status gem_score_ids(const gem_store* s, gem_workspace* w, const float* q,
     return launch_f32_score(s, w, q, q_offsets, n_queries, cand_offsets, cand_ids, n_cands, scores, st);
   }
   if (compute == GEM_CODES) {
+    if (w->sim == GEM_SIM_L2) return fail(GEM_ERR_UNSUPPORTED, "qCH is defined for the inner-product Sim");
     if (!s->d_f32 || s->k1 == 0 || !w->d_qcodes)
       return fail(GEM_ERR_STATE, "the codes form needs a codebook before the workspace is created");
+    if (w->qch_form == GEM_QCH_ASYMMETRIC)
+      return launch_f32_score(s, w, q, q_offsets, n_queries, cand_offsets, cand_ids, n_cands, scores, st, nullptr,
+                              true);
     r = launch_assign(q, n_q_rows, s->d_codebook, s->k1, w->d_qcodes, nullptr, st);
     if (r != GEM_OK) return r;
     return launch_f32_score(s, w, q, q_offsets, n_queries, cand_offsets, cand_ids, n_cands, scores, st,
@@ -631,11 +662,14 @@ gem_status gem_beam_search(const gem_store* s, gem_workspace* w, const float* q,
   if (s->k1 == 0 || !w->d_qcodes)
     return fail(GEM_ERR_STATE, "the search scores by qCH: a codebook is needed before the workspace is created");
   if (s->k2 == 0) return fail(GEM_ERR_STATE, "the cluster test needs C_index (gem_store_set_index_centroids)");
+  if (w->sim == GEM_SIM_L2) return fail(GEM_ERR_UNSUPPORTED, "qCH is defined for the inner-product Sim");
   if ((int64_t)n_queries * ((w->max_q_len + 31) / 32) > 65535)
     return fail(GEM_ERR_INVALID, "more than 65,535 query parts of 32 rows in one search");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  r = launch_assign(q, n_q_rows, s->d_codebook, s->k1, w->d_qcodes, nullptr, st);
-  if (r != GEM_OK) return r;
+  if (w->qch_form == GEM_QCH_SYMMETRIC) {
+    r = launch_assign(q, n_q_rows, s->d_codebook, s->k1, w->d_qcodes, nullptr, st);
+    if (r != GEM_OK) return r;
+  }
   return beam_search(s, w, q, q_offsets, n_queries, graph_off, graph_nbrs, max_degree, cluster_mask, entries,
                      entry_stride, ef, max_rounds, out_ids, out_scores, out_rounds, st);
 }
@@ -647,6 +681,7 @@ gem_status gem_estimate_codes(const gem_store* s, gem_workspace* w, const float*
   gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
   if (r != GEM_OK) return r;
   if (!est) return fail(GEM_ERR_INVALID, "est is NULL");
+  if (w->sim == GEM_SIM_L2) return fail(GEM_ERR_UNSUPPORTED, "qCH is defined for the inner-product Sim");
   if (s->k1 == 0 || !w->d_tables)
     return fail(GEM_ERR_STATE, "store had no codebook when the workspace was created");
   if (cand_offsets && n_cands > 0 && !cand_ids) return fail(GEM_ERR_INVALID, "cand_ids is NULL");
@@ -868,6 +903,14 @@ gem_status gem_score_ids_noalloc(const gem_store* s, const float* q, const int64
 }
 
 int64_t gem_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+gem_status gem_selftest_wait_timeout(gem_workspace* w, int64_t budget_cycles, void* stream) {
+  if (!w) return fail(GEM_ERR_INVALID, "workspace is NULL");
+  if (budget_cycles < 1 || budget_cycles > ((int64_t)1 << 32)) return fail(GEM_ERR_INVALID, "budget out of range");
+  gem_status r = check_current_device(w->device);
+  if (r != GEM_OK) return r;
+  return launch_wait_selftest(w->d_status, budget_cycles, reinterpret_cast<cudaStream_t>(stream));
+}
 
 gem_status gem_stream_status(gem_workspace* w, void* stream) {
   if (!w) return fail(GEM_ERR_INVALID, "workspace is NULL");

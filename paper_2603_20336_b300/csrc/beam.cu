@@ -95,6 +95,7 @@ struct BeamState {
   float* score;       // their scores
   int* flag;          // any queue non-empty at a round's start
   float* tables;      // [B * max_np * k1 * 32] qCH tables of the queries
+  const uint32_t* dead;  // deleted sets (Sec. 4.6), or null
 };
 
 // Entries: accepted entry sets (not -1, not repeated) open one queue each and are
@@ -232,7 +233,8 @@ __global__ void bs_insert_kernel(BeamState st) {
       const int qi = st.candq[j];
       warp_insert(st.qsc + ((int64_t)b * st.S + qi) * st.ef, st.qid + ((int64_t)b * st.S + qi) * st.ef,
                   st.qsize + (int64_t)b * st.S + qi, st.ef, s, id);
-      warp_insert(rsc, rid, st.rsize + b, st.ef, s, id);
+      // a deleted set keeps its place on the paths but never enters R
+      if (!st.dead || !((st.dead[id >> 5] >> (id & 31)) & 1u)) warp_insert(rsc, rid, st.rsize + b, st.ef, s, id);
     }
   }
 }
@@ -289,6 +291,7 @@ gem_status beam_search(const gem_store* s, gem_workspace* w, const float* q, con
   st.cap = std::max(entry_stride, entry_stride * max_degree);
   st.vwords = (int)((s->n_sets + 31) / 32);
   st.mwords = (s->k2 + 31) / 32;
+  st.dead = s->d_dead;
   const size_t B = (size_t)n_queries;
   const int max_np = (w->max_q_len + 31) / 32;
   std::vector<void*> bufs;
@@ -350,7 +353,8 @@ gem_status beam_search(const gem_store* s, gem_workspace* w, const float* q, con
     return cuda_fail(e, "beam search state");
   }
   if (n_queries > 0) {
-    r = launch_qch_tables(s, w->d_qcodes, q_offsets, n_queries, max_np, st.tables, stm);
+    r = launch_qch_tables(s, w->d_qcodes, w->qch_form == GEM_QCH_ASYMMETRIC ? q : nullptr, q_offsets, n_queries,
+                          max_np, st.tables, stm);
     if (r != GEM_OK) {
       release();
       return r;

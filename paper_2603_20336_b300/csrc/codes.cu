@@ -144,10 +144,12 @@ __global__ void gather_rows_kernel(const float* __restrict__ src, const int64_t*
 // Tables of one batch of queries q0 .. q0+nq-1.  Part p of the batch is part
 // pi = p % max_np of query b = q0 + p / max_np (a part that query does not have
 // is skipped): T[p][c][i] = <C_{a_i}, C_c> for the part's rows i, zero beyond.
-// Block = (256 centroids, part).
+// With qvec (the asymmetric form) the exact query rows replace the centroids
+// of their codes: T[p][c][i] = <q_i, C_c>.  Block = (256 centroids, part).
 __global__ void __launch_bounds__(256)
 qch_table_kernel(const float* __restrict__ C, int k1, const int32_t* __restrict__ qcodes,
-                 const int64_t* __restrict__ q_off, int q0, int max_np, float* __restrict__ T) {
+                 const float* __restrict__ qvec, const int64_t* __restrict__ q_off, int q0, int max_np,
+                 float* __restrict__ T) {
   __shared__ __align__(16) float qa[32][kDim + 4];
   const int p = blockIdx.y;
   const int b = q0 + p / max_np, pi = p % max_np;
@@ -157,7 +159,7 @@ qch_table_kernel(const float* __restrict__ C, int k1, const int32_t* __restrict_
   const int rows = (int)min((int64_t)32, rr);
   for (int idx = threadIdx.x; idx < 32 * kDim; idx += blockDim.x) {
     const int i = idx / kDim, k = idx % kDim;
-    qa[i][k] = (i < rows) ? C[(int64_t)qcodes[r0 + i] * kDim + k] : 0.f;
+    qa[i][k] = (i >= rows) ? 0.f : qvec ? qvec[(r0 + i) * kDim + k] : C[(int64_t)qcodes[r0 + i] * kDim + k];
   }
   __syncthreads();
   const int c = blockIdx.x * 256 + threadIdx.x;
@@ -298,11 +300,11 @@ gem_status launch_gather_rows(const float* src, const int64_t* rows, int64_t n, 
   return GEM_OK;
 }
 
-gem_status launch_qch_tables(const gem_store* s, const int32_t* qcodes, const int64_t* q_offsets, int32_t n_queries,
-                             int max_np, float* T, cudaStream_t st) {
+gem_status launch_qch_tables(const gem_store* s, const int32_t* qcodes, const float* qvec, const int64_t* q_offsets,
+                             int32_t n_queries, int max_np, float* T, cudaStream_t st) {
   if (n_queries == 0) return GEM_OK;
   dim3 tg((s->k1 + 255) / 256, n_queries * max_np);
-  qch_table_kernel<<<tg, 256, 0, st>>>(s->d_codebook, s->k1, qcodes, q_offsets, 0, max_np, T);
+  qch_table_kernel<<<tg, 256, 0, st>>>(s->d_codebook, s->k1, qcodes, qvec, q_offsets, 0, max_np, T);
   GEM_CUDA_TRY(cudaGetLastError());
   note_launches(1);
   return GEM_OK;
@@ -336,15 +338,19 @@ gem_status launch_qch(const gem_store* s, gem_workspace* w, const float* q, cons
                       int32_t n_queries, int64_t n_q_rows, const int64_t* cand_offsets,
                       const int64_t* cand_ids, float* est, cudaStream_t st) {
   const int k1 = s->k1;
-  // query codes NN(q_i)
-  gem_status r = launch_assign(q, n_q_rows, s->d_codebook, k1, w->d_qcodes, nullptr, st);
-  if (r != GEM_OK) return r;
+  const bool asym = w->qch_form == GEM_QCH_ASYMMETRIC;
+  // query codes NN(q_i) (the symmetric form)
+  if (!asym) {
+    gem_status r = launch_assign(q, n_q_rows, s->d_codebook, k1, w->d_qcodes, nullptr, st);
+    if (r != GEM_OK) return r;
+  }
   const int max_np = (w->max_q_len + 31) / 32;
   const int q_per_batch = std::max(1, w->table_parts / max_np);
   for (int q0 = 0; q0 < n_queries; q0 += q_per_batch) {
     const int nq = std::min(q_per_batch, n_queries - q0);
     dim3 tg((k1 + 255) / 256, nq * max_np);
-    qch_table_kernel<<<tg, 256, 0, st>>>(s->d_codebook, k1, w->d_qcodes, q_offsets, q0, max_np, w->d_tables);
+    qch_table_kernel<<<tg, 256, 0, st>>>(s->d_codebook, k1, w->d_qcodes, asym ? q : nullptr, q_offsets, q0, max_np,
+                                         w->d_tables);
     ScanArgs a;
     a.T = w->d_tables;
     a.k1 = k1;

@@ -79,6 +79,9 @@ struct gem_store {
   int32_t* d_icodes = nullptr;    // [n_vecs]
   int64_t* d_member_off = nullptr;
   int32_t* d_members = nullptr;   // [n_vecs] set ids
+  // lazy deletion (Sec. 4.6): bit s set = set s is deleted; null until the first
+  // deletion.  Deleted sets are still scored and traversed, never returned.
+  uint32_t* d_dead = nullptr;     // [ceil(n_sets / 32)]
   // tensor maps of the doc copies, keyed by tile rows (box height)
   mutable std::map<int, CUtensorMap> tmap_bf16;
   mutable std::map<int, CUtensorMap> tmap_fp8;
@@ -97,6 +100,8 @@ struct gem_workspace {
   int n_passes = 0;
   int tc_m_tiles = 2;          // schedule of the tensor-core kernels
   int tc_variant = GEM_TC_PLAIN;
+  int qch_form = GEM_QCH_SYMMETRIC;  // every qCH estimate through this workspace
+  int sim = GEM_SIM_IP;              // Sim of Definition 1 for the exact FP32 scorers
   int tc_chunk_rows = 1 << 16;
 
   int* d_status = nullptr;
@@ -208,11 +213,13 @@ gem_status launch_tc_score_all(const gem_store* s, gem_workspace* ws, int comput
                                int variant, int chunk_rows, float* scores, cudaStream_t st);
 
 // FP32 SIMT exact MaxSim (Kahan over query vectors), all sets or id lists;
-// qcodes != nullptr selects the codes form (centroids in place of vectors).
+// qcodes != nullptr selects the codes form (centroids in place of vectors);
+// stored_codes alone (id lists) the asymmetric codes form: exact query rows,
+// stored vectors replaced by their centroids.
 gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* q,
                             const int64_t* q_offsets, int32_t n_queries, const int64_t* cand_offsets,
                             const int64_t* cand_ids, int64_t n_cands, float* scores, cudaStream_t st,
-                            const int32_t* qcodes = nullptr);
+                            const int32_t* qcodes = nullptr, bool stored_codes = false);
 
 // MaxSim forward with argmax and backward (backward.cu).
 gem_status launch_maxsim_fwd(const float* q, const int64_t* q_off, int32_t n_queries, const float* docs,
@@ -250,12 +257,15 @@ gem_status launch_topk(gem_workspace* ws, const float* scores, const int64_t* ro
                        int64_t* out_ids, float* out_scores, cudaStream_t st);
 
 // Codes, k-means and the quantized estimate (codes.cu).
-gem_status launch_qch_tables(const gem_store* s, const int32_t* qcodes, const int64_t* q_offsets, int32_t n_queries,
-                             int max_np, float* T, cudaStream_t st);
+// qvec != nullptr: asymmetric tables from the exact query rows (qcodes unused)
+gem_status launch_qch_tables(const gem_store* s, const int32_t* qcodes, const float* qvec, const int64_t* q_offsets,
+                             int32_t n_queries, int max_np, float* T, cudaStream_t st);
 gem_status launch_qch_scan_ids(const gem_store* s, const float* T, const int64_t* q_offsets, int32_t n_queries,
                                int max_np, const int64_t* cand_offsets, const int64_t* cand_ids, float* out,
                                int* status, cudaStream_t st);
 gem_status launch_cluster_index(gem_store* s, cudaStream_t st);
+gem_status launch_wait_selftest(int* status, long long budget, cudaStream_t st);
+gem_status launch_mark_deleted(gem_store* s, const int64_t* ids, int64_t n, bool deleted, cudaStream_t st);
 gem_status beam_search(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
                        int32_t n_queries, const int64_t* graph_off, const int32_t* graph_nbrs, int32_t max_degree,
                        const uint32_t* cluster_mask, const int64_t* entries, int32_t entry_stride, int32_t ef,

@@ -29,10 +29,12 @@ struct F32Args {
   const int32_t* codes;      // codes form: store codes, centroids and query codes
   const float* centroids;
   const int32_t* qcodes;
+  bool stored_codes;         // id lists, asymmetric codes form: exact query rows
 };
 
 // All sets: one CTA per (segment of kSegDocs sets, query), the query staged in
 // shared memory; consecutive CTAs share a segment, so its sets stay in L2.
+template <bool L2>
 __global__ void __launch_bounds__(kF32Threads, 2)
 f32_all_kernel(F32Args a, int max_q_len) {
   extern __shared__ float sm[];
@@ -62,8 +64,8 @@ f32_all_kernel(F32Args a, int max_q_len) {
     for (int64_t t = t0 + warp; t < t1; t += kF32Warps) {
       const int64_t r0 = a.doc_off[t];
       const int m_p = (int)(a.doc_off[t + 1] - r0);
-      const float score = warp_chamfer(qs, kQStride, m_q, a.docs + r0 * kDim, a.qcodes ? a.codes + r0 : nullptr,
-                                       a.centroids, m_p, stage, rowmax, qr, loaded_rg);
+      const float score = warp_chamfer<L2>(qs, kQStride, m_q, a.docs + r0 * kDim, a.qcodes ? a.codes + r0 : nullptr,
+                                           a.centroids, m_p, stage, rowmax, qr, loaded_rg);
       if (lane == 0) a.scores[(int64_t)b * a.n_sets + t] = score;
     }
   }
@@ -72,7 +74,7 @@ f32_all_kernel(F32Args a, int max_q_len) {
 // Id lists: every warp takes one contiguous range of the n_cands candidates
 // (equal shares, whatever the list lengths) and reads the rows of the current
 // query straight into registers when the query changes.
-template <bool Coded>
+template <bool Coded, bool L2>
 __global__ void __launch_bounds__(kF32Threads, 2)
 f32_ids_kernel(F32Args a, int max_q_len, int64_t n_cands) {
   extern __shared__ float sm[];
@@ -116,8 +118,9 @@ f32_ids_kernel(F32Args a, int max_q_len, int64_t n_cands) {
         score = warp_chamfer_coded_q(a.centroids, a.qcodes + q0, m_q, a.docs + r0 * kDim, a.codes + r0, m_p,
                                      stage, rowmax, qr, loaded_rg);
       } else {
-        score = warp_chamfer(a.q + q0 * kDim, kDim, m_q, a.docs + r0 * kDim, nullptr, nullptr, m_p, stage, rowmax,
-                             qr, loaded_rg);
+        score = warp_chamfer<L2>(a.q + q0 * kDim, kDim, m_q, a.docs + r0 * kDim,
+                                 a.stored_codes ? a.codes + r0 : nullptr, a.centroids, m_p, stage, rowmax, qr,
+                                 loaded_rg);
       }
     }
     if (lane == 0) a.scores[t] = score;
@@ -133,6 +136,7 @@ f32_ids_kernel(F32Args a, int max_q_len, int64_t n_cands) {
 // one per lane, loaded a window in advance.
 constexpr int kRing = 4;
 
+template <bool L2>
 __global__ void __launch_bounds__(kF32Threads, 2)
 f32_ids_stream_kernel(F32Args a, int max_q_len, int64_t n_cands) {
   extern __shared__ float sm[];
@@ -246,34 +250,7 @@ f32_ids_stream_kernel(F32Args a, int max_q_len, int64_t n_cands) {
       if (!bad_q) {
         const float* stage = ring + (consumed % kRing) * (kVecBlock * kStageStride);
         const int nv = min(kVecBlock, m_p - blk * kVecBlock);
-        float acc_a[kVecBlock], acc_b[kVecBlock];
-#pragma unroll
-        for (int v = 0; v < kVecBlock; ++v) { acc_a[v] = 0.f; acc_b[v] = 0.f; }
-#pragma unroll
-        for (int k4 = 0; k4 < kDim / 8; ++k4) {
-#pragma unroll
-          for (int v = 0; v < kVecBlock; ++v) {
-            const float4 p = *reinterpret_cast<const float4*>(stage + v * kStageStride + rd_off + 4 * k4);
-            acc_a[v] = __fmaf_rn(qr[4 * k4 + 0], p.x, acc_a[v]);
-            acc_a[v] = __fmaf_rn(qr[4 * k4 + 1], p.y, acc_a[v]);
-            acc_a[v] = __fmaf_rn(qr[4 * k4 + 2], p.z, acc_a[v]);
-            acc_a[v] = __fmaf_rn(qr[4 * k4 + 3], p.w, acc_a[v]);
-            acc_b[v] = __fmaf_rn(qr[kDim / 2 + 4 * k4 + 0], p.x, acc_b[v]);
-            acc_b[v] = __fmaf_rn(qr[kDim / 2 + 4 * k4 + 1], p.y, acc_b[v]);
-            acc_b[v] = __fmaf_rn(qr[kDim / 2 + 4 * k4 + 2], p.z, acc_b[v]);
-            acc_b[v] = __fmaf_rn(qr[kDim / 2 + 4 * k4 + 3], p.w, acc_b[v]);
-          }
-        }
-#pragma unroll
-        for (int v = 0; v < kVecBlock; ++v) {
-          // c0 + c1 in the lane holding c0 and c1 + c0 in its partner: the same sum
-          const float da = acc_a[v] + __shfl_xor_sync(0xffffffffu, acc_a[v], 1);
-          const float db = acc_b[v] + __shfl_xor_sync(0xffffffffu, acc_b[v], 1);
-          if (v < nv) {
-            best_a = fmaxf(best_a, da);
-            best_b = fmaxf(best_b, db);
-          }
-        }
+        block_terms<L2>(stage, rd_off, qr, nv, best_a, best_b);
       }
       __syncwarp();
       ++consumed;
@@ -286,8 +263,8 @@ f32_ids_stream_kernel(F32Args a, int max_q_len, int64_t n_cands) {
       score = __int_as_float(0x7fc00000);
     } else {
       const int ia = 2 * pair, ib = ia + 1;
-      if (half == 0 && ia < m_q) rowmax[ia] = best_a;
-      if (half == 1 && ib < m_q) rowmax[ib] = best_b;
+      if (half == 0 && ia < m_q) rowmax[ia] = row_term<L2>(best_a);
+      if (half == 1 && ib < m_q) rowmax[ib] = row_term<L2>(best_b);
       __syncwarp();
       float s = 0.f;
       if (lane == 0) {
@@ -312,7 +289,7 @@ f32_ids_stream_kernel(F32Args a, int max_q_len, int64_t n_cands) {
 gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* q,
                             const int64_t* q_offsets, int32_t n_queries, const int64_t* cand_offsets,
                             const int64_t* cand_ids, int64_t n_cands, float* scores, cudaStream_t st,
-                            const int32_t* qcodes) {
+                            const int32_t* qcodes, bool stored_codes) {
   F32Args a;
   a.q = q;
   a.q_off = q_offsets;
@@ -327,33 +304,36 @@ gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* 
   a.codes = s->d_codes;
   a.centroids = s->d_codebook;
   a.qcodes = qcodes;
+  a.stored_codes = stored_codes && !qcodes && cand_ids;
   const int mq = ws->max_q_len;
+  // Sim = -(L2 distance) on the exact rows only (the codes forms are inner products)
+  const bool l2 = ws->sim == GEM_SIM_L2 && !qcodes && !a.stored_codes;
   int per_sm = 0;
   if (cand_ids == nullptr) {
     const size_t smem = sizeof(float) * ((size_t)mq * kQStride + kF32Warps * kVecBlock * kStageStride + (size_t)kF32Warps * mq);
-    GEM_CUDA_TRY(cudaFuncSetAttribute(f32_all_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32_all_kernel, kF32Threads, smem));
+    auto kern = l2 ? f32_all_kernel<true> : f32_all_kernel<false>;
+    GEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kF32Threads, smem));
     if (per_sm < 1) return fail(GEM_ERR_UNSUPPORTED, "f32 scoring kernel does not fit on an SM");
     const int64_t units = ((s->n_sets + kSegDocs - 1) / kSegDocs) * n_queries;
     const int grid = (int)std::min<int64_t>(units, (int64_t)s->n_sm * per_sm);
-    f32_all_kernel<<<grid, kF32Threads, smem, st>>>(a, mq);
+    kern<<<grid, kF32Threads, smem, st>>>(a, mq);
   } else {
-    if (!qcodes && mq <= 32) {
+    if (!qcodes && !a.stored_codes && mq <= 32) {
       const size_t smem = sizeof(float) * (kF32Warps * kRing * kVecBlock * kStageStride + (size_t)kF32Warps * 32);
-      GEM_CUDA_TRY(cudaFuncSetAttribute(f32_ids_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
-      GEM_CUDA_TRY(
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32_ids_stream_kernel, kF32Threads, smem));
+      auto kern = l2 ? f32_ids_stream_kernel<true> : f32_ids_stream_kernel<false>;
+      GEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kF32Threads, smem));
       if (per_sm < 1) return fail(GEM_ERR_UNSUPPORTED, "f32 scoring kernel does not fit on an SM");
       const int64_t max_grid = (n_cands + kF32Warps - 1) / kF32Warps;
       const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(max_grid, (int64_t)s->n_sm * per_sm));
-      f32_ids_stream_kernel<<<grid, kF32Threads, smem, st>>>(a, mq, n_cands);
+      kern<<<grid, kF32Threads, smem, st>>>(a, mq, n_cands);
       GEM_CUDA_TRY(cudaGetLastError());
       note_launches(1);
       return GEM_OK;
     }
     const size_t smem = sizeof(float) * (kF32Warps * kVecBlock * kStageStride + (size_t)kF32Warps * mq);
-    auto kern = qcodes ? f32_ids_kernel<true> : f32_ids_kernel<false>;
+    auto kern = qcodes ? f32_ids_kernel<true, false> : l2 ? f32_ids_kernel<false, true> : f32_ids_kernel<false, false>;
     GEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kF32Threads, smem));
     if (per_sm < 1) return fail(GEM_ERR_UNSUPPORTED, "f32 scoring kernel does not fit on an SM");

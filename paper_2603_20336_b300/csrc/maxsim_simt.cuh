@@ -6,6 +6,10 @@
 //                   over k = 0 .. 63 and k = 64 .. 127 (each in ascending k)
 //   m_i = max_j dot(q_i, p_j)
 //   CH  = Kahan (compensated) sum of m_i over i = 0 .. m_q - 1 in ascending order
+// With Sim = -(L2 distance) (the L2 form of Definition 1) the chains sum
+// (q_ik - p_jk)^2 instead (the difference rounded, then one fused multiply-add),
+// m_i = -sqrt(min_j d2(q_i, p_j)) with the correctly rounded square root, and the
+// same Kahan sum follows.
 //
 // Mapping: lane l holds query rows 2(l/2) and 2(l/2)+1 of the current 32-row
 // group, components k in [64 (l%2), 64 (l%2) + 64), in registers; the set's
@@ -25,6 +29,53 @@ constexpr int kVecBlock = 8;         // set vectors staged per step
 constexpr int kQStride = kDim + 4;   // padded query row stride in shared memory (floats)
 constexpr int kStageStride = kDim + 4;  // staged set vector: [k 0..63][4 pad][k 64..127]
 
+// One block of up to kVecBlock staged set vectors against this lane's two query
+// rows: best_a / best_b take the max of the block's dot products (L2: of the
+// negated squared distances).
+template <bool L2>
+__device__ __forceinline__ void block_terms(const float* __restrict__ stage, int rd_off, const float (&qr)[kDim],
+                                            int nv, float& best_a, float& best_b) {
+  float acc_a[kVecBlock], acc_b[kVecBlock];
+#pragma unroll
+  for (int v = 0; v < kVecBlock; ++v) { acc_a[v] = 0.f; acc_b[v] = 0.f; }
+#pragma unroll
+  for (int k4 = 0; k4 < kDim / 8; ++k4) {
+#pragma unroll
+    for (int v = 0; v < kVecBlock; ++v) {
+      const float4 p = *reinterpret_cast<const float4*>(stage + v * kStageStride + rd_off + 4 * k4);
+      const float pv[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if constexpr (L2) {
+          const float ta = __fsub_rn(qr[4 * k4 + e], pv[e]);
+          const float tb = __fsub_rn(qr[kDim / 2 + 4 * k4 + e], pv[e]);
+          acc_a[v] = __fmaf_rn(ta, ta, acc_a[v]);
+          acc_b[v] = __fmaf_rn(tb, tb, acc_b[v]);
+        } else {
+          acc_a[v] = __fmaf_rn(qr[4 * k4 + e], pv[e], acc_a[v]);
+          acc_b[v] = __fmaf_rn(qr[kDim / 2 + 4 * k4 + e], pv[e], acc_b[v]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < kVecBlock; ++v) {
+    // c0 + c1 in the lane holding c0 and c1 + c0 in its partner: the same sum
+    const float da = acc_a[v] + __shfl_xor_sync(0xffffffffu, acc_a[v], 1);
+    const float db = acc_b[v] + __shfl_xor_sync(0xffffffffu, acc_b[v], 1);
+    if (v < nv) {
+      best_a = fmaxf(best_a, L2 ? -da : da);
+      best_b = fmaxf(best_b, L2 ? -db : db);
+    }
+  }
+}
+
+// The per-query-vector term m_i from the block maxima.
+template <bool L2>
+__device__ __forceinline__ float row_term(float best) {
+  return L2 ? -__fsqrt_rn(-best) : best;
+}
+
 // One row of the set (or its centroid in the codes form) as this lane's float4.
 __device__ __forceinline__ float4 set_row4(const float* __restrict__ P, const int32_t* __restrict__ row_code,
                                            const float* __restrict__ centroids, int j, int lane) {
@@ -38,7 +89,7 @@ __device__ __forceinline__ float4 set_row4(const float* __restrict__ P, const in
 // otherwise rows are centroids[row_code[j] * 128].  The next 8 set vectors are
 // loaded into registers while the current 8 are multiplied, so the loads of a
 // set overlap its arithmetic; the arithmetic order is unchanged.
-template <bool CodedQ>
+template <bool CodedQ, bool L2>
 __device__ __forceinline__ float warp_chamfer_impl(const float* __restrict__ qs, int q_stride,
                                                    const int32_t* __restrict__ q_code, int m_q,
                                                    const float* __restrict__ P, const int32_t* __restrict__ row_code,
@@ -88,37 +139,10 @@ __device__ __forceinline__ float warp_chamfer_impl(const float* __restrict__ qs,
 #pragma unroll
       for (int v = 0; v < kVecBlock; ++v)
         if (v < nv1) pf[v] = set_row4(P, row_code, centroids, j1 + v, lane);
-      float acc_a[kVecBlock], acc_b[kVecBlock];
-#pragma unroll
-      for (int v = 0; v < kVecBlock; ++v) { acc_a[v] = 0.f; acc_b[v] = 0.f; }
-#pragma unroll
-      for (int k4 = 0; k4 < kDim / 8; ++k4) {
-#pragma unroll
-        for (int v = 0; v < kVecBlock; ++v) {
-          const float4 p = *reinterpret_cast<const float4*>(stage + v * kStageStride + rd_off + 4 * k4);
-          acc_a[v] = __fmaf_rn(qr[4 * k4 + 0], p.x, acc_a[v]);
-          acc_a[v] = __fmaf_rn(qr[4 * k4 + 1], p.y, acc_a[v]);
-          acc_a[v] = __fmaf_rn(qr[4 * k4 + 2], p.z, acc_a[v]);
-          acc_a[v] = __fmaf_rn(qr[4 * k4 + 3], p.w, acc_a[v]);
-          acc_b[v] = __fmaf_rn(qr[kDim / 2 + 4 * k4 + 0], p.x, acc_b[v]);
-          acc_b[v] = __fmaf_rn(qr[kDim / 2 + 4 * k4 + 1], p.y, acc_b[v]);
-          acc_b[v] = __fmaf_rn(qr[kDim / 2 + 4 * k4 + 2], p.z, acc_b[v]);
-          acc_b[v] = __fmaf_rn(qr[kDim / 2 + 4 * k4 + 3], p.w, acc_b[v]);
-        }
-      }
-#pragma unroll
-      for (int v = 0; v < kVecBlock; ++v) {
-        // c0 + c1 in the lane holding c0 and c1 + c0 in its partner: the same sum
-        const float da = acc_a[v] + __shfl_xor_sync(0xffffffffu, acc_a[v], 1);
-        const float db = acc_b[v] + __shfl_xor_sync(0xffffffffu, acc_b[v], 1);
-        if (v < nv) {
-          best_a = fmaxf(best_a, da);
-          best_b = fmaxf(best_b, db);
-        }
-      }
+      block_terms<L2>(stage, rd_off, qr, nv, best_a, best_b);
     }
-    if (half == 0 && ia < m_q) rowmax[ia] = best_a;
-    if (half == 1 && ib < m_q) rowmax[ib] = best_b;
+    if (half == 0 && ia < m_q) rowmax[ia] = row_term<L2>(best_a);
+    if (half == 1 && ib < m_q) rowmax[ib] = row_term<L2>(best_b);
   }
   __syncwarp();
   float s = 0.f;
@@ -134,13 +158,14 @@ __device__ __forceinline__ float warp_chamfer_impl(const float* __restrict__ qs,
   return __shfl_sync(0xffffffffu, s, 0);
 }
 
+template <bool L2 = false>
 __device__ __forceinline__ float warp_chamfer(const float* __restrict__ qs, int q_stride, int m_q,
                                               const float* __restrict__ P, const int32_t* __restrict__ row_code,
                                               const float* __restrict__ centroids, int m_p,
                                               float* __restrict__ stage, float* __restrict__ rowmax,
                                               float (&qr)[kDim], int& loaded_rg) {
-  return warp_chamfer_impl<false>(qs, q_stride, nullptr, m_q, P, row_code, centroids, m_p, stage, rowmax, qr,
-                                  loaded_rg);
+  return warp_chamfer_impl<false, L2>(qs, q_stride, nullptr, m_q, P, row_code, centroids, m_p, stage, rowmax, qr,
+                                      loaded_rg);
 }
 
 // Codes form with the query rows given as centroid indices (row i is
@@ -150,8 +175,8 @@ __device__ __forceinline__ float warp_chamfer_coded_q(const float* __restrict__ 
                                                       const float* __restrict__ P, const int32_t* __restrict__ row_code,
                                                       int m_p, float* __restrict__ stage, float* __restrict__ rowmax,
                                                       float (&qr)[kDim], int& loaded_rg) {
-  return warp_chamfer_impl<true>(nullptr, 0, q_code, m_q, P, row_code, centroids, m_p, stage, rowmax, qr,
-                                 loaded_rg);
+  return warp_chamfer_impl<true, false>(nullptr, 0, q_code, m_q, P, row_code, centroids, m_p, stage, rowmax, qr,
+                                        loaded_rg);
 }
 
 }  // namespace gem

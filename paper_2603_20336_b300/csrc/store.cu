@@ -63,6 +63,22 @@ __global__ void quantize_fp8_kernel(const float* __restrict__ src, const int64_t
   }
 }
 
+// lazy deletion (Sec. 4.6): count ids outside [0, n_sets) into bad[0]
+__global__ void check_ids_kernel(const int64_t* __restrict__ ids, int64_t n, int64_t n_sets, int* bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (ids[i] < 0 || ids[i] >= n_sets) atomicAdd(bad, 1);
+}
+
+// set (deleted) or clear the bit of every id; ids are in range
+__global__ void mark_deleted_kernel(const int64_t* __restrict__ ids, int64_t n, bool deleted, uint32_t* dead) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t id = ids[i];
+    const uint32_t bit = 1u << (id & 31);
+    if (deleted) atomicOr(dead + (id >> 5), bit);
+    else atomicAnd(dead + (id >> 5), ~bit);
+  }
+}
+
 __global__ void iota_offsets_kernel(int64_t* off, int n, int64_t step) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x)
     off[i] = (int64_t)i * step;
@@ -134,6 +150,30 @@ void launch_quantize_fp8(const float* src, const int64_t* off, const int64_t* pa
 void launch_iota_offsets(int64_t* off, int32_t n, int64_t step, cudaStream_t st) {
   iota_offsets_kernel<<<(n + 256) / 256, 256, 0, st>>>(off, n, step);
   note_launches(1);
+}
+
+gem_status launch_mark_deleted(gem_store* s, const int64_t* ids, int64_t n, bool deleted, cudaStream_t st) {
+  const size_t words = (size_t)((s->n_sets + 31) / 32);
+  if (!s->d_dead) {
+    // one extra word counts the ids out of range
+    GEM_CUDA_TRY(cudaMalloc(&s->d_dead, sizeof(uint32_t) * (words + 1)));
+    GEM_CUDA_TRY(cudaMemsetAsync(s->d_dead, 0, sizeof(uint32_t) * (words + 1), st));
+  }
+  if (n == 0) return GEM_OK;
+  int* bad = reinterpret_cast<int*>(s->d_dead + words);
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)s->n_sm * 8);
+  GEM_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  check_ids_kernel<<<grid, 256, 0, st>>>(ids, n, s->n_sets, bad);
+  GEM_CUDA_TRY(cudaGetLastError());
+  int h_bad = 0;
+  GEM_CUDA_TRY(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GEM_CUDA_TRY(cudaStreamSynchronize(st));
+  note_launches(1);
+  if (h_bad) return GEM_ERR_INVALID;
+  mark_deleted_kernel<<<grid, 256, 0, st>>>(ids, n, deleted, s->d_dead);
+  GEM_CUDA_TRY(cudaGetLastError());
+  note_launches(1);
+  return GEM_OK;
 }
 
 gem_status store_chunk_map(const gem_store* s, int chunk_rows, const ChunkMap** out) {

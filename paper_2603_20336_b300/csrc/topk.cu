@@ -7,7 +7,8 @@
 // 8-bit digits on that key, reading the row once per digit and stopping as soon
 // as the selected bucket holds exactly the remaining count; a final pass gathers
 // the k winners into shared memory, a bitonic sort orders them and the CTA
-// writes ids and scores.  Elements with a negative id are not candidates.
+// writes ids and scores.  Elements with a negative id, or the id of a set the
+// store marks deleted (Sec. 4.6), are not candidates.
 #include "internal.h"
 #include "ptx.cuh"
 
@@ -17,7 +18,8 @@ namespace {
 constexpr int kTopkThreads = 512;
 
 __device__ __forceinline__ uint32_t score_key(float f) {
-  uint32_t u = __float_as_uint(f);
+  // -0 and +0 are equal scores: both map to the key of +0, so the id decides
+  uint32_t u = __float_as_uint(f == 0.f ? 0.f : f);
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
@@ -30,9 +32,12 @@ struct RowView {
   const float* s;
   const int64_t* ids;  // null: id = index
   int64_t n;
+  const uint32_t* dead;  // null: no set deleted
+  int64_t n_sets;
   __device__ __forceinline__ bool key(int64_t t, uint64_t& k) const {
     int64_t id = ids ? ids[t] : t;
     if (id < 0) return false;
+    if (dead && id < n_sets && ((dead[id >> 5] >> (id & 31)) & 1u)) return false;
     k = ((uint64_t)score_key(s[t]) << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)id);
     return true;
   }
@@ -41,7 +46,8 @@ struct RowView {
 __global__ void __launch_bounds__(kTopkThreads)
 topk_kernel(const float* __restrict__ scores, const int64_t* __restrict__ row_off, int rows,
             int64_t cols, const int64_t* __restrict__ ids, int k, int sort_n,
-            int64_t* __restrict__ out_ids, float* __restrict__ out_scores) {
+            int64_t* __restrict__ out_ids, float* __restrict__ out_scores,
+            const uint32_t* __restrict__ dead, int64_t n_sets) {
   extern __shared__ uint64_t sel[];  // [sort_n]
   __shared__ int hist[256];
   __shared__ int suffix[257];
@@ -54,6 +60,8 @@ topk_kernel(const float* __restrict__ scores, const int64_t* __restrict__ row_of
     v.n = row_off ? row_off[r + 1] - base : cols;
     v.s = scores + base;
     v.ids = ids ? ids + base : nullptr;
+    v.dead = dead;
+    v.n_sets = n_sets;
 
     // count valid elements
     if (threadIdx.x == 0) s_n_valid = 0;
@@ -174,7 +182,6 @@ topk_kernel(const float* __restrict__ scores, const int64_t* __restrict__ row_of
 gem_status launch_topk(gem_workspace* ws, const float* scores, const int64_t* row_offsets,
                        int32_t rows, int64_t cols, const int64_t* ids, int32_t k,
                        int64_t* out_ids, float* out_scores, cudaStream_t st) {
-  (void)ws;
   if (rows == 0) return GEM_OK;
   int sort_n = 1;
   while (sort_n < k) sort_n <<= 1;
@@ -186,7 +193,7 @@ gem_status launch_topk(gem_workspace* ws, const float* scores, const int64_t* ro
   if (per_sm < 1) per_sm = 1;
   const int grid = std::min<int>(rows, ws->store->n_sm * per_sm);
   topk_kernel<<<grid, kTopkThreads, smem, st>>>(scores, row_offsets, rows, cols, ids, k, sort_n,
-                                                out_ids, out_scores);
+                                                out_ids, out_scores, ws->store->d_dead, ws->store->n_sets);
   GEM_CUDA_TRY(cudaGetLastError());
   note_launches(1);
   return GEM_OK;

@@ -85,3 +85,65 @@ def test_beam_search_rejects_a_neighbour_out_of_range(gem, setup):
     with pytest.raises(Exception):
         gem.beam_search(d["store"], d["ws"], d["q"], d["qo"], torch.from_numpy(d["go"]).cuda(),
                         torch.from_numpy(gn).cuda(), d["mask"], d["ent"], ef=8)
+
+
+def test_beam_search_with_deleted_sets_matches_oracle(gem, setup):
+    """Lazy deletion (Sec. 4.6): deleted sets, among them every entry set of the
+    first query and the best sets R held without deletion, are traversed but never
+    enter R; the rounds and R match the oracle exactly."""
+    d = setup
+    args = (d["store"], d["ws"], d["q"], d["qo"], torch.from_numpy(d["go"]).cuda(), torch.from_numpy(d["gn"]).cuda(),
+            d["mask"], d["ent"])
+    ids0, _, _ = gem.beam_search(*args, ef=16)
+    ent = d["ent"].cpu().numpy()
+    rng = np.random.default_rng(3)
+    dead = set(ids0.cpu().numpy()[:, :4].ravel().tolist()) | {int(e) for e in ent[0] if e >= 0}
+    dead |= set(rng.choice(d["store"].n_sets, 300, replace=False).tolist())
+    dead.discard(-1)
+    gem.mark_deleted(d["store"], sorted(dead))
+    try:
+        ids, sc, rounds = gem.beam_search(*args, ef=16)
+    finally:
+        gem.mark_deleted(d["store"], sorted(dead), deleted=False)
+    assert d["ws"].status() == 0
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    want_rounds = 0
+    for b in range(d["B"]):
+        qc = d["lst"][b, :d["cnt"][b]]
+        R, r = oracle.beam_search(lambda s, b=b: float(d["allq"][b, s]), d["go"], d["gn"], d["set_clusters"], qc,
+                                  ent[b], ef=16, dead=dead)
+        want_rounds = max(want_rounds, r)
+        n = len(R)
+        assert ids[b, :n].tolist() == [i for _, i in R], b
+        np.testing.assert_array_equal(sc[b, :n], np.array([s for s, _ in R], dtype=np.float32))
+        assert np.all(ids[b, n:] == -1)
+    assert rounds == want_rounds
+    assert not set(ids.ravel().tolist()) & dead
+
+
+def test_beam_search_asymmetric_qch_matches_oracle(gem, setup):
+    """The search scored by the asymmetric estimate (exact query vectors against
+    the stored vectors' centroids): R and the rounds match the oracle run on the
+    GPU's asymmetric qsim."""
+    d = setup
+    gem.set_qch_form(d["ws"], "asymmetric")
+    try:
+        allq = gem.estimate_codes(d["store"], d["ws"], d["q"], d["qo"]).cpu().numpy()
+        ids, sc, rounds = gem.beam_search(d["store"], d["ws"], d["q"], d["qo"], torch.from_numpy(d["go"]).cuda(),
+                                          torch.from_numpy(d["gn"]).cuda(), d["mask"], d["ent"], ef=16)
+    finally:
+        gem.set_qch_form(d["ws"], "symmetric")
+    assert d["ws"].status() == 0
+    assert np.abs(allq - d["allq"]).max() > 0      # a different estimate
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    ent = d["ent"].cpu().numpy()
+    want_rounds = 0
+    for b in range(d["B"]):
+        qc = d["lst"][b, :d["cnt"][b]]
+        R, r = oracle.beam_search(lambda s, b=b: float(allq[b, s]), d["go"], d["gn"], d["set_clusters"], qc,
+                                  ent[b], ef=16)
+        want_rounds = max(want_rounds, r)
+        n = len(R)
+        assert ids[b, :n].tolist() == [i for _, i in R], b
+        np.testing.assert_array_equal(sc[b, :n], np.array([s for s, _ in R], dtype=np.float32))
+    assert rounds == want_rounds

@@ -138,3 +138,59 @@ def test_qch_matches_oracle_given_gpu_codes(gem, qlens):
     for t in range(len(ids)):
         b = int(np.searchsorted(co, t, side="right") - 1)
         assert est_ids[t] == est[b, ids[t]]
+
+
+def test_asymmetric_qch_lossless_on_the_stored_side(gem):
+    """Asymmetric form: with C_quant holding every stored vector (and none of the
+    query vectors), the estimate is exact CH; the symmetric form is not."""
+    w = synth.exact_fp32(n_sets=60, n_queries=4)
+    X, Q = w.docs.vecs.numpy(), w.queries.vecs.numpy()
+    store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("f32",))
+    gem.set_codebook(store, torch.from_numpy(X.copy()).cuda())
+    ws = gem.Workspace(store, max_queries=4, max_q_rows=128, max_q_len=32)
+    gem.set_qch_form(ws, "asymmetric")
+    q, qo = w.queries.vecs.cuda(), torch.from_numpy(w.queries.offsets).cuda()
+    est = gem.estimate_codes(store, ws, q, qo).cpu().numpy()
+    assert ws.status() == 0
+    S64, L1 = oracle.score_all(Q, w.queries.offsets, X, w.docs.offsets, with_l1=True)
+    assert np.all(np.abs(est - S64) <= 1e-5 * L1 + 1e-6)
+    gem.set_qch_form(ws, "symmetric")
+    sym = gem.estimate_codes(store, ws, q, qo).cpu().numpy()
+    assert np.abs(sym - S64).max() > 1e-3
+    ws.close()
+    store.close()
+
+
+@pytest.mark.parametrize("qlens", [[32] * 5, [1, 7, 33, 64, 100, 20]])
+def test_asymmetric_qch_matches_oracle_given_gpu_codes(gem, qlens):
+    """Tables <q_i, C_c> and lookups: the all-sets form, the id-list form (bit
+    identical to it) and score_ids in the codes form (the SIMT arithmetic) all
+    within 1e-5 * m_q of the FP64 asymmetric estimate on the GPU's stored codes."""
+    w = synth.exact_fp32(n_sets=300, n_queries=1)
+    qs = synth.vector_sets(np.array(qlens), synth.centres(64, 1235), 98)
+    store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("f32",))
+    C = gem.train_codebook(store, k1=256, iters=5, sample=0, seed=1)
+    gem.set_codebook(store, C)
+    ws = gem.Workspace(store, max_queries=8, max_q_rows=512, max_q_len=128, max_cands=1000)
+    gem.set_qch_form(ws, "asymmetric")
+    q, qo = qs.vecs.cuda(), torch.from_numpy(qs.offsets).cuda()
+    est = gem.estimate_codes(store, ws, q, qo).cpu().numpy()
+    assert ws.status() == 0
+    pcodes = store.export("codes").cpu().numpy()
+    want = oracle.qch_asym_score_all(qs.vecs.numpy(), qs.offsets, pcodes, w.docs.offsets, C.cpu().numpy())
+    tol = 1e-5 * np.array(qlens)[:, None]
+    assert np.all(np.abs(est - want) <= tol), np.abs(est - want).max()
+    rng = np.random.default_rng(4)
+    lens = rng.integers(0, 30, size=len(qlens))
+    co = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    ids = rng.integers(0, 300, size=int(co[-1])).astype(np.int64)
+    co_d, ids_d = torch.from_numpy(co).cuda(), torch.from_numpy(ids).cuda()
+    est_ids = gem.estimate_codes(store, ws, q, qo, co_d, ids_d).cpu().numpy()
+    simt = gem.score_ids(store, ws, q, qo, co_d, ids_d, "codes").cpu().numpy()
+    assert ws.status() == 0
+    for t in range(len(ids)):
+        b = int(np.searchsorted(co, t, side="right") - 1)
+        assert est_ids[t] == est[b, ids[t]]
+        assert abs(simt[t] - want[b, ids[t]]) <= 1e-5 * qlens[b]
+    ws.close()
+    store.close()

@@ -233,6 +233,15 @@ def test_topk_matches_oracle(gem, cfg1, n, k):
         assert np.all(ids[r, m:] == -1) and np.all(sc[r, m:] == -np.inf)
 
 
+def test_topk_signed_zeros_tie(gem, cfg1):
+    """-0.0 and +0.0 are equal scores, so the lower id comes first."""
+    s = np.array([[-0.0, 0.0, -0.0, 0.0, 1.0, -1.0]], np.float32)
+    ids, _ = gem.topk(cfg1["ws"], torch.from_numpy(s).cuda(), 6)
+    wi, _ = oracle.topk(s[0], 6)
+    assert wi.tolist() == [4, 0, 1, 2, 3, 5]
+    assert ids.cpu().numpy()[0].tolist() == wi.tolist()
+
+
 def test_topk_explicit_ids_ragged_and_all_equal(gem, cfg1):
     rng = np.random.default_rng(3)
     lens = np.array([0, 7, 500, 3])

@@ -1,0 +1,110 @@
+"""GPU parity of the exact FP32 scorers with Sim = -(L2 distance) (Definition 1's
+other choice of Sim) against the FP64 oracle, on vectors that are NOT unit norm
+(every row scaled by a factor in [0.5, 2], plus a common offset), so a dropped
+norm or a wrong sign shows.
+
+Tolerance: each term -sqrt(d2) carries a relative error of a few 1e-7 (128
+rounded differences squared into two FMA chains, one rounded square root), the
+Kahan sum adds ~1 ulp, so |s - s64| <= 1e-5 * sum_i min_j ||q_i - p_j||.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gem():
+    import paper_2603_20336_b300 as g
+    return g
+
+
+def _spread(x, seed):
+    rng = np.random.default_rng(seed)
+    x = x * rng.uniform(0.5, 2.0, size=(len(x), 1)) + 0.25
+    return x.astype(np.float32)
+
+
+@pytest.fixture(scope="module")
+def cfg(gem):
+    w = synth.exact_fp32(n_sets=240, n_queries=1)
+    X = _spread(w.docs.vecs.numpy(), 1)
+    qlens = np.array([32, 7, 1, 32, 20])
+    qs = synth.vector_sets(qlens, synth.centres(64, 1235), 77)
+    Q = _spread(qs.vecs.numpy(), 2)
+    own = int(np.nonzero(np.diff(w.docs.offsets) >= 32)[0][0])     # a set of at least 32 vectors
+    Q[qs.offsets[3]:qs.offsets[4]] = X[w.docs.offsets[own]:w.docs.offsets[own] + 32]   # query 3 = its head
+    store = gem.Store(torch.from_numpy(X).cuda(), w.docs.offsets, keep=("f32", "bf16"))
+    ws = gem.Workspace(store, max_queries=8, max_q_rows=256, max_q_len=32, max_cands=2000, max_k=50)
+    gem.set_similarity(ws, "l2")
+    S64, L1 = oracle.score_all_l2(Q, qs.offsets, X, w.docs.offsets, with_l1=True)
+    yield dict(own=own, X=X, off=w.docs.offsets, Q=Q, qo=qs.offsets, store=store, ws=ws, S64=S64, L1=L1,
+               q=torch.from_numpy(Q).cuda(), qo_d=torch.from_numpy(qs.offsets).cuda())
+    ws.close()
+    store.close()
+
+
+def test_score_all_l2_matches_oracle(gem, cfg):
+    s = gem.score_all(cfg["store"], cfg["ws"], cfg["q"], cfg["qo_d"], "f32").cpu().numpy()
+    assert cfg["ws"].status() == 0
+    err = np.abs(s.astype(np.float64) - cfg["S64"])
+    assert np.all(err <= 1e-5 * cfg["L1"] + 1e-6), err.max()
+    assert np.all(s <= 0)
+
+
+def test_score_ids_l2_bit_matches_all_sets_and_long_queries(gem, cfg):
+    """Id lists (the streamed kernel for queries of <= 32 vectors, the per-warp
+    kernel on a workspace allowing 64) give the all-sets scores bit for bit."""
+    allq = gem.score_all(cfg["store"], cfg["ws"], cfg["q"], cfg["qo_d"], "f32").cpu().numpy()
+    rng = np.random.default_rng(5)
+    B = len(cfg["qo"]) - 1
+    lens = rng.integers(0, 60, size=B)
+    co = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    ids = rng.integers(0, 240, size=int(co[-1])).astype(np.int64)
+    ids[3] = -1
+    co_d, ids_d = torch.from_numpy(co).cuda(), torch.from_numpy(ids).cuda()
+    got = gem.score_ids(cfg["store"], cfg["ws"], cfg["q"], cfg["qo_d"], co_d, ids_d, "f32").cpu().numpy()
+    ws64 = gem.Workspace(cfg["store"], max_queries=8, max_q_rows=256, max_q_len=64, max_cands=2000)
+    gem.set_similarity(ws64, "l2")
+    got64 = gem.score_ids(cfg["store"], ws64, cfg["q"], cfg["qo_d"], co_d, ids_d, "f32").cpu().numpy()
+    assert cfg["ws"].status() == 0 and ws64.status() == 0
+    ws64.close()
+    for t in range(len(ids)):
+        b = int(np.searchsorted(co, t, side="right") - 1)
+        want = -np.inf if ids[t] < 0 else allq[b, ids[t]]
+        assert got[t] == want and got64[t] == want, t
+
+
+def test_l2_self_distance_is_exactly_zero(gem, cfg):
+    """Query 3 is the first 32 vectors of one stored set: every term is -sqrt(0)."""
+    s = gem.score_all(cfg["store"], cfg["ws"], cfg["q"], cfg["qo_d"], "f32").cpu().numpy()
+    assert s[3, cfg["own"]] == 0.0
+    assert np.argmax(s[3]) == cfg["own"]
+
+
+def test_search_l2_returns_exact_top_k(gem, cfg):
+    ids, sc = gem.search(cfg["store"], cfg["ws"], cfg["q"], cfg["qo_d"], "f32", rerank_depth=40, k=10)
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    S64 = cfg["S64"]
+    for b in range(S64.shape[0]):
+        wi, ws_ = oracle.topk(S64[b], 10)
+        for x in set(wi.tolist()) ^ set(ids[b].tolist()):
+            assert abs(S64[b, x] - ws_[-1]) <= 1e-6 * max(1.0, abs(ws_[-1])), (b, x)
+        err = np.abs(sc[b].astype(np.float64) - S64[b, ids[b]])
+        assert np.all(err <= 1e-5 * cfg["L1"][b, ids[b]] + 1e-6)
+
+
+def test_l2_rejects_the_inner_product_only_paths_and_switches_back(gem, cfg):
+    with pytest.raises(Exception):
+        gem.score_all(cfg["store"], cfg["ws"], cfg["q"], cfg["qo_d"], "bf16")
+    gem.set_similarity(cfg["ws"], "ip")
+    try:
+        s = gem.score_all(cfg["store"], cfg["ws"], cfg["q"], cfg["qo_d"], "f32").cpu().numpy()
+    finally:
+        gem.set_similarity(cfg["ws"], "l2")
+    S64 = oracle.score_all(cfg["Q"], cfg["qo"], cfg["X"], cfg["off"])
+    assert np.abs(s - S64).max() <= 1e-4 * np.abs(S64).max()
