@@ -31,11 +31,14 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
-# tc_score_all_kernel<2,bf16,plain> on the text-500k workload: mean of three
-# launches in one ncu capture (9.417/9.414/9.419 GB read, 2.00 GB written).
-# Set to None when that kernel changes, until it is captured again.
-TC_TRAFFIC_BYTES_TEXT500K = 11.41e9
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# BF16 tensor-core kernel on the text-500k workload, per schedule (m_tiles,
+# variant, chunk_rows): the mean of three launches of one ncu capture.  An
+# entry is removed when the kernel changes, until it is captured again; a
+# schedule without an entry reports null.
+TC_TRAFFIC_BYTES_TEXT500K = {
+    (2, "plain", 65536): 11.41e9,    # 9.417 / 9.414 / 9.419 GB read, 2.00 GB written
+}
 
 # the headline metric: (query set, stored set) pairs scored per second by the
 # exhaustive search step (both arms report it under this name)
@@ -178,7 +181,8 @@ def _time(fn, reps=3, st=None):
     return e0.elapsed_time(e1) / reps
 
 
-def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, only=None, qch_k1=""):
+def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, only=None, qch_k1="",
+                 schedule=None):
     """Every hot-path row measured on its own (after the headline timing)."""
     B = qo.numel() - 1
     rows = q.shape[0]
@@ -420,6 +424,59 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, on
         sp.close()
         return res
 
+    def fp32_l2():
+        # Sim = -(L2 distance) against the inner product on the FP32 scorer, first
+        # 100 queries against every set
+        nq = min(B, 100)
+        o = torch.empty((nq, store.n_sets), dtype=torch.float32, device=dev)
+        qs, qos = q[: 32 * nq], qo[: nq + 1]
+        ms_ip = _time(lambda: gem.score_all(store, ws, qs, qos, "f32", out=o), reps=1)
+        gem.set_similarity(ws, "l2")
+        try:
+            ms_l2 = _time(lambda: gem.score_all(store, ws, qs, qos, "f32", out=o), reps=1)
+        finally:
+            gem.set_similarity(ws, "ip")
+        assert ws.status() == 0
+        return {"queries": nq, "ip_ms": ms_ip, "l2_ms": ms_l2, "l2_pairs_per_s": nq * store.n_sets / (ms_l2 * 1e-3)}
+
+    def nm_scaling():
+        # Sec. 5.4 (effect of N and m): the corpus sampled to 1/8, 1/4 and 1/2 of its
+        # sets (the sets are i.i.d., so a prefix is a random sample), or every set cut
+        # to the same fraction of its vectors (i.i.d. within a set: a prefix again),
+        # one factor at a time; the headline search step (BF16 scoring of every set,
+        # top-R, FP32 rerank, top-K) on each, same queries and schedule
+        off = w.docs.offsets
+        lens = np.diff(off)
+        runs = []
+        for kind in ("N", "m"):
+            for f in (8, 4, 2):
+                if kind == "N":
+                    sub_off = off[: len(lens) // f + 1].copy()
+                    sub = w.docs.vecs[: int(sub_off[-1])]
+                else:
+                    nl = np.maximum(1, -(-lens // f))
+                    sub_off = np.concatenate([[0], np.cumsum(nl)]).astype(np.int64)
+                    idx = np.repeat(off[:-1], nl) + (np.arange(int(sub_off[-1])) - np.repeat(sub_off[:-1], nl))
+                    sub = w.docs.vecs[torch.from_numpy(idx).to(dev)]
+                sp = gem.Store(sub, sub_off, keep=("f32", "bf16"))
+                del sub
+                wsp = gem.Workspace(sp, max_queries=B, max_q_rows=rows, max_q_len=32, max_cands=B * R, max_k=R)
+                if schedule:
+                    gem.set_schedule(wsp, schedule["m_tiles"], schedule["chunk_rows"], variant=schedule["variant"])
+                ms = _time(lambda: gem.search(sp, wsp, q, qo, "bf16", rerank_depth=R, k=K), reps=2)
+                assert wsp.status() == 0
+                runs.append({"vary": kind, "fraction": 1.0 / f, "n_sets": sp.n_sets, "n_vecs": sp.n_vecs,
+                             "mean_m": sp.n_vecs / sp.n_sets, "search_ms": ms,
+                             "doc_sets_per_s": B * sp.n_sets / (ms * 1e-3),
+                             "vectors_per_s": B * sp.n_vecs / (ms * 1e-3)})
+                wsp.close()
+                sp.close()
+        runs.append({"vary": "none", "fraction": 1.0, "n_sets": store.n_sets, "n_vecs": store.n_vecs,
+                     "mean_m": store.n_vecs / store.n_sets, "search_ms": step_ms,
+                     "doc_sets_per_s": B * store.n_sets / (step_ms * 1e-3),
+                     "vectors_per_s": B * store.n_vecs / (step_ms * 1e-3)})
+        return {"queries": B, "runs": runs}
+
     guard("fp8_exhaustive", fp8)
     guard("fp32_exhaustive", fp32)
     guard("pages_50k", pages)
@@ -428,6 +485,8 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, on
     guard("graph_search", graph_search)
     guard("beam_batch", beam)
     guard("backward", backward)
+    guard("nm_scaling", nm_scaling)
+    guard("fp32_l2", fp32_l2)
 
 
 def run_reference(args, dist, rank, world):
@@ -561,9 +620,10 @@ def run_gem(args, dist, rank, world, local):
                    "topk_rerank_topk_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in evs)},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "traffic": (TC_TRAFFIC_BYTES_TEXT500K
-                                 if args.workload == "text" and schedule["m_tiles"] == 2
-                                 and schedule["variant"] == "plain" else None),
+                     "traffic": (TC_TRAFFIC_BYTES_TEXT500K.get(
+                                     (schedule["m_tiles"], schedule["variant"], schedule["chunk_rows"]))
+                                 if args.workload == "text" else None),
+                     "frac_of_sustained_peak": achieved / peaks["bf16_tflops_sustained"],
                      "algorithmic_bytes": store.n_pad_vecs * 256 + n_pairs * 4,
                      "kernel": "tc_score_all_kernel<%d,bf16,%s> (+ query packing)" % (schedule["m_tiles"], schedule["variant"]),
                      "peak_kind": f"{peak_kind} bf16 burst"},
@@ -585,7 +645,8 @@ def run_gem(args, dist, rank, world, local):
     if rank == 0 and not args.no_extras:
         stages = line["stages"]
         extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, ms,
-                     only=set(args.stages.split(",")) if args.stages else None, qch_k1=args.qch_k1)
+                     only=set(args.stages.split(",")) if args.stages else None, qch_k1=args.qch_k1,
+                     schedule=schedule)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

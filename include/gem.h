@@ -213,7 +213,9 @@ gem_status gem_cluster_filter(const float* q, const int64_t* q_offsets, int32_t 
  * set stays in the store and in any graph over it: gem_beam_search still
  * traverses it, and every scoring call still scores it, but gem_topk,
  * gem_search and the R of gem_beam_search never return it.  Repeated ids are
- * fine.  Blocks until the ids are checked.
+ * fine.  Blocks until the ids are checked.  The bitmap is updated on `stream`:
+ * calls on other streams that read this store see the change only once they
+ * are ordered after it (the same rule as any other device write).
  * Errors: GEM_ERR_INVALID (NULL with n > 0, n < 0, an id outside [0, n_sets):
  * then no bit changes), GEM_ERR_OOM (the first call allocates ceil(n_sets / 32)
  * + 1 words).
