@@ -19,6 +19,7 @@ Contents and the passage each follows:
   beam_search                     Algorithm 5 / Sec. 4.5.3: cluster-guided multi-path beam search, in rounds
   qch_distance, qch_similarity    Sec. 4.5.3, Eq. 16, with d_X = 1 - <.,.> (Sec. 4.2.1)
   qch_asym_*                      Eq. 16 with only the stored side quantized (a variant)
+  emd_cost, emd, qemd             Sec. 4.2.1-4.2.2 (Eq. 11-14): EMD with uniform marginals, exact LP (HiGHS)
   k1_for                          Sec. 5.1 parameter settings: |C_quant| = 2^floor(log2(16 sqrt(#vectors)))
   bf16_round, fp8_e4m3_quantize   storage formats of the low-precision path (not in the paper)
   maxsim_grad, contrastive_*      gradient of Eq. 1 (not in the paper)
@@ -33,6 +34,7 @@ from .maxsim import (  # noqa: F401
     chamfer, score_all, score_ids, chamfer_l2, score_all_l2, topk, rerank, recall_at_k,
     assign_codes, cluster_filter, cluster_members, entry_points, entry_hash, splitmix64_next, beam_search,
     qch_distance, qch_similarity, qch_score_all, qch_score_ids, qch_asym_similarity, qch_asym_score_all, k1_for,
+    emd_cost, emd, qemd,
     bf16_round, fp8_e4m3_round, fp8_e4m3_quantize,
     maxsim_grad, contrastive_loss, contrastive_dscores, kmeans_update,
 )

@@ -426,6 +426,43 @@ def qch_asym_score_all(q, q_offsets, p_codes, offsets, C) -> np.ndarray:
     return out
 
 
+def emd_cost(D, a=None, b=None) -> float:
+    """Earth mover's distance for the cost matrix D [m1, m2] (Sec. 4.2.1, Eq. 11-12):
+    min over plans T >= 0 with row sums a and column sums b of sum_ij T_ij D_ij.
+    a, b default to the uniform marginals 1/m1 and 1/m2 of the paper.  The
+    linear program is solved exactly by scipy's HiGHS solver (a library step)."""
+    from scipy.optimize import linprog
+
+    D = _f64(D)
+    m1, m2 = D.shape
+    a = np.full(m1, 1.0 / m1) if a is None else _f64(a)
+    b = np.full(m2, 1.0 / m2) if b is None else _f64(b)
+    # T flattened row-major: T_ij at i * m2 + j
+    rows = np.zeros((m1, m1 * m2))
+    cols = np.zeros((m2, m1 * m2))
+    for i in range(m1):
+        rows[i, i * m2:(i + 1) * m2] = 1.0
+    for j in range(m2):
+        cols[j, j::m2] = 1.0
+    res = linprog(D.reshape(-1), A_eq=np.vstack([rows, cols]), b_eq=np.concatenate([a, b]),
+                  bounds=(0, None), method="highs")
+    if res.status != 0:
+        raise RuntimeError(res.message)
+    return float(res.fun)
+
+
+def emd(P1, P2) -> float:
+    """EMD(P1, P2) with d_X(p, p') = 1 - <p, p'> (the cosine form, Sec. 4.2.1)."""
+    return emd_cost(1.0 - _f64(P1) @ _f64(P2).T)
+
+
+def qemd(codes1, codes2, C) -> float:
+    """qEMD(P1, P2) (Sec. 4.2.2, Eq. 14): EMD with every vector replaced by its
+    nearest centroid of C_quant (Eq. 13), d_X(NN(p_i), NN(p'_j)) = 1 - <C_a_i, C_b_j>."""
+    C = _f64(C)
+    return emd_cost(1.0 - C[_i64(codes1)] @ C[_i64(codes2)].T)
+
+
 def k1_for(n_vectors: int) -> int:
     """|C_quant| = 2^floor(log2(16 * sqrt(#vectors))) (Sec. 5.1, parameter settings)."""
     return 1 << int(math.floor(math.log2(16.0 * math.sqrt(n_vectors))))

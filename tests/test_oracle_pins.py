@@ -271,6 +271,57 @@ def test_l2_chamfer_pins():
     np.testing.assert_array_equal(L1, -S)
 
 
+def _w1_1d(x, y):
+    """Closed form of the 1-D Wasserstein-1 distance between uniform point masses:
+    the integral over u in (0, 1) of |F^-1(u) - G^-1(u)|, by merging the quantile
+    breakpoints of the two sorted samples."""
+    x, y = np.sort(x), np.sort(y)
+    cuts = np.union1d(np.arange(len(x) + 1) / len(x), np.arange(len(y) + 1) / len(y))
+    total = 0.0
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        mid = 0.5 * (lo + hi)
+        total += (hi - lo) * abs(x[int(mid * len(x))] - y[int(mid * len(y))])
+    return total
+
+
+def test_emd_solver_pins():
+    """The LP of Eq. 11-12 against: the 1-D closed form (unequal sizes); the
+    assignment problem for equal sizes (Birkhoff: an optimal plan is a
+    permutation / m, solved by scipy's linear_sum_assignment, another routine);
+    a single source (the only feasible plan); symmetry; zero on a set with itself."""
+    rng = np.random.default_rng(41)
+    for m1, m2 in ((3, 5), (7, 4), (6, 6), (1, 9)):
+        x, y = rng.standard_normal(m1), rng.standard_normal(m2)
+        D = np.abs(x[:, None] - y[None, :])
+        assert oracle.emd_cost(D) == pytest.approx(_w1_1d(x, y), abs=1e-9)
+    from scipy.optimize import linear_sum_assignment
+    D = rng.uniform(0, 2, size=(8, 8))
+    r, c = linear_sum_assignment(D)
+    assert oracle.emd_cost(D) == pytest.approx(D[r, c].sum() / 8, abs=1e-9)
+    D1 = rng.uniform(0, 2, size=(1, 6))
+    assert oracle.emd_cost(D1) == pytest.approx(D1.mean(), abs=1e-12)
+    P, Q = _unit(rng, 5, 16), _unit(rng, 9, 16)
+    assert oracle.emd(P, Q) == pytest.approx(oracle.emd(Q, P), abs=1e-9)
+    assert oracle.emd(P, P) == pytest.approx(0.0, abs=1e-9)
+
+
+def test_chamfer_lower_bounds_emd_and_qemd_reductions():
+    """Eq. 10: the averaged Chamfer distance (1/m_q) sum_i min_j d_X(q_i, p_j)
+    never exceeds EMD(Q, P); with a codebook holding every vector, qEMD is EMD;
+    with both sets coded to the same centroids qEMD is 0 up to rounding."""
+    rng = np.random.default_rng(42)
+    for _ in range(5):
+        Q, P = _unit(rng, int(rng.integers(1, 9)), 16), _unit(rng, int(rng.integers(1, 9)), 16)
+        avg_ch = (len(Q) - oracle.chamfer(Q, P)) / len(Q)
+        assert avg_ch <= oracle.emd(Q, P) + 1e-9
+    Q, P = _unit(rng, 4, 16), _unit(rng, 6, 16)
+    C = np.vstack([Q, P])
+    qc, pc = oracle.assign_codes(Q, C), oracle.assign_codes(P, C)
+    assert oracle.qemd(qc, pc, C) == pytest.approx(oracle.emd(Q, P), abs=1e-9)
+    codes = np.array([2, 5, 5, 7])
+    assert oracle.qemd(codes, codes[::-1], _unit(rng, 9, 16)) == pytest.approx(0.0, abs=1e-9)
+
+
 def test_codebook_size_formula_reproduces_paper():
     g = json.load(open(os.path.join(GOLD, "codebook_sizes.json")))
     for c in g["cases"]:
