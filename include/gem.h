@@ -208,6 +208,25 @@ gem_status gem_cluster_filter(const float* q, const int64_t* q_offsets, int32_t 
                               int32_t* out_count, void* stream);
 
 /*
+ * gem_qemd: quantized earth mover's distance between pairs of stored sets
+ * (Sec. 4.2.2, Eq. 14; EMD of Eq. 11-12 with every vector replaced by its
+ * nearest C_quant centroid, Eq. 13): the minimum over transport plans T >= 0
+ * whose rows sum to 1/m1 and columns to 1/m2 of sum_ij T_ij (1 - <C_a_i, C_b_j>).
+ * It is the edge weight the paper builds its graph with; this call computes it
+ * exactly (successive shortest paths on the transportation problem between the
+ * sets' distinct codes, integer masses) with FP32 costs (one FMA chain per
+ * centroid dot, clamped at 0) and an FP64 final sum.
+ *   set_a, set_b int64 [n_pairs]   stored set ids (device)
+ *   out float [n_pairs]            qEMD of (set_a[p], set_b[p]) (device)
+ * Sets of at most 128 vectors.  Device-side: an id outside [0, n_sets) scores
+ * NaN and records GEM_ERR_BOUNDS, a longer set scores NaN and records
+ * GEM_ERR_INVALID in the workspace's status word.  Asynchronous on `stream`.
+ * Errors: GEM_ERR_INVALID (NULL, n_pairs < 0), GEM_ERR_STATE (no codebook).
+ */
+gem_status gem_qemd(const gem_store* store, gem_workspace* ws, const int64_t* set_a, const int64_t* set_b,
+                    int64_t n_pairs, float* out, void* stream);
+
+/*
  * gem_store_mark_deleted: lazy deletion (Sec. 4.6).  deleted != 0 marks every
  * set in ids (int64 [n], device) deleted, deleted == 0 restores them.  A deleted
  * set stays in the store and in any graph over it: gem_beam_search still

@@ -234,6 +234,19 @@ def set_schedule(ws: Workspace, m_tiles: int = 2, chunk_rows: int = 1 << 16, var
     _check(lib.gem_workspace_set_schedule(ws.handle, m_tiles, TC_VARIANTS[variant], chunk_rows))
 
 
+def qemd(store: Store, ws: Workspace, set_a, set_b, out=None, stream=None):
+    """qEMD (Sec. 4.2.2, Eq. 14) of every pair (set_a[p], set_b[p]) of stored
+    sets of at most 128 vectors: float32 [n_pairs].  Needs the store's codebook."""
+    a = _dev(set_a.contiguous(), torch.int64, "set_a")
+    b = _dev(set_b.contiguous(), torch.int64, "set_b")
+    if a.numel() != b.numel():
+        raise ValueError("set_a and set_b differ in length")
+    if out is None:
+        out = torch.empty(a.numel(), dtype=torch.float32, device=a.device)
+    _check(lib.gem_qemd(store.handle, ws.handle, _ptr(a), _ptr(b), a.numel(), _ptr(out), _stream(stream)))
+    return out
+
+
 def selftest_wait_timeout(ws: Workspace, budget_cycles: int = 1 << 20, stream=None):
     """Run the bounded-wait self-test: a wait on a barrier nothing arrives on
     gives up after budget_cycles and records a timeout in ws's status word."""

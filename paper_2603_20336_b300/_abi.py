@@ -25,6 +25,7 @@ SIGNATURES = {
     "gem_workspace_set_qch_form": (C.c_int, [P, I32]),
     "gem_workspace_set_similarity": (C.c_int, [P, I32]),
     "gem_selftest_wait_timeout": (C.c_int, [P, I64, P]),
+    "gem_qemd": (C.c_int, [P, P, P, P, I64, P, P]),
     "gem_entry_points": (C.c_int, [P, P, P, I32, I32, C.c_uint64, P, P]),
     "gem_beam_search": (C.c_int, [P, P, P, P, I32, I64, P, P, I32, P, P, I32, I32, I32, P, P, P, P]),
     "gem_estimate_codes": (C.c_int, [P, P, P, P, I32, I64, P, P, I64, P, P]),

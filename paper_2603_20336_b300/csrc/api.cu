@@ -904,6 +904,18 @@ gem_status gem_score_ids_noalloc(const gem_store* s, const float* q, const int64
 
 int64_t gem_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+gem_status gem_qemd(const gem_store* s, gem_workspace* w, const int64_t* set_a, const int64_t* set_b, int64_t n_pairs,
+                    float* out, void* stream) {
+  if (!s || !w) return fail(GEM_ERR_INVALID, "NULL argument");
+  if (n_pairs < 0) return fail(GEM_ERR_INVALID, "n_pairs < 0");
+  if (n_pairs > 0 && (!set_a || !set_b || !out)) return fail(GEM_ERR_INVALID, "NULL argument");
+  if (s->k1 == 0 || !s->d_codes) return fail(GEM_ERR_STATE, "qEMD needs the store's codebook (gem_store_set_codebook)");
+  gem_status r = check_current_device(s->device);
+  if (r != GEM_OK) return r;
+  if (n_pairs == 0) return GEM_OK;
+  return launch_qemd(s, set_a, set_b, n_pairs, out, w->d_status, reinterpret_cast<cudaStream_t>(stream));
+}
+
 gem_status gem_selftest_wait_timeout(gem_workspace* w, int64_t budget_cycles, void* stream) {
   if (!w) return fail(GEM_ERR_INVALID, "workspace is NULL");
   if (budget_cycles < 1 || budget_cycles > ((int64_t)1 << 32)) return fail(GEM_ERR_INVALID, "budget out of range");

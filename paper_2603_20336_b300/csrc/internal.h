@@ -264,6 +264,8 @@ gem_status launch_qch_scan_ids(const gem_store* s, const float* T, const int64_t
                                int max_np, const int64_t* cand_offsets, const int64_t* cand_ids, float* out,
                                int* status, cudaStream_t st);
 gem_status launch_cluster_index(gem_store* s, cudaStream_t st);
+gem_status launch_qemd(const gem_store* s, const int64_t* set_a, const int64_t* set_b, int64_t n_pairs, float* out,
+                       int* status, cudaStream_t st);
 gem_status launch_wait_selftest(int* status, long long budget, cudaStream_t st);
 gem_status launch_mark_deleted(gem_store* s, const int64_t* ids, int64_t n, bool deleted, cudaStream_t st);
 gem_status beam_search(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
