@@ -621,7 +621,9 @@ def run_gem(args, dist, rank, world, local):
     peaks, peak_kind = _peaks()
     flops = 2.0 * rows * V * 128
     achieved = flops / (k1_ms * 1e-3) / 1e12
-    peak = peaks["bf16_tflops"]
+    # the kernel is timed inside a seconds-long loop of steps, at the power cap:
+    # the sustained peak is its denominator; the burst fraction is reported too
+    peak = peaks["bf16_tflops_sustained"]
     line = {
         "metric": METRIC,
         "value": world * n_pairs / (ms * 1e-3), "unit": "doc-sets/s", "n_gpus": world, "steps": args.steps,
@@ -638,10 +640,10 @@ def run_gem(args, dist, rank, world, local):
                      "traffic": (TC_TRAFFIC_BYTES_TEXT500K.get(
                                      (schedule["m_tiles"], schedule["variant"], schedule["chunk_rows"]))
                                  if args.workload == "text" else None),
-                     "frac_of_sustained_peak": achieved / peaks["bf16_tflops_sustained"],
+                     "frac_of_burst_peak": achieved / peaks["bf16_tflops"],
                      "algorithmic_bytes": store.n_pad_vecs * 256 + n_pairs * 4,
                      "kernel": "tc_score_all_kernel<%d,bf16,%s> (+ query packing)" % (schedule["m_tiles"], schedule["variant"]),
-                     "peak_kind": f"{peak_kind} bf16 burst"},
+                     "peak_kind": f"{peak_kind} bf16 sustained (the kernel runs inside the timed step loop)"},
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": {"value": world * n_pairs / (e2e_ms * 1e-3), "unit": "doc-sets/s",
