@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 2) batch_score_kernel(BatchA
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* stage = stage_all + warp * kVecBlock * kStageStride;
   float* rowmax = rowmax_all + warp * a.max_q_len;
-  float qr[kDim];
+  uint64_t qr[kQPairs];
   const int B = (int)a.hdr[0];
   const long long total = a.hdr[3];
   int loaded_b = -1;

@@ -44,7 +44,7 @@ f32_all_kernel(F32Args a, int max_q_len) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* stage = stage_all + warp * kVecBlock * kStageStride;
   float* rowmax = rowmax_all + warp * max_q_len;
-  float qr[kDim];
+  uint64_t qr[kQPairs];
   const int64_t n_seg = (a.n_sets + kSegDocs - 1) / kSegDocs;
   const int64_t n_units = n_seg * a.n_queries;
   for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
@@ -81,7 +81,7 @@ f32_ids_kernel(F32Args a, int max_q_len, int64_t n_cands) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* stage = sm + warp * kVecBlock * kStageStride;
   float* rowmax = sm + kF32Warps * kVecBlock * kStageStride + warp * max_q_len;
-  float qr[kDim];
+  uint64_t qr[kQPairs];
   const int64_t n_warps = (int64_t)gridDim.x * kF32Warps;
   const int64_t chunk = (n_cands + n_warps - 1) / n_warps;
   const int64_t t_begin = min(n_cands, ((int64_t)blockIdx.x * kF32Warps + warp) * chunk);
@@ -206,7 +206,7 @@ f32_ids_stream_kernel(F32Args a, int max_q_len, int64_t n_cands) {
   for (int i = 0; i < kRing - 1; ++i) issue();
 
   // ---- consumer
-  float qr[kDim];
+  uint64_t qr[kQPairs];
   int lo = 0, hi = a.n_queries - 1;  // query owning t_begin
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -234,10 +234,10 @@ f32_ids_stream_kernel(F32Args a, int max_q_len, int64_t n_cands) {
     if (!bad_q && m_p > 0 && b != loaded_b) {
       const int ia = 2 * pair, ib = ia + 1;
 #pragma unroll
-      for (int k = 0; k < kDim / 2; ++k) {
-        const int kk = half * (kDim / 2) + k;
-        qr[k] = (ia < m_q) ? a.q[(q0 + ia) * kDim + kk] : 0.f;
-        qr[kDim / 2 + k] = (ib < m_q) ? a.q[(q0 + ib) * kDim + kk] : 0.f;
+      for (int k2 = 0; k2 < kRowPairs; ++k2) {
+        const int kk = half * (kDim / 2) + 2 * k2;
+        qr[k2] = (ia < m_q) ? pack2(a.q[(q0 + ia) * kDim + kk], a.q[(q0 + ia) * kDim + kk + 1]) : 0ull;
+        qr[kRowPairs + k2] = (ib < m_q) ? pack2(a.q[(q0 + ib) * kDim + kk], a.q[(q0 + ib) * kDim + kk + 1]) : 0ull;
       }
       loaded_b = b;
     }

@@ -2,8 +2,10 @@
 // all of them produce bit-identical scores for the same (query, set) pair.
 //
 // Arithmetic order (fixed, independent of launch shape):
-//   dot(q_i, p_j) = c0 + c1, where c0 and c1 are FP32 fused multiply-add chains
-//                   over k = 0 .. 63 and k = 64 .. 127 (each in ascending k)
+//   dot(q_i, p_j) = c0 + c1, c_h = e_h + o_h, where e_h and o_h are FP32 fused
+//                   multiply-add chains over the even and the odd k of the half
+//                   k in [64 h, 64 h + 64), each in ascending k (the two chains of
+//                   a half advance together in packed two-lane FMAs)
 //   m_i = max_j dot(q_i, p_j)
 //   CH  = Kahan (compensated) sum of m_i over i = 0 .. m_q - 1 in ascending order
 // With Sim = -(L2 distance) (the L2 form of Definition 1) the chains sum
@@ -15,13 +17,15 @@
 // group, components k in [64 (l%2), 64 (l%2) + 64), in registers; the set's
 // vectors are staged 8 at a time in the warp's shared slice (the upper half of a
 // staged vector is shifted by 16 bytes so both half-warps' broadcast reads fall
-// in different banks), so one 16-byte shared load feeds 8 FMAs.  The two
-// half-chains of a dot meet through one xor shuffle.  In the codes form every
+// in different banks), so one 16-byte shared load feeds 4 packed FMAs (8
+// products).  The query components are kept as packed pairs (k, k + 1).  The two
+// halves of a dot meet through one xor shuffle.  In the codes form every
 // stored vector p_j is replaced by its centroid C[code_j] and the query rows by
 // the centroids of the query codes, which gives the quantized estimate in
 // similarity form.
 #pragma once
 #include "internal.h"
+#include "ptx.cuh"
 
 namespace gem {
 
@@ -29,40 +33,50 @@ constexpr int kVecBlock = 8;         // set vectors staged per step
 constexpr int kQStride = kDim + 4;   // padded query row stride in shared memory (floats)
 constexpr int kStageStride = kDim + 4;  // staged set vector: [k 0..63][4 pad][k 64..127]
 
+// Query registers of a lane: row a's 64 components as 32 packed pairs
+// (k, k + 1), then row b's.
+constexpr int kQPairs = kDim / 2;
+constexpr int kRowPairs = kDim / 4;
+
 // One block of up to kVecBlock staged set vectors against this lane's two query
 // rows: best_a / best_b take the max of the block's dot products (L2: of the
 // negated squared distances).
 template <bool L2>
-__device__ __forceinline__ void block_terms(const float* __restrict__ stage, int rd_off, const float (&qr)[kDim],
-                                            int nv, float& best_a, float& best_b) {
-  float acc_a[kVecBlock], acc_b[kVecBlock];
+__device__ __forceinline__ void block_terms(const float* __restrict__ stage, int rd_off,
+                                            const uint64_t (&qr)[kQPairs], int nv, float& best_a, float& best_b) {
+  uint64_t acc_a[kVecBlock], acc_b[kVecBlock];  // packed (even k, odd k) chains
 #pragma unroll
-  for (int v = 0; v < kVecBlock; ++v) { acc_a[v] = 0.f; acc_b[v] = 0.f; }
+  for (int v = 0; v < kVecBlock; ++v) { acc_a[v] = 0ull; acc_b[v] = 0ull; }
 #pragma unroll
   for (int k4 = 0; k4 < kDim / 8; ++k4) {
 #pragma unroll
     for (int v = 0; v < kVecBlock; ++v) {
-      const float4 p = *reinterpret_cast<const float4*>(stage + v * kStageStride + rd_off + 4 * k4);
-      const float pv[4] = {p.x, p.y, p.z, p.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        if constexpr (L2) {
-          const float ta = __fsub_rn(qr[4 * k4 + e], pv[e]);
-          const float tb = __fsub_rn(qr[kDim / 2 + 4 * k4 + e], pv[e]);
-          acc_a[v] = __fmaf_rn(ta, ta, acc_a[v]);
-          acc_b[v] = __fmaf_rn(tb, tb, acc_b[v]);
-        } else {
-          acc_a[v] = __fmaf_rn(qr[4 * k4 + e], pv[e], acc_a[v]);
-          acc_b[v] = __fmaf_rn(qr[kDim / 2 + 4 * k4 + e], pv[e], acc_b[v]);
-        }
+      // components (4 k4, 4 k4 + 1) and (4 k4 + 2, 4 k4 + 3) of this half
+      const ulonglong2 p = *reinterpret_cast<const ulonglong2*>(stage + v * kStageStride + rd_off + 4 * k4);
+      if constexpr (L2) {
+        uint64_t d = fsub2(qr[2 * k4], p.x);
+        acc_a[v] = ffma2(d, d, acc_a[v]);
+        d = fsub2(qr[2 * k4 + 1], p.y);
+        acc_a[v] = ffma2(d, d, acc_a[v]);
+        d = fsub2(qr[kRowPairs + 2 * k4], p.x);
+        acc_b[v] = ffma2(d, d, acc_b[v]);
+        d = fsub2(qr[kRowPairs + 2 * k4 + 1], p.y);
+        acc_b[v] = ffma2(d, d, acc_b[v]);
+      } else {
+        acc_a[v] = ffma2(qr[2 * k4], p.x, acc_a[v]);
+        acc_a[v] = ffma2(qr[2 * k4 + 1], p.y, acc_a[v]);
+        acc_b[v] = ffma2(qr[kRowPairs + 2 * k4], p.x, acc_b[v]);
+        acc_b[v] = ffma2(qr[kRowPairs + 2 * k4 + 1], p.y, acc_b[v]);
       }
     }
   }
 #pragma unroll
   for (int v = 0; v < kVecBlock; ++v) {
+    const float ca = __fadd_rn(lo2(acc_a[v]), hi2(acc_a[v]));  // e_h + o_h
+    const float cb = __fadd_rn(lo2(acc_b[v]), hi2(acc_b[v]));
     // c0 + c1 in the lane holding c0 and c1 + c0 in its partner: the same sum
-    const float da = acc_a[v] + __shfl_xor_sync(0xffffffffu, acc_a[v], 1);
-    const float db = acc_b[v] + __shfl_xor_sync(0xffffffffu, acc_b[v], 1);
+    const float da = ca + __shfl_xor_sync(0xffffffffu, ca, 1);
+    const float db = cb + __shfl_xor_sync(0xffffffffu, cb, 1);
     if (v < nv) {
       best_a = fmaxf(best_a, L2 ? -da : da);
       best_b = fmaxf(best_b, L2 ? -db : db);
@@ -95,7 +109,7 @@ __device__ __forceinline__ float warp_chamfer_impl(const float* __restrict__ qs,
                                                    const float* __restrict__ P, const int32_t* __restrict__ row_code,
                                                    const float* __restrict__ centroids, int m_p,
                                                    float* __restrict__ stage, float* __restrict__ rowmax,
-                                                   float (&qr)[kDim], int& loaded_rg) {
+                                                   uint64_t (&qr)[kQPairs], int& loaded_rg) {
   const int lane = threadIdx.x & 31;
   const int half = lane & 1;           // component half of this lane
   const int pair = lane >> 1;          // query rows 2 pair, 2 pair + 1
@@ -107,14 +121,17 @@ __device__ __forceinline__ float warp_chamfer_impl(const float* __restrict__ qs,
     const int ia = rg * 32 + 2 * pair, ib = ia + 1;
     if (rg != loaded_rg) {
 #pragma unroll
-      for (int k = 0; k < kDim / 2; ++k) {
-        const int kk = half * (kDim / 2) + k;
+      for (int k2 = 0; k2 < kRowPairs; ++k2) {
+        const int kk = half * (kDim / 2) + 2 * k2;
         if constexpr (CodedQ) {
-          qr[k] = (ia < m_q) ? centroids[(int64_t)q_code[ia] * kDim + kk] : 0.f;
-          qr[kDim / 2 + k] = (ib < m_q) ? centroids[(int64_t)q_code[ib] * kDim + kk] : 0.f;
+          qr[k2] = (ia < m_q) ? pack2(centroids[(int64_t)q_code[ia] * kDim + kk],
+                                      centroids[(int64_t)q_code[ia] * kDim + kk + 1]) : 0ull;
+          qr[kRowPairs + k2] = (ib < m_q) ? pack2(centroids[(int64_t)q_code[ib] * kDim + kk],
+                                                  centroids[(int64_t)q_code[ib] * kDim + kk + 1]) : 0ull;
         } else {
-          qr[k] = (ia < m_q) ? qs[(int64_t)ia * q_stride + kk] : 0.f;
-          qr[kDim / 2 + k] = (ib < m_q) ? qs[(int64_t)ib * q_stride + kk] : 0.f;
+          qr[k2] = (ia < m_q) ? pack2(qs[(int64_t)ia * q_stride + kk], qs[(int64_t)ia * q_stride + kk + 1]) : 0ull;
+          qr[kRowPairs + k2] =
+              (ib < m_q) ? pack2(qs[(int64_t)ib * q_stride + kk], qs[(int64_t)ib * q_stride + kk + 1]) : 0ull;
         }
       }
       loaded_rg = rg;
@@ -163,7 +180,7 @@ __device__ __forceinline__ float warp_chamfer(const float* __restrict__ qs, int 
                                               const float* __restrict__ P, const int32_t* __restrict__ row_code,
                                               const float* __restrict__ centroids, int m_p,
                                               float* __restrict__ stage, float* __restrict__ rowmax,
-                                              float (&qr)[kDim], int& loaded_rg) {
+                                              uint64_t (&qr)[kQPairs], int& loaded_rg) {
   return warp_chamfer_impl<false, L2>(qs, q_stride, nullptr, m_q, P, row_code, centroids, m_p, stage, rowmax, qr,
                                       loaded_rg);
 }
@@ -174,7 +191,7 @@ __device__ __forceinline__ float warp_chamfer_coded_q(const float* __restrict__ 
                                                       const int32_t* __restrict__ q_code, int m_q,
                                                       const float* __restrict__ P, const int32_t* __restrict__ row_code,
                                                       int m_p, float* __restrict__ stage, float* __restrict__ rowmax,
-                                                      float (&qr)[kDim], int& loaded_rg) {
+                                                      uint64_t (&qr)[kQPairs], int& loaded_rg) {
   return warp_chamfer_impl<true, false>(nullptr, 0, q_code, m_q, P, row_code, centroids, m_p, stage, rowmax, qr,
                                         loaded_rg);
 }

@@ -46,6 +46,27 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
   return d;
 }
 
+// Packed FP32 pairs in one 64-bit register: lo = element 0, hi = element 1.
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+  return (uint64_t)__float_as_uint(lo) | ((uint64_t)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float lo2(uint64_t x) { return __uint_as_float((uint32_t)x); }
+__device__ __forceinline__ float hi2(uint64_t x) { return __uint_as_float((uint32_t)(x >> 32)); }
+
+// Two independent round-to-nearest FMAs (a * b + c per element) in one packed
+// instruction; each element is rounded exactly as a scalar fused multiply-add.
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// Two independent round-to-nearest differences a - b.
+__device__ __forceinline__ uint64_t fsub2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // Two FP32 products in one packed instruction.
 __device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
   uint64_t d;
