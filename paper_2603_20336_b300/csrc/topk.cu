@@ -63,10 +63,11 @@ topk_kernel(const float* __restrict__ scores, const int64_t* __restrict__ row_of
     v.dead = dead;
     v.n_sets = n_sets;
 
-    // count valid elements
-    if (threadIdx.x == 0) s_n_valid = 0;
+    // count valid elements (every element is valid when there are no ids and
+    // no deleted sets: no pass over the row is needed)
+    if (threadIdx.x == 0) s_n_valid = (v.ids == nullptr && v.dead == nullptr) ? v.n : 0;
     __syncthreads();
-    {
+    if (v.ids != nullptr || v.dead != nullptr) {
       long long c = 0;
       for (int64_t t = threadIdx.x; t < v.n; t += blockDim.x) {
         uint64_t key;
