@@ -100,7 +100,10 @@ enum {
   GEM_EXPORT_PAD_OFFSETS = 4, /* int64  [n_sets + 1] offsets of the padded layout */
   GEM_EXPORT_CODES = 5,       /* int32  [n_vecs] NN code of every stored vector */
   GEM_EXPORT_CODEBOOK = 6,    /* float  [k1 * 128] centroids of C_quant */
-  GEM_EXPORT_INDEX_CODES = 7  /* int32  [n_vecs] nearest C_index centroid of every stored vector */
+  GEM_EXPORT_INDEX_CODES = 7, /* int32  [n_vecs] nearest C_index centroid of every stored vector */
+  GEM_EXPORT_F32 = 8,         /* float  [n_vecs * 128] FP32 master copy (original row order) */
+  GEM_EXPORT_INDEX_CENTROIDS = 9, /* float [k2 * 128] centroids of C_index */
+  GEM_EXPORT_DELETED = 10     /* uint32 [ceil(n_sets / 32)] deletion bitmap (all zero if none) */
 };
 
 typedef struct gem_store gem_store;
@@ -133,6 +136,29 @@ void gem_store_destroy(gem_store* store);
  * output pointer may be NULL. */
 gem_status gem_store_info(const gem_store* store, int64_t* n_sets, int64_t* n_vecs,
                           int64_t* n_pad_vecs, uint32_t* keep_mask);
+
+/* k1 = |C_quant| and k2 = |C_index| attached to the store (0 when absent). */
+gem_status gem_store_codebook_sizes(const gem_store* store, int32_t* k1, int32_t* k2);
+
+/*
+ * gem_store_save / gem_store_load: a store on disk (the paper's index is
+ * persisted between runs; it gives no format).  The file holds what cannot be
+ * re-derived: the set offsets, the FP32 vectors, C_quant, C_index and the
+ * deletion bitmap (layout in csrc/persist.cu: a 48-byte header with magic,
+ * version and sizes, the arrays in that order, an 8-byte trailer).  Loading
+ * rebuilds every other array with the same kernels as the original build (bf16
+ * and E4M3 copies, codes, index codes, cluster members), so the loaded store
+ * scores exactly as the saved one.  Host I/O; both calls block until done.
+ *   save: the store must keep GEM_KEEP_F32 (else GEM_ERR_STATE).
+ *   load: keep_mask chooses the copies of the new store (as in
+ *         gem_store_create; GEM_KEEP_F32 is required when the file holds
+ *         centroids).  The store is created on the current device.
+ * Errors: GEM_ERR_INVALID (NULL, a path that cannot be opened, a failed write,
+ * a file that is not a store, of another version, with a corrupt header or
+ * offsets, or shorter or longer than its header says), GEM_ERR_OOM.
+ */
+gem_status gem_store_save(const gem_store* store, const char* path, void* stream);
+gem_status gem_store_load(const char* path, uint32_t keep_mask, void* stream, gem_store** out);
 
 /* Copies one internal array (GEM_EXPORT_*) into the device buffer dst of
  * dst_bytes bytes (must be at least the array's size). */

@@ -84,6 +84,9 @@ class Store:
             off = offsets.contiguous()
             _check(lib.gem_store_create(_ptr(v), _ptr(off), n_sets, v.shape[1], mask, 1,
                                         _stream(stream), ctypes.byref(h)))
+        self._adopt(h, keep)
+
+    def _adopt(self, h, keep):
         self.handle = h
         n_s, n_v, n_p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(lib.gem_store_info(h, ctypes.byref(n_s), ctypes.byref(n_v), ctypes.byref(n_p), None))
@@ -91,6 +94,30 @@ class Store:
         self.n_vecs = n_v.value
         self.n_pad_vecs = n_p.value
         self.keep = tuple(keep)
+        k1, k2 = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.gem_store_codebook_sizes(h, ctypes.byref(k1), ctypes.byref(k2)))
+        if k1.value:
+            self.k1 = k1.value
+        if k2.value:
+            self.k2 = k2.value
+
+    def save(self, path, stream=None):
+        """Write the store to `path` (offsets, FP32 vectors, C_quant, C_index,
+        deletions); needs the FP32 copy."""
+        _check(lib.gem_store_save(self.handle, str(path).encode(), _stream(stream)))
+
+    @classmethod
+    def load(cls, path, keep=("f32", "bf16"), stream=None):
+        """A store read from a file written by save(); every derived array is
+        rebuilt on the current device."""
+        mask = 0
+        for k in keep:
+            mask |= KEEP[k]
+        h = ctypes.c_void_p()
+        _check(lib.gem_store_load(str(path).encode(), mask, _stream(stream), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self._adopt(h, keep)
+        return self
 
     def export(self, what: str, stream=None) -> torch.Tensor:
         """Copy of an internal array: 'bf16' (uint16 bits, padded layout), 'fp8'
@@ -102,7 +129,10 @@ class Store:
                 "pad_offsets": (4, torch.int64, (self.n_sets + 1,)),
                 "codes": (5, torch.int32, (self.n_vecs,)),
                 "codebook": (6, torch.float32, (getattr(self, "k1", 0), 128)),
-                "index_codes": (7, torch.int32, (self.n_vecs,))}
+                "index_codes": (7, torch.int32, (self.n_vecs,)),
+                "f32": (8, torch.float32, (self.n_vecs, 128)),
+                "index_centroids": (9, torch.float32, (getattr(self, "k2", 0), 128)),
+                "deleted": (10, torch.int32, ((self.n_sets + 31) // 32,))}
         code, dt, shape = spec[what]
         out = torch.empty(shape, dtype=dt, device="cuda")
         _check(lib.gem_store_export(self.handle, code, _ptr(out), out.numel() * out.element_size(),

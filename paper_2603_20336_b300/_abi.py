@@ -15,6 +15,9 @@ SIGNATURES = {
     "gem_store_destroy": (None, [P]),
     "gem_store_info": (C.c_int, [P, P, P, P, P]),
     "gem_store_export": (C.c_int, [P, I32, P, SZ, P]),
+    "gem_store_codebook_sizes": (C.c_int, [P, P, P]),
+    "gem_store_save": (C.c_int, [P, C.c_char_p, P]),
+    "gem_store_load": (C.c_int, [C.c_char_p, U32, P, C.POINTER(P)]),
     "gem_assign_codes": (C.c_int, [P, I64, P, I32, P, P, P]),
     "gem_train_codebook": (C.c_int, [P, I32, I32, I64, C.c_uint64, P, P]),
     "gem_store_set_codebook": (C.c_int, [P, P, I32, P]),

@@ -241,6 +241,16 @@ gem_status gem_store_export(const gem_store* s, int32_t what, void* dst, size_t 
     case GEM_EXPORT_CODES: src = s->d_codes; bytes = sizeof(int32_t) * s->n_vecs; break;
     case GEM_EXPORT_CODEBOOK: src = s->d_codebook; bytes = sizeof(float) * (size_t)s->k1 * kDim; break;
     case GEM_EXPORT_INDEX_CODES: src = s->d_icodes; bytes = sizeof(int32_t) * s->n_vecs; break;
+    case GEM_EXPORT_F32: src = s->d_f32; bytes = sizeof(float) * s->n_vecs * kDim; break;
+    case GEM_EXPORT_INDEX_CENTROIDS: src = s->d_cindex; bytes = sizeof(float) * (size_t)s->k2 * kDim; break;
+    case GEM_EXPORT_DELETED: {
+      bytes = sizeof(uint32_t) * (size_t)((s->n_sets + 31) / 32);
+      if (dst_bytes < bytes) return fail(GEM_ERR_INVALID, "dst too small");
+      cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+      if (s->d_dead) GEM_CUDA_TRY(cudaMemcpyAsync(dst, s->d_dead, bytes, cudaMemcpyDeviceToDevice, st));
+      else GEM_CUDA_TRY(cudaMemsetAsync(dst, 0, bytes, st));
+      return GEM_OK;
+    }
     default: return fail(GEM_ERR_INVALID, "unknown export");
   }
   if (!src) return fail(GEM_ERR_STATE, "store does not keep that array");
