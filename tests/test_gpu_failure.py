@@ -36,3 +36,22 @@ def test_a_wait_that_runs_out_reports_timeout_and_the_context_stays_usable(gem):
         gem.selftest_wait_timeout(ws, 0)
     ws.close()
     store.close()
+
+
+def test_a_failed_allocation_is_reported_and_the_context_stays_usable(gem):
+    """An allocation the device cannot satisfy (a workspace sized for 2^45
+    candidates, 256 TB of ids) fails with GEM_ERR_OOM through the ordinary
+    cudaMalloc path, frees what it had allocated, and the next calls work."""
+    w = synth.exact_fp32(n_sets=60, n_queries=1)
+    store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("f32",))
+    with pytest.raises(gem.GemError) as e:
+        gem.Workspace(store, max_queries=1, max_q_rows=32, max_q_len=32, max_cands=1 << 45)
+    assert e.value.code == 2                     # GEM_ERR_OOM
+    ws = gem.Workspace(store, max_queries=1, max_q_rows=32, max_q_len=32, max_cands=60)
+    q, qo = w.queries.vecs.cuda(), torch.from_numpy(w.queries.offsets).cuda()
+    s = gem.score_all(store, ws, q, qo, "f32").cpu().numpy()
+    assert ws.status() == 0
+    S64 = oracle.score_all(w.queries.vecs, w.queries.offsets, w.docs.vecs, w.docs.offsets)
+    assert np.abs(s - S64).max() <= 1e-4
+    ws.close()
+    store.close()
