@@ -14,9 +14,7 @@
 // one unit, so at most m1 m2 augmentations run, and every Dijkstra at most
 // n1 + n2 extractions: the kernel always finishes.  The cost matrix (FP32, one
 // FMA chain per centroid dot, clamped at 0) and the flows (16-bit: a flow never
-// exceeds 128 x 128) live in shared memory.  The CTA builds the codes and costs
-// together; the solve runs in one warp (warp-wide minima, no block barrier per
-// extraction).
+// exceeds 128 x 128) live in shared memory; one __syncthreads per extraction.
 // The result sum_ij flow_ij c_ij / (m1 m2) is summed in FP64 in a fixed order.
 #include "internal.h"
 #include "ptx.cuh"
@@ -160,107 +158,78 @@ qemd_kernel(const float* __restrict__ C, const int32_t* __restrict__ codes, cons
     if (t == 0) s.remaining = m1 * m2;
     __syncthreads();
 
-    // The solve runs in warp 0 alone (no block barrier per extraction): lane l
-    // owns sources and sinks l, l + 32, l + 64, l + 96; the other warps wait at
-    // the barrier after it.
-    if (warp == 0) {
-      bool bad = false;
-      while (s.remaining > 0 && !bad) {
-        // Dijkstra from every source with supply left
-        float ds[4], dk[4];
-        uint32_t done = 0;  // bit m: source lane + 32 m finalised; bit 4 + m: sink
+    bool failed = false;
+    while (s.remaining > 0) {
+      // Dijkstra from every source with supply left
+      float ds = (t < n1 && s.sup[t] > 0) ? 0.f : INFINITY;  // source t
+      float dk = INFINITY;                                   // sink t
+      bool fs = t >= n1, fk = t >= n2;                       // finalised (absent nodes count as done)
+      s.prev[t] = -1;
+      s.prev[kSink + t] = -1;
+      int tsel = -1;
+      float dt = 0.f;
+      __syncthreads();
+      for (int it = 0; it < n1 + n2; ++it) {
+        const uint32_t ks = fs ? 0xFFFFFFFFu : dist_key(ds);
+        const uint32_t kk = fk ? 0xFFFFFFFFu : dist_key(dk);
+        uint32_t kb = ks;
+        uint32_t ib = (uint32_t)t;
+        if (kk < ks) { kb = kk; ib = (uint32_t)(kSink + t); }
+        const uint32_t wmin = __reduce_min_sync(0xffffffffu, kb);
+        const uint32_t widx = __reduce_min_sync(0xffffffffu, kb == wmin ? ib : 0xFFFFFFFFu);
+        if (lane == 0) s.red[it & 1][warp] = ((unsigned long long)wmin << 32) | widx;
+        __syncthreads();
+        unsigned long long best = s.red[it & 1][0];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int x = lane + 32 * m;
-          ds[m] = (x < n1 && s.sup[x] > 0) ? 0.f : INFINITY;
-          dk[m] = INFINITY;
-          if (x >= n1) done |= 1u << m;        // absent nodes count as finalised
-          if (x >= n2) done |= 1u << (4 + m);
-          s.prev[x] = -1;
-          s.prev[kSink + x] = -1;
-        }
-        __syncwarp();
-        int tsel = -1;
-        float dt = 0.f;
-        for (int it = 0; it < n1 + n2; ++it) {
-          unsigned long long best = ~0ull;
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            const unsigned long long bs = ((unsigned long long)dist_key(ds[m]) << 32) | (uint32_t)(lane + 32 * m);
-            const unsigned long long bk = ((unsigned long long)dist_key(dk[m]) << 32) | (uint32_t)(kSink + lane + 32 * m);
-            if (!((done >> m) & 1u)) best = min(best, bs);
-            if (!((done >> (4 + m)) & 1u)) best = min(best, bk);
-          }
-          const uint32_t kb = (uint32_t)(best >> 32);
-          const uint32_t wmin = __reduce_min_sync(0xffffffffu, kb);
-          const uint32_t u32 = __reduce_min_sync(0xffffffffu, kb == wmin ? (uint32_t)best : 0xFFFFFFFFu);
-          const float du = key_dist(wmin);
-          if (wmin == 0xFFFFFFFFu || !isfinite(du)) {  // nothing reachable: cannot happen with supply left
-            bad = true;
-            break;
-          }
-          const int u = (int)u32;
-          const float pu = s.pot[u];
-          if (u < kSink) {
-            if ((u & 31) == lane) done |= 1u << (u >> 5);
-            // relax this lane's sinks over the forward edges u -> j
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              const int j = lane + 32 * m;
-              if (!((done >> (4 + m)) & 1u)) {
-                const float nd = du + s.cost[u * kCStride + j] + pu - s.pot[kSink + j];
-                if (nd < dk[m]) { dk[m] = nd; s.prev[kSink + j] = u; }
-              }
-            }
-          } else {
-            const int jj = u - kSink;
-            if ((jj & 31) == lane) done |= 1u << (4 + (jj >> 5));
-            if (s.dem[jj] > 0) { tsel = u; dt = du; break; }
-            // relax this lane's sources over the backward edges jj -> i
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              const int i2 = lane + 32 * m;
-              if (!((done >> m) & 1u) && s.flow[i2 * kFStride + jj] > 0) {
-                const float nd = du - s.cost[i2 * kCStride + jj] + pu - s.pot[i2];
-                if (nd < ds[m]) { ds[m] = nd; s.prev[i2] = u; }
-              }
-            }
-          }
-        }
-        if (bad || tsel < 0) {  // (every extraction finalises a node, so a demand sink is always reached)
-          bad = true;
+        for (int w = 1; w < kQemdThreads / 32; ++w) best = min(best, s.red[it & 1][w]);
+        const uint32_t bk = (uint32_t)(best >> 32);
+        const int u = (int)(best & 0xFFFFFFFFu);
+        const float du = key_dist(bk);
+        if (bk == 0xFFFFFFFFu || !isfinite(du)) {  // no node reachable: cannot happen with supply left
+          failed = true;
           break;
         }
-        // potentials: finalised nodes move by their distance, the others by dt
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int x = lane + 32 * m;
-          if (x < n1) s.pot[x] += ((done >> m) & 1u) ? fminf(ds[m], dt) : dt;
-          if (x < n2) s.pot[kSink + x] += ((done >> (4 + m)) & 1u) ? fminf(dk[m], dt) : dt;
-        }
-        __syncwarp();
-        if (lane == 0) {
-          // the path's bottleneck, then the augmentation
-          int bott = s.dem[tsel - kSink];
-          int v = tsel;
-          for (int p = s.prev[v]; p >= 0; v = p, p = s.prev[v])
-            if (v < kSink) bott = min(bott, (int)s.flow[v * kFStride + (p - kSink)]);
-          bott = min(bott, s.sup[v]);
-          v = tsel;
-          for (int p = s.prev[v]; p >= 0; v = p, p = s.prev[v]) {
-            if (v >= kSink) s.flow[p * kFStride + (v - kSink)] += (uint16_t)bott;
-            else s.flow[v * kFStride + (p - kSink)] -= (uint16_t)bott;
+        if (u < kSink) {
+          if (t == u) fs = true;
+          // relax this thread's sink over the forward edge u -> t
+          if (!fk) {
+            const float nd = du + s.cost[u * kCStride + t] + s.pot[u] - s.pot[kSink + t];
+            if (nd < dk) { dk = nd; s.prev[kSink + t] = u; }
           }
-          s.sup[v] -= bott;
-          s.dem[tsel - kSink] -= bott;
-          s.remaining -= bott;
+        } else {
+          const int j = u - kSink;
+          if (t == j) fk = true;
+          if (s.dem[j] > 0) { tsel = u; dt = du; break; }
+          // relax this thread's source over the backward edge j -> t
+          if (!fs && s.flow[t * kFStride + j] > 0) {
+            const float nd = du - s.cost[t * kCStride + j] + s.pot[u] - s.pot[t];
+            if (nd < ds) { ds = nd; s.prev[t] = u; }
+          }
         }
-        __syncwarp();
       }
-      if (lane == 0) s.srt[0] = bad ? 1 : 0;
+      if (failed) break;
+      // potentials: finalised nodes move by their distance, the others by dt
+      if (t < n1) s.pot[t] += fs ? fminf(ds, dt) : dt;
+      if (t < n2) s.pot[kSink + t] += fk ? fminf(dk, dt) : dt;
+      __syncthreads();
+      if (t == 0) {
+        // the path's bottleneck, then the augmentation
+        int bott = s.dem[tsel - kSink];
+        int v = tsel;
+        for (int p = s.prev[v]; p >= 0; v = p, p = s.prev[v])
+          if (v < kSink) bott = min(bott, (int)s.flow[v * kFStride + (p - kSink)]);
+        bott = min(bott, s.sup[v]);
+        v = tsel;
+        for (int p = s.prev[v]; p >= 0; v = p, p = s.prev[v]) {
+          if (v >= kSink) s.flow[p * kFStride + (v - kSink)] += (uint16_t)bott;
+          else s.flow[v * kFStride + (p - kSink)] -= (uint16_t)bott;
+        }
+        s.sup[v] -= bott;
+        s.dem[tsel - kSink] -= bott;
+        s.remaining -= bott;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    const bool failed = s.srt[0] != 0;
     if (failed) {
       if (t == 0) {
         set_status(status, kDevInvalid);
