@@ -232,13 +232,15 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, on
                 gem.set_qch_form(ws2, form)
                 ms = _time(lambda: gem.estimate_codes(store, ws2, q[: 32 * nq], qo[: nq + 1], out=est), reps=1)
                 pid, _ = gem.topk(ws2, est, R)
+                est_top = pid[:, :K].cpu().numpy()     # the estimate's own top-K, before the rerank
                 pool_off = torch.arange(nq + 1, dtype=torch.int64, device=dev) * R
                 rs = gem.score_ids(store, ws2, q[: 32 * nq], qo[: nq + 1], pool_off, pid.view(-1), "f32")
                 ids, _ = gem.topk(ws2, rs.view(nq, R), K, ids=pid.contiguous())
                 assert ws2.status() == 0
                 runs.append({"k1": k1, "form": form, "codebook_and_codes_s": t_build, "ms": ms,
                              "pairs_per_s": nq * store.n_sets / (ms * 1e-3),
-                             "recall_at_100_after_rerank": _recall(ids.cpu().numpy(), truth[:nq])})
+                             "recall_at_100_after_rerank": _recall(ids.cpu().numpy(), truth[:nq]),
+                             "recall_at_100_of_the_estimate": _recall(est_top, truth[:nq])})
             ws2.close()
         head = runs[0]
         return {"k1": head["k1"], "codebook_and_codes_s": head["codebook_and_codes_s"], "queries": nq,
