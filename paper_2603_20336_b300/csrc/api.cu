@@ -270,7 +270,7 @@ void gem_workspace_destroy(gem_workspace* w) {
                   w->d_part_pass, w->d_part_slot, w->d_part_row0, w->d_row_part, w->d_qpack_bf16,
                   w->d_qpack_fp8, w->d_qpack_scale, w->d_scores, w->d_pool_ids, w->d_pool_off,
                   w->d_pool_scores, w->d_q_in, w->d_qo_in, w->d_out_ids, w->d_out_scores,
-                  w->d_qcodes, w->d_tables};
+                  w->d_qcodes, w->d_assign_key, w->d_tables};
   for (void* p : ptrs) dfree(p);
   cudaSetDevice(prev);
   delete w;
@@ -340,6 +340,7 @@ gem_status gem_workspace_create(const gem_store* s, int32_t max_queries, int64_t
     const int max_np = (max_q_len + 31) / 32;
     w->table_parts = std::max(max_np, std::min(16, max_queries * max_np));
     WS_ALLOC(d_qcodes, max_q_rows);
+    WS_ALLOC(d_assign_key, max_q_rows);
     WS_ALLOC(d_tables, (size_t)w->table_parts * s->k1 * 32);
   }
 #undef WS_ALLOC
@@ -648,7 +649,7 @@ gem_status gem_score_ids(const gem_store* s, gem_workspace* w, const float* q,
     if (w->qch_form == GEM_QCH_ASYMMETRIC)
       return launch_f32_score(s, w, q, q_offsets, n_queries, cand_offsets, cand_ids, n_cands, scores, st, nullptr,
                               true);
-    r = launch_assign(q, n_q_rows, s->d_codebook, s->k1, w->d_qcodes, nullptr, st);
+    r = launch_assign_split(q, n_q_rows, s->d_codebook, s->k1, w->d_qcodes, w->d_assign_key, s->n_sm, st);
     if (r != GEM_OK) return r;
     return launch_f32_score(s, w, q, q_offsets, n_queries, cand_offsets, cand_ids, n_cands, scores, st,
                             w->d_qcodes);
@@ -677,7 +678,7 @@ gem_status gem_beam_search(const gem_store* s, gem_workspace* w, const float* q,
     return fail(GEM_ERR_INVALID, "more than 65,535 query parts of 32 rows in one search");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (w->qch_form == GEM_QCH_SYMMETRIC) {
-    r = launch_assign(q, n_q_rows, s->d_codebook, s->k1, w->d_qcodes, nullptr, st);
+    r = launch_assign_split(q, n_q_rows, s->d_codebook, s->k1, w->d_qcodes, w->d_assign_key, s->n_sm, st);
     if (r != GEM_OK) return r;
   }
   return beam_search(s, w, q, q_offsets, n_queries, graph_off, graph_nbrs, max_degree, cluster_mask, entries,

@@ -31,10 +31,25 @@ __device__ __forceinline__ bool better(float v, int i, float bv, int bi) {
 
 // 64 vectors x 64 centroids per step; thread (ty, tx) owns rows 4ty..4ty+3 and
 // centroids 4tx..4tx+3 of the step; operands are staged k-major in shared memory.
+// keys: larger key = larger value, then lower index (the order of better());
+// -0 and +0 are the same value
+__device__ __forceinline__ unsigned long long best_key(float v, int i) {
+  const uint32_t u = __float_as_uint(v == 0.f ? 0.f : v);
+  const uint32_t o = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return ((unsigned long long)o << 32) | (0xFFFFFFFFu - (uint32_t)i);
+}
+
+// split != nullptr: blockIdx.y takes the centroids [y * span, (y + 1) * span) and
+// the row's best over them is merged into split[row] by a 64-bit atomic max of
+// best_key; every dot is the same FMA chain as in the unsplit form, so the
+// merged argmax is the same.
 __global__ void __launch_bounds__(kAsgThreads)
 assign_kernel(const float* __restrict__ X, int64_t n, const int64_t* __restrict__ n_dev,
-              const float* __restrict__ C, int k1, int32_t* __restrict__ codes, float* __restrict__ best_out) {
+              const float* __restrict__ C, int k1, int32_t* __restrict__ codes, float* __restrict__ best_out,
+              unsigned long long* __restrict__ split = nullptr, int span = 0) {
   if (n_dev) n = min(n, *n_dev);
+  const int c_begin = split ? (int)blockIdx.y * span : 0;
+  const int c_end = split ? min(k1, c_begin + span) : k1;
   __shared__ __align__(16) float xs[kDim][kAsgRows];
   __shared__ __align__(16) float cs[kDim][kAsgCents];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -48,11 +63,11 @@ assign_kernel(const float* __restrict__ X, int64_t n, const int64_t* __restrict_
   int bi[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) { bv[a] = -INFINITY; bi[a] = 0x7fffffff; }
-  for (int c0 = 0; c0 < k1; c0 += kAsgCents) {
+  for (int c0 = c_begin; c0 < c_end; c0 += kAsgCents) {
     __syncthreads();
     for (int idx = threadIdx.x; idx < kAsgCents * kDim; idx += kAsgThreads) {
       const int c = idx / kDim, k = idx % kDim;
-      cs[k][c] = (c0 + c < k1) ? C[(int64_t)(c0 + c) * kDim + k] : 0.f;
+      cs[k][c] = (c0 + c < c_end) ? C[(int64_t)(c0 + c) * kDim + k] : 0.f;
     }
     __syncthreads();
     float acc[4][4] = {};
@@ -72,7 +87,7 @@ assign_kernel(const float* __restrict__ X, int64_t n, const int64_t* __restrict_
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int c = c0 + tx * 4 + b;
-        if (c < k1 && better(acc[a][b], c, bv[a], bi[a])) { bv[a] = acc[a][b]; bi[a] = c; }
+        if (c < c_end && better(acc[a][b], c, bv[a], bi[a])) { bv[a] = acc[a][b]; bi[a] = c; }
       }
   }
   // reduce over the 16 threads (tx) that share each row: lanes of a half warp
@@ -86,10 +101,21 @@ assign_kernel(const float* __restrict__ X, int64_t n, const int64_t* __restrict_
     }
     const int64_t r = row0 + ty * 4 + a;
     if (tx == 0 && r < n) {
-      codes[r] = bi[a];
-      if (best_out) best_out[r] = bv[a];
+      if (split) {
+        if (bi[a] != 0x7fffffff) atomicMax(split + r, best_key(bv[a], bi[a]));
+      } else {
+        codes[r] = bi[a];
+        if (best_out) best_out[r] = bv[a];
+      }
     }
   }
+}
+
+// codes from the merged keys of the split form
+__global__ void assign_finish_kernel(const unsigned long long* __restrict__ split, int64_t n,
+                                     int32_t* __restrict__ codes) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    codes[r] = (int32_t)(0xFFFFFFFFu - (uint32_t)(split[r] & 0xFFFFFFFFu));
 }
 
 // Spherical Lloyd update, step 1: per-centroid sums (FP64) and counts.
@@ -269,6 +295,26 @@ gem_status launch_assign(const float* X, int64_t n, const float* C, int k1, int3
   return GEM_OK;
 }
 
+gem_status launch_assign_split(const float* X, int64_t n, const float* C, int k1, int32_t* codes,
+                               unsigned long long* scratch, int n_sm, cudaStream_t st) {
+  if (n == 0) return GEM_OK;
+  const int64_t blocks = (n + kAsgRows - 1) / kAsgRows;
+  const int c_tiles = (k1 + kAsgCents - 1) / kAsgCents;
+  // enough CTAs for two waves of the SMs, whole centroid tiles per split
+  const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(c_tiles, (2LL * n_sm + blocks - 1) / blocks));
+  if (splits == 1 || !scratch || blocks > 65535) return launch_assign(X, n, C, k1, codes, nullptr, st);
+  const int span = (c_tiles + splits - 1) / splits * kAsgCents;
+  const int ny = (k1 + span - 1) / span;
+  GEM_CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * n, st));
+  assign_kernel<<<dim3((unsigned)blocks, (unsigned)ny), kAsgThreads, 0, st>>>(X, n, nullptr, C, k1, codes, nullptr,
+                                                                               scratch, span);
+  GEM_CUDA_TRY(cudaGetLastError());
+  assign_finish_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(scratch, n, codes);
+  GEM_CUDA_TRY(cudaGetLastError());
+  note_launches(2);
+  return GEM_OK;
+}
+
 gem_status launch_assign_dev_n(const float* X, int64_t max_n, const int64_t* n_dev, const float* C, int k1,
                                int32_t* codes, cudaStream_t st) {
   if (max_n == 0) return GEM_OK;
@@ -341,7 +387,7 @@ gem_status launch_qch(const gem_store* s, gem_workspace* w, const float* q, cons
   const bool asym = w->qch_form == GEM_QCH_ASYMMETRIC;
   // query codes NN(q_i) (the symmetric form)
   if (!asym) {
-    gem_status r = launch_assign(q, n_q_rows, s->d_codebook, k1, w->d_qcodes, nullptr, st);
+    gem_status r = launch_assign_split(q, n_q_rows, s->d_codebook, k1, w->d_qcodes, w->d_assign_key, s->n_sm, st);
     if (r != GEM_OK) return r;
   }
   const int max_np = (w->max_q_len + 31) / 32;

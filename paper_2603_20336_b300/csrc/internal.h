@@ -126,6 +126,9 @@ struct gem_workspace {
 
   // quantized estimate
   int32_t* d_qcodes = nullptr;     // [max_q_rows]
+  // (ordered best value, ~index) per query row while the centroids of C_quant are
+  // split over CTAs (few rows: see launch_assign_split)
+  unsigned long long* d_assign_key = nullptr;  // [max_q_rows]
   float* d_tables = nullptr;       // [table_parts * k1 * 32]
   int table_parts = 0;
 
@@ -279,6 +282,10 @@ gem_status launch_cluster_filter(const float* q, const int64_t* q_offsets, int32
                                  int32_t* out_count, int n_sm, cudaStream_t st);
 gem_status launch_assign(const float* X, int64_t n, const float* C, int k1, int32_t* codes, float* best,
                          cudaStream_t st);
+// the same codes as launch_assign; with few rows the centroids are split over
+// CTAs and merged through scratch [n] (one 64-bit key per row)
+gem_status launch_assign_split(const float* X, int64_t n, const float* C, int k1, int32_t* codes,
+                               unsigned long long* scratch, int n_sm, cudaStream_t st);
 gem_status launch_assign_dev_n(const float* X, int64_t max_n, const int64_t* n_dev, const float* C, int k1,
                                int32_t* codes, cudaStream_t st);
 gem_status launch_kmeans_step(const float* X, int64_t n, const int32_t* codes, double* sums, int* counts,

@@ -194,3 +194,25 @@ def test_asymmetric_qch_matches_oracle_given_gpu_codes(gem, qlens):
         assert abs(simt[t] - want[b, ids[t]]) <= 1e-5 * qlens[b]
     ws.close()
     store.close()
+
+
+def test_qch_with_a_codebook_of_ragged_size_matches_oracle(gem):
+    """k1 = 1,000 (not a multiple of the 64-centroid tile): the query rows are coded
+    with the centroids split over CTAs; the estimate must equal the oracle's on the
+    codes of the row-parallel assignment (gem.assign_codes) within 1e-5 * m_q."""
+    rng = np.random.default_rng(12)
+    w = synth.exact_fp32(n_sets=200, n_queries=1)
+    qs = synth.vector_sets(np.array([32, 32, 17, 32]), synth.centres(64, 1235), 5)
+    store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("f32",))
+    C = _unit(rng, 1000)
+    gem.set_codebook(store, torch.from_numpy(C).cuda())
+    ws = gem.Workspace(store, max_queries=4, max_q_rows=128, max_q_len=32)
+    q, qo = qs.vecs.cuda(), torch.from_numpy(qs.offsets).cuda()
+    est = gem.estimate_codes(store, ws, q, qo).cpu().numpy()
+    assert ws.status() == 0
+    qcodes = gem.assign_codes(q, torch.from_numpy(C).cuda()).cpu().numpy()
+    pcodes = store.export("codes").cpu().numpy()
+    want = oracle.qch_score_all(qcodes, qs.offsets, pcodes, w.docs.offsets, C)
+    assert np.all(np.abs(est - want) <= 1e-5 * np.array([32, 32, 17, 32])[:, None])
+    ws.close()
+    store.close()
