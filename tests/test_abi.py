@@ -50,3 +50,36 @@ def test_host_side_errors_without_gpu(lib):
     assert b"NULL" in lib.gem_last_error_message()
     assert lib.gem_workspace_create(None, 1, 1, 1, 0, 0, ctypes.byref(out)) == 1
     assert lib.gem_topk(None, None, None, 1, 1, None, 1, None, None, None) == 1
+
+
+def test_store_file_validation_needs_no_gpu(lib, tmp_path):
+    """gem_store_load checks a file's header and length before it touches a
+    device: a missing file, a foreign file, another version and a header whose
+    sizes disagree with the file's length are refused with GEM_ERR_INVALID (1)."""
+    import struct
+    lib.gem_store_load.argtypes = [ctypes.c_char_p, ctypes.c_uint32, ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_void_p)]
+    lib.gem_store_load.restype = ctypes.c_int
+
+    def load(path):
+        out = ctypes.c_void_p()
+        return lib.gem_store_load(str(path).encode(), 1, None, ctypes.byref(out)), out.value
+
+    header = b"GEMSTORE" + struct.pack("<IIqqiiII", 1, 128, 2, 3, 0, 0, 0, 0)
+    body = struct.pack("<3q", 0, 1, 3) + b"\0" * (3 * 128 * 4) + b"GEMEND01"
+    cases = {
+        "missing.gem": None,
+        "foreign.gem": b"NOTASTORE" + b"\0" * 64,
+        "version.gem": b"GEMSTORE" + struct.pack("<IIqqiiII", 2, 128, 2, 3, 0, 0, 0, 0) + body,
+        "dim.gem": b"GEMSTORE" + struct.pack("<IIqqiiII", 1, 64, 2, 3, 0, 0, 0, 0) + body,
+        "short.gem": header + body[:-9],
+        "long.gem": header + body + b"x",
+        "offsets.gem": header + struct.pack("<3q", 0, 2, 1) + body[24:],
+    }
+    for name, data in cases.items():
+        p = tmp_path / name
+        if data is not None:
+            p.write_bytes(data)
+        code, handle = load(p)
+        assert code == 1 and not handle, name
+    assert len(header) == 48
