@@ -172,6 +172,8 @@ gem_status gem_store_export(const gem_store* store, int32_t what, void* dst, siz
  * products are FP32 fused multiply-add chains over k = 0..127; ties go to the
  * lowest index.  x float32 [n * 128], centroids float32 [k1 * 128], codes int32
  * [n]; best (may be NULL) receives the winning inner product.  Device pointers.
+ * A NaN dot product counts as -inf, so every code lies in [0, k1) (a row whose
+ * dots are all NaN gets code 0).
  */
 gem_status gem_assign_codes(const float* x, int64_t n, const float* centroids, int32_t k1,
                             int32_t* codes, float* best, void* stream);
@@ -179,7 +181,7 @@ gem_status gem_assign_codes(const float* x, int64_t n, const float* centroids, i
 /*
  * Stage-1 k-means of Sec. 4.1.1 (spherical Lloyd: assign with gem_assign_codes,
  * then each centroid becomes the L2-normalised mean of its vectors; a centroid
- * without vectors keeps its value).  Runs on `sample` vectors of the store's
+ * without vectors, or whose vectors sum to zero, keeps its value).  Runs on `sample` vectors of the store's
  * FP32 copy drawn with `seed` (all vectors if sample <= 0 or >= n_vecs),
  * initialised with k1 distinct sampled vectors, for `iters` iterations.
  * centroids_out float32 [k1 * 128] (device).  A build step: allocates its own
@@ -453,6 +455,15 @@ gem_status gem_topk(gem_workspace* ws, const float* scores, const int64_t* row_o
  * rerank (the top k of the first pass is returned).  Needs GEM_KEEP_F32 when
  * rerank_depth > 0.  Deleted sets (gem_store_mark_deleted) are scored but never
  * returned.  out_ids int64 [n_queries * k], out_scores float32 [n_queries * k].
+ * compute:
+ *   GEM_F32, GEM_BF16, GEM_FP8_E4M3  the first pass is exact CH in that arithmetic
+ *                                    (as gem_score_all);
+ *   GEM_CODES                        the first pass is the quantized estimate qsim
+ *                                    (Sec. 4.5.3, Eq. 16; as gem_estimate_codes over
+ *                                    every set, in the workspace's qCH form), the
+ *                                    estimate-then-exact-rerank order of Algorithm 5.
+ *                                    Needs the store's codebook before the workspace
+ *                                    was created and Sim = inner product.
  */
 gem_status gem_search(const gem_store* store, gem_workspace* ws, const float* q,
                       const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
@@ -587,7 +598,8 @@ gem_status gem_autotune_batch(const gem_store* store, int32_t mode, int32_t n_qu
  * sets a kernel attribute; make that first call before any stream capture.
  * Device-side problems are not reported through a status word: an id outside
  * [0, n_sets) scores NaN, a negative id scores -inf, and inconsistent
- * cand_offsets leave scores unwritten.
+ * cand_offsets leave scores unwritten, as does a query set longer than
+ * max_q_len (all of that query's scores stay unwritten).
  */
 gem_status gem_score_ids_noalloc(const gem_store* store, const float* q, const int64_t* q_offsets,
                                  int32_t n_queries, int64_t n_q_rows, int32_t max_q_len,

@@ -26,9 +26,10 @@ Contents and the passage each follows:
   kmeans_update                   Sec. 4.1.1, one Lloyd update of the stage-1 k-means
 
 Pinned by tests/test_oracle_pins.py against brute force, closed forms, invariants
-and the paper's worked example, except:
-  parity unpinned: kmeans_update (k-means is a heuristic; only its fixed-point
-  invariants are tested).
+and the paper's worked example.  kmeans_update (one Lloyd update given the
+assignment) is pinned by hand examples with exact answers, an empty centroid and
+a zero-sum centroid included; the k-means iteration as a whole (initial centroids,
+number of iterations) is a heuristic and is not oracled.
 """
 from .maxsim import (  # noqa: F401
     chamfer, score_all, score_ids, chamfer_l2, score_all_l2, topk, rerank, recall_at_k,

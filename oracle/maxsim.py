@@ -567,21 +567,23 @@ def contrastive_dscores(S, tau: float) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# Stage-1 k-means (Sec. 4.1.1) -- parity unpinned (heuristic)
+# Stage-1 k-means (Sec. 4.1.1): one Lloyd update given the assignment
 # ---------------------------------------------------------------------------
 
 def kmeans_update(X, codes, C_prev) -> np.ndarray:
     """One spherical Lloyd update: each centroid becomes the L2-normalised mean of
-    the vectors assigned to it; a centroid with no vectors keeps its old value."""
+    the vectors assigned to it.  Where that mean cannot be normalised -- no vector
+    is assigned, or the assigned vectors sum to the zero vector -- the centroid
+    keeps its old value (the paper is silent; a zero centroid would have no
+    direction for d_X = 1 - <.,.>)."""
     X = _f64(X)
     C_prev = _f64(C_prev)
     codes = _i64(codes)
     k, d = C_prev.shape
     sums = np.zeros((k, d))
     np.add.at(sums, codes, X)
-    counts = np.bincount(codes, minlength=k)
+    norms = np.linalg.norm(sums, axis=1)
     C = C_prev.copy()
-    nz = counts > 0
-    norms = np.linalg.norm(sums[nz], axis=1, keepdims=True)
-    C[nz] = sums[nz] / np.where(norms > 0, norms, 1.0)
+    ok = norms > 0
+    C[ok] = sums[ok] / norms[ok, None]
     return C

@@ -724,7 +724,17 @@ static gem_status search_impl(const gem_store* s, gem_workspace* w, const float*
   if (rerank_depth > 0 && (int64_t)rerank_depth * n_queries > w->max_cands)
     return fail(GEM_ERR_INVALID, "n_queries * rerank_depth exceeds max_cands");
   if (rerank_depth > 0 && !s->d_f32) return fail(GEM_ERR_STATE, "the rerank needs the fp32 copy");
-  gem_status r = score_all_impl(s, w, q, q_offsets, n_queries, n_q_rows, compute, w->d_scores, st);
+  gem_status r;
+  if (compute == GEM_CODES) {
+    // first pass by the quantized estimate (Algorithm 5 scores by qCH and
+    // reranks by exact CH): qsim of every stored set in the workspace's form
+    if (w->sim == GEM_SIM_L2) return fail(GEM_ERR_UNSUPPORTED, "qCH is defined for the inner-product Sim");
+    if (s->k1 == 0 || !w->d_tables)
+      return fail(GEM_ERR_STATE, "the codes pass needs a codebook before the workspace is created");
+    r = launch_qch(s, w, q, q_offsets, n_queries, n_q_rows, nullptr, nullptr, w->d_scores, st);
+  } else {
+    r = score_all_impl(s, w, q, q_offsets, n_queries, n_q_rows, compute, w->d_scores, st);
+  }
   if (r != GEM_OK) return r;
   if (rerank_depth == 0)
     return launch_topk(w, w->d_scores, nullptr, n_queries, s->n_sets, nullptr, k, out_ids, out_scores, st);

@@ -29,6 +29,10 @@ __device__ __forceinline__ bool better(float v, int i, float bv, int bi) {
   return v > bv || (v == bv && i < bi);
 }
 
+// A NaN dot (a NaN component in a row or a centroid) counts as -inf, so every
+// row still gets a code in [0, k1): the lowest index when all its dots are NaN.
+__device__ __forceinline__ float nan_low(float v) { return (v != v) ? -INFINITY : v; }
+
 // 64 vectors x 64 centroids per step; thread (ty, tx) owns rows 4ty..4ty+3 and
 // centroids 4tx..4tx+3 of the step; operands are staged k-major in shared memory.
 // keys: larger key = larger value, then lower index (the order of better());
@@ -87,7 +91,8 @@ assign_kernel(const float* __restrict__ X, int64_t n, const int64_t* __restrict_
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int c = c0 + tx * 4 + b;
-        if (c < c_end && better(acc[a][b], c, bv[a], bi[a])) { bv[a] = acc[a][b]; bi[a] = c; }
+        const float v = nan_low(acc[a][b]);
+        if (c < c_end && better(v, c, bv[a], bi[a])) { bv[a] = v; bi[a] = c; }
       }
   }
   // reduce over the 16 threads (tx) that share each row: lanes of a half warp
@@ -112,10 +117,14 @@ assign_kernel(const float* __restrict__ X, int64_t n, const int64_t* __restrict_
 }
 
 // codes from the merged keys of the split form
+// (a key of 0 -- no CTA merged anything into the row -- gives code 0, so a
+// code is always a valid centroid index)
 __global__ void assign_finish_kernel(const unsigned long long* __restrict__ split, int64_t n,
                                      int32_t* __restrict__ codes) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
-    codes[r] = (int32_t)(0xFFFFFFFFu - (uint32_t)(split[r] & 0xFFFFFFFFu));
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long key = split[r];
+    codes[r] = key == 0ull ? 0 : (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFu));
+  }
 }
 
 // Spherical Lloyd update, step 1: per-centroid sums (FP64) and counts.

@@ -15,6 +15,7 @@
 //   u32      deleted [ceil(n_sets / 32)] (has_deleted)
 //   trailer  "GEMEND01"
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -64,15 +65,25 @@ gem_status put_device(FILE* f, const float* d, int64_t n, cudaStream_t st) {
   return GEM_OK;
 }
 
-// file -> new device array of n floats (caller frees)
-gem_status get_device(FILE* f, int64_t n, float** out, cudaStream_t st) {
+// host array -> new device array of n floats (caller frees)
+gem_status to_device(const std::vector<float>& h, float** out, cudaStream_t st) {
   *out = nullptr;
-  std::vector<float> h((size_t)n);
-  if (!get(f, h.data(), sizeof(float) * n)) return fail(GEM_ERR_INVALID, "store file truncated");
-  GEM_CUDA_TRY(cudaMalloc(out, sizeof(float) * std::max<int64_t>(n, 1)));
-  GEM_CUDA_TRY(cudaMemcpyAsync(*out, h.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
+  GEM_CUDA_TRY(cudaMalloc(out, sizeof(float) * std::max<size_t>(h.size(), 1)));
+  GEM_CUDA_TRY(cudaMemcpyAsync(*out, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, st));
   GEM_CUDA_TRY(cudaStreamSynchronize(st));
   return GEM_OK;
+}
+
+// n floats from the file into h; false when the file is short
+bool get_floats(FILE* f, int64_t n, std::vector<float>& h) {
+  h.resize((size_t)n);
+  return get(f, h.data(), sizeof(float) * n);
+}
+
+bool all_finite(const std::vector<float>& h) {
+  for (float x : h)
+    if (!std::isfinite(x)) return false;
+  return true;
 }
 
 }  // namespace
@@ -143,16 +154,25 @@ extern "C" gem_status gem_store_load(const char* path, uint32_t keep_mask, void*
   std::vector<int64_t> off((size_t)(h.n_sets + 1));
   if (!get(file.f, off.data(), sizeof(int64_t) * off.size())) return fail(GEM_ERR_INVALID, "store file truncated");
   if (off[0] != 0 || off[h.n_sets] != h.n_vecs) return fail(GEM_ERR_INVALID, "corrupt store offsets");
+  for (int64_t i = 0; i < h.n_sets; ++i)
+    if (off[i + 1] <= off[i]) return fail(GEM_ERR_INVALID, "corrupt store offsets");
+  // every float array is read and checked on the host before any device work:
+  // a NaN or an infinity in the vectors or the centroids refuses the file
+  std::vector<float> cq, ci;
   gem_store* s = nullptr;
   {
-    std::vector<float> vecs((size_t)(h.n_vecs * kDim));
-    if (!get(file.f, vecs.data(), sizeof(float) * vecs.size())) return fail(GEM_ERR_INVALID, "store file truncated");
+    std::vector<float> vecs;
+    if (!get_floats(file.f, h.n_vecs * kDim, vecs) || !get_floats(file.f, (int64_t)h.k1 * kDim, cq) ||
+        !get_floats(file.f, (int64_t)h.k2 * kDim, ci))
+      return fail(GEM_ERR_INVALID, "store file truncated");
+    if (!all_finite(vecs)) return fail(GEM_ERR_INVALID, "store file holds a non-finite vector component");
+    if (!all_finite(cq) || !all_finite(ci)) return fail(GEM_ERR_INVALID, "store file holds a non-finite centroid");
     gem_status r = gem_store_create(vecs.data(), off.data(), h.n_sets, kDim, keep_mask, 1, stream, &s);
     if (r != GEM_OK) return r;
   }
   auto attach = [&](int32_t k, bool quant) -> gem_status {
     float* d = nullptr;
-    gem_status r = get_device(file.f, (int64_t)k * kDim, &d, st);
+    gem_status r = to_device(quant ? cq : ci, &d, st);
     if (r == GEM_OK)
       r = quant ? gem_store_set_codebook(s, d, k, stream) : gem_store_set_index_centroids(s, d, k, stream);
     if (r == GEM_OK) {

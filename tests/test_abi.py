@@ -53,9 +53,10 @@ def test_host_side_errors_without_gpu(lib):
 
 
 def test_store_file_validation_needs_no_gpu(lib, tmp_path):
-    """gem_store_load checks a file's header and length before it touches a
-    device: a missing file, a foreign file, another version and a header whose
-    sizes disagree with the file's length are refused with GEM_ERR_INVALID (1)."""
+    """gem_store_load checks a file's header, length, offsets and float values
+    before it touches a device: a missing file, a foreign file, another version,
+    a header whose sizes disagree with the file's length, bad offsets and a
+    non-finite vector or centroid are refused with GEM_ERR_INVALID (1)."""
     import struct
     lib.gem_store_load.argtypes = [ctypes.c_char_p, ctypes.c_uint32, ctypes.c_void_p,
                                    ctypes.POINTER(ctypes.c_void_p)]
@@ -75,6 +76,17 @@ def test_store_file_validation_needs_no_gpu(lib, tmp_path):
         "short.gem": header + body[:-9],
         "long.gem": header + body + b"x",
         "offsets.gem": header + struct.pack("<3q", 0, 2, 1) + body[24:],
+        # finite-size files whose float arrays hold a NaN or an infinity: a NaN
+        # centroid would make every dot NaN, so the file is refused before any
+        # device work (the codes kernels also map NaN dots below every value)
+        "nan_vector.gem": header + struct.pack("<3q", 0, 1, 3) + struct.pack("<f", float("nan"))
+        + b"\0" * (3 * 128 * 4 - 4) + b"GEMEND01",
+        "nan_centroid.gem": b"GEMSTORE" + struct.pack("<IIqqiiII", 1, 128, 2, 3, 1, 0, 0, 0)
+        + struct.pack("<3q", 0, 1, 3) + b"\0" * (3 * 128 * 4) + struct.pack("<f", float("nan"))
+        + b"\0" * (127 * 4) + b"GEMEND01",
+        "inf_index_centroid.gem": b"GEMSTORE" + struct.pack("<IIqqiiII", 1, 128, 2, 3, 0, 1, 0, 0)
+        + struct.pack("<3q", 0, 1, 3) + b"\0" * (3 * 128 * 4) + b"\0" * (127 * 4)
+        + struct.pack("<f", float("inf")) + b"GEMEND01",
     }
     for name, data in cases.items():
         p = tmp_path / name
@@ -82,4 +94,6 @@ def test_store_file_validation_needs_no_gpu(lib, tmp_path):
             p.write_bytes(data)
         code, handle = load(p)
         assert code == 1 and not handle, name
+        if "nan" in name or "inf" in name:
+            assert b"non-finite" in lib.gem_last_error_message(), name
     assert len(header) == 48

@@ -106,9 +106,22 @@ def test_finite_differences_4x4(gem):
             assert G[idx] == pytest.approx(fd, rel=1e-4, abs=1e-6)
 
 
+# Near-tie band of the argmax decision.  Both sides decide j* on the
+# bf16-rounded inputs; the GPU's dots are FP32 sums of exact bf16 products, each
+# within 128 * 2^-24 * sum_k |q_k p_k| <= 128 * 2^-24 * (1 + 2^-8)^2 of the FP64
+# value, so two candidates whose FP64 dots differ by more than twice that are
+# ordered the same way on both sides.
+ARGMAX_BAND = 2 * 128 * 2.0 ** -24 * (1 + 2.0 ** -8) ** 2
+
+
 def test_full_size_gradient_matches_oracle(gem):
     """256 queries x 32 vectors, 64 own sets each (lengths 32..256), BF16 forward,
-    FP32 gradients; compared with the oracle on the rows whose argmax agrees."""
+    FP32 gradients, against the oracle on every 4th query with all 64 of its sets.
+
+    Outside the near-tie band the GPU's argmax must equal the oracle's FP64 argmax
+    exactly; inside it the GPU's choice must be a valid one (within the band of the
+    maximum) and the oracle's gradient takes that choice.  dQ and dP are then
+    compared on every row, within 1e-5 of the L1 of the terms each sums."""
     w = synth.contrastive_batch(device="cuda")
     B, per_q = 256, 64
     po, pid = _pairs(B, per_q)
@@ -120,29 +133,50 @@ def test_full_size_gradient_matches_oracle(gem):
     loss.backward()
     _, am = gem.maxsim_fwd(w.queries.vecs, qo, w.docs.vecs, do, po.cuda(), pid.cuda(), "bf16")
     am = am.cpu().numpy()
-    # sampled outputs: 16 queries with all of their 64 sets
-    Qn = w.queries.vecs.cpu().numpy().astype(np.float64)
-    Dn = w.docs.vecs.cpu().numpy().astype(np.float64)
+    Qf = w.queries.vecs.cpu().numpy()
+    Df = w.docs.vecs.cpu().numpy()
+    Qn, Dn = Qf.astype(np.float64), Df.astype(np.float64)
+    Qr, Dr = oracle.bf16_round(Qf).astype(np.float64), oracle.bf16_round(Df).astype(np.float64)
     g = oracle.contrastive_dscores(s.detach().cpu().numpy().astype(np.float64).reshape(B, per_q), TAU)
     gq_gpu = q.grad.cpu().numpy()
     gd_gpu = D.grad.cpu().numpy()
-    Qr, Dr = oracle.bf16_round(Qn.astype(np.float32)), oracle.bf16_round(Dn.astype(np.float32))
-    n_rows = n_agree = 0
-    for b in range(0, B, 16):
+    n_rows = n_band = 0
+    for b in range(0, B, 4):
         qr = slice(w.queries.offsets[b], w.queries.offsets[b + 1])
-        gq = np.zeros((32, 128))
-        rows_ok = np.ones(32, bool)
+        m_q = qr.stop - qr.start
+        gq = np.zeros((m_q, 128))
+        gq_l1 = np.zeros((m_q, 128))
         for n in range(per_q):
             t = b * per_q + n
             dr = slice(w.docs.offsets[t], w.docs.offsets[t + 1])
-            # j* decided on the bf16-rounded inputs, as the BF16 forward decides it
-            dq, dp, js = oracle.maxsim_grad(Qn[qr], Dn[dr], decide=(Qr[qr], Dr[dr]))
-            same = js == am[t, :32]
-            rows_ok &= same
+            sims = Qr[qr] @ Dr[dr].T
+            js = np.argmax(sims, axis=1)
+            top = sims.max(axis=1)
+            srt = np.sort(sims, axis=1)
+            margin = srt[:, -1] - srt[:, -2] if sims.shape[1] > 1 else np.full(m_q, np.inf)
+            mine = am[t, :m_q]
+            clear = margin > ARGMAX_BAND
+            np.testing.assert_array_equal(mine[clear], js[clear], err_msg=f"pair {t}")
+            # inside the band: a valid choice, which the oracle's gradient then takes
+            assert np.all((mine >= 0) & (mine < sims.shape[1])), t
+            assert np.all(sims[np.arange(m_q), mine] >= top - ARGMAX_BAND), t
+            jstar = np.where(clear, js, mine)
+            n_rows += m_q
+            n_band += int((~clear).sum())
+            dq, dp, js_o = oracle.maxsim_grad(Qn[qr], Dn[dr], decide=(Qr[qr], Dr[dr]))
+            np.testing.assert_array_equal(js_o, js)
+            if not np.array_equal(jstar, js_o):
+                # a near tie the GPU resolved the other way: the gradient at its choice
+                dq = Dn[dr][jstar]
+                dp = np.zeros_like(Dn[dr])
+                np.add.at(dp, jstar, Qn[qr])
+            dp_l1 = np.zeros_like(dp)
+            np.add.at(dp_l1, jstar, np.abs(Qn[qr]))
             gq += g[b, n] * dq
-            if same.all():
-                np.testing.assert_allclose(gd_gpu[dr], g[b, n] * dp, atol=1e-5 * abs(g[b, n]) + 1e-7)
-        n_rows += 32
-        n_agree += int(rows_ok.sum())
-        np.testing.assert_allclose(gq_gpu[qr][rows_ok], gq[rows_ok], rtol=1e-4, atol=1e-6)
-    assert n_agree >= 0.97 * n_rows
+            gq_l1 += abs(g[b, n]) * np.abs(dq)
+            err = np.abs(gd_gpu[dr] - g[b, n] * dp)
+            assert np.all(err <= 1e-5 * abs(g[b, n]) * dp_l1), (t, err.max())
+        err = np.abs(gq_gpu[qr] - gq)
+        assert np.all(err <= 1e-5 * gq_l1), (b, err.max())
+    assert n_rows == 64 * per_q * 32
+    assert n_band <= 0.01 * n_rows, n_band

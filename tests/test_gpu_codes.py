@@ -100,8 +100,12 @@ def test_qch_lossless_codes_equal_exact_chamfer(gem):
     ws = gem.Workspace(store, max_queries=4, max_q_rows=128, max_q_len=32)
     est = gem.estimate_codes(store, ws, w.queries.vecs.cuda(), torch.from_numpy(w.queries.offsets).cuda())
     assert ws.status() == 0
-    S64, L1 = oracle.score_all(Q, w.queries.offsets, X, w.docs.offsets, with_l1=True)
-    assert np.all(np.abs(est.cpu().numpy() - S64) <= 1e-5 * L1 + 1e-6)
+    S64 = oracle.score_all(Q, w.queries.offsets, X, w.docs.offsets)
+    # each table entry is one 128-term FP32 FMA chain of unit vectors (absolute
+    # error <= 128 * 2^-24 < 7.7e-6 per term, whatever the term's size), the
+    # per-set sum a 5-level butterfly (<= 5 * 2^-24 relative): < 1e-5 per query vector
+    m_q = np.diff(w.queries.offsets)[:, None]
+    assert np.all(np.abs(est.cpu().numpy() - S64) <= 1e-5 * m_q)
 
 
 @pytest.mark.parametrize("qlens", [[32] * 5, [1, 7, 33, 64, 100, 20]])
@@ -152,8 +156,9 @@ def test_asymmetric_qch_lossless_on_the_stored_side(gem):
     q, qo = w.queries.vecs.cuda(), torch.from_numpy(w.queries.offsets).cuda()
     est = gem.estimate_codes(store, ws, q, qo).cpu().numpy()
     assert ws.status() == 0
-    S64, L1 = oracle.score_all(Q, w.queries.offsets, X, w.docs.offsets, with_l1=True)
-    assert np.all(np.abs(est - S64) <= 1e-5 * L1 + 1e-6)
+    S64 = oracle.score_all(Q, w.queries.offsets, X, w.docs.offsets)
+    # the bound of the symmetric lossless test: < 1e-5 per query vector
+    assert np.all(np.abs(est - S64) <= 1e-5 * np.diff(w.queries.offsets)[:, None])
     gem.set_qch_form(ws, "symmetric")
     sym = gem.estimate_codes(store, ws, q, qo).cpu().numpy()
     assert np.abs(sym - S64).max() > 1e-3
@@ -214,5 +219,109 @@ def test_qch_with_a_codebook_of_ragged_size_matches_oracle(gem):
     pcodes = store.export("codes").cpu().numpy()
     want = oracle.qch_score_all(qcodes, qs.offsets, pcodes, w.docs.offsets, C)
     assert np.all(np.abs(est - want) <= 1e-5 * np.array([32, 32, 17, 32])[:, None])
+    ws.close()
+    store.close()
+
+
+def test_query_codes_split_tie_break_and_nan_rows(gem):
+    """Query codes with the centroids split over CTAs (k1 = 1,000, few rows).
+    Centroid 4 = e_1 and centroid 700 = e_1 + e_2 (another 64-centroid span) both
+    give exactly 1.0 against a query row e_1: the lower index, 4, must win the
+    merge across CTAs.  The two choices give different estimates (the table rows
+    <C_4, C_c> and <C_700, C_c> differ), so the estimate shows which one won.  A
+    query row of NaNs gets code 0 (every dot counts as -inf, the lowest index
+    wins) and a stored NaN row also gets a code in range."""
+    rng = np.random.default_rng(31)
+    k1 = 1000
+    C = _unit(rng, k1)
+    C[:, 0] *= 0.05                        # no other centroid comes near e_1
+    C /= np.linalg.norm(C, axis=1, keepdims=True)
+    C[4] = 0.0
+    C[4, 0] = 1.0
+    C[700] = 0.0
+    C[700, 0] = 1.0
+    C[700, 1] = 1.0
+    w = synth.exact_fp32(n_sets=150, n_queries=1)
+    X = w.docs.vecs.numpy().copy()
+    X[5] = np.nan                          # one stored row of NaNs (set 0)
+    store = gem.Store(torch.from_numpy(X).cuda(), w.docs.offsets, keep=("f32",))
+    gem.set_codebook(store, torch.from_numpy(C).cuda())
+    pcodes = store.export("codes").cpu().numpy()
+    assert pcodes.min() >= 0 and pcodes.max() < k1 and pcodes[5] == 0
+    qs = synth.vector_sets(np.array([32, 32, 20]), synth.centres(64, 1235), 77)
+    Q = qs.vecs.numpy().copy()
+    Q[[0, 33, 40, 70]] = 0.0
+    Q[[0, 33, 40, 70], 0] = 1.0            # rows equal to e_1: ties 4 / 700
+    Q[50] = np.nan                         # a NaN query row (query 1)
+    q, qo = torch.from_numpy(Q).cuda(), torch.from_numpy(qs.offsets).cuda()
+    qcodes = gem.assign_codes(q, torch.from_numpy(C).cuda()).cpu().numpy().astype(np.int64)
+    assert qcodes[[0, 33, 40, 70]].tolist() == [4, 4, 4, 4] and qcodes[50] == 0
+    ok = np.isfinite(Q).all(axis=1)
+    _check_codes(Q[ok], C, qcodes[ok])
+    ws = gem.Workspace(store, max_queries=3, max_q_rows=96, max_q_len=32)
+    est = gem.estimate_codes(store, ws, q, qo).cpu().numpy()
+    assert ws.status() == 0
+    live = np.arange(1, 150)               # set 0 holds the NaN row
+    want = oracle.qch_score_all(qcodes, qs.offsets, pcodes, w.docs.offsets, C)
+    m_q = np.diff(qs.offsets)[:, None]
+    assert np.all(np.abs(est[:, live] - want[:, live]) <= 1e-5 * m_q)
+    # with code 700 in place of 4 the estimate moves by far more than the tolerance
+    alt = qcodes.copy()
+    alt[[0, 33, 40, 70]] = 700
+    moved = oracle.qch_score_all(alt, qs.offsets, pcodes, w.docs.offsets, C)
+    assert np.abs(moved[:, live] - want[:, live]).max() > 1e-2
+    ws.close()
+    store.close()
+
+
+@pytest.mark.parametrize("form", ["symmetric", "asymmetric"])
+def test_search_codes_first_pass_then_exact_rerank(gem, form):
+    """gem_search with GEM_CODES (Algorithm 5's order): the qCH estimate of every
+    set, its top-R, the exact FP32 rerank of that pool and the top-k of it, in one
+    call.  The pool must be the oracle's top-R of the FP64 estimate on the GPU's
+    codes wherever the R-th and (R+1)-th estimates are apart by more than twice
+    the estimate's tolerance; the result must then be the oracle's rerank of that
+    pool (exact-score swaps within 1e-6 allowed)."""
+    w = synth.exact_fp32(n_sets=400, n_queries=12)
+    store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("f32",))
+    C = gem.train_codebook(store, k1=256, iters=5, sample=0, seed=3)
+    gem.set_codebook(store, C)
+    R, K = 60, 10
+    ws = gem.Workspace(store, max_queries=12, max_q_rows=12 * 32, max_q_len=32, max_cands=12 * R, max_k=R)
+    gem.set_qch_form(ws, form)
+    q, qo = w.queries.vecs.cuda(), torch.from_numpy(w.queries.offsets).cuda()
+    ids, sc = gem.search(store, ws, q, qo, "codes", rerank_depth=R, k=K)
+    ids0, _ = gem.search(store, ws, q, qo, "codes", rerank_depth=0, k=K)
+    assert ws.status() == 0
+    ids, sc, ids0 = ids.cpu().numpy(), sc.cpu().numpy(), ids0.cpu().numpy()
+    Cn = C.cpu().numpy()
+    pcodes = store.export("codes").cpu().numpy()
+    Q, X = w.queries.vecs.numpy(), w.docs.vecs.numpy()
+    if form == "symmetric":
+        qcodes = gem.assign_codes(q, C).cpu().numpy()
+        est = oracle.qch_score_all(qcodes, w.queries.offsets, pcodes, w.docs.offsets, Cn)
+    else:
+        est = oracle.qch_asym_score_all(Q, w.queries.offsets, pcodes, w.docs.offsets, Cn)
+    S64, L1 = oracle.score_all(Q, w.queries.offsets, X, w.docs.offsets, with_l1=True)
+    tol = 1e-5 * 32
+    checked = 0
+    for b in range(12):
+        order = np.lexsort((np.arange(400), -est[b]))
+        if est[b, order[R - 1]] - est[b, order[R]] <= 2 * tol:
+            continue                       # pool boundary inside the estimate's tolerance
+        checked += 1
+        pool = order[:R]
+        want_ids, want_sc = oracle.rerank(Q[w.queries.offsets[b]:w.queries.offsets[b + 1]], np.array([0, 32]),
+                                          X, w.docs.offsets, pool[None, :], K)
+        want_ids, want_sc = want_ids[0], want_sc[0]
+        for x in set(want_ids.tolist()) ^ set(ids[b].tolist()):
+            assert abs(S64[b, x] - want_sc[-1]) <= 1e-6 * max(1.0, abs(want_sc[-1])), (b, x)
+        assert set(ids[b].tolist()) <= set(pool.tolist())
+        assert np.all(np.abs(sc[b] - S64[b, ids[b]]) <= 1e-5 * L1[b, ids[b]])
+        # rerank_depth 0: the estimate's own top-k
+        top0 = order[:K]
+        if est[b, order[K - 1]] - est[b, order[K]] > 2 * tol:
+            assert set(ids0[b].tolist()) == set(top0.tolist())
+    assert checked >= 8, checked
     ws.close()
     store.close()

@@ -457,6 +457,29 @@ def test_kmeans_update_fixed_point_invariants():
     assert np.all(sims[np.arange(300), codes] >= sims.max(1) - 1e-15)
 
 
+def test_kmeans_update_hand_examples():
+    """One Lloyd update on hand-computable inputs (Sec. 4.1.1 stage-1 k-means):
+    a centroid with members becomes the unit mean of its members, a centroid with
+    no member keeps its value, and so does one whose members sum to zero."""
+    X = np.array([[3.0, 0.0, 0.0], [0.0, 4.0, 0.0], [2.0, 0.0, 0.0], [-2.0, 0.0, 0.0]])
+    C0 = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    # centroid 0 <- rows 0, 1 (sum (3, 4, 0)); centroid 1 <- rows 2, 3 (sum 0);
+    # centroid 2 <- nothing
+    C = oracle.kmeans_update(X, np.array([0, 0, 1, 1]), C0)
+    np.testing.assert_array_equal(C[0], [0.6, 0.8, 0.0])
+    np.testing.assert_array_equal(C[1], C0[1])
+    np.testing.assert_array_equal(C[2], C0[2])
+    # three points, two centroids, one of them empty: the means of 2 and 1 rows
+    X = np.array([[1.0, 0.0], [0.0, 1.0], [0.0, 2.0]])
+    C = oracle.kmeans_update(X, np.array([1, 1, 1]), np.array([[0.0, -1.0], [1.0, 0.0]]))
+    np.testing.assert_array_equal(C[0], [0.0, -1.0])
+    np.testing.assert_allclose(C[1], np.array([1.0, 3.0]) / np.sqrt(10.0), rtol=0, atol=1e-15)
+    # the update does not depend on the order of the rows
+    perm = np.array([2, 0, 1])
+    np.testing.assert_array_equal(oracle.kmeans_update(X[perm], np.array([0, 1, 1]), C),
+                                  oracle.kmeans_update(X, np.array([1, 1, 0]), C))
+
+
 def test_synthetic_generators_shapes_and_norms():
     w = synth.exact_fp32(n_sets=100, n_queries=3)
     L = w.docs.lengths()
