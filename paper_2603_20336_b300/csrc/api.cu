@@ -270,7 +270,7 @@ void gem_workspace_destroy(gem_workspace* w) {
                   w->d_part_pass, w->d_part_slot, w->d_part_row0, w->d_row_part, w->d_qpack_bf16,
                   w->d_qpack_fp8, w->d_qpack_scale, w->d_scores, w->d_pool_ids, w->d_pool_off,
                   w->d_pool_scores, w->d_q_in, w->d_qo_in, w->d_out_ids, w->d_out_scores,
-                  w->d_qcodes, w->d_assign_key, w->d_tables};
+                  w->d_qcodes, w->d_assign_key, w->d_tables, w->d_topk_thr, w->d_topk_cnt, w->d_topk_cand};
   for (void* p : ptrs) dfree(p);
   cudaSetDevice(prev);
   delete w;
@@ -330,6 +330,13 @@ gem_status gem_workspace_create(const gem_store* s, int32_t max_queries, int64_t
     WS_ALLOC(d_qo_in, max_queries + 1);
     WS_ALLOC(d_out_ids, (size_t)max_queries * max_k);
     WS_ALLOC(d_out_scores, (size_t)max_queries * max_k);
+    // candidate buffers of the threshold top-k: at most 512 MB, whole rows
+    w->topk_cap = topk_candidate_cap(max_k);
+    const int64_t row_bytes = (int64_t)w->topk_cap * 8;
+    w->topk_rows = (int)std::max<int64_t>(1, std::min<int64_t>(max_queries, ((int64_t)512 << 20) / row_bytes));
+    WS_ALLOC(d_topk_thr, w->topk_rows);
+    WS_ALLOC(d_topk_cnt, w->topk_rows);
+    WS_ALLOC(d_topk_cand, (size_t)w->topk_rows * w->topk_cap);
   }
   if (max_cands > 0) {
     WS_ALLOC(d_pool_ids, max_cands);

@@ -46,22 +46,27 @@ __device__ __forceinline__ unsigned long long best_key(float v, int i) {
 // split != nullptr: blockIdx.y takes the centroids [y * span, (y + 1) * span) and
 // the row's best over them is merged into split[row] by a 64-bit atomic max of
 // best_key; every dot is the same FMA chain as in the unsplit form, so the
-// merged argmax is the same.
+// merged argmax is the same.  rows != nullptr: row r of the launch is row
+// rows[r] of X / codes / best_out (the rows the tensor-core assignment could
+// not decide); n_dev != nullptr bounds n on the device.  CTAs stride over the
+// 64-row blocks.
 __global__ void __launch_bounds__(kAsgThreads)
 assign_kernel(const float* __restrict__ X, int64_t n, const int64_t* __restrict__ n_dev,
               const float* __restrict__ C, int k1, int32_t* __restrict__ codes, float* __restrict__ best_out,
-              unsigned long long* __restrict__ split = nullptr, int span = 0) {
+              unsigned long long* __restrict__ split = nullptr, int span = 0,
+              const int32_t* __restrict__ rows = nullptr) {
   if (n_dev) n = min(n, *n_dev);
   const int c_begin = split ? (int)blockIdx.y * span : 0;
   const int c_end = split ? min(k1, c_begin + span) : k1;
   __shared__ __align__(16) float xs[kDim][kAsgRows];
   __shared__ __align__(16) float cs[kDim][kAsgCents];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t row0 = (int64_t)blockIdx.x * kAsgRows;
-  if (row0 >= n) return;
+  for (int64_t row0 = (int64_t)blockIdx.x * kAsgRows; row0 < n; row0 += (int64_t)gridDim.x * kAsgRows) {
+  __syncthreads();  // the previous block's tiles are no longer read
   for (int idx = threadIdx.x; idx < kAsgRows * kDim; idx += kAsgThreads) {
     const int r = idx / kDim, k = idx % kDim;
-    xs[k][r] = (row0 + r < n) ? X[(row0 + r) * kDim + k] : 0.f;
+    const int64_t src = row0 + r < n ? (rows ? (int64_t)rows[row0 + r] : row0 + r) : -1;
+    xs[k][r] = src >= 0 ? X[src * kDim + k] : 0.f;
   }
   float bv[4];
   int bi[4];
@@ -109,10 +114,12 @@ assign_kernel(const float* __restrict__ X, int64_t n, const int64_t* __restrict_
       if (split) {
         if (bi[a] != 0x7fffffff) atomicMax(split + r, best_key(bv[a], bi[a]));
       } else {
-        codes[r] = bi[a];
-        if (best_out) best_out[r] = bv[a];
+        const int64_t dst = rows ? (int64_t)rows[r] : r;
+        codes[dst] = bi[a];
+        if (best_out) best_out[dst] = bv[a];
       }
     }
+  }
   }
 }
 
@@ -293,9 +300,25 @@ __global__ void __launch_bounds__(256) qch_scan_kernel(ScanArgs a) {
 
 }  // namespace
 
+gem_status launch_assign_rows(const float* X, int64_t max_n, const int64_t* n_dev, const int32_t* rows,
+                              const float* C, int k1, int32_t* codes, float* best, int n_sm, cudaStream_t st) {
+  if (max_n == 0) return GEM_OK;
+  const int64_t blocks = std::min<int64_t>((max_n + kAsgRows - 1) / kAsgRows, (int64_t)n_sm * 4);
+  assign_kernel<<<(unsigned)blocks, kAsgThreads, 0, st>>>(X, max_n, n_dev, C, k1, codes, best, nullptr, 0, rows);
+  GEM_CUDA_TRY(cudaGetLastError());
+  note_launches(1);
+  return GEM_OK;
+}
+
 gem_status launch_assign(const float* X, int64_t n, const float* C, int k1, int32_t* codes, float* best,
                          cudaStream_t st) {
   if (n == 0) return GEM_OK;
+  if (n >= kAssignTcMinRows && k1 >= kAssignTcMinCentroids) {
+    int dev = 0, n_sm = 0;
+    GEM_CUDA_TRY(cudaGetDevice(&dev));
+    GEM_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    return launch_assign_tc(X, n, C, k1, codes, best, n_sm, st);
+  }
   const int64_t blocks = (n + kAsgRows - 1) / kAsgRows;
   if (blocks > INT32_MAX) return fail(GEM_ERR_INVALID, "too many vectors");
   assign_kernel<<<(unsigned)blocks, kAsgThreads, 0, st>>>(X, n, nullptr, C, k1, codes, best);

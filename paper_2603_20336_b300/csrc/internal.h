@@ -138,6 +138,14 @@ struct gem_workspace {
   int64_t* d_pool_off = nullptr;   // [max_queries + 1]
   float* d_pool_scores = nullptr;  // [max_cands]
 
+  // threshold top-k of long dense rows (topk.cu): per row a key threshold, a
+  // counter and a candidate buffer of topk_cap keys, for topk_rows rows at a time
+  int topk_cap = 0;
+  int topk_rows = 0;
+  unsigned long long* d_topk_thr = nullptr;   // [topk_rows]
+  unsigned* d_topk_cnt = nullptr;             // [topk_rows]
+  unsigned long long* d_topk_cand = nullptr;  // [topk_rows * topk_cap]
+
   // host-buffer entry point staging
   float* d_q_in = nullptr;
   int64_t* d_qo_in = nullptr;
@@ -254,6 +262,9 @@ gem_status score_ids_noalloc(const gem_store* s, const float* q, const int64_t* 
                              int64_t n_q_rows, int32_t max_q_len, const int64_t* cand_offsets,
                              const int64_t* cand_ids, int64_t n_cands, float* scores, cudaStream_t st);
 
+// Candidate-buffer entries per row the threshold top-k needs for k <= max_k.
+int topk_candidate_cap(int max_k);
+
 // Per-row top-k by (score desc, id asc).
 gem_status launch_topk(gem_workspace* ws, const float* scores, const int64_t* row_offsets,
                        int32_t rows, int64_t cols, const int64_t* ids, int32_t k,
@@ -280,8 +291,19 @@ gem_status launch_entry_points(const gem_store* s, const int32_t* lists, const i
 gem_status launch_cluster_filter(const float* q, const int64_t* q_offsets, int32_t n_queries, const float* centroids,
                                  int32_t k2, int32_t t, int32_t cap, uint32_t* out_mask, int32_t* out_list,
                                  int32_t* out_count, int n_sm, cudaStream_t st);
+// NN codes of n rows (ties to the lowest index, FP32 chain per dot).  From
+// kAssignTcMinRows rows and kAssignTcMinCentroids centroids on the tensor cores
+// (assign_tc.cu: the same codes; allocates stream-ordered scratch and blocks
+// until done), otherwise the FP32 SIMT kernel (asynchronous).
+constexpr int64_t kAssignTcMinRows = 16384;
+constexpr int kAssignTcMinCentroids = 64;
 gem_status launch_assign(const float* X, int64_t n, const float* C, int k1, int32_t* codes, float* best,
                          cudaStream_t st);
+gem_status launch_assign_tc(const float* X, int64_t n, const float* C, int k1, int32_t* codes, float* best,
+                            int n_sm, cudaStream_t st);
+// the SIMT assignment of the rows rows[0 .. *n_dev - 1] (at most max_n) of X
+gem_status launch_assign_rows(const float* X, int64_t max_n, const int64_t* n_dev, const int32_t* rows,
+                              const float* C, int k1, int32_t* codes, float* best, int n_sm, cudaStream_t st);
 // the same codes as launch_assign; with few rows the centroids are split over
 // CTAs and merged through scratch [n] (one 64-bit key per row)
 gem_status launch_assign_split(const float* X, int64_t n, const float* C, int k1, int32_t* codes,

@@ -129,6 +129,7 @@ def test_full_size_gradient_matches_oracle(gem):
     D = w.docs.vecs.clone().requires_grad_(True)
     qo, do = torch.from_numpy(w.queries.offsets).cuda(), torch.from_numpy(w.docs.offsets).cuda()
     s = gem.MaxSimFn.apply(q, D, qo, do, po.cuda(), pid.cuda(), "bf16")
+    s.retain_grad()
     loss = torch.nn.functional.cross_entropy(s.view(B, per_q) / TAU, torch.zeros(B, dtype=torch.int64, device="cuda"))
     loss.backward()
     _, am = gem.maxsim_fwd(w.queries.vecs, qo, w.docs.vecs, do, po.cuda(), pid.cuda(), "bf16")
@@ -137,7 +138,15 @@ def test_full_size_gradient_matches_oracle(gem):
     Df = w.docs.vecs.cpu().numpy()
     Qn, Dn = Qf.astype(np.float64), Df.astype(np.float64)
     Qr, Dr = oracle.bf16_round(Qf).astype(np.float64), oracle.bf16_round(Df).astype(np.float64)
-    g = oracle.contrastive_dscores(s.detach().cpu().numpy().astype(np.float64).reshape(B, per_q), TAU)
+    # dL/dS: torch's cross-entropy in FP32 (not this library's arithmetic) against
+    # the oracle's FP64 chain rule.  The logits s / tau reach about 600, where an
+    # FP32 ulp is 6e-5, so each softmax entry is off by up to about 1e-4 of itself
+    # (probabilities below FP32's range come out as 0)
+    g64 = oracle.contrastive_dscores(s.detach().cpu().numpy().astype(np.float64).reshape(B, per_q), TAU)
+    g = s.grad.cpu().numpy().astype(np.float64).reshape(B, per_q)
+    assert np.all(np.abs(g - g64) <= 1e-4 * np.abs(g64).max(axis=1, keepdims=True))
+    # the backward kernel's own parity: the oracle takes the very upstream
+    # gradient the kernel received
     gq_gpu = q.grad.cpu().numpy()
     gd_gpu = D.grad.cpu().numpy()
     n_rows = n_band = 0

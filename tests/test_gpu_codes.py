@@ -57,6 +57,49 @@ def test_assign_codes_match_oracle(gem, n, k1):
     np.testing.assert_allclose(best.cpu().numpy(), sims[np.arange(n), codes], atol=EPS)
 
 
+@pytest.mark.parametrize("k1", [4099, 300])
+def test_assign_codes_tensor_core_path_equals_simt_path(gem, k1):
+    """From 16,384 rows the codes come from the tensor cores (three bf16
+    products per dot, six candidates per row, an FP32 recheck by the SIMT
+    kernel's own FMA chain, the SIMT kernel for the rows the candidates cannot
+    decide).  The same rows in slices of 8,192 take the SIMT kernel.  Codes and
+    best values must be bit-identical, on data with dense near-ties (centroids
+    that are perturbed rows of the data), exact ties (a duplicated centroid), a
+    NaN centroid, a zero row, a NaN row and a k1 that is not a multiple of the
+    128-centroid tile."""
+    rng = np.random.default_rng(k1)
+    n = 40_000
+    X = synth.draw_vectors(n, synth.centres(64, 8), 21).numpy().copy()
+    C = X[rng.choice(n, k1, replace=False)] + rng.normal(0, 0.01, (k1, 128)).astype(np.float32)
+    C /= np.linalg.norm(C, axis=1, keepdims=True)
+    C[k1 - 1] = C[5]                      # exact tie: index 5 must win
+    C[17] = np.nan                        # never chosen (a NaN dot counts as -inf)
+    X[100] = 0.0                          # every dot 0: code 0
+    X[200] = np.nan                       # every dot NaN: code 0
+    X[300] = C[5]                         # ties 5 / k1-1 exactly
+    Xd, Cd = torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda()
+    codes, best = gem.assign_codes(Xd, Cd, with_best=True)
+    parts = [gem.assign_codes(Xd[a:a + 8192], Cd, with_best=True) for a in range(0, n, 8192)]
+    codes_s = torch.cat([p[0] for p in parts]).cpu().numpy()
+    best_s = torch.cat([p[1] for p in parts]).cpu().numpy()
+    codes, best = codes.cpu().numpy(), best.cpu().numpy()
+    np.testing.assert_array_equal(codes, codes_s)
+    np.testing.assert_array_equal(best.view(np.uint32), best_s.view(np.uint32))
+    assert codes[100] == 0 and codes[200] == 0 and codes[300] == 5
+    assert codes.min() >= 0 and codes.max() < k1 and not np.any(codes == 17)
+    # against FP64 (the NaN centroid is never the nearest): exact outside the
+    # 2 * EPS band, within it a valid choice
+    ok = np.isfinite(X).all(axis=1) & (np.abs(X).sum(axis=1) > 0)
+    Cf = np.nan_to_num(C.astype(np.float64))
+    sims = X[ok].astype(np.float64) @ Cf.T
+    sims[:, 17] = -np.inf
+    top2 = np.sort(sims, axis=1)[:, -2:]
+    clear = top2[:, 1] - top2[:, 0] > 2 * EPS
+    np.testing.assert_array_equal(codes[ok][clear], np.argmax(sims, axis=1)[clear])
+    got = sims[np.arange(len(sims)), codes[ok]]
+    assert np.all(got >= sims.max(axis=1) - 2 * EPS)
+
+
 def test_assign_codes_centroid_maps_to_itself_and_ties_go_low(gem):
     rng = np.random.default_rng(3)
     C = _unit(rng, 300)
