@@ -606,6 +606,67 @@ gem_status gem_score_ids_noalloc(const gem_store* store, const float* q, const i
                                  const int64_t* cand_offsets, const int64_t* cand_ids, int64_t n_cands,
                                  float* scores, void* stream);
 
+/*
+ * Doc-range sharding (Eq. 2 over a database D split by set id into contiguous
+ * ranges, one store per shard: one per GPU, or several on one GPU).  The four
+ * calls below answer gem_search exactly -- bit for bit the same ids and scores
+ * as gem_search on the whole store with the same compute, rerank_depth and k --
+ * because every (query, set) score depends on the two sets alone:
+ *   1. gem_shard_first_pass on every shard (its top rerank_depth, global ids);
+ *   2. the lists gathered shard-major [n_shards][n_queries][rerank_depth] and
+ *      gem_merge_topk(k = rerank_depth): the whole store's rerank pool;
+ *   3. pool scores filled with -inf, then gem_shard_rerank on every shard (it
+ *      writes the entries it owns); across GPUs an element-wise max of the
+ *      shards' pool scores combines them;
+ *   4. gem_topk(pool scores, ids = pool ids, k).
+ *
+ * gem_shard_ranges: the shard boundaries, host only (no device work).
+ *   offsets_host   int64 [n_sets + 1] CSR offsets of the whole store (host)
+ *   bounds_host    int64 [n_shards + 1] (host, caller-owned): shard s owns the
+ *                  sets bounds[s] .. bounds[s+1]-1; bounds[0] = 0, bounds[n_shards]
+ *                  = n_sets; each boundary is the set boundary closest to
+ *                  s/n_shards of the vectors (balanced by vector count, not set
+ *                  count), every shard non-empty.
+ * Errors: GEM_ERR_INVALID (NULL, n_shards outside 1..n_sets, bad offsets).
+ */
+gem_status gem_shard_ranges(const int64_t* offsets_host, int64_t n_sets, int32_t n_shards, int64_t* bounds_host);
+
+/*
+ * gem_shard_first_pass: step 1 on the shard `store` (its sets are the global
+ * sets id_base .. id_base + n_sets - 1): the first pass of gem_search with
+ * `compute` (exact CH, or the qCH estimate for GEM_CODES) and its top `depth`
+ * per query by (score desc, id asc).  out_ids int64 [n_queries x depth] hold
+ * global set ids (-1 past the shard's size), out_scores float32 [n_queries x
+ * depth]; device, caller-owned.  Needs a workspace created with max_k > 0.
+ * Errors: as gem_search; GEM_ERR_INVALID for depth outside 1..4096 or id_base < 0.
+ */
+gem_status gem_shard_first_pass(const gem_store* store, gem_workspace* ws, const float* q, const int64_t* q_offsets,
+                                int32_t n_queries, int64_t n_q_rows, int32_t compute, int32_t depth, int64_t id_base,
+                                int64_t* out_ids, float* out_scores, void* stream);
+
+/*
+ * gem_shard_rerank: step 3 on one shard: for every entry of pool_ids (int64
+ * [n_queries x depth], global set ids, -1 = empty) that lies in the shard's
+ * range, pool_scores (float32, same shape) receives its exact FP32 CH (the
+ * arithmetic of gem_score_ids with GEM_F32); every other entry is left as it
+ * is.  Needs GEM_KEEP_F32 and a workspace with max_k > 0 and max_cands >=
+ * n_queries x depth.  Device buffers, caller-owned; asynchronous on `stream`.
+ */
+gem_status gem_shard_rerank(const gem_store* store, gem_workspace* ws, const float* q, const int64_t* q_offsets,
+                            int32_t n_queries, int64_t n_q_rows, const int64_t* pool_ids, int32_t depth,
+                            int64_t id_base, float* pool_scores, void* stream);
+
+/*
+ * gem_merge_topk: step 2: per row, the top k (score desc, id asc) of the union
+ * of n_lists lists laid out [n_lists][rows][k_in] (scores float32, ids int64;
+ * negative ids are empty slots).  out_ids int64 [rows x k], out_scores float32
+ * [rows x k] (may be NULL), padded with -1 / -inf.  Ids must be < 2^32 and, for
+ * an exact answer, distinct within a row.  Device buffers; asynchronous.
+ * Errors: GEM_ERR_INVALID (NULL, bad shape, k outside 1..4096).
+ */
+gem_status gem_merge_topk(const float* scores, const int64_t* ids, int32_t n_lists, int32_t rows, int32_t k_in,
+                          int32_t k, int64_t* out_ids, float* out_scores, void* stream);
+
 /* Number of kernels this library has enqueued since it was loaded (all
  * devices and threads); lets a caller count the library's launches in a region. */
 int64_t gem_kernel_launches(void);

@@ -51,6 +51,10 @@ SIGNATURES = {
     "gem_autotune_score_all": (C.c_int, [P, P, P, P, I32, I64, I32, P, C.c_char_p, P, P, P, P, P, P]),
     "gem_autotune_batch": (C.c_int, [P, I32, I32, I64, I32, I64, P, P, P, P, P, C.c_char_p, P, P, P, P, P]),
     "gem_score_ids_noalloc": (C.c_int, [P, P, P, I32, I64, I32, P, P, I64, P, P]),
+    "gem_shard_ranges": (C.c_int, [P, I64, I32, P]),
+    "gem_shard_first_pass": (C.c_int, [P, P, P, P, I32, I64, I32, I32, I64, P, P, P]),
+    "gem_shard_rerank": (C.c_int, [P, P, P, P, I32, I64, P, I32, I64, P, P]),
+    "gem_merge_topk": (C.c_int, [P, P, I32, I32, I32, I32, P, P, P]),
 }
 
 

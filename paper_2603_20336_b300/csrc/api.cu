@@ -588,7 +588,9 @@ gem_status gem_workspace_set_schedule(gem_workspace* w, int32_t m_tiles, int32_t
 
 // ----------------------------------------------------------------------------- scoring
 
-static gem_status check_query_args(const gem_store* s, gem_workspace* w, const float* q,
+}  // extern "C"
+
+gem_status gem::check_query_args(const gem_store* s, gem_workspace* w, const float* q,
                                    const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows) {
   if (!s || !w) return fail(GEM_ERR_INVALID, "store or workspace is NULL");
   if (w->store != s) return fail(GEM_ERR_INVALID, "workspace was created for another store");
@@ -597,6 +599,8 @@ static gem_status check_query_args(const gem_store* s, gem_workspace* w, const f
   if (n_q_rows < n_queries || n_q_rows > w->max_q_rows) return fail(GEM_ERR_INVALID, "n_q_rows out of range");
   return check_current_device(s->device);
 }
+
+extern "C" {
 
 static gem_status score_all_impl(const gem_store* s, gem_workspace* w, const float* q,
                                  const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
@@ -721,6 +725,23 @@ gem_status gem_topk(gem_workspace* w, const float* scores, const int64_t* row_of
                      reinterpret_cast<cudaStream_t>(stream));
 }
 
+}  // extern "C"
+
+gem_status gem::search_first_pass(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
+                             int32_t n_queries, int64_t n_q_rows, int32_t compute, cudaStream_t st) {
+  if (compute == GEM_CODES) {
+    // first pass by the quantized estimate (Algorithm 5 scores by qCH and
+    // reranks by exact CH): qsim of every stored set in the workspace's form
+    if (w->sim == GEM_SIM_L2) return fail(GEM_ERR_UNSUPPORTED, "qCH is defined for the inner-product Sim");
+    if (s->k1 == 0 || !w->d_tables)
+      return fail(GEM_ERR_STATE, "the codes pass needs a codebook before the workspace is created");
+    return launch_qch(s, w, q, q_offsets, n_queries, n_q_rows, nullptr, nullptr, w->d_scores, st);
+  }
+  return score_all_impl(s, w, q, q_offsets, n_queries, n_q_rows, compute, w->d_scores, st);
+}
+
+extern "C" {
+
 static gem_status search_impl(const gem_store* s, gem_workspace* w, const float* q,
                               const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
                               int32_t compute, int32_t rerank_depth, int32_t k, int64_t* out_ids,
@@ -731,17 +752,7 @@ static gem_status search_impl(const gem_store* s, gem_workspace* w, const float*
   if (rerank_depth > 0 && (int64_t)rerank_depth * n_queries > w->max_cands)
     return fail(GEM_ERR_INVALID, "n_queries * rerank_depth exceeds max_cands");
   if (rerank_depth > 0 && !s->d_f32) return fail(GEM_ERR_STATE, "the rerank needs the fp32 copy");
-  gem_status r;
-  if (compute == GEM_CODES) {
-    // first pass by the quantized estimate (Algorithm 5 scores by qCH and
-    // reranks by exact CH): qsim of every stored set in the workspace's form
-    if (w->sim == GEM_SIM_L2) return fail(GEM_ERR_UNSUPPORTED, "qCH is defined for the inner-product Sim");
-    if (s->k1 == 0 || !w->d_tables)
-      return fail(GEM_ERR_STATE, "the codes pass needs a codebook before the workspace is created");
-    r = launch_qch(s, w, q, q_offsets, n_queries, n_q_rows, nullptr, nullptr, w->d_scores, st);
-  } else {
-    r = score_all_impl(s, w, q, q_offsets, n_queries, n_q_rows, compute, w->d_scores, st);
-  }
+  gem_status r = search_first_pass(s, w, q, q_offsets, n_queries, n_q_rows, compute, st);
   if (r != GEM_OK) return r;
   if (rerank_depth == 0)
     return launch_topk(w, w->d_scores, nullptr, n_queries, s->n_sets, nullptr, k, out_ids, out_scores, st);

@@ -262,6 +262,18 @@ gem_status score_ids_noalloc(const gem_store* s, const float* q, const int64_t* 
                              int64_t n_q_rows, int32_t max_q_len, const int64_t* cand_offsets,
                              const int64_t* cand_ids, int64_t n_cands, float* scores, cudaStream_t st);
 
+// Host-side checks shared by the query calls (store, workspace, sizes, device).
+gem_status check_query_args(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
+                            int32_t n_queries, int64_t n_q_rows);
+// The first pass of gem_search into w->d_scores [n_queries x n_sets]: exact CH
+// in `compute` or, for GEM_CODES, the qCH estimate.
+gem_status search_first_pass(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
+                             int32_t n_queries, int64_t n_q_rows, int32_t compute, cudaStream_t st);
+// Per-row top-k of the union of n_lists lists laid out [n_lists][rows][k_in]
+// (scores and ids; negative ids are empty slots).
+gem_status launch_merge_topk(const float* scores, const int64_t* ids, int32_t n_lists, int32_t rows, int32_t k_in,
+                             int32_t k, int64_t* out_ids, float* out_scores, int n_sm, cudaStream_t st);
+
 // Candidate-buffer entries per row the threshold top-k needs for k <= max_k.
 int topk_candidate_cap(int max_k);
 

@@ -82,6 +82,23 @@ struct KeyView {
   }
 };
 
+// Row r of the union of n_lists lists laid out [list][rows][k_in]: element t
+// is entry t % k_in of list t / k_in (negative ids are empty slots).
+struct SegView {
+  const float* s;
+  const int64_t* ids;
+  int64_t n;          // n_lists * k_in
+  int64_t list_stride;  // rows * k_in
+  int k_in;
+  __device__ __forceinline__ bool key(int64_t t, uint64_t& k) const {
+    const int64_t idx = (t / k_in) * list_stride + (t % k_in);
+    const int64_t id = ids[idx];
+    if (id < 0) return false;
+    k = make_key(s[idx], id);
+    return true;
+  }
+};
+
 struct SelectSmem {
   int hist[256];
   int suffix[257];
@@ -288,7 +305,11 @@ topk_sample_kernel(const float* __restrict__ scores, int rows, int64_t cols, con
 
 // Threshold path, step 2: one streaming pass; every valid key >= thr[row] is
 // appended to the row's candidate buffer (cap entries; the counter keeps
-// counting past it).  Work items are (row, 4,096-element chunk).
+// counting past it).  Work items are (row, 4,096-element chunk).  The test is a
+// float comparison with the threshold's score (keys order like their scores,
+// and -0 equals +0 in both); only an element whose score equals it compares
+// ids.  Each thread counts its picks, the warp scans the counts and takes one
+// slot range with a single atomic.
 __global__ void __launch_bounds__(kFilterThreads)
 topk_filter_kernel(const float* __restrict__ scores, int rows, int64_t cols, const int64_t* __restrict__ ids,
                    const uint32_t* __restrict__ dead, int64_t n_sets, const unsigned long long* __restrict__ thr,
@@ -296,13 +317,15 @@ topk_filter_kernel(const float* __restrict__ scores, int rows, int64_t cols, con
   const int64_t cpr = (cols + kFilterChunk - 1) / kFilterChunk;
   const int64_t items = (int64_t)rows * cpr;
   const int lane = threadIdx.x & 31;
-  const unsigned lt_mask = (1u << lane) - 1u;
   for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
     const int r = (int)(item / cpr);
     const int64_t c0 = (item % cpr) * kFilterChunk;
     const float* s = scores + (int64_t)r * cols;
     const int64_t* id_row = ids ? ids + (int64_t)r * cols : nullptr;
     const unsigned long long T = thr[r];
+    const bool take_all = (T == 0ull);
+    const float fT = take_all ? 0.f : key_score((uint32_t)(T >> 32));
+    const uint32_t T_lo = (uint32_t)T;
     float v[kFilterPerThread];
     // four coalesced 16-byte loads per thread, all in flight before use
 #pragma unroll
@@ -316,32 +339,45 @@ topk_filter_kernel(const float* __restrict__ scores, int rows, int64_t cols, con
         for (int e = 0; e < 4; ++e) v[4 * j + e] = (t + e < cols) ? s[t + e] : 0.f;
       }
     }
+    uint32_t picks = 0;  // bit 4 j + e: element (j, e) is a candidate
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int64_t t = c0 + ((int64_t)j * kFilterThreads + threadIdx.x) * 4 + e;
-        bool pick = false;
-        uint64_t key = 0;
-        if (t < cols) {
+        const float sv = v[4 * j + e];
+        bool p = take_all || sv >= fT;
+        if (p && t < cols && (id_row || dead || (!take_all && sv == fT))) {
           const int64_t id = id_row ? id_row[t] : t;
-          if (id >= 0 && !is_dead(dead, n_sets, id)) {
-            key = make_key(v[4 * j + e], id);
-            pick = key >= T;
-          }
+          p = id >= 0 && !is_dead(dead, n_sets, id) &&
+              (take_all || sv > fT || (0xFFFFFFFFu - (uint32_t)id) >= T_lo);
         }
-        const unsigned m = __ballot_sync(0xffffffffu, pick);
-        if (m) {
-          const int leader = __ffs(m) - 1;
-          unsigned base = 0;
-          if (lane == leader) base = atomicAdd(cnt + r, (unsigned)__popc(m));
-          base = __shfl_sync(0xffffffffu, base, leader);
-          if (pick) {
-            const unsigned slot = base + __popc(m & lt_mask);
-            if (slot < (unsigned)cap) cand[(int64_t)r * cap + slot] = key;
-          }
-        }
+        picks |= (p && t < cols) ? (1u << (4 * j + e)) : 0u;
       }
+    }
+    // warp: inclusive scan of the pick counts, one atomic for the warp's slots
+    const unsigned c = __popc(picks);
+    unsigned incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) continue;  // warp-uniform
+    unsigned base = 0;
+    if (lane == 31) base = atomicAdd(cnt + r, total);
+    base = __shfl_sync(0xffffffffu, base, 31) + incl - c;
+    while (picks) {
+      const int b = __ffs(picks) - 1;
+      picks &= picks - 1;
+      const int64_t t = c0 + ((int64_t)(b >> 2) * kFilterThreads + threadIdx.x) * 4 + (b & 3);
+      const int64_t id = id_row ? id_row[t] : t;
+      float sv = 0.f;  // v[b] by selects (no dynamic register indexing)
+#pragma unroll
+      for (int i = 0; i < kFilterPerThread; ++i) sv = (i == b) ? v[i] : sv;
+      if (base < (unsigned)cap) cand[(int64_t)r * cap + base] = make_key(sv, id);
+      ++base;
     }
   }
 }
@@ -374,6 +410,23 @@ topk_select_kernel(const float* __restrict__ scores, int rows, int64_t cols, con
   }
 }
 
+// Merge of per-shard top lists: one CTA per row over the row's n_lists * k_in entries.
+__global__ void __launch_bounds__(kTopkThreads)
+merge_topk_kernel(const float* __restrict__ scores, const int64_t* __restrict__ ids, int n_lists, int rows,
+                  int k_in, int k, int sort_n, int64_t* __restrict__ out_ids, float* __restrict__ out_scores) {
+  extern __shared__ uint64_t sel[];  // [sort_n]
+  __shared__ SelectSmem sm;
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    SegView v;
+    v.s = scores + (int64_t)r * k_in;
+    v.ids = ids + (int64_t)r * k_in;
+    v.n = (int64_t)n_lists * k_in;
+    v.list_stride = (int64_t)rows * k_in;
+    v.k_in = k_in;
+    select_row(v, true, k, sort_n, sel, sm, out_ids + (int64_t)r * k, out_scores ? out_scores + (int64_t)r * k : nullptr);
+  }
+}
+
 int sort_size(int k) {
   int n = 1;
   while (n < k) n <<= 1;
@@ -381,6 +434,19 @@ int sort_size(int k) {
 }
 
 }  // namespace
+
+gem_status launch_merge_topk(const float* scores, const int64_t* ids, int32_t n_lists, int32_t rows, int32_t k_in,
+                             int32_t k, int64_t* out_ids, float* out_scores, int n_sm, cudaStream_t st) {
+  if (rows == 0) return GEM_OK;
+  const int sort_n = sort_size(k);
+  const size_t smem = sizeof(uint64_t) * sort_n;
+  GEM_CUDA_TRY(cudaFuncSetAttribute(merge_topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  merge_topk_kernel<<<std::min(rows, n_sm * 4), kTopkThreads, smem, st>>>(scores, ids, n_lists, rows, k_in, k, sort_n,
+                                                                          out_ids, out_scores);
+  GEM_CUDA_TRY(cudaGetLastError());
+  note_launches(1);
+  return GEM_OK;
+}
 
 int topk_candidate_cap(int max_k) { return max_k > 0 ? 2 * (4 * max_k + 256) : 0; }
 

@@ -112,6 +112,9 @@ def test_finite_differences_4x4(gem):
 # value, so two candidates whose FP64 dots differ by more than twice that are
 # ordered the same way on both sides.
 ARGMAX_BAND = 2 * 128 * 2.0 ** -24 * (1 + 2.0 ** -8) ** 2
+# Products below FP32's normal range: FP32 atomic adds flush subnormal values to
+# zero, so each of at most 64 summed terms may lose up to 2^-126.
+FTZ_FLOOR = 64 * 2.0 ** -126
 
 
 def test_full_size_gradient_matches_oracle(gem):
@@ -184,8 +187,8 @@ def test_full_size_gradient_matches_oracle(gem):
             gq += g[b, n] * dq
             gq_l1 += abs(g[b, n]) * np.abs(dq)
             err = np.abs(gd_gpu[dr] - g[b, n] * dp)
-            assert np.all(err <= 1e-5 * abs(g[b, n]) * dp_l1), (t, err.max())
+            assert np.all(err <= 1e-5 * abs(g[b, n]) * dp_l1 + FTZ_FLOOR), (t, err.max())
         err = np.abs(gq_gpu[qr] - gq)
-        assert np.all(err <= 1e-5 * gq_l1), (b, err.max())
+        assert np.all(err <= 1e-5 * gq_l1 + FTZ_FLOOR), (b, err.max())
     assert n_rows == 64 * per_q * 32
     assert n_band <= 0.01 * n_rows, n_band
