@@ -493,11 +493,16 @@ gem_status gem_search_host(const gem_store* store, gem_workspace* ws, const floa
  * accumulation; GEM_F32 uses the FP32 values.  scores float32 [n_pairs];
  * argmax int32 [n_pairs * max_q_len].  ws (may be NULL) receives device-side
  * errors (an id outside [0, n_docs) scores NaN).
+ * GEM_BF16 with max_q_len <= 128 runs on the tensor cores: the rows are first
+ * rounded into stream-ordered scratch (2 bytes per component of q and docs,
+ * freed at the end of the call), the sum over i is taken in a fixed order (32-row
+ * butterflies, then in ascending blocks of 32); otherwise an FP32 SIMT kernel
+ * with a Kahan sum in ascending i runs.
  */
-gem_status gem_maxsim_fwd(const float* q, const int64_t* q_offsets, int32_t n_queries, const float* docs,
-                          const int64_t* doc_offsets, int64_t n_docs, const int64_t* pair_offsets,
-                          const int64_t* pair_ids, int64_t n_pairs, int32_t max_q_len, int32_t compute,
-                          float* scores, int32_t* argmax, gem_workspace* ws, void* stream);
+gem_status gem_maxsim_fwd(const float* q, const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
+                          const float* docs, const int64_t* doc_offsets, int64_t n_docs, int64_t n_doc_rows,
+                          const int64_t* pair_offsets, const int64_t* pair_ids, int64_t n_pairs, int32_t max_q_len,
+                          int32_t compute, float* scores, int32_t* argmax, gem_workspace* ws, void* stream);
 
 /*
  * Backward of gem_maxsim_fwd for upstream gradients grad_scores [n_pairs]:

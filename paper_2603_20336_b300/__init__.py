@@ -481,8 +481,8 @@ def maxsim_fwd(q, q_offsets, docs, doc_offsets, pair_offsets, pair_ids, compute=
     n = pid.numel()
     scores = torch.empty(n, dtype=torch.float32, device=q.device)
     argmax = torch.empty((n, max_q_len), dtype=torch.int32, device=q.device)
-    _check(lib.gem_maxsim_fwd(_ptr(q), _ptr(qo), B, _ptr(docs), _ptr(do), do.numel() - 1, _ptr(po), _ptr(pid), n,
-                              max_q_len, _dtype_code(compute), _ptr(scores), _ptr(argmax),
+    _check(lib.gem_maxsim_fwd(_ptr(q), _ptr(qo), B, q.shape[0], _ptr(docs), _ptr(do), do.numel() - 1, docs.shape[0],
+                              _ptr(po), _ptr(pid), n, max_q_len, _dtype_code(compute), _ptr(scores), _ptr(argmax),
                               ws.handle if ws is not None else None, _stream(stream)))
     return scores, argmax
 

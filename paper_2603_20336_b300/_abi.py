@@ -41,7 +41,7 @@ SIGNATURES = {
     "gem_search": (C.c_int, [P, P, P, P, I32, I64, I32, I32, I32, P, P, P]),
     "gem_search_host": (C.c_int, [P, P, P, P, I32, I32, I32, I32, P, P, P]),
     "gem_stream_status": (C.c_int, [P, P]),
-    "gem_maxsim_fwd": (C.c_int, [P, P, I32, P, P, I64, P, P, I64, I32, I32, P, P, P, P]),
+    "gem_maxsim_fwd": (C.c_int, [P, P, I32, I64, P, P, I64, I64, P, P, I64, I32, I32, P, P, P, P]),
     "gem_maxsim_bwd": (C.c_int, [P, P, I32, P, P, I64, I64, P, P, I64, P, I32, P, P, P, P]),
     "gem_batch_create": (C.c_int, [P, I32, I32, I64, I32, I64, I32, I32, P, P, P, P, P, C.POINTER(P)]),
     "gem_batch_run": (C.c_int, [P, I32, I64, I64, I32, P]),

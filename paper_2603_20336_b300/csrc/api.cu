@@ -813,19 +813,24 @@ gem_status gem_search_host(const gem_store* s, gem_workspace* w, const float* q_
   return GEM_OK;
 }
 
-gem_status gem_maxsim_fwd(const float* q, const int64_t* q_offsets, int32_t n_queries, const float* docs,
-                          const int64_t* doc_offsets, int64_t n_docs, const int64_t* pair_offsets,
-                          const int64_t* pair_ids, int64_t n_pairs, int32_t max_q_len, int32_t compute,
-                          float* scores, int32_t* argmax, gem_workspace* ws, void* stream) {
+gem_status gem_maxsim_fwd(const float* q, const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
+                          const float* docs, const int64_t* doc_offsets, int64_t n_docs, int64_t n_doc_rows,
+                          const int64_t* pair_offsets, const int64_t* pair_ids, int64_t n_pairs, int32_t max_q_len,
+                          int32_t compute, float* scores, int32_t* argmax, gem_workspace* ws, void* stream) {
   if (!q || !q_offsets || !docs || !doc_offsets || !pair_offsets || !scores || !argmax || (n_pairs > 0 && !pair_ids))
     return fail(GEM_ERR_INVALID, "NULL argument");
-  if (n_queries < 1 || n_docs < 1 || n_pairs < 0) return fail(GEM_ERR_INVALID, "bad sizes");
+  if (n_queries < 1 || n_docs < 1 || n_pairs < 0 || n_q_rows < n_queries || n_doc_rows < n_docs)
+    return fail(GEM_ERR_INVALID, "bad sizes");
   if (max_q_len < 1 || max_q_len > 256) return fail(GEM_ERR_INVALID, "max_q_len must be 1..256");
   if (compute != GEM_F32 && compute != GEM_BF16) return fail(GEM_ERR_INVALID, "compute must be GEM_F32 or GEM_BF16");
   if (n_pairs == 0) return GEM_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (compute == GEM_BF16 && max_q_len <= 128)
+    return launch_maxsim_fwd_tc(q, q_offsets, n_queries, n_q_rows, docs, doc_offsets, n_docs, n_doc_rows,
+                                pair_offsets, pair_ids, n_pairs, max_q_len, scores, argmax,
+                                ws ? ws->d_status : nullptr, current_sm_count(), st);
   return launch_maxsim_fwd(q, q_offsets, n_queries, docs, doc_offsets, n_docs, pair_offsets, pair_ids, max_q_len,
-                           compute == GEM_BF16, scores, argmax, ws ? ws->d_status : nullptr, current_sm_count(),
-                           reinterpret_cast<cudaStream_t>(stream));
+                           compute == GEM_BF16, scores, argmax, ws ? ws->d_status : nullptr, current_sm_count(), st);
 }
 
 gem_status gem_maxsim_bwd(const float* q, const int64_t* q_offsets, int32_t n_queries, const float* docs,

@@ -237,6 +237,10 @@ gem_status launch_maxsim_fwd(const float* q, const int64_t* q_off, int32_t n_que
                              const int64_t* d_off, int64_t n_docs, const int64_t* pair_off,
                              const int64_t* pair_ids, int32_t max_q_len, int bf16, float* scores,
                              int32_t* argmax, int* status, int n_sm, cudaStream_t st);
+gem_status launch_maxsim_fwd_tc(const float* q, const int64_t* q_off, int32_t n_queries, int64_t n_q_rows,
+                                const float* docs, const int64_t* d_off, int64_t n_docs, int64_t n_doc_rows,
+                                const int64_t* pair_off, const int64_t* pair_ids, int64_t n_pairs, int32_t max_q_len,
+                                float* scores, int32_t* argmax, int* status, int n_sm, cudaStream_t st);
 gem_status launch_maxsim_bwd(const float* q, const int64_t* q_off, int32_t n_queries, const float* docs,
                              const int64_t* d_off, int64_t n_docs, int64_t n_doc_rows, const int64_t* pair_off,
                              const int64_t* pair_ids, int64_t n_pairs, const int32_t* argmax, int32_t max_q_len,

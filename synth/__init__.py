@@ -12,9 +12,11 @@ its centre uniformly at random, then it is L2-normalised in FP64 and stored FP32
 Queries are drawn from the same mixture with a different seed stream.
 
 Randomness: set lengths, centre choices and candidate lists come from numpy's
-PCG64 generator; the Gaussian noise comes from torch's generator on the device the
-vectors are built on (CPU for small workloads, CUDA for corpus-sized ones), so a
-given (workload, seed, device type) always yields the same bytes.
+PCG64 generator.  The noise comes either from torch's generator on the device the
+vectors are built on (draw_vectors: a given (workload, seed, device type) always
+yields the same bytes), or, for the text-corpus workload, from a counter-based
+SplitMix64 hash with an Irwin-Hall(12) variate (draw_vectors_portable: the same
+bytes on every device).
 """
 from __future__ import annotations
 
@@ -80,6 +82,66 @@ def draw_vectors(n: int, cents: np.ndarray, seed: int, device="cpu",
     return out
 
 
+# SplitMix64 constants (Steele, Lea and Flood, "Fast splittable pseudorandom
+# number generators", 2014), as signed 64-bit integers
+_SM_GAMMA = 0x9E3779B97F4A7C15 - (1 << 64)
+_SM_M1 = 0xBF58476D1CE4E5B9 - (1 << 64)
+_SM_M2 = 0x94D049BB133111EB - (1 << 64)
+
+
+def _srl(x: torch.Tensor, s: int) -> torch.Tensor:
+    """Logical right shift of int64 bit patterns."""
+    return (x >> s) & ((1 << (64 - s)) - 1)
+
+
+def _splitmix64(state: torch.Tensor) -> torch.Tensor:
+    """SplitMix64 output for each 64-bit state (wrapping int64 arithmetic)."""
+    z = state + _SM_GAMMA
+    z = (z ^ _srl(z, 30)) * _SM_M1
+    z = (z ^ _srl(z, 27)) * _SM_M2
+    return z ^ _srl(z, 31)
+
+
+def draw_vectors_portable(n: int, cents: np.ndarray, seed: int, device="cpu", noise: float = NOISE,
+                          chunk: int = 1 << 18) -> torch.Tensor:
+    """n unit-norm float32 vectors of the mixture, bit-identical on every device.
+
+    Each vector picks a centre uniformly (numpy PCG64).  The noise of coordinate
+    k of vector v is an Irwin-Hall variate: the sum of twelve 16-bit uniforms
+    taken from three SplitMix64 outputs of the counter 3 (128 v + k) + i, at the
+    bins' midpoints, minus 6 -- mean 0, variance 1, the textbook sum-of-twelve
+    approximation of N(0, 1), tails cut at +-6.  Everything after the integer
+    hash is exact or one correctly rounded FP64 operation in a fixed order (the
+    squared norm is summed by a fixed pairwise tree), so CPU and GPU give the
+    same bytes."""
+    rng = np.random.default_rng([seed, 0xA5])
+    which = rng.integers(0, len(cents), size=n)
+    d = cents.shape[1]
+    assert d & (d - 1) == 0, "the pairwise norm tree needs a power-of-two dimension"
+    dev = torch.device(device)
+    cent_t = torch.from_numpy(cents).to(dev)
+    key = (int(seed) * 0x2545F4914F6CDD1D) % (1 << 64)
+    key = key - (1 << 64) if key >= (1 << 63) else key
+    out = torch.empty((n, d), dtype=torch.float32, device=dev)
+    k3 = torch.arange(d * 3, dtype=torch.int64, device=dev)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        ctr = torch.arange(s, e, dtype=torch.int64, device=dev)[:, None] * (3 * d) + k3[None, :]
+        h = _splitmix64(ctr + key).view(e - s, d, 3)
+        acc = torch.zeros((e - s, d), dtype=torch.int64, device=dev)
+        for sh in (0, 16, 32, 48):
+            acc += _srl(h, sh).bitwise_and(0xFFFF).sum(dim=2)
+        z = (acc.to(torch.float64) + 6.0) / 65536.0 - 6.0
+        x = cent_t.index_select(0, torch.from_numpy(which[s:e]).to(dev)) + noise * z
+        sq = x * x
+        w = d
+        while w > 1:                       # fixed pairwise tree over the coordinates
+            w //= 2
+            sq = sq[:, :w] + sq[:, w:2 * w]
+        out[s:e].copy_(x / torch.sqrt(sq))
+    return out
+
+
 def lengths_uniform(n: int, lo: int, hi: int, seed: int) -> np.ndarray:
     """Set lengths i.i.d. uniform on the integers lo..hi (inclusive)."""
     rng = np.random.default_rng([seed, 0x1E])
@@ -94,10 +156,11 @@ def lengths_lognormal(n: int, mean: float, sigma: float, lo: int, hi: int, seed:
     return np.rint(np.clip(x, lo, hi)).astype(np.int64)
 
 
-def vector_sets(lengths: np.ndarray, cents: np.ndarray, seed: int, device="cpu") -> VectorSets:
+def vector_sets(lengths: np.ndarray, cents: np.ndarray, seed: int, device="cpu", portable: bool = False) -> VectorSets:
     lengths = np.asarray(lengths, dtype=np.int64)
     off = _offsets(lengths)
-    return VectorSets(draw_vectors(int(off[-1]), cents, seed, device), off)
+    draw = draw_vectors_portable if portable else draw_vectors
+    return VectorSets(draw(int(off[-1]), cents, seed, device), off)
 
 
 def candidate_lists(n_queries: int, n_docs: int, len_lo: int, len_hi: int, shared_frac: float,
@@ -176,11 +239,13 @@ def exact_fp32(seed: int = 1235, n_sets: int = 2000, n_queries: int = 10, m_q: i
 
 
 def text_corpus(seed: int = 1236, n_sets: int = 500_000, n_queries: int = 1000, m_q: int = 32,
-                n_centres: int = 4096, device="cpu") -> Workload:
-    """Text-corpus shape: lognormal lengths (mean 70, sigma 0.5, clipped 20..180), 4,096 centres."""
+                n_centres: int = 4096, device="cpu", portable: bool = True) -> Workload:
+    """Text-corpus shape: lognormal lengths (mean 70, sigma 0.5, clipped 20..180), 4,096 centres.
+    portable (default): the device-independent noise of draw_vectors_portable, so
+    the FP64 ground truth of the full workload can be computed on any host."""
     cents = centres(n_centres, seed)
-    docs = vector_sets(lengths_lognormal(n_sets, 70.0, 0.5, 20, 180, seed), cents, seed, device)
-    qs = vector_sets(np.full(n_queries, m_q, np.int64), cents, seed + 7919, device)
+    docs = vector_sets(lengths_lognormal(n_sets, 70.0, 0.5, 20, 180, seed), cents, seed, device, portable)
+    qs = vector_sets(np.full(n_queries, m_q, np.int64), cents, seed + 7919, device, portable)
     return Workload("text-500k", seed, docs, qs, {"rerank": 1000, "k": 100})
 
 

@@ -66,6 +66,55 @@ def test_forward_scores_and_argmax_match_oracle(gem):
             np.testing.assert_array_equal(am[t, :len(Qb)][clear], np.argmax(sims, axis=1)[clear])
 
 
+def test_tensor_core_forward_agrees_with_simt_forward(gem):
+    """GEM_BF16 with max_q_len <= 128 runs on the tensor cores, a larger
+    max_q_len on the SIMT kernel; both decide on the same bf16-rounded inputs.
+    Queries of 1..128 vectors, sets of 1..700 vectors (several 256-row tiles),
+    ragged pair lists (a query with none), an out-of-range id: argmax equal
+    wherever the FP64 top-2 margin exceeds the FP32 dot bound, scores within
+    1e-5 of the L1 of their terms, the bad id scored NaN with GEM_ERR_BOUNDS."""
+    rng = np.random.default_rng(8)
+    qlens = np.array([1, 32, 128, 77, 5, 64])
+    dlens = rng.integers(1, 700, size=40)
+    dlens[:4] = [1, 256, 257, 700]
+    cents = synth.centres(64, 4)
+    qs = synth.vector_sets(qlens, cents, 31)
+    ds = synth.vector_sets(dlens, cents, 32)
+    counts = np.array([7, 0, 12, 9, 3, 10])
+    po = torch.from_numpy(np.concatenate([[0], np.cumsum(counts)]).astype(np.int64))
+    pid = torch.from_numpy(rng.integers(0, 40, size=int(counts.sum())).astype(np.int64))
+    pid[5] = 40                                            # out of range
+    st = gem.Store(ds.vecs.cuda(), ds.offsets, keep=("f32",))
+    ws = gem.Workspace(st, max_queries=1, max_q_rows=1)     # for its status word
+    q, qo = qs.vecs.cuda(), torch.from_numpy(qs.offsets).cuda()
+    D, do = ds.vecs.cuda(), torch.from_numpy(ds.offsets).cuda()
+    s_tc, am_tc = gem.maxsim_fwd(q, qo, D, do, po.cuda(), pid.cuda(), "bf16", max_q_len=128, ws=ws)
+    assert ws.status() == 7
+    s_sm, am_sm = gem.maxsim_fwd(q, qo, D, do, po.cuda(), pid.cuda(), "bf16", max_q_len=160, ws=ws)
+    assert ws.status() == 7
+    s_tc, am_tc, s_sm, am_sm = s_tc.cpu().numpy(), am_tc.cpu().numpy(), s_sm.cpu().numpy(), am_sm.cpu().numpy()
+    assert np.isnan(s_tc[5]) and np.isnan(s_sm[5])
+    Qr = oracle.bf16_round(qs.vecs.numpy()).astype(np.float64)
+    Dr = oracle.bf16_round(ds.vecs.numpy()).astype(np.float64)
+    band = 2 * 128 * 2.0 ** -24 * (1 + 2.0 ** -8) ** 2
+    for b in range(len(qlens)):
+        for t in range(int(po[b]), int(po[b + 1])):
+            d = int(pid[t])
+            if d >= 40:
+                continue
+            sims = Qr[qs.offsets[b]:qs.offsets[b + 1]] @ Dr[ds.offsets[d]:ds.offsets[d + 1]].T
+            m = qlens[b]
+            srt = np.sort(sims, axis=1)
+            clear = (srt[:, -1] - srt[:, -2] > band) if sims.shape[1] > 1 else np.ones(m, bool)
+            want = np.argmax(sims, axis=1)
+            np.testing.assert_array_equal(am_tc[t, :m][clear], want[clear])
+            np.testing.assert_array_equal(am_sm[t, :m][clear], want[clear])
+            top = sims.max(axis=1)
+            assert np.all(sims[np.arange(m), am_tc[t, :m]] >= top - band)
+            l1 = np.abs(top).sum()
+            assert abs(s_tc[t] - top.sum()) <= 1e-5 * l1 and abs(s_sm[t] - top.sum()) <= 1e-5 * l1
+
+
 def test_finite_differences_4x4(gem):
     """4 queries x 4 sets, FP32 forward; margins kept away from argmax switches."""
     rng = np.random.default_rng(21)
