@@ -135,17 +135,28 @@ def _barrier(dist):
     torch.cuda.synchronize()
 
 
+def _cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(docs_host: torch.Tensor, offsets: np.ndarray, q_host: torch.Tensor, q_offsets: np.ndarray,
-                 n_queries: int, k: int, n_docs=None):
+                 n_queries: int, k: int, n_docs=None, one_thread: bool = False):
     """The FP64 oracle (exact CH of every pair + exact top-k), timed on host cores
     for the first n_queries queries against the first n_docs sets (all by default).
     Returns the timing and the oracle's top-k (ids, scores) of those queries: the
-    ground truth for recall."""
+    ground truth for recall.  one_thread: also time one query on a single thread."""
     import oracle
     try:
-        from threadpoolctl import threadpool_info
+        from threadpoolctl import threadpool_info, threadpool_limits
         cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
     except Exception:
+        threadpool_limits = None
         cores = os.cpu_count()
     n_docs = len(offsets) - 1 if n_docs is None else n_docs
     off = offsets[: n_docs + 1]
@@ -157,9 +168,44 @@ def cpu_baseline(docs_host: torch.Tensor, offsets: np.ndarray, q_host: torch.Ten
     S = oracle.score_all(Q, qo, X, off)
     truth = [oracle.topk(S[b], k) for b in range(n_queries)]
     dt = time.perf_counter() - t0
-    return {"value": n_queries * n_docs / dt, "unit": "doc-sets/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n_queries} queries x {n_docs} sets (FP64 numpy, exact CH + top-{k})",
-            "seconds": dt}, truth
+    res = {"value": n_queries * n_docs / dt, "unit": "doc-sets/s", "cores": cores, "kind": "oracle",
+           "sample": f"{n_queries} queries x {n_docs} sets (FP64 numpy, exact CH + top-{k})",
+           "seconds": dt, "cpu_model": _cpu_model(), "logical_cpus": os.cpu_count()}
+    if one_thread and threadpool_limits is not None:
+        with threadpool_limits(limits=1):
+            t1 = time.perf_counter()
+            S1 = oracle.score_all(Q[: int(qo[1])], qo[:2], X, off)
+            oracle.topk(S1[0], k)
+            d1 = time.perf_counter() - t1
+        res["one_thread"] = {"value": n_docs / d1, "unit": "doc-sets/s", "sample": f"1 query x {n_docs} sets",
+                             "seconds": d1}
+    return res, truth
+
+
+TRUTH_FILE = os.path.join(ROOT, "tests", "golden", "text500k_truth.npz")
+
+
+def load_truth(w):
+    """The stored exact FP64 top-100 of all text-corpus queries, if it was
+    computed on exactly this data (fingerprint), else None."""
+    if not os.path.exists(TRUTH_FILE):
+        return None, "no stored ground truth"
+    d = np.load(TRUTH_FILE)
+    fp = synth.fingerprint(w.docs, w.queries)
+    if str(d["fingerprint"]) != fp or d["ids"].shape[0] != w.queries.n_sets:
+        return None, "stored ground truth was computed on other data (fingerprint differs)"
+    return (d["ids"].astype(np.int64), d["scores"]), "stored"
+
+
+def recall_vs_truth(found: np.ndarray, truth) -> dict:
+    """Mean |found_top100 ∩ exact_top100| / 100 over all queries; boundary_ties
+    counts queries whose exact 100th and 101st scores tie within 1e-6 (there the
+    exact top-100 itself is ambiguous)."""
+    ids, sc = truth
+    r = [len(set(found[b, :100].tolist()) & set(ids[b].tolist())) / 100.0 for b in range(ids.shape[0])]
+    ties = int(np.sum(np.abs(sc[:, 99] - sc[:, 100]) <= 1e-6 * np.maximum(1.0, np.abs(sc[:, 99]))))
+    return {"recall": float(np.mean(r)), "min": float(np.min(r)), "queries": int(ids.shape[0]),
+            "boundary_ties": ties}
 
 
 def _recall(found: np.ndarray, truth):
@@ -183,8 +229,8 @@ def _time(fn, reps=3, st=None):
     return e0.elapsed_time(e1) / reps
 
 
-def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, only=None, qch_k1="",
-                 schedule=None):
+def extra_stages(gem, store, ws, w, q, qo, R, K, recall, stages, dev, step_ms, only=None, qch_k1="",
+                 schedule=None, bp=None):
     """Every hot-path row measured on its own (after the headline timing)."""
     B = qo.numel() - 1
     rows = q.shape[0]
@@ -204,13 +250,14 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, on
         ms = _time(lambda: gem.score_all(store, ws, q, qo, "fp8", out=out))
         ids, _ = gem.search(store, ws, q, qo, "fp8", rerank_depth=R, k=K)
         return {"ms": ms, "pairs_per_s": B * store.n_sets / (ms * 1e-3), "tflops_equiv": flops / ms / 1e9,
-                "schedule": ch, "recall_at_100_after_rerank": _recall(ids.cpu().numpy(), truth)}
+                "schedule": ch, "recall_at_100_after_rerank": recall(ids.cpu().numpy())}
 
     def fp32():
         ms = _time(lambda: gem.score_all(store, ws, q, qo, "f32", out=out), reps=1)
         ids, _ = gem.search(store, ws, q, qo, "f32", rerank_depth=R, k=K)
         return {"ms": ms, "pairs_per_s": B * store.n_sets / (ms * 1e-3), "tflops": flops / ms / 1e9,
-                "recall_at_100": _recall(ids.cpu().numpy(), truth),
+                "frac_of_builder_fp32_peak": (flops / ms / 1e9) / bp["fp32_tflops"] if bp else None,
+                "recall_at_100": recall(ids.cpu().numpy()),
                 "bf16_rerank_step_speedup_vs_fp32_exhaustive": ms / step_ms}
 
     def qch():
@@ -219,7 +266,7 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, on
         V = store.n_vecs
         k1_formula = 1 << int(np.floor(np.log2(16.0 * np.sqrt(V))))
         sizes = [int(x) for x in qch_k1.split(",")] if qch_k1 else [k1_formula]
-        nq = min(B, 64)
+        nq = B if recall.full else min(B, 64)
         runs = []
         for k1 in sizes:
             t0 = time.perf_counter()
@@ -238,10 +285,13 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, on
                 ids, _ = gem.search(store, ws2, qn, qon, "codes", rerank_depth=R, k=K)
                 est_top, _ = gem.search(store, ws2, qn, qon, "codes", rerank_depth=0, k=K)
                 assert ws2.status() == 0
+                gather_gbs = nq * V * 128 / (ms * 1e-3) / 1e9   # one 128-byte table row per stored vector
                 runs.append({"k1": k1, "form": form, "codebook_and_codes_s": t_build, "ms": ms,
                              "pairs_per_s": nq * store.n_sets / (ms * 1e-3), "search_ms": ms_s,
-                             "recall_at_100_after_rerank": _recall(ids.cpu().numpy(), truth[:nq]),
-                             "recall_at_100_of_the_estimate": _recall(est_top.cpu().numpy(), truth[:nq])})
+                             "table_gather_gbs": gather_gbs,
+                             "frac_of_builder_l2_gather_peak": gather_gbs / bp["l2_gather_gbs"] if bp else None,
+                             "recall_at_100_after_rerank": recall(ids.cpu().numpy()),
+                             "recall_at_100_of_the_estimate": recall(est_top.cpu().numpy())})
             ws2.close()
         head = runs[0]
         return {"k1": head["k1"], "codebook_and_codes_s": head["codebook_and_codes_s"], "queries": nq,
@@ -383,6 +433,10 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, on
         e1.record()
         e1.synchronize()
         ms = e0.elapsed_time(e1) / rounds
+        # flop of one round: 2 m_q m_p 128 per (query, candidate) pair (every round
+        # has the same lengths: its ids are a bijection of round 0's)
+        dl = np.diff(w.docs.offsets)
+        fl = 2.0 * 128 * float(np.sum(np.repeat(np.diff(qs.offsets), np.diff(co)) * dl[ci0]))
         # bit-match of the last round with the per-query path on 8 queries
         got = bt.scores[: len(ci0)].clone()
         ws3 = gem.Workspace(store, max_queries=1, max_q_rows=64, max_q_len=64)
@@ -396,7 +450,9 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, step_ms, on
         assert bt.status() == 0
         bt.close()
         return {"queries": nq, "pairs_per_round": int(len(ci0)), "rounds": rounds, "ms_per_round": ms,
-                "pairs_per_s": len(ci0) / (ms * 1e-3), "schedule": ch, "bit_match_per_query_path": ok}
+                "pairs_per_s": len(ci0) / (ms * 1e-3), "schedule": ch, "bit_match_per_query_path": ok,
+                "tflops": fl / (ms * 1e-3) / 1e12,
+                "frac_of_builder_fp32_peak": fl / (ms * 1e-3) / 1e12 / bp["fp32_tflops"] if bp else None}
 
     def backward():
         wb = synth.contrastive_batch(device=dev)
@@ -576,7 +632,11 @@ def run_gem(args, dist, rank, world, local):
             ev[1].record(st)
         pid, _ = gem.topk(ws, scores, R)
         pool_ids.copy_(pid)
+        if ev:
+            ev[3].record(st)
         gem.score_ids(store, ws, q, qo, pool_off, pool_ids.view(-1), "f32", out=pool_sc)
+        if ev:
+            ev[4].record(st)
         out = gem.topk(ws, pool_sc.view(B, R), K, ids=pool_ids.view(-1).view(B, R).contiguous())
         if ev:
             ev[2].record(st)
@@ -592,7 +652,7 @@ def run_gem(args, dist, rank, world, local):
         step()
     _barrier(dist)
     launches0 = gem.lib.gem_kernel_launches()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     t_start = torch.cuda.Event(enable_timing=True)
@@ -638,7 +698,10 @@ def run_gem(args, dist, rank, world, local):
                    "n_sets": store.n_sets, "n_vecs": V, "queries": B, "m_q": 32, "rerank": R, "k": K,
                    "l2": "inputs larger than L2 (bf16 store %.2f GB)" % (V * 256 / 1e9)},
         "stages": {"maxsim_bf16_ms": k1_ms,
-                   "topk_rerank_topk_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in evs)},
+                   "topk_rerank_topk_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
+                   "topk_1000_of_500k_ms": statistics.mean(e[1].elapsed_time(e[3]) for e in evs),
+                   "fp32_rerank_ms": statistics.mean(e[3].elapsed_time(e[4]) for e in evs),
+                   "topk_100_of_1000_ms": statistics.mean(e[4].elapsed_time(e[2]) for e in evs)},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": (TC_TRAFFIC_BYTES_TEXT500K.get(
@@ -655,19 +718,54 @@ def run_gem(args, dist, rank, world, local):
                 "d2h_bytes_per_step": int(oi.numel() * 8 + osc.numel() * 4)},
     }
     line["config"]["schedule"] = schedule
+    bp = None
+    if rank == 0:
+        # builder-measured denominators of the FP32 and L2-gather kernels
+        bp = gem.measure_peaks()
+        line["builder_peaks"] = dict(bp, how="gem_measure_peaks on this GPU in this run: packed FP32 FMA chains "
+                                              "over a full grid; 128-byte row gathers from a 64 MB L2-resident "
+                                              "buffer (best of three launches)")
+        lens_d = torch.from_numpy(np.diff(w.docs.offsets)).to(dev)
+        pool_vecs = float(lens_d[pool_ids.view(-1)].sum())
+        rr_ms = line["stages"]["fp32_rerank_ms"]
+        tk_ms = line["stages"]["topk_1000_of_500k_ms"]
+        rr = 2.0 * 32 * 128 * pool_vecs / (rr_ms * 1e-3) / 1e12
+        tk = n_pairs * 4 / (tk_ms * 1e-3) / 1e9
+        line["rooflines_other"] = {
+            "fp32_rerank": {"kernel": "f32_ids_stream_kernel", "bound": "alu", "achieved": rr,
+                            "peak": bp["fp32_tflops"], "unit": "TFLOP/s", "frac": rr / bp["fp32_tflops"],
+                            "peak_kind": "builder-measured FP32 FMA", "gathered_gb": pool_vecs * 512 / 1e9},
+            "topk_1000_of_500k": {"kernel": "topk_sample/filter/select", "bound": "hbm", "achieved": tk,
+                                  "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": tk / peaks["hbm_gbs"],
+                                  "peak_kind": f"{peak_kind} HBM copy", "algorithmic_gb": n_pairs * 4 / 1e9}}
     truth = []
+    full_truth, truth_note = (load_truth(w) if rank == 0 and args.workload == "text"
+                              else (None, "not the text-corpus workload"))
     if rank == 0 and not args.no_cpu_baseline:
         docs_host = w.docs.vecs.cpu()
         line["cpu_baseline"], truth = cpu_baseline(docs_host, w.docs.offsets, w.queries.vecs.cpu(),
-                                                   w.queries.offsets, args.cpu_queries, K)
+                                                   w.queries.offsets, args.cpu_queries, K, one_thread=True)
         del docs_host
-        line["recall_at_100"] = {"bf16_rerank": _recall(ids_a.cpu().numpy(), truth), "queries": len(truth),
-                                 "reference": "exact FP64 top-100 of the oracle over all sets"}
+
+    def recall(found):
+        """recall@100 against the exact FP64 top-100: the stored ground truth of
+        all queries when it matches this data, else the oracle's sample above."""
+        if full_truth is not None:
+            ids, sc = full_truth
+            r = recall_vs_truth(found, (ids[: found.shape[0]], sc[: found.shape[0]]))
+            r["reference"] = "stored exact FP64 top-100 of every query (tests/golden/text500k_truth.npz)"
+            return r
+        n = min(len(truth), found.shape[0])
+        return {"recall": _recall(found, truth[:n]) if n else None, "queries": n,
+                "reference": f"oracle top-100 of the first {n} queries ({truth_note})"}
+    recall.full = full_truth is not None
+    if rank == 0 and (full_truth is not None or truth):
+        line["recall_at_100"] = {"bf16_rerank": recall(ids_a.cpu().numpy())}
     if rank == 0 and not args.no_extras:
         stages = line["stages"]
-        extra_stages(gem, store, ws, w, q, qo, R, K, truth, stages, dev, ms,
+        extra_stages(gem, store, ws, w, q, qo, R, K, recall, stages, dev, ms,
                      only=set(args.stages.split(",")) if args.stages else None, qch_k1=args.qch_k1,
-                     schedule=schedule)
+                     schedule=schedule, bp=bp)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -672,6 +672,17 @@ gem_status gem_shard_rerank(const gem_store* store, gem_workspace* ws, const flo
 gem_status gem_merge_topk(const float* scores, const int64_t* ids, int32_t n_lists, int32_t rows, int32_t k_in,
                           int32_t k, int64_t* out_ids, float* out_scores, void* stream);
 
+/*
+ * gem_measure_peaks: measured denominators for the roofline fractions of the
+ * FP32 and table-lookup kernels (the paper has no counterpart; a measurement
+ * helper).  fp32_tflops: FP32 FMA throughput of a full grid of packed two-lane
+ * FMA chains (fma.rn.f32x2, as the FP32 scorers issue them), 2 flop per FMA.
+ * l2_gather_gbs: bandwidth of warps reading 128-byte rows at hashed indices of a
+ * 64 MB buffer held in L2 (the qCH table-lookup pattern).  Best of three timed
+ * launches each.  Allocates and frees a 64 MB buffer and blocks until done.
+ */
+gem_status gem_measure_peaks(float* fp32_tflops, float* l2_gather_gbs, void* stream);
+
 /* Number of kernels this library has enqueued since it was loaded (all
  * devices and threads); lets a caller count the library's launches in a region. */
 int64_t gem_kernel_launches(void);

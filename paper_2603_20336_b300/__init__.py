@@ -499,6 +499,15 @@ def maxsim_bwd(q, q_offsets, docs, doc_offsets, pair_offsets, pair_ids, argmax, 
     return grad_q, grad_d
 
 
+def measure_peaks(stream=None) -> dict:
+    """Measured FP32 FMA peak (TFLOP/s) and L2-resident 128-byte gather bandwidth
+    (GB/s) of the current GPU: the roofline denominators of the FP32 scorers and
+    the qCH table lookups."""
+    f, g = ctypes.c_float(), ctypes.c_float()
+    _check(lib.gem_measure_peaks(ctypes.byref(f), ctypes.byref(g), _stream(stream)))
+    return {"fp32_tflops": f.value, "l2_gather_gbs": g.value}
+
+
 class MaxSimFn(torch.autograd.Function):
     """Differentiable pair scores S_t = CH(Q_b, P_d) (Eq. 1) with the library's
     forward (argmax side output) and hand-written backward."""

@@ -11,16 +11,17 @@
 //    of its exact value (the dropped lo.lo term and the residues of the split,
 //    and 384 accumulations even if each truncates), while the FP32 chain of the
 //    SIMT assignment is within E_f = 128 * 2^-24 * |x| |C_c|.
-// 2. Candidates.  The epilogue keeps, per row, the K = 6 largest tensor-core
-//    values over all k1 centroids.  The FP32 winner c* scores at least
-//    v_max - 2 (E_b + E_f) on the tensor cores, so when the sixth candidate
-//    lies below v_max - band (band = 2 (E_b + E_f) |x| max_c |C_c|, with 1%
-//    slack) every centroid that can win is a candidate.
-// 3. Recheck.  The candidates are rescored with the SIMT assignment's exact FP32
-//    chain and the best one (ties to the lower index) is the code: the same code
-//    and best value as the SIMT kernel.  A row whose candidates do not cover the
-//    band (near-ties, zero or non-finite rows) is listed and assigned afterwards
-//    by the SIMT kernel itself.
+// 2. Candidates.  The epilogue keeps, per row, the running maximum m of the
+//    tensor-core values over the k1 centroids and every centroid whose value
+//    was within band of m when it was seen (band = 2 (E_b + E_f) |x| max_c
+//    |C_c|, with 1% slack), evicting those that fall below m - band, at most
+//    K = 6 at a time.  The FP32 winner c* scores at least m_final - band on the
+//    tensor cores, and m only grows, so c* is always kept.
+// 3. Recheck.  The kept candidates are rescored with the SIMT assignment's
+//    exact FP32 chain and the best one (ties to the lower index) is the code:
+//    the same code and best value as the SIMT kernel.  A row whose list
+//    overflowed (more than K near-ties), or with a zero, infinite or NaN value or
+//    norm, is listed and assigned afterwards by the SIMT kernel itself.
 //
 // Kernel layout: a persistent CTA per SM takes units of 256 rows (two M tiles)
 // from a global counter; the A operands (hi and lo) of a unit sit in shared
@@ -269,26 +270,35 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap tm_xh, const __grid_constan
       return u;
     };
     for (long long u = take_unit(); u < n_units && ok; u = take_unit()) {
-      // the row's K best tensor-core values, largest first (ties: lower index first)
-      float tv[kAtK];
-      int ti[kAtK];
-#pragma unroll
-      for (int i = 0; i < kAtK; ++i) { tv[i] = -INFINITY; ti[i] = -1; }
-      auto consider = [&](float v, int col) {
-        if (v > tv[kAtK - 1]) {
-#pragma unroll
-          for (int i = 0; i < kAtK; ++i) {
-            if (v > tv[i]) {
-              const float fv = tv[i];
-              const int fi = ti[i];
-              tv[i] = v;
-              ti[i] = col;
-              v = fv;
-              col = fi;
-            }
-          }
+      const int64_t row = u * kAtRows + local_row;
+      const bool live = row < a.n_rows;
+      // the row's norm (its band) from the FP32 row; the same FMA chain as the recheck
+      float ss = 0.f;
+      if (live) {
+        const float4* xr = reinterpret_cast<const float4*>(a.X + row * kDim);
+#pragma unroll 8
+        for (int k4 = 0; k4 < kDim / 4; ++k4) {
+          const float4 x = __ldg(xr + k4);
+          ss = __fmaf_rn(x.x, x.x, ss);
+          ss = __fmaf_rn(x.y, x.y, ss);
+          ss = __fmaf_rn(x.z, x.z, ss);
+          ss = __fmaf_rn(x.w, x.w, ss);
         }
-      };
+      }
+      const float band = kAtBand * sqrtf(ss) * cmax;
+      // Running maximum m of the tensor-core values, and every column seen so
+      // far whose value was within `band` of the maximum at the time: a column
+      // within band of the final maximum is always among them (the maximum only
+      // grows), and an entry that falls below max - band is evicted.  More than
+      // kAtK such columns at once overflows the list: the row then goes to the
+      // SIMT assignment.
+      float m = -INFINITY, thr = -INFINITY;
+      float lv[kAtK];
+      int li[kAtK];
+      int n_l = 0;
+      bool overflow = false;
+#pragma unroll
+      for (int i = 0; i < kAtK; ++i) { lv[i] = -INFINITY; li[i] = -1; }
       for (int t = 0; t < n_tiles; ++t) {
         const bool got = mbar_wait(&acc_full[acc * kAtNMW + m_tile], acc_phase, a.status, abort_flag);
         if (!__all_sync(0xffffffffu, got)) {
@@ -298,11 +308,11 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap tm_xh, const __grid_constan
         tc_fence_after();
         const uint32_t tcol = tmem + t_lane + acc * kAtAccCols + m_tile * kAtN;
         const int valid = a.k1 - t * kAtN;  // columns of real centroids in this tile
-#pragma unroll
-        for (int c = 0; c < kAtN / kAtCh; ++c) {
-          float v[kAtCh];
-          tmem_ld64(tcol + c * kAtCh, v);
-          if (c == kAtN / kAtCh - 1) {
+#pragma unroll 1
+        for (int c = 0; c < kAtN / 32; ++c) {
+          float v[32];
+          tmem_ld32(tcol + c * 32, v);
+          if (c == kAtN / 32 - 1) {
             // the accumulator is in registers: hand the buffer back
             tc_fence_before();
             __syncwarp();
@@ -310,67 +320,96 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap tm_xh, const __grid_constan
           }
           if (valid < kAtN) {  // last tile: columns past k1 hold zero-filled rows
 #pragma unroll
-            for (int j = 0; j < kAtCh; ++j)
-              if (c * kAtCh + j >= valid) v[j] = -INFINITY;
+            for (int j = 0; j < 32; ++j)
+              if (c * 32 + j >= valid) v[j] = -INFINITY;
           }
+          // two-input maxima ignore NaN (a NaN centroid's column never counts)
+          float cm[16];
 #pragma unroll
-          for (int g = 0; g < kAtCh / 8; ++g) {
-            // two-input maxima ignore NaN (a NaN centroid's column never hides
-            // the other columns of its group)
-            const float gm = fmaxf(fmaxf(fmaxf(v[8 * g], v[8 * g + 1]), fmaxf(v[8 * g + 2], v[8 * g + 3])),
-                                   fmaxf(fmaxf(v[8 * g + 4], v[8 * g + 5]), fmaxf(v[8 * g + 6], v[8 * g + 7])));
-            if (gm > tv[kAtK - 1]) {
-              const int col0 = t * kAtN + c * kAtCh + 8 * g;
+          for (int j = 0; j < 16; ++j) cm[j] = fmaxf(v[2 * j], v[2 * j + 1]);
 #pragma unroll
-              for (int j = 0; j < 8; ++j) consider(v[8 * g + j], col0 + j);
+          for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+            for (int j = 0; j < w; ++j) cm[j] = fmaxf(cm[j], cm[j + w]);
+          if (cm[0] >= thr) {
+            // rare: the chunk holds a new maximum or a value within band of it
+            uint32_t hits = 0;
+            float tmp[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              tmp[j] = v[j];
+              hits |= (v[j] >= thr) ? (1u << j) : 0u;
+            }
+#pragma unroll 1
+            while (hits) {
+              const int j = __ffs(hits) - 1;
+              hits &= hits - 1;
+              const float x = tmp[j];
+              if (!(x >= thr)) continue;        // the threshold rose within this chunk
+              if (x > m) {
+                m = x;
+                thr = m - band;
+              }
+              if (n_l == kAtK) {                // full: drop entries now below the band
+                int k = 0;
+#pragma unroll 1
+                for (int e = 0; e < kAtK; ++e)
+                  if (lv[e] >= thr) { lv[k] = lv[e]; li[k] = li[e]; ++k; }
+                n_l = k;
+              }
+              if (n_l < kAtK) {
+                lv[n_l] = x;
+                li[n_l] = t * kAtN + c * 32 + j;
+                ++n_l;
+              } else {
+                overflow = true;
+              }
             }
           }
         }
         if (++acc == 2) { acc = 0; acc_phase ^= 1; }
       }
       if (!ok) break;
-      // recheck the candidates with the SIMT assignment's FP32 chain
-      const int64_t row = u * kAtRows + local_row;
-      if (row < a.n_rows) {
+      if (!live) continue;
+      // recheck the candidates within band of the final maximum with the SIMT
+      // assignment's FP32 chain
+      bool complete = !overflow && m == m && band == band && band < INFINITY && m > -INFINITY;
+      int cidx[kAtK];
+#pragma unroll
+      for (int e = 0; e < kAtK; ++e) cidx[e] = (e < n_l && lv[e] >= thr) ? li[e] : -1;
+      if (complete) {
         const float4* xr = reinterpret_cast<const float4*>(a.X + row * kDim);
         const float4* cr = reinterpret_cast<const float4*>(a.C);
         float dot[kAtK];
-        int cidx[kAtK];
 #pragma unroll
-        for (int j = 0; j < kAtK; ++j) { dot[j] = 0.f; cidx[j] = ti[j] < 0 ? 0 : ti[j]; }
-        float ss = 0.f;
+        for (int e = 0; e < kAtK; ++e) dot[e] = 0.f;
 #pragma unroll 4
         for (int k4 = 0; k4 < kDim / 4; ++k4) {
           const float4 x = __ldg(xr + k4);
-          ss = __fmaf_rn(x.x, x.x, ss);
-          ss = __fmaf_rn(x.y, x.y, ss);
-          ss = __fmaf_rn(x.z, x.z, ss);
-          ss = __fmaf_rn(x.w, x.w, ss);
 #pragma unroll
-          for (int j = 0; j < kAtK; ++j) {
-            const float4 c = __ldg(cr + (int64_t)cidx[j] * (kDim / 4) + k4);
-            dot[j] = __fmaf_rn(x.x, c.x, dot[j]);
-            dot[j] = __fmaf_rn(x.y, c.y, dot[j]);
-            dot[j] = __fmaf_rn(x.z, c.z, dot[j]);
-            dot[j] = __fmaf_rn(x.w, c.w, dot[j]);
+          for (int e = 0; e < kAtK; ++e) {
+            const float4 c = __ldg(cr + (int64_t)(cidx[e] < 0 ? 0 : cidx[e]) * (kDim / 4) + k4);
+            dot[e] = __fmaf_rn(x.x, c.x, dot[e]);
+            dot[e] = __fmaf_rn(x.y, c.y, dot[e]);
+            dot[e] = __fmaf_rn(x.z, c.z, dot[e]);
+            dot[e] = __fmaf_rn(x.w, c.w, dot[e]);
           }
         }
-        const float band = kAtBand * sqrtf(ss) * cmax;
-        // NaN anywhere (values, norms) fails the test and leaves the row to the
-        // SIMT assignment
-        const bool complete = tv[kAtK - 1] < tv[0] - band;
-        if (complete) {
-          float bv = -INFINITY;
-          int bi = 0x7fffffff;
+        float bv = -INFINITY;
+        int bi = 0x7fffffff;
 #pragma unroll
-          for (int j = 0; j < kAtK; ++j)
-            if (ti[j] >= 0 && better(dot[j], ti[j], bv, bi)) { bv = dot[j]; bi = ti[j]; }
+        for (int e = 0; e < kAtK; ++e)
+          if (cidx[e] >= 0 && better(dot[e], cidx[e], bv, bi)) { bv = dot[e]; bi = cidx[e]; }
+        if (bi == 0x7fffffff) {
+          complete = false;
+        } else {
           a.codes[row] = bi;
           if (a.best) a.best[row] = bv;
-        } else {
-          const unsigned long long slot = atomicAdd(a.fb_count, 1ull);
-          a.fb_rows[slot] = (int32_t)(a.row_base + row);
         }
+      }
+      if (!complete) {
+        const unsigned long long slot = atomicAdd(a.fb_count, 1ull);
+        a.fb_rows[slot] = (int32_t)(a.row_base + row);
       }
     }
   }

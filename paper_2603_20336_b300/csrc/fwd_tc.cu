@@ -90,6 +90,28 @@ __device__ __forceinline__ PairInfo pair_info(const FtArgs& a, int64_t t) {
   return p;
 }
 
+// pair i's info from the lane that loaded it (every lane of the warp calls it)
+__device__ __forceinline__ PairInfo shfl_pair(const PairInfo& m, int i) {
+  PairInfo p;
+  p.b = __shfl_sync(0xffffffffu, m.b, i);
+  p.m_q = __shfl_sync(0xffffffffu, m.m_q, i);
+  p.q0 = __shfl_sync(0xffffffffu, (long long)m.q0, i);
+  p.r0 = __shfl_sync(0xffffffffu, (long long)m.r0, i);
+  p.m_p = __shfl_sync(0xffffffffu, m.m_p, i);
+  p.tiles = __shfl_sync(0xffffffffu, m.tiles, i);
+  p.bad_id = __shfl_sync(0xffffffffu, (int)m.bad_id, i) != 0;
+  return p;
+}
+
+// the infos of a unit's pairs t0 .. t0 + cnt - 1, lane i holding pair t0 + i:
+// one round of parallel loads per unit instead of a chain of dependent loads
+// per pair
+__device__ __forceinline__ PairInfo unit_pairs(const FtArgs& a, int64_t t0, int cnt, int lane) {
+  PairInfo m{};
+  if (lane < cnt) m = pair_info(a, t0 + lane);
+  return m;
+}
+
 __global__ void __launch_bounds__(kFtThreads, 1)
 fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_d, FtArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -144,44 +166,54 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
 
   if (warp == kFtEpiWarps) {
     // ------------------------------------------------------------------ producer
+    // lane 0 issues; the warp loads each unit's pair infos in parallel
     if (lane == 0) {
       tma_prefetch_desc(&tm_q);
       tma_prefetch_desc(&tm_d);
-      int stage = 0;
-      uint32_t phase = 0;
-      uint32_t issued[kFtStages] = {};
-      uint32_t n_a = 0;  // query blocks loaded
-      int cur_b = -1;
-      bool ok = true;
-      int uslot = 0;
-      uint32_t uphase = 0;
-      auto draw_unit = [&]() -> long long {
-        const long long u = atomicAdd(a.unit_counter, 1);
-        if (!mbar_wait(&unit_empty[uslot], uphase ^ 1, a.status, abort_flag)) {
-          ok = false;
-          return n_units;
+    }
+    int stage = 0;
+    uint32_t phase = 0;
+    uint32_t issued[kFtStages] = {};
+    uint32_t n_a = 0;  // query blocks loaded
+    int cur_b = -1;
+    bool ok = true;
+    int uslot = 0;
+    uint32_t uphase = 0;
+    for (;;) {
+      long long u = 0;
+      int okl = 1;
+      if (lane == 0) {
+        u = atomicAdd(a.unit_counter, 1);
+        okl = mbar_wait(&unit_empty[uslot], uphase ^ 1, a.status, abort_flag) ? 1 : 0;
+        if (okl) {
+          unit_ring[uslot] = (int)(u < n_units ? u : n_units);
+          mbar_arrive(&unit_full[uslot]);
         }
-        unit_ring[uslot] = (int)(u < n_units ? u : n_units);
-        mbar_arrive(&unit_full[uslot]);
-        if (++uslot == kFtUnitRing) { uslot = 0; uphase ^= 1; }
-        return u;
-      };
-      for (long long u = draw_unit(); u < n_units && ok; u = draw_unit()) {
-        const int64_t t1 = min(a.n_pairs, (int64_t)(u + 1) * kFtPairsPerUnit);
-        for (int64_t t = u * kFtPairsPerUnit; t < t1 && ok; ++t) {
-          const PairInfo p = pair_info(a, t);
-          if (p.tiles == 0) continue;
+      }
+      u = __shfl_sync(0xffffffffu, u, 0);
+      if (!__shfl_sync(0xffffffffu, okl, 0)) { ok = false; break; }
+      if (++uslot == kFtUnitRing) { uslot = 0; uphase ^= 1; }
+      if (u >= n_units) break;
+      const int64_t t0 = u * kFtPairsPerUnit;
+      const int cnt = (int)min((int64_t)kFtPairsPerUnit, a.n_pairs - t0);
+      const PairInfo mine = unit_pairs(a, t0, cnt, lane);
+      for (int i = 0; i < cnt && ok; ++i) {
+        const PairInfo p = shfl_pair(mine, i);
+        if (p.tiles == 0) continue;
+        if (lane == 0) {
           if (p.b != cur_b) {
-            if (n_a > 0 && !mbar_wait(q_empty, (n_a - 1) & 1, a.status, abort_flag)) { ok = false; break; }
-            mbar_arrive_expect_tx(q_full, kFtABytes);
-            for (int h = 0; h < 2; ++h) tma_load_2d(a_smem + h * 16384, &tm_q, q_full, h * 64, (int)p.q0);
-            ++n_a;
-            cur_b = p.b;
+            if (n_a > 0 && !mbar_wait(q_empty, (n_a - 1) & 1, a.status, abort_flag)) okl = 0;
+            if (okl) {
+              mbar_arrive_expect_tx(q_full, kFtABytes);
+              for (int h = 0; h < 2; ++h) tma_load_2d(a_smem + h * 16384, &tm_q, q_full, h * 64, (int)p.q0);
+              ++n_a;
+              cur_b = p.b;
+            }
           }
-          for (int tile = 0; tile < p.tiles; ++tile) {
+          for (int tile = 0; tile < p.tiles && okl; ++tile) {
             const int rows = min(kFtN, p.m_p - tile * kFtN);
             const int nb = (rows + kFtBox - 1) / kFtBox;
-            if (!mbar_wait(&empty[stage], phase ^ 1, a.status, abort_flag)) { ok = false; break; }
+            if (!mbar_wait(&empty[stage], phase ^ 1, a.status, abort_flag)) { okl = 0; break; }
             uint8_t* dst = b_smem + stage * kFtStageBytes;
             mbar_arrive_expect_tx(&full[stage], nb * kFtBox * kDim * 2);
             const int row0 = (int)(p.r0 + (int64_t)tile * kFtN);
@@ -193,49 +225,55 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
             if (++stage == kFtStages) { stage = 0; phase ^= 1; }
           }
         }
+        if (!__shfl_sync(0xffffffffu, okl, 0)) ok = false;
       }
-      if (!ok) {
-        for (int s = 0; s < kFtStages; ++s)
-          if (issued[s]) { int z = 0; mbar_wait(&full[s], (issued[s] - 1) & 1, nullptr, &z); }
-        int z = 0;
-        if (n_a) mbar_wait(q_full, (n_a - 1) & 1, nullptr, &z);
-      }
+    }
+    if (!ok && lane == 0) {
+      for (int s2 = 0; s2 < kFtStages; ++s2)
+        if (issued[s2]) { int z = 0; mbar_wait(&full[s2], (issued[s2] - 1) & 1, nullptr, &z); }
+      int z = 0;
+      if (n_a) mbar_wait(q_full, (n_a - 1) & 1, nullptr, &z);
     }
   } else if (warp == kFtEpiWarps + 1) {
     // ------------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      int acc = 0;
-      uint32_t acc_phase = 0;
-      uint32_t n_a = 0;
-      int cur_b = -1;
-      bool ok = true;
-      int uslot = 0;
-      uint32_t uphase = 0;
-      const uint64_t ad0 = sw128_desc(smem_u32(a_smem));
-      for (;;) {
-        if (!mbar_wait(&unit_full[uslot], uphase, a.status, abort_flag)) { ok = false; break; }
-        const long long u = unit_ring[uslot];
-        mbar_arrive(&unit_empty[uslot]);
-        if (++uslot == kFtUnitRing) { uslot = 0; uphase ^= 1; }
-        if (u >= n_units) break;
-        const int64_t t1 = min(a.n_pairs, (int64_t)(u + 1) * kFtPairsPerUnit);
-        for (int64_t t = u * kFtPairsPerUnit; t < t1 && ok; ++t) {
-          const PairInfo p = pair_info(a, t);
-          if (p.tiles == 0) continue;
+    int stage = 0;
+    uint32_t phase = 0;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    uint32_t n_a = 0;
+    int cur_b = -1;
+    bool ok = true;
+    int uslot = 0;
+    uint32_t uphase = 0;
+    const uint64_t ad0 = sw128_desc(smem_u32(a_smem));
+    for (;;) {
+      const bool w = mbar_wait(&unit_full[uslot], uphase, a.status, abort_flag);
+      if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+      const long long u = unit_ring[uslot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&unit_empty[uslot]);
+      if (++uslot == kFtUnitRing) { uslot = 0; uphase ^= 1; }
+      if (u >= n_units) break;
+      const int64_t t0 = u * kFtPairsPerUnit;
+      const int cnt = (int)min((int64_t)kFtPairsPerUnit, a.n_pairs - t0);
+      const PairInfo mine = unit_pairs(a, t0, cnt, lane);
+      for (int i = 0; i < cnt && ok; ++i) {
+        const PairInfo p = shfl_pair(mine, i);
+        if (p.tiles == 0) continue;
+        int okl = 1;
+        if (lane == 0) {
           if (p.b != cur_b) {
             if (n_a > 0) mma_commit(q_empty);   // the previous block's MMAs release it
-            if (!mbar_wait(q_full, n_a & 1, a.status, abort_flag)) { ok = false; break; }
+            if (!mbar_wait(q_full, n_a & 1, a.status, abort_flag)) okl = 0;
             tc_fence_after();
             ++n_a;
             cur_b = p.b;
           }
-          for (int tile = 0; tile < p.tiles; ++tile) {
+          for (int tile = 0; tile < p.tiles && okl; ++tile) {
             const int rows = min(kFtN, p.m_p - tile * kFtN);
             const int nb = (rows + kFtBox - 1) / kFtBox;
-            if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1, a.status, abort_flag)) { ok = false; break; }
-            if (!mbar_wait(&full[stage], phase, a.status, abort_flag)) { ok = false; break; }
+            if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1, a.status, abort_flag)) { okl = 0; break; }
+            if (!mbar_wait(&full[stage], phase, a.status, abort_flag)) { okl = 0; break; }
             tc_fence_after();
             const uint64_t bd0 = sw128_desc(smem_u32(b_smem + stage * kFtStageBytes));
             const uint32_t idesc = make_idesc(128, nb * kFtBox, 1u, 1u);
@@ -253,8 +291,11 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
             if (++acc == 2) { acc = 0; acc_phase ^= 1; }
           }
         }
-        if (!ok) break;
+        if (!__shfl_sync(0xffffffffu, okl, 0)) ok = false;
       }
+      if (!ok) break;
+    }
+    if (lane == 0) {
       mma_commit(done_bar);
       int z = 0;
       mbar_wait(done_bar, 0, nullptr, &z);
@@ -277,9 +318,12 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
       if (lane == 0) mbar_arrive(&unit_empty[uslot]);
       if (++uslot == kFtUnitRing) { uslot = 0; uphase ^= 1; }
       if (u >= n_units) break;
-      const int64_t t1 = min(a.n_pairs, (int64_t)(u + 1) * kFtPairsPerUnit);
-      for (int64_t t = u * kFtPairsPerUnit; t < t1 && ok; ++t) {
-        const PairInfo p = pair_info(a, t);
+      const int64_t t0 = u * kFtPairsPerUnit;
+      const int cnt = (int)min((int64_t)kFtPairsPerUnit, a.n_pairs - t0);
+      const PairInfo mine_p = unit_pairs(a, t0, cnt, lane);
+      for (int i = 0; i < cnt && ok; ++i) {
+        const int64_t t = t0 + i;
+        const PairInfo p = shfl_pair(mine_p, i);
         if (p.tiles == 0) {
           if (warp == 0 && lane == 0) {
             if (p.bad_id) {

@@ -34,7 +34,7 @@ constexpr int kSampleRuns = 256;                  // runs of the threshold sampl
 constexpr int kSampleRun = 32;                    // consecutive elements per run
 constexpr int kSample = kSampleRuns * kSampleRun; // sampled keys per row
 constexpr int kFilterThreads = 256;
-constexpr int kFilterPerThread = 16;              // four 16-byte loads
+constexpr int kFilterPerThread = 32;              // eight 16-byte loads
 constexpr int kFilterChunk = kFilterThreads * kFilterPerThread;
 
 __device__ __forceinline__ uint32_t score_key(float f) {
@@ -327,9 +327,9 @@ topk_filter_kernel(const float* __restrict__ scores, int rows, int64_t cols, con
     const float fT = take_all ? 0.f : key_score((uint32_t)(T >> 32));
     const uint32_t T_lo = (uint32_t)T;
     float v[kFilterPerThread];
-    // four coalesced 16-byte loads per thread, all in flight before use
+    // eight coalesced 16-byte loads per thread, all in flight before use
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kFilterPerThread / 4; ++j) {
       const int64_t t = c0 + ((int64_t)j * kFilterThreads + threadIdx.x) * 4;
       if (vec4 && t + 3 < cols) {
         const float4 f = __ldcs(reinterpret_cast<const float4*>(s + t));
@@ -340,19 +340,37 @@ topk_filter_kernel(const float* __restrict__ scores, int rows, int64_t cols, con
       }
     }
     uint32_t picks = 0;  // bit 4 j + e: element (j, e) is a candidate
+    if (!take_all && !id_row && !dead && c0 + kFilterChunk <= cols) {
+      // the common case: ids are positions, every element valid; a score equal
+      // to the threshold's decides by id
+      uint32_t eq = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+      for (int i = 0; i < kFilterPerThread; ++i) {
+        picks |= (v[i] >= fT) ? (1u << i) : 0u;
+        eq |= (v[i] == fT) ? (1u << i) : 0u;
+      }
+      uint32_t check = picks & eq;
+      while (check) {
+        const int b = __ffs(check) - 1;
+        check &= check - 1;
+        const int64_t t = c0 + ((int64_t)(b >> 2) * kFilterThreads + threadIdx.x) * 4 + (b & 3);
+        if ((0xFFFFFFFFu - (uint32_t)t) < T_lo) picks &= ~(1u << b);
+      }
+    } else {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int64_t t = c0 + ((int64_t)j * kFilterThreads + threadIdx.x) * 4 + e;
-        const float sv = v[4 * j + e];
-        bool p = take_all || sv >= fT;
-        if (p && t < cols && (id_row || dead || (!take_all && sv == fT))) {
-          const int64_t id = id_row ? id_row[t] : t;
-          p = id >= 0 && !is_dead(dead, n_sets, id) &&
-              (take_all || sv > fT || (0xFFFFFFFFu - (uint32_t)id) >= T_lo);
+      for (int j = 0; j < kFilterPerThread / 4; ++j) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int64_t t = c0 + ((int64_t)j * kFilterThreads + threadIdx.x) * 4 + e;
+          const float sv = v[4 * j + e];
+          bool p = take_all || sv >= fT;
+          if (p && t < cols && (id_row || dead || (!take_all && sv == fT))) {
+            const int64_t id = id_row ? id_row[t] : t;
+            p = id >= 0 && !is_dead(dead, n_sets, id) &&
+                (take_all || sv > fT || (0xFFFFFFFFu - (uint32_t)id) >= T_lo);
+          }
+          picks |= (p && t < cols) ? (1u << (4 * j + e)) : 0u;
         }
-        picks |= (p && t < cols) ? (1u << (4 * j + e)) : 0u;
       }
     }
     // warp: inclusive scan of the pick counts, one atomic for the warp's slots

@@ -278,3 +278,19 @@ def contrastive_batch(seed: int = 1239, n_queries: int = 256, docs_per_query: in
     qs = vector_sets(np.full(n_queries, m_q, np.int64), cents, seed + 7919, device)
     return Workload("contrastive-256x64", seed, docs, qs,
                     {"docs_per_query": docs_per_query, "tau": 0.05})
+
+
+def fingerprint(docs: VectorSets, queries: VectorSets, n_sample: int = 1024) -> str:
+    """SHA-256 of a workload's identity: the offsets of both collections and a
+    spread sample of their rows (FP32 bytes).  Equal fingerprints mean the data a
+    stored ground truth was computed on is the data at hand."""
+    import hashlib
+    h = hashlib.sha256()
+    for vs in (docs, queries):
+        h.update(np.ascontiguousarray(vs.offsets, dtype=np.int64).tobytes())
+        n = vs.n_vecs
+        rows = np.unique(np.linspace(0, n - 1, num=min(n, n_sample)).astype(np.int64))
+        sample = vs.vecs[torch.from_numpy(rows).to(vs.vecs.device)].to("cpu", torch.float32).contiguous()
+        h.update(sample.numpy().tobytes())
+    return h.hexdigest()
+
