@@ -49,6 +49,9 @@ METRIC = "doc-sets scored/s (exact MaxSim, BF16 tensor cores + FP32 rerank)"
 WORKLOADS = {
     "text": dict(n_sets=500_000, n_queries=1000, rerank=1000, k=100),
     "small": dict(n_sets=20_000, n_queries=100, rerank=1000, k=100),
+    # the text-corpus recipe at 50,000 sets (3.5M vectors, about 3 GB of store
+    # copies): the size of the small-case kernel profiles
+    "medium": dict(n_sets=50_000, n_queries=1000, rerank=1000, k=100),
 }
 
 
@@ -734,7 +737,11 @@ def run_gem(args, dist, rank, world, local):
         line["rooflines_other"] = {
             "fp32_rerank": {"kernel": "f32_ids_stream_kernel", "bound": "alu", "achieved": rr,
                             "peak": bp["fp32_tflops"], "unit": "TFLOP/s", "frac": rr / bp["fp32_tflops"],
-                            "peak_kind": "builder-measured FP32 FMA", "gathered_gb": pool_vecs * 512 / 1e9},
+                            "peak_kind": "builder-measured FP32 FMA", "gathered_gb": pool_vecs * 512 / 1e9,
+                            # how much a doc-major grouping of the pool could save: the
+                            # FP32 bytes of the distinct sets against those gathered
+                            "distinct_sets": int(torch.unique(pool_ids).numel()),
+                            "distinct_gb": float(lens_d[torch.unique(pool_ids)].sum()) * 512 / 1e9},
             "topk_1000_of_500k": {"kernel": "topk_sample/filter/select", "bound": "hbm", "achieved": tk,
                                   "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": tk / peaks["hbm_gbs"],
                                   "peak_kind": f"{peak_kind} HBM copy", "algorithmic_gb": n_pairs * 4 / 1e9}}

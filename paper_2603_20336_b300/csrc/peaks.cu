@@ -28,20 +28,27 @@ __global__ void __launch_bounds__(kPeakThreads) fp32_peak_kernel(int iters, floa
   if (s == 1.2345f) out[0] = s;  // keeps the chains live
 }
 
-__global__ void __launch_bounds__(kPeakThreads) l2_gather_kernel(const float* __restrict__ buf, int64_t rows,
+// rows_mask + 1 rows of 32 floats (a power of two); eight independent hashed
+// row reads in flight per lane at a time
+__global__ void __launch_bounds__(kPeakThreads) l2_gather_kernel(const float* __restrict__ buf, uint32_t rows_mask,
                                                                   int reads_per_warp, float* out) {
   const int lane = threadIdx.x & 31;
-  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-  float acc = 0.f;
-  uint64_t h = warp * 0x9E3779B97F4A7C15ull + 1;
-#pragma unroll 8
-  for (int r = 0; r < reads_per_warp; ++r) {
-    h ^= h >> 29;
-    h *= 0xBF58476D1CE4E5B9ull;
-    const int64_t row = (int64_t)((h >> 20) % (uint64_t)rows);
-    acc += __ldcg(buf + row * 32 + lane);
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  float acc[8] = {};
+  for (int r = 0; r < reads_per_warp; r += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      uint32_t h = (warp * 2654435761u) ^ ((uint32_t)(r + u) * 0x9E3779B9u);
+      h ^= h >> 15;
+      h *= 0x2C1B3C6Du;
+      h ^= h >> 12;
+      acc[u] += __ldcg(buf + (size_t)(h & rows_mask) * 32 + lane);
+    }
   }
-  if (acc == 1.2345f) out[0] = acc;
+  float s = 0.f;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) s += acc[u];
+  if (s == 1.2345f) out[0] = s;
 }
 
 }  // namespace
@@ -55,7 +62,7 @@ extern "C" gem_status gem_measure_peaks(float* fp32_tflops, float* l2_gather_gbs
   int dev = 0, n_sm = 0;
   GEM_CUDA_TRY(cudaGetDevice(&dev));
   GEM_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-  const int64_t rows = (int64_t)(64 << 20) / 128;  // 64 MB of 128-byte rows
+  const int64_t rows = (int64_t)(64 << 20) / 128;  // 64 MB of 128-byte rows (2^19: a power of two)
   float* buf = nullptr;
   if (cudaMalloc(&buf, rows * 128 + 256) != cudaSuccess) {
     cudaGetLastError();
@@ -88,7 +95,7 @@ extern "C" gem_status gem_measure_peaks(float* fp32_tflops, float* l2_gather_gbs
   best_ms = 1e30f;
   for (int rep = 0; rep < 4 && r == GEM_OK; ++rep) {
     check(cudaEventRecord(e0, st), "cudaEventRecord");
-    l2_gather_kernel<<<grid, kPeakThreads, 0, st>>>(buf, rows, reads, out);
+    l2_gather_kernel<<<grid, kPeakThreads, 0, st>>>(buf, (uint32_t)(rows - 1), reads, out);
     check(cudaEventRecord(e1, st), "cudaEventRecord");
     check(cudaEventSynchronize(e1), "cudaEventSynchronize");
     float ms = 0.f;
