@@ -174,6 +174,14 @@ gem_status gem_store_export(const gem_store* store, int32_t what, void* dst, siz
  * [n]; best (may be NULL) receives the winning inner product.  Device pointers.
  * A NaN dot product counts as -inf, so every code lies in [0, k1) (a row whose
  * dots are all NaN gets code 0).
+ * From 16,384 rows and 64 centroids the work runs on the tensor cores with the
+ * same result (codes and best values bit for bit): rows and centroids split
+ * into two bf16 parts, three products per dot, the centroids within the
+ * products' error band of each row's maximum rechecked with the FP32 chain
+ * above, and the FP32 kernel for rows with more near-ties than that.  That path
+ * allocates stream-ordered scratch (512 bytes per centroid, 512 bytes per row
+ * for up to 4M rows at a time, 4 bytes per row) and blocks until done; smaller
+ * calls are asynchronous and allocate nothing.
  */
 gem_status gem_assign_codes(const float* x, int64_t n, const float* centroids, int32_t k1,
                             int32_t* codes, float* best, void* stream);

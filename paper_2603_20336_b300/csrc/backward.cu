@@ -205,6 +205,57 @@ __global__ void __launch_bounds__(256) maxsim_bwd_p_kernel(BwdArgs a, int64_t n_
   }
 }
 
+// grad_docs for query sets of at most 32 rows: one warp per pair.  The pair's
+// (j*(i), i) are sorted by a warp bitonic sort, so the rows sharing an argmax
+// row j are adjacent; lane k4 then walks the sorted rows in order, sums q_i's
+// components 4 k4 .. 4 k4 + 3 over each run (ascending i, as the CTA-per-pair
+// kernel does) and adds g_t times the sum to row j with one 16-byte atomic.
+__global__ void __launch_bounds__(256) maxsim_bwd_p_warp_kernel(BwdArgs a, int64_t n_pairs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < n_pairs; t += n_warps) {
+    int lo = 0, hi = a.n_queries - 1;  // query of pair t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.pair_off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int b = lo;
+    const int64_t d = a.pair_ids[t];
+    if (d < 0 || d >= a.n_docs) continue;  // warp-uniform
+    const int64_t q0 = a.q_off[b];
+    const int m_q = (int)(a.q_off[b + 1] - q0);
+    if (m_q < 1 || m_q > 32) continue;
+    const int64_t r0 = a.d_off[d];
+    const float gt = a.g[t];
+    // key = j * 32 + i; rows past m_q sort last
+    uint32_t key = lane < m_q ? ((uint32_t)a.argmax[t * a.max_q_len + lane] << 5) | (uint32_t)lane : 0xFFFFFFFFu;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        const uint32_t other = __shfl_xor_sync(0xffffffffu, key, stride);
+        const bool up = ((lane & size) == 0);
+        const bool lower = ((lane & stride) == 0);
+        key = (lower == up) ? min(key, other) : max(key, other);
+      }
+    }
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = 0; e < m_q; ++e) {
+      const uint32_t ke = __shfl_sync(0xffffffffu, key, e);
+      const uint32_t kn = __shfl_sync(0xffffffffu, key, (e + 1) & 31);
+      const int i = (int)(ke & 31u);
+      const int64_t j = (int64_t)(ke >> 5);
+      const float4 qv = reinterpret_cast<const float4*>(a.q + (q0 + i) * kDim)[lane];
+      acc.x += qv.x; acc.y += qv.y; acc.z += qv.z; acc.w += qv.w;
+      if (e + 1 == m_q || (int64_t)(kn >> 5) != j) {
+        atomicAdd(reinterpret_cast<float4*>(a.grad_docs + (r0 + j) * kDim) + lane,
+                  make_float4(gt * acc.x, gt * acc.y, gt * acc.z, gt * acc.w));
+        acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
+}
+
 }  // namespace
 
 gem_status launch_maxsim_fwd(const float* q, const int64_t* q_off, int32_t n_queries, const float* docs,
@@ -234,7 +285,12 @@ gem_status launch_maxsim_bwd(const float* q, const int64_t* q_off, int32_t n_que
   }
   if (grad_docs) {
     GEM_CUDA_TRY(cudaMemsetAsync(grad_docs, 0, sizeof(float) * n_doc_rows * kDim, st));
-    if (n_pairs > 0) {
+    if (n_pairs > 0 && max_q_len <= 32) {
+      maxsim_bwd_p_warp_kernel<<<(int)std::min<int64_t>((n_pairs + 7) / 8, (int64_t)n_sm * 16), 256, 0, st>>>(
+          a, n_pairs);
+      GEM_CUDA_TRY(cudaGetLastError());
+      note_launches(1);
+    } else if (n_pairs > 0) {
       maxsim_bwd_p_kernel<<<(int)std::min<int64_t>(n_pairs, (int64_t)n_sm * 16), 256, 0, st>>>(a, n_pairs);
       GEM_CUDA_TRY(cudaGetLastError());
       note_launches(1);

@@ -6,16 +6,18 @@
 // FP32 -- the arithmetic of the SIMT forward, with the sum over i taken in a
 // fixed order (a butterfly within each warp of 32 rows, then the warps in order).
 //
-// The query and document rows are first rounded to bf16 into scratch.  Work
-// unit = 16 consecutive pairs; a persistent CTA per SM draws units from a
-// counter.  The query block (A, 128 rows) stays in shared memory while its pairs
-// run; each document is loaded by TMA in boxes of 32 rows (at most 31 rows read
-// past its end) into a two-stage ring of 256-row tiles, and one MMA per K step
-// covers the tile with N = 32 x boxes.  The accumulator (128 query rows x 256
-// rows of the set) is double-buffered in TMEM; four epilogue warps, one thread
-// per query row, take the running max and argmax over the set's valid columns,
-// write the argmax row and add the row maxima (a butterfly per warp, the four
-// warp sums in order through shared memory).
+// The query rows are first rounded to bf16 into scratch.  Work unit = 16
+// consecutive pairs; a persistent CTA per SM draws units from a counter.  The
+// query block (A, 128 rows) stays in shared memory while its pairs run.  Each
+// set is read once, as FP32: TMA brings it in boxes of 32 rows (at most 31 rows
+// read past its end) into a four-slot staging ring, and four converter warps
+// round each box to bf16 into the 128-byte-swizzled operand layout of a
+// two-stage ring of 256-row tiles (a proxy fence makes the writes visible to the
+// tensor cores).  One MMA per K step covers the tile with N = 32 x boxes.  The
+// accumulator (128 query rows x 256 rows of the set) is double-buffered in TMEM;
+// four epilogue warps, one thread per query row, take the running max and argmax
+// over the set's valid columns, write the argmax row and add the row maxima (a
+// butterfly per warp, the four warp sums in order through shared memory).
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -29,13 +31,17 @@ constexpr int kFtBox = 32;                      // rows per TMA box
 constexpr int kFtStages = 2;
 constexpr int kFtPairsPerUnit = 16;
 constexpr int kFtEpiWarps = 4;
-constexpr int kFtThreads = (kFtEpiWarps + 2) * 32;   // + producer, MMA warp
+constexpr int kFtConvWarps = 4;                       // FP32 -> bf16 converters, one staging slot each
+constexpr int kFtConv0 = kFtEpiWarps + 2;             // first converter warp
+constexpr int kFtThreads = (kFtEpiWarps + 2 + kFtConvWarps) * 32;   // + producer, MMA warp, converters
 constexpr int kFtABytes = 128 * kDim * 2;             // 32 KB
 constexpr int kFtStageBytes = kFtN * kDim * 2;        // 64 KB
+constexpr int kFtStgBytes = kFtBox * kDim * 4;        // one FP32 box: 16 KB
 constexpr int kFtUnitRing = 2;
-constexpr int kFtNBars = 2 * kFtStages + 4 + 2 + 1 + 2 * kFtUnitRing + 4;
-constexpr int kFtBarBytes = (kFtNBars * 8 + 16 + 4 * kFtUnitRing + 2 * 4 * 4 + 127) / 128 * 128;
-constexpr int kFtSmem = 1024 + kFtABytes + kFtStages * kFtStageBytes + kFtBarBytes;
+constexpr int kFtNBars = 2 * kFtStages + 4 + 2 + 1 + 2 * kFtUnitRing + 4 + 2 * kFtConvWarps;
+constexpr int kFtBarBytes =
+    (kFtNBars * 8 + 16 + 4 * kFtUnitRing + 2 * 4 * 4 + 2 * 4 * kFtConvWarps + 127) / 128 * 128;
+constexpr int kFtSmem = 1024 + kFtABytes + kFtStages * kFtStageBytes + kFtConvWarps * kFtStgBytes + kFtBarBytes;
 static_assert(kFtSmem <= 232448, "shared memory over the per-block limit");
 
 struct FtArgs {
@@ -118,7 +124,8 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* a_smem = smem;                        // [2 halves][128 rows][128 B]
   uint8_t* b_smem = smem + kFtABytes;            // [stage][2 halves][256 rows][128 B]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(b_smem + kFtStages * kFtStageBytes);
+  uint8_t* stg_smem = b_smem + kFtStages * kFtStageBytes;  // [slot][32 rows][128 FP32]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg_smem + kFtConvWarps * kFtStgBytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + kFtStages;
   uint64_t* acc_full = bars + 2 * kFtStages;     // [2]
@@ -134,6 +141,10 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   volatile int* unit_ring = abort_flag + 1;                               // [UNIT_RING]
   float* parts = const_cast<float*>(reinterpret_cast<volatile float*>(unit_ring + kFtUnitRing));  // [2][4]
+  uint64_t* stg_full = reinterpret_cast<uint64_t*>(
+      (reinterpret_cast<uintptr_t>(parts + 8) + 7) & ~uintptr_t(7));   // [slot]: the FP32 box landed
+  uint64_t* stg_empty = stg_full + kFtConvWarps;                         // [slot]: converted
+  volatile int* stg_desc = reinterpret_cast<volatile int*>(stg_empty + kFtConvWarps);  // [slot][2]: stage, box (-1: stop)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -141,7 +152,10 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
   if (blockIdx.x >= n_units) return;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kFtStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    // full[s]: one arrival per 32-row box of the tile (a converter each, the
+    // producer for the boxes past the set's end)
+    for (int s = 0; s < kFtStages; ++s) { mbar_init(&full[s], kFtN / kFtBox); mbar_init(&empty[s], 1); }
+    for (int c = 0; c < kFtConvWarps; ++c) { mbar_init(&stg_full[c], 1); mbar_init(&stg_empty[c], 1); }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], kFtEpiWarps);
@@ -173,7 +187,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
     }
     int stage = 0;
     uint32_t phase = 0;
-    uint32_t issued[kFtStages] = {};
+    uint64_t n_box = 0;  // FP32 boxes issued (box g goes to staging slot g % kFtConvWarps)
     uint32_t n_a = 0;  // query blocks loaded
     int cur_b = -1;
     bool ok = true;
@@ -214,25 +228,44 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
             const int rows = min(kFtN, p.m_p - tile * kFtN);
             const int nb = (rows + kFtBox - 1) / kFtBox;
             if (!mbar_wait(&empty[stage], phase ^ 1, a.status, abort_flag)) { okl = 0; break; }
-            uint8_t* dst = b_smem + stage * kFtStageBytes;
-            mbar_arrive_expect_tx(&full[stage], nb * kFtBox * kDim * 2);
             const int row0 = (int)(p.r0 + (int64_t)tile * kFtN);
-            for (int bx = 0; bx < nb; ++bx)
-              for (int h = 0; h < 2; ++h)
-                tma_load_2d(dst + h * (kFtN * 128) + bx * (kFtBox * 128), &tm_d, &full[stage], h * 64,
-                            row0 + bx * kFtBox);
-            issued[stage]++;
+            for (int bx = 0; bx < nb && okl; ++bx) {
+              // the box's FP32 rows into the next staging slot; its converter
+              // writes them, rounded, into this stage
+              const int sl = (int)(n_box % kFtConvWarps);
+              const uint32_t use = (uint32_t)(n_box / kFtConvWarps);
+              if (use > 0 && !mbar_wait(&stg_empty[sl], (use - 1) & 1, a.status, abort_flag)) { okl = 0; break; }
+              stg_desc[2 * sl] = stage;
+              stg_desc[2 * sl + 1] = bx;
+              mbar_arrive_expect_tx(&stg_full[sl], kFtStgBytes);
+              tma_load_2d(stg_smem + sl * kFtStgBytes, &tm_d, &stg_full[sl], 0, row0 + bx * kFtBox);
+              ++n_box;
+            }
+            for (int bx = nb; bx < kFtN / kFtBox; ++bx) mbar_arrive(&full[stage]);  // no rows there
             if (++stage == kFtStages) { stage = 0; phase ^= 1; }
           }
         }
         if (!__shfl_sync(0xffffffffu, okl, 0)) ok = false;
       }
     }
-    if (!ok && lane == 0) {
-      for (int s2 = 0; s2 < kFtStages; ++s2)
-        if (issued[s2]) { int z = 0; mbar_wait(&full[s2], (issued[s2] - 1) & 1, nullptr, &z); }
-      int z = 0;
-      if (n_a) mbar_wait(q_full, (n_a - 1) & 1, nullptr, &z);
+    if (lane == 0) {
+      if (ok) {
+        // stop every converter: a descriptor of -1 in its slot, once the slot is free
+        for (int sl = 0; sl < kFtConvWarps; ++sl) {
+          const uint64_t uses = n_box / kFtConvWarps + ((uint64_t)sl < n_box % kFtConvWarps ? 1 : 0);
+          if (uses > 0 && !mbar_wait(&stg_empty[sl], (uint32_t)((uses - 1) & 1), a.status, abort_flag)) break;
+          stg_desc[2 * sl] = -1;
+          mbar_arrive(&stg_full[sl]);
+        }
+      } else {
+        // drain: every load this thread issued must land before the CTA exits
+        for (int sl = 0; sl < kFtConvWarps; ++sl) {
+          const uint64_t uses = n_box / kFtConvWarps + ((uint64_t)sl < n_box % kFtConvWarps ? 1 : 0);
+          if (uses) { int z = 0; mbar_wait(&stg_full[sl], (uint32_t)((uses - 1) & 1), nullptr, &z); }
+        }
+        int z = 0;
+        if (n_a) mbar_wait(q_full, (n_a - 1) & 1, nullptr, &z);
+      }
     }
   } else if (warp == kFtEpiWarps + 1) {
     // ------------------------------------------------------------------ MMA issuer
@@ -299,6 +332,40 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
       mma_commit(done_bar);
       int z = 0;
       mbar_wait(done_bar, 0, nullptr, &z);
+    }
+  } else if (warp >= kFtConv0) {
+    // ------------------------------------------------------------------ converters
+    // warp c takes staging slot c: 32 FP32 rows -> bf16 (nearest even) at rows
+    // 32 box .. 32 box + 31 of its stage, in the 128-byte swizzle (16-byte chunk
+    // index XOR row % 8) the MMA descriptors expect
+    const int sl = warp - kFtConv0;
+    const float* stg = reinterpret_cast<const float*>(stg_smem + sl * kFtStgBytes);
+    const int h = lane >> 4;                 // component half of this lane's 4 floats
+    const int cc = (lane & 15) >> 1;         // 16-byte chunk within the half
+    for (uint32_t n = 0;; ++n) {
+      const bool w = mbar_wait(&stg_full[sl], n & 1, a.status, abort_flag);
+      if (!__all_sync(0xffffffffu, w)) break;
+      const int st_i = stg_desc[2 * sl];
+      const int bx = stg_desc[2 * sl + 1];
+      if (st_i < 0) break;
+      uint8_t* dst = b_smem + st_i * kFtStageBytes + h * (kFtN * 128) + (lane & 1) * 8;
+#pragma unroll 4
+      for (int r = 0; r < kFtBox; ++r) {
+        const float4 x = reinterpret_cast<const float4*>(stg + r * kDim)[lane];
+        uint2 o;
+        o.x = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x.x)) |
+              ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x.y)) << 16);
+        o.y = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x.z)) |
+              ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x.w)) << 16);
+        const int R = bx * kFtBox + r;
+        *reinterpret_cast<uint2*>(dst + R * 128 + ((cc ^ (R & 7)) << 4)) = o;
+      }
+      fence_proxy_async_shared();   // the writes, visible to the tensor cores
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&stg_empty[sl]);
+        mbar_arrive(&full[st_i]);
+      }
     }
   } else {
     // ------------------------------------------------------------------ epilogue
@@ -422,16 +489,15 @@ gem_status launch_maxsim_fwd_tc(const float* q, const int64_t* q_off, int32_t n_
   if (n_q_rows >= ((int64_t)1 << 31) || n_doc_rows >= ((int64_t)1 << 31))
     return fail(GEM_ERR_INVALID, "too many rows");
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t qb = up((size_t)n_q_rows * kDim * 2), db = up((size_t)n_doc_rows * kDim * 2);
+  const size_t qb = up((size_t)n_q_rows * kDim * 2);
   uint8_t* base = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), qb + db + 256, st);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), qb + 256, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(GEM_ERR_OOM, "scratch of the tensor-core forward");
   }
   auto* qh = reinterpret_cast<__nv_bfloat16*>(base);
-  auto* dh = reinterpret_cast<__nv_bfloat16*>(base + qb);
-  int* counter = reinterpret_cast<int*>(base + qb + db);
+  int* counter = reinterpret_cast<int*>(base + qb);
   auto done = [&](gem_status r) {
     cudaFreeAsync(base, st);
     return r;
@@ -439,8 +505,8 @@ gem_status launch_maxsim_fwd_tc(const float* q, const int64_t* q_off, int32_t n_
   CUtensorMap tm_q, tm_d;
   if (!encode_tmap_2d(&tm_q, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, qh, kDim, (uint64_t)n_q_rows, kDim * 2, 64, 128,
                       CU_TENSOR_MAP_SWIZZLE_128B) ||
-      !encode_tmap_2d(&tm_d, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, dh, kDim, (uint64_t)n_doc_rows, kDim * 2, 64, kFtBox,
-                      CU_TENSOR_MAP_SWIZZLE_128B))
+      !encode_tmap_2d(&tm_d, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, const_cast<float*>(docs), kDim, (uint64_t)n_doc_rows,
+                      kDim * 4, kDim, kFtBox, CU_TENSOR_MAP_SWIZZLE_NONE))
     return done(fail(GEM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the forward operands"));
   static bool attr_set = false;
   if (!attr_set) {
@@ -448,9 +514,8 @@ gem_status launch_maxsim_fwd_tc(const float* q, const int64_t* q_off, int32_t n_
     if (e != cudaSuccess) return done(cuda_fail(e, "cudaFuncSetAttribute"));
     attr_set = true;
   }
-  const int64_t nq4 = n_q_rows * kDim / 4, nd4 = n_doc_rows * kDim / 4;
+  const int64_t nq4 = n_q_rows * kDim / 4;
   to_bf16_kernel<<<(int)std::min<int64_t>((nq4 + 255) / 256, n_sm * 16LL), 256, 0, st>>>(q, nq4, qh);
-  to_bf16_kernel<<<(int)std::min<int64_t>((nd4 + 255) / 256, n_sm * 16LL), 256, 0, st>>>(docs, nd4, dh);
   e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return done(cuda_fail(e, "cudaMemsetAsync"));
   FtArgs aa;
@@ -469,7 +534,7 @@ gem_status launch_maxsim_fwd_tc(const float* q, const int64_t* q_off, int32_t n_
   const int64_t units = (n_pairs + kFtPairsPerUnit - 1) / kFtPairsPerUnit;
   fwd_tc_kernel<<<(unsigned)std::min<int64_t>(units, n_sm), kFtThreads, kFtSmem, st>>>(tm_q, tm_d, aa);
   e = cudaGetLastError();
-  note_launches(3);
+  note_launches(2);
   if (e != cudaSuccess) return done(cuda_fail(e, "fwd_tc_kernel"));
   return done(GEM_OK);
 }

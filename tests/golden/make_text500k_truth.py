@@ -53,6 +53,8 @@ def main():
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "text500k_truth.npz"))
     args = ap.parse_args()
     t0 = time.time()
+    import torch
+    torch.set_num_threads(os.cpu_count())     # the data draw uses every core; the workers' BLAS one each
     w = synth.text_corpus(seed=1236, n_queries=args.queries, device="cpu")
     fp = synth.fingerprint(w.docs, w.queries)
     print(f"data drawn in {time.time() - t0:.0f} s, fingerprint {fp}", flush=True)
