@@ -21,7 +21,8 @@ Contents and the passage each follows:
   qch_asym_*                      Eq. 16 with only the stored side quantized (a variant)
   emd_cost, emd, qemd             Sec. 4.2.1-4.2.2 (Eq. 11-14): EMD with uniform marginals, exact LP (HiGHS)
   k1_for                          Sec. 5.1 parameter settings: |C_quant| = 2^floor(log2(16 sqrt(#vectors)))
-  bf16_round, fp8_e4m3_quantize   storage formats of the low-precision path (not in the paper)
+  bf16_round, fp8_e4m3_quantize, fp8_e4m3_quantize_sets
+                                  storage formats of the low-precision path (not in the paper)
   maxsim_grad, contrastive_*      gradient of Eq. 1 (not in the paper)
   kmeans_update                   Sec. 4.1.1, one Lloyd update of the stage-1 k-means
 
@@ -36,6 +37,6 @@ from .maxsim import (  # noqa: F401
     assign_codes, cluster_filter, cluster_members, entry_points, entry_hash, splitmix64_next, beam_search,
     qch_distance, qch_similarity, qch_score_all, qch_score_ids, qch_asym_similarity, qch_asym_score_all, k1_for,
     emd_cost, emd, qemd,
-    bf16_round, fp8_e4m3_round, fp8_e4m3_quantize,
+    bf16_round, fp8_e4m3_round, fp8_e4m3_quantize, fp8_e4m3_quantize_sets,
     maxsim_grad, contrastive_loss, contrastive_dscores, kmeans_update,
 )

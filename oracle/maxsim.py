@@ -522,6 +522,30 @@ def fp8_e4m3_quantize(X):
     return fp8_e4m3_round(ratio.astype(np.float64)), scale
 
 
+def fp8_e4m3_quantize_sets(X, offsets):
+    """Per-set scaled E4M3 storage: set n gets one scale s_n, the smallest power of
+    two not below 2^-126 with max |x| over the set's rows <= 448 s_n (1 for an
+    all-zero set); code = E4M3(x / s_n), round to nearest even.  Dividing by a
+    power of two is exact, so the only rounding is E4M3's.  Returns (codes float64
+    [n, d] holding the E4M3 values, set scales float32 [n_sets]); the dequantised
+    row j of set n is codes[j] * s_n.  Because s_n > 0 is common to the set,
+    max_j <q, codes_j * s_n> = s_n * max_j <q, codes_j> (Eq. 1's inner max)."""
+    X = np.asarray(X, dtype=np.float32).astype(np.float64)
+    off = _i64(offsets)
+    scales = np.ones(len(off) - 1, dtype=np.float32)
+    codes = np.zeros_like(X)
+    for n in range(len(off) - 1):
+        rows = X[off[n]:off[n + 1]]
+        amax = np.abs(rows).max() if rows.size else 0.0
+        if amax > 0:
+            k = -126
+            while amax > FP8_E4M3_MAX * 2.0 ** k:
+                k += 1
+            scales[n] = 2.0 ** k
+        codes[off[n]:off[n + 1]] = fp8_e4m3_round(rows / float(scales[n]))
+    return codes, scales
+
+
 # ---------------------------------------------------------------------------
 # Gradient of Eq. 1 and the contrastive loss used to exercise it
 # ---------------------------------------------------------------------------

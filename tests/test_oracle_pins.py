@@ -369,6 +369,48 @@ def test_fp8_quantize_scales_and_error_bound():
     assert s0[0] == 1.0 and np.all(c0 == 0)
 
 
+def test_fp8_quantize_sets_scale_rule_and_codes():
+    """Per-set power-of-two scales: hand cases at the boundaries of the rule, the
+    codes against torch's own E4M3 conversion of x / s, and the scale against a
+    search over exponents written with math.ldexp."""
+    import math
+    rows = np.array([[448.0, -1.0], [3.0, 0.0],          # set 0: max 448 -> s = 1
+                     [-449.0, 0.5],                      # set 1: max 449 -> s = 2
+                     [224.0, 10.0],                      # set 2: max 224 -> s = 1/2 (224 <= 448/2)
+                     [0.0, 0.0], [0.0, -0.0],            # set 3: zero set -> s = 1
+                     [1e-40, 0.0],                       # set 4: subnormal max -> s = 2^-126
+                     [224.5, 0.0]], np.float32)          # set 5: just above 224 -> s = 1
+    off = np.array([0, 2, 3, 4, 6, 7, 8])
+    codes, s = oracle.fp8_e4m3_quantize_sets(rows, off)
+    assert s.tolist() == [1.0, 2.0, 0.5, 1.0, 2.0 ** -126, 1.0]
+    assert codes[2].tolist() == [-224.0, 0.25] and codes[3].tolist() == [448.0, 20.0]
+    assert codes[7].tolist() == [224.0, 0.0]            # 224.5 rounds to the E4M3 grid (spacing 32)
+    assert np.all(codes[4:6] == 0)
+    rng = np.random.default_rng(21)
+    lens = rng.integers(1, 40, 300)
+    off = np.concatenate([[0], np.cumsum(lens)])
+    X = (rng.standard_normal((off[-1], 128)) * np.repeat(10.0 ** rng.uniform(-30, 30, 300), lens)[:, None])
+    X = X.astype(np.float32)
+    codes, s = oracle.fp8_e4m3_quantize_sets(X, off)
+    for n in range(300):
+        a = float(np.abs(X[off[n]:off[n + 1]]).max())
+        k = next(k for k in range(-126, 129) if a <= 448.0 * math.ldexp(1.0, k))
+        assert s[n] == math.ldexp(1.0, k)
+        amax_code = np.abs(codes[off[n]:off[n + 1]]).max()
+        assert amax_code <= 448.0 and (k == -126 or amax_code > 224.0 - 16.0)
+        want = torch.from_numpy(X[off[n]:off[n + 1]] / s[n]).to(torch.float8_e4m3fn).double().numpy()
+        np.testing.assert_array_equal(codes[off[n]:off[n + 1]], want)
+    # dequantisation error: half a spacing of E4M3 relative to the set's scale
+    sv = np.repeat(s, lens)[:, None].astype(np.float64)
+    deq = codes * sv
+    assert np.all(np.abs(deq - X) <= np.maximum(np.abs(X) * 2.0 ** -4, sv * 2.0 ** -10) * (1 + 1e-12))
+    # the common scale leaves the argmax of Eq. 1's inner max unchanged
+    q = rng.standard_normal(128)
+    for n in range(0, 300, 37):
+        blk = codes[off[n]:off[n + 1]]
+        assert np.max(blk @ q) * s[n] == np.max((blk * float(s[n])) @ q)
+
+
 # --------------------------------------------------------------------------- gradients
 
 def test_maxsim_grad_euler_identity_and_finite_differences():
