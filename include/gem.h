@@ -56,8 +56,11 @@ typedef enum {
   GEM_F32 = 0,      /* FP32 SIMT, fixed summation order, Kahan sum over query vectors */
   GEM_BF16 = 1,     /* BF16 operands on tcgen05 tensor cores, FP32 accumulation */
   GEM_FP8_E4M3 = 2, /* E4M3 operands with per-vector FP32 scales, FP32 accumulation */
-  GEM_CODES = 3     /* id lists only: the GEM_F32 arithmetic with every query and stored
+  GEM_CODES = 3,    /* id lists only: the GEM_F32 arithmetic with every query and stored
                        vector replaced by its centroid (the quantized estimate) */
+  GEM_FP8_E4M3_SET = 4  /* E4M3 operands, one power-of-two scale per stored set (per-vector
+                           scales for the query rows), FP32 accumulation: the set's scale
+                           multiplies once per set instead of once per stored vector */
 } gem_dtype;
 
 /* Launch variants of the tensor-core scoring kernels (gem_workspace_set_schedule). */
@@ -84,7 +87,10 @@ typedef enum {
 enum {
   GEM_KEEP_F32 = 1u,   /* FP32 master copy (needed by GEM_F32 scoring and the rerank) */
   GEM_KEEP_BF16 = 2u,  /* BF16, round to nearest even */
-  GEM_KEEP_FP8 = 4u    /* E4M3 codes + per-vector FP32 scale s_j = max_k |x_jk| / 448 */
+  GEM_KEEP_FP8 = 4u,   /* E4M3 codes + per-vector FP32 scale s_j = max_k |x_jk| / 448 */
+  GEM_KEEP_FP8_SET = 8u /* E4M3 codes + one scale per set: the smallest power of two s
+                           (>= FLT_MIN) with max |x| over the set <= 448 s (1 for a zero
+                           set); x / s is exact and only the E4M3 rounding remains */
 };
 
 /* Internal arrays a store can copy out (gem_store_export).  The bf16 and
@@ -103,7 +109,9 @@ enum {
   GEM_EXPORT_INDEX_CODES = 7, /* int32  [n_vecs] nearest C_index centroid of every stored vector */
   GEM_EXPORT_F32 = 8,         /* float  [n_vecs * 128] FP32 master copy (original row order) */
   GEM_EXPORT_INDEX_CENTROIDS = 9, /* float [k2 * 128] centroids of C_index */
-  GEM_EXPORT_DELETED = 10     /* uint32 [ceil(n_sets / 32)] deletion bitmap (all zero if none) */
+  GEM_EXPORT_DELETED = 10,    /* uint32 [ceil(n_sets / 32)] deletion bitmap (all zero if none) */
+  GEM_EXPORT_FP8_SET = 11,    /* uint8  [n_pad_vecs * 128] E4M3 bit patterns of the per-set-scale copy */
+  GEM_EXPORT_SET_SCALE = 12   /* float  [n_sets] the per-set scales of that copy */
 };
 
 typedef struct gem_store gem_store;
@@ -402,8 +410,8 @@ gem_status gem_workspace_set_schedule(gem_workspace* ws, int32_t m_tiles, int32_
  * the scores ranked by Eq. 2).
  *   q          float32 [n_q_rows * 128] query vectors, CSR by q_offsets
  *   q_offsets  int64 [n_queries + 1] (device), q_offsets[n_queries] == n_q_rows
- *   compute    GEM_F32 (FP32 SIMT), GEM_BF16 or GEM_FP8_E4M3 (tensor cores;
- *              the store must keep that copy)
+ *   compute    GEM_F32 (FP32 SIMT), GEM_BF16, GEM_FP8_E4M3 or GEM_FP8_E4M3_SET
+ *              (tensor cores; the store must keep that copy)
  *   scores     float32 [n_queries * n_sets], row-major: scores[b * n_sets + n]
  */
 gem_status gem_score_all(const gem_store* store, gem_workspace* ws, const float* q,
@@ -464,7 +472,8 @@ gem_status gem_topk(gem_workspace* ws, const float* scores, const int64_t* row_o
  * rerank_depth > 0.  Deleted sets (gem_store_mark_deleted) are scored but never
  * returned.  out_ids int64 [n_queries * k], out_scores float32 [n_queries * k].
  * compute:
- *   GEM_F32, GEM_BF16, GEM_FP8_E4M3  the first pass is exact CH in that arithmetic
+ *   GEM_F32, GEM_BF16, GEM_FP8_E4M3, GEM_FP8_E4M3_SET
+ *                                    the first pass is exact CH in that arithmetic
  *                                    (as gem_score_all);
  *   GEM_CODES                        the first pass is the quantized estimate qsim
  *                                    (Sec. 4.5.3, Eq. 16; as gem_estimate_codes over

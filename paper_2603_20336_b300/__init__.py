@@ -28,8 +28,8 @@ if not os.path.exists(_LIB_PATH):
 lib = ctypes.CDLL(_LIB_PATH)
 _abi.declare(lib)
 
-DTYPES = {"f32": 0, "bf16": 1, "fp8": 2, "codes": 3}
-KEEP = {"f32": 1, "bf16": 2, "fp8": 4}
+DTYPES = {"f32": 0, "bf16": 1, "fp8": 2, "codes": 3, "fp8_set": 4}
+KEEP = {"f32": 1, "bf16": 2, "fp8": 4, "fp8_set": 8}
 STATUS = {0: "GEM_OK", 1: "GEM_ERR_INVALID", 2: "GEM_ERR_OOM", 3: "GEM_ERR_CUDA", 4: "GEM_ERR_TIMEOUT",
           5: "GEM_ERR_UNSUPPORTED", 6: "GEM_ERR_STATE", 7: "GEM_ERR_BOUNDS"}
 
@@ -121,8 +121,9 @@ class Store:
 
     def export(self, what: str, stream=None) -> torch.Tensor:
         """Copy of an internal array: 'bf16' (uint16 bits, padded layout), 'fp8'
-        (uint8 bits, padded), 'fp8_scale' (float32, padded), 'offsets' or
-        'pad_offsets' (int64)."""
+        (uint8 bits, padded), 'fp8_scale' (float32, padded), 'fp8_set' (uint8
+        bits of the per-set-scale copy, padded), 'set_scale' (float32 per set),
+        'offsets' or 'pad_offsets' (int64)."""
         P = self.n_pad_vecs
         spec = {"bf16": (0, torch.int16, (P, 128)), "fp8": (1, torch.uint8, (P, 128)),
                 "fp8_scale": (2, torch.float32, (P,)), "offsets": (3, torch.int64, (self.n_sets + 1,)),
@@ -132,7 +133,9 @@ class Store:
                 "index_codes": (7, torch.int32, (self.n_vecs,)),
                 "f32": (8, torch.float32, (self.n_vecs, 128)),
                 "index_centroids": (9, torch.float32, (getattr(self, "k2", 0), 128)),
-                "deleted": (10, torch.int32, ((self.n_sets + 31) // 32,))}
+                "deleted": (10, torch.int32, ((self.n_sets + 31) // 32,)),
+                "fp8_set": (11, torch.uint8, (P, 128)),
+                "set_scale": (12, torch.float32, (self.n_sets,))}
         code, dt, shape = spec[what]
         out = torch.empty(shape, dtype=dt, device="cuda")
         _check(lib.gem_store_export(self.handle, code, _ptr(out), out.numel() * out.element_size(),

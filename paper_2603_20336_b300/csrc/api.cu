@@ -98,6 +98,8 @@ void gem_store_destroy(gem_store* s) {
   dfree(s->d_bf16);
   dfree(s->d_fp8);
   dfree(s->d_fp8_scale);
+  dfree(s->d_fp8s);
+  dfree(s->d_set_scale);
   dfree(s->d_codebook);
   dfree(s->d_codes);
   dfree(s->d_cindex);
@@ -117,7 +119,7 @@ gem_status gem_store_create(const float* vecs, const int64_t* offsets, int64_t n
   if (!vecs || !offsets) return fail(GEM_ERR_INVALID, "vecs/offsets is NULL");
   if (n_sets < 1 || n_sets >= (int64_t)1 << 31) return fail(GEM_ERR_INVALID, "n_sets out of range");
   if (dim != kDim) return fail(GEM_ERR_UNSUPPORTED, "only dim = 128 is supported");
-  if (keep_mask == 0 || (keep_mask & ~7u)) return fail(GEM_ERR_INVALID, "bad keep_mask");
+  if (keep_mask == 0 || (keep_mask & ~15u)) return fail(GEM_ERR_INVALID, "bad keep_mask");
   int dev = 0;
   GEM_CUDA_TRY(cudaGetDevice(&dev));
   if (!device_is_sm103(dev)) return fail(GEM_ERR_UNSUPPORTED, "device is not sm_103 (B300)");
@@ -211,6 +213,12 @@ gem_status gem_store_create(const float* vecs, const int64_t* offsets, int64_t n
       e = cudaGetLastError();
     }
   }
+  if (e == cudaSuccess && (keep_mask & GEM_KEEP_FP8_SET)) {
+    if ((r = dmalloc(&s->d_fp8s, VP * kDim, "per-set fp8 copy")) != GEM_OK) { dfree(tmp); gem_store_destroy(s); return r; }
+    if ((r = dmalloc(&s->d_set_scale, n_sets, "set scales")) != GEM_OK) { dfree(tmp); gem_store_destroy(s); return r; }
+    launch_quantize_fp8_set(src, s->d_offsets, s->d_pad_offsets, n_sets, s->d_fp8s, s->d_set_scale, st);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   dfree(tmp);
   if (e != cudaSuccess) { gem_store_destroy(s); return cuda_fail(e, "building the store"); }
@@ -243,6 +251,8 @@ gem_status gem_store_export(const gem_store* s, int32_t what, void* dst, size_t 
     case GEM_EXPORT_INDEX_CODES: src = s->d_icodes; bytes = sizeof(int32_t) * s->n_vecs; break;
     case GEM_EXPORT_F32: src = s->d_f32; bytes = sizeof(float) * s->n_vecs * kDim; break;
     case GEM_EXPORT_INDEX_CENTROIDS: src = s->d_cindex; bytes = sizeof(float) * (size_t)s->k2 * kDim; break;
+    case GEM_EXPORT_FP8_SET: src = s->d_fp8s; bytes = (size_t)s->n_pad_vecs * kDim; break;
+    case GEM_EXPORT_SET_SCALE: src = s->d_set_scale; bytes = sizeof(float) * s->n_sets; break;
     case GEM_EXPORT_DELETED: {
       bytes = sizeof(uint32_t) * (size_t)((s->n_sets + 31) / 32);
       if (dst_bytes < bytes) return fail(GEM_ERR_INVALID, "dst too small");
@@ -319,7 +329,7 @@ gem_status gem_workspace_create(const gem_store* s, int32_t max_queries, int64_t
   WS_ALLOC(d_part_row0, w->max_parts);
   WS_ALLOC(d_row_part, w->packed_cap);
   if (s->d_bf16) WS_ALLOC(d_qpack_bf16, w->packed_cap * kDim);
-  if (s->d_fp8) {
+  if (s->d_fp8 || s->d_fp8s) {
     WS_ALLOC(d_qpack_fp8, w->packed_cap * kDim);
     WS_ALLOC(d_qpack_scale, w->packed_cap);
   }
@@ -609,7 +619,7 @@ static gem_status score_all_impl(const gem_store* s, gem_workspace* w, const flo
     if (!s->d_f32) return fail(GEM_ERR_STATE, "store keeps no fp32 copy");
     return launch_f32_score(s, w, q, q_offsets, n_queries, nullptr, nullptr, 0, scores, st);
   }
-  if (w->sim == GEM_SIM_L2 && (compute == GEM_BF16 || compute == GEM_FP8_E4M3))
+  if (w->sim == GEM_SIM_L2 && (compute == GEM_BF16 || compute == GEM_FP8_E4M3 || compute == GEM_FP8_E4M3_SET))
     return fail(GEM_ERR_UNSUPPORTED, "Sim = L2 distance is scored by GEM_F32 only");
   if (compute == GEM_BF16) {
     if (!s->d_bf16) return fail(GEM_ERR_STATE, "store keeps no bf16 copy");
@@ -618,10 +628,12 @@ static gem_status score_all_impl(const gem_store* s, gem_workspace* w, const flo
     if (r != GEM_OK) return r;
     return launch_tc_score_all(s, w, compute, mt, w->tc_variant, w->tc_chunk_rows, scores, st);
   }
-  if (compute == GEM_FP8_E4M3) {
-    if (!s->d_fp8) return fail(GEM_ERR_STATE, "store keeps no fp8 copy");
+  if (compute == GEM_FP8_E4M3 || compute == GEM_FP8_E4M3_SET) {
+    if (compute == GEM_FP8_E4M3 && !s->d_fp8) return fail(GEM_ERR_STATE, "store keeps no fp8 copy");
+    if (compute == GEM_FP8_E4M3_SET && !s->d_fp8s) return fail(GEM_ERR_STATE, "store keeps no per-set-scale fp8 copy");
     const int mt = w->tc_m_tiles;
-    gem_status r = launch_plan(w, q, q_offsets, n_queries, n_q_rows, 128 * mt, compute, st);
+    // the query rows take per-row E4M3 scales in both forms
+    gem_status r = launch_plan(w, q, q_offsets, n_queries, n_q_rows, 128 * mt, GEM_FP8_E4M3, st);
     if (r != GEM_OK) return r;
     return launch_tc_score_all(s, w, compute, mt, w->tc_variant, w->tc_chunk_rows, scores, st);
   }
@@ -665,7 +677,7 @@ gem_status gem_score_ids(const gem_store* s, gem_workspace* w, const float* q,
     return launch_f32_score(s, w, q, q_offsets, n_queries, cand_offsets, cand_ids, n_cands, scores, st,
                             w->d_qcodes);
   }
-  if (compute == GEM_BF16 || compute == GEM_FP8_E4M3)
+  if (compute == GEM_BF16 || compute == GEM_FP8_E4M3 || compute == GEM_FP8_E4M3_SET)
     return fail(GEM_ERR_UNSUPPORTED, "id-list scoring runs in GEM_F32 or GEM_CODES");
   return fail(GEM_ERR_INVALID, "unknown compute dtype");
 }
@@ -903,7 +915,9 @@ gem_status gem_autotune_score_all(const gem_store* s, gem_workspace* w, const fl
     return fail(GEM_ERR_INVALID, "NULL argument");
   if (compute == GEM_BF16 && !s->d_bf16) return fail(GEM_ERR_STATE, "store keeps no bf16 copy");
   if (compute == GEM_FP8_E4M3 && !s->d_fp8) return fail(GEM_ERR_STATE, "store keeps no fp8 copy");
-  if (compute != GEM_BF16 && compute != GEM_FP8_E4M3) return fail(GEM_ERR_INVALID, "compute must be bf16 or fp8");
+  if (compute == GEM_FP8_E4M3_SET && !s->d_fp8s) return fail(GEM_ERR_STATE, "store keeps no per-set-scale fp8 copy");
+  if (compute != GEM_BF16 && compute != GEM_FP8_E4M3 && compute != GEM_FP8_E4M3_SET)
+    return fail(GEM_ERR_INVALID, "compute must be bf16 or fp8");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   r = autotune_score_all(s, w, q, q_offsets, n_queries, n_q_rows, compute, scores, cache_path, m_tiles, variant,
                          chunk_rows, ms, from_cache, st);

@@ -175,7 +175,8 @@ gem_status autotune_score_all(const gem_store* s, gem_workspace* w, const float*
       double ms = 0.0;
       gem_status r = time_ms(
           [&]() {
-            gem_status rr = launch_plan(w, q, q_offsets, n_queries, n_q_rows, 128 * mt, compute, st);
+            gem_status rr = launch_plan(w, q, q_offsets, n_queries, n_q_rows, 128 * mt,
+                                        compute == GEM_BF16 ? GEM_BF16 : GEM_FP8_E4M3, st);
             if (rr == GEM_OK) rr = launch_tc_score_all(s, w, compute, mt, at, cr, scores, st);
             return rr;
           },

@@ -349,16 +349,22 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
       const int bx = stg_desc[2 * sl + 1];
       if (st_i < 0) break;
       uint8_t* dst = b_smem + st_i * kFtStageBytes + h * (kFtN * 128) + (lane & 1) * 8;
-#pragma unroll 4
-      for (int r = 0; r < kFtBox; ++r) {
-        const float4 x = reinterpret_cast<const float4*>(stg + r * kDim)[lane];
-        uint2 o;
-        o.x = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x.x)) |
-              ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x.y)) << 16);
-        o.y = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x.z)) |
-              ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x.w)) << 16);
-        const int R = bx * kFtBox + r;
-        *reinterpret_cast<uint2*>(dst + R * 128 + ((cc ^ (R & 7)) << 4)) = o;
+      // eight rows' loads in flight before their conversions and stores
+#pragma unroll 1
+      for (int r0 = 0; r0 < kFtBox; r0 += 8) {
+        float4 x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = reinterpret_cast<const float4*>(stg + (r0 + u) * kDim)[lane];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          uint2 o;
+          o.x = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[u].x)) |
+                ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[u].y)) << 16);
+          o.y = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[u].z)) |
+                ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[u].w)) << 16);
+          const int R = bx * kFtBox + r0 + u;
+          *reinterpret_cast<uint2*>(dst + R * 128 + ((cc ^ (R & 7)) << 4)) = o;
+        }
       }
       fence_proxy_async_shared();   // the writes, visible to the tensor cores
       __syncwarp();

@@ -66,6 +66,9 @@ struct gem_store {
   __nv_bfloat16* d_bf16 = nullptr;
   uint8_t* d_fp8 = nullptr;
   float* d_fp8_scale = nullptr;
+  // E4M3 with one power-of-two scale per set (padded layout as d_fp8)
+  uint8_t* d_fp8s = nullptr;
+  float* d_set_scale = nullptr;   // [n_sets]
   int64_t max_set_len = 0;
   // stage-1 codebook C_quant and the codes NN(p) of every stored vector
   int k1 = 0;
@@ -86,6 +89,7 @@ struct gem_store {
   mutable std::map<int, CUtensorMap> tmap_bf16;
   mutable std::map<int, CUtensorMap> tmap_fp8;
   mutable std::map<int, CUtensorMap> tmap_fp8_scale;
+  mutable std::map<int, CUtensorMap> tmap_fp8s;
   mutable std::map<int, gem::ChunkMap> chunks;
 };
 
@@ -211,6 +215,7 @@ gem_status store_chunk_map(const gem_store* s, int chunk_rows, const ChunkMap** 
 gem_status store_tmap_bf16(const gem_store* s, int box_rows, const CUtensorMap** out);
 gem_status store_tmap_fp8(const gem_store* s, int box_rows, const CUtensorMap** out);
 gem_status store_tmap_fp8_scale(const gem_store* s, int box_rows, const CUtensorMap** out);
+gem_status store_tmap_fp8_set(const gem_store* s, int box_rows, const CUtensorMap** out);
 
 // ---------------------------------------------------------------- launchers
 // Query plan: split sets into <= 32-row parts, pack them into m_res-row blocks
@@ -338,6 +343,8 @@ void launch_quantize_bf16(const float* src, const int64_t* off, const int64_t* p
                           int64_t n_sets, __nv_bfloat16* dst, cudaStream_t st);
 void launch_quantize_fp8(const float* src, const int64_t* off, const int64_t* pad_off,
                          int64_t n_sets, uint8_t* dst, float* scale, cudaStream_t st);
+void launch_quantize_fp8_set(const float* src, const int64_t* off, const int64_t* pad_off,
+                             int64_t n_sets, uint8_t* dst, float* set_scale, cudaStream_t st);
 
 // Build the uniform rerank-pool offsets b * depth.
 void launch_iota_offsets(int64_t* off, int32_t n, int64_t step, cudaStream_t st);

@@ -44,7 +44,10 @@ namespace {
 // every unit (E = 2: each set owns one accumulator buffer), so more warps hide
 // the epilogue's latencies; the running max of a set that crosses a tile
 // boundary passes from set to set through shared memory.
-template <int MT, bool FP8, bool AT = false, int E = 1>
+// SS (with FP8): the stored sets carry one power-of-two scale each (the
+// per-set-scale copy): no per-column scale ring, the set's scale multiplies the
+// row maxima once at the set's end.
+template <int MT, bool FP8, bool AT = false, int E = 1, bool SS = false>
 struct TcCfg {
   static constexpr int M_RES = 128 * MT;
   static constexpr int A_COLS = AT ? (FP8 ? 32 : 64) : 0;  // TMEM columns of A per M tile
@@ -63,7 +66,7 @@ struct TcCfg {
                                    : (MT == 1) ? (FP8 ? 6 : 3) : (MT == 2 ? (FP8 ? 8 : 4) : (FP8 ? 12 : 6));
   // fp8: per-column dequantisation scales of each tile, in a ring of their own
   // (the operand stage is recycled as soon as the MMA has read it)
-  static constexpr int SC_SLOTS = FP8 ? 8 : 0;
+  static constexpr int SC_SLOTS = (FP8 && !SS) ? 8 : 0;
   static constexpr int SC_BYTES = SC_SLOTS * N * 4;
   static constexpr int EPI_SET = 4 * MT;          // epilogue warps per set
   static constexpr int EPI_WARPS = E * EPI_SET;
@@ -104,6 +107,7 @@ struct TcArgs {
   int pass;
   int64_t n_sets;
   float* scores;             // [n_queries * n_sets]
+  const float* set_scale;    // SS: [n_sets]
   int* status;
   int* unit_counter;         // next unit to hand out (zeroed before every launch)
 };
@@ -126,11 +130,12 @@ __device__ __forceinline__ float pick(const float (&o)[L], int s) {
   return a[0];
 }
 
-template <int MT, bool FP8, bool AT, int E>
-__global__ void __launch_bounds__(TcCfg<MT, FP8, AT, E>::THREADS, 1)
+template <int MT, bool FP8, bool AT, int E, bool SS>
+__global__ void __launch_bounds__(TcCfg<MT, FP8, AT, E, SS>::THREADS, 1)
 tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ CUtensorMap tm_d,
                     const __grid_constant__ CUtensorMap tm_scale, TcArgs a) {
-  using C = TcCfg<MT, FP8, AT, E>;
+  using C = TcCfg<MT, FP8, AT, E, SS>;
+  constexpr bool COL_SCALE = FP8 && !SS;  // a scale per stored vector (column)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* q_smem = smem;
@@ -242,7 +247,7 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
             tma_load_2d(dst + h * (C::N * 128), &tm_d, &full[stage], h * 64, row);
           issued[stage]++;
           if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
-          if constexpr (FP8) {
+          if constexpr (COL_SCALE) {
             // the tile's column scales (row is a multiple of 8: 16-byte aligned)
             if (!mbar_wait(&sc_empty[sslot], sphase ^ 1, a.status, abort_flag)) { ok = false; break; }
             mbar_arrive_expect_tx(&sc_full[sslot], C::N * 4);
@@ -440,8 +445,9 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
       // summed in 2^-24 fixed point by one warp reduction (|sum| < 2^30, exact
       // and independent of the order; rounding <= 2^-25 per row), any other
       // slot by a g-lane xor butterfly.
-      auto set_end = [&](float m) {
-        const float val = m * row_scale;
+      auto set_end = [&](float m, float set_sc) {
+        float val = m * row_scale;
+        if constexpr (SS) val *= set_sc;
         float sum;
         if (__all_sync(0xffffffffu, g == 32 && fabsf(val) < 2.f)) {
           sum = (float)__reduce_add_sync(0xffffffffu, __float2int_rn(val * 16777216.f)) * (1.f / 16777216.f);
@@ -472,7 +478,7 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
 #pragma unroll
         for (int s = 0; s < CH / 8; ++s) {
           float x[8];
-          if constexpr (FP8) {
+          if constexpr (COL_SCALE) {
             const float4 s0 = reinterpret_cast<const float4*>(sc)[2 * s];
             const float4 s1 = reinterpret_cast<const float4*>(sc)[2 * s + 1];
             const float2 p0 = fmul2(make_float2(v[8 * s + 0], v[8 * s + 1]), make_float2(s0.x, s0.y));
@@ -528,20 +534,30 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
         if (E > 1 && t % E != eset) {
           // another set's tile: only the set count and the ring positions move
           cur += __popc(ends);
-          if constexpr (FP8) { if (++sslot == C::SC_SLOTS) { sslot = 0; sphase ^= 1; } }
+          if constexpr (COL_SCALE) { if (++sslot == C::SC_SLOTS) { sslot = 0; sphase ^= 1; } }
           if (++acc == 2) { acc = 0; acc_phase ^= 1; }
           continue;
+        }
+        // SS: the scales of this tile's first two set ends, loaded before the
+        // fold so that their latency hides behind it (a tile of N <= 256
+        // columns rarely ends more than two sets)
+        float sc_a = 1.f, sc_b = 1.f;
+        if constexpr (SS) {
+          if (ends != 0) {
+            sc_a = __ldg(a.set_scale + cur);
+            sc_b = __ldg(a.set_scale + min(cur + 1, d1 - 1));
+          }
         }
         // every lane waits, then the warp agrees, so the .sync.aligned TMEM
         // loads below always run with the whole warp
         bool got = mbar_wait(&acc_full[acc * C::NMW + m_tile % C::NMW], acc_phase, a.status, abort_flag);
-        if constexpr (FP8) got = got && mbar_wait(&sc_full[sslot], sphase, a.status, abort_flag);
+        if constexpr (COL_SCALE) got = got && mbar_wait(&sc_full[sslot], sphase, a.status, abort_flag);
         if (!__all_sync(0xffffffffu, got)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const float* sc = FP8 ? sc_smem + sslot * C::N : nullptr;
+        const float* sc = COL_SCALE ? sc_smem + sslot * C::N : nullptr;
         const uint32_t tcol = tmem + t_lane + acc * C::ACC_COLS + m_tile * C::N;
 #pragma unroll
         for (int c = 0; c < C::N / CH; ++c) {
@@ -553,9 +569,9 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[acc * C::NMW + m_tile % C::NMW]);
           }
-          fold(v, c * (CH / 8), ends, FP8 ? sc + c * CH : nullptr);
+          fold(v, c * (CH / 8), ends, COL_SCALE ? sc + c * CH : nullptr);
         }
-        if constexpr (FP8) {
+        if constexpr (COL_SCALE) {
           __syncwarp();
           if (lane == 0) mbar_arrive(&sc_empty[sslot]);
           if (++sslot == C::SC_SLOTS) { sslot = 0; sphase ^= 1; }
@@ -579,12 +595,16 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
         }
         run = -INFINITY;
         uint32_t e = ends;
+        int k_end = 0;
 #pragma unroll 1
         while (e) {
           const int sidx = __ffs(e) - 1;
           e &= e - 1;
-          set_end(fmaxf(cin, pick(out, sidx)));
+          float set_sc = 1.f;
+          if constexpr (SS) set_sc = k_end == 0 ? sc_a : k_end == 1 ? sc_b : __ldg(a.set_scale + cur);
+          set_end(fmaxf(cin, pick(out, sidx)), set_sc);
           cin = -INFINITY;
+          ++k_end;
         }
       }
       flush();  // the scores this warp still keeps
@@ -598,14 +618,14 @@ tc_score_all_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_const
   }
 }
 
-template <int MT, bool FP8, bool AT = false, int E = 1>
+template <int MT, bool FP8, bool AT = false, int E = 1, bool SS = false>
 gem_status launch_tc(const gem_store* s, gem_workspace* ws, const CUtensorMap& tm_q,
                      const CUtensorMap& tm_d, const CUtensorMap& tm_scale, const ChunkMap* cm,
                      float* scores, cudaStream_t st) {
-  using C = TcCfg<MT, FP8, AT, E>;
+  using C = TcCfg<MT, FP8, AT, E, SS>;
   static bool attr_set = false;
   if (!attr_set) {
-    GEM_CUDA_TRY(cudaFuncSetAttribute(tc_score_all_kernel<MT, FP8, AT, E>,
+    GEM_CUDA_TRY(cudaFuncSetAttribute(tc_score_all_kernel<MT, FP8, AT, E, SS>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
     attr_set = true;
   }
@@ -624,38 +644,39 @@ gem_status launch_tc(const gem_store* s, gem_workspace* ws, const CUtensorMap& t
   a.n_chunks = cm->n_chunks;
   a.n_sets = s->n_sets;
   a.scores = scores;
+  a.set_scale = s->d_set_scale;
   a.status = ws->d_status;
   a.unit_counter = ws->d_unit_counter;
   for (int pass = 0; pass < ws->n_passes; ++pass) {
     a.pass = pass;
     GEM_CUDA_TRY(cudaMemsetAsync(ws->d_unit_counter, 0, sizeof(int), st));
-    tc_score_all_kernel<MT, FP8, AT, E><<<s->n_sm, C::THREADS, C::SMEM_BYTES, st>>>(tm_q, tm_d, tm_scale, a);
+    tc_score_all_kernel<MT, FP8, AT, E, SS><<<s->n_sm, C::THREADS, C::SMEM_BYTES, st>>>(tm_q, tm_d, tm_scale, a);
     GEM_CUDA_TRY(cudaGetLastError());
     note_launches(1);
   }
   return GEM_OK;
 }
 
-template <bool FP8>
+template <bool FP8, bool SS = false>
 gem_status launch_tc_dtype(const gem_store* s, gem_workspace* ws, int m_tiles, int variant, const ChunkMap* cm,
                            float* scores, cudaStream_t st) {
   const int n = variant == GEM_TC_A_TMEM ? TcCfg<2, FP8, true>::N : 256 / m_tiles;
   const CUtensorMap* td = nullptr;
   const CUtensorMap* tsc = nullptr;
-  gem_status r = FP8 ? store_tmap_fp8(s, n, &td) : store_tmap_bf16(s, n, &td);
+  gem_status r = !FP8 ? store_tmap_bf16(s, n, &td) : SS ? store_tmap_fp8_set(s, n, &td) : store_tmap_fp8(s, n, &td);
   if (r != GEM_OK) return r;
-  if (FP8 && (r = store_tmap_fp8_scale(s, n, &tsc)) != GEM_OK) return r;
-  if (!FP8) tsc = td;  // unused
+  if (FP8 && !SS && (r = store_tmap_fp8_scale(s, n, &tsc)) != GEM_OK) return r;
+  if (!FP8 || SS) tsc = td;  // unused
   const CUtensorMap& tq = FP8 ? ws->tmap_q_fp8 : ws->tmap_q_bf16;
-  if (variant == GEM_TC_A_TMEM) return launch_tc<2, FP8, true>(s, ws, tq, *td, *tsc, cm, scores, st);
+  if (variant == GEM_TC_A_TMEM) return launch_tc<2, FP8, true, 1, SS>(s, ws, tq, *td, *tsc, cm, scores, st);
   if (variant == GEM_TC_TWO_SETS) {
-    if (m_tiles == 1) return launch_tc<1, FP8, false, 2>(s, ws, tq, *td, *tsc, cm, scores, st);
-    return launch_tc<2, FP8, false, 2>(s, ws, tq, *td, *tsc, cm, scores, st);
+    if (m_tiles == 1) return launch_tc<1, FP8, false, 2, SS>(s, ws, tq, *td, *tsc, cm, scores, st);
+    return launch_tc<2, FP8, false, 2, SS>(s, ws, tq, *td, *tsc, cm, scores, st);
   }
   switch (m_tiles) {
-    case 1: return launch_tc<1, FP8>(s, ws, tq, *td, *tsc, cm, scores, st);
-    case 2: return launch_tc<2, FP8>(s, ws, tq, *td, *tsc, cm, scores, st);
-    case 4: return launch_tc<4, FP8>(s, ws, tq, *td, *tsc, cm, scores, st);
+    case 1: return launch_tc<1, FP8, false, 1, SS>(s, ws, tq, *td, *tsc, cm, scores, st);
+    case 2: return launch_tc<2, FP8, false, 1, SS>(s, ws, tq, *td, *tsc, cm, scores, st);
+    case 4: return launch_tc<4, FP8, false, 1, SS>(s, ws, tq, *td, *tsc, cm, scores, st);
     default: return fail(GEM_ERR_INVALID, "m_tiles must be 1, 2 or 4");
   }
 }
@@ -671,6 +692,7 @@ gem_status launch_tc_score_all(const gem_store* s, gem_workspace* ws, int comput
   if (variant == GEM_TC_TWO_SETS && m_tiles == 4) return fail(GEM_ERR_INVALID, "two_sets needs m_tiles 1 or 2");
   if (compute == GEM_BF16) return launch_tc_dtype<false>(s, ws, m_tiles, variant, cm, scores, st);
   if (compute == GEM_FP8_E4M3) return launch_tc_dtype<true>(s, ws, m_tiles, variant, cm, scores, st);
+  if (compute == GEM_FP8_E4M3_SET) return launch_tc_dtype<true, true>(s, ws, m_tiles, variant, cm, scores, st);
   return fail(GEM_ERR_INVALID, "tensor-core scoring takes bf16 or fp8");
 }
 

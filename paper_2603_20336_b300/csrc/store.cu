@@ -63,6 +63,51 @@ __global__ void quantize_fp8_kernel(const float* __restrict__ src, const int64_t
   }
 }
 
+// One warp per set, padded as above, one scale for the whole set: the smallest
+// power of two s >= FLT_MIN with max |x| over the set <= 448 s (s = 1 for a zero
+// set), so that x / s is exact; codes = E4M3(x / s) round to nearest even, saturating.
+// A common scale factors out of every maximum over the set's vectors.
+__global__ void quantize_fp8_set_kernel(const float* __restrict__ src, const int64_t* __restrict__ off,
+                                        const int64_t* __restrict__ pad_off, int64_t n_sets,
+                                        uint8_t* __restrict__ dst, float* __restrict__ set_scale) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t d = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; d < n_sets;
+       d += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t s0 = off[d], len = off[d + 1] - s0;
+    const int64_t p0 = pad_off[d], plen = pad_off[d + 1] - p0;
+    float a = 0.f;
+    for (int64_t r = 0; r < len; ++r) {
+      const float4 v = reinterpret_cast<const float4*>(src + (s0 + r) * kDim)[lane];
+      a = fmaxf(a, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+    float sc = 1.f;
+    if (a > 0.f) {
+      // a in [2^(e-1), 2^e): 448 * 2^(e-10) < a <= 448 * 2^(e-8), so the smallest
+      // power of two s >= 2^-126 with a <= 448 s is found by at most two doublings
+      // (448 s is exact; it may round up to +inf only where s already holds a)
+      int e = 0;
+      frexpf(a, &e);
+      sc = ldexpf(1.f, max(e - 10, -126));
+      while (a > 448.f * sc) sc *= 2.f;
+    }
+    const float inv = 1.f / sc;        // a power of two: x * inv == x / sc exactly
+    for (int64_t r = 0; r < plen; ++r) {
+      const float4 v = reinterpret_cast<const float4*>(src + (s0 + min(r, len - 1)) * kDim)[lane];
+      const float xs[4] = {v.x, v.y, v.z, v.w};
+      uint32_t packed = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(xs[j] * inv, __NV_SATFINITE, __NV_E4M3);
+        packed |= (uint32_t)c << (8 * j);
+      }
+      reinterpret_cast<uint32_t*>(dst + (p0 + r) * kDim)[lane] = packed;
+    }
+    if (lane == 0) set_scale[d] = sc;
+  }
+}
+
 // lazy deletion (Sec. 4.6): count ids outside [0, n_sets) into bad[0]
 __global__ void check_ids_kernel(const int64_t* __restrict__ ids, int64_t n, int64_t n_sets, int* bad) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -143,6 +188,15 @@ void launch_quantize_fp8(const float* src, const int64_t* off, const int64_t* pa
   const int grid = (int)std::min<int64_t>((n_sets * 32 + 255) / 256, 148 * 16);
   if (grid > 0) {
     quantize_fp8_kernel<<<grid, 256, 0, st>>>(src, off, pad_off, n_sets, dst, scale);
+    note_launches(1);
+  }
+}
+
+void launch_quantize_fp8_set(const float* src, const int64_t* off, const int64_t* pad_off,
+                             int64_t n_sets, uint8_t* dst, float* set_scale, cudaStream_t st) {
+  const int grid = (int)std::min<int64_t>((n_sets * 32 + 255) / 256, 148 * 16);
+  if (grid > 0) {
+    quantize_fp8_set_kernel<<<grid, 256, 0, st>>>(src, off, pad_off, n_sets, dst, set_scale);
     note_launches(1);
   }
 }
@@ -233,6 +287,21 @@ gem_status store_tmap_fp8(const gem_store* s, int box_rows, const CUtensorMap** 
                         box_rows, CU_TENSOR_MAP_SWIZZLE_128B))
       return fail(GEM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the fp8 store");
     it = s->tmap_fp8.emplace(box_rows, m).first;
+  }
+  *out = &it->second;
+  return GEM_OK;
+}
+
+gem_status store_tmap_fp8_set(const gem_store* s, int box_rows, const CUtensorMap** out) {
+  std::lock_guard<std::mutex> lk(g_store_mutex);
+  if (!s->d_fp8s) return fail(GEM_ERR_STATE, "store keeps no per-set-scale fp8 copy");
+  auto it = s->tmap_fp8s.find(box_rows);
+  if (it == s->tmap_fp8s.end()) {
+    CUtensorMap m;
+    if (!encode_tmap_2d(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, s->d_fp8s, kDim, s->n_pad_vecs, kDim, 128,
+                        box_rows, CU_TENSOR_MAP_SWIZZLE_128B))
+      return fail(GEM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the per-set-scale fp8 store");
+    it = s->tmap_fp8s.emplace(box_rows, m).first;
   }
   *out = &it->second;
   return GEM_OK;
