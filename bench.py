@@ -484,7 +484,24 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, recall, stages, dev, step_ms, o
         g = torch.randn_like(s)
         ms_f = _time(lambda: gem.maxsim_fwd(wb.queries.vecs, qo5, wb.docs.vecs, do5, po, pid, "bf16", max_q_len=32))
         ms_b = _time(lambda: gem.maxsim_bwd(wb.queries.vecs, qo5, wb.docs.vecs, do5, po, pid, am, g))
-        return {"pairs": nb * per_q, "fwd_ms": ms_f, "bwd_ms": ms_b, "doc_vectors": int(wb.docs.n_vecs)}
+        # algorithmic work: the forward reads every set row once as FP32 and
+        # does 2 * m_q * m_p * 128 flop per pair; the backward writes every row of
+        # grad_docs and of grad_q once and reads one set row per (pair, query row)
+        n_dv = int(wb.docs.n_vecs)
+        q_rows = int(wb.queries.offsets[-1])
+        fwd_gb = n_dv * 512 / 1e9
+        fwd_tf = 2.0 * 32 * n_dv * 128 / (ms_f * 1e-3) / 1e12
+        bwd_gb = (n_dv * 512 + q_rows * 512 + nb * per_q * 32 * 512) / 1e9
+        pk, kind = _peaks()
+        return {"pairs": nb * per_q, "fwd_ms": ms_f, "bwd_ms": ms_b, "doc_vectors": n_dv,
+                "fwd": {"algorithmic_gb": fwd_gb, "hbm_gbs": fwd_gb / (ms_f * 1e-3),
+                        "frac_of_hbm_peak": fwd_gb / (ms_f * 1e-3) / pk["hbm_gbs"], "tflops": fwd_tf,
+                        "frac_of_bf16_peak": fwd_tf / pk["bf16_tflops"], "bound": "hbm",
+                        "includes": "query rounding launch + forward kernel"},
+                "bwd": {"algorithmic_gb": bwd_gb, "hbm_gbs": bwd_gb / (ms_b * 1e-3),
+                        "frac_of_hbm_peak": bwd_gb / (ms_b * 1e-3) / pk["hbm_gbs"], "bound": "hbm",
+                        "includes": "dQ kernel + set counts + owner rows + atomic pass"},
+                "peak_kind": kind}
 
     def pages():
         # the multi-modal page configuration: 50,000 sets x 1,024 vectors, 500

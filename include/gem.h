@@ -510,11 +510,12 @@ gem_status gem_search_host(const gem_store* store, gem_workspace* ws, const floa
  * accumulation; GEM_F32 uses the FP32 values.  scores float32 [n_pairs];
  * argmax int32 [n_pairs * max_q_len].  ws (may be NULL) receives device-side
  * errors (an id outside [0, n_docs) scores NaN).
- * GEM_BF16 with max_q_len <= 128 runs on the tensor cores: the rows are first
- * rounded into stream-ordered scratch (2 bytes per component of q and docs,
- * freed at the end of the call), the sum over i is taken in a fixed order (32-row
- * butterflies, then in ascending blocks of 32); otherwise an FP32 SIMT kernel
- * with a Kahan sum in ascending i runs.
+ * GEM_BF16 with max_q_len <= 128 runs on the tensor cores: the query rows are
+ * first rounded into stream-ordered scratch (2 bytes per component of q, freed
+ * at the end of the call), the set rows are read once as FP32 and rounded on
+ * chip, and the sum over i is taken in a fixed order (32-row butterflies, then
+ * in ascending blocks of 32); otherwise an FP32 SIMT kernel with a Kahan sum in
+ * ascending i runs.
  */
 gem_status gem_maxsim_fwd(const float* q, const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
                           const float* docs, const int64_t* doc_offsets, int64_t n_docs, int64_t n_doc_rows,
@@ -527,8 +528,13 @@ gem_status gem_maxsim_fwd(const float* q, const int64_t* q_offsets, int32_t n_qu
  *   grad_docs[row j of set d] = sum over pairs t of d of g_t * (sum of q_i with j*(t,i) = j)
  * with the FP32 input values (the bf16 rounding of the forward is treated as the
  * identity).  grad_q float32 [n_q_rows * 128] and grad_docs float32
- * [n_doc_rows * 128] are overwritten (either may be NULL).  grad_q is
- * deterministic; grad_docs is deterministic when no set occurs in two pairs.
+ * [n_doc_rows * 128] are overwritten (either may be NULL); an argmax entry
+ * outside its set's rows adds nothing.  grad_q is deterministic (one FMA chain
+ * per element, pairs ascending).  grad_docs: with max_q_len <= 32 every row is
+ * written once by its set (a set named by one pair gets its sums directly, a
+ * set named by several pairs is zeroed and its pairs add with atomics), using
+ * 12 bytes per set of stream-ordered scratch; otherwise it is zeroed and every
+ * pair adds with atomics.  It is deterministic when no set occurs in two pairs.
  */
 gem_status gem_maxsim_bwd(const float* q, const int64_t* q_offsets, int32_t n_queries, const float* docs,
                           const int64_t* doc_offsets, int64_t n_docs, int64_t n_doc_rows,

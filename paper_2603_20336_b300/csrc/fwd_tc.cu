@@ -10,14 +10,20 @@
 // consecutive pairs; a persistent CTA per SM draws units from a counter.  The
 // query block (A, 128 rows) stays in shared memory while its pairs run.  Each
 // set is read once, as FP32: TMA brings it in boxes of 32 rows (at most 31 rows
-// read past its end) into a four-slot staging ring, and four converter warps
-// round each box to bf16 into the 128-byte-swizzled operand layout of a
-// two-stage ring of 256-row tiles (a proxy fence makes the writes visible to the
-// tensor cores).  One MMA per K step covers the tile with N = 32 x boxes.  The
-// accumulator (128 query rows x 256 rows of the set) is double-buffered in TMEM;
-// four epilogue warps, one thread per query row, take the running max and argmax
-// over the set's valid columns, write the argmax row and add the row maxima (a
-// butterfly per warp, the four warp sums in order through shared memory).
+// read past its end) into a six-slot staging ring (96 KB of loads in flight per
+// SM).  Six converter warps take the boxes in turn: a converter reads its
+// box and rounds it to bf16 in registers, frees the slot, waits until its
+// tile's operand stage is free (the MMAs of the stage's previous tile have
+// completed: a count of completed tiles the epilogue publishes) and writes the
+// box into the 128-byte-swizzled layout of a three-stage ring of 128-row tiles
+// (a proxy fence makes the writes visible to the tensor cores).  So a staging
+// slot is held only for its load, and the loads run ahead of the tensor cores by
+// up to six boxes whatever the tile sizes.  One MMA per K step covers the tile
+// with N = 32 x boxes.  The accumulator (128 query rows x 128 rows of the set)
+// has four buffers in TMEM; four epilogue warps, one thread per query row, take
+// the running max and argmax over the set's valid columns, write the argmax row
+// and add the row maxima (a butterfly per warp, the four warp sums in order
+// through shared memory).
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -26,22 +32,28 @@
 namespace gem {
 namespace {
 
-constexpr int kFtN = 256;                       // set rows per tile
+constexpr int kFtN = 128;                       // set rows per tile
 constexpr int kFtBox = 32;                      // rows per TMA box
-constexpr int kFtStages = 2;
+constexpr int kFtBoxes = kFtN / kFtBox;         // boxes per tile
+constexpr int kFtStages = 3;
 constexpr int kFtPairsPerUnit = 16;
 constexpr int kFtEpiWarps = 4;
-constexpr int kFtConvWarps = 4;                       // FP32 -> bf16 converters, one staging slot each
+constexpr int kFtConvWarps = 6;                       // FP32 -> bf16 converters: boxes c, c + C, ...
+constexpr int kFtSlotsPerConv = 1;
+constexpr int kFtSlots = kFtSlotsPerConv * kFtConvWarps;  // FP32 staging slots; converter c uses c + C s
+constexpr int kFtAccs = 4;                            // TMEM accumulators
 constexpr int kFtConv0 = kFtEpiWarps + 2;             // first converter warp
 constexpr int kFtThreads = (kFtEpiWarps + 2 + kFtConvWarps) * 32;   // + producer, MMA warp, converters
 constexpr int kFtABytes = 128 * kDim * 2;             // 32 KB
-constexpr int kFtStageBytes = kFtN * kDim * 2;        // 64 KB
+constexpr int kFtStageBytes = kFtN * kDim * 2;        // 32 KB
 constexpr int kFtStgBytes = kFtBox * kDim * 4;        // one FP32 box: 16 KB
+constexpr int kFtTmemCols = kFtAccs * kFtN < 32 ? 32 : kFtAccs * kFtN;   // a power of two >= 32
+static_assert((kFtTmemCols & (kFtTmemCols - 1)) == 0 && kFtTmemCols <= 512, "TMEM allocation");
 constexpr int kFtUnitRing = 2;
-constexpr int kFtNBars = 2 * kFtStages + 4 + 2 + 1 + 2 * kFtUnitRing + 4 + 2 * kFtConvWarps;
+constexpr int kFtNBars = kFtStages + 2 * kFtAccs + 2 + 1 + 2 * kFtUnitRing + 4 + 2 * kFtSlots;
 constexpr int kFtBarBytes =
-    (kFtNBars * 8 + 16 + 4 * kFtUnitRing + 2 * 4 * 4 + 2 * 4 * kFtConvWarps + 127) / 128 * 128;
-constexpr int kFtSmem = 1024 + kFtABytes + kFtStages * kFtStageBytes + kFtConvWarps * kFtStgBytes + kFtBarBytes;
+    (kFtNBars * 8 + 16 + 4 * kFtUnitRing + 2 * 4 * 4 + 4 * 4 * kFtSlots + 8 + 127) / 128 * 128;
+constexpr int kFtSmem = 1024 + kFtABytes + kFtStages * kFtStageBytes + kFtSlots * kFtStgBytes + kFtBarBytes;
 static_assert(kFtSmem <= 232448, "shared memory over the per-block limit");
 
 struct FtArgs {
@@ -123,14 +135,13 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* a_smem = smem;                        // [2 halves][128 rows][128 B]
-  uint8_t* b_smem = smem + kFtABytes;            // [stage][2 halves][256 rows][128 B]
+  uint8_t* b_smem = smem + kFtABytes;            // [stage][2 halves][128 rows][128 B]
   uint8_t* stg_smem = b_smem + kFtStages * kFtStageBytes;  // [slot][32 rows][128 FP32]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stg_smem + kFtConvWarps * kFtStgBytes);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + kFtStages;
-  uint64_t* acc_full = bars + 2 * kFtStages;     // [2]
-  uint64_t* acc_empty = acc_full + 2;            // [2]
-  uint64_t* q_full = acc_empty + 2;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg_smem + kFtSlots * kFtStgBytes);
+  uint64_t* full = bars;                         // [kFtStages]
+  uint64_t* acc_full = bars + kFtStages;         // [kFtAccs]
+  uint64_t* acc_empty = acc_full + kFtAccs;      // [kFtAccs]
+  uint64_t* q_full = acc_empty + kFtAccs;
   uint64_t* q_empty = q_full + 1;
   uint64_t* done_bar = q_empty + 1;
   uint64_t* unit_full = done_bar + 1;            // [UNIT_RING]
@@ -143,8 +154,15 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
   float* parts = const_cast<float*>(reinterpret_cast<volatile float*>(unit_ring + kFtUnitRing));  // [2][4]
   uint64_t* stg_full = reinterpret_cast<uint64_t*>(
       (reinterpret_cast<uintptr_t>(parts + 8) + 7) & ~uintptr_t(7));   // [slot]: the FP32 box landed
-  uint64_t* stg_empty = stg_full + kFtConvWarps;                         // [slot]: converted
-  volatile int* stg_desc = reinterpret_cast<volatile int*>(stg_empty + kFtConvWarps);  // [slot][2]: stage, box (-1: stop)
+  uint64_t* stg_empty = stg_full + kFtSlots;                             // [slot]: read out
+  // [slot][4]: operand stage (-1: stop), box, arrivals on the stage's full
+  // barrier beyond one (the tile's boxes with no rows), tile index
+  volatile int* stg_desc = reinterpret_cast<volatile int*>(stg_empty + kFtSlots);
+  // tiles whose MMAs have completed, in order (written by the epilogue when it
+  // sees a tile's accumulator full): a tile's operand stage is free for tile
+  // + kFtStages once tiles_done > tile.  A counter rather than a parity wait:
+  // the converters run an unbounded number of tiles ahead of the MMA.
+  volatile int* tiles_done = stg_desc + 4 * kFtSlots;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -152,13 +170,16 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
   if (blockIdx.x >= n_units) return;
 
   if (threadIdx.x == 0) {
-    // full[s]: one arrival per 32-row box of the tile (a converter each, the
-    // producer for the boxes past the set's end)
-    for (int s = 0; s < kFtStages; ++s) { mbar_init(&full[s], kFtN / kFtBox); mbar_init(&empty[s], 1); }
-    for (int c = 0; c < kFtConvWarps; ++c) { mbar_init(&stg_full[c], 1); mbar_init(&stg_empty[c], 1); }
-    for (int i = 0; i < 2; ++i) {
+    // full[s]: one arrival per 32-row box of the tile, all from converters (the
+    // converter of a tile's last box also arrives for the boxes past the set's
+    // end)
+    for (int s = 0; s < kFtStages; ++s) mbar_init(&full[s], kFtBoxes);
+    for (int c = 0; c < kFtSlots; ++c) { mbar_init(&stg_full[c], 1); mbar_init(&stg_empty[c], 1); }
+    for (int i = 0; i < kFtAccs; ++i) {
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], kFtEpiWarps);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(&part_full[i], kFtEpiWarps);
       mbar_init(&part_empty[i], 1);
     }
@@ -170,9 +191,10 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
       mbar_init(&unit_empty[i], 1 + kFtEpiWarps);
     }
     *abort_flag = 0;
+    *tiles_done = 0;
     fence_barrier_init();
   }
-  if (warp == kFtEpiWarps + 1) tmem_alloc(tmem_slot, 512);
+  if (warp == kFtEpiWarps + 1) tmem_alloc(tmem_slot, kFtTmemCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -185,9 +207,8 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
       tma_prefetch_desc(&tm_q);
       tma_prefetch_desc(&tm_d);
     }
-    int stage = 0;
-    uint32_t phase = 0;
-    uint64_t n_box = 0;  // FP32 boxes issued (box g goes to staging slot g % kFtConvWarps)
+    uint64_t n_tile = 0;  // tiles issued (tile n goes to operand stage n % kFtStages)
+    uint64_t n_box = 0;   // FP32 boxes issued (box g: staging slot g % kFtSlots, converter g % kFtConvWarps)
     uint32_t n_a = 0;  // query blocks loaded
     int cur_b = -1;
     bool ok = true;
@@ -227,22 +248,24 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
           for (int tile = 0; tile < p.tiles && okl; ++tile) {
             const int rows = min(kFtN, p.m_p - tile * kFtN);
             const int nb = (rows + kFtBox - 1) / kFtBox;
-            if (!mbar_wait(&empty[stage], phase ^ 1, a.status, abort_flag)) { okl = 0; break; }
+            const int stage = (int)(n_tile % kFtStages);
             const int row0 = (int)(p.r0 + (int64_t)tile * kFtN);
             for (int bx = 0; bx < nb && okl; ++bx) {
               // the box's FP32 rows into the next staging slot; its converter
-              // writes them, rounded, into this stage
-              const int sl = (int)(n_box % kFtConvWarps);
-              const uint32_t use = (uint32_t)(n_box / kFtConvWarps);
+              // writes them, rounded, into this tile's stage
+              const int sl = (int)(n_box % kFtSlots);
+              const uint32_t use = (uint32_t)(n_box / kFtSlots);
               if (use > 0 && !mbar_wait(&stg_empty[sl], (use - 1) & 1, a.status, abort_flag)) { okl = 0; break; }
-              stg_desc[2 * sl] = stage;
-              stg_desc[2 * sl + 1] = bx;
+              const int extra = bx == nb - 1 ? kFtBoxes - nb : 0;  // boxes with no rows
+              stg_desc[4 * sl] = stage;
+              stg_desc[4 * sl + 1] = bx;
+              stg_desc[4 * sl + 2] = extra;
+              stg_desc[4 * sl + 3] = (int)n_tile;
               mbar_arrive_expect_tx(&stg_full[sl], kFtStgBytes);
               tma_load_2d(stg_smem + sl * kFtStgBytes, &tm_d, &stg_full[sl], 0, row0 + bx * kFtBox);
               ++n_box;
             }
-            for (int bx = nb; bx < kFtN / kFtBox; ++bx) mbar_arrive(&full[stage]);  // no rows there
-            if (++stage == kFtStages) { stage = 0; phase ^= 1; }
+            ++n_tile;
           }
         }
         if (!__shfl_sync(0xffffffffu, okl, 0)) ok = false;
@@ -250,17 +273,21 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
     }
     if (lane == 0) {
       if (ok) {
-        // stop every converter: a descriptor of -1 in its slot, once the slot is free
-        for (int sl = 0; sl < kFtConvWarps; ++sl) {
-          const uint64_t uses = n_box / kFtConvWarps + ((uint64_t)sl < n_box % kFtConvWarps ? 1 : 0);
-          if (uses > 0 && !mbar_wait(&stg_empty[sl], (uint32_t)((uses - 1) & 1), a.status, abort_flag)) break;
-          stg_desc[2 * sl] = -1;
+        // stop every converter: a descriptor of -1 in the slot it reads next
+        // (converter c's k-th box went to slot c + C (k % S), use k / S), once
+        // that slot's previous box has been read out
+        for (int c = 0; c < kFtConvWarps; ++c) {
+          const uint64_t n_c = n_box / kFtConvWarps + ((uint64_t)c < n_box % kFtConvWarps ? 1 : 0);
+          const int sl = c + kFtConvWarps * (int)(n_c % kFtSlotsPerConv);
+          const uint64_t prev = n_c / kFtSlotsPerConv;
+          if (prev > 0 && !mbar_wait(&stg_empty[sl], (uint32_t)((prev - 1) & 1), a.status, abort_flag)) break;
+          stg_desc[4 * sl] = -1;
           mbar_arrive(&stg_full[sl]);
         }
       } else {
         // drain: every load this thread issued must land before the CTA exits
-        for (int sl = 0; sl < kFtConvWarps; ++sl) {
-          const uint64_t uses = n_box / kFtConvWarps + ((uint64_t)sl < n_box % kFtConvWarps ? 1 : 0);
+        for (int sl = 0; sl < kFtSlots; ++sl) {
+          const uint64_t uses = n_box / kFtSlots + ((uint64_t)sl < n_box % kFtSlots ? 1 : 0);
           if (uses) { int z = 0; mbar_wait(&stg_full[sl], (uint32_t)((uses - 1) & 1), nullptr, &z); }
         }
         int z = 0;
@@ -318,10 +345,9 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
               mma_bf16(dt, ad0 + (uint64_t)((half * 16384 + within) >> 4),
                        bd0 + (uint64_t)((half * (kFtN * 128) + within) >> 4), idesc, k > 0);
             }
-            mma_commit(&empty[stage]);
             mma_commit(&acc_full[acc]);
             if (++stage == kFtStages) { stage = 0; phase ^= 1; }
-            if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+            if (++acc == kFtAccs) { acc = 0; acc_phase ^= 1; }
           }
         }
         if (!__shfl_sync(0xffffffffu, okl, 0)) ok = false;
@@ -335,42 +361,70 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
     }
   } else if (warp >= kFtConv0) {
     // ------------------------------------------------------------------ converters
-    // warp c takes staging slot c: 32 FP32 rows -> bf16 (nearest even) at rows
-    // 32 box .. 32 box + 31 of its stage, in the 128-byte swizzle (16-byte chunk
-    // index XOR row % 8) the MMA descriptors expect
-    const int sl = warp - kFtConv0;
-    const float* stg = reinterpret_cast<const float*>(stg_smem + sl * kFtStgBytes);
+    // converter c takes boxes c, c + C, ... (C converters; its k-th box in
+    // staging slot c + C (k % S), S slots each): the 32 FP32 rows read and
+    // rounded to bf16 (nearest even) in registers, the slot freed, then, once
+    // the tile's operand stage is free, the rows stored at rows 32 box ..
+    // 32 box + 31 of the stage, in the 128-byte
+    // swizzle (16-byte chunk index XOR row % 8) the MMA descriptors expect
+    const int c = warp - kFtConv0;
     const int h = lane >> 4;                 // component half of this lane's 4 floats
     const int cc = (lane & 15) >> 1;         // 16-byte chunk within the half
     for (uint32_t n = 0;; ++n) {
-      const bool w = mbar_wait(&stg_full[sl], n & 1, a.status, abort_flag);
+      const int sl = c + kFtConvWarps * (int)(n % kFtSlotsPerConv);
+      const bool w = mbar_wait(&stg_full[sl], (n / kFtSlotsPerConv) & 1, a.status, abort_flag);
       if (!__all_sync(0xffffffffu, w)) break;
-      const int st_i = stg_desc[2 * sl];
-      const int bx = stg_desc[2 * sl + 1];
+      const int st_i = stg_desc[4 * sl];
+      const int bx = stg_desc[4 * sl + 1];
+      const int extra = stg_desc[4 * sl + 2];
+      const int tile = stg_desc[4 * sl + 3];
       if (st_i < 0) break;
-      uint8_t* dst = b_smem + st_i * kFtStageBytes + h * (kFtN * 128) + (lane & 1) * 8;
-      // eight rows' loads in flight before their conversions and stores
-#pragma unroll 1
+      const float* stg = reinterpret_cast<const float*>(stg_smem + sl * kFtStgBytes);
+      uint2 o[kFtBox];
+#pragma unroll
       for (int r0 = 0; r0 < kFtBox; r0 += 8) {
         float4 x[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) x[u] = reinterpret_cast<const float4*>(stg + (r0 + u) * kDim)[lane];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          uint2 o;
-          o.x = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[u].x)) |
-                ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[u].y)) << 16);
-          o.y = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[u].z)) |
-                ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[u].w)) << 16);
-          const int R = bx * kFtBox + r0 + u;
-          *reinterpret_cast<uint2*>(dst + R * 128 + ((cc ^ (R & 7)) << 4)) = o;
+          o[r0 + u].x = pack_bf16x2(x[u].x, x[u].y);   // two components per conversion
+          o[r0 + u].y = pack_bf16x2(x[u].z, x[u].w);
         }
+      }
+      // every lane has consumed its reads of the slot (the rounded values are in
+      // registers); the proxy fence orders those reads before the next TMA write
+      // into the slot, which the producer issues once the slot is released
+      fence_proxy_async_shared();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&stg_empty[sl]);
+      // the stage's previous tile (tile - kFtStages) must be consumed by its MMAs
+      bool e = true;
+      if (tile >= kFtStages) {
+        const long long t0 = clock64();
+        while (*tiles_done <= tile - kFtStages) {
+          if (*abort_flag) { e = false; break; }
+          if (clock64() - t0 > kWaitBudgetCycles) {
+            set_status(a.status, kDevTimeout);
+            *abort_flag = 1;
+            e = false;
+            break;
+          }
+        }
+        __threadfence_block();
+      }
+      if (!__all_sync(0xffffffffu, e)) break;
+      uint8_t* dst = b_smem + st_i * kFtStageBytes + h * (kFtN * 128) + (lane & 1) * 8;
+#pragma unroll
+      for (int r = 0; r < kFtBox; ++r) {
+        const int R = bx * kFtBox + r;
+        *reinterpret_cast<uint2*>(dst + R * 128 + ((cc ^ (R & 7)) << 4)) = o[r];
       }
       fence_proxy_async_shared();   // the writes, visible to the tensor cores
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive(&stg_empty[sl]);
-        mbar_arrive(&full[st_i]);
+        // this box, and for a tile's last box the boxes past the set's end
+        for (int k = 0; k <= extra; ++k) mbar_arrive(&full[st_i]);
       }
     }
   } else {
@@ -379,6 +433,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
     const int row = warp * 32 + lane;  // query row within the block
     int acc = 0;
     uint32_t acc_phase = 0;
+    int n_tiles_seen = 0;
     uint32_t n_pair = 0;  // pairs summed (part buffers alternate)
     bool ok = true;
     int uslot = 0;
@@ -417,6 +472,11 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
           const bool got = mbar_wait(&acc_full[acc], acc_phase, a.status, abort_flag);
           if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
           tc_fence_after();
+          // the tile's MMAs are complete, so its operand stage may be refilled
+          if (warp == 0 && lane == 0) {
+            __threadfence_block();  // the completion seen above, ordered before the count
+            *tiles_done = ++n_tiles_seen;
+          }
           if (any_rows) {
             for (int c = 0; c < nb; ++c) {
               float v[32];
@@ -432,7 +492,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&acc_empty[acc]);
-          if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+          if (++acc == kFtAccs) { acc = 0; acc_phase ^= 1; }
         }
         if (!ok) break;
         const bool mine = row < p.m_q;
@@ -468,7 +528,7 @@ fwd_tc_kernel(const __grid_constant__ CUtensorMap tm_q, const __grid_constant__ 
   __syncthreads();
   if (warp == kFtEpiWarps + 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, 512);
+    tmem_dealloc(tmem, kFtTmemCols);
   }
 }
 

@@ -130,6 +130,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* s
   }
 }
 
+// Two floats rounded to bfloat16 (nearest even) in one instruction: lo in bits
+// 0..15, hi in bits 16..31 (the instruction's first source goes to the upper half).
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
 // Orders this thread's earlier generic-proxy shared-memory writes before later
 // async-proxy reads of them (tcgen05.mma operands, TMA stores).
 __device__ __forceinline__ void fence_proxy_async_shared() {

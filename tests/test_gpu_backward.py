@@ -241,3 +241,78 @@ def test_full_size_gradient_matches_oracle(gem):
         assert np.all(err <= 1e-5 * gq_l1 + FTZ_FLOOR), (b, err.max())
     assert n_rows == 64 * per_q * 32
     assert n_band <= 0.01 * n_rows, n_band
+
+
+def test_backward_shared_sets_and_rows_outside_any_set(gem):
+    """Sets named by several pairs (atomic adds), by one pair (rows written by
+    their owner) and by none; rows before the first set and after the last; an
+    invalid pair id; argmax entries outside their set.  Every row of grad_docs is
+    overwritten (the buffers start as NaN).  A set named by one pair is checked
+    bit for bit against the same FP32 sums taken on the host (each row: the q_i
+    with j* = row added in ascending i, times g_t); the rest against FP64."""
+    from paper_2603_20336_b300 import _check, _ptr, _stream, lib
+    rng = np.random.default_rng(5)
+    lens = rng.integers(3, 21, 10)
+    off = 7 + np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    n_rows = int(off[-1]) + 13
+    D = rng.standard_normal((n_rows, 128)).astype(np.float32)
+    qlens = np.array([5, 32, 1, 17])
+    qo = np.concatenate([[0], np.cumsum(qlens)]).astype(np.int64)
+    Q = rng.standard_normal((int(qo[-1]), 128)).astype(np.float32)
+    lists = [[0, 1, 2], [2, 3, 4, 9], [5], [2, 6, 0, -1]]      # set 2 thrice, set 0 twice; 7, 8 unnamed
+    po = np.concatenate([[0], np.cumsum([len(x) for x in lists])]).astype(np.int64)
+    pid = np.concatenate(lists).astype(np.int64)
+    n_pairs, mq = len(pid), 32
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    qd, qod, Dd, dod, pod, pidd = dev(Q), dev(qo), dev(D), dev(off), dev(po), dev(pid)
+    _, am = gem.maxsim_fwd(qd, qod, Dd, dod, pod, pidd, "f32", max_q_len=mq)
+    am = am.cpu().numpy().copy()
+    am[4, 3] = lens[3]          # pair 4 (query 1, set 3): row 3 points past the set
+    am[9, 0] = -1               # pair 9 (query 3, set 6): row 0 points before it
+    g = rng.standard_normal(n_pairs).astype(np.float32)
+    gq = torch.full((int(qo[-1]), 128), float("nan"), device="cuda")
+    gd = torch.full((n_rows, 128), float("nan"), device="cuda")
+    amd, gdev = dev(am), dev(g)     # kept alive until the kernels have run
+    _check(lib.gem_maxsim_bwd(_ptr(qd), _ptr(qod), len(qlens), _ptr(Dd), _ptr(dod), len(lens), n_rows, _ptr(pod),
+                              _ptr(pidd), n_pairs, _ptr(amd), mq, _ptr(gdev), _ptr(gq), _ptr(gd), _stream()))
+    gq, gd = gq.cpu().numpy(), gd.cpu().numpy()
+    assert not np.isnan(gq).any() and not np.isnan(gd).any()
+    assert np.all(gd[:off[0]] == 0) and np.all(gd[off[-1]:] == 0)
+    for d in (7, 8):
+        assert np.all(gd[off[d]:off[d + 1]] == 0)
+    want_q = np.zeros((int(qo[-1]), 128))
+    l1_q = np.zeros_like(want_q)
+    want_d = np.zeros((n_rows, 128))
+    l1_d = np.zeros_like(want_d)
+    owners = {}
+    for b in range(len(qlens)):
+        for t in range(po[b], po[b + 1]):
+            d = pid[t]
+            if d < 0:
+                continue
+            owners.setdefault(d, []).append((t, b))
+            for i in range(qlens[b]):
+                j = am[t, i]
+                if not 0 <= j < lens[d]:
+                    continue
+                want_q[qo[b] + i] += float(g[t]) * D[off[d] + j]
+                l1_q[qo[b] + i] += abs(float(g[t]) * D[off[d] + j])
+                want_d[off[d] + j] += float(g[t]) * Q[qo[b] + i]
+                l1_d[off[d] + j] += abs(float(g[t]) * Q[qo[b] + i])
+    assert np.all(np.abs(gq - want_q) <= 1e-5 * l1_q + FTZ_FLOOR)
+    assert np.all(np.abs(gd - want_d) <= 1e-5 * l1_d + FTZ_FLOOR)
+    for d, ts in owners.items():
+        if len(ts) != 1:
+            continue
+        (t, b), = ts
+        exp = np.zeros((lens[d], 128), np.float32)
+        for j in range(lens[d]):
+            acc = np.zeros(128, np.float32)
+            hit = False
+            for i in range(qlens[b]):
+                if am[t, i] == j:
+                    acc = (acc + Q[qo[b] + i]).astype(np.float32)
+                    hit = True
+            if hit:
+                exp[j] = (np.float32(g[t]) * acc).astype(np.float32)
+        np.testing.assert_array_equal(gd[off[d]:off[d + 1]], exp, err_msg=f"set {d}")
