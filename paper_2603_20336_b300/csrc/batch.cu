@@ -5,10 +5,11 @@
 //
 // Per round the graph runs: header copy (pinned host -> device) -> work plan
 // (segments of SEG candidates per query, prefix-summed) -> [query codes, codes
-// form only] -> counter reset -> persistent scorer.  The scorer's CTAs pull
-// (query, segment) items from an atomic counter; each warp scores one candidate
-// with warp_chamfer, so a batched score is bit-identical to the score the same
-// pair gets from gem_score_ids.
+// form only] -> counter reset -> persistent scorer.  Exact form: every warp pulls
+// (query, segment) items from an atomic counter and streams the segment's sets
+// (stream_pairs); codes form: the CTAs pull items and each warp scores one
+// candidate with warp_chamfer.  Either way a batched score is bit-identical to
+// the score the same pair gets from gem_score_ids.
 #include <cuda_runtime.h>
 
 #include <map>
@@ -163,9 +164,59 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 2) batch_score_kernel(BatchA
   }
 }
 
-size_t batch_smem(int max_q_len) {
+// Exact form: a warp per item; the pairs of the item's segment stream through
+// the warp's ring (bit-identical to gem_score_ids).  A query longer than
+// max_q_len (or empty) is skipped with a status and its scores stay unwritten.
+__global__ void __launch_bounds__(kBatchWarps * 32, 2) batch_stream_kernel(BatchArgs a) {
+  extern __shared__ float sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* ring = sm + warp * kRing * kVecBlock * kStageStride;
+  float* rowmax = sm + kBatchWarps * kRing * kVecBlock * kStageStride + warp * kStreamRowmax;
+  const int B = (int)a.hdr[0];
+  const long long total = a.hdr[3];
+  const StreamArgs sa{a.q, a.q_off, B, a.co, a.ids, a.docs, a.doc_off, a.n_sets, a.scores, a.status, a.max_q_len};
+  while (true) {
+    long long item = 0;
+    if (lane == 0) item = (long long)atomicAdd(a.counter, 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total) break;
+    int lo = 0, hi = B - 1;  // query owning the item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.item_off[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const int b = lo;
+    const int m_q = (int)(a.q_off[b + 1] - a.q_off[b]);
+    if (m_q < 1 || m_q > a.max_q_len) {
+      if (lane == 0) set_status(a.status, kDevInvalid);
+      continue;
+    }
+    const int64_t t0 = a.co[b] + (item - a.item_off[b]) * a.seg;
+    const int64_t t1 = min(a.co[b + 1], t0 + a.seg);
+    stream_pairs<false>(sa, t0, t1, ring, rowmax);
+  }
+}
+
+size_t batch_smem(int max_q_len, bool stream) {
+  if (stream) return sizeof(float) * ((size_t)kBatchWarps * kRing * kVecBlock * kStageStride + kBatchWarps * kStreamRowmax);
   return sizeof(float) * ((size_t)max_q_len * kQStride + kBatchWarps * kVecBlock * kStageStride +
                           (size_t)kBatchWarps * max_q_len);
+}
+
+// The scorer of a mode, with its shared-memory attribute set once to the
+// largest any caller needs (max_q_len 256), so batches and the no-alloc path
+// never lower it for each other.
+cudaError_t batch_kernel(int32_t mode, void (**kern)(BatchArgs)) {
+  static bool attr_set[2] = {false, false};
+  const bool stream = mode != GEM_CODES;
+  *kern = stream ? batch_stream_kernel : batch_score_kernel;
+  if (!attr_set[stream]) {
+    cudaError_t e = cudaFuncSetAttribute(*kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batch_smem(32 * kMaxPasses, stream));
+    if (e != cudaSuccess) return e;
+    attr_set[stream] = true;
+  }
+  return cudaSuccess;
 }
 
 // The launch sequence of one round, on stream st (captured or direct).
@@ -200,7 +251,9 @@ gem_status enqueue_round(gem_batch* bt, cudaStream_t st) {
   a.max_q_len = bt->max_q_len;
   a.scores = bt->d_scores;
   a.status = bt->d_status;
-  batch_score_kernel<<<bt->grid, kBatchWarps * 32, batch_smem(bt->max_q_len), st>>>(a);
+  void (*kern)(BatchArgs) = nullptr;
+  GEM_CUDA_TRY(batch_kernel(bt->mode, &kern));
+  kern<<<bt->grid, kBatchWarps * 32, batch_smem(bt->max_q_len, bt->mode != GEM_CODES), st>>>(a);
   GEM_CUDA_TRY(cudaGetLastError());
   note_launches(n_launch);
   return GEM_OK;
@@ -244,16 +297,11 @@ gem_status batch_create(const gem_store* s, int32_t mode, int32_t max_queries, i
   if ((e = cudaMemset(bt->d_status, 0, sizeof(int))) != cudaSuccess) return bail(cuda_fail(e, "memset"));
   if ((e = cudaEventCreateWithFlags(&bt->done, cudaEventDisableTiming)) != cudaSuccess)
     return bail(cuda_fail(e, "event"));
-  const size_t smem = batch_smem(max_q_len);
-  // the attribute is the largest any caller needs (max_q_len 256), so batches
-  // and the no-alloc path never lower it for each other
-  if ((e = cudaFuncSetAttribute(batch_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)batch_smem(32 * kMaxPasses))) !=
-      cudaSuccess)
-    return bail(cuda_fail(e, "smem attribute"));
+  const size_t smem = batch_smem(max_q_len, mode != GEM_CODES);
+  void (*kern)(BatchArgs) = nullptr;
+  if ((e = batch_kernel(mode, &kern)) != cudaSuccess) return bail(cuda_fail(e, "smem attribute"));
   int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_score_kernel, kBatchWarps * 32, smem)) !=
-      cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchWarps * 32, smem)) != cudaSuccess)
     return bail(cuda_fail(e, "occupancy"));
   if (per_sm < 1) return bail(fail(GEM_ERR_UNSUPPORTED, "batched scorer does not fit on an SM"));
   bt->grid = s->n_sm * std::min(per_sm, ctas_per_sm > 0 ? ctas_per_sm : per_sm);
@@ -355,8 +403,8 @@ gem_status noalloc_scratch(int dev, NoAllocScratch** out) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-alloc scratch");
-    e = cudaFuncSetAttribute(batch_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)batch_smem(32 * kMaxPasses));
+    void (*kern)(BatchArgs) = nullptr;
+    e = batch_kernel(GEM_F32, &kern);
     if (e != cudaSuccess) return cuda_fail(e, "shared memory attribute");
     it = g_noalloc_addr.emplace(dev, reinterpret_cast<NoAllocScratch*>(p)).first;
   }
@@ -374,9 +422,11 @@ gem_status score_ids_noalloc(const gem_store* s, const float* q, const int64_t* 
   NoAllocScratch* sc = nullptr;
   gem_status r = noalloc_scratch(s->device, &sc);
   if (r != GEM_OK) return r;
-  const size_t smem = batch_smem(max_q_len);
+  const size_t smem = batch_smem(max_q_len, true);
+  void (*kern)(BatchArgs) = nullptr;
+  GEM_CUDA_TRY(batch_kernel(GEM_F32, &kern));
   int per_sm = 0;
-  GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_score_kernel, kBatchWarps * 32, smem));
+  GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchWarps * 32, smem));
   if (per_sm < 1) return fail(GEM_ERR_UNSUPPORTED, "batched scorer does not fit on an SM");
   noalloc_init_kernel<<<1, 1, 0, st>>>(sc, n_queries, n_q_rows, n_cands);
   batch_plan_kernel<<<1, 1024, 0, st>>>(sc->hdr, cand_offsets, kNoAllocSeg, sc->item_off, kNoAllocMaxQueries,
@@ -399,7 +449,7 @@ gem_status score_ids_noalloc(const gem_store* s, const float* q, const int64_t* 
   a.max_q_len = max_q_len;
   a.scores = scores;
   a.status = &sc->status;
-  batch_score_kernel<<<s->n_sm * per_sm, kBatchWarps * 32, smem, st>>>(a);
+  kern<<<s->n_sm * per_sm, kBatchWarps * 32, smem, st>>>(a);
   GEM_CUDA_TRY(cudaGetLastError());
   note_launches(3);
   return GEM_OK;

@@ -127,161 +127,21 @@ f32_ids_kernel(F32Args a, int max_q_len, int64_t n_cands) {
   }
 }
 
-// Id lists, exact form, queries of at most 32 rows: the same per-pair
-// arithmetic as warp_chamfer (bit-identical scores), but every warp streams the
-// set vectors of its whole candidate range through a ring of kRing 8-vector
-// stages with cp.async, kRing - 1 blocks ahead and across pair boundaries, so
-// the gathers of the next sets overlap the arithmetic of the current one.  The
-// (row offset, length) of the pairs ahead come from a window of 32 pairs held
-// one per lane, loaded a window in advance.
-constexpr int kRing = 4;
-
+// Id lists, exact form: every warp takes one contiguous range of the n_cands
+// candidates (equal shares, whatever the list lengths) and streams it
+// (stream_pairs in maxsim_simt.cuh: bit-identical to warp_chamfer).
 template <bool L2>
 __global__ void __launch_bounds__(kF32Threads, 2)
-f32_ids_stream_kernel(F32Args a, int max_q_len, int64_t n_cands) {
+f32_ids_stream_kernel(StreamArgs a, int64_t n_cands) {
   extern __shared__ float sm[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   float* ring = sm + warp * kRing * kVecBlock * kStageStride;
-  float* rowmax = sm + kF32Warps * kRing * kVecBlock * kStageStride + warp * 32;
+  float* rowmax = sm + kF32Warps * kRing * kVecBlock * kStageStride + warp * kStreamRowmax;
   const int64_t n_warps = (int64_t)gridDim.x * kF32Warps;
   const int64_t chunk = (n_cands + n_warps - 1) / n_warps;
   const int64_t t_begin = min(n_cands, ((int64_t)blockIdx.x * kF32Warps + warp) * chunk);
   const int64_t t_end = min(n_cands, t_begin + chunk);
-  if (t_begin >= t_end) return;
-  const int half = lane & 1;
-  const int pair = lane >> 1;
-  const int st_off = 4 * lane + (lane >= 16 ? 4 : 0);
-  const int rd_off = half * (kDim / 2 + 4);
-
-  // ---- producer: blocks of the pairs t_begin .. t_end - 1, in order
-  auto load_window = [&](int64_t w0, int64_t& r0_out, int& mp_out) {
-    const int64_t t = w0 + lane;
-    r0_out = 0;
-    mp_out = 0;
-    if (t < t_end) {
-      const int64_t id = a.cand_ids[t];
-      if (id >= 0 && id < a.n_sets) {
-        const int64_t s0 = a.doc_off[id];
-        r0_out = s0;
-        mp_out = (int)(a.doc_off[id + 1] - s0);
-      }
-    }
-  };
-  int64_t win0 = t_begin, w_r0, nw_r0;
-  int w_mp, nw_mp;
-  load_window(win0, w_r0, w_mp);
-  load_window(win0 + 32, nw_r0, nw_mp);
-  int64_t tp = t_begin;  // pair of the next block to issue
-  int bp = 0;            // its block index
-  int mp_cur = __shfl_sync(0xffffffffu, w_mp, 0);
-  int64_t r0_cur = __shfl_sync(0xffffffffu, w_r0, 0);
-  uint32_t issued = 0;
-  auto issue = [&]() {
-    while (tp < t_end && bp * kVecBlock >= mp_cur) {
-      ++tp;
-      bp = 0;
-      if (tp >= win0 + 32) {
-        win0 += 32;
-        w_r0 = nw_r0;
-        w_mp = nw_mp;
-        load_window(win0 + 32, nw_r0, nw_mp);
-      }
-      const int src = (int)(tp - win0) & 31;
-      mp_cur = __shfl_sync(0xffffffffu, w_mp, src);
-      r0_cur = __shfl_sync(0xffffffffu, w_r0, src);
-    }
-    if (tp < t_end) {
-      float* dst = ring + (issued % kRing) * (kVecBlock * kStageStride);
-      const float* srcp = a.docs + (r0_cur + (int64_t)bp * kVecBlock) * kDim + 4 * lane;
-      const int nv = min(kVecBlock, mp_cur - bp * kVecBlock);
-#pragma unroll
-      for (int v = 0; v < kVecBlock; ++v)
-        if (v < nv) cp_async16(dst + v * kStageStride + st_off, srcp + v * kDim);
-      ++bp;
-    }
-    cp_async_commit();
-    ++issued;
-  };
-#pragma unroll
-  for (int i = 0; i < kRing - 1; ++i) issue();
-
-  // ---- consumer
-  uint64_t qr[kQPairs];
-  int lo = 0, hi = a.n_queries - 1;  // query owning t_begin
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (a.cand_off[mid] <= t_begin) lo = mid; else hi = mid - 1;
-  }
-  int b = lo;
-  int64_t b_end = a.cand_off[b + 1];
-  int loaded_b = -1;
-  uint32_t consumed = 0;
-  for (int64_t t = t_begin; t < t_end; ++t) {
-    while (t >= b_end) {
-      ++b;
-      b_end = a.cand_off[b + 1];
-    }
-    const int64_t q0 = a.q_off[b];
-    const int m_q = (int)(a.q_off[b + 1] - q0);
-    const int64_t id = a.cand_ids[t];
-    int m_p = 0;
-    int64_t r0 = 0;
-    if (id >= 0 && id < a.n_sets) {
-      r0 = a.doc_off[id];
-      m_p = (int)(a.doc_off[id + 1] - r0);
-    }
-    const bool bad_q = m_q > max_q_len;
-    if (!bad_q && m_p > 0 && b != loaded_b) {
-      const int ia = 2 * pair, ib = ia + 1;
-#pragma unroll
-      for (int k2 = 0; k2 < kRowPairs; ++k2) {
-        const int kk = half * (kDim / 2) + 2 * k2;
-        qr[k2] = (ia < m_q) ? pack2(a.q[(q0 + ia) * kDim + kk], a.q[(q0 + ia) * kDim + kk + 1]) : 0ull;
-        qr[kRowPairs + k2] = (ib < m_q) ? pack2(a.q[(q0 + ib) * kDim + kk], a.q[(q0 + ib) * kDim + kk + 1]) : 0ull;
-      }
-      loaded_b = b;
-    }
-    float best_a = -INFINITY, best_b = -INFINITY;
-    const int nb = (m_p + kVecBlock - 1) / kVecBlock;
-    for (int blk = 0; blk < nb; ++blk) {
-      issue();
-      cp_async_wait<kRing - 1>();
-      __syncwarp();
-      if (!bad_q) {
-        const float* stage = ring + (consumed % kRing) * (kVecBlock * kStageStride);
-        const int nv = min(kVecBlock, m_p - blk * kVecBlock);
-        block_terms<L2>(stage, rd_off, qr, nv, best_a, best_b);
-      }
-      __syncwarp();
-      ++consumed;
-    }
-    float score;
-    if (id < 0) {
-      score = -INFINITY;
-    } else if (id >= a.n_sets || bad_q) {
-      if (lane == 0) set_status(a.status, id >= a.n_sets ? kDevBounds : kDevInvalid);
-      score = __int_as_float(0x7fc00000);
-    } else {
-      const int ia = 2 * pair, ib = ia + 1;
-      if (half == 0 && ia < m_q) rowmax[ia] = row_term<L2>(best_a);
-      if (half == 1 && ib < m_q) rowmax[ib] = row_term<L2>(best_b);
-      __syncwarp();
-      float s = 0.f;
-      if (lane == 0) {
-        float c = 0.f;  // Kahan compensation
-        for (int i = 0; i < m_q; ++i) {
-          const float y = __fsub_rn(rowmax[i], c);
-          const float tt = __fadd_rn(s, y);
-          c = __fsub_rn(__fsub_rn(tt, s), y);
-          s = tt;
-        }
-      }
-      score = s;
-      __syncwarp();
-    }
-    if (lane == 0) a.scores[t] = score;
-  }
-  cp_async_wait<0>();
+  stream_pairs<L2>(a, t_begin, t_end, ring, rowmax);
 }
 
 }  // namespace
@@ -319,15 +179,17 @@ gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* 
     const int grid = (int)std::min<int64_t>(units, (int64_t)s->n_sm * per_sm);
     kern<<<grid, kF32Threads, smem, st>>>(a, mq);
   } else {
-    if (!qcodes && !a.stored_codes && mq <= 32) {
-      const size_t smem = sizeof(float) * (kF32Warps * kRing * kVecBlock * kStageStride + (size_t)kF32Warps * 32);
+    if (!qcodes && !a.stored_codes) {
+      const StreamArgs sa{q, q_offsets, n_queries, cand_offsets, cand_ids, s->d_f32, s->d_offsets, s->n_sets,
+                          scores, ws->d_status, mq};
+      const size_t smem = sizeof(float) * (kF32Warps * kRing * kVecBlock * kStageStride + kF32Warps * kStreamRowmax);
       auto kern = l2 ? f32_ids_stream_kernel<true> : f32_ids_stream_kernel<false>;
       GEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kF32Threads, smem));
       if (per_sm < 1) return fail(GEM_ERR_UNSUPPORTED, "f32 scoring kernel does not fit on an SM");
       const int64_t max_grid = (n_cands + kF32Warps - 1) / kF32Warps;
       const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(max_grid, (int64_t)s->n_sm * per_sm));
-      kern<<<grid, kF32Threads, smem, st>>>(a, mq, n_cands);
+      kern<<<grid, kF32Threads, smem, st>>>(sa, n_cands);
       GEM_CUDA_TRY(cudaGetLastError());
       note_launches(1);
       return GEM_OK;

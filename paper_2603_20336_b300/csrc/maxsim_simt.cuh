@@ -196,4 +196,216 @@ __device__ __forceinline__ float warp_chamfer_coded_q(const float* __restrict__ 
                                         loaded_rg);
 }
 
+// ------------------------------------------------------------------ streamed id lists
+
+// The pairs of an id-list batch: query b's candidates are cand_ids[cand_off[b] ..
+// cand_off[b + 1]), query rows q[q_off[b] .. q_off[b + 1]) of 128 floats.
+struct StreamArgs {
+  const float* q;
+  const int64_t* q_off;
+  int n_queries;
+  const int64_t* cand_off;
+  const int64_t* cand_ids;
+  const float* docs;       // FP32 master [n_vecs * 128]
+  const int64_t* doc_off;  // [n_sets + 1]
+  int64_t n_sets;
+  float* scores;
+  int* status;
+  int max_q_len;
+};
+
+constexpr int kRing = 4;  // 8-vector stages in a warp's ring
+constexpr int kStreamRowmax = 1024;  // row maxima a warp keeps (chunk pairs x max_q_len)
+
+// Pairs per chunk for queries of at most max_q_len rows.
+__host__ __device__ constexpr int stream_chunk(int max_q_len) {
+  return kStreamRowmax / max_q_len < 1 ? 1 : (kStreamRowmax / max_q_len > 32 ? 32 : kStreamRowmax / max_q_len);
+}
+
+// Exact scores of the pairs t_begin .. t_end - 1 by one warp, with the per-pair
+// arithmetic of warp_chamfer (bit-identical scores).  The range is cut into
+// chunks of at most stream_chunk(max_q_len) pairs of one query; a chunk is taken
+// one 32-row group of the query at a time (the query registers are loaded once
+// per chunk and group, or once per query when it has one group), and its pairs'
+// row maxima collect in rowmax [chunk][max_q_len] until every group is done; then
+// lane i takes the Kahan sum of pair i.  The set vectors of the whole range
+// stream through a ring of kRing 8-vector stages with cp.async, kRing - 1 blocks
+// ahead and across pair, group and chunk boundaries, so the gathers of the next
+// sets overlap the arithmetic of the current one (a chunk's later groups re-read
+// its sets from L2).  Scores: -inf for a negative id, NaN and a status for an id
+// >= n_sets or a query longer than max_q_len.
+template <bool L2>
+__device__ __forceinline__ void stream_pairs(const StreamArgs& a, int64_t t_begin, int64_t t_end, float* ring,
+                                             float* rowmax) {
+  if (t_begin >= t_end) return;
+  const int lane = threadIdx.x & 31;
+  const int half = lane & 1;
+  const int pair = lane >> 1;
+  const int st_off = 4 * lane + (lane >= 16 ? 4 : 0);
+  const int rd_off = half * (kDim / 2 + 4);
+  const int chunk_max = stream_chunk(a.max_q_len);
+  int q_first = 0;  // the query owning t_begin
+  {
+    int hi = a.n_queries - 1;
+    while (q_first < hi) {
+      const int mid = (q_first + hi + 1) >> 1;
+      if (a.cand_off[mid] <= t_begin) q_first = mid; else hi = mid - 1;
+    }
+  }
+  // the chunk starting at pair c0 (b: a query at or before c0's); nrg = its
+  // 32-row groups, 0 for a query longer than max_q_len
+  struct Chunk {
+    int64_t c0, c1;
+    int b, nrg;
+  };
+  auto chunk_at = [&](int64_t c0, int b) -> Chunk {
+    Chunk c;
+    c.c0 = c0;
+    if (c0 >= t_end) {
+      c.c1 = c0;
+      c.b = b;
+      c.nrg = 0;
+      return c;
+    }
+    while (c0 >= a.cand_off[b + 1]) ++b;
+    c.b = b;
+    c.c1 = min(min(c0 + chunk_max, t_end), a.cand_off[b + 1]);
+    const int m = (int)(a.q_off[b + 1] - a.q_off[b]);
+    c.nrg = m > a.max_q_len ? 0 : (m + 31) >> 5;
+    return c;
+  };
+  // lane i: row offset and length of the chunk's pair i (length 0: nothing to
+  // stream -- an invalid id, or a chunk with no groups)
+  auto chunk_info = [&](const Chunk& c, int64_t& r0, int& mp) {
+    const int64_t t = c.c0 + lane;
+    r0 = 0;
+    mp = 0;
+    if (t < c.c1 && c.nrg > 0) {
+      const int64_t id = a.cand_ids[t];
+      if (id >= 0 && id < a.n_sets) {
+        r0 = a.doc_off[id];
+        mp = (int)(a.doc_off[id + 1] - r0);
+      }
+    }
+  };
+
+  // ---- producer: the blocks in the consumer's order (chunk, group, pair, block)
+  Chunk pc = chunk_at(t_begin, q_first);
+  int64_t p_r0;
+  int p_mp;
+  chunk_info(pc, p_r0, p_mp);
+  Chunk pn = chunk_at(pc.c1, pc.b);  // the next chunk, its infos loaded a chunk ahead
+  int64_t n_r0;
+  int n_mp;
+  chunk_info(pn, n_r0, n_mp);
+  int rgp = 0, ip = 0, bp = 0;
+  int mp_cur = __shfl_sync(0xffffffffu, p_mp, 0);
+  int64_t r0_cur = __shfl_sync(0xffffffffu, p_r0, 0);
+  uint32_t issued = 0;
+  auto issue = [&]() {
+    while (pc.c0 < t_end && bp * kVecBlock >= mp_cur) {
+      bp = 0;
+      if (++ip >= (int)(pc.c1 - pc.c0)) {  // a pass over the chunk is done
+        ip = 0;
+        if (++rgp >= pc.nrg) {             // the chunk is done
+          rgp = 0;
+          pc = pn;
+          p_r0 = n_r0;
+          p_mp = n_mp;
+          if (pc.c0 >= t_end) break;
+          pn = chunk_at(pc.c1, pc.b);
+          chunk_info(pn, n_r0, n_mp);
+        }
+      }
+      mp_cur = __shfl_sync(0xffffffffu, p_mp, ip);
+      r0_cur = __shfl_sync(0xffffffffu, p_r0, ip);
+    }
+    if (pc.c0 < t_end) {
+      float* dst = ring + (issued % kRing) * (kVecBlock * kStageStride);
+      const float* srcp = a.docs + (r0_cur + (int64_t)bp * kVecBlock) * kDim + 4 * lane;
+      const int nv = min(kVecBlock, mp_cur - bp * kVecBlock);
+#pragma unroll
+      for (int v = 0; v < kVecBlock; ++v)
+        if (v < nv) cp_async16(dst + v * kStageStride + st_off, srcp + v * kDim);
+      ++bp;
+    }
+    cp_async_commit();
+    ++issued;
+  };
+#pragma unroll
+  for (int i = 0; i < kRing - 1; ++i) issue();
+
+  // ---- consumer
+  uint64_t qr[kQPairs];
+  int loaded_b = -1;  // query whose only row group is in qr
+  uint32_t consumed = 0;
+  for (Chunk cc = chunk_at(t_begin, q_first); cc.c0 < t_end; cc = chunk_at(cc.c1, cc.b)) {
+    const int64_t q0 = a.q_off[cc.b];
+    const int m_q = (int)(a.q_off[cc.b + 1] - q0);
+    const int n = (int)(cc.c1 - cc.c0);
+    const int64_t my_id = lane < n ? a.cand_ids[cc.c0 + lane] : -1;
+    const int my_mp = (my_id >= 0 && my_id < a.n_sets) ? (int)(a.doc_off[my_id + 1] - a.doc_off[my_id]) : 0;
+    for (int rg = 0; rg < cc.nrg; ++rg) {
+      const int ia = rg * 32 + 2 * pair, ib = ia + 1;
+      if (cc.nrg > 1 || cc.b != loaded_b) {
+        // rows ia and ib, components 64 half .. 64 half + 63, as packed pairs
+        const float4* ra = reinterpret_cast<const float4*>(a.q + (q0 + ia) * kDim + half * (kDim / 2));
+        const float4* rb = reinterpret_cast<const float4*>(a.q + (q0 + ib) * kDim + half * (kDim / 2));
+#pragma unroll
+        for (int j = 0; j < kRowPairs / 2; ++j) {
+          const float4 va = ia < m_q ? ra[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 vb = ib < m_q ? rb[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+          qr[2 * j] = pack2(va.x, va.y);
+          qr[2 * j + 1] = pack2(va.z, va.w);
+          qr[kRowPairs + 2 * j] = pack2(vb.x, vb.y);
+          qr[kRowPairs + 2 * j + 1] = pack2(vb.z, vb.w);
+        }
+        loaded_b = cc.nrg > 1 ? -1 : cc.b;
+      }
+      for (int i = 0; i < n; ++i) {
+        const int m_p = __shfl_sync(0xffffffffu, my_mp, i);
+        if (m_p == 0) continue;
+        float best_a = -INFINITY, best_b = -INFINITY;
+        const int nb = (m_p + kVecBlock - 1) / kVecBlock;
+        for (int blk = 0; blk < nb; ++blk) {
+          issue();
+          cp_async_wait<kRing - 1>();
+          __syncwarp();
+          const float* stage = ring + (consumed % kRing) * (kVecBlock * kStageStride);
+          block_terms<L2>(stage, rd_off, qr, min(kVecBlock, m_p - blk * kVecBlock), best_a, best_b);
+          __syncwarp();
+          ++consumed;
+        }
+        float* rm = rowmax + i * a.max_q_len;
+        if (half == 0 && ia < m_q) rm[ia] = row_term<L2>(best_a);
+        if (half == 1 && ib < m_q) rm[ib] = row_term<L2>(best_b);
+      }
+    }
+    __syncwarp();
+    // lane i: the score of the chunk's pair i
+    if (lane < n) {
+      float score;
+      if (my_id < 0) {
+        score = -INFINITY;
+      } else if (my_id >= a.n_sets || m_q > a.max_q_len) {
+        set_status(a.status, my_id >= a.n_sets ? kDevBounds : kDevInvalid);
+        score = __int_as_float(0x7fc00000);
+      } else {
+        const float* rm = rowmax + lane * a.max_q_len;
+        float s = 0.f, c = 0.f;  // Kahan sum, compensation
+        for (int i = 0; i < m_q; ++i) {
+          const float y = __fsub_rn(rm[i], c);
+          const float tt = __fadd_rn(s, y);
+          c = __fsub_rn(__fsub_rn(tt, s), y);
+          s = tt;
+        }
+        score = s;
+      }
+      a.scores[cc.c0 + lane] = score;
+    }
+    __syncwarp();
+  }
+  cp_async_wait<0>();
+}
+
 }  // namespace gem
