@@ -175,35 +175,53 @@ def test_score_ids_f32_matches_oracle(gem, cfg1):
 
 
 def test_score_ids_streamed_rerank_bit_matches(gem, cfg1):
-    """Queries of at most 32 rows take the streamed id-list kernel (set vectors
-    gathered ahead across pairs); it must give the bits of the per-pair kernel
-    (taken with a workspace for longer queries) and match the oracle.  60,000
-    pairs: every warp crosses several 32-pair windows; -1 ids and empty lists
-    included."""
+    """The exact id-list path streams the set vectors of a warp's whole range
+    (gathered ahead across pairs, chunks and queries).  Query sets of 1 .. 128
+    vectors take 1 to 4 groups of 32 rows per chunk of pairs; 60,000 pairs, so
+    every warp crosses chunk and query boundaries; -1 ids and an empty list.
+    Scores bit-identical to the all-sets FP32 form (the per-pair routine) and
+    within 1e-5 of the L1 of the terms of the oracle."""
     w = cfg1["w"]
     rng = np.random.default_rng(11)
-    B = 10
+    q_lens = np.array([1, 5, 31, 32, 33, 64, 65, 100, 128, 7])
+    qs = synth.vector_sets(q_lens, synth.centres(64, 1235), 991)
+    q, qo = qs.vecs.cuda(), torch.from_numpy(qs.offsets).cuda()
+    B = len(q_lens)
     lens = rng.integers(0, 12000, size=B)
     lens[3] = 0
     co = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
     ids = rng.integers(-1, w.docs.n_sets, size=int(co[-1])).astype(np.int64)
-    ws32 = gem.Workspace(cfg1["store"], max_queries=64, max_q_rows=4096, max_q_len=32, max_cands=int(co[-1]))
-    args = (cfg1["q"], cfg1["qo"], torch.from_numpy(co).cuda(), torch.from_numpy(ids).cuda(), "f32")
-    S32 = gem.score_ids(cfg1["store"], ws32, *args).cpu().numpy()
-    assert ws32.status() == 0
-    wsl = gem.Workspace(cfg1["store"], max_queries=64, max_q_rows=4096, max_q_len=128, max_cands=int(co[-1]))
-    Sl = gem.score_ids(cfg1["store"], wsl, *args).cpu().numpy()
-    np.testing.assert_array_equal(S32.view(np.uint32), Sl.view(np.uint32))
-    b_of = np.repeat(np.arange(B), lens)
-    pick = rng.choice(len(ids), size=300, replace=False)
-    for t in pick:
-        if ids[t] < 0:
-            assert S32[t] == -np.inf
-        else:
-            want = cfg1["S64"][b_of[t], ids[t]]
-            assert abs(S32[t] - want) <= 1e-5 * cfg1["L1"][b_of[t], ids[t]]
-    ws32.close()
-    wsl.close()
+    for mq in (128, 256):
+        ws = gem.Workspace(cfg1["store"], max_queries=64, max_q_rows=4096, max_q_len=mq, max_cands=int(co[-1]))
+        S = gem.score_ids(cfg1["store"], ws, q, qo, torch.from_numpy(co).cuda(), torch.from_numpy(ids).cuda(),
+                          "f32").cpu().numpy()
+        S_all = gem.score_all(cfg1["store"], ws, q, qo, "f32").cpu().numpy()
+        assert ws.status() == 0
+        ws.close()
+        b_of = np.repeat(np.arange(B), lens)
+        ok = ids >= 0
+        np.testing.assert_array_equal(S[ok].view(np.uint32), S_all[b_of[ok], ids[ok]].view(np.uint32))
+        assert np.all(S[~ok] == -np.inf)
+    S64, L1 = oracle.score_all(qs.vecs, qs.offsets, w.docs.vecs, w.docs.offsets, with_l1=True)
+    for t in rng.choice(np.nonzero(ids >= 0)[0], size=300, replace=False):
+        assert abs(S[t] - S64[b_of[t], ids[t]]) <= 1e-5 * L1[b_of[t], ids[t]]
+
+
+def test_score_ids_query_longer_than_workspace_limit(gem, cfg1):
+    """A query set longer than the workspace's max_q_len: its pairs score NaN and
+    the status reads GEM_ERR_INVALID; the other queries' pairs are unaffected."""
+    w = cfg1["w"]
+    qs = synth.vector_sets(np.array([20, 40, 20]), synth.centres(64, 1235), 992)
+    q, qo = qs.vecs.cuda(), torch.from_numpy(qs.offsets).cuda()
+    co = torch.tensor([0, 3, 6, 9], dtype=torch.int64, device="cuda")
+    ids = torch.tensor([0, 1, 2] * 3, dtype=torch.int64, device="cuda")
+    ws = gem.Workspace(cfg1["store"], max_queries=8, max_q_rows=256, max_q_len=32, max_cands=64)
+    S = gem.score_ids(cfg1["store"], ws, q, qo, co, ids, "f32").cpu().numpy()
+    assert ws.status() == 1                # GEM_ERR_INVALID
+    ws.close()
+    assert np.all(np.isnan(S[3:6])) and np.all(np.isfinite(S[:3])) and np.all(np.isfinite(S[6:]))
+    want = oracle.score_ids(qs.vecs, qs.offsets, w.docs.vecs, w.docs.offsets, co.cpu().numpy(), ids.cpu().numpy())
+    assert np.all(np.abs(S[[0, 1, 2, 6, 7, 8]] - want[[0, 1, 2, 6, 7, 8]]) <= 1e-5 * 40)
 
 
 def test_score_ids_out_of_range_id_sets_status(gem, cfg1):
