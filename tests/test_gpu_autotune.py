@@ -21,11 +21,11 @@ def gem():
 
 def test_autotune_score_all_bit_identical_and_cached(gem, tmp_path):
     w = synth.exact_fp32(n_sets=3000, n_queries=40)
-    store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("bf16", "fp8"))
+    store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("bf16", "fp8", "fp8_set"))
     ws = gem.Workspace(store, max_queries=64, max_q_rows=64 * 32, max_q_len=32)
     q, qo = w.queries.vecs.cuda(), torch.from_numpy(w.queries.offsets).cuda()
     cache = str(tmp_path / "tune.json")
-    for compute in ("bf16", "fp8"):
+    for compute in ("bf16", "fp8", "fp8_set"):
         gem.set_schedule(ws, 2, 1 << 16)
         ref = gem.score_all(store, ws, q, qo, compute).clone()
         ch = gem.autotune_score_all(store, ws, q, qo, compute, cache_path=cache)
@@ -35,7 +35,7 @@ def test_autotune_score_all_bit_identical_and_cached(gem, tmp_path):
         again = gem.autotune_score_all(store, ws, q, qo, compute, cache_path=cache)
         assert again["from_cache"] and again["m_tiles"] == ch["m_tiles"]
     entries = json.load(open(cache))["entries"]
-    assert len(entries) == 2 and all(k.startswith("score_all|") for k in entries)
+    assert len(entries) == 3 and all(k.startswith("score_all|") for k in entries)
 
 
 def test_autotune_batch_choice_bit_matches(gem, tmp_path):
@@ -67,7 +67,7 @@ def test_every_schedule_bit_identical(gem, qlens):
     change the launch shape.  "mixed": queries of 1..100 rows, so slots of every
     size and up to four passes that add onto the previous pass's scores."""
     w = synth.exact_fp32(n_sets=2500, n_queries=37)
-    store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("bf16", "fp8"))
+    store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("bf16", "fp8", "fp8_set"))
     if qlens == "mixed":
         lens = np.random.default_rng(3).integers(1, 101, size=37)
         qs = synth.vector_sets(lens, synth.centres(64, 1235), 5150)
@@ -76,7 +76,7 @@ def test_every_schedule_bit_identical(gem, qlens):
     else:
         q, qo = w.queries.vecs.cuda(), torch.from_numpy(w.queries.offsets).cuda()
         ws = gem.Workspace(store, max_queries=64, max_q_rows=64 * 32, max_q_len=32)
-    for compute in ("bf16", "fp8"):
+    for compute in ("bf16", "fp8", "fp8_set"):
         outs = []
         for mt, var, cr in ((2, "two_sets", 1 << 16), (2, "plain", 1 << 16), (2, "a_tmem", 1 << 16),
                             (1, "two_sets", 1 << 16), (4, "plain", 1 << 14), (1, "plain", 1 << 18),
@@ -89,6 +89,14 @@ def test_every_schedule_bit_identical(gem, qlens):
         if qlens == "mixed" and compute == "bf16":
             Sq = oracle.score_all(oracle.bf16_round(qs.vecs.numpy()), qs.offsets,
                                   oracle.bf16_round(w.docs.vecs.numpy()), w.docs.offsets)
+            assert np.all(np.abs(outs[0].cpu().numpy() - Sq) <= 2e-4 * lens[:, None])
+        if qlens == "mixed" and compute == "fp8_set":
+            # multi-pass queries with the per-set scale applied at each pass's set end
+            c8, s8 = oracle.fp8_e4m3_quantize_sets(w.docs.vecs.numpy(), w.docs.offsets)
+            cq, sq = oracle.fp8_e4m3_quantize(qs.vecs.numpy())
+            Sq = oracle.score_all(cq * sq[:, None].astype(np.float64), qs.offsets,
+                                  c8 * np.repeat(s8.astype(np.float64), np.diff(w.docs.offsets))[:, None],
+                                  w.docs.offsets)
             assert np.all(np.abs(outs[0].cpu().numpy() - Sq) <= 2e-4 * lens[:, None])
     with pytest.raises(Exception):
         gem.set_schedule(ws, 4, 1 << 16, variant="a_tmem")
