@@ -243,58 +243,105 @@ struct ScanArgs {
   int* status;
 };
 
-__global__ void __launch_bounds__(256) qch_scan_kernel(ScanArgs a) {
+// A warp takes 32 consecutive (query, set) pairs at a time: lane i loads pair
+// i's set rows (one coalesced round for the 32), then the warp walks the pairs
+// with the first 32 codes of the next pair already loaded, gathering eight
+// table rows per step, and lane i keeps pair i's score for one store.
+constexpr int kScanCtasPerSm = 3;  // resident CTAs of 256 threads at the kernel's 80 registers
+constexpr int kScanUnroll = 16;    // table rows in flight per warp
+
+__global__ void __launch_bounds__(256, kScanCtasPerSm) qch_scan_kernel(ScanArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warp_g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const bool all_sets = (a.cand_ids == nullptr);
   const int64_t base = all_sets ? 0 : a.cand_off[a.q0];
   const int64_t total = all_sets ? (int64_t)a.nq * a.n_sets : a.cand_off[a.q0 + a.nq] - base;
-  for (int64_t w = warp_g; w < total; w += n_warps) {
-    int b;
-    int64_t id, out_idx;
-    if (all_sets) {
-      b = a.q0 + (int)(w / a.n_sets);
-      id = w % a.n_sets;
-      out_idx = (int64_t)b * a.n_sets + id;
-    } else {
-      out_idx = base + w;
-      id = a.cand_ids[out_idx];
-      int lo = a.q0, hi = a.q0 + a.nq - 1;  // query owning this candidate
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.cand_off[mid] <= out_idx) lo = mid; else hi = mid - 1;
-      }
-      b = lo;
-    }
-    float score;
-    if (id < 0) {
-      score = -INFINITY;
-    } else if (id >= a.n_sets) {
-      if (lane == 0) set_status(a.status, kDevBounds);
-      score = __int_as_float(0x7fc00000);
-    } else {
-      const int64_t r0 = a.doc_off[id], r1 = a.doc_off[id + 1];
-      const int np = (int)((a.q_off[b + 1] - a.q_off[b] + 31) / 32);
-      score = 0.f;
-      for (int pi = 0; pi < np; ++pi) {
-        const float* Tp = a.T + (int64_t)((b - a.q0) * a.max_np + pi) * a.k1 * 32;
-        float run = -INFINITY;
-        for (int64_t j0 = r0; j0 < r1; j0 += 32) {
-          const int nj = (int)min((int64_t)32, r1 - j0);
-          const int my_code = (lane < nj) ? a.codes[j0 + lane] : 0;
-          for (int j = 0; j < nj; ++j) {
-            const int cb = __shfl_sync(0xffffffffu, my_code, j);
-            run = fmaxf(run, Tp[(int64_t)cb * 32 + lane]);
-          }
+  const int64_t n_chunks = (total + 31) / 32;
+  for (int64_t ch = warp_g; ch < n_chunks; ch += n_warps) {
+    const int64_t w0 = ch * 32;
+    const int cnt = (int)min((int64_t)32, total - w0);
+    // lane i: pair w0 + i (its query, set id, output slot, set rows)
+    int my_b = a.q0;
+    int64_t my_id = -1, my_out = 0, my_r0 = 0, my_r1 = 0;
+    if (lane < cnt) {
+      const int64_t w = w0 + lane;
+      if (all_sets) {
+        my_b = a.q0 + (int)(w / a.n_sets);
+        my_id = w % a.n_sets;
+        my_out = (int64_t)my_b * a.n_sets + my_id;
+      } else {
+        my_out = base + w;
+        my_id = a.cand_ids[my_out];
+        int lo = a.q0, hi = a.q0 + a.nq - 1;  // query owning this candidate
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (a.cand_off[mid] <= my_out) lo = mid; else hi = mid - 1;
         }
-        float s = run;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        score = (pi == 0) ? s : score + s;
+        my_b = lo;
+      }
+      if (my_id >= 0 && my_id < a.n_sets) {
+        my_r0 = a.doc_off[my_id];
+        my_r1 = a.doc_off[my_id + 1];
       }
     }
-    if (lane == 0) a.out[out_idx] = score;
+    // codes of the next pair's first 32 rows, lane-wise
+    int next_code;
+    {
+      const int64_t r0 = __shfl_sync(0xffffffffu, (long long)my_r0, 0);
+      const int64_t r1 = __shfl_sync(0xffffffffu, (long long)my_r1, 0);
+      next_code = (r0 + lane < r1) ? a.codes[r0 + lane] : 0;
+    }
+    float my_score = 0.f;
+    for (int i = 0; i < cnt; ++i) {
+      const int b = __shfl_sync(0xffffffffu, my_b, i);
+      const int64_t id = __shfl_sync(0xffffffffu, (long long)my_id, i);
+      const int64_t r0 = __shfl_sync(0xffffffffu, (long long)my_r0, i);
+      const int64_t r1 = __shfl_sync(0xffffffffu, (long long)my_r1, i);
+      const int code0 = next_code;
+      {
+        const int nx = i + 1 < cnt ? i + 1 : i;
+        const int64_t n0 = __shfl_sync(0xffffffffu, (long long)my_r0, nx);
+        const int64_t n1 = __shfl_sync(0xffffffffu, (long long)my_r1, nx);
+        if (i + 1 < cnt) next_code = (n0 + lane < n1) ? a.codes[n0 + lane] : 0;
+      }
+      float score;
+      if (id < 0) {
+        score = -INFINITY;
+      } else if (id >= a.n_sets) {
+        if (lane == 0) set_status(a.status, kDevBounds);
+        score = __int_as_float(0x7fc00000);
+      } else {
+        const int np = (int)((a.q_off[b + 1] - a.q_off[b] + 31) / 32);
+        score = 0.f;
+        for (int pi = 0; pi < np; ++pi) {
+          const float* Tp = a.T + (int64_t)((b - a.q0) * a.max_np + pi) * a.k1 * 32;
+          float run = -INFINITY;
+          for (int64_t j0 = r0; j0 < r1; j0 += 32) {
+            const int nj = (int)min((int64_t)32, r1 - j0);
+            const int my_code = j0 == r0 ? code0 : ((lane < nj) ? a.codes[j0 + lane] : 0);
+            // kScanUnroll table rows in flight per step (the max is exact, so the
+            // order of the rows does not matter); rows past nj repeat row 0
+            for (int j = 0; j < nj; j += kScanUnroll) {
+              float v[kScanUnroll];
+#pragma unroll
+              for (int u = 0; u < kScanUnroll; ++u) {
+                const int cb = __shfl_sync(0xffffffffu, my_code, j + u < nj ? j + u : 0);
+                v[u] = Tp[(int64_t)cb * 32 + lane];
+              }
+#pragma unroll
+              for (int u = 0; u < kScanUnroll; ++u) run = fmaxf(run, v[u]);
+            }
+          }
+          float sum = run;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+          score = (pi == 0) ? sum : score + sum;
+        }
+      }
+      if (lane == i) my_score = score;
+    }
+    if (lane < cnt) a.out[my_out] = my_score;
   }
 }
 
@@ -406,7 +453,7 @@ gem_status launch_qch_scan_ids(const gem_store* s, const float* T, const int64_t
   a.cand_ids = cand_ids;
   a.out = out;
   a.status = status;
-  qch_scan_kernel<<<s->n_sm * 8, 256, 0, st>>>(a);
+  qch_scan_kernel<<<s->n_sm * kScanCtasPerSm, 256, 0, st>>>(a);
   GEM_CUDA_TRY(cudaGetLastError());
   note_launches(1);
   return GEM_OK;
@@ -443,7 +490,7 @@ gem_status launch_qch(const gem_store* s, gem_workspace* w, const float* q, cons
     a.cand_ids = cand_ids;
     a.out = est;
     a.status = w->d_status;
-    qch_scan_kernel<<<s->n_sm * 8, 256, 0, st>>>(a);
+    qch_scan_kernel<<<s->n_sm * kScanCtasPerSm, 256, 0, st>>>(a);
     GEM_CUDA_TRY(cudaGetLastError());
     note_launches(2);
   }
