@@ -280,7 +280,8 @@ void gem_workspace_destroy(gem_workspace* w) {
                   w->d_part_pass, w->d_part_slot, w->d_part_row0, w->d_row_part, w->d_qpack_bf16,
                   w->d_qpack_fp8, w->d_qpack_scale, w->d_scores, w->d_pool_ids, w->d_pool_off,
                   w->d_pool_scores, w->d_q_in, w->d_qo_in, w->d_out_ids, w->d_out_scores,
-                  w->d_qcodes, w->d_assign_key, w->d_tables, w->d_topk_thr, w->d_topk_cnt, w->d_topk_cand};
+                  w->d_qcodes, w->d_assign_key, w->d_tables, w->d_topk_thr, w->d_topk_cnt, w->d_topk_cand,
+                  w->d_pool_perm, w->d_pool_bucket};
   for (void* p : ptrs) dfree(p);
   cudaSetDevice(prev);
   delete w;
@@ -351,6 +352,10 @@ gem_status gem_workspace_create(const gem_store* s, int32_t max_queries, int64_t
   if (max_cands > 0) {
     WS_ALLOC(d_pool_ids, max_cands);
     WS_ALLOC(d_pool_scores, max_cands);
+    if (max_cands < INT32_MAX) {
+      WS_ALLOC(d_pool_perm, max_cands);
+      WS_ALLOC(d_pool_bucket, kPoolKeys);
+    }
   }
   if (s->k1 > 0) {
     // tables of up to 16 query parts (8 MB each at k1 = 65536)
@@ -773,8 +778,7 @@ static gem_status search_impl(const gem_store* s, gem_workspace* w, const float*
   if (r != GEM_OK) return r;
   launch_iota_offsets(w->d_pool_off, n_queries, rerank_depth, st);
   GEM_CUDA_TRY(cudaGetLastError());
-  r = launch_f32_score(s, w, q, q_offsets, n_queries, w->d_pool_off, w->d_pool_ids,
-                       (int64_t)n_queries * rerank_depth, w->d_pool_scores, st);
+  r = launch_f32_score_pool(s, w, q, q_offsets, n_queries, rerank_depth, w->d_pool_ids, w->d_pool_scores, st);
   if (r != GEM_OK) return r;
   return launch_topk(w, w->d_pool_scores, nullptr, n_queries, rerank_depth, w->d_pool_ids, k, out_ids,
                      out_scores, st);

@@ -141,6 +141,8 @@ struct gem_workspace {
   int64_t* d_pool_ids = nullptr;   // [max_cands]
   int64_t* d_pool_off = nullptr;   // [max_queries + 1]
   float* d_pool_scores = nullptr;  // [max_cands]
+  int32_t* d_pool_perm = nullptr;  // [max_cands] rerank order: by segment of set ids, then query
+  int* d_pool_bucket = nullptr;    // [kPoolKeys] counts, then cursors, of that order
 
   // threshold top-k of long dense rows (topk.cu): per row a key threshold, a
   // counter and a candidate buffer of topk_cap keys, for topk_rows rows at a time
@@ -236,6 +238,18 @@ gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* 
                             const int64_t* q_offsets, int32_t n_queries, const int64_t* cand_offsets,
                             const int64_t* cand_ids, int64_t n_cands, float* scores, cudaStream_t st,
                             const int32_t* qcodes = nullptr, bool stored_codes = false);
+// Exact FP32 scores of a rerank pool of per_query candidates per query
+// (cand_ids [n_queries * per_query]), taken segment of set ids by segment
+// (the order is built in the workspace), so that a set several queries share is
+// gathered from DRAM about once; scores land in pool order, bit-identical to
+// launch_f32_score.  Pools below kPoolMinEntries are taken in query order.
+constexpr int kPoolSegs = 64;
+constexpr int kPoolKeys = 65536;  // segments x queries
+constexpr int64_t kPoolMinEntries = 65536;
+constexpr int kPoolGroup = 32;    // positions a warp takes at a time
+gem_status launch_f32_score_pool(const gem_store* s, gem_workspace* ws, const float* q, const int64_t* q_offsets,
+                                 int32_t n_queries, int32_t per_query, const int64_t* cand_ids, float* scores,
+                                 cudaStream_t st);
 
 // MaxSim forward with argmax and backward (backward.cu).
 gem_status launch_maxsim_fwd(const float* q, const int64_t* q_off, int32_t n_queries, const float* docs,

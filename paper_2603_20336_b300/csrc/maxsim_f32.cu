@@ -129,7 +129,8 @@ f32_ids_kernel(F32Args a, int max_q_len, int64_t n_cands) {
 
 // Id lists, exact form: every warp takes one contiguous range of the n_cands
 // candidates (equal shares, whatever the list lengths) and streams it
-// (stream_pairs in maxsim_simt.cuh: bit-identical to warp_chamfer).
+// (stream_pairs in maxsim_simt.cuh: bit-identical to warp_chamfer); a pool in
+// segment order is taken in groups of kPoolGroup positions, grid-strided.
 template <bool L2>
 __global__ void __launch_bounds__(kF32Threads, 2)
 f32_ids_stream_kernel(StreamArgs a, int64_t n_cands) {
@@ -138,10 +139,75 @@ f32_ids_stream_kernel(StreamArgs a, int64_t n_cands) {
   float* ring = sm + warp * kRing * kVecBlock * kStageStride;
   float* rowmax = sm + kF32Warps * kRing * kVecBlock * kStageStride + warp * kStreamRowmax;
   const int64_t n_warps = (int64_t)gridDim.x * kF32Warps;
+  const int64_t gw = (int64_t)blockIdx.x * kF32Warps + warp;
+  if (a.perm) {
+    // a pool in segment order: all warps move through the positions together,
+    // kPoolGroup at a time, so the sets in use at any moment come from one or
+    // two segments of set ids
+    for (int64_t p0 = gw * kPoolGroup; p0 < n_cands; p0 += n_warps * kPoolGroup)
+      stream_pairs<L2>(a, p0, min(n_cands, p0 + kPoolGroup), ring, rowmax);
+    return;
+  }
   const int64_t chunk = (n_cands + n_warps - 1) / n_warps;
-  const int64_t t_begin = min(n_cands, ((int64_t)blockIdx.x * kF32Warps + warp) * chunk);
+  const int64_t t_begin = min(n_cands, gw * chunk);
   const int64_t t_end = min(n_cands, t_begin + chunk);
   stream_pairs<L2>(a, t_begin, t_end, ring, rowmax);
+}
+
+// Order of a rerank pool (per_query entries per query) for the exact rescoring:
+// by segment of set ids first (K equal ranges of ids), then by query, so that
+// at any time the warps work inside one segment and a set several queries share
+// is read from DRAM about once (the segment's sets fit in L2), while each warp
+// still takes runs of one query's entries.  A counting sort on the key
+// segment * n_queries + query: count, exclusive scan, scatter (the order inside
+// a key depends on atomics; the scores do not, each entry is scored alone).
+__device__ __forceinline__ int pool_key(const int64_t* ids, int64_t i, int per_query, int n_queries, int64_t n_sets,
+                                        int segs) {
+  const int64_t id = ids[i];
+  const int seg = (id >= 0 && id < n_sets) ? (int)(id * segs / n_sets) : segs - 1;
+  return seg * n_queries + (int)(i / per_query);
+}
+
+__global__ void pool_key_count_kernel(const int64_t* __restrict__ ids, int64_t n, int per_query, int n_queries,
+                                      int64_t n_sets, int segs, int* __restrict__ cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(cnt + pool_key(ids, i, per_query, n_queries, n_sets, segs), 1);
+}
+
+// one block of 1024 threads: cnt[0 .. nk) becomes its exclusive prefix sum
+__global__ void __launch_bounds__(1024) pool_key_scan_kernel(int* __restrict__ cnt, int nk) {
+  __shared__ int part[1024];
+  constexpr int kPer = kPoolKeys / 1024;
+  const int t = threadIdx.x;
+  int sum = 0;
+  for (int j = 0; j < kPer; ++j) {
+    const int i = t * kPer + j;
+    sum += i < nk ? cnt[i] : 0;
+  }
+  part[t] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the per-thread sums
+    const int x = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += x;
+    __syncthreads();
+  }
+  int run = part[t] - sum;
+  for (int j = 0; j < kPer; ++j) {
+    const int i = t * kPer + j;
+    if (i < nk) {
+      const int v = cnt[i];
+      cnt[i] = run;
+      run += v;
+    }
+  }
+}
+
+__global__ void pool_key_scatter_kernel(const int64_t* __restrict__ ids, int64_t n, int per_query, int n_queries,
+                                        int64_t n_sets, int segs, int* __restrict__ cursor,
+                                        int32_t* __restrict__ perm) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    perm[atomicAdd(cursor + pool_key(ids, i, per_query, n_queries, n_sets, segs), 1)] = (int32_t)i;
 }
 
 }  // namespace
@@ -203,6 +269,47 @@ gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* 
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(max_grid, (int64_t)s->n_sm * per_sm));
     kern<<<grid, kF32Threads, smem, st>>>(a, mq, n_cands);
   }
+  GEM_CUDA_TRY(cudaGetLastError());
+  note_launches(1);
+  return GEM_OK;
+}
+
+gem_status launch_f32_score_pool(const gem_store* s, gem_workspace* ws, const float* q, const int64_t* q_offsets,
+                                 int32_t n_queries, int32_t per_query, const int64_t* cand_ids, float* scores,
+                                 cudaStream_t st) {
+  const int64_t n = (int64_t)n_queries * per_query;
+  // small pools (the three grouping launches would not pay) and pools the
+  // workspace has no order buffer for: query order
+  if (n < kPoolMinEntries || !ws->d_pool_perm || n > ws->max_cands)
+    return launch_f32_score(s, ws, q, q_offsets, n_queries, ws->d_pool_off, cand_ids, n, scores, st);
+  // segments: up to kPoolSegs, at most kPoolKeys keys
+  const int segs = (int)std::max<int64_t>(1, std::min<int64_t>(kPoolSegs, kPoolKeys / n_queries));
+  if (segs < 2) return launch_f32_score(s, ws, q, q_offsets, n_queries, ws->d_pool_off, cand_ids, n, scores, st);
+  const int nk = segs * n_queries;
+  GEM_CUDA_TRY(cudaMemsetAsync(ws->d_pool_bucket, 0, sizeof(int) * nk, st));
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)s->n_sm * 8);
+  pool_key_count_kernel<<<grid, 256, 0, st>>>(cand_ids, n, per_query, n_queries, s->n_sets, segs,
+                                              ws->d_pool_bucket);
+  pool_key_scan_kernel<<<1, 1024, 0, st>>>(ws->d_pool_bucket, nk);
+  pool_key_scatter_kernel<<<grid, 256, 0, st>>>(cand_ids, n, per_query, n_queries, s->n_sets, segs,
+                                                ws->d_pool_bucket, ws->d_pool_perm);
+  GEM_CUDA_TRY(cudaGetLastError());
+  note_launches(3);
+  const int mq = ws->max_q_len;
+  const bool l2 = ws->sim == GEM_SIM_L2;
+  StreamArgs sa{q, q_offsets, n_queries, ws->d_pool_off, cand_ids, s->d_f32, s->d_offsets, s->n_sets,
+                scores, ws->d_status, mq};
+  sa.perm = ws->d_pool_perm;
+  sa.per_query = per_query;
+  const size_t smem = sizeof(float) * (kF32Warps * kRing * kVecBlock * kStageStride + kF32Warps * kStreamRowmax);
+  auto kern = l2 ? f32_ids_stream_kernel<true> : f32_ids_stream_kernel<false>;
+  GEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kF32Threads, smem));
+  if (per_sm < 1) return fail(GEM_ERR_UNSUPPORTED, "f32 scoring kernel does not fit on an SM");
+  const int64_t max_grid = (n + kF32Warps - 1) / kF32Warps;
+  const int kgrid = (int)std::max<int64_t>(1, std::min<int64_t>(max_grid, (int64_t)s->n_sm * per_sm));
+  kern<<<kgrid, kF32Threads, smem, st>>>(sa, n);
   GEM_CUDA_TRY(cudaGetLastError());
   note_launches(1);
   return GEM_OK;

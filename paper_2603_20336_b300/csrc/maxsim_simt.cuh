@@ -212,6 +212,11 @@ struct StreamArgs {
   float* scores;
   int* status;
   int max_q_len;
+  // optional processing order: position i takes pair perm[i], whose query is
+  // perm[i] / per_query (a pool of per_query candidates per query); a chunk is
+  // then a run of positions whose pairs share a query
+  const int32_t* perm = nullptr;
+  int per_query = 0;
 };
 
 constexpr int kRing = 4;  // 8-vector stages in a warp's ring
@@ -245,13 +250,15 @@ __device__ __forceinline__ void stream_pairs(const StreamArgs& a, int64_t t_begi
   const int rd_off = half * (kDim / 2 + 4);
   const int chunk_max = stream_chunk(a.max_q_len);
   int q_first = 0;  // the query owning t_begin
-  {
+  if (!a.perm) {
     int hi = a.n_queries - 1;
     while (q_first < hi) {
       const int mid = (q_first + hi + 1) >> 1;
       if (a.cand_off[mid] <= t_begin) q_first = mid; else hi = mid - 1;
     }
   }
+  // the pair at position i
+  auto pair_at = [&](int64_t i) -> int64_t { return a.perm ? (int64_t)a.perm[i] : i; };
   // the chunk starting at pair c0 (b: a query at or before c0's); nrg = its
   // 32-row groups, 0 for a query longer than max_q_len
   struct Chunk {
@@ -267,9 +274,19 @@ __device__ __forceinline__ void stream_pairs(const StreamArgs& a, int64_t t_begi
       c.nrg = 0;
       return c;
     }
-    while (c0 >= a.cand_off[b + 1]) ++b;
+    if (a.perm) {
+      // the run of positions from c0 whose pairs belong to c0's query (at most
+      // chunk_max): lane i looks at position c0 + i
+      b = (int)(pair_at(c0) / a.per_query);
+      const int64_t pi = c0 + lane;
+      const bool other = lane >= chunk_max || pi >= t_end || (int)(pair_at(pi) / a.per_query) != b;
+      const uint32_t m = __ballot_sync(0xffffffffu, other);
+      c.c1 = c0 + (m ? __ffs(m) - 1 : 32);
+    } else {
+      while (c0 >= a.cand_off[b + 1]) ++b;
+      c.c1 = min(min(c0 + chunk_max, t_end), a.cand_off[b + 1]);
+    }
     c.b = b;
-    c.c1 = min(min(c0 + chunk_max, t_end), a.cand_off[b + 1]);
     const int m = (int)(a.q_off[b + 1] - a.q_off[b]);
     c.nrg = m > a.max_q_len ? 0 : (m + 31) >> 5;
     return c;
@@ -281,7 +298,7 @@ __device__ __forceinline__ void stream_pairs(const StreamArgs& a, int64_t t_begi
     r0 = 0;
     mp = 0;
     if (t < c.c1 && c.nrg > 0) {
-      const int64_t id = a.cand_ids[t];
+      const int64_t id = a.cand_ids[pair_at(t)];
       if (id >= 0 && id < a.n_sets) {
         r0 = a.doc_off[id];
         mp = (int)(a.doc_off[id + 1] - r0);
@@ -343,7 +360,8 @@ __device__ __forceinline__ void stream_pairs(const StreamArgs& a, int64_t t_begi
     const int64_t q0 = a.q_off[cc.b];
     const int m_q = (int)(a.q_off[cc.b + 1] - q0);
     const int n = (int)(cc.c1 - cc.c0);
-    const int64_t my_id = lane < n ? a.cand_ids[cc.c0 + lane] : -1;
+    const int64_t my_pair = lane < n ? pair_at(cc.c0 + lane) : 0;
+    const int64_t my_id = lane < n ? a.cand_ids[my_pair] : -1;
     const int my_mp = (my_id >= 0 && my_id < a.n_sets) ? (int)(a.doc_off[my_id + 1] - a.doc_off[my_id]) : 0;
     for (int rg = 0; rg < cc.nrg; ++rg) {
       const int ia = rg * 32 + 2 * pair, ib = ia + 1;
@@ -401,7 +419,7 @@ __device__ __forceinline__ void stream_pairs(const StreamArgs& a, int64_t t_begi
         }
         score = s;
       }
-      a.scores[cc.c0 + lane] = score;
+      a.scores[my_pair] = score;
     }
     __syncwarp();
   }

@@ -296,6 +296,34 @@ def test_search_pipeline_matches_exact_top10(gem, cfg1, compute):
         assert np.all(err <= 1e-5 * cfg1["L1"][b, ids[b]])
 
 
+def test_search_large_pool_grouped_by_set_bit_matches_query_order(gem, cfg1):
+    """A rerank pool of 72 x 1,000 entries (past the size where the pool is
+    taken grouped by set id) and queries of 1..64 vectors: the search's ids and
+    scores equal the top-k of gem_score_ids over the same pool in query order,
+    bit for bit, and the reranked scores stay within the FP32 bound of the
+    oracle."""
+    w = cfg1["w"]
+    B, R, K = 72, 1000, 10
+    lens = np.random.default_rng(23).integers(1, 65, size=B)
+    qs = synth.vector_sets(lens, synth.centres(64, 1235), 4321)
+    q, qo = qs.vecs.cuda(), torch.from_numpy(qs.offsets).cuda()
+    ws = gem.Workspace(cfg1["store"], max_queries=B, max_q_rows=int(lens.sum()), max_q_len=64,
+                       max_cands=B * R, max_k=R)
+    pool, _ = gem.search(cfg1["store"], ws, q, qo, "bf16", rerank_depth=0, k=R)
+    co = torch.arange(0, B * R + 1, R, dtype=torch.int64, device="cuda")
+    ref = gem.score_ids(cfg1["store"], ws, q, qo, co, pool.reshape(-1).contiguous(), "f32")
+    want_i, want_s = gem.topk(ws, ref.view(B, R), K, ids=pool.contiguous())
+    got_i, got_s = gem.search(cfg1["store"], ws, q, qo, "bf16", rerank_depth=R, k=K)
+    assert ws.status() == 0
+    ws.close()
+    assert torch.equal(got_i, want_i)
+    assert torch.equal(got_s.view(torch.int32), want_s.view(torch.int32))
+    S64, L1 = oracle.score_all(qs.vecs, qs.offsets, w.docs.vecs, w.docs.offsets, with_l1=True)
+    gi, gs = got_i.cpu().numpy(), got_s.cpu().numpy().astype(np.float64)
+    for b in range(B):
+        assert np.all(np.abs(gs[b] - S64[b, gi[b]]) <= 1e-5 * L1[b, gi[b]])
+
+
 def test_search_host_buffers(gem, cfg1):
     w = cfg1["w"]
     q = w.queries.vecs.pin_memory()
