@@ -636,13 +636,18 @@ def run_reference(args, dist, rank, world):
             per_step.append(r)
     value = statistics.mean(r["value"] for r in per_step)
     ms = 1000.0 * statistics.mean(r["seconds"] for r in per_step)
+    # the GEM arm's workload (same sizes and recipe), of which each step scores a sample
+    V = int(synth.lengths_lognormal(cfg["n_sets"], 70.0, 0.5, 20, 180, 1236).sum())
+    B, R, K = cfg["n_queries"], cfg["rerank"], cfg["k"]
     line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "doc-sets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "text-corpus 500000 sets, 1000 queries x 32 (sample per step: 1 query x "
-                                   "20,000 sets of the same recipe drawn on the host; exact CH + top-100)",
-                       "queries_per_step": 1, "m_q": 32},
+            "config": {"workload": f"text-corpus {cfg['n_sets']} sets / {V} vectors, {B} queries x 32, "
+                                   f"top-{R} -> FP32 rerank -> top-{K}",
+                       "n_sets": cfg["n_sets"], "n_vecs": V, "queries": B, "m_q": 32, "rerank": R, "k": K,
+                       "sample_per_step": "1 query x the first 20,000 sets of the same recipe, drawn on the host; "
+                                          "exact CH (FP64) + top-100"},
             "cpu_baseline": {"value": value, "unit": "doc-sets/s", "cores": per_step[0]["cores"],
                              "kind": "oracle", "sample": "1 query x first 20,000 sets per step"},
             "e2e": {"value": value, "unit": "doc-sets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
