@@ -685,6 +685,23 @@ gem_status gem_shard_rerank(const gem_store* store, gem_workspace* ws, const flo
                             int64_t id_base, float* pool_scores, void* stream);
 
 /*
+ * gem_shard_score_ids: candidate lists routed to their owner shard (the scoring
+ * step of a beam expansion, Algorithm 5, over a sharded store).  cand_offsets
+ * int64 [n_queries + 1] and cand_ids int64 [n_cands] are as in gem_score_ids
+ * but hold GLOBAL set ids (-1 = empty); for every entry in the shard's range
+ * (id_base .. id_base + n_sets - 1) scores[j] receives what gem_score_ids with
+ * `compute` (GEM_F32 or GEM_CODES) gives on the whole store, bit for bit; every
+ * other entry is left as it is.  With scores filled with -inf beforehand, an
+ * element-wise max over the shards' buffers gives the whole-store scores.
+ * Needs a workspace with max_cands >= n_cands.  Device buffers, caller-owned;
+ * asynchronous on `stream`.
+ */
+gem_status gem_shard_score_ids(const gem_store* store, gem_workspace* ws, const float* q, const int64_t* q_offsets,
+                               int32_t n_queries, int64_t n_q_rows, const int64_t* cand_offsets,
+                               const int64_t* cand_ids, int64_t n_cands, int32_t compute, int64_t id_base,
+                               float* scores, void* stream);
+
+/*
  * gem_merge_topk: step 2: per row, the top k (score desc, id asc) of the union
  * of n_lists lists laid out [n_lists][rows][k_in] (scores float32, ids int64;
  * negative ids are empty slots).  out_ids int64 [rows x k], out_scores float32

@@ -54,6 +54,7 @@ SIGNATURES = {
     "gem_shard_ranges": (C.c_int, [P, I64, I32, P]),
     "gem_shard_first_pass": (C.c_int, [P, P, P, P, I32, I64, I32, I32, I64, P, P, P]),
     "gem_shard_rerank": (C.c_int, [P, P, P, P, I32, I64, P, I32, I64, P, P]),
+    "gem_shard_score_ids": (C.c_int, [P, P, P, P, I32, I64, P, P, I64, I32, I64, P, P]),
     "gem_merge_topk": (C.c_int, [P, P, I32, I32, I32, I32, P, P, P]),
     "gem_measure_peaks": (C.c_int, [P, P, P]),
 }

@@ -14,6 +14,10 @@
 //      entries the shard owns (the others keep the -inf the caller filled in);
 //      across GPUs an element-wise max combines them;
 //   4. gem_topk of the pool scores with the pool ids gives the top k.
+// Candidate lists (the scoring step of a beam expansion, Algorithm 5) are
+// routed the same way: every shard scores the listed ids it owns
+// (gem_shard_score_ids) into a buffer filled with -inf, and an element-wise max
+// across shards gives gem_score_ids on the whole store.
 #include <algorithm>
 #include <vector>
 
@@ -115,6 +119,30 @@ gem_status gem_shard_rerank(const gem_store* s, gem_workspace* w, const float* q
   r = launch_f32_score(s, w, q, q_offsets, n_queries, w->d_pool_off, w->d_pool_ids, n, w->d_pool_scores, st);
   if (r != GEM_OK) return r;
   scatter_owned_kernel<<<grid_for(n, s->n_sm), 256, 0, st>>>(w->d_pool_ids, w->d_pool_scores, n, pool_scores);
+  GEM_CUDA_TRY(cudaGetLastError());
+  note_launches(1);
+  return GEM_OK;
+}
+
+gem_status gem_shard_score_ids(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
+                               int32_t n_queries, int64_t n_q_rows, const int64_t* cand_offsets,
+                               const int64_t* cand_ids, int64_t n_cands, int32_t compute, int64_t id_base,
+                               float* scores, void* stream) {
+  gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
+  if (r != GEM_OK) return r;
+  if (!cand_offsets || (n_cands > 0 && (!cand_ids || !scores))) return fail(GEM_ERR_INVALID, "NULL argument");
+  if (n_cands < 0) return fail(GEM_ERR_INVALID, "n_cands < 0");
+  if (n_cands == 0) return GEM_OK;
+  if (!w->d_pool_ids || n_cands > w->max_cands) return fail(GEM_ERR_INVALID, "n_cands exceeds the workspace's max_cands");
+  if (id_base < 0) return fail(GEM_ERR_INVALID, "id_base < 0");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  local_ids_kernel<<<grid_for(n_cands, s->n_sm), 256, 0, st>>>(cand_ids, n_cands, id_base, s->n_sets, w->d_pool_ids);
+  GEM_CUDA_TRY(cudaGetLastError());
+  note_launches(1);
+  r = gem_score_ids(s, w, q, q_offsets, n_queries, n_q_rows, cand_offsets, w->d_pool_ids, n_cands, compute,
+                    w->d_pool_scores, stream);
+  if (r != GEM_OK) return r;
+  scatter_owned_kernel<<<grid_for(n_cands, s->n_sm), 256, 0, st>>>(w->d_pool_ids, w->d_pool_scores, n_cands, scores);
   GEM_CUDA_TRY(cudaGetLastError());
   note_launches(1);
   return GEM_OK;

@@ -13,6 +13,8 @@ operations: `GemEngine` runs them through the library's kernels) and an optional
 communicator: without one, every shard lives in this process and the gathered
 lists are written in place; with one (`DistComm` over torch.distributed, one shard
 per rank), the lists are all-gathered and the pool scores all-reduced by max.
+`sharded_score_ids` routes candidate lists of global ids the same way: each
+shard scores the entries it owns, and a max across shards combines them.
 """
 from __future__ import annotations
 
@@ -89,6 +91,11 @@ class GemEngine:
         _check(lib.gem_shard_rerank(sh.store.handle, sh.ws.handle, _ptr(q), _ptr(qo), rows, q.shape[0],
                                     _ptr(pool_ids), depth, sh.id_base, _ptr(pool_scores), _stream()))
 
+    def score_owned(self, sh: Shard, q, qo, cand_off, cand_ids, compute, scores):
+        _check(lib.gem_shard_score_ids(sh.store.handle, sh.ws.handle, _ptr(q), _ptr(qo), qo.numel() - 1,
+                                       q.shape[0], _ptr(cand_off), _ptr(cand_ids), cand_ids.numel(),
+                                       _dtype_code(compute), sh.id_base, _ptr(scores), _stream()))
+
     def topk(self, ws_shard: Shard, scores, ids, k):
         rows, cols = scores.shape
         out_i = self.ids((rows, k))
@@ -147,3 +154,21 @@ def sharded_search(engine, shards, n_shards: int, q, qo, compute, rerank_depth: 
     if comm is not None:
         comm.all_reduce_max(pool_sc)
     return engine.topk(shards[0], pool_sc, pool_ids, k)
+
+
+def sharded_score_ids(engine, shards, n_shards: int, q, qo, cand_off, cand_ids, compute="f32", comm=None):
+    """Scores of per-query candidate lists of GLOBAL set ids over all shards (the
+    scoring step of a beam expansion, Algorithm 5, routed to the owners): every
+    shard writes the entries it owns into a buffer of -inf, and an element-wise
+    max across shards combines them.  Equal, bit for bit, to gem_score_ids on the
+    whole store.  shards as in sharded_search.  Returns float32 [n_cands]."""
+    sc = engine.scores((cand_ids.numel(),), fill=float("-inf"))
+    if comm is None:
+        assert len(shards) == n_shards
+    else:
+        assert len(shards) == 1 and comm.world == n_shards
+    for sh in shards:
+        engine.score_owned(sh, q, qo, cand_off, cand_ids, compute, sc)
+    if comm is not None:
+        comm.all_reduce_max(sc)
+    return sc

@@ -85,3 +85,42 @@ def test_merge_topk_of_shard_major_lists(gem):
         wi, wsc = oracle.topk(s[keep], k, i[keep])
         np.testing.assert_array_equal(gi[r], wi)
         np.testing.assert_array_equal(gs[r].astype(np.float64), wsc)
+
+
+@pytest.mark.parametrize("n_shards", [2, 3])
+@pytest.mark.parametrize("compute", ["f32", "codes"])
+def test_routed_candidate_lists_bit_match_single_store(gem, data, n_shards, compute):
+    """Candidate lists of global ids (uneven lengths, an empty list, -1 entries)
+    scored by their owner shards and combined by a max: bit-identical to
+    gem_score_ids on the whole store."""
+    from paper_2603_20336_b300 import shard
+    w, B = data["w"], 24
+    rng = np.random.default_rng(31)
+    lens = rng.integers(0, 400, size=B)
+    lens[5] = 0
+    co = torch.from_numpy(np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)).cuda()
+    ci = torch.from_numpy(rng.integers(-1, w.docs.n_sets, size=int(lens.sum())).astype(np.int64)).cuda()
+    n = ci.numel()
+    ws_kw = dict(max_queries=B, max_q_rows=B * 32, max_q_len=32, max_cands=n, max_k=16)
+    ws = gem.Workspace(data["full"], **ws_kw)
+    want = gem.score_ids(data["full"], ws, data["q"], data["qo"], co, ci, compute)
+    assert ws.status() == 0
+    ws.close()
+    off = w.docs.offsets
+    bounds = shard.shard_ranges(off, n_shards)
+    shards = []
+    for s in range(n_shards):
+        a, b = int(bounds[s]), int(bounds[s + 1])
+        st = gem.Store(w.docs.vecs[int(off[a]):int(off[b])], off[a:b + 1] - off[a], keep=("f32",))
+        gem.set_codebook(st, data["C"])
+        shards.append(shard.Shard(st, gem.Workspace(st, **ws_kw), a, b - a))
+    try:
+        got = shard.sharded_score_ids(shard.GemEngine("cuda"), shards, n_shards, data["q"], data["qo"], co, ci,
+                                      compute)
+        for sh in shards:
+            assert sh.ws.status() == 0
+        assert torch.equal(got.view(torch.int32), want.view(torch.int32))
+    finally:
+        for sh in shards:
+            sh.ws.close()
+            sh.store.close()

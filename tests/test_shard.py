@@ -106,6 +106,14 @@ class OracleEngine:
         sc = oracle.score_ids(q.numpy(), qo.numpy(), Xs, os_, co, ids).reshape(B, depth)
         pool_scores[torch.from_numpy(own)] = torch.from_numpy(sc[own])
 
+    def score_owned(self, sh, q, qo, cand_off, cand_ids, compute, scores):
+        Xs, os_ = self._rows(sh)
+        ids = cand_ids.numpy()
+        local = ids - sh.id_base
+        own = (ids >= 0) & (local >= 0) & (local < sh.n_sets)
+        sc = oracle.score_ids(q.numpy(), qo.numpy(), Xs, os_, cand_off.numpy(), np.where(own, local, -1))
+        scores[torch.from_numpy(own)] = torch.from_numpy(sc[own])
+
     def topk(self, shard, scores, ids, k):
         rows = scores.shape[0]
         oi, os_ = self.ids((rows, k)).fill_(-1), self.scores((rows, k), -np.inf)
@@ -120,6 +128,16 @@ class OracleEngine:
 def _data():
     w = synth.exact_fp32(n_sets=90, n_queries=4)
     return w.docs.vecs.numpy(), w.docs.offsets, w.queries.vecs, torch.from_numpy(w.queries.offsets)
+
+
+def _lists():
+    """Candidate lists of global ids over the 90-set store: 4 queries, uneven
+    lengths, an empty list, -1 entries."""
+    rng = np.random.default_rng(17)
+    lens = np.array([7, 0, 19, 12])
+    co = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    ci = rng.integers(-1, 90, size=int(co[-1])).astype(np.int64)
+    return co, ci
 
 
 def _free_port():
@@ -168,7 +186,10 @@ def _worker(rank, world, port, out):
             got = [None] * world
             dist.all_gather_object(got, local.numpy())
             layout_ok &= all(np.array_equal(full[s].numpy(), got[s]) for s in range(world))
-        out.put((rank, bounds, ids.numpy(), sc.numpy(), layout_ok))
+        co, ci = _lists()
+        routed = shard.sharded_score_ids(OracleEngine(X, off), [mine], world, q, qo, torch.from_numpy(co),
+                                         torch.from_numpy(ci), "f32", comm=comm)
+        out.put((rank, bounds, ids.numpy(), sc.numpy(), layout_ok, routed.numpy()))
         dist.barrier()
     finally:
         dist.destroy_process_group()
@@ -183,6 +204,7 @@ def test_sharded_protocol_on_gloo_ranks_equals_single_store_search(world):
     for p in procs:
         p.start()
     res = sorted([out.get(timeout=300) for _ in procs], key=lambda x: x[0])
+    co, ci = _lists()
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
@@ -190,11 +212,28 @@ def test_sharded_protocol_on_gloo_ranks_equals_single_store_search(world):
     S = oracle.score_all(q.numpy(), qo.numpy(), X, off)
     pool = np.stack([oracle.topk(S[b], R)[0] for b in range(S.shape[0])])
     want_ids, want_sc = oracle.rerank(q.numpy(), qo.numpy(), X, off, pool, K)
-    for rank, bounds, ids, sc, layout_ok in res:
+    want_routed = oracle.score_ids(q.numpy(), qo.numpy(), X, off, co, ci)
+    for rank, bounds, ids, sc, layout_ok, routed in res:
         assert layout_ok
         assert np.array_equal(bounds, res[0][1])
         np.testing.assert_array_equal(ids, want_ids)      # every rank returns the answer
         np.testing.assert_array_equal(sc, want_sc)
+        np.testing.assert_array_equal(routed, want_routed)  # candidate lists routed to their owners
+
+
+def test_routed_candidate_lists_in_one_process():
+    """Candidate lists of global ids routed to their owner shards: each shard
+    scores what it owns and the max over shards equals the single-store scores."""
+    from paper_2603_20336_b300 import shard
+    X, off, q, qo = _data()
+    co, ci = _lists()
+    want = oracle.score_ids(q.numpy(), qo.numpy(), X, off, co, ci)
+    for n in (1, 2, 3):
+        bounds = shard.shard_ranges(off, n)
+        shards = [shard.Shard(None, None, int(bounds[s]), int(bounds[s + 1] - bounds[s])) for s in range(n)]
+        got = shard.sharded_score_ids(OracleEngine(X, off), shards, n, q, qo, torch.from_numpy(co),
+                                      torch.from_numpy(ci), "f32")
+        np.testing.assert_array_equal(got.numpy(), want)
 
 
 def test_sharded_protocol_in_one_process_equals_single_store_search():
