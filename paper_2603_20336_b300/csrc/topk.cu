@@ -305,12 +305,13 @@ topk_sample_kernel(const float* __restrict__ scores, int rows, int64_t cols, con
 
 // Threshold path, step 2: one streaming pass; every valid key >= thr[row] is
 // appended to the row's candidate buffer (cap entries; the counter keeps
-// counting past it).  Work items are (row, 4,096-element chunk).  The test is a
+// counting past it).  Work items are (row, 8,192-element chunk); four CTAs per
+// SM (at most 64 registers) keep 128 KB of loads in flight per SM.  The test is a
 // float comparison with the threshold's score (keys order like their scores,
 // and -0 equals +0 in both); only an element whose score equals it compares
 // ids.  Each thread counts its picks, the warp scans the counts and takes one
 // slot range with a single atomic.
-__global__ void __launch_bounds__(kFilterThreads)
+__global__ void __launch_bounds__(kFilterThreads, 4)
 topk_filter_kernel(const float* __restrict__ scores, int rows, int64_t cols, const int64_t* __restrict__ ids,
                    const uint32_t* __restrict__ dead, int64_t n_sets, const unsigned long long* __restrict__ thr,
                    unsigned* __restrict__ cnt, unsigned long long* __restrict__ cand, int cap, bool vec4) {
