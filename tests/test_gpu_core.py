@@ -370,3 +370,35 @@ def test_invalid_arguments_are_rejected_before_launch(gem, cfg1):
     gem.score_all(cfg1["store"], cfg1["ws"], cfg1["q"], bad, "bf16", out=out)
     assert cfg1["ws"].status() == 1
     assert torch.all(out == 7.0)             # nothing was scored
+
+
+def test_longest_query_sets_every_path(gem, cfg1):
+    """Query sets of 200..256 vectors (up to 8 passes of the tensor-core plan,
+    8 row groups of the streamed scorer) next to sets of 1 and 32 vectors: BF16
+    all-sets within 2e-4 m_q of the FP64 score of the rounded inputs, FP32
+    all-sets and id lists within 1e-5 of the L1 of the terms, the id-list scores
+    bit-identical to the all-sets FP32 form."""
+    w = cfg1["w"]
+    lens = np.array([256, 1, 200, 32, 255, 129])
+    qs = synth.vector_sets(lens, synth.centres(64, 1235), 6060)
+    q, qo = qs.vecs.cuda(), torch.from_numpy(qs.offsets).cuda()
+    B = len(lens)
+    rng = np.random.default_rng(61)
+    cl = rng.integers(50, 300, size=B)
+    co = np.concatenate([[0], np.cumsum(cl)]).astype(np.int64)
+    ids = rng.integers(0, w.docs.n_sets, size=int(co[-1])).astype(np.int64)
+    ws = gem.Workspace(cfg1["store"], max_queries=B, max_q_rows=int(lens.sum()), max_q_len=256,
+                       max_cands=int(co[-1]), max_k=16)
+    Sb = gem.score_all(cfg1["store"], ws, q, qo, "bf16").cpu().numpy()
+    Sf = gem.score_all(cfg1["store"], ws, q, qo, "f32").cpu().numpy()
+    Si = gem.score_ids(cfg1["store"], ws, q, qo, torch.from_numpy(co).cuda(), torch.from_numpy(ids).cuda(),
+                       "f32").cpu().numpy()
+    assert ws.status() == 0
+    ws.close()
+    Sq = oracle.score_all(oracle.bf16_round(qs.vecs.numpy()), qs.offsets,
+                          oracle.bf16_round(w.docs.vecs.numpy()), w.docs.offsets)
+    assert np.all(np.abs(Sb - Sq) <= 2e-4 * lens[:, None]), np.abs(Sb - Sq).max()
+    S64, L1 = oracle.score_all(qs.vecs, qs.offsets, w.docs.vecs, w.docs.offsets, with_l1=True)
+    assert np.all(np.abs(Sf - S64) <= 1e-5 * L1)
+    b_of = np.repeat(np.arange(B), cl)
+    np.testing.assert_array_equal(Si.view(np.uint32), Sf[b_of, ids].view(np.uint32))
