@@ -111,8 +111,9 @@ def test_assign_codes_centroid_maps_to_itself_and_ties_go_low(gem):
 
 
 def test_train_codebook_fixed_point_invariants(gem):
-    """k-means is a heuristic (parity unpinned); its fixed point is checked:
-    unit centroids, each the normalised mean of the vectors coded to it."""
+    """After many Lloyd steps the trained codebook is a fixed point of the
+    update: unit centroids, each the normalised mean of the vectors coded to it.
+    (A single step against the oracle's update is in test_gpu_cluster.py.)"""
     w = synth.exact_fp32(n_sets=120, n_queries=1)
     store = gem.Store(w.docs.vecs.cuda(), w.docs.offsets, keep=("f32",))
     C = gem.train_codebook(store, k1=32, iters=40, sample=0, seed=7)

@@ -480,7 +480,7 @@ def test_contrastive_dscores_rows_sum_to_zero():
     assert np.all(g[:, 0] <= 0) and np.all(g[:, 1:] >= 0)
 
 
-# --------------------------------------------------------------------------- k-means (unpinned)
+# --------------------------------------------------------------------------- k-means (Sec. 4.1.1)
 
 def test_kmeans_update_fixed_point_invariants():
     rng = np.random.default_rng(16)
