@@ -76,10 +76,6 @@ __device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
   return make_float2(__uint_as_float((uint32_t)d), __uint_as_float((uint32_t)(d >> 32)));
 }
 
-__device__ __forceinline__ bool elect_one_lane() {
-  return (threadIdx.x & 31) == 0;
-}
-
 // ------------------------------------------------------------------ mbarrier
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -383,10 +379,6 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[N]) {
 #pragma unroll
     for (int c = 0; c < N / 32; ++c) tmem_ld32(taddr + 32 * c, *reinterpret_cast<float(*)[32]>(&v[32 * c]));
   }
-}
-
-__device__ __forceinline__ void tmem_ld_wait() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 }  // namespace gem
