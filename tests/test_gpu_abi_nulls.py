@@ -1,7 +1,8 @@
 """Every entry point of the C ABI called with NULL handles and pointers (and
 every size 1, which no call can honour with NULL data) returns an error status
-(or, for the destroy calls, nothing) without touching memory.  The sweep runs in a child process that names each call
-before making it, so a crash points at the call."""
+(or, for the destroy calls, nothing) without touching memory.  The sweep runs
+in a child process that names each call before making it, so a crash points at
+the call."""
 import os
 import subprocess
 import sys
