@@ -29,6 +29,12 @@
  *    calling thread.
  *  - A store is immutable after creation and may be shared by concurrent calls;
  *    a workspace must be used by one stream at a time.
+ *  - Test hook, off unless set: the environment variable GEM_FAULT_INJECT=alloc:N
+ *    makes the N-th device allocation of gem_store_create / gem_workspace_create
+ *    fail with GEM_ERR_OOM (counted from the first allocation after the variable
+ *    took its value); the call unwinds what it had built.
+ *  - Each entry point marks its host time with an NVTX range of its own name
+ *    (gem_search also its four stages), which profilers can filter on.
  */
 #ifndef GEM_H_
 #define GEM_H_

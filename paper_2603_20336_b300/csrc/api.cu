@@ -5,7 +5,9 @@
 #include <cstdio>
 #include <numeric>
 #include <random>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "internal.h"
@@ -28,10 +30,30 @@ gem_status check_current_device(int want) {
   return GEM_OK;
 }
 
+// Host-side fault injection for tests, off unless GEM_FAULT_INJECT is set:
+// "alloc:N" makes the N-th device allocation of the store and workspace
+// creation calls fail as if the device were out of memory, counting from the
+// first allocation after the variable took its current value.
+bool injected_alloc_failure() {
+  static std::mutex mu;
+  static std::string last;
+  static long count = 0;
+  const char* env = std::getenv("GEM_FAULT_INJECT");
+  const std::string cur = env ? env : "";
+  std::lock_guard<std::mutex> lk(mu);
+  if (cur != last) {
+    last = cur;
+    count = 0;
+  }
+  if (cur.rfind("alloc:", 0) != 0) return false;
+  return ++count == std::strtol(cur.c_str() + 6, nullptr, 10);
+}
+
 template <typename T>
 gem_status dmalloc(T** p, size_t count, const char* what) {
   *p = nullptr;
   if (count == 0) return GEM_OK;
+  if (injected_alloc_failure()) return fail(GEM_ERR_OOM, std::string("injected allocation failure for ") + what);
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -114,6 +136,7 @@ void gem_store_destroy(gem_store* s) {
 
 gem_status gem_store_create(const float* vecs, const int64_t* offsets, int64_t n_sets, int32_t dim,
                             uint32_t keep_mask, int inputs_on_host, void* stream, gem_store** out) {
+  GEM_NVTX_RANGE("gem_store_create");
   if (!out) return fail(GEM_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (!vecs || !offsets) return fail(GEM_ERR_INVALID, "vecs/offsets is NULL");
@@ -290,6 +313,7 @@ void gem_workspace_destroy(gem_workspace* w) {
 gem_status gem_workspace_create(const gem_store* s, int32_t max_queries, int64_t max_q_rows,
                                 int32_t max_q_len, int64_t max_cands, int32_t max_k,
                                 gem_workspace** out) {
+  GEM_NVTX_RANGE("gem_workspace_create");
   if (!out) return fail(GEM_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (!s) return fail(GEM_ERR_INVALID, "store is NULL");
@@ -387,6 +411,7 @@ gem_status gem_workspace_create(const gem_store* s, int32_t max_queries, int64_t
 
 gem_status gem_assign_codes(const float* x, int64_t n, const float* centroids, int32_t k1,
                             int32_t* codes, float* best, void* stream) {
+  GEM_NVTX_RANGE("gem_assign_codes");
   if (!x || !centroids || !codes) return fail(GEM_ERR_INVALID, "NULL argument");
   if (n < 0 || k1 < 1) return fail(GEM_ERR_INVALID, "bad sizes");
   return launch_assign(x, n, centroids, k1, codes, best, reinterpret_cast<cudaStream_t>(stream));
@@ -394,6 +419,7 @@ gem_status gem_assign_codes(const float* x, int64_t n, const float* centroids, i
 
 gem_status gem_train_codebook(const gem_store* s, int32_t k1, int32_t iters, int64_t sample,
                               uint64_t seed, float* centroids_out, void* stream) {
+  GEM_NVTX_RANGE("gem_train_codebook");
   if (!s || !centroids_out) return fail(GEM_ERR_INVALID, "NULL argument");
   if (!s->d_f32) return fail(GEM_ERR_STATE, "training reads the fp32 copy");
   if (iters < 0) return fail(GEM_ERR_INVALID, "iters < 0");
@@ -462,6 +488,7 @@ static int current_sm_count() {
 
 gem_status gem_kmeans(const float* x, int64_t n, int32_t k, int32_t iters, uint64_t seed, float* centroids_out,
                       void* stream) {
+  GEM_NVTX_RANGE("gem_kmeans");
   if (!x || !centroids_out) return fail(GEM_ERR_INVALID, "NULL argument");
   if (k < 1 || k > n) return fail(GEM_ERR_INVALID, "k must be 1..n");
   if (iters < 0) return fail(GEM_ERR_INVALID, "iters < 0");
@@ -503,6 +530,7 @@ gem_status gem_kmeans(const float* x, int64_t n, int32_t k, int32_t iters, uint6
 gem_status gem_cluster_filter(const float* q, const int64_t* q_offsets, int32_t n_queries, int32_t max_q_len,
                               const float* centroids, int32_t k2, int32_t t, uint32_t* out_mask, int32_t* out_list,
                               int32_t* out_count, void* stream) {
+  GEM_NVTX_RANGE("gem_cluster_filter");
   if (!q || !q_offsets || !centroids || !out_mask || !out_list || !out_count)
     return fail(GEM_ERR_INVALID, "NULL argument");
   if (n_queries < 0 || max_q_len < 1) return fail(GEM_ERR_INVALID, "bad sizes");
@@ -547,6 +575,7 @@ gem_status gem_store_mark_deleted(gem_store* s, const int64_t* ids, int64_t n, i
 
 gem_status gem_entry_points(const gem_store* s, const int32_t* cluster_lists, const int32_t* cluster_counts,
                             int32_t n_queries, int32_t stride, uint64_t seed, int64_t* out_sets, void* stream) {
+  GEM_NVTX_RANGE("gem_entry_points");
   if (!s || !cluster_lists || !cluster_counts || !out_sets) return fail(GEM_ERR_INVALID, "NULL argument");
   if (n_queries < 0 || stride < 1) return fail(GEM_ERR_INVALID, "bad sizes");
   if (s->k2 <= 0) return fail(GEM_ERR_STATE, "store has no C_index (gem_store_set_index_centroids)");
@@ -648,6 +677,7 @@ static gem_status score_all_impl(const gem_store* s, gem_workspace* w, const flo
 gem_status gem_score_all(const gem_store* s, gem_workspace* w, const float* q,
                          const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
                          int32_t compute, float* scores, void* stream) {
+  GEM_NVTX_RANGE("gem_score_all");
   gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
   if (r != GEM_OK) return r;
   if (!scores) return fail(GEM_ERR_INVALID, "scores is NULL");
@@ -659,6 +689,7 @@ gem_status gem_score_ids(const gem_store* s, gem_workspace* w, const float* q,
                          const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
                          const int64_t* cand_offsets, const int64_t* cand_ids, int64_t n_cands,
                          int32_t compute, float* scores, void* stream) {
+  GEM_NVTX_RANGE("gem_score_ids");
   gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
   if (r != GEM_OK) return r;
   if (!cand_offsets || (n_cands > 0 && (!cand_ids || !scores)))
@@ -692,6 +723,7 @@ gem_status gem_beam_search(const gem_store* s, gem_workspace* w, const float* q,
                            int32_t max_degree, const uint32_t* cluster_mask, const int64_t* entries,
                            int32_t entry_stride, int32_t ef, int32_t max_rounds, int64_t* out_ids, float* out_scores,
                            int32_t* out_rounds, void* stream) {
+  GEM_NVTX_RANGE("gem_beam_search");
   gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
   if (r != GEM_OK) return r;
   if (!graph_off || !graph_nbrs || !cluster_mask || !entries || !out_ids || !out_scores)
@@ -717,6 +749,7 @@ gem_status gem_estimate_codes(const gem_store* s, gem_workspace* w, const float*
                               const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
                               const int64_t* cand_offsets, const int64_t* cand_ids, int64_t n_cands,
                               float* est, void* stream) {
+  GEM_NVTX_RANGE("gem_estimate_codes");
   gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
   if (r != GEM_OK) return r;
   if (!est) return fail(GEM_ERR_INVALID, "est is NULL");
@@ -732,6 +765,7 @@ gem_status gem_estimate_codes(const gem_store* s, gem_workspace* w, const float*
 gem_status gem_topk(gem_workspace* w, const float* scores, const int64_t* row_offsets, int32_t rows,
                     int64_t cols, const int64_t* ids, int32_t k, int64_t* out_ids, float* out_scores,
                     void* stream) {
+  GEM_NVTX_RANGE("gem_topk");
   if (!w) return fail(GEM_ERR_INVALID, "workspace is NULL");
   if (!scores || !out_ids) return fail(GEM_ERR_INVALID, "scores or out_ids is NULL");
   if (rows < 0 || (!row_offsets && cols < 0)) return fail(GEM_ERR_INVALID, "bad shape");
@@ -769,17 +803,28 @@ static gem_status search_impl(const gem_store* s, gem_workspace* w, const float*
   if (rerank_depth > 0 && (int64_t)rerank_depth * n_queries > w->max_cands)
     return fail(GEM_ERR_INVALID, "n_queries * rerank_depth exceeds max_cands");
   if (rerank_depth > 0 && !s->d_f32) return fail(GEM_ERR_STATE, "the rerank needs the fp32 copy");
-  gem_status r = search_first_pass(s, w, q, q_offsets, n_queries, n_q_rows, compute, st);
+  gem_status r;
+  {
+    GEM_NVTX_RANGE("search: first pass");
+    r = search_first_pass(s, w, q, q_offsets, n_queries, n_q_rows, compute, st);
+  }
   if (r != GEM_OK) return r;
   if (rerank_depth == 0)
     return launch_topk(w, w->d_scores, nullptr, n_queries, s->n_sets, nullptr, k, out_ids, out_scores, st);
-  r = launch_topk(w, w->d_scores, nullptr, n_queries, s->n_sets, nullptr, rerank_depth, w->d_pool_ids,
-                  nullptr, st);
+  {
+    GEM_NVTX_RANGE("search: top-R");
+    r = launch_topk(w, w->d_scores, nullptr, n_queries, s->n_sets, nullptr, rerank_depth, w->d_pool_ids,
+                    nullptr, st);
+  }
   if (r != GEM_OK) return r;
   launch_iota_offsets(w->d_pool_off, n_queries, rerank_depth, st);
   GEM_CUDA_TRY(cudaGetLastError());
-  r = launch_f32_score_pool(s, w, q, q_offsets, n_queries, rerank_depth, w->d_pool_ids, w->d_pool_scores, st);
+  {
+    GEM_NVTX_RANGE("search: FP32 rerank");
+    r = launch_f32_score_pool(s, w, q, q_offsets, n_queries, rerank_depth, w->d_pool_ids, w->d_pool_scores, st);
+  }
   if (r != GEM_OK) return r;
+  GEM_NVTX_RANGE("search: top-k");
   return launch_topk(w, w->d_pool_scores, nullptr, n_queries, rerank_depth, w->d_pool_ids, k, out_ids,
                      out_scores, st);
 }
@@ -788,6 +833,7 @@ gem_status gem_search(const gem_store* s, gem_workspace* w, const float* q,
                       const int64_t* q_offsets, int32_t n_queries, int64_t n_q_rows,
                       int32_t compute, int32_t rerank_depth, int32_t k, int64_t* out_ids,
                       float* out_scores, void* stream) {
+  GEM_NVTX_RANGE("gem_search");
   gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
   if (r != GEM_OK) return r;
   if (!out_ids) return fail(GEM_ERR_INVALID, "out_ids is NULL");
@@ -800,6 +846,7 @@ gem_status gem_search_host(const gem_store* s, gem_workspace* w, const float* q_
                            const int64_t* q_offsets_host, int32_t n_queries, int32_t compute,
                            int32_t rerank_depth, int32_t k, int64_t* out_ids_host,
                            float* out_scores_host, void* stream) {
+  GEM_NVTX_RANGE("gem_search_host");
   if (!s || !w || !q_host || !q_offsets_host || !out_ids_host)
     return fail(GEM_ERR_INVALID, "NULL argument");
   if (!w->d_scores) return fail(GEM_ERR_STATE, "workspace was created with max_k = 0");
@@ -833,6 +880,7 @@ gem_status gem_maxsim_fwd(const float* q, const int64_t* q_offsets, int32_t n_qu
                           const float* docs, const int64_t* doc_offsets, int64_t n_docs, int64_t n_doc_rows,
                           const int64_t* pair_offsets, const int64_t* pair_ids, int64_t n_pairs, int32_t max_q_len,
                           int32_t compute, float* scores, int32_t* argmax, gem_workspace* ws, void* stream) {
+  GEM_NVTX_RANGE("gem_maxsim_fwd");
   if (!q || !q_offsets || !docs || !doc_offsets || !pair_offsets || !scores || !argmax || (n_pairs > 0 && !pair_ids))
     return fail(GEM_ERR_INVALID, "NULL argument");
   if (n_queries < 1 || n_docs < 1 || n_pairs < 0 || n_q_rows < n_queries || n_doc_rows < n_docs)
@@ -854,6 +902,7 @@ gem_status gem_maxsim_bwd(const float* q, const int64_t* q_offsets, int32_t n_qu
                           const int64_t* pair_offsets, const int64_t* pair_ids, int64_t n_pairs,
                           const int32_t* argmax, int32_t max_q_len, const float* grad_scores, float* grad_q,
                           float* grad_docs, void* stream) {
+  GEM_NVTX_RANGE("gem_maxsim_bwd");
   if (!q || !q_offsets || !docs || !doc_offsets || !pair_offsets || !argmax || !grad_scores ||
       (n_pairs > 0 && !pair_ids))
     return fail(GEM_ERR_INVALID, "NULL argument");
@@ -868,6 +917,7 @@ gem_status gem_batch_create(const gem_store* s, int32_t mode, int32_t max_querie
                             int32_t max_q_len, int64_t max_cands, int32_t seg, int32_t ctas_per_sm,
                             float* q, int64_t* q_offsets, int64_t* cand_offsets, int64_t* cand_ids,
                             float* scores, gem_batch** out) {
+  GEM_NVTX_RANGE("gem_batch_create");
   if (!out) return fail(GEM_ERR_INVALID, "out is NULL");
   if (!q || !q_offsets || !cand_offsets || (max_cands > 0 && (!cand_ids || !scores)))
     return fail(GEM_ERR_INVALID, "batch buffer is NULL");
@@ -887,6 +937,7 @@ gem_status gem_batch_create(const gem_store* s, int32_t mode, int32_t max_querie
 
 gem_status gem_batch_run(gem_batch* b, int32_t n_queries, int64_t n_q_rows, int64_t n_cands,
                          int32_t use_graph, void* stream) {
+  GEM_NVTX_RANGE("gem_batch_run");
   if (!b) return fail(GEM_ERR_INVALID, "batch is NULL");
   if (n_queries < 1 || n_queries > b->max_queries) return fail(GEM_ERR_INVALID, "n_queries out of range");
   if (n_q_rows < n_queries || n_q_rows > b->max_q_rows) return fail(GEM_ERR_INVALID, "n_q_rows out of range");
@@ -913,6 +964,7 @@ gem_status gem_autotune_score_all(const gem_store* s, gem_workspace* w, const fl
                                   int32_t compute, float* scores, const char* cache_path, int32_t* m_tiles,
                                   int32_t* variant, int32_t* chunk_rows, float* ms, int32_t* from_cache,
                                   void* stream) {
+  GEM_NVTX_RANGE("gem_autotune_score_all");
   gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
   if (r != GEM_OK) return r;
   if (!scores || !m_tiles || !variant || !chunk_rows || !ms || !from_cache)
@@ -933,6 +985,7 @@ gem_status gem_autotune_batch(const gem_store* s, int32_t mode, int32_t n_querie
                               int32_t max_q_len, int64_t n_cands, float* q, int64_t* q_offsets,
                               int64_t* cand_offsets, int64_t* cand_ids, float* scores, const char* cache_path,
                               int32_t* seg, int32_t* ctas_per_sm, float* ms, int32_t* from_cache, void* stream) {
+  GEM_NVTX_RANGE("gem_autotune_batch");
   if (!s || !q || !q_offsets || !cand_offsets || !cand_ids || !scores || !seg || !ctas_per_sm || !ms || !from_cache)
     return fail(GEM_ERR_INVALID, "NULL argument");
   if (mode != GEM_F32 && mode != GEM_CODES) return fail(GEM_ERR_INVALID, "mode must be GEM_F32 or GEM_CODES");
@@ -952,6 +1005,7 @@ gem_status gem_score_ids_noalloc(const gem_store* s, const float* q, const int64
                                  int32_t n_queries, int64_t n_q_rows, int32_t max_q_len,
                                  const int64_t* cand_offsets, const int64_t* cand_ids, int64_t n_cands,
                                  float* scores, void* stream) {
+  GEM_NVTX_RANGE("gem_score_ids_noalloc");
   if (!s || !q || !q_offsets || !cand_offsets || (n_cands > 0 && (!cand_ids || !scores)))
     return fail(GEM_ERR_INVALID, "NULL argument");
   if (!s->d_f32) return fail(GEM_ERR_STATE, "id-list scoring reads the fp32 copy");
@@ -968,6 +1022,7 @@ int64_t gem_kernel_launches(void) { return g_launches.load(std::memory_order_rel
 
 gem_status gem_qemd(const gem_store* s, gem_workspace* w, const int64_t* set_a, const int64_t* set_b, int64_t n_pairs,
                     float* out, void* stream) {
+  GEM_NVTX_RANGE("gem_qemd");
   if (!s || !w) return fail(GEM_ERR_INVALID, "NULL argument");
   if (n_pairs < 0) return fail(GEM_ERR_INVALID, "n_pairs < 0");
   if (n_pairs > 0 && (!set_a || !set_b || !out)) return fail(GEM_ERR_INVALID, "NULL argument");

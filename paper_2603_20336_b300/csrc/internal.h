@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <map>
@@ -197,6 +198,16 @@ namespace gem {
 void set_error(const std::string& msg);
 gem_status fail(gem_status code, const std::string& msg);
 gem_status cuda_fail(cudaError_t e, const char* what);
+// A named range on the host timeline for profilers (NVTX; a no-op when no tool
+// is attached), from construction to the end of the scope.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define GEM_NVTX_RANGE(name) ::gem::NvtxRange gem_nvtx_range_(name)
+
 #define GEM_CUDA_TRY(expr)                                  \
   do {                                                      \
     cudaError_t e__ = (expr);                               \

@@ -92,6 +92,7 @@ bool all_finite(const std::vector<float>& h) {
 using namespace gem;
 
 extern "C" gem_status gem_store_save(const gem_store* s, const char* path, void* stream) {
+  GEM_NVTX_RANGE("gem_store_save");
   if (!s || !path) return fail(GEM_ERR_INVALID, "NULL argument");
   if (!s->d_f32) return fail(GEM_ERR_STATE, "saving needs the FP32 copy (GEM_KEEP_F32)");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -129,6 +130,7 @@ extern "C" gem_status gem_store_save(const gem_store* s, const char* path, void*
 }
 
 extern "C" gem_status gem_store_load(const char* path, uint32_t keep_mask, void* stream, gem_store** out) {
+  GEM_NVTX_RANGE("gem_store_load");
   if (!path || !out) return fail(GEM_ERR_INVALID, "NULL argument");
   *out = nullptr;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -57,6 +57,7 @@ using namespace gem;
 extern "C" {
 
 gem_status gem_shard_ranges(const int64_t* offsets_host, int64_t n_sets, int32_t n_shards, int64_t* bounds_host) {
+  GEM_NVTX_RANGE("gem_shard_ranges");
   if (!offsets_host || !bounds_host) return fail(GEM_ERR_INVALID, "NULL argument");
   if (n_sets < 1 || n_shards < 1 || n_shards > n_sets) return fail(GEM_ERR_INVALID, "need 1 <= n_shards <= n_sets");
   if (offsets_host[0] != 0) return fail(GEM_ERR_INVALID, "offsets[0] != 0");
@@ -80,6 +81,7 @@ gem_status gem_shard_ranges(const int64_t* offsets_host, int64_t n_sets, int32_t
 gem_status gem_shard_first_pass(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
                                 int32_t n_queries, int64_t n_q_rows, int32_t compute, int32_t depth, int64_t id_base,
                                 int64_t* out_ids, float* out_scores, void* stream) {
+  GEM_NVTX_RANGE("gem_shard_first_pass");
   gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
   if (r != GEM_OK) return r;
   if (!out_ids || !out_scores) return fail(GEM_ERR_INVALID, "NULL output");
@@ -103,6 +105,7 @@ gem_status gem_shard_first_pass(const gem_store* s, gem_workspace* w, const floa
 gem_status gem_shard_rerank(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
                             int32_t n_queries, int64_t n_q_rows, const int64_t* pool_ids, int32_t depth,
                             int64_t id_base, float* pool_scores, void* stream) {
+  GEM_NVTX_RANGE("gem_shard_rerank");
   gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
   if (r != GEM_OK) return r;
   if (!pool_ids || !pool_scores) return fail(GEM_ERR_INVALID, "NULL argument");
@@ -128,6 +131,7 @@ gem_status gem_shard_score_ids(const gem_store* s, gem_workspace* w, const float
                                int32_t n_queries, int64_t n_q_rows, const int64_t* cand_offsets,
                                const int64_t* cand_ids, int64_t n_cands, int32_t compute, int64_t id_base,
                                float* scores, void* stream) {
+  GEM_NVTX_RANGE("gem_shard_score_ids");
   gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
   if (r != GEM_OK) return r;
   if (!cand_offsets || (n_cands > 0 && (!cand_ids || !scores))) return fail(GEM_ERR_INVALID, "NULL argument");
@@ -150,6 +154,7 @@ gem_status gem_shard_score_ids(const gem_store* s, gem_workspace* w, const float
 
 gem_status gem_merge_topk(const float* scores, const int64_t* ids, int32_t n_lists, int32_t rows, int32_t k_in,
                           int32_t k, int64_t* out_ids, float* out_scores, void* stream) {
+  GEM_NVTX_RANGE("gem_merge_topk");
   if (!scores || !ids || !out_ids) return fail(GEM_ERR_INVALID, "NULL argument");
   if (n_lists < 1 || rows < 0 || k_in < 1) return fail(GEM_ERR_INVALID, "bad shape");
   if (k < 1 || k > kMaxK) return fail(GEM_ERR_INVALID, "k must be 1..4096");
