@@ -170,8 +170,8 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 2) batch_score_kernel(BatchA
 __global__ void __launch_bounds__(kBatchWarps * 32, 2) batch_stream_kernel(BatchArgs a) {
   extern __shared__ float sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* ring = sm + warp * kRing * kVecBlock * kStageStride;
-  float* rowmax = sm + kBatchWarps * kRing * kVecBlock * kStageStride + warp * kStreamRowmax;
+  float* ring = sm + warp * kRing * ring_block(true);
+  float* rowmax = sm + kBatchWarps * kRing * ring_block(true) + warp * kStreamRowmax;
   const int B = (int)a.hdr[0];
   const long long total = a.hdr[3];
   const StreamArgs sa{a.q, a.q_off, B, a.co, a.ids, a.docs, a.doc_off, a.n_sets, a.scores, a.status, a.max_q_len};
@@ -193,12 +193,12 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 2) batch_stream_kernel(Batch
     }
     const int64_t t0 = a.co[b] + (item - a.item_off[b]) * a.seg;
     const int64_t t1 = min(a.co[b + 1], t0 + a.seg);
-    stream_pairs<false>(sa, t0, t1, ring, rowmax);
+    stream_pairs<false, true>(sa, t0, t1, ring, rowmax);
   }
 }
 
 size_t batch_smem(int max_q_len, bool stream) {
-  if (stream) return sizeof(float) * ((size_t)kBatchWarps * kRing * kVecBlock * kStageStride + kBatchWarps * kStreamRowmax);
+  if (stream) return sizeof(float) * ((size_t)kBatchWarps * kRing * ring_block(true) + kBatchWarps * kStreamRowmax);
   return sizeof(float) * ((size_t)max_q_len * kQStride + kBatchWarps * kVecBlock * kStageStride +
                           (size_t)kBatchWarps * max_q_len);
 }

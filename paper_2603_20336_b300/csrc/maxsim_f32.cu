@@ -136,8 +136,8 @@ __global__ void __launch_bounds__(kF32Threads, 2)
 f32_ids_stream_kernel(StreamArgs a, int64_t n_cands) {
   extern __shared__ float sm[];
   const int warp = threadIdx.x >> 5;
-  float* ring = sm + warp * kRing * kVecBlock * kStageStride;
-  float* rowmax = sm + kF32Warps * kRing * kVecBlock * kStageStride + warp * kStreamRowmax;
+  float* ring = sm + warp * kRing * ring_block(false);
+  float* rowmax = sm + kF32Warps * kRing * ring_block(false) + warp * kStreamRowmax;
   const int64_t n_warps = (int64_t)gridDim.x * kF32Warps;
   const int64_t gw = (int64_t)blockIdx.x * kF32Warps + warp;
   if (a.perm) {
@@ -248,7 +248,7 @@ gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* 
     if (!qcodes && !a.stored_codes) {
       const StreamArgs sa{q, q_offsets, n_queries, cand_offsets, cand_ids, s->d_f32, s->d_offsets, s->n_sets,
                           scores, ws->d_status, mq};
-      const size_t smem = sizeof(float) * (kF32Warps * kRing * kVecBlock * kStageStride + kF32Warps * kStreamRowmax);
+      const size_t smem = sizeof(float) * (kF32Warps * kRing * ring_block(false) + kF32Warps * kStreamRowmax);
       auto kern = l2 ? f32_ids_stream_kernel<true> : f32_ids_stream_kernel<false>;
       GEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kF32Threads, smem));
@@ -301,7 +301,7 @@ gem_status launch_f32_score_pool(const gem_store* s, gem_workspace* ws, const fl
                 scores, ws->d_status, mq};
   sa.perm = ws->d_pool_perm;
   sa.per_query = per_query;
-  const size_t smem = sizeof(float) * (kF32Warps * kRing * kVecBlock * kStageStride + kF32Warps * kStreamRowmax);
+  const size_t smem = sizeof(float) * (kF32Warps * kRing * ring_block(false) + kF32Warps * kStreamRowmax);
   auto kern = l2 ? f32_ids_stream_kernel<true> : f32_ids_stream_kernel<false>;
   GEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;

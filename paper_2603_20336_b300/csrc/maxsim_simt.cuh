@@ -220,6 +220,10 @@ struct StreamArgs {
 };
 
 constexpr int kRing = 4;  // 8-vector stages in a warp's ring
+// floats per ring stage: 8 staged vectors and 8 of padding, so that two stages
+// read at once (the two half-warps of a short row group) fall in different banks
+constexpr int kRingBlock = kVecBlock * kStageStride + 8;
+__host__ __device__ constexpr int ring_block(bool dual) { return dual ? kRingBlock : kVecBlock * kStageStride; }
 constexpr int kStreamRowmax = 1024;  // row maxima a warp keeps (chunk pairs x max_q_len)
 
 // Pairs per chunk for queries of at most max_q_len rows.
@@ -238,10 +242,14 @@ __host__ __device__ constexpr int stream_chunk(int max_q_len) {
 // ahead and across pair, group and chunk boundaries, so the gathers of the next
 // sets overlap the arithmetic of the current one (a chunk's later groups re-read
 // its sets from L2).  Scores: -inf for a negative id, NaN and a status for an id
-// >= n_sets or a query longer than max_q_len.
-template <bool L2>
+// >= n_sets or a query longer than max_q_len.  DUAL: a row group of at most 16
+// rows is taken by both half-warps on alternate 8-vector blocks (the same
+// per-dot arithmetic; the maxima of the halves meet at the end, so the scores
+// are unchanged); the rerank's instantiation keeps the plain loop.
+template <bool L2, bool DUAL = false>
 __device__ __forceinline__ void stream_pairs(const StreamArgs& a, int64_t t_begin, int64_t t_end, float* ring,
                                              float* rowmax) {
+  constexpr int RB = ring_block(DUAL);  // floats per ring stage
   if (t_begin >= t_end) return;
   const int lane = threadIdx.x & 31;
   const int half = lane & 1;
@@ -338,7 +346,7 @@ __device__ __forceinline__ void stream_pairs(const StreamArgs& a, int64_t t_begi
       r0_cur = __shfl_sync(0xffffffffu, p_r0, ip);
     }
     if (pc.c0 < t_end) {
-      float* dst = ring + (issued % kRing) * (kVecBlock * kStageStride);
+      float* dst = ring + (issued % kRing) * RB;
       const float* srcp = a.docs + (r0_cur + (int64_t)bp * kVecBlock) * kDim + 4 * lane;
       const int nv = min(kVecBlock, mp_cur - bp * kVecBlock);
 #pragma unroll
@@ -364,7 +372,12 @@ __device__ __forceinline__ void stream_pairs(const StreamArgs& a, int64_t t_begi
     const int64_t my_id = lane < n ? a.cand_ids[my_pair] : -1;
     const int my_mp = (my_id >= 0 && my_id < a.n_sets) ? (int)(a.doc_off[my_id + 1] - a.doc_off[my_id]) : 0;
     for (int rg = 0; rg < cc.nrg; ++rg) {
-      const int ia = rg * 32 + 2 * pair, ib = ia + 1;
+      // a group of at most 16 rows: both half-warps hold its rows (lanes 16-31
+      // as lanes 0-15) and take alternate 8-vector blocks of each set, so no
+      // lane idles on empty rows; the two halves' row maxima meet at the end
+      const bool dual = DUAL && m_q - rg * 32 <= 16;  // uniform over the warp
+      const int ia = rg * 32 + 2 * (dual ? (pair & 7) : pair), ib = ia + 1;
+      const int second = (dual && lane >= 16) ? 1 : 0;  // this lane takes the odd blocks
       if (cc.nrg > 1 || cc.b != loaded_b) {
         // rows ia and ib, components 64 half .. 64 half + 63, as packed pairs
         const float4* ra = reinterpret_cast<const float4*>(a.q + (q0 + ia) * kDim + half * (kDim / 2));
@@ -385,18 +398,42 @@ __device__ __forceinline__ void stream_pairs(const StreamArgs& a, int64_t t_begi
         if (m_p == 0) continue;
         float best_a = -INFINITY, best_b = -INFINITY;
         const int nb = (m_p + kVecBlock - 1) / kVecBlock;
-        for (int blk = 0; blk < nb; ++blk) {
-          issue();
-          cp_async_wait<kRing - 1>();
-          __syncwarp();
-          const float* stage = ring + (consumed % kRing) * (kVecBlock * kStageStride);
-          block_terms<L2>(stage, rd_off, qr, min(kVecBlock, m_p - blk * kVecBlock), best_a, best_b);
-          __syncwarp();
-          ++consumed;
+        if constexpr (!DUAL) {
+          for (int blk = 0; blk < nb; ++blk) {
+            issue();
+            cp_async_wait<kRing - 1>();
+            __syncwarp();
+            const float* stage = ring + (consumed % kRing) * RB;
+            block_terms<L2>(stage, rd_off, qr, min(kVecBlock, m_p - blk * kVecBlock), best_a, best_b);
+            __syncwarp();
+            ++consumed;
+          }
+        } else {
+          // a dual group takes blocks blk (lanes 0-15) and blk + 1 (lanes 16-31)
+          // at once: one block is issued before the two are read (into the stage
+          // the last step freed) and, when there is a second, one after they are
+          // consumed, so no stage is refilled while it is read
+          for (int blk = 0; blk < nb; blk += dual ? 2 : 1) {
+            const bool two = dual && blk + 1 < nb;
+            issue();
+            if (two) cp_async_wait<kRing - 2>(); else cp_async_wait<kRing - 1>();
+            __syncwarp();
+            const int mine = blk + second;
+            const float* stage = ring + ((consumed + second) % kRing) * RB;
+            block_terms<L2>(stage, rd_off, qr, mine < nb ? min(kVecBlock, m_p - mine * kVecBlock) : 0, best_a,
+                            best_b);
+            __syncwarp();
+            consumed += two ? 2 : 1;
+            if (two) issue();
+          }
+          if (dual) {
+            best_a = fmaxf(best_a, __shfl_xor_sync(0xffffffffu, best_a, 16));
+            best_b = fmaxf(best_b, __shfl_xor_sync(0xffffffffu, best_b, 16));
+          }
         }
         float* rm = rowmax + i * a.max_q_len;
-        if (half == 0 && ia < m_q) rm[ia] = row_term<L2>(best_a);
-        if (half == 1 && ib < m_q) rm[ib] = row_term<L2>(best_b);
+        if (!second && half == 0 && ia < m_q) rm[ia] = row_term<L2>(best_a);
+        if (!second && half == 1 && ib < m_q) rm[ib] = row_term<L2>(best_b);
       }
     }
     __syncwarp();
