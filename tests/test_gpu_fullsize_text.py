@@ -107,3 +107,37 @@ def test_text500k_search_against_stored_exact_top100(gem, text):
         for s, f in zip(ids[b].tolist(), sc[b].tolist()):
             Q, P = _rows(w, b, s)
             assert abs(f - oracle.chamfer(Q, P)) <= 1e-5 * _l1(Q, P), (b, s)
+
+
+def test_beam_batch_4096_queries_on_the_full_store(gem, text):
+    """Config 4 at full size: 4,096 queries of 8..64 vectors, candidate lists of
+    64..512 ids (30% from a 10,000-id pool) over the 500,000-set store, two
+    graph-replayed rounds (the second with its ids mapped by the round shift):
+    every score bit-identical to the non-batched id-list path over the same
+    lists, and sampled pairs within 1e-5·L1 of FP64."""
+    w, store = text[0], text[1]
+    dev = torch.device("cuda", 0)
+    nq = 4096
+    qs = synth.vector_sets(synth.lengths_uniform(nq, 8, 64, 1238 + 7919), synth.centres(4096, 1236),
+                           1238 + 7919, dev)
+    co, ci0 = synth.candidate_lists(nq, store.n_sets, 64, 512, 0.3, 10_000, 1238)
+    qv, qoff, co_d = qs.vecs, torch.from_numpy(qs.offsets).to(dev), torch.from_numpy(co).to(dev)
+    bt = gem.Batch(store, "f32", max_queries=nq, max_q_rows=qv.shape[0], max_q_len=64, max_cands=len(ci0), seg=16)
+    ws64 = gem.Workspace(store, max_queries=nq, max_q_rows=qv.shape[0], max_q_len=64)
+    for rnd in range(2):
+        ci = torch.from_numpy(synth.shift_lists(ci0, rnd, store.n_sets)).to(dev)
+        got = bt.run(qv, qoff, co_d, ci).clone()
+        assert bt.status() == 0
+        ref = gem.score_ids(store, ws64, qv, qoff, co_d, ci, "f32")
+        assert ws64.status() == 0
+        assert torch.equal(got.view(torch.int32), ref.view(torch.int32)), rnd
+    cih = ci.cpu().numpy()
+    off = w.docs.offsets
+    for t in np.random.default_rng(8).choice(len(cih), size=48, replace=False):
+        b = int(np.searchsorted(co, t, side="right") - 1)
+        Q = qv[int(qs.offsets[b]): int(qs.offsets[b + 1])].cpu().numpy().astype(np.float64)
+        s = int(cih[t])
+        P = w.docs.vecs[int(off[s]): int(off[s + 1])].cpu().numpy().astype(np.float64)
+        assert abs(got[t].item() - oracle.chamfer(Q, P)) <= 1e-5 * _l1(Q, P), (b, s)
+    ws64.close()
+    bt.close()
