@@ -110,13 +110,20 @@ class ClockSampler:
 
 
 def _dist():
+    """One process per GPU (torchrun); NCCL for the barrier and the max over ranks.
+    GEM_BENCH_BACKEND=gloo keeps those host-side (ranks sharing a GPU can then run
+    the whole path: their kernels never wait on one another)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
         import torch.distributed as dist
         rank = int(os.environ["RANK"])
-        local = int(os.environ.get("LOCAL_RANK", rank))
+        local = int(os.environ.get("LOCAL_RANK", rank)) % max(1, torch.cuda.device_count())
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        backend = os.environ.get("GEM_BENCH_BACKEND", "nccl")
+        if backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
         return dist, rank, ws, local
     return None, 0, 1, 0
 
