@@ -37,13 +37,15 @@ import synth  # noqa: E402
 # capture of one launch on the medium text case (1,000 queries x 50,000 sets,
 # 1.090 GB algorithmic); the reported traffic is this ratio times the run's own
 # algorithmic bytes (the store is read once per launch and the scores written
-# once, so traffic grows in proportion: the same ratios were seen on full-size
-# launches).  An entry is removed when the kernel changes, until it is captured
-# again; a schedule without an entry reports null.
+# once, so traffic grows in proportion).  An entry is removed when the kernel
+# changes, until it is captured again; a schedule without an entry reports null.
 TC_TRAFFIC_RATIO = {
     (2, "plain", 65536): 1.19538e9 / 1.08980e9,     # 1.0009 GB read + 0.1945 GB written
     (2, "two_sets", 16384): 1.14127e9 / 1.08980e9,  # 0.9468 GB read + 0.1945 GB written
     (2, "plain", 16384): 1.14045e9 / 1.08980e9,     # 0.9464 GB read + 0.1940 GB written
+    (2, "plain", 32768): 1.16730e9 / 1.08980e9,     # 0.9729 GB read + 0.1944 GB written
+    (2, "two_sets", 32768): 1.16270e9 / 1.08980e9,  # 0.9683 GB read + 0.1944 GB written
+    (2, "two_sets", 65536): 1.19810e9 / 1.08980e9,  # 1.0028 GB read + 0.1953 GB written
 }
 
 # the headline metric: (query set, stored set) pairs scored per second by the

@@ -590,7 +590,7 @@ void gem_batch_destroy(gem_batch* batch);
  * gem_autotune_score_all: schedules of gem_score_all for compute GEM_BF16 or
  * GEM_FP8_E4M3 ((m_tiles, variant) in {(2, TWO_SETS), (2, PLAIN), (4, PLAIN),
  * (2, A_TMEM), (1, PLAIN)} x
- * chunk_rows in {2^14, 2^15, 2^16, 2^17, 2^18}); the choice is applied to `ws` (as
+ * chunk_rows in {2^14, 2^15, 2^16}); the choice is applied to `ws` (as
  * gem_workspace_set_schedule).  scores float32 [n_queries * n_sets] is scratch
  * for the timing runs.
  */
