@@ -103,3 +103,41 @@ def test_batched_rejects_inconsistent_offsets(gem, beam):
     s = bt.run(q, qo, co, ids)
     assert bt.status() == 7 and torch.isnan(s[3]).item()
     bt.close()
+
+
+def test_batched_short_groups_bit_match_on_boundary_lengths(gem):
+    """The batch scorer splits a row group of at most 16 query rows over both
+    half-warps (alternate 8-vector blocks).  Query lengths on every side of the
+    16 / 32 / 48 boundaries and sets of 1..20 vectors (one block, an odd or an
+    even number of blocks) score bit-identically to the id-list path, which
+    keeps whole 32-row groups, and within 1e-5·L1 of FP64."""
+    seed = 77
+    cents = synth.centres(64, seed)
+    lens = np.random.default_rng(seed).integers(1, 21, size=400)
+    docs = synth.vector_sets(lens.astype(np.int64), cents, seed)
+    store = gem.Store(docs.vecs.cuda(), docs.offsets, keep=("f32",))
+    qlens = np.array([1, 2, 8, 15, 16, 17, 31, 32, 33, 40, 47, 48, 49, 63, 64], dtype=np.int64)
+    qs = synth.vector_sets(qlens, cents, seed + 1)
+    rng = np.random.default_rng(seed + 2)
+    counts = rng.integers(1, 40, size=len(qlens))
+    co = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    ci = rng.integers(0, 400, size=int(co[-1])).astype(np.int64)
+    bt = gem.Batch(store, "f32", max_queries=len(qlens), max_q_rows=int(qlens.sum()), max_q_len=64,
+                   max_cands=len(ci), seg=8)
+    args = (qs.vecs.cuda(), torch.from_numpy(qs.offsets).cuda(), torch.from_numpy(co).cuda(),
+            torch.from_numpy(ci).cuda())
+    got = bt.run(*args).clone()
+    assert bt.status() == 0
+    ws = gem.Workspace(store, max_queries=len(qlens), max_q_rows=int(qlens.sum()), max_q_len=64)
+    ref = gem.score_ids(store, ws, *args, "f32")
+    assert torch.equal(got.view(torch.int32), ref.view(torch.int32))
+    want = oracle.score_ids(qs.vecs, qs.offsets, docs.vecs, docs.offsets, co, ci)
+    Q = qs.vecs.numpy().astype(np.float64)
+    for t in range(len(ci)):
+        b = int(np.searchsorted(co, t, side="right") - 1)
+        P = docs.vecs[docs.offsets[ci[t]]:docs.offsets[ci[t] + 1]].numpy().astype(np.float64)
+        l1 = np.abs((Q[qs.offsets[b]:qs.offsets[b + 1]] @ P.T).max(axis=1)).sum()
+        assert abs(got[t].item() - want[t]) <= 1e-5 * l1
+    ws.close()
+    bt.close()
+    store.close()
