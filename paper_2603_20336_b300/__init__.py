@@ -189,7 +189,9 @@ def _queries(q, q_offsets):
 
 
 def score_all(store: Store, ws: Workspace, q, q_offsets, compute="bf16", out=None, stream=None):
-    """Exact CH (Eq. 1) of every query set against every stored set: float32 [B, n_sets]."""
+    """Exact CH (Eq. 1) of every query set against every stored set: float32 [B, n_sets].
+    compute: "bf16", "fp8" (per-vector scales), "fp8_set" (one power-of-two scale per
+    set) on the tensor cores, from the store copy of that name; or "f32" (SIMT)."""
     q, qo, B, rows = _queries(q, q_offsets)
     if out is None:
         out = torch.empty((B, store.n_sets), dtype=torch.float32, device=q.device)
@@ -200,7 +202,9 @@ def score_all(store: Store, ws: Workspace, q, q_offsets, compute="bf16", out=Non
 
 def score_ids(store: Store, ws: Workspace, q, q_offsets, cand_offsets, cand_ids, compute="f32",
               out=None, stream=None):
-    """Exact CH over per-query candidate id lists (Algorithm 5 candidate scoring)."""
+    """Exact CH over per-query candidate id lists (Algorithm 5 candidate scoring),
+    aligned with cand_ids.  compute: "f32" (the FP32 chain, Kahan sum over query
+    vectors) or "codes" (the qCH estimate in similarity form)."""
     q, qo, B, rows = _queries(q, q_offsets)
     co = _dev(cand_offsets, torch.int64, "cand_offsets")
     ci = _dev(cand_ids, torch.int64, "cand_ids")
@@ -231,7 +235,10 @@ def topk(ws: Workspace, scores, k: int, ids=None, row_offsets=None, stream=None)
 
 def search(store: Store, ws: Workspace, q, q_offsets, compute="bf16", rerank_depth=1000, k=100,
            stream=None):
-    """Exhaustive search (Eq. 2) with an exact FP32 rerank of the top rerank_depth."""
+    """Exhaustive search (Eq. 2): a first pass in `compute` ("bf16", "fp8", "fp8_set",
+    "f32" or "codes"), its top rerank_depth per query rescored exactly in FP32, then
+    the top k: (ids int64 [B, k], scores float32 [B, k]).  rerank_depth 0 returns
+    the first pass's own top k."""
     q, qo, B, rows = _queries(q, q_offsets)
     out_i = torch.empty((B, k), dtype=torch.int64, device=q.device)
     out_s = torch.empty((B, k), dtype=torch.float32, device=q.device)
