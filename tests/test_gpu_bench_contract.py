@@ -33,7 +33,7 @@ def test_main_arm_small_workload_contract_line():
     assert abs(rf["frac"] - rf["achieved"] / rf["peak"]) <= 1e-9
     assert abs(rf["achieved"] - 2.0 * B * 32 * d["config"]["n_vecs"] * 128 / (st["maxsim_bf16_ms"] * 1e-3) / 1e12) \
         <= 1e-6 * rf["achieved"]
-    assert d["gpu_launches"] >= 5
+    assert d["gpu_launches_per_step"] >= 5 and d["gpu_launches"] == 2 * d["gpu_launches_per_step"]
     assert "sm_mhz" in d["clocks"] and "reasons" in d["clocks"]
     e2e = d["e2e"]
     assert e2e["value"] > 0 and e2e["unit"] == d["unit"]
