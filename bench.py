@@ -499,10 +499,34 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, recall, stages, dev, step_ms, o
             ok &= bool(torch.equal(one, got[lo:hi]))
         assert bt.status() == 0
         bt.close()
-        return {"queries": nq, "pairs_per_round": int(len(ci0)), "rounds": rounds, "ms_per_round": ms,
-                "pairs_per_s": len(ci0) / (ms * 1e-3), "schedule": ch, "bit_match_per_query_path": ok,
-                "tflops": fl / (ms * 1e-3) / 1e12,
-                "frac_of_builder_fp32_peak": fl / (ms * 1e-3) / 1e12 / bp["fp32_tflops"] if bp else None}
+        res = {"queries": nq, "pairs_per_round": int(len(ci0)), "rounds": rounds, "ms_per_round": ms,
+               "pairs_per_s": len(ci0) / (ms * 1e-3), "schedule": ch, "bit_match_per_query_path": ok,
+               "tflops": fl / (ms * 1e-3) / 1e12,
+               "frac_of_builder_fp32_peak": fl / (ms * 1e-3) / 1e12 / bp["fp32_tflops"] if bp else None}
+        # the codes form of the same rounds (the qCH estimate per pair), when the
+        # store has a codebook (the qch stage trains one)
+        try:
+            btc = gem.Batch(store, "codes", max_queries=nq, max_q_rows=qv.shape[0], max_q_len=64,
+                            max_cands=len(ci0))
+        except gem.GemError as e:
+            res["codes"] = {"skipped": str(e)[:120]}
+            return res
+        btc.run(qv, qoff, co_d, lists[0])
+        e0.record()
+        for r in range(rounds):
+            btc.run(qv, qoff, co_d, lists[r])
+        e1.record()
+        e1.synchronize()
+        msc = e0.elapsed_time(e1) / rounds
+        gotc = btc.scores[: len(ci0)].clone()
+        wsc = gem.Workspace(store, max_queries=nq, max_q_rows=qv.shape[0], max_q_len=64)
+        refc = gem.score_ids(store, wsc, qv, qoff, co_d, lists[-1], "codes")
+        assert btc.status() == 0 and wsc.status() == 0
+        res["codes"] = {"ms_per_round": msc, "pairs_per_s": len(ci0) / (msc * 1e-3),
+                        "bit_match_id_list_path": bool(torch.equal(gotc, refc))}
+        wsc.close()
+        btc.close()
+        return res
 
     def backward():
         wb = synth.contrastive_batch(device=dev)
@@ -619,6 +643,30 @@ def extra_stages(gem, store, ws, w, q, qo, R, K, recall, stages, dev, step_ms, o
                      "vectors_per_s": B * store.n_vecs / (step_ms * 1e-3)})
         return {"queries": B, "runs": runs}
 
+    def exact_2k():
+        # config 1, the parity-sized case (launch-bound, reported, not a bench
+        # line): 2,000 sets of 16..64 vectors, 10 queries of 32, top-10 (its
+        # parity against the oracle is in the tests; here the BF16 top-10 is
+        # compared with the FP32 path's)
+        w1 = synth.exact_fp32(device=dev)
+        s1 = gem.Store(w1.docs.vecs, w1.docs.offsets, keep=("f32", "bf16"))
+        ws1 = gem.Workspace(s1, max_queries=10, max_q_rows=320, max_q_len=32)
+        q1, qo1 = w1.queries.vecs, torch.from_numpy(w1.queries.offsets).to(dev)
+        res = {"n_sets": s1.n_sets, "queries": 10}
+        top = {}
+        for dt in ("f32", "bf16"):
+            def run():
+                return gem.topk(ws1, gem.score_all(s1, ws1, q1, qo1, dt), 10)
+            ms1 = _time(run, reps=20)
+            top[dt] = run()[0].cpu().numpy()
+            res[dt] = {"ms": ms1, "pairs_per_s": 10 * s1.n_sets / (ms1 * 1e-3)}
+        res["bf16_top10_overlap_with_f32"] = float(np.mean(
+            [len(set(top["bf16"][b].tolist()) & set(top["f32"][b].tolist())) / 10.0 for b in range(10)]))
+        ws1.close()
+        s1.close()
+        return res
+
+    guard("exact_fp32_2k", exact_2k)
     guard("fp8_exhaustive", fp8)
     guard("fp32_exhaustive", fp32)
     guard("pages_50k", pages)

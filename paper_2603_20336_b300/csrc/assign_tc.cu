@@ -65,7 +65,8 @@ constexpr float kAtBand =
 struct AtArgs {
   const float* X;          // FP32 rows of this launch [n_rows x 128]
   const float* C;          // FP32 centroids [k1 x 128]
-  int64_t n_rows;
+  int64_t n_rows;          // rows of this launch (an upper bound when n_dev is set)
+  const int64_t* n_dev;    // rows of the whole call, read on the device, or null
   int k1;
   const float* cmax;       // largest centroid norm (device scalar)
   int32_t* codes;          // [n_rows] of this launch
@@ -105,7 +106,9 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap tm_xh, const __grid_constan
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const long long n_units = (a.n_rows + kAtRows - 1) / kAtRows;
+  const int64_t n_rows =
+      a.n_dev ? max((int64_t)0, min(a.n_rows, (int64_t)__ldg(a.n_dev) - a.row_base)) : a.n_rows;
+  const long long n_units = (n_rows + kAtRows - 1) / kAtRows;
   const int n_tiles = (a.k1 + kAtN - 1) / kAtN;
   if (blockIdx.x >= n_units) return;  // uniform for the CTA
 
@@ -271,7 +274,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap tm_xh, const __grid_constan
     };
     for (long long u = take_unit(); u < n_units && ok; u = take_unit()) {
       const int64_t row = u * kAtRows + local_row;
-      const bool live = row < a.n_rows;
+      const bool live = row < n_rows;
       // the row's norm (its band) from the FP32 row; the same FMA chain as the recheck
       float ss = 0.f;
       if (live) {
@@ -331,8 +334,10 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap tm_xh, const __grid_constan
           for (int w = 8; w >= 1; w >>= 1)
 #pragma unroll
             for (int j = 0; j < w; ++j) cm[j] = fmaxf(cm[j], cm[j + w]);
-          if (cm[0] >= thr) {
-            // rare: the chunk holds a new maximum or a value within band of it
+          // rare: the chunk holds a new maximum or a value within band of it.  A
+          // row past the end (zero-filled: every column would tie) and a row
+          // whose list has overflowed (it goes to the SIMT assignment) track nothing.
+          if (live && !overflow && cm[0] >= thr) {
             uint32_t hits = 0;
             float tmp[32];
 #pragma unroll
@@ -456,94 +461,128 @@ __global__ void split_bf16_kernel(const float* __restrict__ X, int64_t n, __nv_b
 
 }  // namespace
 
-gem_status launch_assign_tc(const float* X, int64_t n, const float* C, int k1, int32_t* codes, float* best,
-                            int n_sm, cudaStream_t st) {
-  if (n == 0) return GEM_OK;
-  if (n >= ((int64_t)1 << 31)) return fail(GEM_ERR_INVALID, "too many rows");
-  const int64_t chunk = std::min<int64_t>(n, (int64_t)1 << 22);
-  // one stream-ordered scratch block: C hi/lo, X hi/lo of a chunk, the
-  // fallback list, the counters and the centroid-norm maximum
-  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t c_op = up((size_t)k1 * kDim * 2), x_op = up((size_t)chunk * kDim * 2), fb = up((size_t)n * 4);
-  const size_t total = 2 * c_op + 2 * x_op + fb + 256;
-  uint8_t* base = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), total, st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(GEM_ERR_OOM, "scratch of the tensor-core assignment");
-  }
-  auto* c_hi = reinterpret_cast<__nv_bfloat16*>(base);
-  auto* c_lo = reinterpret_cast<__nv_bfloat16*>(base + c_op);
-  auto* x_hi = reinterpret_cast<__nv_bfloat16*>(base + 2 * c_op);
-  auto* x_lo = reinterpret_cast<__nv_bfloat16*>(base + 2 * c_op + x_op);
-  auto* fb_rows = reinterpret_cast<int32_t*>(base + 2 * c_op + 2 * x_op);
+namespace {
+
+struct AtScratch {
+  __nv_bfloat16 *c_hi, *c_lo, *x_hi, *x_lo;
+  int32_t* fb_rows;
+  unsigned long long* fb_count;
+  float* cmax;
+  int* unit_counter;
+  int* status;
+};
+
+size_t at_up(size_t b) { return (b + 255) / 256 * 256; }
+int64_t at_chunk(int64_t max_n) { return std::min<int64_t>(max_n, (int64_t)1 << 22); }
+
+// One block: C hi/lo, X hi/lo of a chunk, the fallback list, the counters and
+// the centroid-norm maximum.
+AtScratch at_carve(void* scratch, int64_t max_n, int k1) {
+  uint8_t* base = static_cast<uint8_t*>(scratch);
+  const size_t c_op = at_up((size_t)k1 * kDim * 2), x_op = at_up((size_t)at_chunk(max_n) * kDim * 2),
+               fb = at_up((size_t)max_n * 4);
+  AtScratch sc;
+  sc.c_hi = reinterpret_cast<__nv_bfloat16*>(base);
+  sc.c_lo = reinterpret_cast<__nv_bfloat16*>(base + c_op);
+  sc.x_hi = reinterpret_cast<__nv_bfloat16*>(base + 2 * c_op);
+  sc.x_lo = reinterpret_cast<__nv_bfloat16*>(base + 2 * c_op + x_op);
+  sc.fb_rows = reinterpret_cast<int32_t*>(base + 2 * c_op + 2 * x_op);
   uint8_t* small = base + 2 * c_op + 2 * x_op + fb;
-  auto* fb_count = reinterpret_cast<unsigned long long*>(small);
-  auto* cmax = reinterpret_cast<float*>(small + 8);
-  auto* unit_counter = reinterpret_cast<int*>(small + 12);
-  auto* status = reinterpret_cast<int*>(small + 16);
-  gem_status r = GEM_OK;
-  auto done = [&](gem_status rr) {
-    cudaFreeAsync(base, st);
-    return rr;
-  };
-  CUtensorMap tm_ch, tm_cl, tm_xh, tm_xl;
-  if (!encode_tmap_2d(&tm_ch, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, c_hi, kDim, (uint64_t)k1, kDim * 2, 64, kAtN,
-                      CU_TENSOR_MAP_SWIZZLE_128B) ||
-      !encode_tmap_2d(&tm_cl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, c_lo, kDim, (uint64_t)k1, kDim * 2, 64, kAtN,
-                      CU_TENSOR_MAP_SWIZZLE_128B) ||
-      !encode_tmap_2d(&tm_xh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, x_hi, kDim, (uint64_t)chunk, kDim * 2, 64, 128,
-                      CU_TENSOR_MAP_SWIZZLE_128B) ||
-      !encode_tmap_2d(&tm_xl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, x_lo, kDim, (uint64_t)chunk, kDim * 2, 64, 128,
-                      CU_TENSOR_MAP_SWIZZLE_128B))
-    return done(fail(GEM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the assignment operands"));
+  sc.fb_count = reinterpret_cast<unsigned long long*>(small);
+  sc.cmax = reinterpret_cast<float*>(small + 8);
+  sc.unit_counter = reinterpret_cast<int*>(small + 12);
+  sc.status = reinterpret_cast<int*>(small + 16);
+  return sc;
+}
+
+}  // namespace
+
+size_t assign_tc_scratch_bytes(int64_t max_n, int k1) {
+  return 2 * at_up((size_t)k1 * kDim * 2) + 2 * at_up((size_t)at_chunk(max_n) * kDim * 2) +
+         at_up((size_t)max_n * 4) + 256;
+}
+
+cudaError_t assign_tc_prepare() {
   static bool attr_set = false;
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(assign_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kAtSmem);
-    if (e != cudaSuccess) return done(cuda_fail(e, "cudaFuncSetAttribute"));
-    attr_set = true;
-  }
-  e = cudaMemsetAsync(small, 0, 256, st);
+  if (attr_set) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(assign_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kAtSmem);
+  if (e == cudaSuccess) attr_set = true;
+  return e;
+}
+
+gem_status enqueue_assign_tc(const float* X, int64_t max_n, const int64_t* n_dev, const float* C, int k1,
+                             int32_t* codes, float* best, void* scratch, int* status, int n_sm, cudaStream_t st) {
+  if (max_n == 0) return GEM_OK;
+  if (max_n >= ((int64_t)1 << 31)) return fail(GEM_ERR_INVALID, "too many rows");
+  const int64_t chunk = at_chunk(max_n);
+  const AtScratch sc = at_carve(scratch, max_n, k1);
+  if (!status) status = sc.status;
+  CUtensorMap tm_ch, tm_cl, tm_xh, tm_xl;
+  if (!encode_tmap_2d(&tm_ch, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, sc.c_hi, kDim, (uint64_t)k1, kDim * 2, 64, kAtN,
+                      CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !encode_tmap_2d(&tm_cl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, sc.c_lo, kDim, (uint64_t)k1, kDim * 2, 64, kAtN,
+                      CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !encode_tmap_2d(&tm_xh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, sc.x_hi, kDim, (uint64_t)chunk, kDim * 2, 64, 128,
+                      CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !encode_tmap_2d(&tm_xl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, sc.x_lo, kDim, (uint64_t)chunk, kDim * 2, 64, 128,
+                      CU_TENSOR_MAP_SWIZZLE_128B))
+    return fail(GEM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the assignment operands");
+  GEM_CUDA_TRY(assign_tc_prepare());
+  // fallback count, centroid-norm maximum, unit counter and own status start at zero
+  GEM_CUDA_TRY(cudaMemsetAsync(sc.fb_count, 0, 256, st));
   // every code is a valid index even if a bounded wait gives up mid-way
-  if (e == cudaSuccess) e = cudaMemsetAsync(codes, 0, sizeof(int32_t) * n, st);
-  if (e != cudaSuccess) return done(cuda_fail(e, "cudaMemsetAsync"));
+  GEM_CUDA_TRY(cudaMemsetAsync(codes, 0, sizeof(int32_t) * max_n, st));
   const int split_grid = (int)std::min<int64_t>(((int64_t)k1 * 32 + 255) / 256, (int64_t)n_sm * 16);
-  split_bf16_kernel<<<split_grid, 256, 0, st>>>(C, k1, c_hi, c_lo, cmax);
+  split_bf16_kernel<<<split_grid, 256, 0, st>>>(C, k1, sc.c_hi, sc.c_lo, sc.cmax);
   int launches = 1;
-  for (int64_t r0 = 0; r0 < n; r0 += chunk) {
-    const int64_t nr = std::min(chunk, n - r0);
+  for (int64_t r0 = 0; r0 < max_n; r0 += chunk) {
+    const int64_t nr = std::min(chunk, max_n - r0);
     const int g = (int)std::min<int64_t>((nr * 32 + 255) / 256, (int64_t)n_sm * 16);
-    split_bf16_kernel<<<g, 256, 0, st>>>(X + r0 * kDim, nr, x_hi, x_lo, nullptr);
-    e = cudaMemsetAsync(unit_counter, 0, sizeof(int), st);
-    if (e != cudaSuccess) return done(cuda_fail(e, "cudaMemsetAsync"));
+    split_bf16_kernel<<<g, 256, 0, st>>>(X + r0 * kDim, nr, sc.x_hi, sc.x_lo, nullptr);
+    GEM_CUDA_TRY(cudaMemsetAsync(sc.unit_counter, 0, sizeof(int), st));
     AtArgs aa;
     aa.X = X + r0 * kDim;
     aa.C = C;
     aa.n_rows = nr;
+    aa.n_dev = n_dev;
     aa.k1 = k1;
-    aa.cmax = cmax;
+    aa.cmax = sc.cmax;
     aa.codes = codes + r0;
     aa.best = best ? best + r0 : nullptr;
     aa.row_base = r0;
-    aa.fb_rows = fb_rows;
-    aa.fb_count = fb_count;
+    aa.fb_rows = sc.fb_rows;
+    aa.fb_count = sc.fb_count;
     aa.status = status;
-    aa.unit_counter = unit_counter;
+    aa.unit_counter = sc.unit_counter;
     const int64_t units = (nr + kAtRows - 1) / kAtRows;
     assign_tc_kernel<<<(unsigned)std::min<int64_t>(units, n_sm), kAtThreads, kAtSmem, st>>>(tm_xh, tm_xl, tm_ch,
                                                                                            tm_cl, aa);
     launches += 2;
   }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return done(cuda_fail(e, "assign_tc_kernel"));
-  // the rows the candidates could not decide: the SIMT assignment itself
-  r = launch_assign_rows(X, n, reinterpret_cast<const int64_t*>(fb_count), fb_rows, C, k1, codes, best, n_sm, st);
+  GEM_CUDA_TRY(cudaGetLastError());
   note_launches(launches);
-  if (r != GEM_OK) return done(r);
+  // the rows the candidates could not decide: the SIMT assignment itself
+  return launch_assign_rows(X, max_n, reinterpret_cast<const int64_t*>(sc.fb_count), sc.fb_rows, C, k1, codes, best,
+                            n_sm, st);
+}
+
+gem_status launch_assign_tc(const float* X, int64_t n, const float* C, int k1, int32_t* codes, float* best,
+                            int n_sm, cudaStream_t st) {
+  if (n == 0) return GEM_OK;
+  if (n >= ((int64_t)1 << 31)) return fail(GEM_ERR_INVALID, "too many rows");
+  void* base = nullptr;
+  cudaError_t e = cudaMallocAsync(&base, assign_tc_scratch_bytes(n, k1), st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GEM_ERR_OOM, "scratch of the tensor-core assignment");
+  }
+  const gem_status r = enqueue_assign_tc(X, n, nullptr, C, k1, codes, best, base, nullptr, n_sm, st);
   // a bounded wait that gave up is reported here (the call blocks)
   int h_status = 0;
-  e = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st);
-  done(GEM_OK);
+  e = r == GEM_OK ? cudaMemcpyAsync(&h_status, at_carve(base, n, k1).status, sizeof(int), cudaMemcpyDeviceToHost, st)
+                  : cudaSuccess;
+  cudaFreeAsync(base, st);
+  if (r != GEM_OK) return r;
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core assignment");
   if (h_status != 0) return fail((gem_status)h_status, "a wait of the tensor-core assignment gave up");

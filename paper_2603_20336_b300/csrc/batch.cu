@@ -5,11 +5,11 @@
 //
 // Per round the graph runs: header copy (pinned host -> device) -> work plan
 // (segments of SEG candidates per query, prefix-summed) -> [query codes, codes
-// form only] -> counter reset -> persistent scorer.  Exact form: every warp pulls
-// (query, segment) items from an atomic counter and streams the segment's sets
-// (stream_pairs); codes form: the CTAs pull items and each warp scores one
-// candidate with warp_chamfer.  Either way a batched score is bit-identical to
-// the score the same pair gets from gem_score_ids.
+// form only] -> counter reset -> persistent scorer: every warp pulls (query,
+// segment) items from an atomic counter and streams the segment's sets
+// (stream_pairs; the codes form gathers the centroid rows the codes name).
+// Either way a batched score is bit-identical to the score the same pair gets
+// from gem_score_ids.
 #include <cuda_runtime.h>
 
 #include <map>
@@ -102,71 +102,12 @@ struct BatchArgs {
   int* status;
 };
 
-__global__ void __launch_bounds__(kBatchWarps * 32, 2) batch_score_kernel(BatchArgs a) {
-  extern __shared__ float sm[];
-  float* qs = sm;
-  float* stage_all = qs + a.max_q_len * kQStride;
-  float* rowmax_all = stage_all + kBatchWarps * kVecBlock * kStageStride;
-  __shared__ long long s_item;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* stage = stage_all + warp * kVecBlock * kStageStride;
-  float* rowmax = rowmax_all + warp * a.max_q_len;
-  uint64_t qr[kQPairs];
-  const int B = (int)a.hdr[0];
-  const long long total = a.hdr[3];
-  int loaded_b = -1;
-  while (true) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.counter, 1ull);
-    __syncthreads();
-    const long long item = s_item;
-    if (item >= total) break;
-    int lo = 0, hi = B - 1;  // query owning the item
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (a.item_off[mid] <= item) lo = mid; else hi = mid - 1;
-    }
-    const int b = lo;
-    const int64_t q0 = a.q_off[b];
-    const int m_q = (int)(a.q_off[b + 1] - q0);
-    if (m_q < 1 || m_q > a.max_q_len) {
-      if (threadIdx.x == 0) set_status(a.status, kDevInvalid);
-      continue;
-    }
-    if (b != loaded_b) {
-      for (int idx = threadIdx.x; idx < m_q * (kDim / 4); idx += blockDim.x) {
-        const int i = idx / (kDim / 4), k4 = idx % (kDim / 4);
-        const float* src = a.qcodes ? a.centroids + (int64_t)a.qcodes[q0 + i] * kDim : a.q + (q0 + i) * kDim;
-        reinterpret_cast<float4*>(qs + i * kQStride)[k4] = reinterpret_cast<const float4*>(src)[k4];
-      }
-      loaded_b = b;
-      __syncthreads();
-    }
-    int loaded_rg = -1;
-    const int64_t t0 = a.co[b] + (item - a.item_off[b]) * a.seg;
-    const int64_t t1 = min(a.co[b + 1], t0 + a.seg);
-    for (int64_t t = t0 + warp; t < t1; t += kBatchWarps) {
-      const int64_t id = a.ids[t];
-      float score;
-      if (id < 0) {
-        score = -INFINITY;
-      } else if (id >= a.n_sets) {
-        if (lane == 0) set_status(a.status, kDevBounds);
-        score = __int_as_float(0x7fc00000);
-      } else {
-        const int64_t r0 = a.doc_off[id];
-        const int m_p = (int)(a.doc_off[id + 1] - r0);
-        score = warp_chamfer(qs, kQStride, m_q, a.docs + r0 * kDim, a.codes ? a.codes + r0 : nullptr, a.centroids,
-                             m_p, stage, rowmax, qr, loaded_rg);
-      }
-      if (lane == 0) a.scores[t] = score;
-    }
-  }
-}
-
-// Exact form: a warp per item; the pairs of the item's segment stream through
-// the warp's ring (bit-identical to gem_score_ids).  A query longer than
-// max_q_len (or empty) is skipped with a status and its scores stay unwritten.
+// A warp per item; the pairs of the item's segment stream through the warp's
+// ring (bit-identical to gem_score_ids).  CODES: the codes form, whose staged rows
+// are the centroids the store codes name and whose query rows are the centroids
+// of the query codes.  A query longer than max_q_len (or empty) is skipped with a
+// status and its scores stay unwritten.
+template <bool CODES>
 __global__ void __launch_bounds__(kBatchWarps * 32, 2) batch_stream_kernel(BatchArgs a) {
   extern __shared__ float sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -174,7 +115,12 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 2) batch_stream_kernel(Batch
   float* rowmax = sm + kBatchWarps * kRing * ring_block(true) + warp * kStreamRowmax;
   const int B = (int)a.hdr[0];
   const long long total = a.hdr[3];
-  const StreamArgs sa{a.q, a.q_off, B, a.co, a.ids, a.docs, a.doc_off, a.n_sets, a.scores, a.status, a.max_q_len};
+  StreamArgs sa{a.q, a.q_off, B, a.co, a.ids, a.docs, a.doc_off, a.n_sets, a.scores, a.status, a.max_q_len};
+  if constexpr (CODES) {
+    sa.codes = a.codes;
+    sa.centroids = a.centroids;
+    sa.qcodes = a.qcodes;
+  }
   while (true) {
     long long item = 0;
     if (lane == 0) item = (long long)atomicAdd(a.counter, 1ull);
@@ -193,28 +139,23 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 2) batch_stream_kernel(Batch
     }
     const int64_t t0 = a.co[b] + (item - a.item_off[b]) * a.seg;
     const int64_t t1 = min(a.co[b + 1], t0 + a.seg);
-    stream_pairs<false, true>(sa, t0, t1, ring, rowmax);
+    stream_pairs<false, true, CODES>(sa, t0, t1, ring, rowmax);
   }
 }
 
-size_t batch_smem(int max_q_len, bool stream) {
-  if (stream) return sizeof(float) * ((size_t)kBatchWarps * kRing * ring_block(true) + kBatchWarps * kStreamRowmax);
-  return sizeof(float) * ((size_t)max_q_len * kQStride + kBatchWarps * kVecBlock * kStageStride +
-                          (size_t)kBatchWarps * max_q_len);
+size_t batch_smem() {
+  return sizeof(float) * ((size_t)kBatchWarps * kRing * ring_block(true) + kBatchWarps * kStreamRowmax);
 }
 
-// The scorer of a mode, with its shared-memory attribute set once to the
-// largest any caller needs (max_q_len 256), so batches and the no-alloc path
-// never lower it for each other.
+// The scorer of a mode, with its shared-memory attribute set once.
 cudaError_t batch_kernel(int32_t mode, void (**kern)(BatchArgs)) {
   static bool attr_set[2] = {false, false};
-  const bool stream = mode != GEM_CODES;
-  *kern = stream ? batch_stream_kernel : batch_score_kernel;
-  if (!attr_set[stream]) {
-    cudaError_t e = cudaFuncSetAttribute(*kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)batch_smem(32 * kMaxPasses, stream));
+  const int codes = mode == GEM_CODES ? 1 : 0;
+  *kern = codes ? batch_stream_kernel<true> : batch_stream_kernel<false>;
+  if (!attr_set[codes]) {
+    cudaError_t e = cudaFuncSetAttribute(*kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem());
     if (e != cudaSuccess) return e;
-    attr_set[stream] = true;
+    attr_set[codes] = true;
   }
   return cudaSuccess;
 }
@@ -228,8 +169,12 @@ gem_status enqueue_round(gem_batch* bt, cudaStream_t st) {
   GEM_CUDA_TRY(cudaGetLastError());
   int n_launch = 2;
   if (bt->mode == GEM_CODES) {
-    gem_status r = launch_assign_dev_n(bt->d_q, bt->max_q_rows, bt->d_hdr + 1, s->d_codebook, s->k1,
-                                       bt->d_qcodes, st);
+    // the round's query rows (their count on the device) to NN codes
+    gem_status r = bt->d_asg_scratch
+                       ? enqueue_assign_tc(bt->d_q, bt->max_q_rows, bt->d_hdr + 1, s->d_codebook, s->k1,
+                                           bt->d_qcodes, nullptr, bt->d_asg_scratch, bt->d_status, s->n_sm, st)
+                       : launch_assign_dev_n(bt->d_q, bt->max_q_rows, bt->d_hdr + 1, s->d_codebook, s->k1,
+                                             bt->d_qcodes, st);
     if (r != GEM_OK) return r;
   }
   GEM_CUDA_TRY(cudaMemsetAsync(bt->d_counter, 0, sizeof(unsigned long long), st));
@@ -253,7 +198,7 @@ gem_status enqueue_round(gem_batch* bt, cudaStream_t st) {
   a.status = bt->d_status;
   void (*kern)(BatchArgs) = nullptr;
   GEM_CUDA_TRY(batch_kernel(bt->mode, &kern));
-  kern<<<bt->grid, kBatchWarps * 32, batch_smem(bt->max_q_len, bt->mode != GEM_CODES), st>>>(a);
+  kern<<<bt->grid, kBatchWarps * 32, batch_smem(), st>>>(a);
   GEM_CUDA_TRY(cudaGetLastError());
   note_launches(n_launch);
   return GEM_OK;
@@ -291,13 +236,17 @@ gem_status batch_create(const gem_store* s, int32_t mode, int32_t max_queries, i
   BT_ALLOC(d_counter, sizeof(unsigned long long));
   BT_ALLOC(d_status, sizeof(int));
   if (mode == GEM_CODES) BT_ALLOC(d_qcodes, sizeof(int32_t) * max_q_rows);
+  if (mode == GEM_CODES && max_q_rows >= kAssignTcMinRows && s->k1 >= kAssignTcMinCentroids) {
+    BT_ALLOC(d_asg_scratch, assign_tc_scratch_bytes(max_q_rows, s->k1));
+    if ((e = assign_tc_prepare()) != cudaSuccess) return bail(cuda_fail(e, "smem attribute"));
+  }
 #undef BT_ALLOC
   if ((e = cudaMallocHost(reinterpret_cast<void**>(&bt->h_hdr), sizeof(int64_t) * 4)) != cudaSuccess)
     return bail(cuda_fail(e, "cudaMallocHost"));
   if ((e = cudaMemset(bt->d_status, 0, sizeof(int))) != cudaSuccess) return bail(cuda_fail(e, "memset"));
   if ((e = cudaEventCreateWithFlags(&bt->done, cudaEventDisableTiming)) != cudaSuccess)
     return bail(cuda_fail(e, "event"));
-  const size_t smem = batch_smem(max_q_len, mode != GEM_CODES);
+  const size_t smem = batch_smem();
   void (*kern)(BatchArgs) = nullptr;
   if ((e = batch_kernel(mode, &kern)) != cudaSuccess) return bail(cuda_fail(e, "smem attribute"));
   int per_sm = 0;
@@ -317,7 +266,8 @@ gem_status batch_create(const gem_store* s, int32_t mode, int32_t max_queries, i
     const int64_t before = gem_kernel_launches();
     r = enqueue_round(bt, cap);
     // launches inside a capture are counted when the graph is replayed
-    note_launches((int)(before - gem_kernel_launches()));
+    bt->round_launches = (int)(gem_kernel_launches() - before);
+    note_launches(-bt->round_launches);
     cudaError_t e2 = cudaStreamEndCapture(cap, &bt->graph);
     if (r == GEM_OK && e2 != cudaSuccess) e = e2;
   }
@@ -338,7 +288,7 @@ gem_status batch_run(gem_batch* bt, int32_t n_queries, int64_t n_q_rows, int64_t
   bt->h_hdr[2] = n_cands;
   if (use_graph) {
     GEM_CUDA_TRY(cudaGraphLaunch(bt->exec, st));
-    note_launches(bt->mode == GEM_CODES ? 3 : 2);
+    note_launches(bt->round_launches);
   } else {
     gem_status r = enqueue_round(bt, st);
     if (r != GEM_OK) return r;
@@ -354,7 +304,7 @@ void batch_destroy(gem_batch* bt) {
   if (bt->exec) cudaGraphExecDestroy(bt->exec);
   if (bt->graph) cudaGraphDestroy(bt->graph);
   if (bt->done) cudaEventDestroy(bt->done);
-  void* ptrs[] = {bt->d_hdr, bt->d_item_off, bt->d_counter, bt->d_qcodes, bt->d_status};
+  void* ptrs[] = {bt->d_hdr, bt->d_item_off, bt->d_counter, bt->d_qcodes, bt->d_asg_scratch, bt->d_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (bt->h_hdr) cudaFreeHost(bt->h_hdr);
@@ -422,7 +372,7 @@ gem_status score_ids_noalloc(const gem_store* s, const float* q, const int64_t* 
   NoAllocScratch* sc = nullptr;
   gem_status r = noalloc_scratch(s->device, &sc);
   if (r != GEM_OK) return r;
-  const size_t smem = batch_smem(max_q_len, true);
+  const size_t smem = batch_smem();
   void (*kern)(BatchArgs) = nullptr;
   GEM_CUDA_TRY(batch_kernel(GEM_F32, &kern));
   int per_sm = 0;

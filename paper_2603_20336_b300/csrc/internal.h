@@ -185,7 +185,9 @@ struct gem_batch {
   int64_t* d_item_off = nullptr;
   unsigned long long* d_counter = nullptr;
   int32_t* d_qcodes = nullptr;
+  void* d_asg_scratch = nullptr;  // codes form: scratch of the tensor-core query assignment, or null
   int* d_status = nullptr;
+  int round_launches = 0;         // kernels of one captured round
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t done = nullptr;
@@ -347,6 +349,16 @@ gem_status launch_assign(const float* X, int64_t n, const float* C, int k1, int3
                          cudaStream_t st);
 gem_status launch_assign_tc(const float* X, int64_t n, const float* C, int k1, int32_t* codes, float* best,
                             int n_sm, cudaStream_t st);
+// The same tensor-core assignment of the rows 0 .. *n_dev - 1 (at most max_n)
+// as stream work only: scratch of assign_tc_scratch_bytes(max_n, k1) bytes from
+// the caller, no allocation and no host wait, so that it can be captured into a
+// graph.  A bounded wait that gives up writes its code to *status (null: a word
+// of the scratch).  assign_tc_prepare() sets the kernel's shared-memory limit
+// and is called once outside any capture.
+size_t assign_tc_scratch_bytes(int64_t max_n, int k1);
+cudaError_t assign_tc_prepare();
+gem_status enqueue_assign_tc(const float* X, int64_t max_n, const int64_t* n_dev, const float* C, int k1,
+                             int32_t* codes, float* best, void* scratch, int* status, int n_sm, cudaStream_t st);
 // the SIMT assignment of the rows rows[0 .. *n_dev - 1] (at most max_n) of X
 gem_status launch_assign_rows(const float* X, int64_t max_n, const int64_t* n_dev, const int32_t* rows,
                               const float* C, int k1, int32_t* codes, float* best, int n_sm, cudaStream_t st);

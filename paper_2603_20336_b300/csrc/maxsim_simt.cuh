@@ -217,6 +217,12 @@ struct StreamArgs {
   // then a run of positions whose pairs share a query
   const int32_t* perm = nullptr;
   int per_query = 0;
+  // codes form (optional): stored row r is centroids[codes[r]] and, with qcodes,
+  // query row i is centroids[qcodes[i]] (the quantized estimate in similarity
+  // form, the same per-dot arithmetic)
+  const int32_t* codes = nullptr;
+  const float* centroids = nullptr;
+  const int32_t* qcodes = nullptr;
 };
 
 constexpr int kRing = 4;  // 8-vector stages in a warp's ring
@@ -245,8 +251,10 @@ __host__ __device__ constexpr int stream_chunk(int max_q_len) {
 // >= n_sets or a query longer than max_q_len.  DUAL: a row group of at most 16
 // rows is taken by both half-warps on alternate 8-vector blocks (the same
 // per-dot arithmetic; the maxima of the halves meet at the end, so the scores
-// are unchanged); the rerank's instantiation keeps the plain loop.
-template <bool L2, bool DUAL = false>
+// are unchanged); the rerank's instantiation keeps the plain loop.  CODES: the
+// codes form of StreamArgs (stored rows, and with qcodes query rows, replaced by
+// the centroids their codes name).
+template <bool L2, bool DUAL = false, bool CODES = false>
 __device__ __forceinline__ void stream_pairs(const StreamArgs& a, int64_t t_begin, int64_t t_end, float* ring,
                                              float* rowmax) {
   constexpr int RB = ring_block(DUAL);  // floats per ring stage
@@ -327,7 +335,8 @@ __device__ __forceinline__ void stream_pairs(const StreamArgs& a, int64_t t_begi
   int mp_cur = __shfl_sync(0xffffffffu, p_mp, 0);
   int64_t r0_cur = __shfl_sync(0xffffffffu, p_r0, 0);
   uint32_t issued = 0;
-  auto issue = [&]() {
+  // move the cursor to the next block that holds vectors (warp-uniform)
+  auto seek = [&]() {
     while (pc.c0 < t_end && bp * kVecBlock >= mp_cur) {
       bp = 0;
       if (++ip >= (int)(pc.c1 - pc.c0)) {  // a pass over the chunk is done
@@ -345,18 +354,45 @@ __device__ __forceinline__ void stream_pairs(const StreamArgs& a, int64_t t_begi
       mp_cur = __shfl_sync(0xffffffffu, p_mp, ip);
       r0_cur = __shfl_sync(0xffffffffu, p_r0, ip);
     }
+  };
+  // CODES: the codes of a block are loaded one call ahead of its copies, so the
+  // load's latency overlaps a block of arithmetic (lane v < pend_nv: code v)
+  int pend_code = 0, pend_nv = 0;
+  auto load_next = [&]() {
+    seek();
+    pend_nv = 0;
     if (pc.c0 < t_end) {
-      float* dst = ring + (issued % kRing) * RB;
-      const float* srcp = a.docs + (r0_cur + (int64_t)bp * kVecBlock) * kDim + 4 * lane;
-      const int nv = min(kVecBlock, mp_cur - bp * kVecBlock);
-#pragma unroll
-      for (int v = 0; v < kVecBlock; ++v)
-        if (v < nv) cp_async16(dst + v * kStageStride + st_off, srcp + v * kDim);
+      const int64_t row = r0_cur + (int64_t)bp * kVecBlock;
+      pend_nv = min(kVecBlock, mp_cur - bp * kVecBlock);
+      pend_code = lane < pend_nv ? a.codes[row + lane] : 0;
       ++bp;
+    }
+  };
+  auto issue = [&]() {
+    float* dst = ring + (issued % kRing) * RB;
+    if constexpr (CODES) {
+#pragma unroll
+      for (int v = 0; v < kVecBlock; ++v) {
+        const int cv = __shfl_sync(0xffffffffu, pend_code, v);
+        if (v < pend_nv) cp_async16(dst + v * kStageStride + st_off, a.centroids + (int64_t)cv * kDim + 4 * lane);
+      }
+      load_next();
+    } else {
+      seek();
+      if (pc.c0 < t_end) {
+        const int64_t row = r0_cur + (int64_t)bp * kVecBlock;
+        const int nv = min(kVecBlock, mp_cur - bp * kVecBlock);
+        const float* srcp = a.docs + row * kDim + 4 * lane;
+#pragma unroll
+        for (int v = 0; v < kVecBlock; ++v)
+          if (v < nv) cp_async16(dst + v * kStageStride + st_off, srcp + v * kDim);
+        ++bp;
+      }
     }
     cp_async_commit();
     ++issued;
   };
+  if constexpr (CODES) load_next();
 #pragma unroll
   for (int i = 0; i < kRing - 1; ++i) issue();
 
@@ -379,9 +415,16 @@ __device__ __forceinline__ void stream_pairs(const StreamArgs& a, int64_t t_begi
       const int ia = rg * 32 + 2 * (dual ? (pair & 7) : pair), ib = ia + 1;
       const int second = (dual && lane >= 16) ? 1 : 0;  // this lane takes the odd blocks
       if (cc.nrg > 1 || cc.b != loaded_b) {
-        // rows ia and ib, components 64 half .. 64 half + 63, as packed pairs
-        const float4* ra = reinterpret_cast<const float4*>(a.q + (q0 + ia) * kDim + half * (kDim / 2));
-        const float4* rb = reinterpret_cast<const float4*>(a.q + (q0 + ib) * kDim + half * (kDim / 2));
+        // rows ia and ib, components 64 half .. 64 half + 63, as packed pairs (codes
+        // form with query codes: the rows of the centroids they name)
+        const float* qa = a.q + (q0 + ia) * kDim;
+        const float* qbr = a.q + (q0 + ib) * kDim;
+        if (CODES && a.qcodes) {
+          qa = ia < m_q ? a.centroids + (int64_t)a.qcodes[q0 + ia] * kDim : a.centroids;
+          qbr = ib < m_q ? a.centroids + (int64_t)a.qcodes[q0 + ib] * kDim : a.centroids;
+        }
+        const float4* ra = reinterpret_cast<const float4*>(qa + half * (kDim / 2));
+        const float4* rb = reinterpret_cast<const float4*>(qbr + half * (kDim / 2));
 #pragma unroll
         for (int j = 0; j < kRowPairs / 2; ++j) {
           const float4 va = ia < m_q ? ra[j] : make_float4(0.f, 0.f, 0.f, 0.f);
