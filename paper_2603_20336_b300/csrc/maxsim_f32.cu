@@ -72,66 +72,12 @@ f32_all_kernel(F32Args a, int max_q_len) {
 }
 
 // Id lists: every warp takes one contiguous range of the n_cands candidates
-// (equal shares, whatever the list lengths) and reads the rows of the current
-// query straight into registers when the query changes.
-template <bool Coded, bool L2>
-__global__ void __launch_bounds__(kF32Threads, 2)
-f32_ids_kernel(F32Args a, int max_q_len, int64_t n_cands) {
-  extern __shared__ float sm[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* stage = sm + warp * kVecBlock * kStageStride;
-  float* rowmax = sm + kF32Warps * kVecBlock * kStageStride + warp * max_q_len;
-  uint64_t qr[kQPairs];
-  const int64_t n_warps = (int64_t)gridDim.x * kF32Warps;
-  const int64_t chunk = (n_cands + n_warps - 1) / n_warps;
-  const int64_t t_begin = min(n_cands, ((int64_t)blockIdx.x * kF32Warps + warp) * chunk);
-  const int64_t t_end = min(n_cands, t_begin + chunk);
-  if (t_begin >= t_end) return;
-  int lo = 0, hi = a.n_queries - 1;  // query owning t_begin
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (a.cand_off[mid] <= t_begin) lo = mid; else hi = mid - 1;
-  }
-  int b = lo;
-  int64_t b_end = a.cand_off[b + 1];
-  int loaded_rg = -1;
-  for (int64_t t = t_begin; t < t_end; ++t) {
-    while (t >= b_end) {
-      ++b;
-      b_end = a.cand_off[b + 1];
-      loaded_rg = -1;
-    }
-    const int64_t q0 = a.q_off[b];
-    const int m_q = (int)(a.q_off[b + 1] - q0);
-    const int64_t id = a.cand_ids[t];
-    float score;
-    if (id < 0) {
-      score = -INFINITY;
-    } else if (id >= a.n_sets || m_q > max_q_len) {
-      if (lane == 0) set_status(a.status, id >= a.n_sets ? kDevBounds : kDevInvalid);
-      score = __int_as_float(0x7fc00000);
-    } else {
-      const int64_t r0 = a.doc_off[id];
-      const int m_p = (int)(a.doc_off[id + 1] - r0);
-      if constexpr (Coded) {
-        // codes form: query rows are centroids of the query codes
-        score = warp_chamfer_coded_q(a.centroids, a.qcodes + q0, m_q, a.docs + r0 * kDim, a.codes + r0, m_p,
-                                     stage, rowmax, qr, loaded_rg);
-      } else {
-        score = warp_chamfer<L2>(a.q + q0 * kDim, kDim, m_q, a.docs + r0 * kDim,
-                                 a.stored_codes ? a.codes + r0 : nullptr, a.centroids, m_p, stage, rowmax, qr,
-                                 loaded_rg);
-      }
-    }
-    if (lane == 0) a.scores[t] = score;
-  }
-}
-
-// Id lists, exact form: every warp takes one contiguous range of the n_cands
-// candidates (equal shares, whatever the list lengths) and streams it
-// (stream_pairs in maxsim_simt.cuh: bit-identical to warp_chamfer); a pool in
-// segment order is taken in groups of kPoolGroup positions, grid-strided.
-template <bool L2>
+// (equal shares, whatever the list lengths) and streams it (stream_pairs in
+// maxsim_simt.cuh: bit-identical to warp_chamfer); a pool in segment order is
+// taken in groups of kPoolGroup positions, grid-strided.  CODES: the codes
+// forms, whose stored rows are the centroids the store codes name (and whose
+// query rows, given query codes, are centroids too).
+template <bool L2, bool CODES = false>
 __global__ void __launch_bounds__(kF32Threads, 2)
 f32_ids_stream_kernel(StreamArgs a, int64_t n_cands) {
   extern __shared__ float sm[];
@@ -145,13 +91,13 @@ f32_ids_stream_kernel(StreamArgs a, int64_t n_cands) {
     // kPoolGroup at a time, so the sets in use at any moment come from one or
     // two segments of set ids
     for (int64_t p0 = gw * kPoolGroup; p0 < n_cands; p0 += n_warps * kPoolGroup)
-      stream_pairs<L2>(a, p0, min(n_cands, p0 + kPoolGroup), ring, rowmax);
+      stream_pairs<L2, false, CODES>(a, p0, min(n_cands, p0 + kPoolGroup), ring, rowmax);
     return;
   }
   const int64_t chunk = (n_cands + n_warps - 1) / n_warps;
   const int64_t t_begin = min(n_cands, gw * chunk);
   const int64_t t_end = min(n_cands, t_begin + chunk);
-  stream_pairs<L2>(a, t_begin, t_end, ring, rowmax);
+  stream_pairs<L2, false, CODES>(a, t_begin, t_end, ring, rowmax);
 }
 
 // Order of a rerank pool (per_query entries per query) for the exact rescoring:
@@ -245,29 +191,23 @@ gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* 
     const int grid = (int)std::min<int64_t>(units, (int64_t)s->n_sm * per_sm);
     kern<<<grid, kF32Threads, smem, st>>>(a, mq);
   } else {
-    if (!qcodes && !a.stored_codes) {
-      const StreamArgs sa{q, q_offsets, n_queries, cand_offsets, cand_ids, s->d_f32, s->d_offsets, s->n_sets,
-                          scores, ws->d_status, mq};
-      const size_t smem = sizeof(float) * (kF32Warps * kRing * ring_block(false) + kF32Warps * kStreamRowmax);
-      auto kern = l2 ? f32_ids_stream_kernel<true> : f32_ids_stream_kernel<false>;
-      GEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kF32Threads, smem));
-      if (per_sm < 1) return fail(GEM_ERR_UNSUPPORTED, "f32 scoring kernel does not fit on an SM");
-      const int64_t max_grid = (n_cands + kF32Warps - 1) / kF32Warps;
-      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(max_grid, (int64_t)s->n_sm * per_sm));
-      kern<<<grid, kF32Threads, smem, st>>>(sa, n_cands);
-      GEM_CUDA_TRY(cudaGetLastError());
-      note_launches(1);
-      return GEM_OK;
+    StreamArgs sa{q, q_offsets, n_queries, cand_offsets, cand_ids, s->d_f32, s->d_offsets, s->n_sets,
+                  scores, ws->d_status, mq};
+    const bool coded = qcodes || a.stored_codes;
+    if (coded) {
+      sa.codes = s->d_codes;
+      sa.centroids = s->d_codebook;
+      sa.qcodes = qcodes;  // null: the asymmetric form (exact query rows)
     }
-    const size_t smem = sizeof(float) * (kF32Warps * kVecBlock * kStageStride + (size_t)kF32Warps * mq);
-    auto kern = qcodes ? f32_ids_kernel<true, false> : l2 ? f32_ids_kernel<false, true> : f32_ids_kernel<false, false>;
+    const size_t smem = sizeof(float) * (kF32Warps * kRing * ring_block(false) + kF32Warps * kStreamRowmax);
+    auto kern = coded ? f32_ids_stream_kernel<false, true>
+                      : l2 ? f32_ids_stream_kernel<true> : f32_ids_stream_kernel<false>;
     GEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     GEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kF32Threads, smem));
     if (per_sm < 1) return fail(GEM_ERR_UNSUPPORTED, "f32 scoring kernel does not fit on an SM");
     const int64_t max_grid = (n_cands + kF32Warps - 1) / kF32Warps;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(max_grid, (int64_t)s->n_sm * per_sm));
-    kern<<<grid, kF32Threads, smem, st>>>(a, mq, n_cands);
+    kern<<<grid, kF32Threads, smem, st>>>(sa, n_cands);
   }
   GEM_CUDA_TRY(cudaGetLastError());
   note_launches(1);

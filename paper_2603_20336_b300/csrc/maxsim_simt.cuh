@@ -103,13 +103,12 @@ __device__ __forceinline__ float4 set_row4(const float* __restrict__ P, const in
 // otherwise rows are centroids[row_code[j] * 128].  The next 8 set vectors are
 // loaded into registers while the current 8 are multiplied, so the loads of a
 // set overlap its arithmetic; the arithmetic order is unchanged.
-template <bool CodedQ, bool L2>
-__device__ __forceinline__ float warp_chamfer_impl(const float* __restrict__ qs, int q_stride,
-                                                   const int32_t* __restrict__ q_code, int m_q,
-                                                   const float* __restrict__ P, const int32_t* __restrict__ row_code,
-                                                   const float* __restrict__ centroids, int m_p,
-                                                   float* __restrict__ stage, float* __restrict__ rowmax,
-                                                   uint64_t (&qr)[kQPairs], int& loaded_rg) {
+template <bool L2 = false>
+__device__ __forceinline__ float warp_chamfer(const float* __restrict__ qs, int q_stride, int m_q,
+                                              const float* __restrict__ P, const int32_t* __restrict__ row_code,
+                                              const float* __restrict__ centroids, int m_p,
+                                              float* __restrict__ stage, float* __restrict__ rowmax,
+                                              uint64_t (&qr)[kQPairs], int& loaded_rg) {
   const int lane = threadIdx.x & 31;
   const int half = lane & 1;           // component half of this lane
   const int pair = lane >> 1;          // query rows 2 pair, 2 pair + 1
@@ -123,16 +122,9 @@ __device__ __forceinline__ float warp_chamfer_impl(const float* __restrict__ qs,
 #pragma unroll
       for (int k2 = 0; k2 < kRowPairs; ++k2) {
         const int kk = half * (kDim / 2) + 2 * k2;
-        if constexpr (CodedQ) {
-          qr[k2] = (ia < m_q) ? pack2(centroids[(int64_t)q_code[ia] * kDim + kk],
-                                      centroids[(int64_t)q_code[ia] * kDim + kk + 1]) : 0ull;
-          qr[kRowPairs + k2] = (ib < m_q) ? pack2(centroids[(int64_t)q_code[ib] * kDim + kk],
-                                                  centroids[(int64_t)q_code[ib] * kDim + kk + 1]) : 0ull;
-        } else {
-          qr[k2] = (ia < m_q) ? pack2(qs[(int64_t)ia * q_stride + kk], qs[(int64_t)ia * q_stride + kk + 1]) : 0ull;
-          qr[kRowPairs + k2] =
-              (ib < m_q) ? pack2(qs[(int64_t)ib * q_stride + kk], qs[(int64_t)ib * q_stride + kk + 1]) : 0ull;
-        }
+        qr[k2] = (ia < m_q) ? pack2(qs[(int64_t)ia * q_stride + kk], qs[(int64_t)ia * q_stride + kk + 1]) : 0ull;
+        qr[kRowPairs + k2] =
+            (ib < m_q) ? pack2(qs[(int64_t)ib * q_stride + kk], qs[(int64_t)ib * q_stride + kk + 1]) : 0ull;
       }
       loaded_rg = rg;
     }
@@ -173,27 +165,6 @@ __device__ __forceinline__ float warp_chamfer_impl(const float* __restrict__ qs,
     }
   }
   return __shfl_sync(0xffffffffu, s, 0);
-}
-
-template <bool L2 = false>
-__device__ __forceinline__ float warp_chamfer(const float* __restrict__ qs, int q_stride, int m_q,
-                                              const float* __restrict__ P, const int32_t* __restrict__ row_code,
-                                              const float* __restrict__ centroids, int m_p,
-                                              float* __restrict__ stage, float* __restrict__ rowmax,
-                                              uint64_t (&qr)[kQPairs], int& loaded_rg) {
-  return warp_chamfer_impl<false, L2>(qs, q_stride, nullptr, m_q, P, row_code, centroids, m_p, stage, rowmax, qr,
-                                      loaded_rg);
-}
-
-// Codes form with the query rows given as centroid indices (row i is
-// centroids[q_code[i] * 128]).
-__device__ __forceinline__ float warp_chamfer_coded_q(const float* __restrict__ centroids,
-                                                      const int32_t* __restrict__ q_code, int m_q,
-                                                      const float* __restrict__ P, const int32_t* __restrict__ row_code,
-                                                      int m_p, float* __restrict__ stage, float* __restrict__ rowmax,
-                                                      uint64_t (&qr)[kQPairs], int& loaded_rg) {
-  return warp_chamfer_impl<true, false>(nullptr, 0, q_code, m_q, P, row_code, centroids, m_p, stage, rowmax, qr,
-                                        loaded_rg);
 }
 
 // ------------------------------------------------------------------ streamed id lists
