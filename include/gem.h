@@ -558,8 +558,11 @@ gem_status gem_maxsim_bwd(const float* q, const int64_t* q_offsets, int32_t n_qu
  *   max_*        capacity of the batch's own device buffers
  *   seg          candidates per work item (1..1024; the autotuner's knob)
  *   ctas_per_sm  persistent CTAs per SM (0 = as many as fit)
- * GEM_CODES needs a store codebook.  The caller owns the device buffers the
- * graph reads and writes; their addresses are fixed for the batch's lifetime and
+ * GEM_CODES needs a store codebook.  Each run of it first assigns the run's
+ * query rows to their NN codes (from 16,384 rows of capacity and 64 centroids
+ * on the tensor cores, the same codes as gem_assign_codes), for which the batch
+ * then holds about 512 (k1 + min(max_q_rows, 2^22)) + 4 max_q_rows bytes of its
+ * own device memory (bf16 halves of the centroids and rows, a fallback list).  The caller owns the device buffers the graph reads and writes; their addresses are fixed for the batch's lifetime and
  * the caller refills them before each run: q float32 [max_q_rows * 128],
  * q_offsets and cand_offsets int64 [max_queries + 1], cand_ids int64
  * [max_cands] (same meaning as in gem_score_ids), scores float32 [max_cands]
