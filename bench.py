@@ -734,7 +734,6 @@ def run_gem(args, dist, rank, world, local):
 
     scores = torch.empty((B, store.n_sets), dtype=torch.float32, device=dev)
     pool_ids = torch.empty((B, R), dtype=torch.int64, device=dev)
-    pool_off = torch.arange(B + 1, dtype=torch.int64, device=dev) * R
     pool_sc = torch.empty(B * R, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
     if args.schedule:
@@ -754,7 +753,7 @@ def run_gem(args, dist, rank, world, local):
         pool_ids.copy_(pid)
         if ev:
             ev[3].record(st)
-        gem.score_ids(store, ws, q, qo, pool_off, pool_ids.view(-1), "f32", out=pool_sc)
+        gem.rerank_pool(store, ws, q, qo, pool_ids, out=pool_sc.view(B, R))
         if ev:
             ev[4].record(st)
         out = gem.topk(ws, pool_sc.view(B, R), K, ids=pool_ids.view(-1).view(B, R).contiguous())

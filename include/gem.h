@@ -442,6 +442,25 @@ gem_status gem_score_ids(const gem_store* store, gem_workspace* ws, const float*
                          int32_t compute, float* scores, void* stream);
 
 /*
+ * gem_rerank_pool: the exact rescoring of a rerank pool, the final step of
+ * Algorithm 5 (exact CH of Sec. 3.1 Eq. 1 over the pool the first pass kept)
+ * as its own call, the step gem_search runs between its two top-k selections.
+ *   pool_ids     int64 [n_queries x depth], row b = query b's pool (-1 = empty
+ *                entry: score -inf; an id >= n_sets: NaN and GEM_ERR_BOUNDS in
+ *                gem_workspace_status)
+ *   pool_scores  float32 [n_queries x depth] (output)
+ * The scores are those of gem_score_ids with GEM_F32 over the rows as per-query
+ * lists (bit-identical).  From 65,536 entries the pool is scored in the order of
+ * its set ids (up to 64 ranges of ids, then query), so that a set in several
+ * queries' pools is read from DRAM about once; the output order is unaffected.
+ * Needs GEM_KEEP_F32 and a workspace with max_k > 0 and max_cands >= n_queries x
+ * depth.  Device buffers, caller-owned; asynchronous on `stream`.
+ */
+gem_status gem_rerank_pool(const gem_store* store, gem_workspace* ws, const float* q, const int64_t* q_offsets,
+                           int32_t n_queries, int64_t n_q_rows, const int64_t* pool_ids, int32_t depth,
+                           float* pool_scores, void* stream);
+
+/*
  * Quantized Chamfer estimate (Sec. 4.5.3, Eq. 16) in similarity form:
  *   est = sum_i max_j <C_{NN(q_i)}, C_{NN(p_j)}> = m_q - qCH(Q, P)
  * The query vectors are coded on the fly; stored vectors use the store's codes.

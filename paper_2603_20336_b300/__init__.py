@@ -215,6 +215,21 @@ def score_ids(store: Store, ws: Workspace, q, q_offsets, cand_offsets, cand_ids,
     return out
 
 
+def rerank_pool(store: Store, ws: Workspace, q, q_offsets, pool_ids, out=None, stream=None):
+    """Exact FP32 CH of a rerank pool (Algorithm 5's final rescoring): pool_ids
+    int64 [n_queries, depth] (-1 = empty) -> float32 [n_queries, depth], the same
+    scores as score_ids with "f32" over the rows as per-query lists."""
+    q, qo, B, rows = _queries(q, q_offsets)
+    pid = _dev(pool_ids, torch.int64, "pool_ids")
+    if pid.dim() != 2 or pid.shape[0] != B:
+        raise ValueError("pool_ids must be [n_queries, depth]")
+    if out is None:
+        out = torch.empty(pid.shape, dtype=torch.float32, device=q.device)
+    _check(lib.gem_rerank_pool(store.handle, ws.handle, _ptr(q), _ptr(qo), B, rows, _ptr(pid), pid.shape[1],
+                               _ptr(out), _stream(stream)))
+    return out
+
+
 def topk(ws: Workspace, scores, k: int, ids=None, row_offsets=None, stream=None):
     """Per-row top-k by (score desc, id asc): (ids int64 [rows, k], scores float32 [rows, k])."""
     scores = _dev(scores, torch.float32, "scores")

@@ -37,6 +37,7 @@ SIGNATURES = {
     "gem_workspace_set_schedule": (C.c_int, [P, I32, I32, I32]),
     "gem_score_all": (C.c_int, [P, P, P, P, I32, I64, I32, P, P]),
     "gem_score_ids": (C.c_int, [P, P, P, P, I32, I64, P, P, I64, I32, P, P]),
+    "gem_rerank_pool": (C.c_int, [P, P, P, P, I32, I64, P, I32, P, P]),
     "gem_topk": (C.c_int, [P, P, P, I32, I64, P, I32, P, P, P]),
     "gem_search": (C.c_int, [P, P, P, P, I32, I64, I32, I32, I32, P, P, P]),
     "gem_search_host": (C.c_int, [P, P, P, P, I32, I32, I32, I32, P, P, P]),

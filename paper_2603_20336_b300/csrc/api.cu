@@ -718,6 +718,23 @@ gem_status gem_score_ids(const gem_store* s, gem_workspace* w, const float* q,
   return fail(GEM_ERR_INVALID, "unknown compute dtype");
 }
 
+gem_status gem_rerank_pool(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
+                           int32_t n_queries, int64_t n_q_rows, const int64_t* pool_ids, int32_t depth,
+                           float* pool_scores, void* stream) {
+  GEM_NVTX_RANGE("gem_rerank_pool");
+  gem_status r = check_query_args(s, w, q, q_offsets, n_queries, n_q_rows);
+  if (r != GEM_OK) return r;
+  if (!pool_ids || !pool_scores) return fail(GEM_ERR_INVALID, "pool_ids or pool_scores is NULL");
+  if (!w->d_pool_off) return fail(GEM_ERR_STATE, "workspace was created with max_k or max_cands 0");
+  if (depth < 1 || (int64_t)depth * n_queries > w->max_cands)
+    return fail(GEM_ERR_INVALID, "n_queries * depth must be 1..max_cands");
+  if (!s->d_f32) return fail(GEM_ERR_STATE, "the rerank needs the fp32 copy");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  launch_iota_offsets(w->d_pool_off, n_queries, depth, st);
+  GEM_CUDA_TRY(cudaGetLastError());
+  return launch_f32_score_pool(s, w, q, q_offsets, n_queries, depth, pool_ids, pool_scores, st);
+}
+
 gem_status gem_beam_search(const gem_store* s, gem_workspace* w, const float* q, const int64_t* q_offsets,
                            int32_t n_queries, int64_t n_q_rows, const int64_t* graph_off, const int32_t* graph_nbrs,
                            int32_t max_degree, const uint32_t* cluster_mask, const int64_t* entries,

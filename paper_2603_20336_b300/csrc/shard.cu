@@ -119,7 +119,7 @@ gem_status gem_shard_rerank(const gem_store* s, gem_workspace* w, const float* q
   launch_iota_offsets(w->d_pool_off, n_queries, depth, st);
   GEM_CUDA_TRY(cudaGetLastError());
   note_launches(1);
-  r = launch_f32_score(s, w, q, q_offsets, n_queries, w->d_pool_off, w->d_pool_ids, n, w->d_pool_scores, st);
+  r = launch_f32_score_pool(s, w, q, q_offsets, n_queries, depth, w->d_pool_ids, w->d_pool_scores, st);
   if (r != GEM_OK) return r;
   scatter_owned_kernel<<<grid_for(n, s->n_sm), 256, 0, st>>>(w->d_pool_ids, w->d_pool_scores, n, pool_scores);
   GEM_CUDA_TRY(cudaGetLastError());

@@ -207,6 +207,44 @@ def test_score_ids_streamed_rerank_bit_matches(gem, cfg1):
         assert abs(S[t] - S64[b_of[t], ids[t]]) <= 1e-5 * L1[b_of[t], ids[t]]
 
 
+def test_rerank_pool_bit_matches_score_ids(gem, cfg1):
+    """gem_rerank_pool on a pool of n_queries x depth ids: from 65,536 entries it
+    scores the pool in the order of its set ids (ranges of ids, then query),
+    below that in query order.  Pools of 64 x 1,200 (64 ranges) and 10 x 300
+    with repeated ids and -1 entries: scores bit-identical to score_ids over the
+    same rows as per-query lists, -1 entries -inf; an id past the store reads
+    NaN with GEM_ERR_BOUNDS."""
+    w, store = cfg1["w"], cfg1["store"]
+    rng = np.random.default_rng(17)
+    for nq, depth in ((64, 1200), (10, 300)):
+        qs = synth.vector_sets(rng.integers(1, 129, size=nq), synth.centres(64, 1235), 993 + nq)
+        q, qo = qs.vecs.cuda(), torch.from_numpy(qs.offsets).cuda()
+        ws = gem.Workspace(store, max_queries=nq, max_q_rows=int(qs.offsets[-1]), max_q_len=128,
+                           max_cands=nq * depth, max_k=256)
+        # a shared pool: many queries name the same sets, as a top-R pool does
+        pool = rng.integers(0, w.docs.n_sets, size=(nq, depth))
+        shared = rng.integers(0, 40, size=(nq, depth))
+        pool = np.where(rng.random((nq, depth)) < 0.5, shared, pool).astype(np.int64)
+        pool[rng.random((nq, depth)) < 0.02] = -1
+        pid = torch.from_numpy(pool).cuda()
+        got = gem.rerank_pool(store, ws, q, qo, pid)
+        assert ws.status() == 0
+        co = torch.arange(0, nq * depth + 1, depth, dtype=torch.int64, device="cuda")
+        ref = gem.score_ids(store, ws, q, qo, co, pid.view(-1), "f32").view(nq, depth)
+        assert ws.status() == 0
+        assert torch.equal(got.view(torch.int32), ref.view(torch.int32)), (nq, depth)
+        assert torch.all(got[pid < 0] == -float("inf"))
+        if nq == 10:
+            pid[3, 7] = w.docs.n_sets
+            got = gem.rerank_pool(store, ws, q, qo, pid)
+            assert ws.status() == 7                # GEM_ERR_BOUNDS
+            assert torch.isnan(got[3, 7]).item()
+            keep = torch.ones_like(got, dtype=torch.bool)
+            keep[3, 7] = False
+            assert torch.equal(got[keep].view(torch.int32), ref[keep].view(torch.int32))
+        ws.close()
+
+
 def test_score_ids_query_longer_than_workspace_limit(gem, cfg1):
     """A query set longer than the workspace's max_q_len: its pairs score NaN and
     the status reads GEM_ERR_INVALID; the other queries' pairs are unaffected."""
