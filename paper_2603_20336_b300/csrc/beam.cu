@@ -13,8 +13,10 @@
 //   insert   in queue order, each scored set into its W_e and into R
 // and the host runs rounds until no queue is left.  W_e and R keep the ef best
 // sets under the total order (higher score, then lower id); they are unsorted
-// arrays, so pop and eviction are warp arg-max / arg-min searches.  One warp owns
-// one query in every kernel, so no two threads ever update the same query state.
+// arrays, so pop and eviction are warp arg-max / arg-min searches (the insert
+// keeps the worst entry in registers until it changes).  One warp owns one query
+// in every kernel, so no two warps ever update the same query state; the expand
+// tests a popped set's neighbours 32 at a time, one per lane.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -57,23 +59,6 @@ __device__ __forceinline__ int warp_arg(const float* sc, const int32_t* id, int 
     }
   }
   return bj;
-}
-
-// Insert (s, i) into the bounded set sc/id of size *n (capacity cap): append while
-// there is room, else replace the worst entry if (s, i) is better.  Warp-uniform.
-__device__ __forceinline__ void warp_insert(float* sc, int32_t* id, int* n, int cap, float s, int i) {
-  const int lane = threadIdx.x & 31;
-  const int m = *n;
-  if (m < cap) {
-    if (lane == 0) { sc[m] = s; id[m] = i; *n = m + 1; }
-  } else {
-    const int w = warp_arg(sc, id, m, false);
-    if (bs_better(s, i, sc[w], id[w])) {
-      __syncwarp();
-      if (lane == 0) { sc[w] = s; id[w] = i; }
-    }
-  }
-  __syncwarp();
 }
 
 struct BeamState {
@@ -158,25 +143,50 @@ __global__ void bs_expand_kernel(BeamState st, const int64_t* __restrict__ graph
       }
       __syncwarp();
       if (psc < tau) continue;
-      for (int64_t e = graph_off[pid]; e < graph_off[pid + 1] && !bad; ++e) {
-        const int nb = graph_nbrs[e];
-        if (nb < 0 || nb >= n_sets) { bad = true; break; }
-        if ((vis[nb >> 5] >> (nb & 31)) & 1u) continue;
-        // a vector of nb in a cluster of C_query?
-        bool hit = false;
-        for (int64_t v = set_off[nb] + lane; v < set_off[nb + 1] && !hit; v += 32) {
-          const int cl = icodes[v];
-          hit = (mask[cl >> 5] >> (cl & 31)) & 1u;
+      // the neighbours of P in list order, 32 at a time (lane i: the i-th of the
+      // group), with the outcome of the sequential walk: a neighbour is queued
+      // if it is not visited, has a vector in a cluster of C_query and is not a
+      // repeat of an earlier one in the list; the walk stops at the first id
+      // outside [0, n_sets) and once the round buffer is full
+      const int64_t e1 = graph_off[pid + 1];
+      for (int64_t eb = graph_off[pid]; eb < e1 && !bad; eb += 32) {
+        const int64_t e = eb + lane;
+        const bool in = e < e1;
+        const int nb = in ? graph_nbrs[e] : 0;
+        const unsigned badm = __ballot_sync(0xffffffffu, in && (nb < 0 || nb >= n_sets));
+        const int n_ok = badm ? __ffs(badm) - 1 : 32;  // lanes before the first bad id
+        bool take = in && lane < n_ok;
+        const unsigned okm = __ballot_sync(0xffffffffu, take);
+        // a repeat of an earlier neighbour of this group takes that one's outcome
+#pragma unroll 1
+        for (int j = 0; j < 32; ++j) {
+          const int other = __shfl_sync(0xffffffffu, nb, j);
+          if (j < lane && ((okm >> j) & 1u) && other == nb) take = false;
         }
-        if (!__any_sync(0xffffffffu, hit)) continue;
-        if (c >= st.cap) { bad = true; break; }
-        if (lane == 0) {
-          vis[nb >> 5] |= 1u << (nb & 31);
-          st.raw[(int64_t)b * st.cap + c] = nb;
-          st.rawq[(int64_t)b * st.cap + c] = qi;
+        // visited (read past L1: earlier groups set bits with atomics)
+        if (take) take = !((__ldcg(vis + (nb >> 5)) >> (nb & 31)) & 1u);
+        if (take) {
+          bool hit = false;
+          const int64_t v1 = set_off[nb + 1];
+          for (int64_t v = set_off[nb]; v < v1; ++v) {
+            const int cl = icodes[v];
+            if ((mask[cl >> 5] >> (cl & 31)) & 1u) { hit = true; break; }
+          }
+          take = hit;
         }
+        const unsigned qm = __ballot_sync(0xffffffffu, take);
+        const int rank = __popc(qm & ((1u << lane) - 1u));
+        const int room = st.cap - c;
+        if (take && rank < room) {
+          atomicOr(vis + (nb >> 5), 1u << (nb & 31));
+          st.raw[(int64_t)b * st.cap + c + rank] = nb;
+          st.rawq[(int64_t)b * st.cap + c + rank] = qi;
+        }
+        const int n_new = __popc(qm);
+        if (n_new > room) bad = true;  // the walk stops at the first set with no room
+        c += min(n_new, room);
+        if (badm) bad = true;
         __syncwarp();
-        ++c;
       }
     }
     if (lane == 0) {
@@ -223,18 +233,72 @@ __global__ void bs_compact_kernel(BeamState st) {
   }
 }
 
+// Insert (s, i) into the bounded set sc/id holding n entries (capacity cap):
+// append while there is room, else replace the worst entry if (s, i) is better.
+// n and the worst entry (index w, -1 when not known; its score and id) live in
+// registers, so a set that cannot enter costs no memory read.  Ids within a
+// query are distinct, so the worst entry is unique.  Warp-uniform.
+__device__ __forceinline__ void cached_insert(float* sc, int32_t* id, int& n, int& w, float& ws, int& wi, int cap,
+                                              float s, int i) {
+  const int lane = threadIdx.x & 31;
+  if (n < cap) {
+    if (lane == 0) { sc[n] = s; id[n] = i; }
+    ++n;
+    w = -1;
+  } else {
+    if (w < 0) {
+      w = warp_arg(sc, id, n, false);
+      ws = sc[w];
+      wi = id[w];
+    }
+    if (bs_better(s, i, ws, wi)) {
+      if (lane == 0) { sc[w] = s; id[w] = i; }
+      w = -1;
+    }
+  }
+  __syncwarp();
+}
+
 __global__ void bs_insert_kernel(BeamState st) {
+  const int lane = threadIdx.x & 31;
   for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < st.n_queries; b += (gridDim.x * blockDim.x) >> 5) {
     float* rsc = st.rsc + (int64_t)b * st.ef;
     int32_t* rid = st.rid + (int64_t)b * st.ef;
-    for (int64_t j = st.off[b]; j < st.off[b + 1]; ++j) {
-      const float s = st.score[j];
-      const int id = (int)st.cand[j];
-      const int qi = st.candq[j];
-      warp_insert(st.qsc + ((int64_t)b * st.S + qi) * st.ef, st.qid + ((int64_t)b * st.S + qi) * st.ef,
-                  st.qsize + (int64_t)b * st.S + qi, st.ef, s, id);
-      // a deleted set keeps its place on the paths but never enters R
-      if (!st.dead || !((st.dead[id >> 5] >> (id & 31)) & 1u)) warp_insert(rsc, rid, st.rsize + b, st.ef, s, id);
+    int rn = st.rsize[b], rw = -1, rwi = 0;
+    float rws = 0.f;
+    int cur = -1, qn = 0, qw = -1, qwi = 0;  // the queue of the current run of candidates
+    float qws = 0.f;
+    float* qsc = nullptr;
+    int32_t* qid = nullptr;
+    const int64_t j1 = st.off[b + 1];
+    for (int64_t jb = st.off[b]; jb < j1; jb += 32) {
+      // 32 candidates' (score, id, queue) in one load, then in order
+      const int64_t jl = jb + lane;
+      float sl = 0.f;
+      int il = 0, ql = 0;
+      if (jl < j1) { sl = st.score[jl]; il = (int)st.cand[jl]; ql = st.candq[jl]; }
+      const int m = (int)(j1 - jb < 32 ? j1 - jb : 32);
+      for (int t = 0; t < m; ++t) {
+        const float s = __shfl_sync(0xffffffffu, sl, t);
+        const int id = __shfl_sync(0xffffffffu, il, t);
+        const int qi = __shfl_sync(0xffffffffu, ql, t);
+        if (qi != cur) {
+          if (cur >= 0 && lane == 0) st.qsize[(int64_t)b * st.S + cur] = qn;
+          cur = qi;
+          qsc = st.qsc + ((int64_t)b * st.S + qi) * st.ef;
+          qid = st.qid + ((int64_t)b * st.S + qi) * st.ef;
+          qn = st.qsize[(int64_t)b * st.S + qi];
+          qw = -1;
+        }
+        cached_insert(qsc, qid, qn, qw, qws, qwi, st.ef, s, id);
+        // a deleted set keeps its place on the paths but never enters R
+        if (!st.dead || !((st.dead[id >> 5] >> (id & 31)) & 1u))
+          cached_insert(rsc, rid, rn, rw, rws, rwi, st.ef, s, id);
+      }
+    }
+    if (lane == 0) {
+      if (cur >= 0) st.qsize[(int64_t)b * st.S + cur] = qn;
+      st.rsize[b] = rn;
     }
   }
 }

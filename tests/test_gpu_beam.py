@@ -56,7 +56,7 @@ def setup(gem):
     store.close()
 
 
-@pytest.mark.parametrize("ef,max_rounds", [(16, 1000), (5, 1000), (40, 3)])
+@pytest.mark.parametrize("ef,max_rounds", [(16, 1000), (5, 1000), (40, 3), (300, 1000)])
 def test_beam_search_matches_oracle_rounds(gem, setup, ef, max_rounds):
     d = setup
     ids, sc, rounds = gem.beam_search(d["store"], d["ws"], d["q"], d["qo"], torch.from_numpy(d["go"]).cuda(),
@@ -142,6 +142,38 @@ def test_beam_search_asymmetric_qch_matches_oracle(gem, setup):
         qc = d["lst"][b, :d["cnt"][b]]
         R, r = oracle.beam_search(lambda s, b=b: float(allq[b, s]), d["go"], d["gn"], d["set_clusters"], qc,
                                   ent[b], ef=16)
+        want_rounds = max(want_rounds, r)
+        n = len(R)
+        assert ids[b, :n].tolist() == [i for _, i in R], b
+        np.testing.assert_array_equal(sc[b, :n], np.array([s for s, _ in R], dtype=np.float32))
+    assert rounds == want_rounds
+
+
+@pytest.mark.parametrize("ef", [16, 300])
+def test_beam_search_dense_graph_with_repeated_neighbours(gem, setup, ef):
+    """Neighbour lists of about 40 sets, tested 32 at a time on the GPU, with
+    repeats inside a group of 32 and across groups (the walk of the oracle queues
+    a set once: its second occurrence is visited or fails the same cluster test),
+    with R smaller and larger than a round's candidates (ef 16 and 300).
+    R and the number of rounds bit-exact against the oracle."""
+    d = setup
+    go, gn = synth.random_graph(3000, 20, 777)
+    gn = gn.copy()
+    for node in range(0, 3000, 5):
+        lo, hi = int(go[node]), int(go[node + 1])
+        if hi - lo >= 36:
+            gn[lo + 1] = gn[lo]            # a repeat within the first group
+            gn[lo + 34] = gn[lo + 2]       # a repeat in the next group
+    ids, sc, rounds = gem.beam_search(d["store"], d["ws"], d["q"], d["qo"], torch.from_numpy(go).cuda(),
+                                      torch.from_numpy(gn).cuda(), d["mask"], d["ent"], ef=ef)
+    assert d["ws"].status() == 0
+    ids, sc = ids.cpu().numpy(), sc.cpu().numpy()
+    ent = d["ent"].cpu().numpy()
+    want_rounds = 0
+    for b in range(d["B"]):
+        qc = d["lst"][b, :d["cnt"][b]]
+        R, r = oracle.beam_search(lambda s, b=b: float(d["allq"][b, s]), go, gn, d["set_clusters"], qc, ent[b],
+                                  ef=ef)
         want_rounds = max(want_rounds, r)
         n = len(R)
         assert ids[b, :n].tolist() == [i for _, i in R], b
