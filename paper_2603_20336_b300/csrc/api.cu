@@ -344,7 +344,7 @@ gem_status gem_workspace_create(const gem_store* s, int32_t max_queries, int64_t
     return r;                                                               \
   }
   WS_ALLOC(d_status, 1);
-  WS_ALLOC(d_unit_counter, 1);
+  WS_ALLOC(d_unit_counter, 2);
   WS_ALLOC(d_plan_hdr, kPlanHdrInts);
   WS_ALLOC(d_part_query, w->max_parts);
   WS_ALLOC(d_part_rows, w->max_parts);

@@ -401,7 +401,7 @@ gem_status beam_search(const gem_store* s, gem_workspace* w, const float* q, con
     note_launches(2);
     if (total > 0) {
       gem_status rr = launch_qch_scan_ids(s, st.tables, q_offsets, n_queries, max_np, st.off, st.cand, st.score,
-                                          w->d_status, stm);
+                                          w->d_status, reinterpret_cast<unsigned long long*>(w->d_unit_counter), stm);
       if (rr != GEM_OK) return rr;
       bs_insert_kernel<<<grid, kBsThreads, 0, stm>>>(st);
       GEM_CUDA_TRY(cudaGetLastError());

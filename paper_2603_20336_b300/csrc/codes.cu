@@ -241,6 +241,7 @@ struct ScanArgs {
   const int64_t* cand_ids;
   float* out;
   int* status;
+  unsigned long long* counter;  // chunk counter, zero at launch
 };
 
 // A warp takes 32 consecutive (query, set) pairs at a time: lane i loads pair
@@ -252,13 +253,19 @@ constexpr int kScanUnroll = 16;    // table rows in flight per warp
 
 __global__ void __launch_bounds__(256, kScanCtasPerSm) qch_scan_kernel(ScanArgs a) {
   const int lane = threadIdx.x & 31;
-  const int64_t warp_g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const bool all_sets = (a.cand_ids == nullptr);
   const int64_t base = all_sets ? 0 : a.cand_off[a.q0];
   const int64_t total = all_sets ? (int64_t)a.nq * a.n_sets : a.cand_off[a.q0 + a.nq] - base;
   const int64_t n_chunks = (total + 31) / 32;
-  for (int64_t ch = warp_g; ch < n_chunks; ch += n_warps) {
+  // chunks are claimed in order from a counter, so the warps in flight work on
+  // neighbouring pairs: a few queries' tables at a time, which stay in L2 (a
+  // fixed grid stride lets the warps drift apart until the tables in use exceed
+  // L2 and every row is read from DRAM several times)
+  for (;;) {
+    unsigned long long claim = 0;
+    if (lane == 0) claim = atomicAdd(a.counter, 1ull);
+    const int64_t ch = (int64_t)__shfl_sync(0xffffffffu, claim, 0);
+    if (ch >= n_chunks) break;
     const int64_t w0 = ch * 32;
     const int cnt = (int)min((int64_t)32, total - w0);
     // lane i: pair w0 + i (its query, set id, output slot, set rows)
@@ -437,8 +444,9 @@ gem_status launch_qch_tables(const gem_store* s, const int32_t* qcodes, const fl
 
 gem_status launch_qch_scan_ids(const gem_store* s, const float* T, const int64_t* q_offsets, int32_t n_queries,
                                int max_np, const int64_t* cand_offsets, const int64_t* cand_ids, float* out,
-                               int* status, cudaStream_t st) {
+                               int* status, unsigned long long* counter, cudaStream_t st) {
   if (n_queries == 0) return GEM_OK;
+  GEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
   ScanArgs a;
   a.T = T;
   a.k1 = s->k1;
@@ -453,6 +461,7 @@ gem_status launch_qch_scan_ids(const gem_store* s, const float* T, const int64_t
   a.cand_ids = cand_ids;
   a.out = out;
   a.status = status;
+  a.counter = counter;
   qch_scan_kernel<<<s->n_sm * kScanCtasPerSm, 256, 0, st>>>(a);
   GEM_CUDA_TRY(cudaGetLastError());
   note_launches(1);
@@ -490,6 +499,8 @@ gem_status launch_qch(const gem_store* s, gem_workspace* w, const float* q, cons
     a.cand_ids = cand_ids;
     a.out = est;
     a.status = w->d_status;
+    a.counter = reinterpret_cast<unsigned long long*>(w->d_unit_counter);
+    GEM_CUDA_TRY(cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st));
     qch_scan_kernel<<<s->n_sm * kScanCtasPerSm, 256, 0, st>>>(a);
     GEM_CUDA_TRY(cudaGetLastError());
     note_launches(2);

@@ -110,7 +110,8 @@ struct gem_workspace {
   int tc_chunk_rows = 1 << 16;
 
   int* d_status = nullptr;
-  int* d_unit_counter = nullptr;  // work-unit counter of the tensor-core kernels
+  int* d_unit_counter = nullptr;  // 8 bytes: work-unit counter of the tensor-core kernels (low 32 bits)
+                                  // and, as 64 bits, the chunk counter of the qCH scan
 
   // query plan
   int64_t packed_cap = 0;  // rows of the packed query buffers
@@ -324,7 +325,7 @@ gem_status launch_qch_tables(const gem_store* s, const int32_t* qcodes, const fl
                              int32_t n_queries, int max_np, float* T, cudaStream_t st);
 gem_status launch_qch_scan_ids(const gem_store* s, const float* T, const int64_t* q_offsets, int32_t n_queries,
                                int max_np, const int64_t* cand_offsets, const int64_t* cand_ids, float* out,
-                               int* status, cudaStream_t st);
+                               int* status, unsigned long long* counter, cudaStream_t st);
 gem_status launch_cluster_index(gem_store* s, cudaStream_t st);
 gem_status launch_qemd(const gem_store* s, const int64_t* set_a, const int64_t* set_b, int64_t n_pairs, float* out,
                        int* status, cudaStream_t st);
