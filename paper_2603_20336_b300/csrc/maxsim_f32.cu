@@ -87,11 +87,17 @@ f32_ids_stream_kernel(StreamArgs a, int64_t n_cands) {
   const int64_t n_warps = (int64_t)gridDim.x * kF32Warps;
   const int64_t gw = (int64_t)blockIdx.x * kF32Warps + warp;
   if (a.perm) {
-    // a pool in segment order: all warps move through the positions together,
-    // kPoolGroup at a time, so the sets in use at any moment come from one or
-    // two segments of set ids
-    for (int64_t p0 = gw * kPoolGroup; p0 < n_cands; p0 += n_warps * kPoolGroup)
+    // a pool in segment order: the warps claim kPoolGroup positions at a time,
+    // in order, from a counter, so they move through the positions together and
+    // the sets in use at any moment come from one or two segments of set ids
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+      unsigned long long claim = 0;
+      if (lane == 0) claim = atomicAdd(a.counter, 1ull);
+      const int64_t p0 = (int64_t)__shfl_sync(0xffffffffu, claim, 0) * kPoolGroup;
+      if (p0 >= n_cands) break;
       stream_pairs<L2, false, CODES>(a, p0, min(n_cands, p0 + kPoolGroup), ring, rowmax);
+    }
     return;
   }
   const int64_t chunk = (n_cands + n_warps - 1) / n_warps;
@@ -241,6 +247,8 @@ gem_status launch_f32_score_pool(const gem_store* s, gem_workspace* ws, const fl
                 scores, ws->d_status, mq};
   sa.perm = ws->d_pool_perm;
   sa.per_query = per_query;
+  sa.counter = reinterpret_cast<unsigned long long*>(ws->d_unit_counter);
+  GEM_CUDA_TRY(cudaMemsetAsync(sa.counter, 0, sizeof(unsigned long long), st));
   const size_t smem = sizeof(float) * (kF32Warps * kRing * ring_block(false) + kF32Warps * kStreamRowmax);
   auto kern = l2 ? f32_ids_stream_kernel<true> : f32_ids_stream_kernel<false>;
   GEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -188,6 +188,7 @@ struct StreamArgs {
   // then a run of positions whose pairs share a query
   const int32_t* perm = nullptr;
   int per_query = 0;
+  unsigned long long* counter = nullptr;  // with perm: group counter, zero at launch
   // codes form (optional): stored row r is centroids[codes[r]] and, with qcodes,
   // query row i is centroids[qcodes[i]] (the quantized estimate in similarity
   // form, the same per-dot arithmetic)
