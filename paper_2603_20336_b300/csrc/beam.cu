@@ -14,7 +14,8 @@
 // and the host runs rounds until no queue is left.  W_e and R keep the ef best
 // sets under the total order (higher score, then lower id); they are unsorted
 // arrays, so pop and eviction are warp arg-max / arg-min searches (the insert
-// keeps the worst entry in registers until it changes).  One warp owns one query
+// keeps the worst entry in registers until it changes, appends a queue's run of
+// candidates at once and discards by ballot the candidates R cannot take).  One warp owns one query
 // in every kernel, so no two warps ever update the same query state; the expand
 // tests a popped set's neighbours 32 at a time, one per lane.
 #include <cuda_runtime.h>
@@ -278,10 +279,12 @@ __global__ void bs_insert_kernel(BeamState st) {
       int il = 0, ql = 0;
       if (jl < j1) { sl = st.score[jl]; il = (int)st.cand[jl]; ql = st.candq[jl]; }
       const int m = (int)(j1 - jb < 32 ? j1 - jb : 32);
-      for (int t = 0; t < m; ++t) {
-        const float s = __shfl_sync(0xffffffffu, sl, t);
-        const int id = __shfl_sync(0xffffffffu, il, t);
+      // the queues: runs of candidates of one queue, in order; a run that fits in
+      // the queue's free room is appended at once
+      for (int t = 0; t < m;) {
         const int qi = __shfl_sync(0xffffffffu, ql, t);
+        const unsigned other = __ballot_sync(0xffffffffu, lane < m && ql != qi) & (0xffffffffu << t);
+        const int e = other ? __ffs(other) - 1 : m;  // the run is [t, e)
         if (qi != cur) {
           if (cur >= 0 && lane == 0) st.qsize[(int64_t)b * st.S + cur] = qn;
           cur = qi;
@@ -290,10 +293,50 @@ __global__ void bs_insert_kernel(BeamState st) {
           qn = st.qsize[(int64_t)b * st.S + qi];
           qw = -1;
         }
-        cached_insert(qsc, qid, qn, qw, qws, qwi, st.ef, s, id);
-        // a deleted set keeps its place on the paths but never enters R
-        if (!st.dead || !((st.dead[id >> 5] >> (id & 31)) & 1u))
-          cached_insert(rsc, rid, rn, rw, rws, rwi, st.ef, s, id);
+        if (qn + (e - t) <= st.ef) {
+          if (lane >= t && lane < e) { qsc[qn + lane - t] = sl; qid[qn + lane - t] = il; }
+          qn += e - t;
+          qw = -1;
+          __syncwarp();
+        } else {
+          for (int k = t; k < e; ++k)
+            cached_insert(qsc, qid, qn, qw, qws, qwi, st.ef, __shfl_sync(0xffffffffu, sl, k),
+                          __shfl_sync(0xffffffffu, il, k));
+        }
+        t = e;
+      }
+      // R (a deleted set keeps its place on the paths but never enters R): free
+      // slots are filled in order; once R is full, the worst entry only improves,
+      // so a candidate not better than it now never enters, and the first one
+      // that is better replaces it
+      const bool live = lane < m && (!st.dead || !((st.dead[il >> 5] >> (il & 31)) & 1u));
+      unsigned pend = __ballot_sync(0xffffffffu, live);
+      while (pend) {
+        if (rn < st.ef) {
+          const int rank = __popc(pend & ((1u << lane) - 1u));
+          const bool take = ((pend >> lane) & 1u) && rank < st.ef - rn;
+          if (take) { rsc[rn + rank] = sl; rid[rn + rank] = il; }
+          const unsigned taken = __ballot_sync(0xffffffffu, take);
+          rn += __popc(taken);
+          rw = -1;
+          pend &= ~taken;
+          __syncwarp();
+          continue;
+        }
+        if (rw < 0) {
+          rw = warp_arg(rsc, rid, rn, false);
+          rws = rsc[rw];
+          rwi = rid[rw];
+        }
+        const unsigned better = __ballot_sync(0xffffffffu, ((pend >> lane) & 1u) && bs_better(sl, il, rws, rwi));
+        if (!better) break;
+        const int k = __ffs(better) - 1;
+        const float ks = __shfl_sync(0xffffffffu, sl, k);
+        const int ki = __shfl_sync(0xffffffffu, il, k);
+        if (lane == 0) { rsc[rw] = ks; rid[rw] = ki; }
+        rw = -1;
+        pend &= (k == 31) ? 0u : (0xffffffffu << (k + 1));
+        __syncwarp();
       }
     }
     if (lane == 0) {
