@@ -155,3 +155,20 @@ def test_batched_short_groups_bit_match_on_boundary_lengths(gem):
     ws.close()
     bt.close()
     store.close()
+
+
+def test_batched_codes_below_tensor_core_size_uses_simt_assignment(gem, beam):
+    """A codes-form batch with less than 16,384 query rows of room assigns its
+    query codes with the SIMT kernel (row count read on the device): scores
+    bit-identical to the per-query path over two rounds of different sizes."""
+    bt = gem.Batch(beam["store"], "codes", max_queries=200, max_q_rows=200 * 64 - 1, max_q_len=64,
+                   max_cands=200 * 64, seg=16)
+    for rnd, nq in ((11, 150), (12, 7)):
+        qs, co, ci = _round(beam, rnd, n_queries=nq)
+        assert int(qs.offsets[-1]) < 200 * 64 - 1
+        args = (qs.vecs.cuda(), torch.from_numpy(qs.offsets).cuda(), torch.from_numpy(co).cuda(),
+                torch.from_numpy(ci).cuda())
+        s_graph = bt.run(*args).clone()
+        assert bt.status() == 0
+        assert torch.equal(s_graph, _per_query(gem, beam, qs, co, ci, "codes")), nq
+    bt.close()
