@@ -87,6 +87,20 @@ def test_beam_search_rejects_a_neighbour_out_of_range(gem, setup):
                         torch.from_numpy(gn).cuda(), d["mask"], d["ent"], ef=8)
 
 
+def test_beam_search_rejects_lists_longer_than_max_degree(gem, setup):
+    """The round buffer holds max_degree sets per queue; a popped set with more
+    neighbours to queue than that stops the walk and the call reports it (the
+    writes past the buffer are never made)."""
+    d = setup
+    with pytest.raises(Exception, match="max_degree"):
+        gem.beam_search(d["store"], d["ws"], d["q"], d["qo"], torch.from_numpy(d["go"]).cuda(),
+                        torch.from_numpy(d["gn"]).cuda(), d["mask"], d["ent"], ef=8, max_degree=1)
+    # the workspace stays usable: the same search with the true degree succeeds
+    gem.beam_search(d["store"], d["ws"], d["q"], d["qo"], torch.from_numpy(d["go"]).cuda(),
+                    torch.from_numpy(d["gn"]).cuda(), d["mask"], d["ent"], ef=8)
+    assert d["ws"].status() == 0
+
+
 def test_beam_search_with_deleted_sets_matches_oracle(gem, setup):
     """Lazy deletion (Sec. 4.6): deleted sets, among them every entry set of the
     first query and the best sets R held without deletion, are traversed but never
