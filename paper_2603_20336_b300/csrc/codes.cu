@@ -244,10 +244,11 @@ struct ScanArgs {
   unsigned long long* counter;  // chunk counter, zero at launch
 };
 
-// A warp takes 32 consecutive (query, set) pairs at a time: lane i loads pair
-// i's set rows (one coalesced round for the 32), then the warp walks the pairs
-// with the first 32 codes of the next pair already loaded, gathering eight
-// table rows per step, and lane i keeps pair i's score for one store.
+// A warp takes 32 consecutive (query, set) pairs at a time, claimed in order
+// from a counter: lane i loads pair i's set rows (one coalesced round for the
+// 32), then the warp walks the pairs with the first 32 codes of the next pair
+// already loaded, gathering kScanUnroll table rows per step, and lane i keeps
+// pair i's score for one store.
 constexpr int kScanCtasPerSm = 3;  // resident CTAs of 256 threads at the kernel's 80 registers
 constexpr int kScanUnroll = 16;    // table rows in flight per warp
 

@@ -29,7 +29,6 @@ struct F32Args {
   const int32_t* codes;      // codes form: store codes, centroids and query codes
   const float* centroids;
   const int32_t* qcodes;
-  bool stored_codes;         // id lists, asymmetric codes form: exact query rows
 };
 
 // All sets: one CTA per (segment of kSegDocs sets, query), the query staged in
@@ -182,10 +181,11 @@ gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* 
   a.codes = s->d_codes;
   a.centroids = s->d_codebook;
   a.qcodes = qcodes;
-  a.stored_codes = stored_codes && !qcodes && cand_ids;
+  // id lists, asymmetric codes form: stored rows by their codes, exact query rows
+  const bool asym_codes = stored_codes && !qcodes && cand_ids;
   const int mq = ws->max_q_len;
   // Sim = -(L2 distance) on the exact rows only (the codes forms are inner products)
-  const bool l2 = ws->sim == GEM_SIM_L2 && !qcodes && !a.stored_codes;
+  const bool l2 = ws->sim == GEM_SIM_L2 && !qcodes && !asym_codes;
   int per_sm = 0;
   if (cand_ids == nullptr) {
     const size_t smem = sizeof(float) * ((size_t)mq * kQStride + kF32Warps * kVecBlock * kStageStride + (size_t)kF32Warps * mq);
@@ -199,7 +199,7 @@ gem_status launch_f32_score(const gem_store* s, gem_workspace* ws, const float* 
   } else {
     StreamArgs sa{q, q_offsets, n_queries, cand_offsets, cand_ids, s->d_f32, s->d_offsets, s->n_sets,
                   scores, ws->d_status, mq};
-    const bool coded = qcodes || a.stored_codes;
+    const bool coded = qcodes || asym_codes;
     if (coded) {
       sa.codes = s->d_codes;
       sa.centroids = s->d_codebook;
